@@ -1,0 +1,348 @@
+"""Benchmark of the sampled-space local-energy hot path on GB300.
+
+One step = one pass of the whole path over one batch resident in HBM:
+stage U (membership structure) -> FindCoupledPairs (count + fill, LoopOverTerms)
+-> MatrixElement + ScatterAdd -> E_loc^var (FP32 compensated) -> E^var (FP64)
+-> adjoint (pair-list VJP of L = E^var + sum_x g(x) E_loc^var(x)).
+The Hamiltonian upload (grouping by XY) is set-up and not timed.
+
+Workload (default): 56 qubits (28 orbitals, 14 electrons), ~2.3e5 Pauli terms,
+1e5 peaked unique samples (the configuration the headline metric is quoted
+on).  value = unique samples whose E_loc^var (and gradient) the step produced,
+per second.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "unique-sample E_loc/s at 56 qubits (E_loc^var + E^var + adjoint per step)"
+UNIT = "samples/s"
+L2_FLUSH_BYTES = 512 << 20
+SEARCH_SOURCE = os.path.join(ROOT, "paper_2408_07625_gb300", "csrc", "k_pairs.cu")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pairs_terms_fill_h56.md")
+SM_COUNT, LANES_PER_SM, SM_MAX_GHZ = 152, 128, 2.07
+OPS_PER_PROBE = 4  # algorithmic minimum per (sample, XY) probe: hash XOR, filter address, filter load, bit test
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload_config(inst, ham_info, n_pairs=None):
+    cfg = {"workload": f"{inst.name}: {inst.n_qubits} qubits, {inst.n_alpha + inst.n_beta} electrons, "
+                       f"{inst.n_terms} Pauli terms, {inst.n_unq} peaked unique samples",
+           "n_qubits": inst.n_qubits, "n_terms": int(ham_info["n_terms"]), "n_xy": int(ham_info["n_xy"]),
+           "n_unq": inst.n_unq, "schedule": "terms", "precision": "fp32c",
+           "l2": "flushed between timed steps (512 MiB write); inputs are smaller than L2"}
+    if n_pairs is not None:
+        cfg["n_pairs"] = int(n_pairs)
+    return cfg
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = [r.split(",") for r in out.strip().splitlines() if r.strip()]
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _profile_traffic():
+    """Per-launch DRAM bytes of the search kernel from the committed ncu summary,
+    or None if absent or taken on a different kernel source."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    text = open(PROFILE_SUMMARY).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    if not m or not h:
+        return None
+    cur = hashlib.sha256(open(SEARCH_SOURCE, "rb").read()).hexdigest()
+    return float(m.group(1)) if h.group(1) == cur else None
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def cpu_baseline(inst, seconds=15.0, max_rows=None):
+    """The oracle (pure Python, one core) on the first rows of the same batch."""
+    import oracle
+    t0 = time.time()
+    ro = oracle.RowOracle.from_instance(inst)
+    setup = time.time() - t0
+    done = 0
+    t0 = time.time()
+    while time.time() - t0 < seconds and (max_rows is None or done < max_rows):
+        ro.row(done)
+        done += 1
+    dt = time.time() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"E_loc^var of the first {done} rows of the same batch, LoopOverTerms per row in "
+                      f"pure Python FP64 ({dt:.1f} s; oracle set-up {setup:.1f} s not timed)"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    from synth import config_instance
+    inst = config_instance(args.workload)
+    import oracle
+    ro = oracle.RowOracle.from_instance(inst)
+    rows_per_step = args.ref_rows
+    nxt = 0
+    for _ in range(args.warmup):
+        for _ in range(rows_per_step):
+            ro.row(nxt % inst.n_unq); nxt += 1
+    t0 = time.time()
+    for _ in range(args.steps):
+        for _ in range(rows_per_step):
+            ro.row(nxt % inst.n_unq); nxt += 1
+    dt = time.time() - t0
+    value = args.steps * rows_per_step / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{inst.name}: {inst.n_qubits} qubits, {inst.n_terms} Pauli terms, "
+                                   f"{inst.n_unq} peaked unique samples",
+                       "sample_rows_per_step": rows_per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{rows_per_step} rows of the batch per step (pure Python FP64 oracle, "
+                                       "LoopOverTerms per row)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2408_07625_gb300 as nqs
+    from synth import config_instance
+
+    inst = config_instance(args.workload)
+    ham = nqs.Hamiltonian.from_instance(inst)
+    n = inst.n_unq
+    U_host = torch.from_numpy(np.ascontiguousarray(inst.U).view(np.int64)).pin_memory()
+    a_host = torch.from_numpy(inst.logpsi_re.copy()).pin_memory()
+    U = U_host.to(dev)
+    a = a_host.to(dev)
+    rng = np.random.default_rng(7)
+    g_host = torch.from_numpy(rng.normal(0, 1e-3, size=n)).pin_memory()
+    g = g_host.to(dev)
+    gE = torch.ones(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    prec = args.precision
+    batch = nqs.Batch(ham, U, check=True)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    ev = {k: [] for k in ("stage", "count", "fill", "energy", "evar", "backward")}
+
+    def step(batch_obj, Udev, adev, record=False):
+        marks = []
+        def mark():
+            if record:
+                e = torch.cuda.Event(enable_timing=True); e.record(stream); marks.append(e)
+        mark()
+        batch_obj.restage(Udev)
+        mark()
+        rp, total = nqs.count_pairs(batch_obj)
+        mark()
+        pj, pk = nqs.fill_pairs(batch_obj, rp, total)
+        mark()
+        er, ei, hd = nqs.local_energy(batch_obj, adev, None, (rp, pj, pk), prec)
+        mark()
+        evar = nqs.variational_energy(adev, er)
+        mark()
+        gr, gi = nqs.local_energy_backward(batch_obj, adev, None, er, ei, hd, evar, g, None, gE,
+                                           (rp, pj, pk), prec)
+        mark()
+        return er, evar, gr, total, marks
+
+    for _ in range(args.warmup):
+        step(batch, U, a)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    starts, ends, fills = [], [], []
+    total_pairs = 0
+    for it in range(args.steps):
+        flush.zero_()
+        s0 = torch.cuda.Event(enable_timing=True); s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        er, evar, gr, total_pairs, marks = step(batch, U, a, record=True)
+        s1.record(stream)
+        starts.append(s0); ends.append(s1)
+        fills.append((marks[2], marks[3]))
+        for name, (m0, m1) in zip(ev.keys(), zip(marks[:-1], marks[1:])):
+            ev[name].append((m0, m1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_ms = float(np.sum(step_ms))
+    if ws > 1:
+        t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+        torch.distributed.barrier()
+    ms_per_step = t_ms / args.steps
+    value = ws * n * args.steps / (t_ms * 1e-3)
+    phases = {k: float(np.mean([m0.elapsed_time(m1) for m0, m1 in v])) for k, v in ev.items()}
+    fill_ms = float(np.mean([m0.elapsed_time(m1) for m0, m1 in fills]))
+
+    # e2e: public API with host buffers (H2D of U and log psi, D2H of E_loc, gradient, E^var)
+    out_e = torch.empty(n, dtype=torch.float64).pin_memory()
+    out_g = torch.empty(n, dtype=torch.float64).pin_memory()
+    out_v = torch.empty(3, dtype=torch.float64).pin_memory()
+    U2 = torch.empty_like(U); a2 = torch.empty_like(a)
+    batch2 = nqs.Batch(ham, U, check=True)
+    e_starts, e_ends = [], []
+    for it in range(args.steps):
+        flush.zero_()
+        s0 = torch.cuda.Event(enable_timing=True); s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        U2.copy_(U_host, non_blocking=True)
+        a2.copy_(a_host, non_blocking=True)
+        er, evar, gr, _, _ = step(batch2, U2, a2)
+        out_e.copy_(er, non_blocking=True)
+        out_g.copy_(gr, non_blocking=True)
+        out_v.copy_(evar, non_blocking=True)
+        s1.record(stream)
+        e_starts.append(s0); e_ends.append(s1)
+    torch.cuda.synchronize()
+    e2e_ms = float(np.sum([s.elapsed_time(e) for s, e in zip(e_starts, e_ends)]))
+    if ws > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = ws * n * args.steps / (e2e_ms * 1e-3)
+    h2d = U.numel() * 8 + a.numel() * 8
+    d2h = n * 8 * 2 + 3 * 8
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # FP32C vs FP64 (untimed)
+    r64 = nqs.evaluate(batch, a, None, "fp64")
+    r32 = nqs.evaluate(batch, a, None, "fp32c")
+    err = {"max_abs_dE_loc": float((r64["eloc_re"] - r32["eloc_re"]).abs().max().item()),
+           "abs_dE_var": abs(float(r64["evar"][0].item()) - float(r32["evar"][0].item())),
+           "E_var_fp64": float(r64["evar"][0].item())}
+
+    # roofline of the dominant kernel: the LoopOverTerms search (one launch per fill call)
+    info = ham.info
+    probes = n * (info["n_xy"] - info["has_diag"])
+    achieved = OPS_PER_PROBE * probes / (fill_ms * 1e-3) / 1e12
+    peak = SM_COUNT * LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12
+    roof = {"bound": "alu", "kernel": "pairs_terms_kernel (fill)", "achieved": achieved, "peak": peak,
+            "unit": "Tops/s (integer lane-ops; 4 per sample-XY probe)", "frac": achieved / peak,
+            "traffic": _profile_traffic(), "launch_ms": fill_ms,
+            "peak_source": "derived: 152 SMs x 128 lanes x 2.07 GHz"}
+
+    kernels_per_step = 12  # stage 1, count 1 + scan 3, fill 1, energy 2, evar 1, backward 3
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64+f32c (FP32 compensated, FP64 reduction)",
+            "data": "synthetic (seeded integrals, JW, peaked samples)",
+            "config": _workload_config(inst, info, total_pairs),
+            "pairs_per_s": total_pairs / ((phases["count"] + phases["fill"]) / 2 * 1e-3),
+            "phases_ms": phases, "precision_error": err,
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": kernels_per_step * args.steps,
+            "clocks": clk}
+    peaks, src = _peaks()
+    line["hbm_peak_gbs"] = {"value": peaks.get("hbm_gbs"), "source": src}
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(inst, seconds=args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="h56")
+    p.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--ref-rows", type=int, default=40)
+    args = p.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

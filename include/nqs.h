@@ -1,0 +1,233 @@
+/*
+ * nqs.h -- C ABI of the GB300 (sm_103a) sampled-space local-energy library.
+ *
+ * The library evaluates, for a batch U of unique sampled basis vectors and a
+ * Jordan-Wigner qubit Hamiltonian H = sum_l h_l P^(l) (Eq. jw_hamiltonian),
+ *   - the coupled pairs (x, x') in U x U with x XOR x' equal to one of the
+ *     Hamiltonian's unique XY patterns (FindCoupledPairs, Sec. "Unique XY"
+ *     and Algs. 2A-2C),
+ *   - the matrix elements H_xx' (Eq. pauli_melem and the supplementary
+ *     algorithm "Calculating the Hamiltonian matrix element"),
+ *   - the surrogate local energies E_loc^var(x) = sum_{x' in SC_x}
+ *     H_xx' psi(x')/psi(x) (Eq. local_energy restricted to U, Fig.
+ *     scatter_local_energies),
+ *   - the variational energy E^var (Eq. variational_energy), and
+ *   - the vector-Jacobian product of E_loc^var and E^var with respect to
+ *     log psi (the adjoint; Eq. grad_def is its special case).
+ *
+ * Conventions shared by every call
+ *   - Bit vectors: an N-qubit vector is W = ceil(N/64) uint64 words; qubit i
+ *     is bit (i % 64) of word (i / 64).  A batch is row-major [n][W].
+ *     Bits at positions >= N must be zero.
+ *   - Pauli strings are given in the symplectic encoding (x, z): qubit i
+ *     carries I (0,0), X (1,0), Y (1,1) or Z (0,1).  So the paper's
+ *     XY^(l) = x, Y^(l) = x AND z, YZ^(l) = z.
+ *   - Amplitudes enter as log psi = a + i b (two real FP64 arrays; b may be
+ *     NULL for real, positive amplitudes).
+ *   - "device" pointers are CUDA device (or managed) memory of the current
+ *     device; "host" pointers are ordinary host memory.  The caller owns
+ *     every buffer it passes; the library never frees caller memory.
+ *   - Every call that takes a stream enqueues its kernels on that stream
+ *     (cudaStream_t passed as void*; NULL = legacy default stream).  Calls
+ *     that return a count to the host synchronise that stream; all others
+ *     are asynchronous and perform no host synchronisation.
+ *   - Return value: NQS_OK (0) or a negative NQS_ERR_* code.  A failing call
+ *     leaves caller buffers unspecified but valid; nqs_last_error() gives a
+ *     thread-local message.  No call aborts the process or traps the GPU:
+ *     device-side problems (repeated samples, bounded loops running out) are
+ *     recorded in a status word and reported by the next synchronising call
+ *     or by nqs_stage_status().
+ *   - Scope of version 1: real Hamiltonians (every string has an even number
+ *     of Y, real h_l; molecular Hamiltonians are of this kind); complex log
+ *     psi is supported; 1 <= N <= 256.
+ */
+#ifndef NQS_H
+#define NQS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NQS_VERSION 100
+
+enum {
+    NQS_OK = 0,
+    NQS_ERR_ARG = -1,          /* bad argument (null pointer, size, range)          */
+    NQS_ERR_UNSUPPORTED = -2,  /* outside the scope above (odd |Y|, N > 256)        */
+    NQS_ERR_CUDA = -3,         /* a CUDA runtime call failed                        */
+    NQS_ERR_CAPACITY = -4,     /* output buffer too small; required size returned  */
+    NQS_ERR_DUPLICATE = -5,    /* the sample batch repeats a basis vector           */
+    NQS_ERR_DEVICE_LIMIT = -6, /* a bounded device loop ran out (corrupt input)     */
+    NQS_ERR_OOM = -7,          /* device allocation inside nqs_ham_load failed      */
+    NQS_ERR_RANGE = -8         /* an amplitude ratio leaves the FP32 exponent range */
+};
+
+enum {
+    NQS_SCHED_AUTO = 0,   /* library's choice                                      */
+    NQS_SCHED_TERMS = 1,  /* loop over unique XY per sample (Alg. 2A)               */
+    NQS_SCHED_BATCH = 2,  /* loop over the batch per sample (Alg. 2B)               */
+    NQS_SCHED_TRIE = 3    /* joint prefix-tree traversal (Algs. 3 and 2C)          */
+};
+
+enum {
+    NQS_PREC_FP64 = 0,    /* FP64 arithmetic throughout                             */
+    NQS_PREC_FP32C = 1    /* FP32 with compensated (double-float) accumulation;     */
+                          /* FP64 for the final energy reduction                    */
+};
+
+typedef struct nqs_ham nqs_ham;
+
+/* ---------------------------------------------------------------------------
+ * Hamiltonian (Sec. "Preparation", Fig. ham_prep; Eq. xy_to_yz_set)
+ * ------------------------------------------------------------------------- */
+
+/* Copy n_terms Pauli strings to the current device, grouped by XY pattern.
+ *   x_mask, z_mask : host, [n_terms][W] uint64, symplectic encoding.
+ *   coef           : host, [n_terms] FP64 real coefficients h_l.
+ * Identical strings are merged (coefficients summed); terms whose merged
+ * coefficient is exactly zero are dropped.  Errors: NQS_ERR_ARG (n_qubits
+ * out of range, bits >= N set, null pointer), NQS_ERR_UNSUPPORTED (a term
+ * with an odd number of Y), NQS_ERR_OOM, NQS_ERR_CUDA.  On success *out
+ * owns the device tables until nqs_ham_free. */
+int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask,
+                 const uint64_t* z_mask, const double* coef, nqs_ham** out);
+
+/* Release the tables of nqs_ham_load (NULL is accepted). */
+int nqs_ham_free(nqs_ham* ham);
+
+/* Sizes after merging: info[0] = N, [1] = W, [2] = terms, [3] = unique XY
+ * patterns, [4] = 1 if the XY = 0 (diagonal) pattern exists, [5] = size of
+ * the largest P_XY, [6] = number of search-table slots (with padding). */
+int nqs_ham_info(const nqs_ham* ham, int64_t info[8]);
+
+/* Host copy of the grouped tables (any pointer may be NULL):
+ *   xy      [n_xy][W]   unique XY patterns, in library order
+ *   row_ptr [n_xy+1]    P_XY of pattern m = terms row_ptr[m] .. row_ptr[m+1]-1
+ *   yz      [terms][W]  YZ^(l) (= z mask) per grouped term
+ *   coef    [terms]     h_l * i^{|Y^(l)|} (real, since |Y| is even)           */
+int nqs_ham_export(const nqs_ham* ham, uint64_t* xy, int64_t* row_ptr,
+                   uint64_t* yz, double* coef);
+
+/* ---------------------------------------------------------------------------
+ * Batch workspace and sample staging: the membership structure of U used by
+ * the test "x' in U" of Algs. 2A-2C (Sec. "Unique XY"), plus per-sample
+ * scratch used by the energy and adjoint calls.
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of the batch workspace for n_unq samples (device memory, 256-byte
+ * aligned, caller-owned; one workspace per batch and stream). */
+int64_t nqs_stage_bytes(const nqs_ham* ham, int64_t n_unq);
+
+/* Build the membership structure of U (device [n_unq][W]) in work.  U must
+ * stay unchanged while the workspace is in use.  If check != 0 the call
+ * synchronises the stream and returns NQS_ERR_DUPLICATE if U repeats a
+ * vector, NQS_ERR_ARG if a sample has bits >= N.  With check == 0 it is
+ * asynchronous and the same conditions are reported by nqs_stage_status(). */
+int nqs_stage(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, void* work,
+              int64_t work_bytes, int check, void* stream);
+
+/* Synchronise the stream and return the workspace's status: NQS_OK or the
+ * first of NQS_ERR_DUPLICATE, NQS_ERR_ARG (bits >= N), NQS_ERR_DEVICE_LIMIT,
+ * NQS_ERR_RANGE recorded by device code since nqs_stage. */
+int nqs_stage_status(const void* work, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * FindCoupledPairs (Sec. "FindCoupledPairs implementations")
+ * Output: CSR over the rows [row_begin, row_end) of U:
+ *   row_ptr[r - row_begin] .. row_ptr[r - row_begin + 1] - 1 index the pairs
+ *   of row r; pair_j = column (index into U), pair_k = pattern index (into
+ *   the library's unique-XY table).  Within a row the diagonal pair comes
+ *   first (if the XY = 0 pattern exists), then pairs whose P_XY is large,
+ *   then the rest, in a fixed order.  Both (i, j) and (j, i) are listed.
+ * All calls need a workspace staged with the same U.  Readers of the CSR
+ * (fill, energy, adjoint) take positions relative to row_ptr[0], so a slice
+ * row_ptr + (r0 - row_begin) of a larger offset array can be passed for the
+ * sub-range [r0, r1) together with pair arrays that start at that slice's
+ * first pair.
+ * ------------------------------------------------------------------------- */
+
+/* Count pass: row_ptr (device int64 [row_end-row_begin+1]) receives the CSR
+ * offsets, *n_pairs (host) the total.  Synchronises the stream; returns the
+ * workspace status if device code recorded a problem. */
+int nqs_count_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
+                            void* work, int64_t row_begin, int64_t row_end,
+                            int schedule, int64_t* row_ptr, int64_t* n_pairs,
+                            void* stream);
+
+/* Fill pass for offsets from nqs_count_coupled_pairs with the same arguments:
+ * pair_j, pair_k device uint32 [row_ptr[last]].  Asynchronous. */
+int nqs_fill_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
+                           void* work, int64_t row_begin, int64_t row_end,
+                           int schedule, const int64_t* row_ptr, uint32_t* pair_j,
+                           uint32_t* pair_k, void* stream);
+
+/* Count + fill.  If capacity < total the call returns NQS_ERR_CAPACITY with
+ * row_ptr and *n_pairs valid and nothing written to pair_j/pair_k. */
+int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
+                           void* work, int64_t row_begin, int64_t row_end,
+                           int schedule, int64_t* row_ptr, uint32_t* pair_j,
+                           uint32_t* pair_k, int64_t capacity, int64_t* n_pairs,
+                           void* stream);
+
+/* ---------------------------------------------------------------------------
+ * MatrixElement + ScatterAdd -> E_loc^var (Sec. "MatrixElement
+ * implementation", Fig. scatter_local_energies)
+ * ------------------------------------------------------------------------- */
+
+/* For rows r in [row_begin, row_end), with their pairs from a fill pass over
+ * the same range, write
+ *   eloc_re[r], eloc_im[r] = E_loc^var(U_r)  (eloc_im may be NULL only if
+ *                                              logpsi_im is NULL),
+ *   hdiag[r] = H_{U_r U_r} (may be NULL).
+ * logpsi_re/_im: device FP64 [n_unq] for the whole batch.  Each row is a
+ * fixed-order reduction, so results are bitwise reproducible.  The call
+ * overwrites the per-sample scratch of work.  Asynchronous. */
+int nqs_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, void* work,
+                     const double* logpsi_re, const double* logpsi_im,
+                     int64_t row_begin, int64_t row_end, const int64_t* row_ptr,
+                     const uint32_t* pair_j, const uint32_t* pair_k, int precision,
+                     double* eloc_re, double* eloc_im, double* hdiag, void* stream);
+
+/* E^var = sum_x p(x) Re E_loc^var(x) / sum_x p(x) with p = exp(2 a) over the
+ * whole batch (Eq. variational_energy), FP64, deterministic.  Writes
+ * out[0] = E^var, out[1] = max a, out[2] = sum_x exp(2 (a - max a)) (device
+ * FP64 [3]).  Asynchronous. */
+int nqs_variational_energy(int64_t n_unq, const double* logpsi_re, const double* eloc_re,
+                           double* out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Adjoint: gradient of L = sum_x [g_re(x) Re E_loc(x) + g_im(x) Im E_loc(x)]
+ *          + g_evar E^var with respect to (Re log psi, Im log psi).
+ * For rows y in [row_begin, row_end) (pairs of those rows) writes
+ * grad_re[y], grad_im[y] (grad_im may be NULL if logpsi_im is NULL).
+ *   eloc_re/_im, hdiag: the forward results for the WHOLE batch.
+ *   evar: device FP64 [3] from nqs_variational_energy.
+ *   g_eloc_re/_im: device FP64 [n_unq] or NULL (zero upstream).
+ *   g_evar: device FP64 [1] or NULL (zero).
+ * With both g_eloc arrays NULL no pair data is read (row_ptr may be NULL)
+ * and the result is the closed form 2 w_y (E_loc(y) - E) g_evar.  The sum
+ * over x of each pair (x, y) is evaluated on row y, which lists the same
+ * pairs because x XOR y is symmetric and H is real symmetric.
+ * Asynchronous. */
+int nqs_local_energy_backward(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
+                              void* work, const double* logpsi_re, const double* logpsi_im,
+                              int64_t row_begin, int64_t row_end, const int64_t* row_ptr,
+                              const uint32_t* pair_j, const uint32_t* pair_k,
+                              const double* eloc_re, const double* eloc_im,
+                              const double* hdiag, const double* evar,
+                              const double* g_eloc_re, const double* g_eloc_im,
+                              const double* g_evar, int precision,
+                              double* grad_re, double* grad_im, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Misc
+ * ------------------------------------------------------------------------- */
+const char* nqs_last_error(void);   /* thread-local message of the last error */
+int nqs_version(void);              /* NQS_VERSION                               */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NQS_H */

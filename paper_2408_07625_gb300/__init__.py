@@ -1,0 +1,401 @@
+"""Python binding of the GB300 sampled-space local-energy library (libnqs.so).
+
+Argument marshalling only: every step of the path (staging, FindCoupledPairs,
+MatrixElement, ScatterAdd, E^var, adjoint) runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if the library is missing, importing the binding's entry points
+raises.
+
+Names follow the paper: ``coupled_pairs`` is FindCoupledPairs, ``local_energy``
+returns E_loc^var (Eq. local_energy restricted to the sampled batch),
+``variational_energy`` returns E^var (Eq. variational_energy).
+"""
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+__all__ = ["NQSError", "load_library", "Hamiltonian", "Batch", "coupled_pairs",
+           "local_energy", "variational_energy", "local_energy_backward", "LocalEnergy",
+           "evaluate", "SCHEDULES", "PRECISIONS", "library_path"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "libnqs.so")
+
+SCHEDULES = {"auto": 0, "terms": 1, "batch": 2, "trie": 3}
+PRECISIONS = {"fp64": 0, "fp32c": 1}
+
+_c_i64p = ctypes.POINTER(ctypes.c_int64)
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int
+
+
+class NQSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"nqs error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = None):
+    """Load libnqs.so (built by ``paper_2408_07625_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or library_path
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_2408_07625_gb300.build` (no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "nqs_ham_load": (_i32, [_i32, _i64, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+        "nqs_ham_free": (_i32, [_vp]),
+        "nqs_ham_info": (_i32, [_vp, _c_i64p]),
+        "nqs_ham_export": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+        "nqs_stage_bytes": (_i64, [_vp, _i64]),
+        "nqs_stage": (_i32, [_vp, _vp, _i64, _vp, _i64, _i32, _vp]),
+        "nqs_stage_status": (_i32, [_vp, _vp]),
+        "nqs_count_coupled_pairs": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _vp, _c_i64p, _vp]),
+        "nqs_fill_coupled_pairs": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _vp, _vp, _vp, _vp]),
+        "nqs_find_coupled_pairs": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _vp, _vp, _vp, _i64,
+                                          _c_i64p, _vp]),
+        "nqs_local_energy": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _i32,
+                                    _vp, _vp, _vp, _vp]),
+        "nqs_variational_energy": (_i32, [_i64, _vp, _vp, _vp, _vp]),
+        "nqs_local_energy_backward": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp,
+                                             _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp]),
+        "nqs_last_error": (ctypes.c_char_p, []),
+        "nqs_version": (_i32, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise NQSError(rc, _lib.nqs_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+_EMPTY = {}
+
+
+def _pair_ptr(t):
+    """Pointer of a pair array; an empty list still passes a valid (unread) buffer."""
+    if t is None:
+        return None
+    if t.numel() == 0:
+        key = t.device
+        if key not in _EMPTY:
+            _EMPTY[key] = torch.zeros(1, dtype=torch.int32, device=t.device)
+        return ctypes.c_void_p(_EMPTY[key].data_ptr())
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_u64(U):
+    """U as a contiguous int64 CUDA tensor [n, W] holding the uint64 words."""
+    if isinstance(U, np.ndarray):
+        U = torch.from_numpy(np.ascontiguousarray(U.astype(np.uint64)).view(np.int64))
+    if U.dtype not in (torch.int64, torch.uint64):
+        raise TypeError("U must hold 64-bit words")
+    if U.dtype == torch.uint64:
+        U = U.view(torch.int64)
+    if U.dim() == 1:
+        U = U[:, None]
+    if not U.is_cuda:
+        U = U.cuda()
+    return U.contiguous()
+
+
+def _f64(t, device):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        t = torch.from_numpy(np.ascontiguousarray(t, dtype=np.float64))
+    return t.to(device=device, dtype=torch.float64).contiguous()
+
+
+class Hamiltonian:
+    """Pauli strings (symplectic x/z masks, real coefficients) grouped by XY on the GPU.
+
+    Follows Sec. "Preparation" (Fig. ham_prep): unique XY patterns, the sets
+    P_XY (Eq. xy_to_yz_set) and their term tables.
+    """
+
+    def __init__(self, x_mask, z_mask, coef, n_qubits: int):
+        lib = load_library()
+        x = np.ascontiguousarray(np.asarray(x_mask, dtype=np.uint64))
+        z = np.ascontiguousarray(np.asarray(z_mask, dtype=np.uint64))
+        c = np.ascontiguousarray(np.asarray(coef, dtype=np.float64).ravel())
+        W = max(1, (int(n_qubits) + 63) // 64)
+        x = x.reshape(-1, W)
+        z = z.reshape(-1, W)
+        if not (x.shape[0] == z.shape[0] == c.shape[0]):
+            raise ValueError("mask/coef lengths differ")
+        h = ctypes.c_void_p()
+        _check(lib.nqs_ham_load(int(n_qubits), int(c.shape[0]), x.ctypes.data, z.ctypes.data,
+                                c.ctypes.data, ctypes.byref(h)))
+        self._h = h
+        self.n_qubits = int(n_qubits)
+        info = (ctypes.c_int64 * 8)()
+        _check(lib.nqs_ham_info(h, info))
+        self.info = {"n_qubits": info[0], "n_words": info[1], "n_terms": info[2], "n_xy": info[3],
+                     "has_diag": info[4], "max_group": info[5], "n_search": info[6],
+                     "heavy_end": info[7]}
+        self.n_words = int(info[1])
+
+    @property
+    def handle(self):
+        return self._h
+
+    def export(self):
+        """Host copies of the grouped tables: (xy [n_xy, W], row_ptr, yz [T, W], coef)."""
+        W, nxy, T = self.n_words, self.info["n_xy"], self.info["n_terms"]
+        xy = np.zeros((nxy, W), np.uint64)
+        rp = np.zeros(nxy + 1, np.int64)
+        yz = np.zeros((T, W), np.uint64)
+        cf = np.zeros(T, np.float64)
+        _check(_lib.nqs_ham_export(self._h, xy.ctypes.data, rp.ctypes.data, yz.ctypes.data, cf.ctypes.data))
+        return xy, rp, yz, cf
+
+    @classmethod
+    def from_instance(cls, inst):
+        return cls(inst.x_mask, inst.z_mask, inst.coef, inst.n_qubits)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.nqs_ham_free(self._h)
+            self._h = None
+
+
+class Batch:
+    """A staged batch of unique samples U (device) with its workspace."""
+
+    def __init__(self, ham: Hamiltonian, U, check: bool = True, stream=None):
+        self.ham = ham
+        self.U = _dev_u64(U)
+        if self.U.shape[1] != ham.n_words:
+            raise ValueError("U word count does not match the Hamiltonian")
+        self.n = int(self.U.shape[0])
+        self.device = self.U.device
+        nbytes = int(_lib.nqs_stage_bytes(ham.handle, self.n))
+        if nbytes < 0:
+            _check(nbytes)
+        self.work = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        _check(_lib.nqs_stage(ham.handle, _ptr(self.U), self.n, _ptr(self.work), nbytes,
+                              1 if check else 0, _stream(stream)))
+
+    def restage(self, U=None, check: bool = False, stream=None):
+        """Rebuild the membership structure (for new contents of U, same size)."""
+        if U is not None:
+            U = _dev_u64(U)
+            if tuple(U.shape) != tuple(self.U.shape):
+                raise ValueError("restage needs a batch of the same shape")
+            self.U = U
+        _check(_lib.nqs_stage(self.ham.handle, _ptr(self.U), self.n, _ptr(self.work), self.work.numel(),
+                              1 if check else 0, _stream(stream)))
+
+    def status(self, stream=None):
+        _check(_lib.nqs_stage_status(_ptr(self.work), _stream(stream)))
+
+
+def count_pairs(batch: Batch, row_begin=0, row_end=None, schedule="terms", stream=None):
+    row_end = batch.n if row_end is None else int(row_end)
+    row_ptr = torch.empty(row_end - row_begin + 1, dtype=torch.int64, device=batch.device)
+    n = ctypes.c_int64()
+    _check(_lib.nqs_count_coupled_pairs(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work),
+                                        int(row_begin), row_end, SCHEDULES[schedule], _ptr(row_ptr),
+                                        ctypes.byref(n), _stream(stream)))
+    return row_ptr, int(n.value)
+
+
+def fill_pairs(batch: Batch, row_ptr, n_pairs, row_begin=0, row_end=None, schedule="terms", stream=None):
+    row_end = batch.n if row_end is None else int(row_end)
+    pj = torch.empty(max(n_pairs, 1), dtype=torch.int32, device=batch.device)
+    pk = torch.empty(max(n_pairs, 1), dtype=torch.int32, device=batch.device)
+    _check(_lib.nqs_fill_coupled_pairs(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work),
+                                       int(row_begin), row_end, SCHEDULES[schedule], _ptr(row_ptr),
+                                       _pair_ptr(pj), _pair_ptr(pk), _stream(stream)))
+    return pj[:n_pairs], pk[:n_pairs]
+
+
+def coupled_pairs(batch: Batch, row_begin=0, row_end=None, schedule="terms", stream=None):
+    """FindCoupledPairs over rows [row_begin, row_end): CSR (row_ptr, j, k) as CUDA tensors.
+
+    ``j`` and ``k`` are int32 tensors holding uint32 column and pattern indices.
+    """
+    row_ptr, n = count_pairs(batch, row_begin, row_end, schedule, stream)
+    pj, pk = fill_pairs(batch, row_ptr, n, row_begin, row_end, schedule, stream)
+    return row_ptr, pj, pk
+
+
+def local_energy(batch: Batch, logpsi_re, logpsi_im=None, pairs=None, precision="fp32c",
+                 row_begin=0, row_end=None, out=None, stream=None):
+    """E_loc^var for rows [row_begin, row_end) from their CSR pairs.
+
+    Returns (eloc_re, eloc_im or None, hdiag), full-length tensors of which the
+    rows in range are written.
+    """
+    row_end = batch.n if row_end is None else int(row_end)
+    dev = batch.device
+    a = _f64(logpsi_re, dev)
+    b = _f64(logpsi_im, dev)
+    if pairs is None:
+        pairs = coupled_pairs(batch, row_begin, row_end, stream=stream)
+    rp, pj, pk = pairs
+    if out is None:
+        er = torch.zeros(batch.n, dtype=torch.float64, device=dev)
+        ei = torch.zeros(batch.n, dtype=torch.float64, device=dev) if b is not None else None
+        hd = torch.zeros(batch.n, dtype=torch.float64, device=dev)
+    else:
+        er, ei, hd = out
+    _check(_lib.nqs_local_energy(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work), _ptr(a), _ptr(b),
+                                 int(row_begin), row_end, _ptr(rp), _pair_ptr(pj), _pair_ptr(pk),
+                                 PRECISIONS[precision], _ptr(er), _ptr(ei), _ptr(hd), _stream(stream)))
+    return er, ei, hd
+
+
+def variational_energy(logpsi_re, eloc_re, out=None, stream=None):
+    """E^var (Eq. variational_energy) as a device tensor [E, max Re log psi, sum of weights]."""
+    a = _f64(logpsi_re, eloc_re.device)
+    if out is None:
+        out = torch.empty(3, dtype=torch.float64, device=eloc_re.device)
+    _check(_lib.nqs_variational_energy(int(a.shape[0]), _ptr(a), _ptr(eloc_re), _ptr(out), _stream(stream)))
+    return out
+
+
+def local_energy_backward(batch: Batch, logpsi_re, logpsi_im, eloc_re, eloc_im, hdiag, evar,
+                          g_eloc_re=None, g_eloc_im=None, g_evar=None, pairs=None, precision="fp32c",
+                          row_begin=0, row_end=None, out=None, stream=None):
+    """Gradient of sum g_re Re E_loc + g_im Im E_loc + g_E E^var w.r.t. (Re, Im) log psi."""
+    row_end = batch.n if row_end is None else int(row_end)
+    dev = batch.device
+    a = _f64(logpsi_re, dev)
+    b = _f64(logpsi_im, dev)
+    if (g_eloc_re is not None or g_eloc_im is not None) and pairs is None:
+        pairs = coupled_pairs(batch, row_begin, row_end, stream=stream)
+    rp, pj, pk = pairs if pairs is not None else (None, None, None)
+    if out is None:
+        gr = torch.zeros(batch.n, dtype=torch.float64, device=dev)
+        gi = torch.zeros(batch.n, dtype=torch.float64, device=dev) if b is not None else None
+    else:
+        gr, gi = out
+    _check(_lib.nqs_local_energy_backward(
+        batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work), _ptr(a), _ptr(b), int(row_begin), row_end,
+        _ptr(rp), _pair_ptr(pj), _pair_ptr(pk), _ptr(eloc_re), _ptr(eloc_im), _ptr(hdiag), _ptr(evar),
+        _ptr(_f64(g_eloc_re, dev)), _ptr(_f64(g_eloc_im, dev)), _ptr(_f64(g_evar, dev)),
+        PRECISIONS[precision], _ptr(gr), _ptr(gi), _stream(stream)))
+    return gr, gi
+
+
+def _row_chunks(row_ptr_host, max_pairs):
+    """Split rows into contiguous ranges holding at most max_pairs pairs each."""
+    n = len(row_ptr_host) - 1
+    chunks, start = [], 0
+    while start < n:
+        limit = row_ptr_host[start] + max_pairs
+        end = int(np.searchsorted(row_ptr_host, limit, side="right")) - 1
+        end = max(end, start + 1)
+        end = min(end, n)
+        chunks.append((start, end))
+        start = end
+    return chunks
+
+
+def evaluate(batch: Batch, logpsi_re, logpsi_im=None, precision="fp32c", schedule="terms",
+             max_pairs=None, keep_pairs=True, stream=None):
+    """Whole forward path: pairs (chunked by rows under ``max_pairs``), E_loc^var, E^var.
+
+    Returns dict(eloc_re, eloc_im, hdiag, evar, n_pairs, pairs or None, chunks).
+    """
+    dev = batch.device
+    a = _f64(logpsi_re, dev)
+    b = _f64(logpsi_im, dev)
+    row_ptr, total = count_pairs(batch, 0, batch.n, schedule, stream)
+    er = torch.zeros(batch.n, dtype=torch.float64, device=dev)
+    ei = torch.zeros(batch.n, dtype=torch.float64, device=dev) if b is not None else None
+    hd = torch.zeros(batch.n, dtype=torch.float64, device=dev)
+    rp_host = None
+    if max_pairs is None or total <= max_pairs:
+        chunks = [(0, batch.n)]
+    else:
+        rp_host = row_ptr.cpu().numpy()
+        chunks = _row_chunks(rp_host, int(max_pairs))
+    kept = None
+    for (r0, r1) in chunks:
+        rp = row_ptr[r0:r1 + 1]
+        npairs = total if rp_host is None else int(rp_host[r1] - rp_host[r0])
+        pj, pk = fill_pairs(batch, rp, npairs, r0, r1, schedule, stream)
+        local_energy(batch, a, b, (rp, pj, pk), precision, r0, r1, (er, ei, hd), stream)
+        if len(chunks) == 1 and keep_pairs:
+            kept = (rp, pj, pk)
+    evar = variational_energy(a, er, stream=stream)
+    return {"eloc_re": er, "eloc_im": ei, "hdiag": hd, "evar": evar, "n_pairs": total,
+            "pairs": kept, "chunks": chunks, "row_ptr": row_ptr, "row_ptr_host": rp_host,
+            "schedule": schedule}
+
+
+class LocalEnergy(torch.autograd.Function):
+    """(E_loc^var re, E_loc^var im, E^var) as a differentiable function of log psi.
+
+    ``forward(ctx, batch, logpsi_re, logpsi_im, precision, max_pairs)``; pass
+    ``logpsi_im=None`` for real amplitudes (then the second output is zeros).
+    The pair list is kept for the backward pass when it fits under
+    ``max_pairs``; otherwise the backward pass recomputes it row chunk by row
+    chunk.
+    """
+
+    @staticmethod
+    def forward(ctx, batch, logpsi_re, logpsi_im, precision="fp32c", max_pairs=None):
+        res = evaluate(batch, logpsi_re.detach(), None if logpsi_im is None else logpsi_im.detach(),
+                       precision, "terms", max_pairs, keep_pairs=True)
+        ctx.batch, ctx.precision, ctx.max_pairs = batch, precision, max_pairs
+        ctx.res = res
+        ctx.cplx = logpsi_im is not None
+        ctx.save_for_backward(logpsi_re, logpsi_im if logpsi_im is not None else logpsi_re)
+        ei = res["eloc_im"] if res["eloc_im"] is not None else torch.zeros_like(res["eloc_re"])
+        return res["eloc_re"], ei, res["evar"][0]
+
+    @staticmethod
+    def backward(ctx, g_er, g_ei, g_e):
+        lre, lim = ctx.saved_tensors
+        lim = lim if ctx.cplx else None
+        res, batch = ctx.res, ctx.batch
+        g_er = None if g_er is None else g_er.contiguous()
+        g_ei = None if (g_ei is None or not ctx.cplx) else g_ei.contiguous()
+        g_e = None if g_e is None else g_e.reshape(1).to(torch.float64).contiguous()
+        need_pairs = g_er is not None or g_ei is not None
+        if not need_pairs or res["pairs"] is not None:
+            gr, gi = local_energy_backward(batch, lre, lim, res["eloc_re"], res["eloc_im"], res["hdiag"],
+                                           res["evar"], g_er, g_ei, g_e, res["pairs"], ctx.precision)
+        else:
+            gr = torch.zeros(batch.n, dtype=torch.float64, device=batch.device)
+            gi = torch.zeros(batch.n, dtype=torch.float64, device=batch.device) if ctx.cplx else None
+            row_ptr, rp_host = res["row_ptr"], res["row_ptr_host"]
+            if rp_host is None:
+                rp_host = row_ptr.cpu().numpy()
+            for (r0, r1) in res["chunks"]:
+                rp = row_ptr[r0:r1 + 1]
+                npairs = int(rp_host[r1] - rp_host[r0])
+                pj, pk = fill_pairs(batch, rp, npairs, r0, r1, res["schedule"])
+                local_energy_backward(batch, lre, lim, res["eloc_re"], res["eloc_im"], res["hdiag"],
+                                      res["evar"], g_er, g_ei, g_e, (rp, pj, pk), ctx.precision,
+                                      r0, r1, (gr, gi))
+        return None, gr, gi, None, None

@@ -1,0 +1,498 @@
+// C ABI entry points and host-side preparation (Sec. "Preparation", Fig. ham_prep).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "nqs_internal.cuh"
+
+namespace nqs {
+
+static thread_local std::string g_error;
+
+void set_error(const std::string& msg) { g_error = msg; }
+
+int fail(int code, const std::string& msg) {
+  g_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return NQS_ERR_CUDA;
+}
+
+int num_sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+static inline int64_t align256(int64_t v) { return (v + 255) & ~int64_t(255); }
+
+static inline int64_t next_pow2(int64_t v) {
+  int64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+StageHeader stage_layout(const nqs_ham* ham, int64_t n) {
+  StageHeader L;
+  std::memset(&L, 0, sizeof(L));
+  L.magic = kStageMagic;
+  L.n_unq = n;
+  L.W = ham->W;
+  L.cap = next_pow2(std::max<int64_t>(2 * n, 64));
+  L.nwords = std::min<int64_t>(std::max<int64_t>(next_pow2(std::max<int64_t>(n / 2, 1)), 32), 32768);
+  int64_t off = align256(sizeof(StageHeader));
+  L.off_hx = off;     off = align256(off + 4 * std::max<int64_t>(n, 1));
+  L.off_table = off;  off = align256(off + 4 * L.cap);
+  L.off_bloom = off;  off = align256(off + 4 * L.nwords);
+  L.scan_blocks = (std::max<int64_t>(n, 1) + 1023) / 1024 + 1;
+  L.off_scan = off;   off = align256(off + 8 * L.scan_blocks);
+  L.off_ampP = off;   off = align256(off + 16 * std::max<int64_t>(n, 1));
+  L.off_ampQ = off;   off = align256(off + 16 * std::max<int64_t>(n, 1));
+  L.off_ampK = off;   off = align256(off + 4 * std::max<int64_t>(n, 1));
+  L.off_geff = off;   off = align256(off + 16 * std::max<int64_t>(n, 1));
+  L.total_bytes = off;
+  return L;
+}
+
+// --------------------------------------------------------------------------
+// Hamiltonian preparation
+// --------------------------------------------------------------------------
+
+static uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static int popc_words(const uint64_t* v, int W) {
+  int c = 0;
+  for (int w = 0; w < W; ++w) c += __builtin_popcountll(v[w]);
+  return c;
+}
+
+static bool words_less(const uint64_t* a, const uint64_t* b, int W) {
+  for (int w = W - 1; w >= 0; --w)
+    if (a[w] != b[w]) return a[w] < b[w];
+  return false;
+}
+
+static bool words_equal(const uint64_t* a, const uint64_t* b, int W) {
+  for (int w = 0; w < W; ++w)
+    if (a[w] != b[w]) return false;
+  return true;
+}
+
+template <typename T>
+static int upload(T** dst, const std::vector<T>& src) {
+  size_t bytes = std::max<size_t>(src.size(), 1) * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)dst, bytes);
+  if (e != cudaSuccess) return fail(NQS_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  if (!src.empty()) {
+    e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy (ham tables)");
+  }
+  return NQS_OK;
+}
+
+static void free_ham(nqs_ham* h) {
+  if (!h) return;
+  cudaFree(h->xy); cudaFree(h->row_ptr); cudaFree(h->yz); cudaFree(h->coef);
+  cudaFree(h->coef_f); cudaFree(h->srch_hash); cudaFree(h->srch_id); cudaFree(h->hash_basis);
+  delete h;
+}
+
+}  // namespace nqs
+
+using namespace nqs;
+
+extern "C" {
+
+const char* nqs_last_error(void) { return g_error.c_str(); }
+int nqs_version(void) { return NQS_VERSION; }
+
+int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const uint64_t* z_mask,
+                 const double* coef, nqs_ham** out) {
+  if (!out) return fail(NQS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_qubits < 1) return fail(NQS_ERR_ARG, "n_qubits must be >= 1");
+  if (n_qubits > 64 * kMaxWords) return fail(NQS_ERR_UNSUPPORTED, "n_qubits > 256");
+  if (n_terms < 0) return fail(NQS_ERR_ARG, "n_terms < 0");
+  if (n_terms > 0 && (!x_mask || !z_mask || !coef)) return fail(NQS_ERR_ARG, "null term array");
+  if (n_terms >= (int64_t(1) << 31)) return fail(NQS_ERR_UNSUPPORTED, "more than 2^31 terms");
+  const int W = (n_qubits + 63) / 64;
+  const int tail = n_qubits - 64 * (W - 1);
+  const uint64_t tail_mask = tail == 64 ? ~0ull : ((1ull << tail) - 1);
+
+  for (int64_t t = 0; t < n_terms; ++t) {
+    if ((x_mask[t * W + W - 1] & ~tail_mask) || (z_mask[t * W + W - 1] & ~tail_mask))
+      return fail(NQS_ERR_ARG, "term " + std::to_string(t) + " has bits >= n_qubits");
+    if (!std::isfinite(coef[t])) return fail(NQS_ERR_ARG, "non-finite coefficient");
+  }
+
+  // merge identical (x, z) strings: stable sort keeps input order inside a key
+  std::vector<int64_t> idx(n_terms);
+  std::iota(idx.begin(), idx.end(), 0);
+  auto key_less = [&](int64_t a, int64_t b) {
+    const uint64_t* xa = x_mask + a * W; const uint64_t* xb = x_mask + b * W;
+    if (!words_equal(xa, xb, W)) return words_less(xa, xb, W);
+    return words_less(z_mask + a * W, z_mask + b * W, W);
+  };
+  std::stable_sort(idx.begin(), idx.end(), key_less);
+  struct Merged { int64_t first; double h; };
+  std::vector<Merged> merged;
+  for (int64_t a = 0; a < n_terms;) {
+    int64_t b = a;
+    // Neumaier-compensated sum in input order
+    double s = 0.0, c = 0.0;
+    while (b < n_terms && words_equal(x_mask + idx[a] * W, x_mask + idx[b] * W, W) &&
+           words_equal(z_mask + idx[a] * W, z_mask + idx[b] * W, W)) {
+      double v = coef[idx[b]];
+      double t = s + v;
+      c += (std::fabs(s) >= std::fabs(v)) ? (s - t) + v : (v - t) + s;
+      s = t;
+      ++b;
+    }
+    double h = s + c;
+    if (h != 0.0) merged.push_back({idx[a], h});
+    a = b;
+  }
+  // odd |Y| -> complex matrix elements (outside version 1)
+  for (auto& m : merged) {
+    uint64_t y[kMaxWords];
+    for (int w = 0; w < W; ++w) y[w] = x_mask[m.first * W + w] & z_mask[m.first * W + w];
+    if (popc_words(y, W) & 1)
+      return fail(NQS_ERR_UNSUPPORTED, "a Pauli string has an odd number of Y (complex H)");
+  }
+
+  nqs_ham* h = new nqs_ham();
+  h->n_qubits = n_qubits;
+  h->W = W;
+  cudaGetDevice(&h->device);
+
+  // group by XY = x mask; classes: diagonal, heavy (|P_XY| > kHeavyTerms), light
+  const int64_t M = (int64_t)merged.size();
+  std::vector<int64_t> grp_start;
+  for (int64_t a = 0; a < M; ++a) {
+    if (a == 0 || !words_equal(x_mask + merged[a].first * W, x_mask + merged[a - 1].first * W, W))
+      grp_start.push_back(a);
+  }
+  const int64_t G = (int64_t)grp_start.size();
+  grp_start.push_back(M);
+  std::vector<int> cls(G);
+  for (int64_t g = 0; g < G; ++g) {
+    const uint64_t* xg = x_mask + merged[grp_start[g]].first * W;
+    int64_t sz = grp_start[g + 1] - grp_start[g];
+    bool zero = true;
+    for (int w = 0; w < W; ++w) zero = zero && xg[w] == 0;
+    cls[g] = zero ? 0 : (sz > kHeavyTerms ? 1 : 2);
+  }
+  std::vector<int64_t> order(G);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cls[a] < cls[b]; });
+
+  h->n_xy = G;
+  h->n_terms = M;
+  h->has_diag = (G > 0 && cls[order[0]] == 0) ? 1 : 0;
+  h->heavy_end = h->has_diag;
+  for (int64_t p = 0; p < G; ++p) if (cls[order[p]] == 1) h->heavy_end = p + 1;
+  if (h->heavy_end < h->has_diag) h->heavy_end = h->has_diag;
+
+  h->h_xy.assign(G * W, 0);
+  h->h_row_ptr.assign(G + 1, 0);
+  h->h_yz.assign(M * W, 0);
+  h->h_coef.assign(M, 0.0);
+  std::vector<float2> coef_f(M);
+  int64_t t = 0;
+  for (int64_t p = 0; p < G; ++p) {
+    int64_t g = order[p];
+    const uint64_t* xg = x_mask + merged[grp_start[g]].first * W;
+    for (int w = 0; w < W; ++w) h->h_xy[p * W + w] = xg[w];
+    h->h_row_ptr[p] = t;
+    h->max_group = std::max<int64_t>(h->max_group, grp_start[g + 1] - grp_start[g]);
+    for (int64_t a = grp_start[g]; a < grp_start[g + 1]; ++a, ++t) {
+      const int64_t src = merged[a].first;
+      uint64_t y[kMaxWords];
+      for (int w = 0; w < W; ++w) {
+        h->h_yz[t * W + w] = z_mask[src * W + w];
+        y[w] = x_mask[src * W + w] & z_mask[src * W + w];
+      }
+      // <x|P|x'> = i^{|Y|} (-1)^{|x' & YZ|}; |Y| even -> i^{|Y|} = (-1)^{|Y|/2}
+      double c = merged[a].h * (((popc_words(y, W) / 2) & 1) ? -1.0 : 1.0);
+      h->h_coef[t] = c;
+      float hi = (float)c;
+      float lo = (float)(c - (double)hi);
+      coef_f[t] = make_float2(hi, lo);
+    }
+  }
+  h->h_row_ptr[G] = t;
+
+  // linear hash basis: h(v) = XOR over set bits b of R[b] (GF(2)-linear, so
+  // h(x ^ xy) = h(x) ^ h(xy) and a candidate's hash costs one XOR)
+  h->h_hash_basis.resize(64 * W);
+  uint64_t seed = 0x243F6A8885A308D3ull;
+  for (int b = 0; b < 64 * W; ++b) h->h_hash_basis[b] = (uint32_t)(splitmix64(seed) >> 32);
+  std::vector<uint32_t> hxy(G);
+  for (int64_t p = 0; p < G; ++p) {
+    uint32_t v = 0;
+    for (int w = 0; w < W; ++w) {
+      uint64_t m = h->h_xy[p * W + w];
+      while (m) { int b = __builtin_ctzll(m); v ^= h->h_hash_basis[64 * w + b]; m &= m - 1; }
+    }
+    hxy[p] = v;
+  }
+
+  // search table: non-diagonal patterns, class by class; inside a class each
+  // group of 32 slots holds patterns with 32 distinct (hash & 31) values, so
+  // the 32 lanes of a warp probing one sample touch 32 distinct shared-memory
+  // banks of the membership filter.
+  std::vector<uint32_t> srch_hash, srch_id;
+  auto build_class = [&](int64_t lo, int64_t hi) {
+    std::vector<std::vector<uint32_t>> buckets(32);
+    for (int64_t p = lo; p < hi; ++p) buckets[hxy[p] & 31].push_back((uint32_t)p);
+    size_t Gc = 0;
+    for (auto& b : buckets) Gc = std::max(Gc, b.size());
+    for (size_t g = 0; g < Gc; ++g)
+      for (int b = 0; b < 32; ++b) {
+        if (g < buckets[b].size()) {
+          uint32_t id = buckets[b][g];
+          srch_hash.push_back(hxy[id]);
+          srch_id.push_back(id);
+        } else {
+          srch_hash.push_back((uint32_t)b);
+          srch_id.push_back(kDummy);
+        }
+      }
+  };
+  build_class(h->has_diag, h->heavy_end);
+  build_class(h->heavy_end, G);
+  h->n_srch = (int64_t)srch_hash.size();
+
+  std::vector<uint32_t> rp32(G + 1);
+  for (int64_t p = 0; p <= G; ++p) rp32[p] = (uint32_t)h->h_row_ptr[p];
+
+  int rc;
+  if ((rc = upload(&h->xy, h->h_xy)) || (rc = upload(&h->row_ptr, rp32)) ||
+      (rc = upload(&h->yz, h->h_yz)) || (rc = upload(&h->coef, h->h_coef)) ||
+      (rc = upload(&h->coef_f, coef_f)) || (rc = upload(&h->srch_hash, srch_hash)) ||
+      (rc = upload(&h->srch_id, srch_id)) || (rc = upload(&h->hash_basis, h->h_hash_basis))) {
+    free_ham(h);
+    return rc;
+  }
+  *out = h;
+  return NQS_OK;
+}
+
+int nqs_ham_free(nqs_ham* ham) {
+  free_ham(ham);
+  return NQS_OK;
+}
+
+int nqs_ham_info(const nqs_ham* h, int64_t info[8]) {
+  if (!h || !info) return fail(NQS_ERR_ARG, "null argument");
+  info[0] = h->n_qubits; info[1] = h->W; info[2] = h->n_terms; info[3] = h->n_xy;
+  info[4] = h->has_diag; info[5] = h->max_group; info[6] = h->n_srch; info[7] = h->heavy_end;
+  return NQS_OK;
+}
+
+int nqs_ham_export(const nqs_ham* h, uint64_t* xy, int64_t* row_ptr, uint64_t* yz, double* coef) {
+  if (!h) return fail(NQS_ERR_ARG, "null ham");
+  if (xy) std::copy(h->h_xy.begin(), h->h_xy.end(), xy);
+  if (row_ptr) std::copy(h->h_row_ptr.begin(), h->h_row_ptr.end(), row_ptr);
+  if (yz) std::copy(h->h_yz.begin(), h->h_yz.end(), yz);
+  if (coef) std::copy(h->h_coef.begin(), h->h_coef.end(), coef);
+  return NQS_OK;
+}
+
+int64_t nqs_stage_bytes(const nqs_ham* ham, int64_t n_unq) {
+  if (!ham || n_unq < 0) return fail(NQS_ERR_ARG, "bad argument to nqs_stage_bytes");
+  return stage_layout(ham, n_unq).total_bytes;
+}
+
+static int status_to_code(int st) {
+  if (st & kStatusDuplicate) return fail(NQS_ERR_DUPLICATE, "the sample batch repeats a basis vector");
+  if (st & kStatusBadBits) return fail(NQS_ERR_ARG, "a sample has bits >= n_qubits");
+  if (st & kStatusLimit) return fail(NQS_ERR_DEVICE_LIMIT, "a bounded device loop ran out");
+  if (st & kStatusRange) return fail(NQS_ERR_RANGE, "an amplitude ratio leaves the FP32 range");
+  return NQS_OK;
+}
+
+static int read_status(const void* work, cudaStream_t s, StageHeader* hdr_out = nullptr) {
+  StageHeader hdr;
+  cudaError_t e = cudaMemcpyAsync(&hdr, work, sizeof(hdr), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "status copy");
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  if (hdr.magic != kStageMagic) return fail(NQS_ERR_ARG, "workspace was not staged");
+  if (hdr_out) *hdr_out = hdr;
+  return status_to_code(hdr.status);
+}
+
+static int check_work(const nqs_ham* ham, const uint64_t* U, int64_t n, const void* work, StageHeader* L) {
+  if (!ham) return fail(NQS_ERR_ARG, "null ham");
+  if (n < 0) return fail(NQS_ERR_ARG, "n_unq < 0");
+  if (n > 0 && !U) return fail(NQS_ERR_ARG, "null U");
+  if (n >= (int64_t(1) << 31)) return fail(NQS_ERR_UNSUPPORTED, "more than 2^31 samples");
+  if (!work) return fail(NQS_ERR_ARG, "null workspace");
+  if (((uintptr_t)work) & 255) return fail(NQS_ERR_ARG, "workspace not 256-byte aligned");
+  *L = stage_layout(ham, n);
+  return NQS_OK;
+}
+
+int nqs_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, int64_t bytes,
+              int check, void* stream) {
+  StageHeader L;
+  int rc = check_work(ham, U, n, work, &L);
+  if (rc) return rc;
+  if (bytes < L.total_bytes) return fail(NQS_ERR_CAPACITY, "workspace smaller than nqs_stage_bytes");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)work;
+  cudaError_t e = cudaMemcpyAsync(base, &L, sizeof(L), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "header copy");
+  if ((e = cudaMemsetAsync(base + L.off_table, 0xFF, 4 * L.cap, s)) != cudaSuccess) return cuda_fail(e, "memset");
+  if ((e = cudaMemsetAsync(base + L.off_bloom, 0, 4 * L.nwords, s)) != cudaSuccess) return cuda_fail(e, "memset");
+  if ((e = launch_stage(ham, U, n, base, L, s)) != cudaSuccess) return cuda_fail(e, "stage kernel");
+  if (check) return read_status(work, s);
+  return NQS_OK;
+}
+
+int nqs_stage_status(const void* work, void* stream) {
+  if (!work) return fail(NQS_ERR_ARG, "null workspace");
+  return read_status(work, (cudaStream_t)stream);
+}
+
+static int check_rows(int64_t n, int64_t rb, int64_t re) {
+  if (rb < 0 || re < rb || re > n) return fail(NQS_ERR_ARG, "bad row range");
+  return NQS_OK;
+}
+
+static cudaError_t launch_search(const nqs_ham* ham, const uint64_t* U, const char* work,
+                                 const StageHeader& L, int64_t rb, int64_t re, int schedule,
+                                 int64_t* rp, uint32_t* pj, uint32_t* pk, bool fill, cudaStream_t s) {
+  if (schedule == NQS_SCHED_BATCH)
+    return launch_pairs_batch(ham, U, work, L, rb, re, rp, pj, pk, fill, s);
+  return launch_pairs_terms(ham, U, work, L, rb, re, rp, pj, pk, fill, s);
+}
+
+static int check_schedule(int schedule) {
+  if (schedule == NQS_SCHED_AUTO || schedule == NQS_SCHED_TERMS || schedule == NQS_SCHED_BATCH)
+    return NQS_OK;
+  if (schedule == NQS_SCHED_TRIE) return fail(NQS_ERR_UNSUPPORTED, "trie schedule not built yet");
+  return fail(NQS_ERR_ARG, "unknown schedule");
+}
+
+int nqs_count_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work,
+                            int64_t rb, int64_t re, int schedule, int64_t* row_ptr,
+                            int64_t* n_pairs, void* stream) {
+  StageHeader L;
+  int rc = check_work(ham, U, n, work, &L);
+  if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(schedule))) return rc;
+  if (!row_ptr || !n_pairs) return fail(NQS_ERR_ARG, "null row_ptr or n_pairs");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t rows = re - rb;
+  cudaError_t e = cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), s);
+  if (e != cudaSuccess) return cuda_fail(e, "memset row_ptr");
+  if (rows > 0) {
+    if ((e = launch_search(ham, U, (char*)work, L, rb, re, schedule, row_ptr + 1, nullptr, nullptr,
+                           false, s)) != cudaSuccess)
+      return cuda_fail(e, "pair count kernel");
+    if ((e = launch_scan(row_ptr + 1, rows, (char*)work, L, s)) != cudaSuccess)
+      return cuda_fail(e, "scan kernel");
+  }
+  e = cudaMemcpyAsync(n_pairs, row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "count copy");
+  return read_status(work, s);
+}
+
+int nqs_fill_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work,
+                           int64_t rb, int64_t re, int schedule, const int64_t* row_ptr,
+                           uint32_t* pair_j, uint32_t* pair_k, void* stream) {
+  StageHeader L;
+  int rc = check_work(ham, U, n, work, &L);
+  if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(schedule))) return rc;
+  if (!row_ptr || !pair_j || !pair_k) return fail(NQS_ERR_ARG, "null output");
+  if (re == rb) return NQS_OK;
+  cudaError_t e = launch_search(ham, U, (char*)work, L, rb, re, schedule, (int64_t*)row_ptr,
+                                pair_j, pair_k, true, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pair fill kernel");
+  return NQS_OK;
+}
+
+int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work,
+                           int64_t rb, int64_t re, int schedule, int64_t* row_ptr,
+                           uint32_t* pair_j, uint32_t* pair_k, int64_t capacity,
+                           int64_t* n_pairs, void* stream) {
+  int rc = nqs_count_coupled_pairs(ham, U, n, work, rb, re, schedule, row_ptr, n_pairs, stream);
+  if (rc) return rc;
+  if (*n_pairs > capacity) return fail(NQS_ERR_CAPACITY, "pair capacity too small");
+  return nqs_fill_coupled_pairs(ham, U, n, work, rb, re, schedule, row_ptr, pair_j, pair_k, stream);
+}
+
+int nqs_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work,
+                     const double* a, const double* b, int64_t rb, int64_t re,
+                     const int64_t* row_ptr, const uint32_t* pair_j, const uint32_t* pair_k,
+                     int precision, double* eloc_re, double* eloc_im, double* hdiag,
+                     void* stream) {
+  StageHeader L;
+  int rc = check_work(ham, U, n, work, &L);
+  if (rc || (rc = check_rows(n, rb, re))) return rc;
+  if (precision != NQS_PREC_FP64 && precision != NQS_PREC_FP32C) return fail(NQS_ERR_ARG, "bad precision");
+  if (n > 0 && !a) return fail(NQS_ERR_ARG, "null logpsi_re");
+  if (!eloc_re) return fail(NQS_ERR_ARG, "null eloc_re");
+  if (b && !eloc_im) return fail(NQS_ERR_ARG, "complex log psi needs eloc_im");
+  if (re > rb && (!row_ptr || !pair_j || !pair_k)) return fail(NQS_ERR_ARG, "null pair arrays");
+  if (re == rb) return NQS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_amplitudes(a, b, n, precision, (char*)work, L, s);
+  if (e != cudaSuccess) return cuda_fail(e, "amplitude kernel");
+  e = launch_local_energy(ham, U, n, (char*)work, L, b != nullptr, rb, re, row_ptr, pair_j, pair_k,
+                          precision, eloc_re, eloc_im, hdiag, s);
+  if (e != cudaSuccess) return cuda_fail(e, "local energy kernel");
+  return NQS_OK;
+}
+
+int nqs_variational_energy(int64_t n, const double* a, const double* eloc_re, double* out, void* stream) {
+  if (n <= 0 || !a || !eloc_re || !out) return fail(NQS_ERR_ARG, "bad argument");
+  cudaError_t e = launch_variational_energy(n, a, eloc_re, out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "variational energy kernel");
+  return NQS_OK;
+}
+
+int nqs_local_energy_backward(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work,
+                              const double* a, const double* b, int64_t rb, int64_t re,
+                              const int64_t* row_ptr, const uint32_t* pair_j, const uint32_t* pair_k,
+                              const double* eloc_re, const double* eloc_im, const double* hdiag,
+                              const double* evar, const double* g_re, const double* g_im,
+                              const double* g_evar, int precision, double* grad_re,
+                              double* grad_im, void* stream) {
+  StageHeader L;
+  int rc = check_work(ham, U, n, work, &L);
+  if (rc || (rc = check_rows(n, rb, re))) return rc;
+  if (precision != NQS_PREC_FP64 && precision != NQS_PREC_FP32C) return fail(NQS_ERR_ARG, "bad precision");
+  if (n > 0 && (!a || !eloc_re || !evar)) return fail(NQS_ERR_ARG, "null forward input");
+  if (!grad_re) return fail(NQS_ERR_ARG, "null grad_re");
+  if (b && (!grad_im || !eloc_im)) return fail(NQS_ERR_ARG, "complex log psi needs grad_im and eloc_im");
+  const bool pairs_needed = g_re || g_im;
+  if (pairs_needed && re > rb && (!row_ptr || !pair_j || !pair_k || !hdiag))
+    return fail(NQS_ERR_ARG, "upstream E_loc gradient needs pairs and hdiag");
+  if (re == rb) return NQS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (pairs_needed) {
+    e = launch_amplitudes(a, b, n, precision, (char*)work, L, s);
+    if (e != cudaSuccess) return cuda_fail(e, "amplitude kernel");
+  }
+  e = launch_backward(ham, U, n, (char*)work, L, b != nullptr, a, b, rb, re, row_ptr, pair_j, pair_k,
+                      eloc_re, eloc_im, hdiag, evar, g_re, g_im, g_evar, precision, grad_re, grad_im, s);
+  if (e != cudaSuccess) return cuda_fail(e, "backward kernel");
+  return NQS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// Device helpers: bit-vector words, parities, compensated FP32 arithmetic.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace nqs {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+template <int W>
+__device__ __forceinline__ void load_words(const uint64_t* __restrict__ p, uint64_t (&v)[W]) {
+#pragma unroll
+  for (int w = 0; w < W; ++w) v[w] = __ldg(p + w);
+}
+
+// parity of |x AND m| (the sign (-1)^{|x' & YZ|} of Eq. pauli_melem)
+template <int W>
+__device__ __forceinline__ uint32_t parity_and(const uint64_t (&x)[W], const uint64_t* __restrict__ m) {
+  uint64_t t = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) t ^= x[w] & __ldg(m + w);
+  return __popc((uint32_t)t ^ (uint32_t)(t >> 32)) & 1u;
+}
+
+// two bits of a 32-bit blocked Bloom word per key, taken from hash bits 17.. and 22..
+__device__ __forceinline__ uint32_t bloom_bits(uint32_t h) {
+  return (1u << ((h >> 17) & 31)) | (1u << ((h >> 22) & 31));
+}
+__device__ __forceinline__ uint32_t bloom_hit(uint32_t w, uint32_t s) {
+  return __funnelshift_r(w, w, s >> 17) & __funnelshift_r(w, w, s >> 22) & 1u;
+}
+
+// --------------------------------------------------------------------------
+// double-float ("df"): value = hi + lo with |lo| <= ulp(hi)/2.
+// Error-free transformations: Knuth's TwoSum and the FMA-based TwoProduct.
+// --------------------------------------------------------------------------
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), s.lo);
+  return fast_two_sum(s.hi, lo);
+}
+
+// accumulate a df term without renormalising (renormalise once at the end)
+__device__ __forceinline__ void df_acc(df& acc, df t) {
+  df s = two_sum(acc.hi, t.hi);
+  acc.hi = s.hi;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, t.lo));
+}
+
+__device__ __forceinline__ df df_norm(df a) { return fast_two_sum(a.hi, a.lo); }
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df df_from_double(double v) {
+  float hi = __double2float_rn(v);
+  float lo = __double2float_rn(v - (double)hi);
+  return {hi, lo};
+}
+
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ df df_ldexp(df a, int e) { return {ldexpf(a.hi, e), ldexpf(a.lo, e)}; }
+
+// flip the sign of both parts when bit is 1 (exact)
+__device__ __forceinline__ df df_signflip(float2 c, uint32_t bit) {
+  uint32_t m = bit << 31;
+  return {__uint_as_float(__float_as_uint(c.x) ^ m), __uint_as_float(__float_as_uint(c.y) ^ m)};
+}
+
+__device__ __forceinline__ double dsignflip(double c, uint32_t bit) {
+  return __longlong_as_double(__double_as_longlong(c) ^ ((unsigned long long)bit << 63));
+}
+
+// warp all-reduce (butterfly): every lane ends with the same, order-fixed value
+__device__ __forceinline__ df warp_sum(df v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    df u;
+    u.hi = __shfl_xor_sync(kFull, v.hi, o);
+    u.lo = __shfl_xor_sync(kFull, v.lo, o);
+    v = df_add(v, u);
+  }
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+}  // namespace nqs

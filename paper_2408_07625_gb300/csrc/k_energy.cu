@@ -1,0 +1,526 @@
+// MatrixElement + ScatterAdd -> E_loc^var, the variational energy and the adjoint.
+//
+// MatrixElement (supplementary algorithm "Calculating the Hamiltonian matrix
+// element"): H_xx' = sum_{l in P_XY} c_l (-1)^{|x' & YZ_l|}, c_l = h_l i^{|Y_l|}.
+// ScatterAdd (Fig. scatter_local_energies) becomes a row-owned reduction: one
+// warp owns row x and sums H_xx' psi(x')/psi(x) over its CSR pairs in a fixed
+// order, so no atomics are needed and results are bitwise reproducible.
+//
+// Amplitude ratios: psi(x) = P_x 2^{K_x} with |P_x| in [1, 2) (precomputed per
+// sample in FP64), 1/psi(x) = Q_x 2^{-K_x}; psi(x')/psi(x) = P_x' Q_x 2^{K_x'-K_x}.
+// This replaces one exp per pair by a (double-float) product and an exact
+// power-of-two scaling.
+#include <cfloat>
+
+#include "device_util.cuh"
+#include "nqs_internal.cuh"
+
+namespace nqs {
+
+constexpr int kEnergyThreads = 256;
+constexpr int kEnergyWarps = kEnergyThreads / 32;
+
+// --------------------------------------------------------------------------
+// per-sample amplitude factors
+// --------------------------------------------------------------------------
+__global__ void amplitudes_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                  int64_t n, int fp64, float4* __restrict__ Pf,
+                                  float4* __restrict__ Qf, double2* __restrict__ Pd,
+                                  double2* __restrict__ Qd, int* __restrict__ K) {
+  const double kLn2 = 0.6931471805599453094;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double ai = a[i];
+    const double k = floor(ai / kLn2);
+    const double m = exp(ai - k * kLn2);     // in [1, 2) up to rounding
+    double c = 1.0, s = 0.0;
+    if (b) sincos(b[i], &s, &c);
+    const double pr = m * c, pi = m * s;
+    const double qr = c / m, qi = -s / m;
+    K[i] = (int)k;
+    if (fp64) {
+      Pd[i] = make_double2(pr, pi);
+      Qd[i] = make_double2(qr, qi);
+    } else {
+      df dpr = df_from_double(pr), dpi = df_from_double(pi);
+      df dqr = df_from_double(qr), dqi = df_from_double(qi);
+      Pf[i] = make_float4(dpr.hi, dpr.lo, dpi.hi, dpi.lo);
+      Qf[i] = make_float4(dqr.hi, dqr.lo, dqi.hi, dqi.lo);
+    }
+  }
+}
+
+cudaError_t launch_amplitudes(const double* a, const double* b, int64_t n, int precision,
+                              char* stage, const StageHeader& L, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8 * num_sms());
+  const bool fp64 = precision == NQS_PREC_FP64;
+  amplitudes_kernel<<<blocks, 256, 0, s>>>(
+      a, b, n, fp64 ? 1 : 0, (float4*)(stage + L.off_ampP), (float4*)(stage + L.off_ampQ),
+      (double2*)(stage + L.off_ampP), (double2*)(stage + L.off_ampQ), (int*)(stage + L.off_ampK));
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// arithmetic policies: FP32 compensated (double-float) and FP64
+// --------------------------------------------------------------------------
+struct PolicyF {
+  using T = df;
+  static constexpr int kMaxExp = 100;
+  __device__ static T zero() { return {0.f, 0.f}; }
+  __device__ static T coef(const float2* cf, const double*, int64_t l, uint32_t par) {
+    return df_signflip(__ldg(cf + l), par);
+  }
+  __device__ static void acc(T& a, T t) { df_acc(a, t); }
+  __device__ static T add(T a, T b) { return df_add(a, b); }
+  __device__ static T mul(T a, T b) { return df_mul(a, b); }
+  __device__ static T neg(T a) { return df_neg(a); }
+  __device__ static T scale(T a, int e) { return df_ldexp(a, e); }
+  __device__ static T fin(T a) { return df_norm(a); }
+  __device__ static T warp_sum(T a) { return nqs::warp_sum(df_norm(a)); }
+  __device__ static double to_d(T a) { return df_to_double(a); }
+  __device__ static T from_d(double v) { return df_from_double(v); }
+  __device__ static void load_amp(const char* P, int64_t i, T& re, T& im) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(P) + i);
+    re = {v.x, v.y};
+    im = {v.z, v.w};
+  }
+};
+
+struct PolicyD {
+  using T = double;
+  static constexpr int kMaxExp = 1000;
+  __device__ static T zero() { return 0.0; }
+  __device__ static T coef(const float2*, const double* cd, int64_t l, uint32_t par) {
+    return dsignflip(__ldg(cd + l), par);
+  }
+  __device__ static void acc(T& a, T t) { a += t; }
+  __device__ static T add(T a, T b) { return a + b; }
+  __device__ static T mul(T a, T b) { return a * b; }
+  __device__ static T neg(T a) { return -a; }
+  __device__ static T scale(T a, int e) { return ldexp(a, e); }
+  __device__ static T fin(T a) { return a; }
+  __device__ static T warp_sum(T a) { return nqs::warp_sum(a); }
+  __device__ static double to_d(T a) { return a; }
+  __device__ static T from_d(double v) { return v; }
+  __device__ static void load_amp(const char* P, int64_t i, T& re, T& im) {
+    double2 v = __ldg(reinterpret_cast<const double2*>(P) + i);
+    re = v.x;
+    im = v.y;
+  }
+};
+
+// complex ratio psi(num) / psi(den) = P_num Q_den 2^{K_num - K_den}
+template <class Pol, bool CPLX>
+__device__ __forceinline__ void ratio(const char* P, const char* Q, const int* K, int64_t num,
+                                      int64_t den, typename Pol::T& rr, typename Pol::T& ri,
+                                      int32_t* status) {
+  using T = typename Pol::T;
+  T pr, pi, qr, qi;
+  Pol::load_amp(P, num, pr, pi);
+  Pol::load_amp(Q, den, qr, qi);
+  int e = __ldg(K + num) - __ldg(K + den);
+  if (e > Pol::kMaxExp || e < -Pol::kMaxExp) {
+    atomicOr(status, kStatusRange);
+    e = e > 0 ? Pol::kMaxExp : -Pol::kMaxExp;
+  }
+  if (CPLX) {
+    rr = Pol::add(Pol::mul(pr, qr), Pol::neg(Pol::mul(pi, qi)));
+    ri = Pol::add(Pol::mul(pr, qi), Pol::mul(pi, qr));
+    rr = Pol::scale(rr, e);
+    ri = Pol::scale(ri, e);
+  } else {
+    rr = Pol::scale(Pol::mul(pr, qr), e);
+    ri = Pol::zero();
+  }
+}
+
+// partial matrix element over the terms l = t0 + lane0, t0 + lane0 + step, ... < t1
+template <class Pol, int W>
+__device__ __forceinline__ typename Pol::T melem_part(const uint64_t (&xp)[W], int64_t t0, int64_t t1,
+                                                       int step, const uint64_t* __restrict__ yz,
+                                                       const float2* __restrict__ cf,
+                                                       const double* __restrict__ cd) {
+  typename Pol::T h = Pol::zero();
+  for (int64_t l = t0; l < t1; l += step) {
+    const uint32_t par = parity_and<W>(xp, yz + l * W);
+    Pol::acc(h, Pol::coef(cf, cd, l, par));
+  }
+  return h;
+}
+
+// --------------------------------------------------------------------------
+// E_loc^var over CSR pairs: one warp per row
+// --------------------------------------------------------------------------
+template <class Pol, int W, bool CPLX>
+__global__ void __launch_bounds__(kEnergyThreads)
+local_energy_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict__ t_ptr,
+                    const uint64_t* __restrict__ yz, const float2* __restrict__ cf,
+                    const double* __restrict__ cd, int has_diag, int64_t heavy_end,
+                    const char* __restrict__ P, const char* __restrict__ Q,
+                    const int* __restrict__ K, int64_t row_begin, int64_t row_end,
+                    const int64_t* __restrict__ rp, const uint32_t* __restrict__ pair_j,
+                    const uint32_t* __restrict__ pair_k, double* __restrict__ eloc_re,
+                    double* __restrict__ eloc_im, double* __restrict__ hdiag,
+                    int32_t* __restrict__ status) {
+  using T = typename Pol::T;
+  const int lane = threadIdx.x & 31;
+  const int64_t tw = (int64_t)gridDim.x * kEnergyWarps;
+  for (int64_t row = (int64_t)blockIdx.x * kEnergyWarps + (threadIdx.x >> 5); row < row_end - row_begin;
+       row += tw) {
+    const int64_t i = row + row_begin;
+    int64_t p = rp[row] - rp[0];
+    const int64_t p1 = rp[row + 1] - rp[0];
+    T acc_re = Pol::zero(), acc_im = Pol::zero();
+    double hd = 0.0;
+    if (has_diag && p < p1 && __ldg(pair_k + p) == 0u) {
+      uint64_t xi[W];
+      load_words<W>(U + i * W, xi);
+      T h = melem_part<Pol, W>(xi, (int64_t)__ldg(t_ptr) + lane, (int64_t)__ldg(t_ptr + 1), 32, yz, cf, cd);
+      h = Pol::warp_sum(h);
+      hd = Pol::to_d(h);
+      if (lane == 0) Pol::acc(acc_re, h);  // psi(x)/psi(x) = 1
+      ++p;
+    }
+    for (int64_t base = p; base < p1; base += 32) {
+      const int64_t q = base + lane;
+      const bool have = q < p1;
+      const uint32_t j = have ? __ldg(pair_j + q) : 0u;
+      const uint32_t k = have ? __ldg(pair_k + q) : 0u;
+      const bool heavy = have && (int64_t)k < heavy_end;
+      uint32_t hb = __ballot_sync(kFull, heavy);
+      while (hb) {  // large P_XY: all lanes share the term loop of one pair
+        const int src = __ffs(hb) - 1;
+        hb &= hb - 1;
+        const uint32_t jj = __shfl_sync(kFull, j, src);
+        const uint32_t kk = __shfl_sync(kFull, k, src);
+        uint64_t xp[W];
+        load_words<W>(U + (int64_t)jj * W, xp);
+        T part = melem_part<Pol, W>(xp, (int64_t)__ldg(t_ptr + kk) + lane, (int64_t)__ldg(t_ptr + kk + 1),
+                                    32, yz, cf, cd);
+        part = Pol::fin(part);
+        T rr, ri;
+        ratio<Pol, CPLX>(P, Q, K, jj, i, rr, ri, status);
+        Pol::acc(acc_re, Pol::mul(part, rr));
+        if (CPLX) Pol::acc(acc_im, Pol::mul(part, ri));
+      }
+      if (have && !heavy) {  // small P_XY: one lane per pair
+        uint64_t xp[W];
+        load_words<W>(U + (int64_t)j * W, xp);
+        T h = melem_part<Pol, W>(xp, (int64_t)__ldg(t_ptr + k), (int64_t)__ldg(t_ptr + k + 1), 1, yz, cf, cd);
+        h = Pol::fin(h);
+        T rr, ri;
+        ratio<Pol, CPLX>(P, Q, K, j, i, rr, ri, status);
+        Pol::acc(acc_re, Pol::mul(h, rr));
+        if (CPLX) Pol::acc(acc_im, Pol::mul(h, ri));
+      }
+    }
+    const T er = Pol::warp_sum(acc_re);
+    const T ei = CPLX ? Pol::warp_sum(acc_im) : Pol::zero();
+    if (lane == 0) {
+      eloc_re[i] = Pol::to_d(er);
+      if (eloc_im) eloc_im[i] = Pol::to_d(ei);
+      if (hdiag) hdiag[i] = hd;
+    }
+  }
+}
+
+template <class Pol, int W, bool CPLX>
+static void launch_le(const nqs_ham* ham, const uint64_t* U, const char* stage, const StageHeader& L,
+                      int64_t rb, int64_t re, const int64_t* rp, const uint32_t* pj,
+                      const uint32_t* pk, double* er, double* ei, double* hd, cudaStream_t s) {
+  const int64_t rows = re - rb;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + kEnergyWarps - 1) / kEnergyWarps,
+                                                                  (int64_t)num_sms() * 8));
+  local_energy_kernel<Pol, W, CPLX><<<blocks, kEnergyThreads, 0, s>>>(
+      U, ham->row_ptr, ham->yz, ham->coef_f, ham->coef, ham->has_diag, ham->heavy_end,
+      stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK), rb, re, rp, pj, pk,
+      er, ei, hd, (int32_t*)(stage + offsetof(StageHeader, status)));
+}
+
+template <class Pol, bool CPLX>
+static void launch_le_w(const nqs_ham* ham, const uint64_t* U, const char* stage, const StageHeader& L,
+                        int64_t rb, int64_t re, const int64_t* rp, const uint32_t* pj,
+                        const uint32_t* pk, double* er, double* ei, double* hd, cudaStream_t s) {
+  switch (ham->W) {
+    case 1: launch_le<Pol, 1, CPLX>(ham, U, stage, L, rb, re, rp, pj, pk, er, ei, hd, s); break;
+    case 2: launch_le<Pol, 2, CPLX>(ham, U, stage, L, rb, re, rp, pj, pk, er, ei, hd, s); break;
+    case 3: launch_le<Pol, 3, CPLX>(ham, U, stage, L, rb, re, rp, pj, pk, er, ei, hd, s); break;
+    default: launch_le<Pol, 4, CPLX>(ham, U, stage, L, rb, re, rp, pj, pk, er, ei, hd, s); break;
+  }
+}
+
+cudaError_t launch_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t, const char* stage,
+                                const StageHeader& L, bool cplx, int64_t rb, int64_t re,
+                                const int64_t* rp, const uint32_t* pj, const uint32_t* pk,
+                                int precision, double* er, double* ei, double* hd, cudaStream_t s) {
+  if (precision == NQS_PREC_FP64) {
+    if (cplx) launch_le_w<PolicyD, true>(ham, U, stage, L, rb, re, rp, pj, pk, er, ei, hd, s);
+    else launch_le_w<PolicyD, false>(ham, U, stage, L, rb, re, rp, pj, pk, er, ei, hd, s);
+  } else {
+    if (cplx) launch_le_w<PolicyF, true>(ham, U, stage, L, rb, re, rp, pj, pk, er, ei, hd, s);
+    else launch_le_w<PolicyF, false>(ham, U, stage, L, rb, re, rp, pj, pk, er, ei, hd, s);
+  }
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// E^var: one block, FP64, fixed reduction order
+// --------------------------------------------------------------------------
+constexpr int kRedThreads = 1024;
+
+__device__ double block_reduce_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (warp == 0) {
+    r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sh[0] = r;
+  __syncthreads();
+  return sh[0];
+}
+
+__device__ double block_reduce_max(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double r = -DBL_MAX;
+  if (warp == 0) {
+    r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : -DBL_MAX;
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(kFull, r, o));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sh[0] = r;
+  __syncthreads();
+  return sh[0];
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+evar_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ er,
+            double* __restrict__ out) {
+  __shared__ double sh[32];
+  double m = -DBL_MAX;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, a[i]);
+  const double amax = block_reduce_max(m, sh);
+  double sw = 0.0, swe = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double w = exp(2.0 * (a[i] - amax));
+    sw += w;
+    swe += w * er[i];
+  }
+  const double S = block_reduce_sum(sw, sh);
+  const double N = block_reduce_sum(swe, sh);
+  if (threadIdx.x == 0) {
+    out[0] = N / S;
+    out[1] = amax;
+    out[2] = S;
+  }
+}
+
+cudaError_t launch_variational_energy(int64_t n, const double* a, const double* er, double* out,
+                                      cudaStream_t s) {
+  evar_kernel<<<1, kRedThreads, 0, s>>>(n, a, er, out);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// adjoint
+// --------------------------------------------------------------------------
+// per-sample effective upstream: ge(x) = g_re(x) + g_E w(x), gi(x) = g_im(x)
+__global__ void geff_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ evar,
+                            const double* __restrict__ g_re, const double* __restrict__ g_im,
+                            const double* __restrict__ g_evar, int fp64, double2* __restrict__ gd,
+                            float4* __restrict__ gf) {
+  const double gE = g_evar ? g_evar[0] : 0.0;
+  const double amax = evar[1], S = evar[2];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double w = exp(2.0 * (a[i] - amax)) / S;
+    const double ge = (g_re ? g_re[i] : 0.0) + gE * w;
+    const double gi = g_im ? g_im[i] : 0.0;
+    if (fp64) {
+      gd[i] = make_double2(ge, gi);
+    } else {
+      df a1 = df_from_double(ge), a2 = df_from_double(gi);
+      gf[i] = make_float4(a1.hi, a1.lo, a2.hi, a2.lo);
+    }
+  }
+}
+
+// closed form: g(y) = g_E 2 w_y (E_loc(y) - E) (+ i g_E 2 w_y Im E_loc(y))
+__global__ void backward_closed_kernel(int64_t rb, int64_t re, const double* __restrict__ a,
+                                       const double* __restrict__ er, const double* __restrict__ ei,
+                                       const double* __restrict__ evar, const double* __restrict__ g_evar,
+                                       double* __restrict__ gre, double* __restrict__ gim) {
+  const double gE = g_evar ? g_evar[0] : 0.0;
+  const double E = evar[0], amax = evar[1], S = evar[2];
+  for (int64_t y = rb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; y < re;
+       y += (int64_t)gridDim.x * blockDim.x) {
+    const double w = exp(2.0 * (a[y] - amax)) / S;
+    gre[y] = gE * 2.0 * w * (er[y] - E);
+    if (gim) gim[y] = ei ? gE * 2.0 * w * ei[y] : 0.0;
+  }
+}
+
+template <class Pol>
+__device__ __forceinline__ void load_geff(const char* G, int64_t i, typename Pol::T& ge, typename Pol::T& gi) {
+  Pol::load_amp(G, i, ge, gi);
+}
+
+// row y: sum over pairs (y, x), x != y, of ge(x) Re T + gi(x) Im T (and the
+// Im-part analogue) with T = H_yx psi(y)/psi(x) = H_xy psi(y)/psi(x); then the
+// diagonal term D_yy = -(E_loc(y) - H_yy) and g_E 2 w_y (Re E_loc(y) - E).
+template <class Pol, int W, bool CPLX>
+__global__ void __launch_bounds__(kEnergyThreads)
+backward_pairs_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict__ t_ptr,
+                      const uint64_t* __restrict__ yz, const float2* __restrict__ cf,
+                      const double* __restrict__ cd, int has_diag, int64_t heavy_end,
+                      const char* __restrict__ P, const char* __restrict__ Q,
+                      const int* __restrict__ K, const char* __restrict__ G,
+                      int64_t row_begin, int64_t row_end, const int64_t* __restrict__ rp,
+                      const uint32_t* __restrict__ pair_j, const uint32_t* __restrict__ pair_k,
+                      const double* __restrict__ a, const double* __restrict__ er,
+                      const double* __restrict__ ei, const double* __restrict__ hdiag,
+                      const double* __restrict__ evar, const double* __restrict__ g_re,
+                      const double* __restrict__ g_im, const double* __restrict__ g_evar,
+                      double* __restrict__ gre, double* __restrict__ gim, int32_t* __restrict__ status) {
+  using T = typename Pol::T;
+  const int lane = threadIdx.x & 31;
+  const int64_t tw = (int64_t)gridDim.x * kEnergyWarps;
+  const double gE = g_evar ? g_evar[0] : 0.0;
+  const double E = evar[0], amax = evar[1], S = evar[2];
+  for (int64_t row = (int64_t)blockIdx.x * kEnergyWarps + (threadIdx.x >> 5); row + row_begin < row_end;
+       row += tw) {
+    const int64_t y = row + row_begin;
+    int64_t p = rp[row] - rp[0];
+    const int64_t p1 = rp[row + 1] - rp[0];
+    T da = Pol::zero(), db = Pol::zero();
+    if (has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
+    for (int64_t base = p; base < p1; base += 32) {
+      const int64_t q = base + lane;
+      const bool have = q < p1;
+      const uint32_t j = have ? __ldg(pair_j + q) : 0u;
+      const uint32_t k = have ? __ldg(pair_k + q) : 0u;
+      const bool heavy = have && (int64_t)k < heavy_end;
+      uint32_t hb = __ballot_sync(kFull, heavy);
+      while (hb) {
+        const int src = __ffs(hb) - 1;
+        hb &= hb - 1;
+        const uint32_t jj = __shfl_sync(kFull, j, src);
+        const uint32_t kk = __shfl_sync(kFull, k, src);
+        uint64_t xp[W];
+        load_words<W>(U + (int64_t)jj * W, xp);
+        T part = Pol::fin(melem_part<Pol, W>(xp, (int64_t)__ldg(t_ptr + kk) + lane,
+                                             (int64_t)__ldg(t_ptr + kk + 1), 32, yz, cf, cd));
+        T rr, ri, ge, gi;
+        ratio<Pol, CPLX>(P, Q, K, y, jj, rr, ri, status);
+        load_geff<Pol>(G, jj, ge, gi);
+        const T tr = Pol::mul(part, rr);
+        Pol::acc(da, Pol::mul(ge, tr));
+        if (CPLX) {
+          const T ti = Pol::mul(part, ri);
+          Pol::acc(da, Pol::mul(gi, ti));
+          Pol::acc(db, Pol::neg(Pol::mul(ge, ti)));
+          Pol::acc(db, Pol::mul(gi, tr));
+        }
+      }
+      if (have && !heavy) {
+        uint64_t xp[W];
+        load_words<W>(U + (int64_t)j * W, xp);
+        T h = Pol::fin(melem_part<Pol, W>(xp, (int64_t)__ldg(t_ptr + k), (int64_t)__ldg(t_ptr + k + 1), 1,
+                                          yz, cf, cd));
+        T rr, ri, ge, gi;
+        ratio<Pol, CPLX>(P, Q, K, y, j, rr, ri, status);
+        load_geff<Pol>(G, j, ge, gi);
+        const T tr = Pol::mul(h, rr);
+        Pol::acc(da, Pol::mul(ge, tr));
+        if (CPLX) {
+          const T ti = Pol::mul(h, ri);
+          Pol::acc(da, Pol::mul(gi, ti));
+          Pol::acc(db, Pol::neg(Pol::mul(ge, ti)));
+          Pol::acc(db, Pol::mul(gi, tr));
+        }
+      }
+    }
+    const double sa = Pol::to_d(Pol::warp_sum(da));
+    const double sb = CPLX ? Pol::to_d(Pol::warp_sum(db)) : 0.0;
+    if (lane == 0) {
+      const double w = exp(2.0 * (a[y] - amax)) / S;
+      const double ge_y = (g_re ? g_re[y] : 0.0) + gE * w;
+      const double gi_y = g_im ? g_im[y] : 0.0;
+      const double Dr = -(er[y] - hdiag[y]);
+      const double Di = CPLX ? -ei[y] : 0.0;
+      gre[y] = sa + ge_y * Dr + gi_y * Di + gE * 2.0 * w * (er[y] - E);
+      if (gim) gim[y] = CPLX ? (sb - ge_y * Di + gi_y * Dr) : 0.0;
+    }
+  }
+}
+
+template <class Pol, int W, bool CPLX>
+static void launch_bw(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L,
+                      int64_t rb, int64_t re, const int64_t* rp, const uint32_t* pj, const uint32_t* pk,
+                      const double* a, const double* er, const double* ei, const double* hd,
+                      const double* evar, const double* g_re, const double* g_im, const double* g_evar,
+                      double* gre, double* gim, cudaStream_t s) {
+  const int64_t rows = re - rb;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + kEnergyWarps - 1) / kEnergyWarps,
+                                                                  (int64_t)num_sms() * 8));
+  backward_pairs_kernel<Pol, W, CPLX><<<blocks, kEnergyThreads, 0, s>>>(
+      U, ham->row_ptr, ham->yz, ham->coef_f, ham->coef, ham->has_diag, ham->heavy_end,
+      stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK), stage + L.off_geff,
+      rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim,
+      (int32_t*)(stage + offsetof(StageHeader, status)));
+}
+
+template <class Pol, bool CPLX>
+static void launch_bw_w(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L,
+                        int64_t rb, int64_t re, const int64_t* rp, const uint32_t* pj, const uint32_t* pk,
+                        const double* a, const double* er, const double* ei, const double* hd,
+                        const double* evar, const double* g_re, const double* g_im, const double* g_evar,
+                        double* gre, double* gim, cudaStream_t s) {
+  switch (ham->W) {
+    case 1: launch_bw<Pol, 1, CPLX>(ham, U, stage, L, rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, s); break;
+    case 2: launch_bw<Pol, 2, CPLX>(ham, U, stage, L, rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, s); break;
+    case 3: launch_bw<Pol, 3, CPLX>(ham, U, stage, L, rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, s); break;
+    default: launch_bw<Pol, 4, CPLX>(ham, U, stage, L, rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, s); break;
+  }
+}
+
+cudaError_t launch_backward(const nqs_ham* ham, const uint64_t* U, int64_t n, char* stage,
+                            const StageHeader& L, bool cplx, const double* a, const double*,
+                            int64_t rb, int64_t re, const int64_t* rp, const uint32_t* pj,
+                            const uint32_t* pk, const double* er, const double* ei, const double* hd,
+                            const double* evar, const double* g_re, const double* g_im,
+                            const double* g_evar, int precision, double* gre, double* gim,
+                            cudaStream_t s) {
+  const int64_t rows = re - rb;
+  if (!g_re && !g_im) {
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 8 * num_sms()));
+    backward_closed_kernel<<<blocks, 256, 0, s>>>(rb, re, a, er, ei, evar, g_evar, gre, gim);
+    return cudaGetLastError();
+  }
+  const bool fp64 = precision == NQS_PREC_FP64;
+  {
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * num_sms()));
+    geff_kernel<<<blocks, 256, 0, s>>>(n, a, evar, g_re, g_im, g_evar, fp64 ? 1 : 0,
+                                       (double2*)(stage + L.off_geff), (float4*)(stage + L.off_geff));
+  }
+  if (fp64) {
+    if (cplx) launch_bw_w<PolicyD, true>(ham, U, stage, L, rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, s);
+    else launch_bw_w<PolicyD, false>(ham, U, stage, L, rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, s);
+  } else {
+    if (cplx) launch_bw_w<PolicyF, true>(ham, U, stage, L, rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, s);
+    else launch_bw_w<PolicyF, false>(ham, U, stage, L, rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, s);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace nqs

@@ -1,0 +1,128 @@
+// Internal declarations of the GB300 local-energy library (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <string>
+#include <vector>
+
+#include "nqs.h"
+
+namespace nqs {
+
+constexpr int kMaxWords = 4;                 // N <= 256 qubits
+constexpr uint32_t kDummy = 0xFFFFFFFFu;     // padding slot of the search table
+constexpr int kHeavyTerms = 24;              // |P_XY| above this: warp-cooperative term loop
+constexpr int kQueueCap = 512;               // per-warp candidate queue (entries)
+constexpr int kRowsPerWarp = 4;              // rows scanned together by one warp
+
+// status bits (device status word)
+constexpr int kStatusDuplicate = 1;
+constexpr int kStatusBadBits = 2;
+constexpr int kStatusLimit = 4;
+constexpr int kStatusRange = 8;
+
+// ---------------------------------------------------------------------------
+// Hamiltonian tables (device) -- Fig. ham_prep, regrouped:
+//   pattern ids: [diag (XY = 0) if present][heavy patterns][light patterns],
+//   each class sorted by XY value; terms grouped by pattern id, sorted by z.
+// ---------------------------------------------------------------------------
+struct nqs_ham_dev {
+  int n_qubits = 0;
+  int W = 0;
+  int64_t n_terms = 0;
+  int64_t n_xy = 0;
+  int has_diag = 0;              // pattern 0 is XY = 0
+  int64_t heavy_end = 0;         // ids < heavy_end (and >= has_diag) are heavy
+  int64_t max_group = 0;
+  int64_t n_srch = 0;            // search-table slots, multiple of 32
+
+  uint64_t* xy = nullptr;        // [n_xy][W]
+  uint32_t* row_ptr = nullptr;   // [n_xy + 1]
+  uint64_t* yz = nullptr;        // [n_terms][W]
+  double* coef = nullptr;        // [n_terms]   h_l * (-1)^{|Y|/2}
+  float2* coef_f = nullptr;      // [n_terms]   (hi, lo) split of coef
+  uint32_t* srch_hash = nullptr; // [n_srch]    linear hash of each pattern
+  uint32_t* srch_id = nullptr;   // [n_srch]    pattern id or kDummy
+  uint32_t* hash_basis = nullptr;// [64 * W]    R[b]: h(v) = XOR of R[b] over set bits b
+
+  // host copies (export, tests)
+  std::vector<uint64_t> h_xy, h_yz;
+  std::vector<int64_t> h_row_ptr;
+  std::vector<double> h_coef;
+  std::vector<uint32_t> h_hash_basis;
+  int device = 0;
+};
+
+}  // namespace nqs
+
+struct nqs_ham : public nqs::nqs_ham_dev {};
+
+namespace nqs {
+
+// ---------------------------------------------------------------------------
+// Batch workspace ("stage") layout: all offsets 256-byte aligned.
+// ---------------------------------------------------------------------------
+struct StageHeader {
+  uint64_t magic;
+  int64_t n_unq;
+  int64_t cap;          // hash-table slots (power of two)
+  int64_t nwords;       // bloom words (power of two)
+  int32_t W;
+  int32_t status;       // device status word (kStatus* bits)
+  int64_t off_hx, off_table, off_bloom, off_scan, off_ampP, off_ampQ, off_ampK, off_geff;
+  int64_t scan_blocks;
+  int64_t total_bytes;
+};
+constexpr uint64_t kStageMagic = 0x6E71735F73746731ull;
+
+StageHeader stage_layout(const nqs_ham* ham, int64_t n_unq);
+
+// error reporting
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+// launchers (defined in the kernel translation units) -------------------------
+cudaError_t launch_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, char* stage,
+                         const StageHeader& L, cudaStream_t s);
+
+cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, const char* stage,
+                               const StageHeader& L, int64_t row_begin, int64_t row_end,
+                               int64_t* counts_or_rowptr, uint32_t* pair_j, uint32_t* pair_k,
+                               bool fill, cudaStream_t s);
+
+cudaError_t launch_pairs_batch(const nqs_ham* ham, const uint64_t* U, const char* stage,
+                               const StageHeader& L, int64_t row_begin, int64_t row_end,
+                               int64_t* counts_or_rowptr, uint32_t* pair_j, uint32_t* pair_k,
+                               bool fill, cudaStream_t s);
+
+cudaError_t launch_scan(int64_t* data, int64_t n, char* stage, const StageHeader& L,
+                        cudaStream_t s);
+
+cudaError_t launch_amplitudes(const double* a, const double* b, int64_t n, int precision,
+                              char* stage, const StageHeader& L, cudaStream_t s);
+
+cudaError_t launch_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
+                                const char* stage, const StageHeader& L, bool cplx,
+                                int64_t row_begin, int64_t row_end, const int64_t* row_ptr,
+                                const uint32_t* pair_j, const uint32_t* pair_k, int precision,
+                                double* eloc_re, double* eloc_im, double* hdiag,
+                                cudaStream_t s);
+
+cudaError_t launch_variational_energy(int64_t n, const double* a, const double* eloc_re,
+                                      double* out, cudaStream_t s);
+
+cudaError_t launch_backward(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
+                            char* stage, const StageHeader& L, bool cplx,
+                            const double* a, const double* b,
+                            int64_t row_begin, int64_t row_end, const int64_t* row_ptr,
+                            const uint32_t* pair_j, const uint32_t* pair_k,
+                            const double* eloc_re, const double* eloc_im, const double* hdiag,
+                            const double* evar, const double* g_re, const double* g_im,
+                            const double* g_evar, int precision, double* grad_re,
+                            double* grad_im, cudaStream_t s);
+
+int num_sms();
+
+}  // namespace nqs

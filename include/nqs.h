@@ -140,7 +140,10 @@ int nqs_stage_status(const void* work, void* stream);
  *   of row r; pair_j = column (index into U), pair_k = pattern index (into
  *   the library's unique-XY table).  Within a row the diagonal pair comes
  *   first (if the XY = 0 pattern exists), then pairs whose P_XY is large,
- *   then the rest, in a fixed order.  Both (i, j) and (j, i) are listed.
+ *   then the rest.  Rows are searched in batches of 8 starting at row_begin;
+ *   for a given row range the order is fixed (count, fill and one-pass calls
+ *   agree), while calls over other ranges may order a row's pairs
+ *   differently.  Both (i, j) and (j, i) are listed.
  * All calls need a workspace staged with the same U.  Readers of the CSR
  * (fill, energy, adjoint) take positions relative to row_ptr[0], so a slice
  * row_ptr + (r0 - row_begin) of a larger offset array can be passed for the
@@ -163,13 +166,23 @@ int nqs_fill_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
                            int schedule, const int64_t* row_ptr, uint32_t* pair_j,
                            uint32_t* pair_k, void* stream);
 
-/* Count + fill.  If capacity < total the call returns NQS_ERR_CAPACITY with
- * row_ptr and *n_pairs valid and nothing written to pair_j/pair_k. */
+/* Bytes of the scratch that nqs_find_coupled_pairs needs to list up to
+ * max_pairs pairs of `rows` rows in one pass. */
+int64_t nqs_pairs_scratch_bytes(int64_t rows, int64_t max_pairs);
+
+/* One search pass.  The pairs are written to scratch (device, 256-byte
+ * aligned, scratch_bytes from nqs_pairs_scratch_bytes) while the rows are
+ * counted, then copied in CSR order to pair_j/pair_k (device uint32,
+ * `capacity` entries).  Synchronises the stream (the total is returned in
+ * *n_pairs).  If the scratch or `capacity` is too small the call returns
+ * NQS_ERR_CAPACITY with row_ptr and *n_pairs valid and pair_j/pair_k
+ * unwritten; nqs_fill_coupled_pairs with the same row_ptr then completes the
+ * list.  scratch == NULL selects the two-pass form (count, then fill). */
 int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
                            void* work, int64_t row_begin, int64_t row_end,
-                           int schedule, int64_t* row_ptr, uint32_t* pair_j,
-                           uint32_t* pair_k, int64_t capacity, int64_t* n_pairs,
-                           void* stream);
+                           int schedule, void* scratch, int64_t scratch_bytes,
+                           int64_t* row_ptr, uint32_t* pair_j, uint32_t* pair_k,
+                           int64_t capacity, int64_t* n_pairs, void* stream);
 
 /* ---------------------------------------------------------------------------
  * MatrixElement + ScatterAdd -> E_loc^var (Sec. "MatrixElement

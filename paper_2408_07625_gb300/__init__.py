@@ -62,8 +62,9 @@ def load_library(path: str = None):
         "nqs_stage_status": (_i32, [_vp, _vp]),
         "nqs_count_coupled_pairs": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _vp, _c_i64p, _vp]),
         "nqs_fill_coupled_pairs": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _vp, _vp, _vp, _vp]),
-        "nqs_find_coupled_pairs": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _vp, _vp, _vp, _i64,
-                                          _c_i64p, _vp]),
+        "nqs_find_coupled_pairs": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _vp, _i64, _vp, _vp, _vp,
+                                          _i64, _c_i64p, _vp]),
+        "nqs_pairs_scratch_bytes": (_i64, [_i64, _i64]),
         "nqs_local_energy": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _i32,
                                     _vp, _vp, _vp, _vp]),
         "nqs_variational_energy": (_i32, [_i64, _vp, _vp, _vp, _vp]),
@@ -199,6 +200,9 @@ class Batch:
         if nbytes < 0:
             _check(nbytes)
         self.work = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self._scratch = None          # one-pass search scratch, grown on demand
+        self._pair_buf = None         # (pair_j, pair_k) buffers reused between calls
+        self._pair_guess = None
         _check(_lib.nqs_stage(ham.handle, _ptr(self.U), self.n, _ptr(self.work), nbytes,
                               1 if check else 0, _stream(stream)))
 
@@ -236,14 +240,53 @@ def fill_pairs(batch: Batch, row_ptr, n_pairs, row_begin=0, row_end=None, schedu
     return pj[:n_pairs], pk[:n_pairs]
 
 
-def coupled_pairs(batch: Batch, row_begin=0, row_end=None, schedule="terms", stream=None):
+def _grow(batch, rows, max_pairs):
+    nbytes = int(_lib.nqs_pairs_scratch_bytes(rows, max_pairs))
+    if batch._scratch is None or batch._scratch.numel() < nbytes:
+        batch._scratch = torch.empty(nbytes, dtype=torch.uint8, device=batch.device)
+    if batch._pair_buf is None or batch._pair_buf[0].numel() < max_pairs:
+        batch._pair_buf = (torch.empty(max(max_pairs, 1), dtype=torch.int32, device=batch.device),
+                           torch.empty(max(max_pairs, 1), dtype=torch.int32, device=batch.device))
+
+
+def coupled_pairs(batch: Batch, row_begin=0, row_end=None, schedule="terms", one_pass=True,
+                  reuse=False, stream=None):
     """FindCoupledPairs over rows [row_begin, row_end): CSR (row_ptr, j, k) as CUDA tensors.
 
     ``j`` and ``k`` are int32 tensors holding uint32 column and pattern indices.
+    With ``one_pass`` the search runs once, writing into a scratch kept on the
+    batch (grown and retried through the fill pass when too small).  With
+    ``reuse`` the returned pair tensors are views of buffers that the next
+    call on this batch overwrites.
     """
-    row_ptr, n = count_pairs(batch, row_begin, row_end, schedule, stream)
-    pj, pk = fill_pairs(batch, row_ptr, n, row_begin, row_end, schedule, stream)
-    return row_ptr, pj, pk
+    row_end = batch.n if row_end is None else int(row_end)
+    rows = row_end - int(row_begin)
+    if not one_pass:
+        row_ptr, n = count_pairs(batch, row_begin, row_end, schedule, stream)
+        pj, pk = fill_pairs(batch, row_ptr, n, row_begin, row_end, schedule, stream)
+        return row_ptr, pj, pk
+    guess = batch._pair_guess or max(256 * rows, 1024)
+    _grow(batch, rows, guess)
+    row_ptr = torch.empty(rows + 1, dtype=torch.int64, device=batch.device)
+    n = ctypes.c_int64()
+    pj, pk = batch._pair_buf
+    rc = _lib.nqs_find_coupled_pairs(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work),
+                                     int(row_begin), row_end, SCHEDULES[schedule], _ptr(batch._scratch),
+                                     batch._scratch.numel(), _ptr(row_ptr), _ptr(pj), _ptr(pk),
+                                     pj.numel(), ctypes.byref(n), _stream(stream))
+    total = int(n.value)
+    batch._pair_guess = max(guess, int(total * 1.15) + 1024)
+    if rc == -4:  # scratch or buffers too small: row_ptr is valid, complete with the fill pass
+        _grow(batch, rows, batch._pair_guess)
+        pj, pk = batch._pair_buf
+        _check(_lib.nqs_fill_coupled_pairs(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work),
+                                           int(row_begin), row_end, SCHEDULES[schedule], _ptr(row_ptr),
+                                           _pair_ptr(pj), _pair_ptr(pk), _stream(stream)))
+    else:
+        _check(rc)
+    if reuse:
+        return row_ptr, pj[:total], pk[:total]
+    return row_ptr, pj[:total].clone(), pk[:total].clone()
 
 
 def local_energy(batch: Batch, logpsi_re, logpsi_im=None, pairs=None, precision="fp32c",
@@ -321,31 +364,36 @@ def _row_chunks(row_ptr_host, max_pairs):
 
 def evaluate(batch: Batch, logpsi_re, logpsi_im=None, precision="fp32c", schedule="terms",
              max_pairs=None, keep_pairs=True, stream=None):
-    """Whole forward path: pairs (chunked by rows under ``max_pairs``), E_loc^var, E^var.
+    """Whole forward path: FindCoupledPairs, E_loc^var, E^var.
 
+    Without ``max_pairs`` the search runs once (one-pass mode).  With it, rows
+    are split into contiguous chunks holding at most ``max_pairs`` pairs each,
+    and each chunk's pairs are listed, consumed and dropped in turn.
     Returns dict(eloc_re, eloc_im, hdiag, evar, n_pairs, pairs or None, chunks).
     """
     dev = batch.device
     a = _f64(logpsi_re, dev)
     b = _f64(logpsi_im, dev)
-    row_ptr, total = count_pairs(batch, 0, batch.n, schedule, stream)
     er = torch.zeros(batch.n, dtype=torch.float64, device=dev)
     ei = torch.zeros(batch.n, dtype=torch.float64, device=dev) if b is not None else None
     hd = torch.zeros(batch.n, dtype=torch.float64, device=dev)
     rp_host = None
-    if max_pairs is None or total <= max_pairs:
-        chunks = [(0, batch.n)]
-    else:
-        rp_host = row_ptr.cpu().numpy()
-        chunks = _row_chunks(rp_host, int(max_pairs))
     kept = None
-    for (r0, r1) in chunks:
-        rp = row_ptr[r0:r1 + 1]
-        npairs = total if rp_host is None else int(rp_host[r1] - rp_host[r0])
-        pj, pk = fill_pairs(batch, rp, npairs, r0, r1, schedule, stream)
-        local_energy(batch, a, b, (rp, pj, pk), precision, r0, r1, (er, ei, hd), stream)
-        if len(chunks) == 1 and keep_pairs:
-            kept = (rp, pj, pk)
+    if max_pairs is None:
+        pairs = coupled_pairs(batch, 0, batch.n, schedule, reuse=not keep_pairs, stream=stream)
+        row_ptr, total, chunks = pairs[0], int(pairs[1].numel()), [(0, batch.n)]
+        local_energy(batch, a, b, pairs, precision, 0, batch.n, (er, ei, hd), stream)
+        kept = pairs if keep_pairs else None
+    else:
+        row_ptr, total = count_pairs(batch, 0, batch.n, schedule, stream)
+        rp_host = row_ptr.cpu().numpy()
+        chunks = _row_chunks(rp_host, int(max_pairs)) if total > max_pairs else [(0, batch.n)]
+        for (r0, r1) in chunks:
+            rp = row_ptr[r0:r1 + 1]
+            pj, pk = fill_pairs(batch, rp, int(rp_host[r1] - rp_host[r0]), r0, r1, schedule, stream)
+            local_energy(batch, a, b, (rp, pj, pk), precision, r0, r1, (er, ei, hd), stream)
+            if len(chunks) == 1 and keep_pairs:
+                kept = (rp, pj, pk)
     evar = variational_energy(a, er, stream=stream)
     return {"eloc_re": er, "eloc_im": ei, "hdiag": hd, "evar": evar, "n_pairs": total,
             "pairs": kept, "chunks": chunks, "row_ptr": row_ptr, "row_ptr_host": rp_host,

@@ -49,7 +49,7 @@ StageHeader stage_layout(const nqs_ham* ham, int64_t n) {
   L.nwords = std::min<int64_t>(std::max<int64_t>(next_pow2(std::max<int64_t>(n / 2, 1)), 32), 32768);
   int64_t off = align256(sizeof(StageHeader));
   L.off_hx = off;     off = align256(off + 4 * std::max<int64_t>(n, 1));
-  L.off_table = off;  off = align256(off + 4 * L.cap);
+  L.off_table = off;  off = align256(off + 8 * (L.W + 1) * L.cap);
   L.off_bloom = off;  off = align256(off + 4 * L.nwords);
   L.scan_blocks = (std::max<int64_t>(n, 1) + 1023) / 1024 + 1;
   L.off_scan = off;   off = align256(off + 8 * L.scan_blocks);
@@ -57,6 +57,7 @@ StageHeader stage_layout(const nqs_ham* ham, int64_t n) {
   L.off_ampQ = off;   off = align256(off + 16 * std::max<int64_t>(n, 1));
   L.off_ampK = off;   off = align256(off + 4 * std::max<int64_t>(n, 1));
   L.off_geff = off;   off = align256(off + 16 * std::max<int64_t>(n, 1));
+  L.off_counters = off; off = align256(off + 256);
   L.total_bytes = off;
   return L;
 }
@@ -356,7 +357,7 @@ int nqs_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, int6
   char* base = (char*)work;
   cudaError_t e = cudaMemcpyAsync(base, &L, sizeof(L), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e, "header copy");
-  if ((e = cudaMemsetAsync(base + L.off_table, 0xFF, 4 * L.cap, s)) != cudaSuccess) return cuda_fail(e, "memset");
+  if ((e = cudaMemsetAsync(base + L.off_table, 0xFF, 8 * (L.W + 1) * L.cap, s)) != cudaSuccess) return cuda_fail(e, "memset");
   if ((e = cudaMemsetAsync(base + L.off_bloom, 0, 4 * L.nwords, s)) != cudaSuccess) return cuda_fail(e, "memset");
   if ((e = launch_stage(ham, U, n, base, L, s)) != cudaSuccess) return cuda_fail(e, "stage kernel");
   if (check) return read_status(work, s);
@@ -373,19 +374,26 @@ static int check_rows(int64_t n, int64_t rb, int64_t re) {
   return NQS_OK;
 }
 
-static cudaError_t launch_search(const nqs_ham* ham, const uint64_t* U, const char* work,
-                                 const StageHeader& L, int64_t rb, int64_t re, int schedule,
-                                 int64_t* rp, uint32_t* pj, uint32_t* pk, bool fill, cudaStream_t s) {
-  if (schedule == NQS_SCHED_BATCH)
-    return launch_pairs_batch(ham, U, work, L, rb, re, rp, pj, pk, fill, s);
-  return launch_pairs_terms(ham, U, work, L, rb, re, rp, pj, pk, fill, s);
+static int check_schedule(int schedule) {
+  if (schedule == NQS_SCHED_AUTO || schedule == NQS_SCHED_TERMS) return NQS_OK;
+  if (schedule == NQS_SCHED_BATCH || schedule == NQS_SCHED_TRIE)
+    return fail(NQS_ERR_UNSUPPORTED, "schedule not built yet");
+  return fail(NQS_ERR_ARG, "unknown schedule");
 }
 
-static int check_schedule(int schedule) {
-  if (schedule == NQS_SCHED_AUTO || schedule == NQS_SCHED_TERMS || schedule == NQS_SCHED_BATCH)
-    return NQS_OK;
-  if (schedule == NQS_SCHED_TRIE) return fail(NQS_ERR_UNSUPPORTED, "trie schedule not built yet");
-  return fail(NQS_ERR_ARG, "unknown schedule");
+static int count_pass(const nqs_ham* ham, const uint64_t* U, void* work, const StageHeader& L,
+                      int64_t rb, int64_t re, int64_t* row_ptr, const PairScratch* sc, cudaStream_t s) {
+  const int64_t rows = re - rb;
+  cudaError_t e = cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), s);
+  if (e != cudaSuccess) return cuda_fail(e, "memset row_ptr");
+  if (rows > 0) {
+    if ((e = launch_pairs_terms(ham, U, (char*)work, L, rb, re, row_ptr + 1, nullptr, nullptr,
+                                sc ? kEmit : kCount, sc, s)) != cudaSuccess)
+      return cuda_fail(e, "pair search kernel");
+    if ((e = launch_scan(row_ptr + 1, rows, (char*)work, L, s)) != cudaSuccess)
+      return cuda_fail(e, "scan kernel");
+  }
+  return NQS_OK;
 }
 
 int nqs_count_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work,
@@ -396,17 +404,8 @@ int nqs_count_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, vo
   if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(schedule))) return rc;
   if (!row_ptr || !n_pairs) return fail(NQS_ERR_ARG, "null row_ptr or n_pairs");
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t rows = re - rb;
-  cudaError_t e = cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), s);
-  if (e != cudaSuccess) return cuda_fail(e, "memset row_ptr");
-  if (rows > 0) {
-    if ((e = launch_search(ham, U, (char*)work, L, rb, re, schedule, row_ptr + 1, nullptr, nullptr,
-                           false, s)) != cudaSuccess)
-      return cuda_fail(e, "pair count kernel");
-    if ((e = launch_scan(row_ptr + 1, rows, (char*)work, L, s)) != cudaSuccess)
-      return cuda_fail(e, "scan kernel");
-  }
-  e = cudaMemcpyAsync(n_pairs, row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if ((rc = count_pass(ham, U, work, L, rb, re, row_ptr, nullptr, s))) return rc;
+  cudaError_t e = cudaMemcpyAsync(n_pairs, row_ptr + (re - rb), sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_fail(e, "count copy");
   return read_status(work, s);
 }
@@ -419,20 +418,51 @@ int nqs_fill_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
   if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(schedule))) return rc;
   if (!row_ptr || !pair_j || !pair_k) return fail(NQS_ERR_ARG, "null output");
   if (re == rb) return NQS_OK;
-  cudaError_t e = launch_search(ham, U, (char*)work, L, rb, re, schedule, (int64_t*)row_ptr,
-                                pair_j, pair_k, true, (cudaStream_t)stream);
+  cudaError_t e = launch_pairs_terms(ham, U, (char*)work, L, rb, re, (int64_t*)row_ptr, pair_j, pair_k,
+                                     kFill, nullptr, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "pair fill kernel");
   return NQS_OK;
 }
 
+int64_t nqs_pairs_scratch_bytes(int64_t rows, int64_t max_pairs) {
+  if (rows < 0 || max_pairs < 0) return fail(NQS_ERR_ARG, "negative size");
+  return pair_scratch_bytes(rows, max_pairs);
+}
+
 int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work,
-                           int64_t rb, int64_t re, int schedule, int64_t* row_ptr,
-                           uint32_t* pair_j, uint32_t* pair_k, int64_t capacity,
+                           int64_t rb, int64_t re, int schedule, void* scratch, int64_t scratch_bytes,
+                           int64_t* row_ptr, uint32_t* pair_j, uint32_t* pair_k, int64_t capacity,
                            int64_t* n_pairs, void* stream) {
-  int rc = nqs_count_coupled_pairs(ham, U, n, work, rb, re, schedule, row_ptr, n_pairs, stream);
-  if (rc) return rc;
+  StageHeader L;
+  int rc = check_work(ham, U, n, work, &L);
+  if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(schedule))) return rc;
+  if (!row_ptr || !n_pairs) return fail(NQS_ERR_ARG, "null row_ptr or n_pairs");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t rows = re - rb;
+  if (!scratch) {  // two passes: count, then fill
+    rc = nqs_count_coupled_pairs(ham, U, n, work, rb, re, schedule, row_ptr, n_pairs, stream);
+    if (rc) return rc;
+    if (*n_pairs > capacity) return fail(NQS_ERR_CAPACITY, "pair capacity too small");
+    if (*n_pairs > 0 && (!pair_j || !pair_k)) return fail(NQS_ERR_ARG, "null pair arrays");
+    return nqs_fill_coupled_pairs(ham, U, n, work, rb, re, schedule, row_ptr, pair_j, pair_k, stream);
+  }
+  if (((uintptr_t)scratch) & 255) return fail(NQS_ERR_ARG, "scratch not 256-byte aligned");
+  PairScratch sc = pair_scratch_view(scratch, rows, scratch_bytes);
+  if (sc.max_chunks < 1) return fail(NQS_ERR_CAPACITY, "scratch too small");
+  if ((rc = count_pass(ham, U, work, L, rb, re, row_ptr, &sc, s))) return rc;
+  int64_t overflow = 0;
+  cudaError_t e = cudaMemcpyAsync(n_pairs, row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "count copy");
+  e = cudaMemcpyAsync(&overflow, sc.cursor + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "flag copy");
+  if ((rc = read_status(work, s))) return rc;
+  if (overflow) return fail(NQS_ERR_CAPACITY, "scratch too small for the pairs found");
   if (*n_pairs > capacity) return fail(NQS_ERR_CAPACITY, "pair capacity too small");
-  return nqs_fill_coupled_pairs(ham, U, n, work, rb, re, schedule, row_ptr, pair_j, pair_k, stream);
+  if (rows == 0 || *n_pairs == 0) return NQS_OK;
+  if (!pair_j || !pair_k) return fail(NQS_ERR_ARG, "null pair arrays");
+  e = launch_pairs_compact(sc, rows, row_ptr, pair_j, pair_k, s);
+  if (e != cudaSuccess) return cuda_fail(e, "compaction kernel");
+  return NQS_OK;
 }
 
 int nqs_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work,

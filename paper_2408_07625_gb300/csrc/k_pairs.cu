@@ -5,19 +5,20 @@
 // of two precomputed values, h(x) ^ h(XY).  A blocked Bloom filter of U
 // (one 32-bit word per key, two bits set) lives in shared memory and rejects
 // most candidates; survivors are verified in an open-addressing table of U
-// (linear probing, load <= 1/2) that stays resident in L2.
+// (keys stored in the slots, linear probing, load <= 1/2) resident in L2.
 #include "device_util.cuh"
 #include "nqs_internal.cuh"
 
 namespace nqs {
 
 // --------------------------------------------------------------------------
-// staging: hash of each sample, hash table and Bloom filter of U
+// staging: hash of each sample, keyed hash table and Bloom filter of U
+// table slot = W key words followed by the sample index (all ones: empty)
 // --------------------------------------------------------------------------
 template <int W>
 __global__ void stage_kernel(const uint64_t* __restrict__ U, int64_t n, int n_qubits,
                              const uint32_t* __restrict__ basis, int64_t cap, uint32_t wmask,
-                             uint32_t* __restrict__ hx_out, int32_t* __restrict__ table,
+                             uint32_t* __restrict__ hx_out, unsigned long long* __restrict__ table,
                              uint32_t* __restrict__ bloom, int32_t* __restrict__ status) {
   __shared__ uint32_t R[64 * W];
   for (int i = threadIdx.x; i < 64 * W; i += blockDim.x) R[i] = basis[i];
@@ -43,8 +44,14 @@ __global__ void stage_kernel(const uint64_t* __restrict__ U, int64_t n, int n_qu
     int64_t slot = h & (cap - 1);
     bool placed = false;
     for (int64_t it = 0; it < cap; ++it) {
-      int prev = atomicCAS(&table[slot], -1, (int)i);
-      if (prev == -1) { placed = true; break; }
+      unsigned long long* sl = table + slot * (W + 1);
+      unsigned long long prev = atomicCAS(sl + W, ~0ull, (unsigned long long)i);
+      if (prev == ~0ull) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) sl[w] = v[w];
+        placed = true;
+        break;
+      }
       bool eq = true;
 #pragma unroll
       for (int w = 0; w < W; ++w) eq = eq && (__ldg(U + (int64_t)prev * W + w) == v[w]);
@@ -61,7 +68,7 @@ cudaError_t launch_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, char*
   if (n == 0) return cudaSuccess;
   int blocks = (int)std::min<int64_t>((n + 255) / 256, 4 * num_sms());
   auto* hx = (uint32_t*)(stage + L.off_hx);
-  auto* table = (int32_t*)(stage + L.off_table);
+  auto* table = (unsigned long long*)(stage + L.off_table);
   auto* bloom = (uint32_t*)(stage + L.off_bloom);
   auto* status = (int32_t*)(stage + offsetof(StageHeader, status));
   uint32_t wmask = (uint32_t)(L.nwords - 1);
@@ -75,189 +82,361 @@ cudaError_t launch_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, char*
 }
 
 // --------------------------------------------------------------------------
-// LoopOverTerms search.  One warp scans kRowsPerWarp rows against the whole
-// search table; lanes take 32 consecutive slots, whose hash low bits are
-// distinct, so each shared-memory Bloom probe is conflict-free.  Filter hits
-// go to a per-warp queue; a full queue is verified lane-parallel against the
-// hash table.  COUNT writes per-row pair counts; FILL writes (j, k) at the
-// offsets of a previous COUNT, in the same deterministic order.
+// one-pass scratch: linked chunks of pair records per row batch
+// --------------------------------------------------------------------------
+static inline int64_t a256(int64_t v) { return (v + 255) & ~int64_t(255); }
+
+int64_t pair_scratch_bytes(int64_t rows, int64_t max_pairs) {
+  const int64_t nb = (rows + kRowsPerWarp - 1) / kRowsPerWarp;
+  const int64_t chunks = (max_pairs + kChunk - 1) / kChunk + nb;
+  return 256 + a256(4 * std::max<int64_t>(nb, 1)) + a256(4 * chunks) + 8 * kChunk * chunks;
+}
+
+PairScratch pair_scratch_view(void* base, int64_t rows, int64_t bytes) {
+  PairScratch sc;
+  const int64_t nb = (rows + kRowsPerWarp - 1) / kRowsPerWarp;
+  char* p = (char*)base;
+  sc.cursor = (int64_t*)p;
+  sc.heads = (int32_t*)(p + 256);
+  int64_t rest = bytes - 256 - a256(4 * std::max<int64_t>(nb, 1));
+  int64_t chunks = rest / (4 + 8 * kChunk);
+  while (chunks > 0 && a256(4 * chunks) + 8 * kChunk * chunks > rest) --chunks;
+  sc.max_chunks = std::max<int64_t>(chunks, 0);
+  sc.next = (int32_t*)(p + 256 + a256(4 * std::max<int64_t>(nb, 1)));
+  sc.records = (uint64_t*)((char*)sc.next + a256(4 * std::max<int64_t>(sc.max_chunks, 1)));
+  return sc;
+}
+
+// --------------------------------------------------------------------------
+// LoopOverTerms search.  A warp owns a batch of kRowsPerWarp rows (taken from
+// a global counter) and streams the search table: lane t takes slot 32g + t.
+// The 32 slots of a group have distinct low hash bits, so the 32 Bloom-word
+// loads of one row hit 32 distinct shared-memory banks.  Per slot a lane keeps
+// a bit mask of the rows whose filter test passed; one ballot per group pushes
+// (mask, slot) entries to a per-warp queue, verified lane-parallel against the
+// hash table when the queue fills.
 // --------------------------------------------------------------------------
 constexpr int kSearchThreads = 1024;
 constexpr int kSearchWarps = kSearchThreads / 32;
+constexpr int R = kRowsPerWarp;
 
-template <int W, bool FILL>
-__device__ __forceinline__ void flush_queue(const uint32_t* q, int qn, int64_t r0,
-                                            const uint64_t* __restrict__ U,
-                                            const uint32_t* __restrict__ hx,
-                                            const int32_t* __restrict__ table, int64_t capmask,
-                                            const uint32_t* __restrict__ srch_hash,
-                                            const uint32_t* __restrict__ srch_id,
-                                            const uint64_t* __restrict__ xy,
-                                            int64_t (&acc)[kRowsPerWarp],
-                                            uint32_t* __restrict__ pair_j,
-                                            uint32_t* __restrict__ pair_k, int32_t* status) {
+struct SearchArgs {
+  const uint64_t* U;
+  const uint32_t* hx;
+  const unsigned long long* table;
+  int64_t capmask;
+  const uint32_t* bloom_g;
+  uint32_t wmask;
+  int nwords;
+  const uint32_t* srch_hash;
+  const uint32_t* srch_id;
+  int64_t n_groups;
+  const uint64_t* xy;
+  int has_diag;
+  int64_t row_begin, row_end;
+  int64_t* rp;
+  uint32_t* pair_j;
+  uint32_t* pair_k;
+  int32_t* status;
+  unsigned long long* batch_counter;
+  PairScratch sc;
+};
+
+struct EmitState {  // warp-uniform chunk state of the one-pass mode
+  int32_t chunk, fill, first;
+};
+
+template <int MODE>
+__device__ __forceinline__ void emit_round(bool found, int r, uint32_t j, uint32_t id,
+                                           int64_t (&acc)[R], EmitState& es, const SearchArgs& a) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
-  for (int e0 = 0; e0 < qn; e0 += 32) {
-    const int e = e0 + lane;
-    bool found = false;
-    uint32_t j = 0, id = 0, r = 0;
-    if (e < qn) {
-      const uint32_t v = q[e];
-      r = v >> 28;
-      const uint32_t pos = v & 0x0FFFFFFFu;
-      id = __ldg(srch_id + pos);
-      if (id != kDummy) {
-        const int64_t row = r0 + r;
-        uint64_t key[W];
 #pragma unroll
-        for (int w = 0; w < W; ++w) key[w] = __ldg(U + row * W + w) ^ __ldg(xy + (int64_t)id * W + w);
-        int64_t slot = (__ldg(hx + row) ^ __ldg(srch_hash + pos)) & capmask;
-        int64_t it = 0;
-        for (; it <= capmask; ++it) {
-          const int t = __ldg(table + slot);
-          if (t < 0) break;
-          bool eq = true;
-#pragma unroll
-          for (int w = 0; w < W; ++w) eq = eq && (__ldg(U + (int64_t)t * W + w) == key[w]);
-          if (eq) { found = true; j = (uint32_t)t; break; }
-          slot = (slot + 1) & capmask;
-        }
-        if (it > capmask) atomicOr(status, kStatusLimit);
+  for (int rr = 0; rr < R; ++rr) {
+    const uint32_t m = __ballot_sync(kFull, found && r == rr);
+    if (MODE == kFill && found && r == rr) {
+      const int64_t p = acc[rr] + __popc(m & lt);
+      a.pair_j[p] = j;
+      a.pair_k[p] = id;
+    }
+    acc[rr] += __popc(m);
+  }
+  if (MODE == kEmit) {
+    const uint32_t m = __ballot_sync(kFull, found);
+    const int n = __popc(m);
+    if (n == 0 || es.chunk == -2) return;
+    const int off = __popc(m & lt);
+    const uint64_t rec = (uint64_t)j | ((uint64_t)id << 32) | ((uint64_t)r << 61);
+    const int room = es.chunk >= 0 ? kChunk - es.fill : 0;
+    if (n <= room) {
+      if (found) a.sc.records[(int64_t)es.chunk * kChunk + es.fill + off] = rec;
+      es.fill += n;
+      return;
+    }
+    int32_t fresh = -2;
+    if (lane == 0) {
+      const unsigned long long c = atomicAdd((unsigned long long*)a.sc.cursor, 1ull);
+      if ((int64_t)c < a.sc.max_chunks) {
+        fresh = (int32_t)c;
+        if (es.chunk >= 0) a.sc.next[es.chunk] = fresh;
+      } else {
+        atomicOr((unsigned long long*)(a.sc.cursor + 1), 1ull);
       }
     }
+    fresh = __shfl_sync(kFull, fresh, 0);
+    if (found) {
+      if (off < room) a.sc.records[(int64_t)es.chunk * kChunk + es.fill + off] = rec;
+      else if (fresh >= 0) a.sc.records[(int64_t)fresh * kChunk + (off - room)] = rec;
+    }
+    if (fresh >= 0 && es.first < 0) es.first = fresh;
+    es.chunk = fresh;
+    es.fill = n - room;
+  }
+}
+
+template <int W, int MODE>
+__device__ __forceinline__ void flush_queue(const uint32_t* q, int qn, int64_t r0, int64_t (&acc)[R],
+                                            EmitState& es, const SearchArgs& a) {
+  const int lane = threadIdx.x & 31;
+  for (int e0 = 0; e0 < qn; e0 += 32) {
+    const int e = e0 + lane;
+    const uint32_t ent = e < qn ? q[e] : 0u;
+    uint32_t bits = ent >> 24;
+    const uint32_t pos = ent & 0x00FFFFFFu;
+    while (__any_sync(kFull, bits != 0u)) {
+      bool found = false;
+      int r = 0;
+      uint32_t j = 0, id = 0;
+      if (bits) {
+        const int b = 31 - __clz(bits);
+        bits &= ~(1u << b);
+        r = R - 1 - b;
+        id = __ldg(a.srch_id + pos);
+        if (id != kDummy) {
+          const int64_t row = r0 + r;
+          uint64_t key[W];
 #pragma unroll
-    for (int rr = 0; rr < kRowsPerWarp; ++rr) {
-      const uint32_t m = __ballot_sync(kFull, found && r == (uint32_t)rr);
-      if (FILL) {
-        if (found && r == (uint32_t)rr) {
-          const int64_t p = acc[rr] + __popc(m & lt);
-          pair_j[p] = j;
-          pair_k[p] = id;
+          for (int w = 0; w < W; ++w) key[w] = __ldg(a.U + row * W + w) ^ __ldg(a.xy + (int64_t)id * W + w);
+          int64_t slot = (__ldg(a.hx + row) ^ __ldg(a.srch_hash + pos)) & a.capmask;
+          int64_t it = 0;
+          for (; it <= a.capmask; ++it) {
+            const unsigned long long* sl = a.table + slot * (W + 1);
+            const unsigned long long idx = __ldg(sl + W);
+            if (idx == ~0ull) break;
+            bool eq = true;
+#pragma unroll
+            for (int w = 0; w < W; ++w) eq = eq && (__ldg(sl + w) == key[w]);
+            if (eq) { found = true; j = (uint32_t)idx; break; }
+            slot = (slot + 1) & a.capmask;
+          }
+          if (it > a.capmask) atomicOr(a.status, kStatusLimit);
         }
       }
-      acc[rr] += __popc(m);
+      emit_round<MODE>(found, r, j, id, acc, es, a);
     }
   }
 }
 
-template <int W, bool FILL>
-__global__ void __launch_bounds__(kSearchThreads, 1)
-pairs_terms_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict__ hx,
-                   const int32_t* __restrict__ table, int64_t capmask,
-                   const uint32_t* __restrict__ bloom_g, uint32_t wmask, int nwords,
-                   const uint32_t* __restrict__ srch_hash, const uint32_t* __restrict__ srch_id,
-                   int64_t n_groups, const uint64_t* __restrict__ xy, int has_diag,
-                   int64_t row_begin, int64_t row_end, int64_t* __restrict__ rp,
-                   uint32_t* __restrict__ pair_j, uint32_t* __restrict__ pair_k,
-                   int32_t* __restrict__ status) {
-  extern __shared__ uint32_t smem[];
+template <int W, int MODE>
+__global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const SearchArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* bloom = smem;
-  uint32_t* queue = smem + nwords;
+  uint32_t* queue = smem + a.nwords;
   {
-    const uint4* src = reinterpret_cast<const uint4*>(bloom_g);
+    const uint4* src = reinterpret_cast<const uint4*>(a.bloom_g);
     uint4* dst = reinterpret_cast<uint4*>(bloom);
-    for (int i = threadIdx.x; i < nwords / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+    for (int i = threadIdx.x; i < a.nwords / 4; i += blockDim.x) dst[i] = __ldg(src + i);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   uint32_t* q = queue + warp * kQueueCap;
   const uint32_t lt = (1u << lane) - 1u;
-  const int64_t n_rows = row_end - row_begin;
-  const int64_t n_batches = (n_rows + kRowsPerWarp - 1) / kRowsPerWarp;
-  const int64_t tw = (int64_t)gridDim.x * kSearchWarps;
-  const int64_t pbase = FILL ? rp[0] : 0;
-  for (int64_t bt = (int64_t)blockIdx.x * kSearchWarps + warp; bt < n_batches; bt += tw) {
-    const int64_t r0 = row_begin + bt * kRowsPerWarp;
-    uint32_t hr[kRowsPerWarp];
-    bool val[kRowsPerWarp];
-    int64_t acc[kRowsPerWarp];
+  const int64_t n_rows = a.row_end - a.row_begin;
+  const int64_t n_batches = (n_rows + R - 1) / R;
+  const uint32_t wmask4 = a.wmask << 2;
+  const char* bloom_bytes = reinterpret_cast<const char*>(bloom);
+  const int64_t pbase = (MODE == kFill) ? a.rp[0] : 0;
+  while (true) {
+    unsigned long long btu = 0;
+    if (lane == 0) btu = atomicAdd(a.batch_counter, 1ull);
+    const int64_t bt = (int64_t)__shfl_sync(kFull, btu, 0);
+    if (bt >= n_batches) break;
+    const int64_t r0 = a.row_begin + bt * R;
+    uint32_t hr4[R], hr17[R], hr22[R];
+    uint32_t vmask = 0;
+    int64_t acc[R];
 #pragma unroll
-    for (int r = 0; r < kRowsPerWarp; ++r) {
+    for (int r = 0; r < R; ++r) {
       const int64_t row = r0 + r;
-      val[r] = row < row_end;
-      hr[r] = val[r] ? __ldg(hx + row) : 0u;
-      acc[r] = (FILL && val[r]) ? rp[row - row_begin] - pbase : 0;
-      if (has_diag && val[r]) {  // the diagonal pair (x, x) comes first
-        if (FILL && lane == 0) {
-          pair_j[acc[r]] = (uint32_t)row;
-          pair_k[acc[r]] = 0u;
-        }
-        acc[r] += 1;
-      }
+      const bool valid = row < a.row_end;
+      const uint32_t h = valid ? __ldg(a.hx + row) : 0u;
+      hr4[r] = h << 2;
+      hr17[r] = h >> 17;
+      hr22[r] = h >> 22;
+      if (valid) vmask |= 1u << (R - 1 - r);
+      acc[r] = (MODE == kFill && valid) ? a.rp[row - a.row_begin] - pbase : 0;
+    }
+    EmitState es{-1, 0, -1};
+    if (a.has_diag) {  // the diagonal pair (x, x) comes first in its row
+      const bool d = lane < R && r0 + lane < a.row_end;
+      emit_round<MODE>(d, lane, (uint32_t)(r0 + lane), 0u, acc, es, a);
     }
     int qn = 0;
-    for (int64_t g = 0; g < n_groups; ++g) {
+    for (int64_t g = 0; g < a.n_groups; ++g) {
       const uint32_t pos = (uint32_t)(g * 32 + lane);
-      const uint32_t hk = __ldg(srch_hash + pos);
+      const uint32_t hk = __ldg(a.srch_hash + pos);
+      const uint32_t hk4 = hk << 2, hk17 = hk >> 17, hk22 = hk >> 22;
+      uint32_t hm = 0;
 #pragma unroll
-      for (int r = 0; r < kRowsPerWarp; ++r) {
-        const uint32_t s = hr[r] ^ hk;
-        const uint32_t w = bloom[s & wmask];
-        const bool hit = val[r] && bloom_hit(w, s);
-        const uint32_t bal = __ballot_sync(kFull, hit);
-        if (bal) {
-          if (hit) q[qn + __popc(bal & lt)] = ((uint32_t)r << 28) | pos;
-          qn += __popc(bal);
-        }
+      for (int r = 0; r < R; ++r) {
+        const uint32_t w = *reinterpret_cast<const uint32_t*>(bloom_bytes + ((hr4[r] ^ hk4) & wmask4));
+        const uint32_t t = __funnelshift_r(w, w, hr17[r] ^ hk17) & __funnelshift_r(w, w, hr22[r] ^ hk22);
+        hm = (hm << 1) | (t & 1u);
       }
-      if (qn > kQueueCap - 32 * kRowsPerWarp) {
-        __syncwarp();
-        flush_queue<W, FILL>(q, qn, r0, U, hx, table, capmask, srch_hash, srch_id, xy, acc, pair_j,
-                             pair_k, status);
-        __syncwarp();
-        qn = 0;
+      hm &= vmask;
+      const uint32_t bal = __ballot_sync(kFull, hm != 0u);
+      if (bal) {
+        if (hm) q[qn + __popc(bal & lt)] = (hm << 24) | pos;
+        qn += __popc(bal);
+        if (qn > kQueueCap - 32) {
+          __syncwarp();
+          flush_queue<W, MODE>(q, qn, r0, acc, es, a);
+          __syncwarp();
+          qn = 0;
+        }
       }
     }
     __syncwarp();
-    flush_queue<W, FILL>(q, qn, r0, U, hx, table, capmask, srch_hash, srch_id, xy, acc, pair_j,
-                         pair_k, status);
+    flush_queue<W, MODE>(q, qn, r0, acc, es, a);
     __syncwarp();
-    if (!FILL && lane == 0) {
+    if (MODE != kFill && lane == 0) {
 #pragma unroll
-      for (int r = 0; r < kRowsPerWarp; ++r)
-        if (val[r]) rp[r0 + r - row_begin] = acc[r];
+      for (int r = 0; r < R; ++r)
+        if (r0 + r < a.row_end) a.rp[r0 + r - a.row_begin] = acc[r];
+    }
+    if (MODE == kEmit && lane == 0) {
+      a.sc.heads[bt] = es.first;
+      if (es.chunk >= 0) a.sc.next[es.chunk] = -1;
     }
   }
 }
 
-template <int W, bool FILL>
-static cudaError_t launch_terms_w(const nqs_ham* ham, const uint64_t* U, const char* stage,
-                                  const StageHeader& L, int64_t rb, int64_t re, int64_t* rp,
-                                  uint32_t* pj, uint32_t* pk, cudaStream_t s) {
-  const size_t smem = 4 * (size_t)L.nwords + (size_t)kSearchWarps * kQueueCap * 4;
-  auto kern = pairs_terms_kernel<W, FILL>;
+template <int W, int MODE>
+static cudaError_t launch_terms_w(const SearchArgs& args, int64_t rows, size_t smem, cudaStream_t s) {
+  auto kern = pairs_terms_kernel<W, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kSearchThreads, smem);
   if (occ < 1) occ = 1;
-  const int64_t batches = (re - rb + kRowsPerWarp - 1) / kRowsPerWarp;
+  const int64_t batches = (rows + R - 1) / R;
   const int64_t need = (batches + kSearchWarps - 1) / kSearchWarps;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * occ));
-  kern<<<blocks, kSearchThreads, smem, s>>>(
-      U, (const uint32_t*)(stage + L.off_hx), (const int32_t*)(stage + L.off_table), L.cap - 1,
-      (const uint32_t*)(stage + L.off_bloom), (uint32_t)(L.nwords - 1), (int)L.nwords,
-      ham->srch_hash, ham->srch_id, ham->n_srch / 32, ham->xy, ham->has_diag, rb, re, rp, pj, pk,
-      (int32_t*)(stage + offsetof(StageHeader, status)));
+  kern<<<blocks, kSearchThreads, smem, s>>>(args);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, const char* stage,
                                const StageHeader& L, int64_t rb, int64_t re, int64_t* rp,
-                               uint32_t* pj, uint32_t* pk, bool fill, cudaStream_t s) {
-  if (ham->n_srch >= (int64_t(1) << 28)) return cudaErrorInvalidValue;
-  switch (ham->W) {
-    case 1: return fill ? launch_terms_w<1, true>(ham, U, stage, L, rb, re, rp, pj, pk, s)
-                        : launch_terms_w<1, false>(ham, U, stage, L, rb, re, rp, pj, pk, s);
-    case 2: return fill ? launch_terms_w<2, true>(ham, U, stage, L, rb, re, rp, pj, pk, s)
-                        : launch_terms_w<2, false>(ham, U, stage, L, rb, re, rp, pj, pk, s);
-    case 3: return fill ? launch_terms_w<3, true>(ham, U, stage, L, rb, re, rp, pj, pk, s)
-                        : launch_terms_w<3, false>(ham, U, stage, L, rb, re, rp, pj, pk, s);
-    default: return fill ? launch_terms_w<4, true>(ham, U, stage, L, rb, re, rp, pj, pk, s)
-                         : launch_terms_w<4, false>(ham, U, stage, L, rb, re, rp, pj, pk, s);
+                               uint32_t* pj, uint32_t* pk, int mode, const PairScratch* sc,
+                               cudaStream_t s) {
+  if (ham->n_srch >= (int64_t(1) << 24) || ham->n_xy >= (int64_t(1) << 29)) return cudaErrorInvalidValue;
+  SearchArgs a;
+  a.U = U;
+  a.hx = (const uint32_t*)(stage + L.off_hx);
+  a.table = (const unsigned long long*)(stage + L.off_table);
+  a.capmask = L.cap - 1;
+  a.bloom_g = (const uint32_t*)(stage + L.off_bloom);
+  a.wmask = (uint32_t)(L.nwords - 1);
+  a.nwords = (int)L.nwords;
+  a.srch_hash = ham->srch_hash;
+  a.srch_id = ham->srch_id;
+  a.n_groups = ham->n_srch / 32;
+  a.xy = ham->xy;
+  a.has_diag = ham->has_diag;
+  a.row_begin = rb;
+  a.row_end = re;
+  a.rp = rp;
+  a.pair_j = pj;
+  a.pair_k = pk;
+  a.status = (int32_t*)(stage + offsetof(StageHeader, status));
+  a.batch_counter = (unsigned long long*)(stage + L.off_counters);
+  if (sc) a.sc = *sc; else a.sc = PairScratch{0, nullptr, nullptr, nullptr, nullptr};
+  cudaError_t e = cudaMemsetAsync(a.batch_counter, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  if (mode == kEmit) {
+    e = cudaMemsetAsync(sc->cursor, 0, 2 * sizeof(int64_t), s);
+    if (e != cudaSuccess) return e;
   }
+  const size_t smem = 4 * (size_t)L.nwords + (size_t)kSearchWarps * kQueueCap * 4;
+  const int64_t rows = re - rb;
+#define NQS_TERMS(WW)                                                              \
+  case WW:                                                                         \
+    if (mode == kCount) return launch_terms_w<WW, kCount>(a, rows, smem, s);       \
+    if (mode == kFill) return launch_terms_w<WW, kFill>(a, rows, smem, s);         \
+    return launch_terms_w<WW, kEmit>(a, rows, smem, s);
+  switch (ham->W) {
+    NQS_TERMS(1)
+    NQS_TERMS(2)
+    NQS_TERMS(3)
+    default:
+    NQS_TERMS(4)
+  }
+#undef NQS_TERMS
+}
+
+// --------------------------------------------------------------------------
+// compaction of the one-pass records into CSR order (one warp per row batch)
+// --------------------------------------------------------------------------
+__global__ void pairs_compact_kernel(PairScratch sc, int64_t rows, const int64_t* __restrict__ rp,
+                                     uint32_t* __restrict__ pair_j, uint32_t* __restrict__ pair_k) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  const int64_t n_batches = (rows + R - 1) / R;
+  const int64_t tw = (int64_t)gridDim.x * (blockDim.x / 32);
+  const int64_t p0 = rp[0];
+  for (int64_t bt = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); bt < n_batches; bt += tw) {
+    const int64_t l0 = bt * R;
+    const int64_t l1 = std::min<int64_t>(l0 + R, rows);
+    int64_t base[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) base[r] = (l0 + r < rows) ? rp[l0 + r] - p0 : 0;
+    const int64_t total = rp[l1] - rp[l0];
+    int64_t consumed = 0;
+    int32_t c = sc.heads[bt];
+    while (consumed < total && c >= 0) {
+      const int n_here = (int)std::min<int64_t>(kChunk, total - consumed);
+      for (int e0 = 0; e0 < n_here; e0 += 32) {
+        const int e = e0 + lane;
+        const bool v = e < n_here;
+        const uint64_t rec = v ? sc.records[(int64_t)c * kChunk + e] : 0ull;
+        const int r = (int)(rec >> 61);
+        const uint32_t j = (uint32_t)rec;
+        const uint32_t k = (uint32_t)(rec >> 32) & 0x1FFFFFFFu;
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+          const uint32_t m = __ballot_sync(kFull, v && r == rr);
+          if (v && r == rr) {
+            const int64_t p = base[rr] + __popc(m & lt);
+            pair_j[p] = j;
+            pair_k[p] = k;
+          }
+          base[rr] += __popc(m);
+        }
+      }
+      consumed += n_here;
+      c = sc.next[c];
+    }
+  }
+}
+
+cudaError_t launch_pairs_compact(const PairScratch& sc, int64_t rows, const int64_t* row_ptr,
+                                 uint32_t* pair_j, uint32_t* pair_k, cudaStream_t s) {
+  const int64_t batches = (rows + R - 1) / R;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((batches + 7) / 8, (int64_t)num_sms() * 8));
+  pairs_compact_kernel<<<blocks, 256, 0, s>>>(sc, rows, row_ptr, pair_j, pair_k);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pairs_batch(const nqs_ham*, const uint64_t*, const char*, const StageHeader&,

@@ -13,8 +13,9 @@ namespace nqs {
 constexpr int kMaxWords = 4;                 // N <= 256 qubits
 constexpr uint32_t kDummy = 0xFFFFFFFFu;     // padding slot of the search table
 constexpr int kHeavyTerms = 24;              // |P_XY| above this: warp-cooperative term loop
-constexpr int kQueueCap = 512;               // per-warp candidate queue (entries)
-constexpr int kRowsPerWarp = 4;              // rows scanned together by one warp
+constexpr int kQueueCap = 256;               // per-warp candidate queue (entries)
+constexpr int kRowsPerWarp = 8;              // rows scanned together by one warp
+constexpr int kChunk = 128;                  // records per scratch chunk (one-pass search)
 
 // status bits (device status word)
 constexpr int kStatusDuplicate = 1;
@@ -70,7 +71,7 @@ struct StageHeader {
   int64_t nwords;       // bloom words (power of two)
   int32_t W;
   int32_t status;       // device status word (kStatus* bits)
-  int64_t off_hx, off_table, off_bloom, off_scan, off_ampP, off_ampQ, off_ampK, off_geff;
+  int64_t off_hx, off_table, off_bloom, off_scan, off_ampP, off_ampQ, off_ampK, off_geff, off_counters;
   int64_t scan_blocks;
   int64_t total_bytes;
 };
@@ -87,10 +88,27 @@ int cuda_fail(cudaError_t e, const char* what);
 cudaError_t launch_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, char* stage,
                          const StageHeader& L, cudaStream_t s);
 
+// search modes: COUNT writes per-row counts, FILL writes pairs at given CSR
+// offsets, EMIT writes per-row counts and the pairs into scratch chunks
+enum SearchMode { kCount = 0, kFill = 1, kEmit = 2 };
+
+struct PairScratch {        // one-pass search scratch (caller memory)
+  int64_t max_chunks;
+  int64_t* cursor;          // [2]: next chunk, overflow flag
+  int32_t* heads;           // [n_batches] first chunk of each row batch (-1: none)
+  int32_t* next;            // [max_chunks]
+  uint64_t* records;        // [max_chunks * kChunk]: j | k << 32 | r << 61
+};
+int64_t pair_scratch_bytes(int64_t rows, int64_t max_pairs);
+PairScratch pair_scratch_view(void* base, int64_t rows, int64_t bytes);
+
 cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, const char* stage,
                                const StageHeader& L, int64_t row_begin, int64_t row_end,
                                int64_t* counts_or_rowptr, uint32_t* pair_j, uint32_t* pair_k,
-                               bool fill, cudaStream_t s);
+                               int mode, const PairScratch* scratch, cudaStream_t s);
+
+cudaError_t launch_pairs_compact(const PairScratch& sc, int64_t rows, const int64_t* row_ptr,
+                                 uint32_t* pair_j, uint32_t* pair_k, cudaStream_t s);
 
 cudaError_t launch_pairs_batch(const nqs_ham* ham, const uint64_t* U, const char* stage,
                                const StageHeader& L, int64_t row_begin, int64_t row_end,

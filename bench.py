@@ -209,7 +209,7 @@ def run_ours(args):
         mark()
         er, ei, hd = nqs.local_energy(batch_obj, adev, None, (rp, pj, pk), prec)
         mark()
-        evar = nqs.variational_energy(adev, er)
+        evar = nqs.variational_energy(batch_obj, adev, er)
         mark()
         gr, gi = nqs.local_energy_backward(batch_obj, adev, None, er, ei, hd, evar, g, None, gE,
                                            (rp, pj, pk), prec)

@@ -140,10 +140,9 @@ int nqs_stage_status(const void* work, void* stream);
  *   of row r; pair_j = column (index into U), pair_k = pattern index (into
  *   the library's unique-XY table).  Within a row the diagonal pair comes
  *   first (if the XY = 0 pattern exists), then pairs whose P_XY is large,
- *   then the rest.  Rows are searched in batches of 8 starting at row_begin;
- *   for a given row range the order is fixed (count, fill and one-pass calls
- *   agree), while calls over other ranges may order a row's pairs
- *   differently.  Both (i, j) and (j, i) are listed.
+ *   then the rest, in a fixed order that depends neither on the row range
+ *   nor on the call (count, fill and one-pass calls agree).  Both (i, j)
+ *   and (j, i) are listed.
  * All calls need a workspace staged with the same U.  Readers of the CSR
  * (fill, energy, adjoint) take positions relative to row_ptr[0], so a slice
  * row_ptr + (r0 - row_begin) of a larger offset array can be passed for the
@@ -204,11 +203,13 @@ int nqs_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, void*
                      double* eloc_re, double* eloc_im, double* hdiag, void* stream);
 
 /* E^var = sum_x p(x) Re E_loc^var(x) / sum_x p(x) with p = exp(2 a) over the
- * whole batch (Eq. variational_energy), FP64, deterministic.  Writes
- * out[0] = E^var, out[1] = max a, out[2] = sum_x exp(2 (a - max a)) (device
- * FP64 [3]).  Asynchronous. */
+ * whole batch (Eq. variational_energy), FP64, deterministic (fixed block
+ * partition and summation order).  work: a batch workspace that nqs_stage
+ * has initialised (its reduction scratch is used; calls sharing one
+ * workspace must not overlap).  Writes out[0] = E^var, out[1] = max a,
+ * out[2] = sum_x exp(2 (a - max a)) (device FP64 [3]).  Asynchronous. */
 int nqs_variational_energy(int64_t n_unq, const double* logpsi_re, const double* eloc_re,
-                           double* out, void* stream);
+                           void* work, double* out, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Adjoint: gradient of L = sum_x [g_re(x) Re E_loc(x) + g_im(x) Im E_loc(x)]

@@ -67,7 +67,7 @@ def load_library(path: str = None):
         "nqs_pairs_scratch_bytes": (_i64, [_i64, _i64]),
         "nqs_local_energy": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _i32,
                                     _vp, _vp, _vp, _vp]),
-        "nqs_variational_energy": (_i32, [_i64, _vp, _vp, _vp, _vp]),
+        "nqs_variational_energy": (_i32, [_i64, _vp, _vp, _vp, _vp, _vp]),
         "nqs_local_energy_backward": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp,
                                              _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp]),
         "nqs_last_error": (ctypes.c_char_p, []),
@@ -315,12 +315,13 @@ def local_energy(batch: Batch, logpsi_re, logpsi_im=None, pairs=None, precision=
     return er, ei, hd
 
 
-def variational_energy(logpsi_re, eloc_re, out=None, stream=None):
+def variational_energy(batch: Batch, logpsi_re, eloc_re, out=None, stream=None):
     """E^var (Eq. variational_energy) as a device tensor [E, max Re log psi, sum of weights]."""
     a = _f64(logpsi_re, eloc_re.device)
     if out is None:
         out = torch.empty(3, dtype=torch.float64, device=eloc_re.device)
-    _check(_lib.nqs_variational_energy(int(a.shape[0]), _ptr(a), _ptr(eloc_re), _ptr(out), _stream(stream)))
+    _check(_lib.nqs_variational_energy(int(a.shape[0]), _ptr(a), _ptr(eloc_re), _ptr(batch.work), _ptr(out),
+                                       _stream(stream)))
     return out
 
 
@@ -394,7 +395,7 @@ def evaluate(batch: Batch, logpsi_re, logpsi_im=None, precision="fp32c", schedul
             local_energy(batch, a, b, (rp, pj, pk), precision, r0, r1, (er, ei, hd), stream)
             if len(chunks) == 1 and keep_pairs:
                 kept = (rp, pj, pk)
-    evar = variational_energy(a, er, stream=stream)
+    evar = variational_energy(batch, a, er, stream=stream)
     return {"eloc_re": er, "eloc_im": ei, "hdiag": hd, "evar": evar, "n_pairs": total,
             "pairs": kept, "chunks": chunks, "row_ptr": row_ptr, "row_ptr_host": rp_host,
             "schedule": schedule}

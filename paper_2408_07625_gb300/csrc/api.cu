@@ -47,7 +47,7 @@ StageHeader stage_layout(const nqs_ham* ham, int64_t n) {
   L.W = ham->W;
   L.cap = next_pow2(std::max<int64_t>(2 * n, 64));
   L.nwords = std::min<int64_t>(std::max<int64_t>(next_pow2(std::max<int64_t>(n / 2, 1)), 32), 32768);
-  int64_t off = align256(sizeof(StageHeader));
+  int64_t off = align256(kRedOffset + kRedBytes);
   L.off_hx = off;     off = align256(off + 4 * std::max<int64_t>(n, 1));
   L.off_table = off;  off = align256(off + 8 * (L.W + 1) * L.cap);
   L.off_bloom = off;  off = align256(off + 4 * L.nwords);
@@ -106,7 +106,7 @@ static int upload(T** dst, const std::vector<T>& src) {
 static void free_ham(nqs_ham* h) {
   if (!h) return;
   cudaFree(h->xy); cudaFree(h->row_ptr); cudaFree(h->yz); cudaFree(h->coef);
-  cudaFree(h->coef_f); cudaFree(h->srch_hash); cudaFree(h->srch_id); cudaFree(h->hash_basis);
+  cudaFree(h->coef_f); cudaFree(h->srch_hash); cudaFree(h->srch_id); cudaFree(h->srch_rec); cudaFree(h->hash_basis);
   delete h;
 }
 
@@ -255,6 +255,8 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
   // the 32 lanes of a warp probing one sample touch 32 distinct shared-memory
   // banks of the membership filter.
   std::vector<uint32_t> srch_hash, srch_id;
+  std::vector<uint64_t> srch_rec;
+  h->rec_words = 2 * ((1 + W + 1) / 2);
   auto build_class = [&](int64_t lo, int64_t hi) {
     std::vector<std::vector<uint32_t>> buckets(32);
     for (int64_t p = lo; p < hi; ++p) buckets[hxy[p] & 31].push_back((uint32_t)p);
@@ -266,9 +268,14 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
           uint32_t id = buckets[b][g];
           srch_hash.push_back(hxy[id]);
           srch_id.push_back(id);
+          srch_rec.push_back((uint64_t)hxy[id] | ((uint64_t)id << 32));
+          for (int w = 0; w < W; ++w) srch_rec.push_back(h->h_xy[(int64_t)id * W + w]);
+          for (int w = 1 + W; w < h->rec_words; ++w) srch_rec.push_back(0);
         } else {
           srch_hash.push_back((uint32_t)b);
           srch_id.push_back(kDummy);
+          srch_rec.push_back((uint64_t)b | ((uint64_t)kDummy << 32));
+          for (int w = 1; w < h->rec_words; ++w) srch_rec.push_back(0);
         }
       }
   };
@@ -283,7 +290,8 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
   if ((rc = upload(&h->xy, h->h_xy)) || (rc = upload(&h->row_ptr, rp32)) ||
       (rc = upload(&h->yz, h->h_yz)) || (rc = upload(&h->coef, h->h_coef)) ||
       (rc = upload(&h->coef_f, coef_f)) || (rc = upload(&h->srch_hash, srch_hash)) ||
-      (rc = upload(&h->srch_id, srch_id)) || (rc = upload(&h->hash_basis, h->h_hash_basis))) {
+      (rc = upload(&h->srch_id, srch_id)) || (rc = upload(&h->srch_rec, srch_rec)) ||
+      (rc = upload(&h->hash_basis, h->h_hash_basis))) {
     free_ham(h);
     return rc;
   }
@@ -359,6 +367,7 @@ int nqs_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, int6
   if (e != cudaSuccess) return cuda_fail(e, "header copy");
   if ((e = cudaMemsetAsync(base + L.off_table, 0xFF, 8 * (L.W + 1) * L.cap, s)) != cudaSuccess) return cuda_fail(e, "memset");
   if ((e = cudaMemsetAsync(base + L.off_bloom, 0, 4 * L.nwords, s)) != cudaSuccess) return cuda_fail(e, "memset");
+  if ((e = cudaMemsetAsync(base + kRedOffset, 0, 256, s)) != cudaSuccess) return cuda_fail(e, "memset");
   if ((e = launch_stage(ham, U, n, base, L, s)) != cudaSuccess) return cuda_fail(e, "stage kernel");
   if (check) return read_status(work, s);
   return NQS_OK;
@@ -488,9 +497,11 @@ int nqs_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n, void* wor
   return NQS_OK;
 }
 
-int nqs_variational_energy(int64_t n, const double* a, const double* eloc_re, double* out, void* stream) {
-  if (n <= 0 || !a || !eloc_re || !out) return fail(NQS_ERR_ARG, "bad argument");
-  cudaError_t e = launch_variational_energy(n, a, eloc_re, out, (cudaStream_t)stream);
+int nqs_variational_energy(int64_t n, const double* a, const double* eloc_re, void* work, double* out,
+                           void* stream) {
+  if (n <= 0 || !a || !eloc_re || !out || !work) return fail(NQS_ERR_ARG, "bad argument");
+  if (((uintptr_t)work) & 255) return fail(NQS_ERR_ARG, "workspace not 256-byte aligned");
+  cudaError_t e = launch_variational_energy(n, a, eloc_re, (char*)work, out, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "variational energy kernel");
   return NQS_OK;
 }

@@ -303,31 +303,65 @@ __device__ double block_reduce_max(double v, double* sh) {
   return sh[0];
 }
 
+// One pass: block b takes a contiguous chunk, finds its own max m_b and the
+// sums S_b = sum exp(2 (a - m_b)), N_b = sum exp(2 (a - m_b)) E_loc; the last
+// block to finish rescales them to the global max in block order.
 __global__ void __launch_bounds__(kRedThreads)
 evar_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ er,
-            double* __restrict__ out) {
+            unsigned int* __restrict__ done, double* __restrict__ part, double* __restrict__ out) {
   __shared__ double sh[32];
+  __shared__ bool last;
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * chunk;
+  const int64_t i1 = i0 + chunk < n ? i0 + chunk : n;
   double m = -DBL_MAX;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, a[i]);
-  const double amax = block_reduce_max(m, sh);
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) m = fmax(m, a[i]);
+  const double mb = block_reduce_max(m, sh);
   double sw = 0.0, swe = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const double w = exp(2.0 * (a[i] - amax));
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const double w = exp(2.0 * (a[i] - mb));
     sw += w;
     swe += w * er[i];
   }
-  const double S = block_reduce_sum(sw, sh);
-  const double N = block_reduce_sum(swe, sh);
+  const double Sb = block_reduce_sum(sw, sh);
+  const double Nb = block_reduce_sum(swe, sh);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = mb;
+    part[3 * blockIdx.x + 1] = Sb;
+    part[3 * blockIdx.x + 2] = Nb;
+    __threadfence();
+    last = atomicAdd(done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int G = gridDim.x;
+  double mm = -DBL_MAX;
+  for (int b = threadIdx.x; b < G; b += blockDim.x) mm = fmax(mm, __ldcg(part + 3 * b));
+  const double amax = block_reduce_max(mm, sh);
+  double s1 = 0.0, s2 = 0.0;
+  for (int b = threadIdx.x; b < G; b += blockDim.x) {
+    const double mbb = __ldcg(part + 3 * b);
+    const double f = (mbb == -DBL_MAX) ? 0.0 : exp(2.0 * (mbb - amax));
+    s1 += __ldcg(part + 3 * b + 1) * f;
+    s2 += __ldcg(part + 3 * b + 2) * f;
+  }
+  const double S = block_reduce_sum(s1, sh);
+  const double N = block_reduce_sum(s2, sh);
   if (threadIdx.x == 0) {
     out[0] = N / S;
     out[1] = amax;
     out[2] = S;
+    *done = 0u;  // ready for the next call
   }
 }
 
-cudaError_t launch_variational_energy(int64_t n, const double* a, const double* er, double* out,
-                                      cudaStream_t s) {
-  evar_kernel<<<1, kRedThreads, 0, s>>>(n, a, er, out);
+cudaError_t launch_variational_energy(int64_t n, const double* a, const double* er, char* work,
+                                      double* out, cudaStream_t s) {
+  const int G = (int)std::max<int64_t>(1, std::min<int64_t>((n + 2047) / 2048, std::min(kRedBlocks, num_sms())));
+  unsigned int* done = (unsigned int*)(work + kRedOffset);
+  double* part = (double*)(work + kRedOffset + 256);
+  evar_kernel<<<G, kRedThreads, 0, s>>>(n, a, er, done, part, out);
   return cudaGetLastError();
 }
 

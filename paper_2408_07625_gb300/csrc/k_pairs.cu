@@ -112,9 +112,10 @@ PairScratch pair_scratch_view(void* base, int64_t rows, int64_t bytes) {
 // a global counter) and streams the search table: lane t takes slot 32g + t.
 // The 32 slots of a group have distinct low hash bits, so the 32 Bloom-word
 // loads of one row hit 32 distinct shared-memory banks.  Per slot a lane keeps
-// a bit mask of the rows whose filter test passed; one ballot per group pushes
-// (mask, slot) entries to a per-warp queue, verified lane-parallel against the
-// hash table when the queue fills.
+// a bit mask of the rows whose filter test passed; groups with a hit append
+// one (row, slot) entry per passed test to a per-warp queue (warp prefix sum),
+// so a row's candidates stay in slot order whatever the other rows of its
+// batch do.  A full queue is verified lane-parallel against the hash table.
 // --------------------------------------------------------------------------
 constexpr int kSearchThreads = 1024;
 constexpr int kSearchWarps = kSearchThreads / 32;
@@ -129,9 +130,9 @@ struct SearchArgs {
   uint32_t wmask;
   int nwords;
   const uint32_t* srch_hash;
-  const uint32_t* srch_id;
+  const uint64_t* srch_rec;
+  int rec_words;
   int64_t n_groups;
-  const uint64_t* xy;
   int has_diag;
   int64_t row_begin, row_end;
   int64_t* rp;
@@ -146,21 +147,36 @@ struct EmitState {  // warp-uniform chunk state of the one-pass mode
   int32_t chunk, fill, first;
 };
 
-template <int MODE>
+template <int W>
+struct RowCache {   // per-warp copy of the batch's rows (shared memory)
+  uint64_t u[R][W];
+  uint32_t hx[R];
+  uint32_t cnt[R];
+};
+
+// Emit one round of verified candidates (lane order).  COUNT/EMIT count per
+// row with shared-memory atomics; FILL places pairs at per-row ranks; EMIT
+// appends records to the warp's current scratch chunk.
+template <int MODE, int W>
 __device__ __forceinline__ void emit_round(bool found, int r, uint32_t j, uint32_t id,
-                                           int64_t (&acc)[R], EmitState& es, const SearchArgs& a) {
+                                           int64_t (&acc)[R], EmitState& es, RowCache<W>* rc,
+                                           const SearchArgs& a) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
+  if (MODE == kFill) {
 #pragma unroll
-  for (int rr = 0; rr < R; ++rr) {
-    const uint32_t m = __ballot_sync(kFull, found && r == rr);
-    if (MODE == kFill && found && r == rr) {
-      const int64_t p = acc[rr] + __popc(m & lt);
-      a.pair_j[p] = j;
-      a.pair_k[p] = id;
+    for (int rr = 0; rr < R; ++rr) {
+      const uint32_t m = __ballot_sync(kFull, found && r == rr);
+      if (found && r == rr) {
+        const int64_t p = acc[rr] + __popc(m & lt);
+        a.pair_j[p] = j;
+        a.pair_k[p] = id;
+      }
+      acc[rr] += __popc(m);
     }
-    acc[rr] += __popc(m);
+    return;
   }
+  if (found) atomicAdd(&rc->cnt[r], 1u);
   if (MODE == kEmit) {
     const uint32_t m = __ballot_sync(kFull, found);
     const int n = __popc(m);
@@ -194,54 +210,148 @@ __device__ __forceinline__ void emit_round(bool found, int r, uint32_t j, uint32
   }
 }
 
+// Verification of queued candidates: each lane takes several entries at a
+// time so their loads overlap (search record, then hash-table slot).
+template <int W>
+struct FlushWays { static constexpr int value = W == 1 ? 4 : (W == 2 ? 2 : 1); };
+
+template <int W>
+__device__ __forceinline__ void load_slot(const unsigned long long* sl, unsigned long long (&v)[W + 1]) {
+  if (W == 1) {
+    const ulonglong2 t = __ldg(reinterpret_cast<const ulonglong2*>(sl));
+    v[0] = t.x;
+    v[W] = t.y;
+  } else {
+#pragma unroll
+    for (int w = 0; w <= W; ++w) v[w] = __ldg(sl + w);
+  }
+}
+
 template <int W, int MODE>
-__device__ __forceinline__ void flush_queue(const uint32_t* q, int qn, int64_t r0, int64_t (&acc)[R],
-                                            EmitState& es, const SearchArgs& a) {
+__device__ __forceinline__ void verify_items(const uint32_t* q, int qn, int64_t (&acc)[R],
+                                             EmitState& es, RowCache<W>* rc, const SearchArgs& a) {
+  constexpr int kFlushWays = FlushWays<W>::value;
   const int lane = threadIdx.x & 31;
-  for (int e0 = 0; e0 < qn; e0 += 32) {
-    const int e = e0 + lane;
+  for (int e0 = 0; e0 < qn; e0 += 32 * kFlushWays) {
+    int r[kFlushWays];
+    bool live[kFlushWays], found[kFlushWays];
+    uint32_t id[kFlushWays], j[kFlushWays];
+    uint64_t key[kFlushWays][W];
+    int64_t slot[kFlushWays];
+#pragma unroll
+    for (int u = 0; u < kFlushWays; ++u) {
+      const int e = e0 + u * 32 + lane;
+      live[u] = e < qn;
+      found[u] = false;
+      j[u] = 0;
+      const uint32_t ent = live[u] ? q[e] : 0u;
+      r[u] = (int)(ent >> 24);
+      const uint64_t* rec = a.srch_rec + (int64_t)(ent & 0x00FFFFFFu) * a.rec_words;
+      uint64_t w0 = 0;
+      uint64_t xyw[W];
+      if (W == 1) {
+        const ulonglong2 t = live[u] ? __ldg(reinterpret_cast<const ulonglong2*>(rec)) : make_ulonglong2(0, 0);
+        w0 = t.x;
+        xyw[0] = t.y;
+      } else {
+        w0 = live[u] ? __ldg(rec) : 0ull;
+#pragma unroll
+        for (int w = 0; w < W; ++w) xyw[w] = live[u] ? __ldg(rec + 1 + w) : 0ull;
+      }
+      id[u] = (uint32_t)(w0 >> 32);
+#pragma unroll
+      for (int w = 0; w < W; ++w) key[u][w] = rc->u[r[u]][w] ^ xyw[w];
+      slot[u] = (rc->hx[r[u]] ^ (uint32_t)w0) & a.capmask;
+    }
+    bool more[kFlushWays];
+#pragma unroll
+    for (int u = 0; u < kFlushWays; ++u) {  // first table slot of every candidate
+      more[u] = false;
+      if (live[u]) {
+        unsigned long long v[W + 1];
+        load_slot<W>(a.table + slot[u] * (W + 1), v);
+        bool eq = v[W] != ~0ull;
+#pragma unroll
+        for (int w = 0; w < W; ++w) eq = eq && (v[w] == key[u][w]);
+        if (eq) { found[u] = true; j[u] = (uint32_t)v[W]; }
+        else if (v[W] != ~0ull) more[u] = true;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kFlushWays; ++u) {  // rare: continue linear probing
+      if (more[u]) {
+        int64_t sl = slot[u];
+        int64_t it = 1;
+        for (; it <= a.capmask; ++it) {
+          sl = (sl + 1) & a.capmask;
+          unsigned long long v[W + 1];
+          load_slot<W>(a.table + sl * (W + 1), v);
+          if (v[W] == ~0ull) break;
+          bool eq = true;
+#pragma unroll
+          for (int w = 0; w < W; ++w) eq = eq && (v[w] == key[u][w]);
+          if (eq) { found[u] = true; j[u] = (uint32_t)v[W]; break; }
+        }
+        if (it > a.capmask) atomicOr(a.status, kStatusLimit);
+      }
+      found[u] = found[u] && id[u] != kDummy;  // padding slots carry XY = 0 and never count
+    }
+#pragma unroll
+    for (int u = 0; u < kFlushWays; ++u) {
+      if (e0 + u * 32 < qn) emit_round<MODE, W>(found[u], r[u], j[u], id[u], acc, es, rc, a);
+    }
+  }
+}
+
+// Queue entries are (row mask << 24 | slot).  Each 32-entry slice is expanded
+// into one (row << 24 | slot) item per set bit, rows of an entry in increasing
+// order and entries in queue order, so a row's items keep their slot order.
+// Items accumulate in xbuf and are verified in full chunks.
+constexpr int kXbufCap = 384;
+
+template <int W, int MODE>
+__device__ __forceinline__ void flush_queue(const uint32_t* q, int qn, uint32_t* xbuf, int64_t (&acc)[R],
+                                            EmitState& es, RowCache<W>* rc, const SearchArgs& a) {
+  const int lane = threadIdx.x & 31;
+  int xn = 0;
+  for (int c0 = 0; c0 < qn; c0 += 32) {
+    if (xn + 32 * R > kXbufCap) {
+      __syncwarp();
+      verify_items<W, MODE>(xbuf, xn, acc, es, rc, a);
+      __syncwarp();
+      xn = 0;
+    }
+    const int e = c0 + lane;
     const uint32_t ent = e < qn ? q[e] : 0u;
     uint32_t bits = ent >> 24;
     const uint32_t pos = ent & 0x00FFFFFFu;
-    while (__any_sync(kFull, bits != 0u)) {
-      bool found = false;
-      int r = 0;
-      uint32_t j = 0, id = 0;
-      if (bits) {
-        const int b = 31 - __clz(bits);
-        bits &= ~(1u << b);
-        r = R - 1 - b;
-        id = __ldg(a.srch_id + pos);
-        if (id != kDummy) {
-          const int64_t row = r0 + r;
-          uint64_t key[W];
+    const int c = __popc(bits);
+    int incl = c;
 #pragma unroll
-          for (int w = 0; w < W; ++w) key[w] = __ldg(a.U + row * W + w) ^ __ldg(a.xy + (int64_t)id * W + w);
-          int64_t slot = (__ldg(a.hx + row) ^ __ldg(a.srch_hash + pos)) & a.capmask;
-          int64_t it = 0;
-          for (; it <= a.capmask; ++it) {
-            const unsigned long long* sl = a.table + slot * (W + 1);
-            const unsigned long long idx = __ldg(sl + W);
-            if (idx == ~0ull) break;
-            bool eq = true;
-#pragma unroll
-            for (int w = 0; w < W; ++w) eq = eq && (__ldg(sl + w) == key[w]);
-            if (eq) { found = true; j = (uint32_t)idx; break; }
-            slot = (slot + 1) & a.capmask;
-          }
-          if (it > a.capmask) atomicOr(a.status, kStatusLimit);
-        }
-      }
-      emit_round<MODE>(found, r, j, id, acc, es, a);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += t;
     }
+    int at = xn + incl - c;
+    while (bits) {
+      const int b = 31 - __clz(bits);
+      bits &= ~(1u << b);
+      xbuf[at++] = ((uint32_t)(R - 1 - b) << 24) | pos;
+    }
+    xn += __shfl_sync(kFull, incl, 31);
   }
+  __syncwarp();
+  verify_items<W, MODE>(xbuf, xn, acc, es, rc, a);
+  __syncwarp();
 }
 
 template <int W, int MODE>
 __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const SearchArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* bloom = smem;
-  uint32_t* queue = smem + a.nwords;
+  RowCache<W>* caches = reinterpret_cast<RowCache<W>*>(smem + a.nwords);
+  uint32_t* queue = reinterpret_cast<uint32_t*>(caches + kSearchWarps);
+  uint32_t* xbufs = queue + kSearchWarps * kQueueCap;
   {
     const uint4* src = reinterpret_cast<const uint4*>(a.bloom_g);
     uint4* dst = reinterpret_cast<uint4*>(bloom);
@@ -251,7 +361,9 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Se
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   uint32_t* q = queue + warp * kQueueCap;
+  uint32_t* xbuf = xbufs + warp * kXbufCap;
   const uint32_t lt = (1u << lane) - 1u;
+  RowCache<W>* rc = caches + warp;
   const int64_t n_rows = a.row_end - a.row_begin;
   const int64_t n_batches = (n_rows + R - 1) / R;
   const uint32_t wmask4 = a.wmask << 2;
@@ -263,6 +375,16 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Se
     const int64_t bt = (int64_t)__shfl_sync(kFull, btu, 0);
     if (bt >= n_batches) break;
     const int64_t r0 = a.row_begin + bt * R;
+    __syncwarp();
+    if (lane < R) {
+      const int64_t row = r0 + lane;
+      const bool valid = row < a.row_end;
+#pragma unroll
+      for (int w = 0; w < W; ++w) rc->u[lane][w] = valid ? __ldg(a.U + row * W + w) : 0ull;
+      rc->hx[lane] = valid ? __ldg(a.hx + row) : 0u;
+      rc->cnt[lane] = 0u;
+    }
+    __syncwarp();
     uint32_t hr4[R], hr17[R], hr22[R];
     uint32_t vmask = 0;
     int64_t acc[R];
@@ -270,7 +392,7 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Se
     for (int r = 0; r < R; ++r) {
       const int64_t row = r0 + r;
       const bool valid = row < a.row_end;
-      const uint32_t h = valid ? __ldg(a.hx + row) : 0u;
+      const uint32_t h = rc->hx[r];
       hr4[r] = h << 2;
       hr17[r] = h >> 17;
       hr22[r] = h >> 22;
@@ -280,7 +402,7 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Se
     EmitState es{-1, 0, -1};
     if (a.has_diag) {  // the diagonal pair (x, x) comes first in its row
       const bool d = lane < R && r0 + lane < a.row_end;
-      emit_round<MODE>(d, lane, (uint32_t)(r0 + lane), 0u, acc, es, a);
+      emit_round<MODE, W>(d, lane, (uint32_t)(r0 + lane), 0u, acc, es, rc, a);
     }
     int qn = 0;
     for (int64_t g = 0; g < a.n_groups; ++g) {
@@ -301,20 +423,17 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Se
         qn += __popc(bal);
         if (qn > kQueueCap - 32) {
           __syncwarp();
-          flush_queue<W, MODE>(q, qn, r0, acc, es, a);
+          flush_queue<W, MODE>(q, qn, xbuf, acc, es, rc, a);
           __syncwarp();
           qn = 0;
         }
       }
     }
     __syncwarp();
-    flush_queue<W, MODE>(q, qn, r0, acc, es, a);
+    flush_queue<W, MODE>(q, qn, xbuf, acc, es, rc, a);
     __syncwarp();
-    if (MODE != kFill && lane == 0) {
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (r0 + r < a.row_end) a.rp[r0 + r - a.row_begin] = acc[r];
-    }
+    if (MODE != kFill && lane < R && r0 + lane < a.row_end)
+      a.rp[r0 + lane - a.row_begin] = (int64_t)rc->cnt[lane];
     if (MODE == kEmit && lane == 0) {
       a.sc.heads[bt] = es.first;
       if (es.chunk >= 0) a.sc.next[es.chunk] = -1;
@@ -337,6 +456,12 @@ static cudaError_t launch_terms_w(const SearchArgs& args, int64_t rows, size_t s
   return cudaGetLastError();
 }
 
+template <int W>
+static size_t search_smem(const StageHeader& L) {
+  return 4 * (size_t)L.nwords + kSearchWarps * sizeof(RowCache<W>) +
+         (size_t)kSearchWarps * (kQueueCap + kXbufCap) * 4;
+}
+
 cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, const char* stage,
                                const StageHeader& L, int64_t rb, int64_t re, int64_t* rp,
                                uint32_t* pj, uint32_t* pk, int mode, const PairScratch* sc,
@@ -351,9 +476,9 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, const char
   a.wmask = (uint32_t)(L.nwords - 1);
   a.nwords = (int)L.nwords;
   a.srch_hash = ham->srch_hash;
-  a.srch_id = ham->srch_id;
+  a.srch_rec = ham->srch_rec;
+  a.rec_words = ham->rec_words;
   a.n_groups = ham->n_srch / 32;
-  a.xy = ham->xy;
   a.has_diag = ham->has_diag;
   a.row_begin = rb;
   a.row_end = re;
@@ -369,13 +494,14 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, const char
     e = cudaMemsetAsync(sc->cursor, 0, 2 * sizeof(int64_t), s);
     if (e != cudaSuccess) return e;
   }
-  const size_t smem = 4 * (size_t)L.nwords + (size_t)kSearchWarps * kQueueCap * 4;
   const int64_t rows = re - rb;
-#define NQS_TERMS(WW)                                                              \
-  case WW:                                                                         \
-    if (mode == kCount) return launch_terms_w<WW, kCount>(a, rows, smem, s);       \
-    if (mode == kFill) return launch_terms_w<WW, kFill>(a, rows, smem, s);         \
-    return launch_terms_w<WW, kEmit>(a, rows, smem, s);
+#define NQS_TERMS(WW)                                                                    \
+  case WW: {                                                                             \
+    const size_t smem = search_smem<WW>(L);                                              \
+    if (mode == kCount) return launch_terms_w<WW, kCount>(a, rows, smem, s);             \
+    if (mode == kFill) return launch_terms_w<WW, kFill>(a, rows, smem, s);               \
+    return launch_terms_w<WW, kEmit>(a, rows, smem, s);                                  \
+  }
   switch (ham->W) {
     NQS_TERMS(1)
     NQS_TERMS(2)
@@ -398,7 +524,7 @@ __global__ void pairs_compact_kernel(PairScratch sc, int64_t rows, const int64_t
   const int64_t p0 = rp[0];
   for (int64_t bt = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); bt < n_batches; bt += tw) {
     const int64_t l0 = bt * R;
-    const int64_t l1 = std::min<int64_t>(l0 + R, rows);
+    const int64_t l1 = (l0 + R < rows) ? l0 + R : rows;
     int64_t base[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) base[r] = (l0 + r < rows) ? rp[l0 + r] - p0 : 0;
@@ -406,7 +532,7 @@ __global__ void pairs_compact_kernel(PairScratch sc, int64_t rows, const int64_t
     int64_t consumed = 0;
     int32_t c = sc.heads[bt];
     while (consumed < total && c >= 0) {
-      const int n_here = (int)std::min<int64_t>(kChunk, total - consumed);
+      const int n_here = (int)((total - consumed < kChunk) ? total - consumed : kChunk);
       for (int e0 = 0; e0 < n_here; e0 += 32) {
         const int e = e0 + lane;
         const bool v = e < n_here;

@@ -45,6 +45,8 @@ struct nqs_ham_dev {
   float2* coef_f = nullptr;      // [n_terms]   (hi, lo) split of coef
   uint32_t* srch_hash = nullptr; // [n_srch]    linear hash of each pattern
   uint32_t* srch_id = nullptr;   // [n_srch]    pattern id or kDummy
+  uint64_t* srch_rec = nullptr;  // [n_srch][rec_words]: (hash | id << 32), XY words (0 for padding)
+  int rec_words = 0;             // 64-bit words per search record (16-byte multiple)
   uint32_t* hash_basis = nullptr;// [64 * W]    R[b]: h(v) = XOR of R[b] over set bits b
 
   // host copies (export, tests)
@@ -76,6 +78,9 @@ struct StageHeader {
   int64_t total_bytes;
 };
 constexpr uint64_t kStageMagic = 0x6E71735F73746731ull;
+constexpr int64_t kRedOffset = 256;        // E^var reduction scratch: fixed offset in the workspace
+constexpr int kRedBlocks = 1024;           // at most this many partial sums
+constexpr int64_t kRedBytes = 256 + 3 * 8 * kRedBlocks;
 
 StageHeader stage_layout(const nqs_ham* ham, int64_t n_unq);
 
@@ -129,7 +134,7 @@ cudaError_t launch_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n
                                 cudaStream_t s);
 
 cudaError_t launch_variational_energy(int64_t n, const double* a, const double* eloc_re,
-                                      double* out, cudaStream_t s);
+                                      char* work, double* out, cudaStream_t s);
 
 cudaError_t launch_backward(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
                             char* stage, const StageHeader& L, bool cplx,

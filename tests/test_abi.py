@@ -60,7 +60,7 @@ def test_host_side_argument_errors(lib):
     nan = np.array([np.nan])
     assert lib.nqs_ham_load(4, 1, x.ctypes.data, z.ctypes.data, nan.ctypes.data, ctypes.byref(h)) == -1
     assert lib.nqs_stage_bytes(None, 10) < 0
-    assert lib.nqs_variational_energy(0, None, None, None, None) == -1
+    assert lib.nqs_variational_energy(0, None, None, None, None, None) == -1
     assert lib.nqs_ham_free(None) == 0
 
 

@@ -211,6 +211,24 @@ int nqs_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, void*
 int nqs_variational_energy(int64_t n_unq, const double* logpsi_re, const double* eloc_re,
                            void* work, double* out, void* stream);
 
+/* Same result as nqs_variational_energy, for callers that cannot allocate
+ * device memory: for instance code whose device memory is entirely owned by
+ * another allocator, or that must not make the device-wide synchronising
+ * allocation calls on its hot path.  It allocates nothing (no cudaMalloc,
+ * cudaFree or library allocation) and needs no workspace: its partial sums
+ * live in one fixed device array of the library (about 24 KB, kept by every
+ * device that loads the library until the process exits).
+ *   n_unq <= 2097152 (2048 samples for each of the array's 1024 slots);
+ *   larger batches return NQS_ERR_CAPACITY and launch nothing.
+ * The first call on a device looks up the array's device address (a
+ * one-time set-up per device); make that first call before any stream
+ * capture.  Every call uses the same array: calls that overlap on the GPU
+ * (different streams, or different host threads, at the same time) race and
+ * corrupt each other's result, so serialise them.  The paper has no
+ * counterpart to this entry point.  Asynchronous. */
+int nqs_variational_energy_noalloc(int64_t n_unq, const double* logpsi_re,
+                                   const double* eloc_re, double* out, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Adjoint: gradient of L = sum_x [g_re(x) Re E_loc(x) + g_im(x) Im E_loc(x)]
  *          + g_evar E^var with respect to (Re log psi, Im log psi).

@@ -11,6 +11,7 @@
 // This replaces one exp per pair by a (double-float) product and an exact
 // power-of-two scaling.
 #include <cfloat>
+#include <mutex>
 
 #include "device_util.cuh"
 #include "nqs_internal.cuh"
@@ -366,6 +367,37 @@ cudaError_t launch_variational_energy(int64_t n, const double* a, const double* 
 }
 
 // --------------------------------------------------------------------------
+// E^var without caller memory: the partial sums live in a file-scope device
+// array instead of the batch workspace.  For callers that cannot allocate
+// device memory (see nqs_variational_energy_noalloc in nqs.h).
+// --------------------------------------------------------------------------
+constexpr int kStaticRedBlocks = 1024;           // partial-sum slots in the array
+constexpr int64_t kStaticRedChunk = 2048;        // samples per block
+constexpr int64_t kStaticRedMax = kStaticRedBlocks * kStaticRedChunk;  // 2,097,152 samples
+static __device__ __align__(256) unsigned char g_evar_scratch[256 + 3 * 8 * kStaticRedBlocks];
+
+static std::mutex g_evar_scratch_mu;
+static void* g_evar_scratch_addr[256] = {};      // device address of the array, per device
+
+// Device address of g_evar_scratch on the current device; looked up once per
+// device (the host-side name is only a stand-in for the device array).
+static cudaError_t evar_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_evar_scratch_mu);
+  if (!g_evar_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_evar_scratch);
+    if (e != cudaSuccess) return e;
+    g_evar_scratch_addr[dev] = p;
+  }
+  *out = g_evar_scratch_addr[dev];
+  return cudaSuccess;
+}
+
+// --------------------------------------------------------------------------
 // adjoint
 // --------------------------------------------------------------------------
 // per-sample effective upstream: ge(x) = g_re(x) + g_E w(x), gi(x) = g_im(x)
@@ -558,3 +590,25 @@ cudaError_t launch_backward(const nqs_ham* ham, const uint64_t* U, int64_t n, ch
 }
 
 }  // namespace nqs
+
+extern "C" int nqs_variational_energy_noalloc(int64_t n, const double* a, const double* eloc_re,
+                                              double* out, void* stream) {
+  using namespace nqs;
+  if (n <= 0 || !a || !eloc_re || !out) return fail(NQS_ERR_ARG, "bad argument");
+  if (n > kStaticRedMax)
+    return fail(NQS_ERR_CAPACITY, "n_unq exceeds the 2097152-sample limit of the built-in scratch; "
+                                  "use nqs_variational_energy with a workspace");
+  void* base = nullptr;
+  cudaError_t e = evar_scratch_address(&base);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress (E^var scratch)");
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned int* done = (unsigned int*)base;
+  double* part = (double*)((char*)base + 256);
+  e = cudaMemsetAsync(done, 0, sizeof(unsigned int), s);  // the completion counter starts at zero
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (E^var scratch)");
+  const int G = (int)((n + kStaticRedChunk - 1) / kStaticRedChunk);
+  evar_kernel<<<G, kRedThreads, 0, s>>>(n, a, eloc_re, done, part, out);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "E^var kernel");
+  return NQS_OK;
+}

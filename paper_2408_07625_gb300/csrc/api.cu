@@ -45,11 +45,11 @@ StageHeader stage_layout(const nqs_ham* ham, int64_t n) {
   L.magic = kStageMagic;
   L.n_unq = n;
   L.W = ham->W;
-  L.cap = next_pow2(std::max<int64_t>(2 * n, 64));
+  L.cap = next_pow2(std::max<int64_t>(n, 16));        // buckets of 4 slots, <= 1 key per bucket on average
   L.nwords = std::min<int64_t>(std::max<int64_t>(next_pow2(std::max<int64_t>(n / 2, 1)), 32), 32768);
   int64_t off = align256(kRedOffset + kRedBytes);
   L.off_hx = off;     off = align256(off + 4 * std::max<int64_t>(n, 1));
-  L.off_table = off;  off = align256(off + 8 * (L.W + 1) * L.cap);
+  L.off_table = off;  off = align256(off + 32 * L.cap);
   L.off_bloom = off;  off = align256(off + 4 * L.nwords);
   L.scan_blocks = (std::max<int64_t>(n, 1) + 1023) / 1024 + 1;
   L.off_scan = off;   off = align256(off + 8 * L.scan_blocks);
@@ -107,6 +107,7 @@ static void free_ham(nqs_ham* h) {
   if (!h) return;
   cudaFree(h->xy); cudaFree(h->row_ptr); cudaFree(h->yz); cudaFree(h->coef);
   cudaFree(h->coef_f); cudaFree(h->srch_hash); cudaFree(h->srch_id); cudaFree(h->srch_rec); cudaFree(h->hash_basis);
+  cudaFree(h->xy_table); cudaFree(h->wmask);
   delete h;
 }
 
@@ -283,6 +284,21 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
   build_class(h->heavy_end, G);
   h->n_srch = (int64_t)srch_hash.size();
 
+  // XY hash set for the batch schedule (Alg. 2B): same linear hash, so the
+  // hash of x ^ x' is h(x) ^ h(x'); slot = W key words, then id | hash << 32
+  h->xy_cap = 64;
+  while (h->xy_cap < 2 * std::max<int64_t>(G, 1)) h->xy_cap <<= 1;
+  std::vector<unsigned long long> xy_table((size_t)h->xy_cap * (W + 1), ~0ull);
+  std::vector<unsigned long long> wmask(5, 0ull);
+  for (int64_t p = 0; p < G; ++p) {
+    int64_t slot = hxy[p] & (h->xy_cap - 1);
+    while (xy_table[slot * (W + 1) + W] != ~0ull) slot = (slot + 1) & (h->xy_cap - 1);
+    for (int w = 0; w < W; ++w) xy_table[slot * (W + 1) + w] = h->h_xy[p * W + w];
+    xy_table[slot * (W + 1) + W] = (unsigned long long)p | ((unsigned long long)hxy[p] << 32);
+    const int wt = popc_words(&h->h_xy[p * W], W);
+    wmask[wt >> 6] |= 1ull << (wt & 63);
+  }
+
   std::vector<uint32_t> rp32(G + 1);
   for (int64_t p = 0; p <= G; ++p) rp32[p] = (uint32_t)h->h_row_ptr[p];
 
@@ -291,7 +307,8 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
       (rc = upload(&h->yz, h->h_yz)) || (rc = upload(&h->coef, h->h_coef)) ||
       (rc = upload(&h->coef_f, coef_f)) || (rc = upload(&h->srch_hash, srch_hash)) ||
       (rc = upload(&h->srch_id, srch_id)) || (rc = upload(&h->srch_rec, srch_rec)) ||
-      (rc = upload(&h->hash_basis, h->h_hash_basis))) {
+      (rc = upload(&h->hash_basis, h->h_hash_basis)) || (rc = upload(&h->xy_table, xy_table)) ||
+      (rc = upload(&h->wmask, wmask))) {
     free_ham(h);
     return rc;
   }
@@ -365,7 +382,7 @@ int nqs_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, int6
   char* base = (char*)work;
   cudaError_t e = cudaMemcpyAsync(base, &L, sizeof(L), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e, "header copy");
-  if ((e = cudaMemsetAsync(base + L.off_table, 0xFF, 8 * (L.W + 1) * L.cap, s)) != cudaSuccess) return cuda_fail(e, "memset");
+  if ((e = cudaMemsetAsync(base + L.off_table, 0xFF, 32 * L.cap, s)) != cudaSuccess) return cuda_fail(e, "memset");
   if ((e = cudaMemsetAsync(base + L.off_bloom, 0, 4 * L.nwords, s)) != cudaSuccess) return cuda_fail(e, "memset");
   if ((e = cudaMemsetAsync(base + kRedOffset, 0, 256, s)) != cudaSuccess) return cuda_fail(e, "memset");
   if ((e = launch_stage(ham, U, n, base, L, s)) != cudaSuccess) return cuda_fail(e, "stage kernel");
@@ -384,20 +401,37 @@ static int check_rows(int64_t n, int64_t rb, int64_t re) {
 }
 
 static int check_schedule(int schedule) {
-  if (schedule == NQS_SCHED_AUTO || schedule == NQS_SCHED_TERMS) return NQS_OK;
-  if (schedule == NQS_SCHED_BATCH || schedule == NQS_SCHED_TRIE)
-    return fail(NQS_ERR_UNSUPPORTED, "schedule not built yet");
+  if (schedule == NQS_SCHED_AUTO || schedule == NQS_SCHED_TERMS || schedule == NQS_SCHED_BATCH)
+    return NQS_OK;
+  if (schedule == NQS_SCHED_TRIE) return fail(NQS_ERR_UNSUPPORTED, "schedule not built yet");
   return fail(NQS_ERR_ARG, "unknown schedule");
 }
 
-static int count_pass(const nqs_ham* ham, const uint64_t* U, void* work, const StageHeader& L,
-                      int64_t rb, int64_t re, int64_t* row_ptr, const PairScratch* sc, cudaStream_t s) {
+// AUTO: LoopOverBatch costs ~N_unq^2 / 2 cheap pair tests, LoopOverTerms
+// N_unq * |XY| filter probes; take the batch loop when it has fewer.
+static int pick_schedule(const nqs_ham* ham, int64_t n, int schedule) {
+  if (schedule != NQS_SCHED_AUTO) return schedule;
+  return (n < ham->n_xy) ? NQS_SCHED_BATCH : NQS_SCHED_TERMS;
+}
+
+static cudaError_t launch_search(const nqs_ham* ham, const uint64_t* U, int64_t n, const char* work,
+                                 const StageHeader& L, int64_t rb, int64_t re, int schedule,
+                                 int64_t* rp, uint32_t* pj, uint32_t* pk, int mode,
+                                 const PairScratch* sc, cudaStream_t s) {
+  if (pick_schedule(ham, n, schedule) == NQS_SCHED_BATCH)
+    return launch_pairs_batch(ham, U, n, work, L, rb, re, rp, pj, pk, mode, sc, s);
+  return launch_pairs_terms(ham, U, work, L, rb, re, rp, pj, pk, mode, sc, s);
+}
+
+static int count_pass(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, const StageHeader& L,
+                      int64_t rb, int64_t re, int schedule, int64_t* row_ptr, const PairScratch* sc,
+                      cudaStream_t s) {
   const int64_t rows = re - rb;
   cudaError_t e = cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), s);
   if (e != cudaSuccess) return cuda_fail(e, "memset row_ptr");
   if (rows > 0) {
-    if ((e = launch_pairs_terms(ham, U, (char*)work, L, rb, re, row_ptr + 1, nullptr, nullptr,
-                                sc ? kEmit : kCount, sc, s)) != cudaSuccess)
+    if ((e = launch_search(ham, U, n, (char*)work, L, rb, re, schedule, row_ptr + 1, nullptr, nullptr,
+                           sc ? kEmit : kCount, sc, s)) != cudaSuccess)
       return cuda_fail(e, "pair search kernel");
     if ((e = launch_scan(row_ptr + 1, rows, (char*)work, L, s)) != cudaSuccess)
       return cuda_fail(e, "scan kernel");
@@ -413,7 +447,7 @@ int nqs_count_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, vo
   if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(schedule))) return rc;
   if (!row_ptr || !n_pairs) return fail(NQS_ERR_ARG, "null row_ptr or n_pairs");
   cudaStream_t s = (cudaStream_t)stream;
-  if ((rc = count_pass(ham, U, work, L, rb, re, row_ptr, nullptr, s))) return rc;
+  if ((rc = count_pass(ham, U, n, work, L, rb, re, schedule, row_ptr, nullptr, s))) return rc;
   cudaError_t e = cudaMemcpyAsync(n_pairs, row_ptr + (re - rb), sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_fail(e, "count copy");
   return read_status(work, s);
@@ -427,8 +461,8 @@ int nqs_fill_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
   if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(schedule))) return rc;
   if (!row_ptr || !pair_j || !pair_k) return fail(NQS_ERR_ARG, "null output");
   if (re == rb) return NQS_OK;
-  cudaError_t e = launch_pairs_terms(ham, U, (char*)work, L, rb, re, (int64_t*)row_ptr, pair_j, pair_k,
-                                     kFill, nullptr, (cudaStream_t)stream);
+  cudaError_t e = launch_search(ham, U, n, (char*)work, L, rb, re, schedule, (int64_t*)row_ptr, pair_j,
+                                pair_k, kFill, nullptr, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "pair fill kernel");
   return NQS_OK;
 }
@@ -458,7 +492,7 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
   if (((uintptr_t)scratch) & 255) return fail(NQS_ERR_ARG, "scratch not 256-byte aligned");
   PairScratch sc = pair_scratch_view(scratch, rows, scratch_bytes);
   if (sc.max_chunks < 1) return fail(NQS_ERR_CAPACITY, "scratch too small");
-  if ((rc = count_pass(ham, U, work, L, rb, re, row_ptr, &sc, s))) return rc;
+  if ((rc = count_pass(ham, U, n, work, L, rb, re, schedule, row_ptr, &sc, s))) return rc;
   int64_t overflow = 0;
   cudaError_t e = cudaMemcpyAsync(n_pairs, row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_fail(e, "count copy");

@@ -4,8 +4,12 @@
 // h(v) = XOR_{b in v} R[b] makes the hash of a candidate x' = x XOR XY one XOR
 // of two precomputed values, h(x) ^ h(XY).  A blocked Bloom filter of U
 // (one 32-bit word per key, two bits set) lives in shared memory and rejects
-// most candidates; survivors are verified in an open-addressing table of U
-// (keys stored in the slots, linear probing, load <= 1/2) resident in L2.
+// most candidates; survivors are verified in a bucketed table of U resident
+// in L2: 32-byte buckets of four (hash tag, index) slots, at most one key per
+// bucket on average, so a miss reads one sector; only a tag match reads the
+// sample itself for the exact comparison.
+#include <cstring>
+
 #include "device_util.cuh"
 #include "nqs_internal.cuh"
 
@@ -41,22 +45,23 @@ __global__ void stage_kernel(const uint64_t* __restrict__ U, int64_t n, int n_qu
       }
     }
     hx_out[i] = h;
-    int64_t slot = h & (cap - 1);
+    const unsigned long long mine = (unsigned long long)h | ((unsigned long long)i << 32);
+    int64_t b = h & (cap - 1);
     bool placed = false;
-    for (int64_t it = 0; it < cap; ++it) {
-      unsigned long long* sl = table + slot * (W + 1);
-      unsigned long long prev = atomicCAS(sl + W, ~0ull, (unsigned long long)i);
-      if (prev == ~0ull) {
+    for (int64_t it = 0; it < cap && !placed; ++it) {
+      unsigned long long* bk = table + b * 4;
+      for (int k = 0; k < 4; ++k) {
+        const unsigned long long prev = atomicCAS(bk + k, ~0ull, mine);
+        if (prev == ~0ull) { placed = true; break; }
+        if ((uint32_t)prev == h) {  // same tag: compare the samples themselves
+          const int64_t o = (int64_t)(prev >> 32);
+          bool eq = true;
 #pragma unroll
-        for (int w = 0; w < W; ++w) sl[w] = v[w];
-        placed = true;
-        break;
+          for (int w = 0; w < W; ++w) eq = eq && (__ldg(U + o * W + w) == v[w]);
+          if (eq) { atomicOr(status, kStatusDuplicate); placed = true; break; }
+        }
       }
-      bool eq = true;
-#pragma unroll
-      for (int w = 0; w < W; ++w) eq = eq && (__ldg(U + (int64_t)prev * W + w) == v[w]);
-      if (eq) { atomicOr(status, kStatusDuplicate); placed = true; break; }
-      slot = (slot + 1) & (cap - 1);
+      b = (b + 1) & (cap - 1);
     }
     if (!placed) atomicOr(status, kStatusLimit);
     atomicOr(&bloom[h & wmask], bloom_bits(h));
@@ -213,7 +218,7 @@ __device__ __forceinline__ void emit_round(bool found, int r, uint32_t j, uint32
 // Verification of queued candidates: each lane takes several entries at a
 // time so their loads overlap (search record, then hash-table slot).
 template <int W>
-struct FlushWays { static constexpr int value = W == 1 ? 4 : (W == 2 ? 2 : 1); };
+struct FlushWays { static constexpr int value = W == 1 ? 2 : 1; };
 
 template <int W>
 __device__ __forceinline__ void load_slot(const unsigned long long* sl, unsigned long long (&v)[W + 1]) {
@@ -234,71 +239,56 @@ __device__ __forceinline__ void verify_items(const uint32_t* q, int qn, int64_t 
   const int lane = threadIdx.x & 31;
   for (int e0 = 0; e0 < qn; e0 += 32 * kFlushWays) {
     int r[kFlushWays];
-    bool live[kFlushWays], found[kFlushWays];
-    uint32_t id[kFlushWays], j[kFlushWays];
-    uint64_t key[kFlushWays][W];
-    int64_t slot[kFlushWays];
+    uint32_t pos[kFlushWays], s[kFlushWays];
+    uint4 b0[kFlushWays], b1[kFlushWays];
+    bool live[kFlushWays];
 #pragma unroll
-    for (int u = 0; u < kFlushWays; ++u) {
+    for (int u = 0; u < kFlushWays; ++u) {  // candidate hash, then its bucket
       const int e = e0 + u * 32 + lane;
       live[u] = e < qn;
-      found[u] = false;
-      j[u] = 0;
       const uint32_t ent = live[u] ? q[e] : 0u;
       r[u] = (int)(ent >> 24);
-      const uint64_t* rec = a.srch_rec + (int64_t)(ent & 0x00FFFFFFu) * a.rec_words;
-      uint64_t w0 = 0;
-      uint64_t xyw[W];
-      if (W == 1) {
-        const ulonglong2 t = live[u] ? __ldg(reinterpret_cast<const ulonglong2*>(rec)) : make_ulonglong2(0, 0);
-        w0 = t.x;
-        xyw[0] = t.y;
-      } else {
-        w0 = live[u] ? __ldg(rec) : 0ull;
-#pragma unroll
-        for (int w = 0; w < W; ++w) xyw[w] = live[u] ? __ldg(rec + 1 + w) : 0ull;
-      }
-      id[u] = (uint32_t)(w0 >> 32);
-#pragma unroll
-      for (int w = 0; w < W; ++w) key[u][w] = rc->u[r[u]][w] ^ xyw[w];
-      slot[u] = (rc->hx[r[u]] ^ (uint32_t)w0) & a.capmask;
-    }
-    bool more[kFlushWays];
-#pragma unroll
-    for (int u = 0; u < kFlushWays; ++u) {  // first table slot of every candidate
-      more[u] = false;
-      if (live[u]) {
-        unsigned long long v[W + 1];
-        load_slot<W>(a.table + slot[u] * (W + 1), v);
-        bool eq = v[W] != ~0ull;
-#pragma unroll
-        for (int w = 0; w < W; ++w) eq = eq && (v[w] == key[u][w]);
-        if (eq) { found[u] = true; j[u] = (uint32_t)v[W]; }
-        else if (v[W] != ~0ull) more[u] = true;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kFlushWays; ++u) {  // rare: continue linear probing
-      if (more[u]) {
-        int64_t sl = slot[u];
-        int64_t it = 1;
-        for (; it <= a.capmask; ++it) {
-          sl = (sl + 1) & a.capmask;
-          unsigned long long v[W + 1];
-          load_slot<W>(a.table + sl * (W + 1), v);
-          if (v[W] == ~0ull) break;
-          bool eq = true;
-#pragma unroll
-          for (int w = 0; w < W; ++w) eq = eq && (v[w] == key[u][w]);
-          if (eq) { found[u] = true; j[u] = (uint32_t)v[W]; break; }
-        }
-        if (it > a.capmask) atomicOr(a.status, kStatusLimit);
-      }
-      found[u] = found[u] && id[u] != kDummy;  // padding slots carry XY = 0 and never count
+      pos[u] = ent & 0x00FFFFFFu;
+      s[u] = live[u] ? (rc->hx[r[u]] ^ __ldg(a.srch_hash + pos[u])) : 0u;
+      const uint4* bk = reinterpret_cast<const uint4*>(a.table + (int64_t)(s[u] & a.capmask) * 4);
+      b0[u] = live[u] ? __ldg(bk) : make_uint4(~0u, ~0u, ~0u, ~0u);
+      b1[u] = live[u] ? __ldg(bk + 1) : make_uint4(~0u, ~0u, ~0u, ~0u);
     }
 #pragma unroll
     for (int u = 0; u < kFlushWays; ++u) {
-      if (e0 + u * 32 < qn) emit_round<MODE, W>(found[u], r[u], j[u], id[u], acc, es, rc, a);
+      bool found = false;
+      uint32_t j = 0, id = kDummy;
+      if (live[u]) {
+        const uint64_t* rec = a.srch_rec + (int64_t)pos[u] * a.rec_words;
+        uint4 c0 = b0[u], c1 = b1[u];
+        int64_t b = s[u] & a.capmask;
+        for (int64_t it = 0; it <= a.capmask; ++it) {
+          const uint32_t tag[4] = {c0.x, c0.z, c1.x, c1.z};
+          const uint32_t idx[4] = {c0.y, c0.w, c1.y, c1.w};
+          bool done = false;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (done) break;
+            if (idx[k] == ~0u) { done = true; break; }  // empty slot ends the probe
+            if (tag[k] == s[u]) {                        // tag match: exact comparison
+              id = (uint32_t)(__ldg(rec) >> 32);
+              bool eq = true;
+#pragma unroll
+              for (int w = 0; w < W; ++w)
+                eq = eq && ((rc->u[r[u]][w] ^ __ldg(rec + 1 + w)) == __ldg(a.U + (int64_t)idx[k] * W + w));
+              if (eq) { found = true; j = idx[k]; done = true; }
+            }
+          }
+          if (done) break;
+          if (it == a.capmask) atomicOr(a.status, kStatusLimit);
+          b = (b + 1) & a.capmask;  // the bucket was full: continue in the next one
+          const uint4* bk = reinterpret_cast<const uint4*>(a.table + b * 4);
+          c0 = __ldg(bk);
+          c1 = __ldg(bk + 1);
+        }
+      }
+      found = found && id != kDummy;  // padding slots carry XY = 0 and never count
+      if (e0 + u * 32 < qn) emit_round<MODE, W>(found, r[u], j, id, acc, es, rc, a);
     }
   }
 }
@@ -565,9 +555,275 @@ cudaError_t launch_pairs_compact(const PairScratch& sc, int64_t rows, const int6
   return cudaGetLastError();
 }
 
-cudaError_t launch_pairs_batch(const nqs_ham*, const uint64_t*, const char*, const StageHeader&,
-                               int64_t, int64_t, int64_t*, uint32_t*, uint32_t*, bool, cudaStream_t) {
-  return cudaErrorNotSupported;
+// --------------------------------------------------------------------------
+// LoopOverBatch schedule (Alg. 2B).  A warp owns 8 rows and streams the
+// columns j of U (lane t takes column 32c + t): d = x_r XOR U_j passes the
+// cheap test "popcount(d) is the weight of some XY pattern"; survivors are
+// verified in the XY hash set (same linear hash: h(d) = h(x_r) ^ h(U_j)).
+// Items keep column order per row; the diagonal pair leads its row.
+// --------------------------------------------------------------------------
+struct BatchArgs {
+  const uint64_t* U;
+  int64_t n;
+  const uint32_t* hx;
+  const unsigned long long* xy_table;
+  int64_t xy_capmask;
+  const unsigned long long* wmask;
+  int has_diag;
+  int64_t row_begin, row_end;
+  int64_t* rp;
+  uint32_t* pair_j;
+  uint32_t* pair_k;
+  int32_t* status;
+  unsigned long long* batch_counter;
+  PairScratch sc;
+  SearchArgs emit;  // pair_j, pair_k, sc for emit_round
+};
+
+constexpr int kBatchThreads = 512;
+constexpr int kBatchWarps = kBatchThreads / 32;
+
+template <int W, int MODE>
+__device__ __forceinline__ void batch_verify(const uint32_t* items, int n_items, int64_t (&acc)[R], EmitState& es,
+                                             RowCache<W>* rc, const BatchArgs& a) {
+  const int lane = threadIdx.x & 31;
+  for (int e0 = 0; e0 < n_items; e0 += 32) {
+    const int e = e0 + lane;
+    bool found = false;
+    int r = 0;
+    uint32_t j = 0, id = 0;
+    if (e < n_items) {
+      const uint32_t it = items[e];
+      r = (int)(it >> 24);
+      j = it & 0x00FFFFFFu;
+      uint64_t d[W];
+#pragma unroll
+      for (int w = 0; w < W; ++w) d[w] = rc->u[r][w] ^ __ldg(a.U + (int64_t)j * W + w);
+      int64_t slot = (rc->hx[r] ^ __ldg(a.hx + j)) & a.xy_capmask;
+      int64_t k = 0;
+      for (; k <= a.xy_capmask; ++k) {
+        const unsigned long long* sl = a.xy_table + slot * (W + 1);
+        const unsigned long long tag = __ldg(sl + W);
+        if (tag == ~0ull) break;
+        bool eq = true;
+#pragma unroll
+        for (int w = 0; w < W; ++w) eq = eq && (__ldg(sl + w) == d[w]);
+        if (eq) { found = true; id = (uint32_t)tag; break; }
+        slot = (slot + 1) & a.xy_capmask;
+      }
+      if (k > a.xy_capmask) atomicOr(a.status, kStatusLimit);
+    }
+    emit_round<MODE, W>(found, r, j, id, acc, es, rc, a.emit);
+  }
+}
+
+template <int W, int MODE>
+__global__ void __launch_bounds__(kBatchThreads) pairs_batch_kernel(const BatchArgs a) {
+  __shared__ RowCache<W> caches[kBatchWarps];
+  __shared__ uint32_t queue[kBatchWarps][kQueueCap];
+  __shared__ uint32_t xbufs[kBatchWarps][kXbufCap];
+  __shared__ unsigned long long wm[5];
+  if (threadIdx.x < 5) wm[threadIdx.x] = __ldg(a.wmask + threadIdx.x);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t* q = queue[warp];
+  uint32_t* xbuf = xbufs[warp];
+  RowCache<W>* rc = caches + warp;
+  const int64_t n_rows = a.row_end - a.row_begin;
+  const int64_t n_batches = (n_rows + R - 1) / R;
+  const int64_t pbase = (MODE == kFill) ? a.rp[0] : 0;
+  while (true) {
+    unsigned long long btu = 0;
+    if (lane == 0) btu = atomicAdd(a.batch_counter, 1ull);
+    const int64_t bt = (int64_t)__shfl_sync(kFull, btu, 0);
+    if (bt >= n_batches) break;
+    const int64_t r0 = a.row_begin + bt * R;
+    __syncwarp();
+    if (lane < R) {
+      const int64_t row = r0 + lane;
+      const bool valid = row < a.row_end;
+#pragma unroll
+      for (int w = 0; w < W; ++w) rc->u[lane][w] = valid ? __ldg(a.U + row * W + w) : 0ull;
+      rc->hx[lane] = valid ? __ldg(a.hx + row) : 0u;
+      rc->cnt[lane] = 0u;
+    }
+    __syncwarp();
+    uint64_t xr[R][W];
+    uint32_t vmask = 0;
+    int64_t acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t row = r0 + r;
+      const bool valid = row < a.row_end;
+#pragma unroll
+      for (int w = 0; w < W; ++w) xr[r][w] = rc->u[r][w];
+      if (valid) vmask |= 1u << (R - 1 - r);
+      acc[r] = (MODE == kFill && valid) ? a.rp[row - a.row_begin] - pbase : 0;
+    }
+    EmitState es{-1, 0, -1};
+    if (a.has_diag) {
+      const bool d = lane < R && r0 + lane < a.row_end;
+      emit_round<MODE, W>(d, lane, (uint32_t)(r0 + lane), 0u, acc, es, rc, a.emit);
+    }
+    int qn = 0;
+    for (int64_t c0 = 0; c0 < a.n; c0 += 32) {
+      const int64_t j = c0 + lane;
+      const bool vj = j < a.n;
+      uint64_t uj[W];
+#pragma unroll
+      for (int w = 0; w < W; ++w) uj[w] = vj ? __ldg(a.U + j * W + w) : 0ull;
+      uint32_t hm = 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        int wt = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) wt += __popcll(xr[r][w] ^ uj[w]);
+        const uint32_t t = (uint32_t)(wm[wt >> 6] >> (wt & 63)) & (wt != 0 ? 1u : 0u);
+        hm = (hm << 1) | t;
+      }
+      hm &= vj ? vmask : 0u;
+      const uint32_t bal = __ballot_sync(kFull, hm != 0u);
+      if (bal) {
+        if (hm) q[qn + __popc(bal & lt)] = (hm << 24) | (uint32_t)j;
+        qn += __popc(bal);
+        if (qn > kQueueCap - 32) {
+          __syncwarp();
+          // expand and verify (same order rules as the LoopOverTerms flush)
+          int xn = 0;
+          for (int s0 = 0; s0 < qn; s0 += 32) {
+            if (xn + 32 * R > kXbufCap) {
+              __syncwarp();
+              batch_verify<W, MODE>(xbuf, xn, acc, es, rc, a);
+              __syncwarp();
+              xn = 0;
+            }
+            const int e = s0 + lane;
+            const uint32_t ent = e < qn ? q[e] : 0u;
+            uint32_t bits = ent >> 24;
+            const uint32_t col = ent & 0x00FFFFFFu;
+            const int c = __popc(bits);
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int t = __shfl_up_sync(kFull, incl, o);
+              if (lane >= o) incl += t;
+            }
+            int at = xn + incl - c;
+            while (bits) {
+              const int b = 31 - __clz(bits);
+              bits &= ~(1u << b);
+              xbuf[at++] = ((uint32_t)(R - 1 - b) << 24) | col;
+            }
+            xn += __shfl_sync(kFull, incl, 31);
+          }
+          __syncwarp();
+          batch_verify<W, MODE>(xbuf, xn, acc, es, rc, a);
+          __syncwarp();
+          qn = 0;
+        }
+      }
+    }
+    __syncwarp();
+    {
+      int xn = 0;
+      for (int s0 = 0; s0 < qn; s0 += 32) {
+        if (xn + 32 * R > kXbufCap) {
+          __syncwarp();
+          batch_verify<W, MODE>(xbuf, xn, acc, es, rc, a);
+          __syncwarp();
+          xn = 0;
+        }
+        const int e = s0 + lane;
+        const uint32_t ent = e < qn ? q[e] : 0u;
+        uint32_t bits = ent >> 24;
+        const uint32_t col = ent & 0x00FFFFFFu;
+        const int c = __popc(bits);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += t;
+        }
+        int at = xn + incl - c;
+        while (bits) {
+          const int b = 31 - __clz(bits);
+          bits &= ~(1u << b);
+          xbuf[at++] = ((uint32_t)(R - 1 - b) << 24) | col;
+        }
+        xn += __shfl_sync(kFull, incl, 31);
+      }
+      __syncwarp();
+      batch_verify<W, MODE>(xbuf, xn, acc, es, rc, a);
+      __syncwarp();
+    }
+    if (MODE != kFill && lane < R && r0 + lane < a.row_end)
+      a.rp[r0 + lane - a.row_begin] = (int64_t)rc->cnt[lane];
+    if (MODE == kEmit && lane == 0) {
+      a.sc.heads[bt] = es.first;
+      if (es.chunk >= 0) a.sc.next[es.chunk] = -1;
+    }
+  }
+}
+
+template <int W, int MODE>
+static cudaError_t launch_batch_w(const BatchArgs& args, int64_t rows, cudaStream_t s) {
+  auto kern = pairs_batch_kernel<W, MODE>;
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBatchThreads, 0);
+  if (occ < 1) occ = 1;
+  const int64_t batches = (rows + R - 1) / R;
+  const int64_t need = (batches + kBatchWarps - 1) / kBatchWarps;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * occ));
+  kern<<<blocks, kBatchThreads, 0, s>>>(args);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pairs_batch(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, const char* stage,
+                               const StageHeader& L, int64_t rb, int64_t re, int64_t* rp, uint32_t* pj,
+                               uint32_t* pk, int mode, const PairScratch* sc, cudaStream_t s) {
+  if (n_unq >= (int64_t(1) << 24)) return cudaErrorInvalidValue;
+  BatchArgs a;
+  a.U = U;
+  a.n = n_unq;
+  a.hx = (const uint32_t*)(stage + L.off_hx);
+  a.xy_table = ham->xy_table;
+  a.xy_capmask = ham->xy_cap - 1;
+  a.wmask = ham->wmask;
+  a.has_diag = ham->has_diag;
+  a.row_begin = rb;
+  a.row_end = re;
+  a.rp = rp;
+  a.pair_j = pj;
+  a.pair_k = pk;
+  a.status = (int32_t*)(stage + offsetof(StageHeader, status));
+  a.batch_counter = (unsigned long long*)(stage + L.off_counters);
+  if (sc) a.sc = *sc; else a.sc = PairScratch{0, nullptr, nullptr, nullptr, nullptr};
+  std::memset(&a.emit, 0, sizeof(a.emit));
+  a.emit.pair_j = pj;
+  a.emit.pair_k = pk;
+  a.emit.sc = a.sc;
+  cudaError_t e = cudaMemsetAsync(a.batch_counter, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  if (mode == kEmit) {
+    e = cudaMemsetAsync(sc->cursor, 0, 2 * sizeof(int64_t), s);
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t rows = re - rb;
+#define NQS_BATCH(WW)                                                          \
+  case WW:                                                                     \
+    if (mode == kCount) return launch_batch_w<WW, kCount>(a, rows, s);         \
+    if (mode == kFill) return launch_batch_w<WW, kFill>(a, rows, s);           \
+    return launch_batch_w<WW, kEmit>(a, rows, s);
+  switch (ham->W) {
+    NQS_BATCH(1)
+    NQS_BATCH(2)
+    NQS_BATCH(3)
+    default:
+    NQS_BATCH(4)
+  }
+#undef NQS_BATCH
 }
 
 // --------------------------------------------------------------------------

@@ -48,6 +48,9 @@ struct nqs_ham_dev {
   uint64_t* srch_rec = nullptr;  // [n_srch][rec_words]: (hash | id << 32), XY words (0 for padding)
   int rec_words = 0;             // 64-bit words per search record (16-byte multiple)
   uint32_t* hash_basis = nullptr;// [64 * W]    R[b]: h(v) = XOR of R[b] over set bits b
+  unsigned long long* xy_table = nullptr;  // XY hash set: slots of W key words + (id | hash << 32), id = ~0: empty
+  int64_t xy_cap = 0;            // slots (power of two)
+  unsigned long long* wmask = nullptr;     // [5] bit w set if some pattern has Hamming weight w
 
   // host copies (export, tests)
   std::vector<uint64_t> h_xy, h_yz;
@@ -69,7 +72,7 @@ namespace nqs {
 struct StageHeader {
   uint64_t magic;
   int64_t n_unq;
-  int64_t cap;          // hash-table slots (power of two)
+  int64_t cap;          // hash-table buckets of 4 slots (power of two)
   int64_t nwords;       // bloom words (power of two)
   int32_t W;
   int32_t status;       // device status word (kStatus* bits)
@@ -115,10 +118,10 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, const char
 cudaError_t launch_pairs_compact(const PairScratch& sc, int64_t rows, const int64_t* row_ptr,
                                  uint32_t* pair_j, uint32_t* pair_k, cudaStream_t s);
 
-cudaError_t launch_pairs_batch(const nqs_ham* ham, const uint64_t* U, const char* stage,
+cudaError_t launch_pairs_batch(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, const char* stage,
                                const StageHeader& L, int64_t row_begin, int64_t row_end,
                                int64_t* counts_or_rowptr, uint32_t* pair_j, uint32_t* pair_k,
-                               bool fill, cudaStream_t s);
+                               int mode, const PairScratch* scratch, cudaStream_t s);
 
 cudaError_t launch_scan(int64_t* data, int64_t n, char* stage, const StageHeader& L,
                         cudaStream_t s);

@@ -184,6 +184,48 @@ def test_one_pass_equals_two_pass(h28):
         assert sorted(zip(rows.tolist(), j.tolist())) == want
 
 
+@pytest.mark.parametrize("schedule", ["batch", "auto"])
+def test_batch_schedule_matches_terms(h28, schedule):
+    """LoopOverBatch (Alg. 2B) lists the same pairs; energies agree to rounding."""
+    inst, ref_ham, ref = h28
+    ham, batch = gpu_objects(inst)
+    for r0, r1 in [(0, inst.n_unq), (17, 1234)]:
+        t = nqs.coupled_pairs(batch, r0, r1, schedule="terms")
+        b = nqs.coupled_pairs(batch, r0, r1, schedule=schedule)
+        assert torch.equal(t[0], b[0])  # same counts per row
+        rt, jt, kt = pair_set_gpu(batch, t, r0)
+        rb, jb, kb = pair_set_gpu(batch, b, r0)
+        assert sorted(zip(rt.tolist(), jt.tolist(), kt.tolist())) == sorted(zip(rb.tolist(), jb.tolist(), kb.tolist()))
+        # the diagonal pair leads each row in both schedules
+        rp = b[0].cpu().numpy()
+        assert np.all(jb[rp[:-1] - rp[0]] == np.arange(r0, r1))
+    two = nqs.coupled_pairs(batch, schedule=schedule, one_pass=False)
+    one = nqs.coupled_pairs(batch, schedule=schedule)
+    for x, y in zip(one, two):
+        assert torch.equal(x, y)
+    eb = nqs.evaluate(batch, inst.logpsi_re, None, "fp64", schedule=schedule)
+    want = np.array([e.real for e in ref["eloc"]])
+    assert np.abs(eb["eloc_re"].cpu().numpy() - want).max() < TOL64
+
+
+def test_batch_schedule_random_multiword():
+    for n, seed in ((70, 4), (130, 5)):
+        x, z, c = random_pauli_hamiltonian(n, 150, seed, allow_odd_y=False, max_weight=4)
+        pyrng = __import__("random").Random(seed)
+        Ui = set()
+        while len(Ui) < 300:
+            v = pyrng.getrandbits(n)
+            Ui.add(v)
+            Ui.add(v ^ (3 << 5))  # make some pairs couple through 2-bit patterns
+        Ui = sorted(Ui)[:300]
+        ref_ham = oracle.prepare_hamiltonian(x, z, c, n)
+        ref_pairs = oracle.find_coupled_pairs(Ui, ref_ham, "batch")
+        ham = nqs.Hamiltonian(x, z, c, n)
+        batch = nqs.Batch(ham, to_dev_u(pack_ints(Ui, n)))
+        pairs = nqs.coupled_pairs(batch, schedule="batch")
+        _check_pairs(batch, pairs, ref_pairs, Ui, _xy_ints(ham))
+
+
 def test_deterministic(h28):
     inst, _, _ = h28
     ham, batch = gpu_objects(inst)

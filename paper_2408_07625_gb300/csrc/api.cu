@@ -46,11 +46,12 @@ StageHeader stage_layout(const nqs_ham* ham, int64_t n) {
   L.n_unq = n;
   L.W = ham->W;
   L.cap = next_pow2(std::max<int64_t>(n, 16));        // buckets of 4 slots, <= 1 key per bucket on average
-  L.nwords = std::min<int64_t>(std::max<int64_t>(next_pow2(std::max<int64_t>(n / 2, 1)), 32), 32768);
+  // two filters (one per pass), each for about half of the samples
+  L.nwords = std::min<int64_t>(std::max<int64_t>(next_pow2(std::max<int64_t>(n / 4, 1)), 32), 32768);
   int64_t off = align256(kRedOffset + kRedBytes);
   L.off_hx = off;     off = align256(off + 4 * std::max<int64_t>(n, 1));
   L.off_table = off;  off = align256(off + 32 * L.cap);
-  L.off_bloom = off;  off = align256(off + 4 * L.nwords);
+  L.off_bloom = off;  off = align256(off + 2 * 4 * L.nwords);
   L.scan_blocks = (std::max<int64_t>(n, 1) + 1023) / 1024 + 1;
   L.off_scan = off;   off = align256(off + 8 * L.scan_blocks);
   L.off_ampP = off;   off = align256(off + 16 * std::max<int64_t>(n, 1));
@@ -58,6 +59,8 @@ StageHeader stage_layout(const nqs_ham* ham, int64_t n) {
   L.off_ampK = off;   off = align256(off + 4 * std::max<int64_t>(n, 1));
   L.off_geff = off;   off = align256(off + 16 * std::max<int64_t>(n, 1));
   L.off_counters = off; off = align256(off + 256);
+  L.off_perm = off;   off = align256(off + 2 * 4 * std::max<int64_t>(n, 1));
+  L.off_rowcur = off; off = align256(off + 8 * std::max<int64_t>(n, 1));
   L.total_bytes = off;
   return L;
 }
@@ -258,9 +261,13 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
   std::vector<uint32_t> srch_hash, srch_id;
   std::vector<uint64_t> srch_rec;
   h->rec_words = 2 * ((1 + W + 1) / 2);
-  auto build_class = [&](int64_t lo, int64_t hi) {
+  // The table is split in two halves by the top hash bit t = hash >> 31: a
+  // row x probes half t in the pass that holds the samples whose top hash bit
+  // is (h(x) >> 31) ^ t, so every (row, pattern) pair is probed exactly once.
+  auto build_class = [&](int64_t lo, int64_t hi, uint32_t half) {
     std::vector<std::vector<uint32_t>> buckets(32);
-    for (int64_t p = lo; p < hi; ++p) buckets[hxy[p] & 31].push_back((uint32_t)p);
+    for (int64_t p = lo; p < hi; ++p)
+      if ((hxy[p] >> 31) == half) buckets[hxy[p] & 31].push_back((uint32_t)p);
     size_t Gc = 0;
     for (auto& b : buckets) Gc = std::max(Gc, b.size());
     for (size_t g = 0; g < Gc; ++g)
@@ -273,15 +280,20 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
           for (int w = 0; w < W; ++w) srch_rec.push_back(h->h_xy[(int64_t)id * W + w]);
           for (int w = 1 + W; w < h->rec_words; ++w) srch_rec.push_back(0);
         } else {
-          srch_hash.push_back((uint32_t)b);
+          const uint32_t dh = (uint32_t)b | (half << 31);
+          srch_hash.push_back(dh);
           srch_id.push_back(kDummy);
-          srch_rec.push_back((uint64_t)b | ((uint64_t)kDummy << 32));
+          srch_rec.push_back((uint64_t)dh | ((uint64_t)kDummy << 32));
           for (int w = 1; w < h->rec_words; ++w) srch_rec.push_back(0);
         }
       }
   };
-  build_class(h->has_diag, h->heavy_end);
-  build_class(h->heavy_end, G);
+  for (uint32_t half = 0; half < 2; ++half) {
+    h->half_begin[half] = (int64_t)srch_hash.size() / 32;
+    build_class(h->has_diag, h->heavy_end, half);
+    build_class(h->heavy_end, G, half);
+    h->half_end[half] = (int64_t)srch_hash.size() / 32;
+  }
   h->n_srch = (int64_t)srch_hash.size();
 
   // XY hash set for the batch schedule (Alg. 2B): same linear hash, so the
@@ -383,7 +395,7 @@ int nqs_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, int6
   cudaError_t e = cudaMemcpyAsync(base, &L, sizeof(L), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e, "header copy");
   if ((e = cudaMemsetAsync(base + L.off_table, 0xFF, 32 * L.cap, s)) != cudaSuccess) return cuda_fail(e, "memset");
-  if ((e = cudaMemsetAsync(base + L.off_bloom, 0, 4 * L.nwords, s)) != cudaSuccess) return cuda_fail(e, "memset");
+  if ((e = cudaMemsetAsync(base + L.off_bloom, 0, 2 * 4 * L.nwords, s)) != cudaSuccess) return cuda_fail(e, "memset");
   if ((e = cudaMemsetAsync(base + kRedOffset, 0, 256, s)) != cudaSuccess) return cuda_fail(e, "memset");
   if ((e = launch_stage(ham, U, n, base, L, s)) != cudaSuccess) return cuda_fail(e, "stage kernel");
   if (check) return read_status(work, s);
@@ -482,7 +494,7 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
   if (!row_ptr || !n_pairs) return fail(NQS_ERR_ARG, "null row_ptr or n_pairs");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t rows = re - rb;
-  if (!scratch) {  // two passes: count, then fill
+  if (!scratch || pick_schedule(ham, n, schedule) == NQS_SCHED_BATCH) {  // count, then fill
     rc = nqs_count_coupled_pairs(ham, U, n, work, rb, re, schedule, row_ptr, n_pairs, stream);
     if (rc) return rc;
     if (*n_pairs > capacity) return fail(NQS_ERR_CAPACITY, "pair capacity too small");
@@ -503,7 +515,7 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
   if (*n_pairs > capacity) return fail(NQS_ERR_CAPACITY, "pair capacity too small");
   if (rows == 0 || *n_pairs == 0) return NQS_OK;
   if (!pair_j || !pair_k) return fail(NQS_ERR_ARG, "null pair arrays");
-  e = launch_pairs_compact(sc, rows, row_ptr, pair_j, pair_k, s);
+  e = launch_pairs_compact(sc, (const char*)work, L, rb, rows, row_ptr, pair_j, pair_k, s);
   if (e != cudaSuccess) return cuda_fail(e, "compaction kernel");
   return NQS_OK;
 }

@@ -64,7 +64,7 @@ __global__ void stage_kernel(const uint64_t* __restrict__ U, int64_t n, int n_qu
       b = (b + 1) & (cap - 1);
     }
     if (!placed) atomicOr(status, kStatusLimit);
-    atomicOr(&bloom[h & wmask], bloom_bits(h));
+    atomicOr(&bloom[(int64_t)(h >> 31) * (wmask + 1) + (h & wmask)], bloom_bits(h));
   }
 }
 
@@ -91,23 +91,25 @@ cudaError_t launch_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, char*
 // --------------------------------------------------------------------------
 static inline int64_t a256(int64_t v) { return (v + 255) & ~int64_t(255); }
 
+static inline int64_t nb_max(int64_t rows) { return (rows + kRowsPerWarp - 1) / kRowsPerWarp + 2; }
+
 int64_t pair_scratch_bytes(int64_t rows, int64_t max_pairs) {
-  const int64_t nb = (rows + kRowsPerWarp - 1) / kRowsPerWarp;
-  const int64_t chunks = (max_pairs + kChunk - 1) / kChunk + nb;
-  return 256 + a256(4 * std::max<int64_t>(nb, 1)) + a256(4 * chunks) + 8 * kChunk * chunks;
+  const int64_t nb = nb_max(rows);
+  const int64_t chunks = (max_pairs + kChunk - 1) / kChunk + 2 * nb;
+  return 256 + a256(16 * nb) + a256(4 * chunks) + 8 * kChunk * chunks;
 }
 
 PairScratch pair_scratch_view(void* base, int64_t rows, int64_t bytes) {
   PairScratch sc;
-  const int64_t nb = (rows + kRowsPerWarp - 1) / kRowsPerWarp;
+  const int64_t nb = nb_max(rows);
   char* p = (char*)base;
   sc.cursor = (int64_t*)p;
   sc.heads = (int32_t*)(p + 256);
-  int64_t rest = bytes - 256 - a256(4 * std::max<int64_t>(nb, 1));
+  int64_t rest = bytes - 256 - a256(16 * nb);
   int64_t chunks = rest / (4 + 8 * kChunk);
   while (chunks > 0 && a256(4 * chunks) + 8 * kChunk * chunks > rest) --chunks;
   sc.max_chunks = std::max<int64_t>(chunks, 0);
-  sc.next = (int32_t*)(p + 256 + a256(4 * std::max<int64_t>(nb, 1)));
+  sc.next = (int32_t*)(p + 256 + a256(16 * nb));
   sc.records = (uint64_t*)((char*)sc.next + a256(4 * std::max<int64_t>(sc.max_chunks, 1)));
   return sc;
 }
@@ -146,10 +148,18 @@ struct SearchArgs {
   int32_t* status;
   unsigned long long* batch_counter;
   PairScratch sc;
+  // two-pass filtering: rows of each class (top hash bit) in perm, pass index
+  int pass;
+  const int32_t* perm;
+  int64_t perm_stride;
+  const unsigned long long* cls_cnt;
+  int64_t g_begin[2], g_end[2];
+  int64_t* rowcur;
+  int64_t nbm;
 };
 
 struct EmitState {  // warp-uniform chunk state of the one-pass mode
-  int32_t chunk, fill, first;
+  int32_t chunk, fill, first, total;
 };
 
 template <int W>
@@ -157,6 +167,7 @@ struct RowCache {   // per-warp copy of the batch's rows (shared memory)
   uint64_t u[R][W];
   uint32_t hx[R];
   uint32_t cnt[R];
+  int64_t row[R];
 };
 
 // Emit one round of verified candidates (lane order).  COUNT/EMIT count per
@@ -186,6 +197,7 @@ __device__ __forceinline__ void emit_round(bool found, int r, uint32_t j, uint32
     const uint32_t m = __ballot_sync(kFull, found);
     const int n = __popc(m);
     if (n == 0 || es.chunk == -2) return;
+    es.total += n;
     const int off = __popc(m & lt);
     const uint64_t rec = (uint64_t)j | ((uint64_t)id << 32) | ((uint64_t)r << 61);
     const int room = es.chunk >= 0 ? kChunk - es.fill : 0;
@@ -232,6 +244,34 @@ __device__ __forceinline__ void load_slot(const unsigned long long* sl, unsigned
   }
 }
 
+// Exact membership of x' = x_r XOR XY(pos) in the bucket chain starting at
+// bucket b (slow path: full buckets, several equal tags).
+template <int W>
+__device__ __noinline__ bool verify_slow(int r, uint32_t pos, uint32_t sh, const RowCache<W>* rc,
+                                         const SearchArgs& a, uint32_t& j) {
+  const uint64_t* rec = a.srch_rec + (int64_t)pos * a.rec_words;
+  uint64_t key[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) key[w] = rc->u[r][w] ^ __ldg(rec + 1 + w);
+  int64_t b = sh & a.capmask;
+  for (int64_t it = 0; it <= a.capmask; ++it) {
+    const uint2* bk = reinterpret_cast<const uint2*>(a.table + b * 4);
+    for (int k = 0; k < 4; ++k) {
+      const uint2 sl = __ldg(bk + k);
+      if (sl.y == ~0u) return false;  // an empty slot ends the chain
+      if (sl.x == sh) {
+        bool eq = true;
+#pragma unroll
+        for (int w = 0; w < W; ++w) eq = eq && (__ldg(a.U + (int64_t)sl.y * W + w) == key[w]);
+        if (eq) { j = sl.y; return true; }
+      }
+    }
+    b = (b + 1) & a.capmask;
+  }
+  atomicOr(a.status, kStatusLimit);
+  return false;
+}
+
 template <int W, int MODE>
 __device__ __forceinline__ void verify_items(const uint32_t* q, int qn, int64_t (&acc)[R],
                                              EmitState& es, RowCache<W>* rc, const SearchArgs& a) {
@@ -246,46 +286,41 @@ __device__ __forceinline__ void verify_items(const uint32_t* q, int qn, int64_t 
     for (int u = 0; u < kFlushWays; ++u) {  // candidate hash, then its bucket
       const int e = e0 + u * 32 + lane;
       live[u] = e < qn;
-      const uint32_t ent = live[u] ? q[e] : 0u;
+      const uint32_t ent = q[live[u] ? e : e0];
       r[u] = (int)(ent >> 24);
       pos[u] = ent & 0x00FFFFFFu;
-      s[u] = live[u] ? (rc->hx[r[u]] ^ __ldg(a.srch_hash + pos[u])) : 0u;
+      s[u] = rc->hx[r[u]] ^ __ldg(a.srch_hash + pos[u]);
       const uint4* bk = reinterpret_cast<const uint4*>(a.table + (int64_t)(s[u] & a.capmask) * 4);
-      b0[u] = live[u] ? __ldg(bk) : make_uint4(~0u, ~0u, ~0u, ~0u);
-      b1[u] = live[u] ? __ldg(bk + 1) : make_uint4(~0u, ~0u, ~0u, ~0u);
+      b0[u] = __ldg(bk);
+      b1[u] = __ldg(bk + 1);
     }
 #pragma unroll
     for (int u = 0; u < kFlushWays; ++u) {
+      // tag matches among occupied slots; slots fill in order, so slot 3 occupied = full
+      const uint32_t sh = s[u];
+      const uint32_t mm = (uint32_t)(b0[u].x == sh && b0[u].y != ~0u) | ((uint32_t)(b0[u].z == sh && b0[u].w != ~0u) << 1) |
+                          ((uint32_t)(b1[u].x == sh && b1[u].y != ~0u) << 2) | ((uint32_t)(b1[u].z == sh && b1[u].w != ~0u) << 3);
+      const uint32_t jc = (mm & 1u) ? b0[u].y : (mm & 2u) ? b0[u].w : (mm & 4u) ? b1[u].y : b1[u].w;
+      const bool full = b1[u].w != ~0u;
       bool found = false;
       uint32_t j = 0, id = kDummy;
-      if (live[u]) {
+      bool slow = false;
+      if (live[u] && mm) {  // confirm the first match exactly (almost always the only one)
         const uint64_t* rec = a.srch_rec + (int64_t)pos[u] * a.rec_words;
-        uint4 c0 = b0[u], c1 = b1[u];
-        int64_t b = s[u] & a.capmask;
-        for (int64_t it = 0; it <= a.capmask; ++it) {
-          const uint32_t tag[4] = {c0.x, c0.z, c1.x, c1.z};
-          const uint32_t idx[4] = {c0.y, c0.w, c1.y, c1.w};
-          bool done = false;
+        id = (uint32_t)(__ldg(rec) >> 32);
+        bool eq = true;
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            if (done) break;
-            if (idx[k] == ~0u) { done = true; break; }  // empty slot ends the probe
-            if (tag[k] == s[u]) {                        // tag match: exact comparison
-              id = (uint32_t)(__ldg(rec) >> 32);
-              bool eq = true;
-#pragma unroll
-              for (int w = 0; w < W; ++w)
-                eq = eq && ((rc->u[r[u]][w] ^ __ldg(rec + 1 + w)) == __ldg(a.U + (int64_t)idx[k] * W + w));
-              if (eq) { found = true; j = idx[k]; done = true; }
-            }
-          }
-          if (done) break;
-          if (it == a.capmask) atomicOr(a.status, kStatusLimit);
-          b = (b + 1) & a.capmask;  // the bucket was full: continue in the next one
-          const uint4* bk = reinterpret_cast<const uint4*>(a.table + b * 4);
-          c0 = __ldg(bk);
-          c1 = __ldg(bk + 1);
-        }
+        for (int w = 0; w < W; ++w)
+          eq = eq && ((rc->u[r[u]][w] ^ __ldg(rec + 1 + w)) == __ldg(a.U + (int64_t)jc * W + w));
+        found = eq;
+        j = jc;
+        slow = !eq && ((mm & (mm - 1u)) != 0u || full);
+      } else if (live[u] && full) {
+        slow = true;
+      }
+      if (slow) {
+        id = (uint32_t)(__ldg(a.srch_rec + (int64_t)pos[u] * a.rec_words) >> 32);
+        found = verify_slow<W>(r[u], pos[u], sh, rc, a, j);
       }
       found = found && id != kDummy;  // padding slots carry XY = 0 and never count
       if (e0 + u * 32 < qn) emit_round<MODE, W>(found, r[u], j, id, acc, es, rc, a);
@@ -354,25 +389,30 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Se
   uint32_t* xbuf = xbufs + warp * kXbufCap;
   const uint32_t lt = (1u << lane) - 1u;
   RowCache<W>* rc = caches + warp;
-  const int64_t n_rows = a.row_end - a.row_begin;
-  const int64_t n_batches = (n_rows + R - 1) / R;
+  const int64_t cnt0 = (int64_t)a.cls_cnt[0], cnt1 = (int64_t)a.cls_cnt[1];
+  const int64_t nb0 = (cnt0 + R - 1) / R;
+  const int64_t n_batches = nb0 + (cnt1 + R - 1) / R;
   const uint32_t wmask4 = a.wmask << 2;
   const char* bloom_bytes = reinterpret_cast<const char*>(bloom);
-  const int64_t pbase = (MODE == kFill) ? a.rp[0] : 0;
+  const int64_t pbase = (MODE == kFill && a.pass == 0) ? a.rp[0] : 0;
   while (true) {
     unsigned long long btu = 0;
     if (lane == 0) btu = atomicAdd(a.batch_counter, 1ull);
     const int64_t bt = (int64_t)__shfl_sync(kFull, btu, 0);
     if (bt >= n_batches) break;
-    const int64_t r0 = a.row_begin + bt * R;
+    const int cls = bt < nb0 ? 0 : 1;
+    const int64_t b0 = (cls ? bt - nb0 : bt) * R;
+    const int64_t ccount = cls ? cnt1 : cnt0;
+    const int half = cls ^ a.pass;  // patterns whose top hash bit sends x' to this pass's samples
     __syncwarp();
     if (lane < R) {
-      const int64_t row = r0 + lane;
-      const bool valid = row < a.row_end;
+      const bool valid = b0 + lane < ccount;
+      const int64_t row = valid ? (int64_t)a.perm[cls * a.perm_stride + b0 + lane] : -1;
 #pragma unroll
       for (int w = 0; w < W; ++w) rc->u[lane][w] = valid ? __ldg(a.U + row * W + w) : 0ull;
       rc->hx[lane] = valid ? __ldg(a.hx + row) : 0u;
       rc->cnt[lane] = 0u;
+      rc->row[lane] = row;
     }
     __syncwarp();
     uint32_t hr4[R], hr17[R], hr22[R];
@@ -380,22 +420,25 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Se
     int64_t acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int64_t row = r0 + r;
-      const bool valid = row < a.row_end;
+      const int64_t row = rc->row[r];
+      const bool valid = row >= 0;
       const uint32_t h = rc->hx[r];
       hr4[r] = h << 2;
       hr17[r] = h >> 17;
       hr22[r] = h >> 22;
       if (valid) vmask |= 1u << (R - 1 - r);
-      acc[r] = (MODE == kFill && valid) ? a.rp[row - a.row_begin] - pbase : 0;
+      acc[r] = 0;
+      if (MODE == kFill && valid)
+        acc[r] = a.pass == 0 ? a.rp[row - a.row_begin] - pbase : a.rowcur[row - a.row_begin];
     }
-    EmitState es{-1, 0, -1};
-    if (a.has_diag) {  // the diagonal pair (x, x) comes first in its row
-      const bool d = lane < R && r0 + lane < a.row_end;
-      emit_round<MODE, W>(d, lane, (uint32_t)(r0 + lane), 0u, acc, es, rc, a);
+    EmitState es{-1, 0, -1, 0};
+    if (a.has_diag && a.pass == 0) {  // the diagonal pair (x, x) comes first in its row
+      const int64_t myrow = rc->row[lane < R ? lane : 0];
+      const bool d = lane < R && myrow >= 0;
+      emit_round<MODE, W>(d, lane, (uint32_t)(d ? myrow : 0), 0u, acc, es, rc, a);
     }
     int qn = 0;
-    for (int64_t g = 0; g < a.n_groups; ++g) {
+    for (int64_t g = a.g_begin[half]; g < a.g_end[half]; ++g) {
       const uint32_t pos = (uint32_t)(g * 32 + lane);
       const uint32_t hk = __ldg(a.srch_hash + pos);
       const uint32_t hk4 = hk << 2, hk17 = hk >> 17, hk22 = hk >> 22;
@@ -422,12 +465,35 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Se
     __syncwarp();
     flush_queue<W, MODE>(q, qn, xbuf, acc, es, rc, a);
     __syncwarp();
-    if (MODE != kFill && lane < R && r0 + lane < a.row_end)
-      a.rp[r0 + lane - a.row_begin] = (int64_t)rc->cnt[lane];
+    if (MODE != kFill && lane < R && rc->row[lane] >= 0) {
+      const int64_t rl = rc->row[lane] - a.row_begin;
+      if (a.pass == 0) a.rp[rl] = (int64_t)rc->cnt[lane];
+      else a.rp[rl] += (int64_t)rc->cnt[lane];
+    }
+    if (MODE == kFill && a.pass == 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (lane == r && rc->row[r] >= 0) a.rowcur[rc->row[r] - a.row_begin] = acc[r];
+    }
     if (MODE == kEmit && lane == 0) {
-      a.sc.heads[bt] = es.first;
+      a.sc.heads[a.pass * a.nbm + bt] = es.first;
+      a.sc.heads[(2 + a.pass) * a.nbm + bt] = es.total;
       if (es.chunk >= 0) a.sc.next[es.chunk] = -1;
     }
+  }
+}
+
+// Split the rows of [row_begin, row_end) by the top bit of their hash.  The
+// order inside a class does not matter: a row's pairs come out in the same
+// order whatever rows share its batch.
+__global__ void partition_rows_kernel(const uint32_t* __restrict__ hx, int64_t rb, int64_t re,
+                                      int32_t* __restrict__ perm, int64_t stride,
+                                      unsigned long long* __restrict__ cnt) {
+  for (int64_t row = rb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < re;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(__ldg(hx + row) >> 31);
+    const unsigned long long p = atomicAdd(cnt + c, 1ull);
+    perm[c * stride + (int64_t)p] = (int32_t)row;
   }
 }
 
@@ -439,7 +505,7 @@ static cudaError_t launch_terms_w(const SearchArgs& args, int64_t rows, size_t s
   int occ = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kSearchThreads, smem);
   if (occ < 1) occ = 1;
-  const int64_t batches = (rows + R - 1) / R;
+  const int64_t batches = nb_max(rows);
   const int64_t need = (batches + kSearchWarps - 1) / kSearchWarps;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * occ));
   kern<<<blocks, kSearchThreads, smem, s>>>(args);
@@ -457,12 +523,13 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, const char
                                uint32_t* pj, uint32_t* pk, int mode, const PairScratch* sc,
                                cudaStream_t s) {
   if (ham->n_srch >= (int64_t(1) << 24) || ham->n_xy >= (int64_t(1) << 29)) return cudaErrorInvalidValue;
+  const int64_t rows = re - rb;
+  unsigned long long* counters = (unsigned long long*)(stage + L.off_counters);
   SearchArgs a;
   a.U = U;
   a.hx = (const uint32_t*)(stage + L.off_hx);
   a.table = (const unsigned long long*)(stage + L.off_table);
   a.capmask = L.cap - 1;
-  a.bloom_g = (const uint32_t*)(stage + L.off_bloom);
   a.wmask = (uint32_t)(L.nwords - 1);
   a.nwords = (int)L.nwords;
   a.srch_hash = ham->srch_hash;
@@ -476,82 +543,112 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, const char
   a.pair_j = pj;
   a.pair_k = pk;
   a.status = (int32_t*)(stage + offsetof(StageHeader, status));
-  a.batch_counter = (unsigned long long*)(stage + L.off_counters);
   if (sc) a.sc = *sc; else a.sc = PairScratch{0, nullptr, nullptr, nullptr, nullptr};
-  cudaError_t e = cudaMemsetAsync(a.batch_counter, 0, sizeof(unsigned long long), s);
+  a.perm = (const int32_t*)(stage + L.off_perm);
+  a.perm_stride = rows;
+  a.cls_cnt = counters + 2;
+  for (int t = 0; t < 2; ++t) { a.g_begin[t] = ham->half_begin[t]; a.g_end[t] = ham->half_end[t]; }
+  a.rowcur = (int64_t*)(stage + L.off_rowcur);
+  a.nbm = nb_max(rows);
+  cudaError_t e = cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
+  {
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 4 * num_sms()));
+    partition_rows_kernel<<<blocks, 256, 0, s>>>(a.hx, rb, re, (int32_t*)a.perm, rows, counters + 2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if (mode == kEmit) {
     e = cudaMemsetAsync(sc->cursor, 0, 2 * sizeof(int64_t), s);
     if (e != cudaSuccess) return e;
   }
-  const int64_t rows = re - rb;
+  for (int pass = 0; pass < 2; ++pass) {
+    a.pass = pass;
+    a.bloom_g = (const uint32_t*)(stage + L.off_bloom) + (int64_t)pass * L.nwords;
+    a.batch_counter = counters + pass;
 #define NQS_TERMS(WW)                                                                    \
   case WW: {                                                                             \
     const size_t smem = search_smem<WW>(L);                                              \
-    if (mode == kCount) return launch_terms_w<WW, kCount>(a, rows, smem, s);             \
-    if (mode == kFill) return launch_terms_w<WW, kFill>(a, rows, smem, s);               \
-    return launch_terms_w<WW, kEmit>(a, rows, smem, s);                                  \
+    if (mode == kCount) e = launch_terms_w<WW, kCount>(a, rows, smem, s);                \
+    else if (mode == kFill) e = launch_terms_w<WW, kFill>(a, rows, smem, s);             \
+    else e = launch_terms_w<WW, kEmit>(a, rows, smem, s);                                \
+    break;                                                                               \
   }
-  switch (ham->W) {
-    NQS_TERMS(1)
-    NQS_TERMS(2)
-    NQS_TERMS(3)
-    default:
-    NQS_TERMS(4)
-  }
+    switch (ham->W) {
+      NQS_TERMS(1)
+      NQS_TERMS(2)
+      NQS_TERMS(3)
+      default:
+      NQS_TERMS(4)
+    }
 #undef NQS_TERMS
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // --------------------------------------------------------------------------
 // compaction of the one-pass records into CSR order (one warp per row batch)
 // --------------------------------------------------------------------------
 __global__ void pairs_compact_kernel(PairScratch sc, int64_t rows, const int64_t* __restrict__ rp,
-                                     uint32_t* __restrict__ pair_j, uint32_t* __restrict__ pair_k) {
+                                     const int32_t* __restrict__ perm, const unsigned long long* __restrict__ cls_cnt,
+                                     int64_t rb, int64_t nbm, uint32_t* __restrict__ pair_j,
+                                     uint32_t* __restrict__ pair_k) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
-  const int64_t n_batches = (rows + R - 1) / R;
+  const int64_t cnt0 = (int64_t)cls_cnt[0], cnt1 = (int64_t)cls_cnt[1];
+  const int64_t nb0 = (cnt0 + R - 1) / R;
+  const int64_t n_batches = nb0 + (cnt1 + R - 1) / R;
   const int64_t tw = (int64_t)gridDim.x * (blockDim.x / 32);
   const int64_t p0 = rp[0];
   for (int64_t bt = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); bt < n_batches; bt += tw) {
-    const int64_t l0 = bt * R;
-    const int64_t l1 = (l0 + R < rows) ? l0 + R : rows;
+    const int cls = bt < nb0 ? 0 : 1;
+    const int64_t b0 = (cls ? bt - nb0 : bt) * R;
+    const int64_t ccount = cls ? cnt1 : cnt0;
     int64_t base[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) base[r] = (l0 + r < rows) ? rp[l0 + r] - p0 : 0;
-    const int64_t total = rp[l1] - rp[l0];
-    int64_t consumed = 0;
-    int32_t c = sc.heads[bt];
-    while (consumed < total && c >= 0) {
-      const int n_here = (int)((total - consumed < kChunk) ? total - consumed : kChunk);
-      for (int e0 = 0; e0 < n_here; e0 += 32) {
-        const int e = e0 + lane;
-        const bool v = e < n_here;
-        const uint64_t rec = v ? sc.records[(int64_t)c * kChunk + e] : 0ull;
-        const int r = (int)(rec >> 61);
-        const uint32_t j = (uint32_t)rec;
-        const uint32_t k = (uint32_t)(rec >> 32) & 0x1FFFFFFFu;
+    for (int r = 0; r < R; ++r) {
+      const bool valid = b0 + r < ccount;
+      base[r] = valid ? rp[perm[cls * rows + b0 + r] - rb] - p0 : 0;
+    }
+    for (int pass = 0; pass < 2; ++pass) {  // a row's pass-0 pairs precede its pass-1 pairs
+      const int64_t total = sc.heads[(2 + pass) * nbm + bt];
+      int64_t consumed = 0;
+      int32_t c = sc.heads[pass * nbm + bt];
+      while (consumed < total && c >= 0) {
+        const int n_here = (int)((total - consumed < kChunk) ? total - consumed : kChunk);
+        for (int e0 = 0; e0 < n_here; e0 += 32) {
+          const int e = e0 + lane;
+          const bool v = e < n_here;
+          const uint64_t rec = v ? sc.records[(int64_t)c * kChunk + e] : 0ull;
+          const int r = (int)(rec >> 61);
+          const uint32_t j = (uint32_t)rec;
+          const uint32_t k = (uint32_t)(rec >> 32) & 0x1FFFFFFFu;
 #pragma unroll
-        for (int rr = 0; rr < R; ++rr) {
-          const uint32_t m = __ballot_sync(kFull, v && r == rr);
-          if (v && r == rr) {
-            const int64_t p = base[rr] + __popc(m & lt);
-            pair_j[p] = j;
-            pair_k[p] = k;
+          for (int rr = 0; rr < R; ++rr) {
+            const uint32_t m = __ballot_sync(kFull, v && r == rr);
+            if (v && r == rr) {
+              const int64_t p = base[rr] + __popc(m & lt);
+              pair_j[p] = j;
+              pair_k[p] = k;
+            }
+            base[rr] += __popc(m);
           }
-          base[rr] += __popc(m);
         }
+        consumed += n_here;
+        c = sc.next[c];
       }
-      consumed += n_here;
-      c = sc.next[c];
     }
   }
 }
 
-cudaError_t launch_pairs_compact(const PairScratch& sc, int64_t rows, const int64_t* row_ptr,
-                                 uint32_t* pair_j, uint32_t* pair_k, cudaStream_t s) {
-  const int64_t batches = (rows + R - 1) / R;
+cudaError_t launch_pairs_compact(const PairScratch& sc, const char* stage, const StageHeader& L, int64_t rb,
+                                 int64_t rows, const int64_t* row_ptr, uint32_t* pair_j, uint32_t* pair_k,
+                                 cudaStream_t s) {
+  const int64_t batches = nb_max(rows);
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((batches + 7) / 8, (int64_t)num_sms() * 8));
-  pairs_compact_kernel<<<blocks, 256, 0, s>>>(sc, rows, row_ptr, pair_j, pair_k);
+  pairs_compact_kernel<<<blocks, 256, 0, s>>>(sc, rows, row_ptr, (const int32_t*)(stage + L.off_perm),
+                                              (const unsigned long long*)(stage + L.off_counters) + 2, rb,
+                                              nb_max(rows), pair_j, pair_k);
   return cudaGetLastError();
 }
 
@@ -662,7 +759,7 @@ __global__ void __launch_bounds__(kBatchThreads) pairs_batch_kernel(const BatchA
       if (valid) vmask |= 1u << (R - 1 - r);
       acc[r] = (MODE == kFill && valid) ? a.rp[row - a.row_begin] - pbase : 0;
     }
-    EmitState es{-1, 0, -1};
+    EmitState es{-1, 0, -1, 0};
     if (a.has_diag) {
       const bool d = lane < R && r0 + lane < a.row_end;
       emit_round<MODE, W>(d, lane, (uint32_t)(r0 + lane), 0u, acc, es, rc, a.emit);

@@ -37,6 +37,7 @@ struct nqs_ham_dev {
   int64_t heavy_end = 0;         // ids < heavy_end (and >= has_diag) are heavy
   int64_t max_group = 0;
   int64_t n_srch = 0;            // search-table slots, multiple of 32
+  int64_t half_begin[2] = {0, 0}, half_end[2] = {0, 0};  // groups of each half (top hash bit)
 
   uint64_t* xy = nullptr;        // [n_xy][W]
   uint32_t* row_ptr = nullptr;   // [n_xy + 1]
@@ -77,6 +78,7 @@ struct StageHeader {
   int32_t W;
   int32_t status;       // device status word (kStatus* bits)
   int64_t off_hx, off_table, off_bloom, off_scan, off_ampP, off_ampQ, off_ampK, off_geff, off_counters;
+  int64_t off_perm, off_rowcur;
   int64_t scan_blocks;
   int64_t total_bytes;
 };
@@ -103,7 +105,8 @@ enum SearchMode { kCount = 0, kFill = 1, kEmit = 2 };
 struct PairScratch {        // one-pass search scratch (caller memory)
   int64_t max_chunks;
   int64_t* cursor;          // [2]: next chunk, overflow flag
-  int32_t* heads;           // [n_batches] first chunk of each row batch (-1: none)
+  int32_t* heads;           // [2][nb_max] first chunk of each row batch and pass (-1: none), then
+                            // [2][nb_max] number of records of each row batch and pass
   int32_t* next;            // [max_chunks]
   uint64_t* records;        // [max_chunks * kChunk]: j | k << 32 | r << 61
 };
@@ -115,8 +118,9 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, const char
                                int64_t* counts_or_rowptr, uint32_t* pair_j, uint32_t* pair_k,
                                int mode, const PairScratch* scratch, cudaStream_t s);
 
-cudaError_t launch_pairs_compact(const PairScratch& sc, int64_t rows, const int64_t* row_ptr,
-                                 uint32_t* pair_j, uint32_t* pair_k, cudaStream_t s);
+cudaError_t launch_pairs_compact(const PairScratch& sc, const char* stage, const StageHeader& L, int64_t rb,
+                                 int64_t rows, const int64_t* row_ptr, uint32_t* pair_j, uint32_t* pair_k,
+                                 cudaStream_t s);
 
 cudaError_t launch_pairs_batch(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, const char* stage,
                                const StageHeader& L, int64_t row_begin, int64_t row_end,

@@ -254,6 +254,51 @@ int nqs_local_energy_backward(const nqs_ham* ham, const uint64_t* U, int64_t n_u
                               double* grad_re, double* grad_im, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched instances: many independent (Hamiltonian, sample batch) problems
+ * of uneven size evaluated by one CUDA-graph launch (forward path: staging,
+ * FindCoupledPairs, E_loc^var, E^var for every instance).  The paper runs one
+ * instance at a time; its schedule comparison (Sec. "FindCoupledPairs
+ * implementations", LoopOverTerms vs LoopOverBatch) motivates choosing the
+ * schedule per instance.
+ * ------------------------------------------------------------------------- */
+typedef struct nqs_plan nqs_plan;
+
+typedef struct {
+    const nqs_ham* ham;       /* loaded Hamiltonian (its device)                    */
+    const uint64_t* U;        /* device [n_unq][W]; contents may change between runs */
+    int64_t n_unq;            /* fixed for the plan's lifetime                        */
+    const double* logpsi_re;  /* device [n_unq] (real amplitudes)                    */
+    double* eloc_re;          /* device [n_unq] output E_loc^var                      */
+    double* evar;             /* device [3] output as nqs_variational_energy          */
+} nqs_instance;
+
+/* Plan n_inst instances (arrays are read during the call; the pointers inside
+ * must stay valid for the plan's lifetime).  Planning stages every instance,
+ * counts its pairs, picks its schedule (flags bit 0: time LoopOverTerms and
+ * LoopOverBatch and keep the faster; otherwise the cost model of
+ * NQS_SCHED_AUTO), allocates its buffers with 25% headroom over the planned
+ * pair count, and captures all instances into one CUDA graph on forked
+ * streams.  Synchronises `stream`.  The plan owns its device memory. */
+int nqs_batch_plan(const nqs_instance* instances, int n_inst, int precision, int flags,
+                   nqs_plan** out, void* stream);
+
+/* One graph launch evaluating every instance: no host synchronisation, no
+ * allocation.  If new sample contents need more pairs than planned, that
+ * instance's outputs are left unwritten and nqs_batch_status reports it. */
+int nqs_batch_run(nqs_plan* plan, void* stream);
+
+/* Synchronise and return NQS_OK or the first instance's error
+ * (NQS_ERR_CAPACITY when its pairs outgrew the planned buffers; re-plan). */
+int nqs_batch_status(const nqs_plan* plan, int* failed_instance, void* stream);
+
+/* info[0] schedule, [1] pair capacity, [2] planned pairs, [3] graph nodes,
+ * [4] LoopOverTerms count time (us), [5] LoopOverBatch count time (us, -1 if
+ * not timed) of instance i. */
+int nqs_batch_info(const nqs_plan* plan, int i, int64_t info[6]);
+
+int nqs_batch_free(nqs_plan* plan);
+
+/* ---------------------------------------------------------------------------
  * Misc
  * ------------------------------------------------------------------------- */
 const char* nqs_last_error(void);   /* thread-local message of the last error */

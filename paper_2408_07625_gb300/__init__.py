@@ -19,7 +19,7 @@ import torch
 
 __all__ = ["NQSError", "load_library", "Hamiltonian", "Batch", "coupled_pairs",
            "local_energy", "variational_energy", "local_energy_backward", "LocalEnergy",
-           "evaluate", "SCHEDULES", "PRECISIONS", "library_path"]
+           "evaluate", "BatchedPlan", "SCHEDULES", "PRECISIONS", "library_path"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "libnqs.so")
@@ -70,6 +70,11 @@ def load_library(path: str = None):
         "nqs_variational_energy": (_i32, [_i64, _vp, _vp, _vp, _vp, _vp]),
         "nqs_local_energy_backward": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp,
                                              _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp]),
+        "nqs_batch_plan": (_i32, [_vp, _i32, _i32, _i32, ctypes.POINTER(_vp), _vp]),
+        "nqs_batch_run": (_i32, [_vp, _vp]),
+        "nqs_batch_status": (_i32, [_vp, ctypes.POINTER(_i32), _vp]),
+        "nqs_batch_info": (_i32, [_vp, _i32, _c_i64p]),
+        "nqs_batch_free": (_i32, [_vp]),
         "nqs_last_error": (ctypes.c_char_p, []),
         "nqs_version": (_i32, []),
     }
@@ -448,3 +453,60 @@ class LocalEnergy(torch.autograd.Function):
                                       res["evar"], g_er, g_ei, g_e, (rp, pj, pk), ctx.precision,
                                       r0, r1, (gr, gi))
         return None, gr, gi, None, None
+
+
+class _Instance(ctypes.Structure):
+    _fields_ = [("ham", ctypes.c_void_p), ("U", ctypes.c_void_p), ("n_unq", ctypes.c_int64),
+                ("logpsi_re", ctypes.c_void_p), ("eloc_re", ctypes.c_void_p), ("evar", ctypes.c_void_p)]
+
+
+class BatchedPlan:
+    """Many independent (Hamiltonian, batch) instances evaluated by one CUDA-graph launch.
+
+    ``items``: list of (Hamiltonian, U, logpsi_re).  ``U`` and ``logpsi_re``
+    are kept as device tensors whose contents may be overwritten between
+    runs (same sizes).  ``run()`` launches the graph asynchronously; results
+    are ``eloc[i]`` (E_loc^var) and ``evar[i]`` ([E^var, max log psi, sum of
+    weights]).  ``autotune`` times both pair-search schedules per instance
+    at planning time.
+    """
+
+    def __init__(self, items, precision="fp32c", autotune=True, stream=None):
+        lib = load_library()
+        self.hams, self.U, self.logpsi, self.eloc, self.evar = [], [], [], [], []
+        arr = (_Instance * len(items))()
+        for i, (ham, U, lre) in enumerate(items):
+            Ud = _dev_u64(U)
+            if Ud.shape[1] != ham.n_words:
+                raise ValueError(f"instance {i}: word count does not match its Hamiltonian")
+            a = _f64(lre, Ud.device)
+            er = torch.zeros(Ud.shape[0], dtype=torch.float64, device=Ud.device)
+            ev = torch.zeros(3, dtype=torch.float64, device=Ud.device)
+            self.hams.append(ham); self.U.append(Ud); self.logpsi.append(a)
+            self.eloc.append(er); self.evar.append(ev)
+            arr[i] = _Instance(ham.handle.value, Ud.data_ptr(), Ud.shape[0], a.data_ptr(), er.data_ptr(),
+                               ev.data_ptr())
+        h = ctypes.c_void_p()
+        _check(lib.nqs_batch_plan(arr, len(items), PRECISIONS[precision], 1 if autotune else 0,
+                                  ctypes.byref(h), _stream(stream)))
+        self._h = h
+
+    def run(self, stream=None):
+        _check(_lib.nqs_batch_run(self._h, _stream(stream)))
+
+    def status(self, stream=None):
+        bad = ctypes.c_int()
+        rc = _lib.nqs_batch_status(self._h, ctypes.byref(bad), _stream(stream))
+        return rc, int(bad.value)
+
+    def info(self, i):
+        v = (ctypes.c_int64 * 6)()
+        _check(_lib.nqs_batch_info(self._h, int(i), v))
+        sched = {v2: k for k, v2 in SCHEDULES.items()}[int(v[0])]
+        return {"schedule": sched, "capacity": v[1], "planned_pairs": v[2], "graph_nodes": v[3],
+                "t_terms_us": v[4], "t_batch_us": v[5]}
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.nqs_batch_free(self._h)
+            self._h = None

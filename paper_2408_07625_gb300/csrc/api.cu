@@ -359,6 +359,7 @@ static int status_to_code(int st) {
   if (st & kStatusBadBits) return fail(NQS_ERR_ARG, "a sample has bits >= n_qubits");
   if (st & kStatusLimit) return fail(NQS_ERR_DEVICE_LIMIT, "a bounded device loop ran out");
   if (st & kStatusRange) return fail(NQS_ERR_RANGE, "an amplitude ratio leaves the FP32 range");
+  if (st & kStatusCapacity) return fail(NQS_ERR_CAPACITY, "a pair buffer sized at planning time was too small");
   return NQS_OK;
 }
 
@@ -515,7 +516,7 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
   if (*n_pairs > capacity) return fail(NQS_ERR_CAPACITY, "pair capacity too small");
   if (rows == 0 || *n_pairs == 0) return NQS_OK;
   if (!pair_j || !pair_k) return fail(NQS_ERR_ARG, "null pair arrays");
-  e = launch_pairs_compact(sc, (const char*)work, L, rb, rows, row_ptr, pair_j, pair_k, s);
+  e = launch_pairs_compact(sc, (const char*)work, L, rb, rows, row_ptr, pair_j, pair_k, capacity, s);
   if (e != cudaSuccess) return cuda_fail(e, "compaction kernel");
   return NQS_OK;
 }

@@ -165,6 +165,7 @@ local_energy_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict__
                     double* __restrict__ eloc_im, double* __restrict__ hdiag,
                     int32_t* __restrict__ status) {
   using T = typename Pol::T;
+  if (*(volatile int32_t*)status & kStatusCapacity) return;  // the pair list was not written
   const int lane = threadIdx.x & 31;
   const int64_t tw = (int64_t)gridDim.x * kEnergyWarps;
   for (int64_t row = (int64_t)blockIdx.x * kEnergyWarps + (threadIdx.x >> 5); row < row_end - row_begin;
@@ -459,6 +460,7 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict
                       const double* __restrict__ g_im, const double* __restrict__ g_evar,
                       double* __restrict__ gre, double* __restrict__ gim, int32_t* __restrict__ status) {
   using T = typename Pol::T;
+  if (*(volatile int32_t*)status & kStatusCapacity) return;  // the pair list was not written
   const int lane = threadIdx.x & 31;
   const int64_t tw = (int64_t)gridDim.x * kEnergyWarps;
   const double gE = g_evar ? g_evar[0] : 0.0;

@@ -372,6 +372,7 @@ __device__ __forceinline__ void flush_queue(const uint32_t* q, int qn, uint32_t*
 
 template <int W, int MODE>
 __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const SearchArgs a) {
+  if (MODE == kFill && (*(volatile int32_t*)a.status & kStatusCapacity)) return;  // buffers too small
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* bloom = smem;
   RowCache<W>* caches = reinterpret_cast<RowCache<W>*>(smem + a.nwords);
@@ -592,7 +593,12 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, const char
 __global__ void pairs_compact_kernel(PairScratch sc, int64_t rows, const int64_t* __restrict__ rp,
                                      const int32_t* __restrict__ perm, const unsigned long long* __restrict__ cls_cnt,
                                      int64_t rb, int64_t nbm, uint32_t* __restrict__ pair_j,
-                                     uint32_t* __restrict__ pair_k) {
+                                     uint32_t* __restrict__ pair_k, int64_t capacity, int32_t* status) {
+  // buffers sized ahead of time (graph replay) may be too small: report, write nothing
+  if (rp[rows] - rp[0] > capacity || sc.cursor[1] != 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusCapacity);
+    return;
+  }
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   const int64_t cnt0 = (int64_t)cls_cnt[0], cnt1 = (int64_t)cls_cnt[1];
@@ -643,12 +649,13 @@ __global__ void pairs_compact_kernel(PairScratch sc, int64_t rows, const int64_t
 
 cudaError_t launch_pairs_compact(const PairScratch& sc, const char* stage, const StageHeader& L, int64_t rb,
                                  int64_t rows, const int64_t* row_ptr, uint32_t* pair_j, uint32_t* pair_k,
-                                 cudaStream_t s) {
+                                 int64_t capacity, cudaStream_t s) {
   const int64_t batches = nb_max(rows);
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((batches + 7) / 8, (int64_t)num_sms() * 8));
   pairs_compact_kernel<<<blocks, 256, 0, s>>>(sc, rows, row_ptr, (const int32_t*)(stage + L.off_perm),
                                               (const unsigned long long*)(stage + L.off_counters) + 2, rb,
-                                              nb_max(rows), pair_j, pair_k);
+                                              nb_max(rows), pair_j, pair_k, capacity,
+                                              (int32_t*)(stage + offsetof(StageHeader, status)));
   return cudaGetLastError();
 }
 
@@ -716,6 +723,7 @@ __device__ __forceinline__ void batch_verify(const uint32_t* items, int n_items,
 
 template <int W, int MODE>
 __global__ void __launch_bounds__(kBatchThreads) pairs_batch_kernel(const BatchArgs a) {
+  if (MODE == kFill && (*(volatile int32_t*)a.status & kStatusCapacity)) return;  // buffers too small
   __shared__ RowCache<W> caches[kBatchWarps];
   __shared__ uint32_t queue[kBatchWarps][kQueueCap];
   __shared__ uint32_t xbufs[kBatchWarps][kXbufCap];

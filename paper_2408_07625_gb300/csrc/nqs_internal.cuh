@@ -22,6 +22,7 @@ constexpr int kStatusDuplicate = 1;
 constexpr int kStatusBadBits = 2;
 constexpr int kStatusLimit = 4;
 constexpr int kStatusRange = 8;
+constexpr int kStatusCapacity = 16;        // a pair buffer sized ahead of time was too small
 
 // ---------------------------------------------------------------------------
 // Hamiltonian tables (device) -- Fig. ham_prep, regrouped:
@@ -120,7 +121,7 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, const char
 
 cudaError_t launch_pairs_compact(const PairScratch& sc, const char* stage, const StageHeader& L, int64_t rb,
                                  int64_t rows, const int64_t* row_ptr, uint32_t* pair_j, uint32_t* pair_k,
-                                 cudaStream_t s);
+                                 int64_t capacity, cudaStream_t s);
 
 cudaError_t launch_pairs_batch(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, const char* stage,
                                const StageHeader& L, int64_t row_begin, int64_t row_end,

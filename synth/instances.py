@@ -114,15 +114,30 @@ def config_instance(name: str, n_unq: int = None, use_cache: bool = True,
 
 def batched_instances(n_inst: int = 64, seed: int = 5000):
     """Uneven instances: N uniform in {20,28,36,44,56}, n_alpha = n_beta =
-    ceil(N/8), |U| = round(10^U(3,5)) capped by the sector's size."""
+    ceil(N/8), |U| = round(10^U(3,5)) capped at half the sector's size.
+
+    Returns a list of Instance.  Instances of the same N share that N's
+    Hamiltonian (integrals seed 1000+N); every instance has its own peaked
+    batch (samples seed 6000+t) and log-amplitudes (seed 7000+t).
+    """
     rng = np.random.default_rng(seed)
+    hams = {}
     out = []
     for t in range(n_inst):
         N = int(rng.choice([20, 28, 36, 44, 56]))
         n_orb = N // 2
         ne = math.ceil(N / 8)
-        n_unq = int(round(10 ** rng.uniform(3, 5)))
-        out.append((N, n_orb, ne, n_unq, 6000 + t))
+        sector = math.comb(n_orb, ne) ** 2
+        n_unq = min(int(round(10 ** rng.uniform(3, 5))), sector // 2)
+        if N not in hams:
+            x, z, c, _, _, _ = _hamiltonian(n_orb, 2, 1000 + N)
+            hams[N] = (x, z, c)
+        x, z, c = hams[N]
+        vals, ranks = peaked_samples(n_orb, ne, ne, n_unq, 6000 + t)
+        rng_l = np.random.default_rng(7000 + t)
+        lre = -2.0 * ranks + rng_l.normal(0.0, 0.3, size=len(vals))
+        out.append(Instance(f"b{t}_N{N}", N, ne, ne, x, z, c, pack_ints(vals, N), ranks, lre,
+                            np.zeros_like(lre), {"n_orb": n_orb, "batched": True}))
     return out
 
 

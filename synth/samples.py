@@ -59,9 +59,9 @@ def rank_quotas(n_orb, n_a, n_b, n_unq, k_max=6, decay=0.1):
 def _det_int(occ_a, occ_b):
     v = 0
     for p in occ_a:
-        v |= 1 << (2 * p)
+        v |= 1 << (2 * int(p))
     for p in occ_b:
-        v |= 1 << (2 * p + 1)
+        v |= 1 << (2 * int(p) + 1)
     return v
 
 

@@ -1,0 +1,103 @@
+"""Batched instances of uneven size in one CUDA-graph launch (GPU).
+
+Every instance's E_loc^var and E^var from the graph must equal the
+single-instance path (bitwise when both use LoopOverTerms, to rounding when
+the plan picked LoopOverBatch) and the oracle on the small instances; a run
+after new sample contents must reflect them; outgrown buffers are reported.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import config_instance, batched_instances, unpack_ints, pack_ints
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_2408_07625_gb300 as nqs
+    from gpu_helpers import to_dev_u, oracle_for
+
+
+def _items(insts):
+    hams = {}
+    items = []
+    for inst in insts:
+        key = id(inst.coef)
+        if key not in hams:
+            hams[key] = nqs.Hamiltonian.from_instance(inst)
+        items.append((hams[key], to_dev_u(inst.U), torch.from_numpy(inst.logpsi_re).cuda()))
+    return items
+
+
+@pytest.fixture(scope="module")
+def small_batch():
+    insts = [config_instance("h12", use_cache=False), config_instance("h28", n_unq=1500, use_cache=False),
+             config_instance("h28", n_unq=300, use_cache=False)]
+    insts += [b for b in batched_instances(6, seed=77) if b.n_unq <= 3000][:3]
+    return insts
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_graph_matches_single_instance_and_oracle(small_batch, precision):
+    items = _items(small_batch)
+    plan = nqs.BatchedPlan(items, precision=precision, autotune=True)
+    plan.run()
+    torch.cuda.synchronize()
+    assert plan.status() == (0, -1)
+    tol = 1e-9 if precision == "fp64" else 1e-6
+    for i, (inst, (ham, U, lre)) in enumerate(zip(small_batch, items)):
+        info = plan.info(i)
+        batch = nqs.Batch(ham, U)
+        ref = nqs.evaluate(batch, lre, None, precision, schedule=info["schedule"])
+        if info["schedule"] == "terms":
+            assert torch.equal(plan.eloc[i], ref["eloc_re"])
+        else:
+            assert (plan.eloc[i] - ref["eloc_re"]).abs().max().item() < tol
+        assert abs(plan.evar[i][0].item() - ref["evar"][0].item()) < tol
+        if inst.n_unq <= 400:
+            ref_ham = oracle_for(inst)
+            res = oracle.forward(inst.U, inst.logpsi_re, None, ref_ham)
+            want = np.array([e.real for e in res["eloc"]])
+            assert np.abs(plan.eloc[i].cpu().numpy() - want).max() < tol
+    # replay twice: same results
+    first = [e.clone() for e in plan.eloc]
+    plan.run(); plan.run()
+    torch.cuda.synchronize()
+    for a, b in zip(first, plan.eloc):
+        assert torch.equal(a, b)
+
+
+def test_graph_sees_new_sample_contents(small_batch):
+    items = _items(small_batch[:2])
+    plan = nqs.BatchedPlan(items, precision="fp64", autotune=False)
+    # permute the rows of instance 1 in place: E_loc must follow the permutation
+    U, lre = items[1][1], items[1][2]
+    perm = torch.randperm(U.shape[0], generator=torch.Generator().manual_seed(3)).cuda()
+    plan.run(); torch.cuda.synchronize()
+    before = plan.eloc[1].clone()
+    U.copy_(U[perm]); lre.copy_(lre[perm])
+    plan.run(); torch.cuda.synchronize()
+    assert plan.status() == (0, -1)
+    assert torch.allclose(plan.eloc[1], before[perm], rtol=0, atol=1e-9)
+
+
+def test_graph_reports_outgrown_buffers():
+    inst = config_instance("h28", n_unq=1500, use_cache=False)
+    ham = nqs.Hamiltonian.from_instance(inst)
+    # plan on a sparse batch (the 1500 highest-rank samples couple little) ...
+    order = np.argsort(-inst.ranks, kind="stable")
+    big = config_instance("h28", n_unq=6000, use_cache=False)
+    sparse = big.U[np.argsort(-big.ranks, kind="stable")[:1500]]
+    U = to_dev_u(sparse)
+    lre = torch.zeros(1500, dtype=torch.float64, device="cuda")
+    plan = nqs.BatchedPlan([(ham, U, lre)], precision="fp64", autotune=False)
+    plan.run(); torch.cuda.synchronize()
+    assert plan.status() == (0, -1)
+    # ... then run it on a dense one (the lowest ranks couple strongly)
+    dense = big.U[np.argsort(big.ranks, kind="stable")[:1500]]
+    U.copy_(to_dev_u(dense))
+    plan.run(); torch.cuda.synchronize()
+    rc, bad = plan.status()
+    assert rc == -4 and bad == 0

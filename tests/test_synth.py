@@ -51,3 +51,12 @@ def test_term_counts_track_the_configs():
     assert 1.2e4 < inst.n_terms < 1.8e4  # config: ~1.5e4 Pauli terms
     assert np.all(np.bitwise_count(inst.x_mask).sum(axis=1) <= 4)
     assert len(np.unique(np.concatenate([inst.x_mask, inst.z_mask], axis=1), axis=0)) == inst.n_terms
+
+
+def test_samples_beyond_64_qubits():
+    from synth.samples import peaked_samples
+    vals, ranks = peaked_samples(42, 10, 10, 3000, 7)
+    assert all(v > 0 and v < (1 << 84) for v in vals)
+    even = int("01" * 42, 2)
+    assert all(bin(v & even).count("1") == 10 and bin(v & ~even).count("1") == 10 for v in vals)
+    assert any(v >> 64 for v in vals)

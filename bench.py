@@ -44,11 +44,11 @@ def _dist():
     return ws, rank, local
 
 
-def _workload_config(inst, ham_info, n_pairs=None):
+def _workload_config(inst, ham_info, n_pairs=None, schedule="terms", precision="fp32c"):
     cfg = {"workload": f"{inst.name}: {inst.n_qubits} qubits, {inst.n_alpha + inst.n_beta} electrons, "
                        f"{inst.n_terms} Pauli terms, {inst.n_unq} peaked unique samples",
            "n_qubits": inst.n_qubits, "n_terms": int(ham_info["n_terms"]), "n_xy": int(ham_info["n_xy"]),
-           "n_unq": inst.n_unq, "schedule": "terms", "precision": "fp32c",
+           "n_unq": inst.n_unq, "schedule": schedule, "precision": precision,
            "l2": "flushed between timed steps (512 MiB write); inputs are smaller than L2"}
     if n_pairs is not None:
         cfg["n_pairs"] = int(n_pairs)
@@ -204,7 +204,7 @@ def run_ours(args):
         mark()
         batch_obj.restage(Udev)
         mark()
-        rp, pj, pk = nqs.coupled_pairs(batch_obj, reuse=True)
+        rp, pj, pk = nqs.coupled_pairs(batch_obj, schedule=args.schedule, reuse=True)
         total = int(pj.numel())
         mark()
         er, ei, hd = nqs.local_energy(batch_obj, adev, None, (rp, pj, pk), prec)
@@ -286,8 +286,8 @@ def run_ours(args):
         return
 
     # FP32C vs FP64 (untimed)
-    r64 = nqs.evaluate(batch, a, None, "fp64")
-    r32 = nqs.evaluate(batch, a, None, "fp32c")
+    r64 = nqs.evaluate(batch, a, None, "fp64", schedule=args.schedule)
+    r32 = nqs.evaluate(batch, a, None, "fp32c", schedule=args.schedule)
     err = {"max_abs_dE_loc": float((r64["eloc_re"] - r32["eloc_re"]).abs().max().item()),
            "abs_dE_var": abs(float(r64["evar"][0].item()) - float(r32["evar"][0].item())),
            "E_var_fp64": float(r64["evar"][0].item())}
@@ -308,7 +308,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64+f32c (FP32 compensated, FP64 reduction)",
             "data": "synthetic (seeded integrals, JW, peaked samples)",
-            "config": _workload_config(inst, info, total_pairs),
+            "config": _workload_config(inst, info, total_pairs, args.schedule, prec),
             "pairs_per_s": total_pairs / (phases["pairs"] * 1e-3),
             "phases_ms": phases, "precision_error": err,
             "roofline": roof,
@@ -333,6 +333,7 @@ def main():
     p.add_argument("--workload", default="h56")
     p.add_argument("--n-unq", type=int, default=None, help="smaller peaked batch of the same Hamiltonian")
     p.add_argument("--precision", default="fp32c", choices=["fp32c", "fp64"])
+    p.add_argument("--schedule", default="terms", choices=["terms", "batch", "trie"])
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ref-rows", type=int, default=40)

@@ -128,6 +128,18 @@ int64_t nqs_stage_bytes(const nqs_ham* ham, int64_t n_unq);
 int nqs_stage(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, void* work,
               int64_t work_bytes, int check, void* stream);
 
+/* Build the prefix tree of U (Alg. 3, Sec. "Prefix tree construction") in
+ * the workspace of an nqs_stage call with the same U, for searches with
+ * NQS_SCHED_TRIE.  Levels follow the qubit index; the tree is stored as U
+ * sorted in qubit order with, per position, the levels where the run it
+ * starts branches (see the implementation notes).  Needs n_qubits <= 255 and
+ * n_unq < 2^23 (NQS_ERR_UNSUPPORTED otherwise).  Every nqs_stage call
+ * invalidates the tree; a trie search on a workspace without one records
+ * an error that the search call (or nqs_stage_status) returns as
+ * NQS_ERR_ARG.  Asynchronous. */
+int nqs_stage_trie(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, void* work,
+                   void* stream);
+
 /* Synchronise the stream and return the workspace's status: NQS_OK or the
  * first of NQS_ERR_DUPLICATE, NQS_ERR_ARG (bits >= N), NQS_ERR_DEVICE_LIMIT,
  * NQS_ERR_RANGE recorded by device code since nqs_stage. */
@@ -139,10 +151,11 @@ int nqs_stage_status(const void* work, void* stream);
  *   row_ptr[r - row_begin] .. row_ptr[r - row_begin + 1] - 1 index the pairs
  *   of row r; pair_j = column (index into U), pair_k = pattern index (into
  *   the library's unique-XY table).  Within a row the diagonal pair comes
- *   first (if the XY = 0 pattern exists), then pairs whose P_XY is large,
- *   then the rest, in a fixed order that depends neither on the row range
- *   nor on the call (count, fill and one-pass calls agree).  Both (i, j)
- *   and (j, i) are listed.
+ *   first (if the XY = 0 pattern exists), then the others in an order fixed
+ *   by the schedule and the row alone: it depends neither on the row range
+ *   nor on the call (count, fill and one-pass calls agree).  LoopOverTerms
+ *   lists pairs whose P_XY is large before the rest.  Both (i, j) and (j, i)
+ *   are listed.  NQS_SCHED_TRIE needs nqs_stage_trie after nqs_stage.
  * All calls need a workspace staged with the same U.  Readers of the CSR
  * (fill, energy, adjoint) take positions relative to row_ptr[0], so a slice
  * row_ptr + (r0 - row_begin) of a larger offset array can be passed for the
@@ -274,9 +287,9 @@ typedef struct {
 
 /* Plan n_inst instances (arrays are read during the call; the pointers inside
  * must stay valid for the plan's lifetime).  Planning stages every instance,
- * counts its pairs, picks its schedule (flags bit 0: time LoopOverTerms and
- * LoopOverBatch and keep the faster; otherwise the cost model of
- * NQS_SCHED_AUTO), allocates its buffers with 25% headroom over the planned
+ * counts its pairs, picks its schedule (flags bit 0: time the count pass of
+ * LoopOverTerms, LoopOverBatch and LoopOverTrie (with its prefix-tree build)
+ * and keep the fastest; otherwise the cost model of NQS_SCHED_AUTO), allocates its buffers with 25% headroom over the planned
  * pair count, and captures all instances into one CUDA graph on forked
  * streams.  Synchronises `stream`.  The plan owns its device memory. */
 int nqs_batch_plan(const nqs_instance* instances, int n_inst, int precision, int flags,
@@ -292,9 +305,10 @@ int nqs_batch_run(nqs_plan* plan, void* stream);
 int nqs_batch_status(const nqs_plan* plan, int* failed_instance, void* stream);
 
 /* info[0] schedule, [1] pair capacity, [2] planned pairs, [3] graph nodes,
- * [4] LoopOverTerms count time (us), [5] LoopOverBatch count time (us, -1 if
- * not timed) of instance i. */
-int nqs_batch_info(const nqs_plan* plan, int i, int64_t info[6]);
+ * [4] LoopOverTerms count time (us), [5] LoopOverBatch count time (us),
+ * [6] LoopOverTrie tree build + count time (us) of instance i (-1: not
+ * timed). */
+int nqs_batch_info(const nqs_plan* plan, int i, int64_t info[7]);
 
 int nqs_batch_free(nqs_plan* plan);
 

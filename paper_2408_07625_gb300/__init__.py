@@ -60,6 +60,7 @@ def load_library(path: str = None):
         "nqs_stage_bytes": (_i64, [_vp, _i64]),
         "nqs_stage": (_i32, [_vp, _vp, _i64, _vp, _i64, _i32, _vp]),
         "nqs_stage_status": (_i32, [_vp, _vp]),
+        "nqs_stage_trie": (_i32, [_vp, _vp, _i64, _vp, _vp]),
         "nqs_count_coupled_pairs": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _vp, _c_i64p, _vp]),
         "nqs_fill_coupled_pairs": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _vp, _vp, _vp, _vp]),
         "nqs_find_coupled_pairs": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _vp, _i64, _vp, _vp, _vp,
@@ -208,6 +209,7 @@ class Batch:
         self._scratch = None          # one-pass search scratch, grown on demand
         self._pair_buf = None         # (pair_j, pair_k) buffers reused between calls
         self._pair_guess = None
+        self._trie = False            # prefix tree of U built since the last staging
         _check(_lib.nqs_stage(ham.handle, _ptr(self.U), self.n, _ptr(self.work), nbytes,
                               1 if check else 0, _stream(stream)))
 
@@ -220,6 +222,13 @@ class Batch:
             self.U = U
         _check(_lib.nqs_stage(self.ham.handle, _ptr(self.U), self.n, _ptr(self.work), self.work.numel(),
                               1 if check else 0, _stream(stream)))
+        self._trie = False
+
+    def prefix_tree(self, stream=None):
+        """Build the prefix tree of U (Alg. 3) for the trie schedule, once per staging."""
+        if not self._trie:
+            _check(_lib.nqs_stage_trie(self.ham.handle, _ptr(self.U), self.n, _ptr(self.work), _stream(stream)))
+            self._trie = True
 
     def status(self, stream=None):
         _check(_lib.nqs_stage_status(_ptr(self.work), _stream(stream)))
@@ -227,6 +236,8 @@ class Batch:
 
 def count_pairs(batch: Batch, row_begin=0, row_end=None, schedule="terms", stream=None):
     row_end = batch.n if row_end is None else int(row_end)
+    if schedule == "trie":
+        batch.prefix_tree(stream)
     row_ptr = torch.empty(row_end - row_begin + 1, dtype=torch.int64, device=batch.device)
     n = ctypes.c_int64()
     _check(_lib.nqs_count_coupled_pairs(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work),
@@ -237,6 +248,8 @@ def count_pairs(batch: Batch, row_begin=0, row_end=None, schedule="terms", strea
 
 def fill_pairs(batch: Batch, row_ptr, n_pairs, row_begin=0, row_end=None, schedule="terms", stream=None):
     row_end = batch.n if row_end is None else int(row_end)
+    if schedule == "trie":
+        batch.prefix_tree(stream)
     pj = torch.empty(max(n_pairs, 1), dtype=torch.int32, device=batch.device)
     pk = torch.empty(max(n_pairs, 1), dtype=torch.int32, device=batch.device)
     _check(_lib.nqs_fill_coupled_pairs(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work),
@@ -266,6 +279,8 @@ def coupled_pairs(batch: Batch, row_begin=0, row_end=None, schedule="terms", one
     """
     row_end = batch.n if row_end is None else int(row_end)
     rows = row_end - int(row_begin)
+    if schedule == "trie":
+        batch.prefix_tree(stream)
     if not one_pass:
         row_ptr, n = count_pairs(batch, row_begin, row_end, schedule, stream)
         pj, pk = fill_pairs(batch, row_ptr, n, row_begin, row_end, schedule, stream)
@@ -500,11 +515,11 @@ class BatchedPlan:
         return rc, int(bad.value)
 
     def info(self, i):
-        v = (ctypes.c_int64 * 6)()
+        v = (ctypes.c_int64 * 7)()
         _check(_lib.nqs_batch_info(self._h, int(i), v))
         sched = {v2: k for k, v2 in SCHEDULES.items()}[int(v[0])]
         return {"schedule": sched, "capacity": v[1], "planned_pairs": v[2], "graph_nodes": v[3],
-                "t_terms_us": v[4], "t_batch_us": v[5]}
+                "t_terms_us": v[4], "t_batch_us": v[5], "t_trie_us": v[6]}
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

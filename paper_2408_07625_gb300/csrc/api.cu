@@ -61,6 +61,7 @@ StageHeader stage_layout(const nqs_ham* ham, int64_t n) {
   L.off_counters = off; off = align256(off + 256);
   L.off_perm = off;   off = align256(off + 2 * 4 * std::max<int64_t>(n, 1));
   L.off_rowcur = off; off = align256(off + 8 * std::max<int64_t>(n, 1));
+  L.off_trie = off;   off = align256(off + trie_bytes(ham->W, n));
   L.total_bytes = off;
   return L;
 }
@@ -110,7 +111,7 @@ static void free_ham(nqs_ham* h) {
   if (!h) return;
   cudaFree(h->xy); cudaFree(h->row_ptr); cudaFree(h->yz); cudaFree(h->coef);
   cudaFree(h->coef_f); cudaFree(h->srch_hash); cudaFree(h->srch_id); cudaFree(h->srch_rec); cudaFree(h->hash_basis);
-  cudaFree(h->xy_table); cudaFree(h->wmask);
+  cudaFree(h->xy_table); cudaFree(h->wmask); cudaFree(h->xy_trie); cudaFree(h->xy_hash);
   delete h;
 }
 
@@ -314,13 +315,22 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
   std::vector<uint32_t> rp32(G + 1);
   for (int64_t p = 0; p <= G; ++p) rp32[p] = (uint32_t)h->h_row_ptr[p];
 
+  // prefix tree of the patterns for LoopOverTrie (Alg. 3)
+  std::vector<int32_t> xy_nodes;
+  build_xy_trie(h->h_xy, G, W, xy_nodes);
+  h->n_xy_nodes = (int64_t)xy_nodes.size() / 4;
+  std::vector<int4> xy_trie(h->n_xy_nodes);
+  for (int64_t v = 0; v < h->n_xy_nodes; ++v)
+    xy_trie[v] = make_int4(xy_nodes[4 * v], xy_nodes[4 * v + 1], xy_nodes[4 * v + 2], 0);
+
   int rc;
   if ((rc = upload(&h->xy, h->h_xy)) || (rc = upload(&h->row_ptr, rp32)) ||
       (rc = upload(&h->yz, h->h_yz)) || (rc = upload(&h->coef, h->h_coef)) ||
       (rc = upload(&h->coef_f, coef_f)) || (rc = upload(&h->srch_hash, srch_hash)) ||
       (rc = upload(&h->srch_id, srch_id)) || (rc = upload(&h->srch_rec, srch_rec)) ||
       (rc = upload(&h->hash_basis, h->h_hash_basis)) || (rc = upload(&h->xy_table, xy_table)) ||
-      (rc = upload(&h->wmask, wmask))) {
+      (rc = upload(&h->wmask, wmask)) || (rc = upload(&h->xy_trie, xy_trie)) ||
+      (rc = upload(&h->xy_hash, hxy))) {
     free_ham(h);
     return rc;
   }
@@ -360,6 +370,7 @@ static int status_to_code(int st) {
   if (st & kStatusLimit) return fail(NQS_ERR_DEVICE_LIMIT, "a bounded device loop ran out");
   if (st & kStatusRange) return fail(NQS_ERR_RANGE, "an amplitude ratio leaves the FP32 range");
   if (st & kStatusCapacity) return fail(NQS_ERR_CAPACITY, "a pair buffer sized at planning time was too small");
+  if (st & kStatusNoTrie) return fail(NQS_ERR_ARG, "trie schedule without nqs_stage_trie after nqs_stage");
   return NQS_OK;
 }
 
@@ -413,11 +424,24 @@ static int check_rows(int64_t n, int64_t rb, int64_t re) {
   return NQS_OK;
 }
 
-static int check_schedule(int schedule) {
+static int check_schedule(const nqs_ham* ham, int64_t n, int schedule) {
   if (schedule == NQS_SCHED_AUTO || schedule == NQS_SCHED_TERMS || schedule == NQS_SCHED_BATCH)
     return NQS_OK;
-  if (schedule == NQS_SCHED_TRIE) return fail(NQS_ERR_UNSUPPORTED, "schedule not built yet");
+  if (schedule == NQS_SCHED_TRIE) {
+    if (ham->n_qubits > 255) return fail(NQS_ERR_UNSUPPORTED, "trie schedule needs n_qubits <= 255");
+    if (n >= (int64_t(1) << 23)) return fail(NQS_ERR_UNSUPPORTED, "trie schedule needs n_unq < 2^23");
+    return NQS_OK;
+  }
   return fail(NQS_ERR_ARG, "unknown schedule");
+}
+
+int nqs_stage_trie(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, void* stream) {
+  StageHeader L;
+  int rc = check_work(ham, U, n, work, &L);
+  if (rc || (rc = check_schedule(ham, n, NQS_SCHED_TRIE))) return rc;
+  cudaError_t e = launch_trie_build(ham, U, n, (char*)work, L, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "prefix tree build");
+  return NQS_OK;
 }
 
 // AUTO: LoopOverBatch costs ~N_unq^2 / 2 cheap pair tests, LoopOverTerms
@@ -431,8 +455,11 @@ static cudaError_t launch_search(const nqs_ham* ham, const uint64_t* U, int64_t 
                                  const StageHeader& L, int64_t rb, int64_t re, int schedule,
                                  int64_t* rp, uint32_t* pj, uint32_t* pk, int mode,
                                  const PairScratch* sc, cudaStream_t s) {
-  if (pick_schedule(ham, n, schedule) == NQS_SCHED_BATCH)
+  const int sched = pick_schedule(ham, n, schedule);
+  if (sched == NQS_SCHED_BATCH)
     return launch_pairs_batch(ham, U, n, work, L, rb, re, rp, pj, pk, mode, sc, s);
+  if (sched == NQS_SCHED_TRIE)
+    return launch_pairs_trie(ham, U, n, work, L, rb, re, rp, pj, pk, mode == kFill ? kFill : kCount, s);
   return launch_pairs_terms(ham, U, work, L, rb, re, rp, pj, pk, mode, sc, s);
 }
 
@@ -457,7 +484,7 @@ int nqs_count_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, vo
                             int64_t* n_pairs, void* stream) {
   StageHeader L;
   int rc = check_work(ham, U, n, work, &L);
-  if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(schedule))) return rc;
+  if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(ham, n, schedule))) return rc;
   if (!row_ptr || !n_pairs) return fail(NQS_ERR_ARG, "null row_ptr or n_pairs");
   cudaStream_t s = (cudaStream_t)stream;
   if ((rc = count_pass(ham, U, n, work, L, rb, re, schedule, row_ptr, nullptr, s))) return rc;
@@ -471,7 +498,7 @@ int nqs_fill_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
                            uint32_t* pair_j, uint32_t* pair_k, void* stream) {
   StageHeader L;
   int rc = check_work(ham, U, n, work, &L);
-  if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(schedule))) return rc;
+  if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(ham, n, schedule))) return rc;
   if (!row_ptr || !pair_j || !pair_k) return fail(NQS_ERR_ARG, "null output");
   if (re == rb) return NQS_OK;
   cudaError_t e = launch_search(ham, U, n, (char*)work, L, rb, re, schedule, (int64_t*)row_ptr, pair_j,
@@ -491,11 +518,12 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
                            int64_t* n_pairs, void* stream) {
   StageHeader L;
   int rc = check_work(ham, U, n, work, &L);
-  if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(schedule))) return rc;
+  if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(ham, n, schedule))) return rc;
   if (!row_ptr || !n_pairs) return fail(NQS_ERR_ARG, "null row_ptr or n_pairs");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t rows = re - rb;
-  if (!scratch || pick_schedule(ham, n, schedule) == NQS_SCHED_BATCH) {  // count, then fill
+  const int sched = pick_schedule(ham, n, schedule);
+  if (!scratch || sched == NQS_SCHED_BATCH || sched == NQS_SCHED_TRIE) {  // count, then fill
     rc = nqs_count_coupled_pairs(ham, U, n, work, rb, re, schedule, row_ptr, n_pairs, stream);
     if (rc) return rc;
     if (*n_pairs > capacity) return fail(NQS_ERR_CAPACITY, "pair capacity too small");

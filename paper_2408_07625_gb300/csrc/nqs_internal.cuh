@@ -23,6 +23,7 @@ constexpr int kStatusBadBits = 2;
 constexpr int kStatusLimit = 4;
 constexpr int kStatusRange = 8;
 constexpr int kStatusCapacity = 16;        // a pair buffer sized ahead of time was too small
+constexpr int kStatusNoTrie = 32;          // trie search on a workspace whose prefix tree was not built
 
 // ---------------------------------------------------------------------------
 // Hamiltonian tables (device) -- Fig. ham_prep, regrouped:
@@ -53,6 +54,9 @@ struct nqs_ham_dev {
   unsigned long long* xy_table = nullptr;  // XY hash set: slots of W key words + (id | hash << 32), id = ~0: empty
   int64_t xy_cap = 0;            // slots (power of two)
   unsigned long long* wmask = nullptr;     // [5] bit w set if some pattern has Hamming weight w
+  int4* xy_trie = nullptr;       // prefix tree of the patterns: {child0, child1, single pattern or -1, 0}
+  int64_t n_xy_nodes = 0;
+  uint32_t* xy_hash = nullptr;   // [n_xy] linear hash of each pattern
 
   // host copies (export, tests)
   std::vector<uint64_t> h_xy, h_yz;
@@ -78,6 +82,9 @@ struct StageHeader {
   int64_t nwords;       // bloom words (power of two)
   int32_t W;
   int32_t status;       // device status word (kStatus* bits)
+  int32_t trie_ok;      // nonzero once the prefix tree of U is built for this staging
+  int32_t pad0;
+  int64_t off_trie;     // prefix tree of U (LoopOverTrie)
   int64_t off_hx, off_table, off_bloom, off_scan, off_ampP, off_ampQ, off_ampK, off_geff, off_counters;
   int64_t off_perm, off_rowcur;
   int64_t scan_blocks;
@@ -127,6 +134,16 @@ cudaError_t launch_pairs_batch(const nqs_ham* ham, const uint64_t* U, int64_t n_
                                const StageHeader& L, int64_t row_begin, int64_t row_end,
                                int64_t* counts_or_rowptr, uint32_t* pair_j, uint32_t* pair_k,
                                int mode, const PairScratch* scratch, cudaStream_t s);
+
+// prefix trees (LoopOverTrie)
+void build_xy_trie(const std::vector<uint64_t>& xy, int64_t n_xy, int W, std::vector<int32_t>& nodes);
+int64_t trie_bytes(int W, int64_t n_unq);
+cudaError_t launch_trie_build(const nqs_ham* ham, const uint64_t* U, int64_t n, char* stage,
+                              const StageHeader& L, cudaStream_t s);
+cudaError_t launch_pairs_trie(const nqs_ham* ham, const uint64_t* U, int64_t n, const char* stage,
+                              const StageHeader& L, int64_t row_begin, int64_t row_end,
+                              int64_t* counts_or_rowptr, uint32_t* pair_j, uint32_t* pair_k,
+                              int mode, cudaStream_t s);
 
 cudaError_t launch_scan(int64_t* data, int64_t n, char* stage, const StageHeader& L,
                         cudaStream_t s);

@@ -1,6 +1,7 @@
 // Batched evaluation of many independent (Hamiltonian, sample batch) instances
 // as one CUDA graph: planning stages every instance, picks its FindCoupledPairs
-// schedule by timing both (LoopOverTerms, Alg. 2A; LoopOverBatch, Alg. 2B),
+// schedule by timing the candidates (LoopOverTerms, Alg. 2A; LoopOverBatch,
+// Alg. 2B; LoopOverTrie, Alg. 2C with the prefix-tree build of Alg. 3),
 // sizes its buffers, and captures all instances' kernels on forked streams
 // into a single graph; each run is one graph launch with no host
 // synchronisation and no allocation.  Buffers sized at planning time are
@@ -27,7 +28,7 @@ struct PlanInstance {
   double* hdiag = nullptr;
   int64_t capacity = 0;
   int64_t planned_pairs = 0;
-  float t_terms_ms = -1.f, t_batch_ms = -1.f;
+  float t_terms_ms = -1.f, t_batch_ms = -1.f, t_trie_ms = -1.f;
 };
 
 }  // namespace nqs
@@ -80,6 +81,15 @@ static cudaError_t enqueue_instance(PlanInstance& I, int precision, cudaStream_t
     capacity_check_kernel<<<1, 32, 0, s>>>(I.row_ptr, n, I.capacity, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_pairs_batch(ham, I.in.U, n, w, I.L, 0, n, I.row_ptr, I.pair_j, I.pair_k, kFill, nullptr, s)))
+      return e;
+  } else if (I.schedule == NQS_SCHED_TRIE) {
+    if ((e = launch_trie_build(ham, I.in.U, n, w, I.L, s)) != cudaSuccess) return e;
+    if ((e = launch_pairs_trie(ham, I.in.U, n, w, I.L, 0, n, I.row_ptr + 1, nullptr, nullptr, kCount, s)))
+      return e;
+    if ((e = launch_scan(I.row_ptr + 1, n, w, I.L, s)) != cudaSuccess) return e;
+    capacity_check_kernel<<<1, 32, 0, s>>>(I.row_ptr, n, I.capacity, status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_pairs_trie(ham, I.in.U, n, w, I.L, 0, n, I.row_ptr, I.pair_j, I.pair_k, kFill, s)))
       return e;
   } else {
     PairScratch sc = pair_scratch_view(I.scratch, n, I.scratch_bytes);
@@ -149,12 +159,28 @@ int nqs_batch_plan(const nqs_instance* insts, int n_inst, int precision, int fla
       cudaEventElapsedTime(&I.t_batch_ms, t0, t1);
       if (!rc && np_batch != np_terms) rc = fail(NQS_ERR_DEVICE_LIMIT, "schedules disagree on the pair count");
     }
+    const bool try_trie = (flags & 1) && I.in.ham->n_qubits <= 255 && n < (int64_t(1) << 23);
+    if (!rc && try_trie) {
+      int64_t np_trie = -1;
+      cudaEventRecord(t0, s);
+      rc = nqs_stage_trie(I.in.ham, I.in.U, n, I.work, stream);
+      if (!rc)
+        rc = nqs_count_coupled_pairs(I.in.ham, I.in.U, n, I.work, 0, n, NQS_SCHED_TRIE, I.row_ptr, &np_trie,
+                                     stream);
+      cudaEventRecord(t1, s);
+      cudaEventSynchronize(t1);
+      cudaEventElapsedTime(&I.t_trie_ms, t0, t1);
+      if (!rc && np_trie != np_terms) rc = fail(NQS_ERR_DEVICE_LIMIT, "schedules disagree on the pair count");
+    }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     if (rc) break;
-    if (flags & 1)
-      I.schedule = (try_batch && I.t_batch_ms < I.t_terms_ms) ? NQS_SCHED_BATCH : NQS_SCHED_TERMS;
-    else
+    if (flags & 1) {
+      I.schedule = NQS_SCHED_TERMS;
+      float best = I.t_terms_ms;
+      if (try_batch && I.t_batch_ms < best) { I.schedule = NQS_SCHED_BATCH; best = I.t_batch_ms; }
+      if (try_trie && I.t_trie_ms < best) { I.schedule = NQS_SCHED_TRIE; best = I.t_trie_ms; }
+    } else
       I.schedule = (n < I.in.ham->n_xy) ? NQS_SCHED_BATCH : NQS_SCHED_TERMS;
     I.planned_pairs = np_terms;
     I.capacity = np_terms + np_terms / 4 + 4096;
@@ -223,7 +249,7 @@ int nqs_batch_status(const nqs_plan* p, int* failed_instance, void* stream) {
   return NQS_OK;
 }
 
-int nqs_batch_info(const nqs_plan* p, int i, int64_t info[6]) {
+int nqs_batch_info(const nqs_plan* p, int i, int64_t info[7]) {
   if (!p || !info || i < 0 || i >= (int)p->inst.size()) return fail(NQS_ERR_ARG, "bad argument");
   const PlanInstance& I = p->inst[i];
   info[0] = I.schedule;
@@ -232,6 +258,7 @@ int nqs_batch_info(const nqs_plan* p, int i, int64_t info[6]) {
   info[3] = (int64_t)p->n_nodes;
   info[4] = (int64_t)(1000.0f * I.t_terms_ms);
   info[5] = (int64_t)(1000.0f * I.t_batch_ms);
+  info[6] = (int64_t)(1000.0f * I.t_trie_ms);
   return NQS_OK;
 }
 

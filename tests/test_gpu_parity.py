@@ -184,9 +184,10 @@ def test_one_pass_equals_two_pass(h28):
         assert sorted(zip(rows.tolist(), j.tolist())) == want
 
 
-@pytest.mark.parametrize("schedule", ["batch", "auto"])
+@pytest.mark.parametrize("schedule", ["batch", "auto", "trie"])
 def test_batch_schedule_matches_terms(h28, schedule):
-    """LoopOverBatch (Alg. 2B) lists the same pairs; energies agree to rounding."""
+    """LoopOverBatch (Alg. 2B) and LoopOverTrie (Alg. 2C) list the same pairs;
+    energies agree to rounding."""
     inst, ref_ham, ref = h28
     ham, batch = gpu_objects(inst)
     for r0, r1 in [(0, inst.n_unq), (17, 1234)]:
@@ -208,7 +209,8 @@ def test_batch_schedule_matches_terms(h28, schedule):
     assert np.abs(eb["eloc_re"].cpu().numpy() - want).max() < TOL64
 
 
-def test_batch_schedule_random_multiword():
+@pytest.mark.parametrize("schedule", ["batch", "trie"])
+def test_batch_schedule_random_multiword(schedule):
     for n, seed in ((70, 4), (130, 5)):
         x, z, c = random_pauli_hamiltonian(n, 150, seed, allow_odd_y=False, max_weight=4)
         pyrng = __import__("random").Random(seed)
@@ -222,7 +224,7 @@ def test_batch_schedule_random_multiword():
         ref_pairs = oracle.find_coupled_pairs(Ui, ref_ham, "batch")
         ham = nqs.Hamiltonian(x, z, c, n)
         batch = nqs.Batch(ham, to_dev_u(pack_ints(Ui, n)))
-        pairs = nqs.coupled_pairs(batch, schedule="batch")
+        pairs = nqs.coupled_pairs(batch, schedule=schedule)
         _check_pairs(batch, pairs, ref_pairs, Ui, _xy_ints(ham))
 
 

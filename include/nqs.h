@@ -307,8 +307,8 @@ int nqs_batch_status(const nqs_plan* plan, int* failed_instance, void* stream);
 /* info[0] schedule, [1] pair capacity, [2] planned pairs, [3] graph nodes,
  * [4] LoopOverTerms count time (us), [5] LoopOverBatch count time (us),
  * [6] LoopOverTrie tree build + count time (us) of instance i (-1: not
- * timed). */
-int nqs_batch_info(const nqs_plan* plan, int i, int64_t info[7]);
+ * timed), [7] kernel nodes of the graph. */
+int nqs_batch_info(const nqs_plan* plan, int i, int64_t info[8]);
 
 int nqs_batch_free(nqs_plan* plan);
 

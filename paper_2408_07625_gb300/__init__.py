@@ -515,11 +515,11 @@ class BatchedPlan:
         return rc, int(bad.value)
 
     def info(self, i):
-        v = (ctypes.c_int64 * 7)()
+        v = (ctypes.c_int64 * 8)()
         _check(_lib.nqs_batch_info(self._h, int(i), v))
         sched = {v2: k for k, v2 in SCHEDULES.items()}[int(v[0])]
         return {"schedule": sched, "capacity": v[1], "planned_pairs": v[2], "graph_nodes": v[3],
-                "t_terms_us": v[4], "t_batch_us": v[5], "t_trie_us": v[6]}
+                "t_terms_us": v[4], "t_batch_us": v[5], "t_trie_us": v[6], "graph_kernels": v[7]}
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

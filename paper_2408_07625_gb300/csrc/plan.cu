@@ -41,6 +41,7 @@ struct nqs_plan {
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
   size_t n_nodes = 0;
+  size_t n_kernels = 0;
 };
 
 namespace nqs {
@@ -221,6 +222,15 @@ int nqs_batch_plan(const nqs_instance* insts, int n_inst, int precision, int fla
     return cuda_fail(ce != cudaSuccess ? ce : e, "graph capture");
   }
   cudaGraphGetNodes(p->graph, nullptr, &p->n_nodes);
+  {
+    std::vector<cudaGraphNode_t> nodes(p->n_nodes);
+    size_t nn = p->n_nodes;
+    if (nn) cudaGraphGetNodes(p->graph, nodes.data(), &nn);
+    for (size_t k = 0; k < nn; ++k) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++p->n_kernels;
+    }
+  }
   if ((e = cudaGraphInstantiate(&p->exec, p->graph, 0)) != cudaSuccess) {
     free_plan(p);
     return cuda_fail(e, "cudaGraphInstantiate");
@@ -249,7 +259,7 @@ int nqs_batch_status(const nqs_plan* p, int* failed_instance, void* stream) {
   return NQS_OK;
 }
 
-int nqs_batch_info(const nqs_plan* p, int i, int64_t info[7]) {
+int nqs_batch_info(const nqs_plan* p, int i, int64_t info[8]) {
   if (!p || !info || i < 0 || i >= (int)p->inst.size()) return fail(NQS_ERR_ARG, "bad argument");
   const PlanInstance& I = p->inst[i];
   info[0] = I.schedule;
@@ -259,6 +269,7 @@ int nqs_batch_info(const nqs_plan* p, int i, int64_t info[7]) {
   info[4] = (int64_t)(1000.0f * I.t_terms_ms);
   info[5] = (int64_t)(1000.0f * I.t_batch_ms);
   info[6] = (int64_t)(1000.0f * I.t_trie_ms);
+  info[7] = (int64_t)p->n_kernels;
   return NQS_OK;
 }
 

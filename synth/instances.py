@@ -112,7 +112,7 @@ def config_instance(name: str, n_unq: int = None, use_cache: bool = True,
     return inst
 
 
-def batched_instances(n_inst: int = 64, seed: int = 5000):
+def batched_instances(n_inst: int = 64, seed: int = 5000, use_cache: bool = True):
     """Uneven instances: N uniform in {20,28,36,44,56}, n_alpha = n_beta =
     ceil(N/8), |U| = round(10^U(3,5)) capped at half the sector's size.
 
@@ -120,24 +120,38 @@ def batched_instances(n_inst: int = 64, seed: int = 5000):
     Hamiltonian (integrals seed 1000+N); every instance has its own peaked
     batch (samples seed 6000+t) and log-amplitudes (seed 7000+t).
     """
+    path = os.path.join(_cache_dir(), f"batched_{n_inst}_s{seed}_v{_GEN_VERSION}.npz")
     rng = np.random.default_rng(seed)
-    hams = {}
-    out = []
+    plan = []
     for t in range(n_inst):
         N = int(rng.choice([20, 28, 36, 44, 56]))
-        n_orb = N // 2
         ne = math.ceil(N / 8)
-        sector = math.comb(n_orb, ne) ** 2
-        n_unq = min(int(round(10 ** rng.uniform(3, 5))), sector // 2)
+        sector = math.comb(N // 2, ne) ** 2
+        plan.append((N, ne, min(int(round(10 ** rng.uniform(3, 5))), sector // 2)))
+    cached = np.load(path, allow_pickle=False) if use_cache and os.path.exists(path) else None
+    hams, out, save = {}, [], {}
+    for t, (N, ne, n_unq) in enumerate(plan):
+        n_orb = N // 2
         if N not in hams:
-            x, z, c, _, _, _ = _hamiltonian(n_orb, 2, 1000 + N)
-            hams[N] = (x, z, c)
+            if cached is not None:
+                hams[N] = (cached[f"x{N}"], cached[f"z{N}"], cached[f"c{N}"])
+            else:
+                x, z, c, _, _, _ = _hamiltonian(n_orb, 2, 1000 + N)
+                hams[N] = (x, z, c)
+                save.update({f"x{N}": x, f"z{N}": z, f"c{N}": c})
         x, z, c = hams[N]
-        vals, ranks = peaked_samples(n_orb, ne, ne, n_unq, 6000 + t)
-        rng_l = np.random.default_rng(7000 + t)
-        lre = -2.0 * ranks + rng_l.normal(0.0, 0.3, size=len(vals))
-        out.append(Instance(f"b{t}_N{N}", N, ne, ne, x, z, c, pack_ints(vals, N), ranks, lre,
+        if cached is not None:
+            U, ranks, lre = cached[f"U{t}"], cached[f"r{t}"], cached[f"l{t}"]
+        else:
+            vals, ranks = peaked_samples(n_orb, ne, ne, n_unq, 6000 + t)
+            U = pack_ints(vals, N)
+            rng_l = np.random.default_rng(7000 + t)
+            lre = -2.0 * ranks + rng_l.normal(0.0, 0.3, size=len(vals))
+            save.update({f"U{t}": U, f"r{t}": ranks, f"l{t}": lre})
+        out.append(Instance(f"b{t}_N{N}", N, ne, ne, x, z, c, U, ranks, lre,
                             np.zeros_like(lre), {"n_orb": n_orb, "batched": True}))
+    if cached is None and use_cache:
+        np.savez(path, **save)
     return out
 
 

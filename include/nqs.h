@@ -242,6 +242,19 @@ int nqs_variational_energy(int64_t n_unq, const double* logpsi_re, const double*
 int nqs_variational_energy_noalloc(int64_t n_unq, const double* logpsi_re,
                                    const double* eloc_re, double* out, void* stream);
 
+/* E^var of a batch whose rows are split into k blocks (one per GPU when the
+ * rows are sharded across ranks), from the k triples that
+ * nqs_variational_energy wrote for the blocks (each called on its block's
+ * slices of logpsi_re and eloc_re).  With m = max_r max_r and
+ * f_r = exp(2 (max_r - m)) (Eq. variational_energy, weights |psi|^2):
+ *   out[1] = m,  out[2] = sum_r sum_r f_r,  out[0] = sum_r E_r sum_r f_r / out[2].
+ * Blocks with a zero weight sum (empty) are skipped.  The result can be
+ * passed as `evar` to nqs_local_energy_backward for any block.
+ * nqs_evar_combine: device parts [k][3] and out [3], asynchronous.
+ * nqs_evar_combine_host: the same on host arrays (synchronous). */
+int nqs_evar_combine(const double* parts, int k, double* out, void* stream);
+int nqs_evar_combine_host(const double* parts, int k, double* out);
+
 /* ---------------------------------------------------------------------------
  * Adjoint: gradient of L = sum_x [g_re(x) Re E_loc(x) + g_im(x) Im E_loc(x)]
  *          + g_evar E^var with respect to (Re log psi, Im log psi).

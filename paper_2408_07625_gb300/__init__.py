@@ -76,6 +76,8 @@ def load_library(path: str = None):
         "nqs_batch_status": (_i32, [_vp, ctypes.POINTER(_i32), _vp]),
         "nqs_batch_info": (_i32, [_vp, _i32, _c_i64p]),
         "nqs_batch_free": (_i32, [_vp]),
+        "nqs_evar_combine": (_i32, [_vp, _i32, _vp, _vp]),
+        "nqs_evar_combine_host": (_i32, [_vp, _i32, _vp]),
         "nqs_last_error": (ctypes.c_char_p, []),
         "nqs_version": (_i32, []),
     }

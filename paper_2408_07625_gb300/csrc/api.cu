@@ -581,6 +581,31 @@ int nqs_variational_energy(int64_t n, const double* a, const double* eloc_re, vo
   return NQS_OK;
 }
 
+int nqs_evar_combine(const double* parts, int k, double* out, void* stream) {
+  if (!parts || !out || k < 1) return fail(NQS_ERR_ARG, "bad argument to nqs_evar_combine");
+  cudaError_t e = launch_evar_combine(parts, k, out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "E^var combine kernel");
+  return NQS_OK;
+}
+
+int nqs_evar_combine_host(const double* parts, int k, double* out) {
+  if (!parts || !out || k < 1) return fail(NQS_ERR_ARG, "bad argument to nqs_evar_combine_host");
+  double amax = -1.7976931348623157e308;
+  for (int r = 0; r < k; ++r)
+    if (parts[3 * r + 2] > 0.0) amax = std::max(amax, parts[3 * r + 1]);
+  double S = 0.0, N = 0.0;
+  for (int r = 0; r < k; ++r) {
+    if (!(parts[3 * r + 2] > 0.0)) continue;
+    const double f = std::exp(2.0 * (parts[3 * r + 1] - amax));
+    S += parts[3 * r + 2] * f;
+    N += parts[3 * r] * parts[3 * r + 2] * f;
+  }
+  out[0] = S > 0.0 ? N / S : 0.0;
+  out[1] = amax;
+  out[2] = S;
+  return NQS_OK;
+}
+
 int nqs_local_energy_backward(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work,
                               const double* a, const double* b, int64_t rb, int64_t re,
                               const int64_t* row_ptr, const uint32_t* pair_j, const uint32_t* pair_k,

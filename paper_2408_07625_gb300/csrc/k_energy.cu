@@ -367,6 +367,31 @@ cudaError_t launch_variational_energy(int64_t n, const double* a, const double* 
   return cudaGetLastError();
 }
 
+// E^var of a batch from the triples of row blocks that partition it (one
+// per rank when the rows are sharded): rescale every block's weight sum to
+// the largest max, in block order.
+__global__ void evar_combine_kernel(const double* __restrict__ parts, int k, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double amax = -DBL_MAX;
+  for (int r = 0; r < k; ++r)
+    if (parts[3 * r + 2] > 0.0) amax = fmax(amax, parts[3 * r + 1]);
+  double S = 0.0, N = 0.0;
+  for (int r = 0; r < k; ++r) {
+    if (!(parts[3 * r + 2] > 0.0)) continue;
+    const double f = exp(2.0 * (parts[3 * r + 1] - amax));
+    S += parts[3 * r + 2] * f;
+    N += parts[3 * r] * parts[3 * r + 2] * f;
+  }
+  out[0] = S > 0.0 ? N / S : 0.0;
+  out[1] = amax;
+  out[2] = S;
+}
+
+cudaError_t launch_evar_combine(const double* parts, int k, double* out, cudaStream_t s) {
+  evar_combine_kernel<<<1, 32, 0, s>>>(parts, k, out);
+  return cudaGetLastError();
+}
+
 // --------------------------------------------------------------------------
 // E^var without caller memory: the partial sums live in a file-scope device
 // array instead of the batch workspace.  For callers that cannot allocate

@@ -160,6 +160,7 @@ cudaError_t launch_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n
 
 cudaError_t launch_variational_energy(int64_t n, const double* a, const double* eloc_re,
                                       char* work, double* out, cudaStream_t s);
+cudaError_t launch_evar_combine(const double* parts, int k, double* out, cudaStream_t s);
 
 cudaError_t launch_backward(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
                             char* stage, const StageHeader& L, bool cplx,

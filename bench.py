@@ -202,6 +202,8 @@ def run_ours(args):
         rp_all, _ = nqs.count_pairs(batch)
         r0, r1 = row_blocks(rp_all.cpu().numpy(), ws)[rank]
 
+    hbuf = [None]  # per-pair matrix elements, kept from E_loc^var for the adjoint
+
     def step(batch_obj, Udev, adev, record=False):
         marks = []
         def mark():
@@ -213,14 +215,17 @@ def run_ours(args):
         rp, pj, pk = nqs.coupled_pairs(batch_obj, r0, r1, schedule=args.schedule, reuse=True)
         total = int(pj.numel())
         mark()
-        er, ei, hd = nqs.local_energy(batch_obj, adev, None, (rp, pj, pk), prec, r0, r1)
+        if hbuf[0] is None or hbuf[0].numel() < (2 if prec == "fp32c" else 1) * total:
+            hbuf[0] = nqs.pair_h_buffer(int(total * 1.1) + 1024, prec, dev)
+        hp = hbuf[0][:total] if total > 0 else None
+        er, ei, hd = nqs.local_energy(batch_obj, adev, None, (rp, pj, pk), prec, r0, r1, hpair=hp)
         mark()
         evar = nqs.variational_energy(batch_obj, adev[r0:r1], er[r0:r1])
         if ws > 1:  # the one exchange: every rank's [E, max, sum] triple
             evar = combine_evar(evar)
         mark()
         gr, gi = nqs.local_energy_backward(batch_obj, adev, None, er, ei, hd, evar, g, None, gE,
-                                           (rp, pj, pk), prec, r0, r1)
+                                           (rp, pj, pk), prec, r0, r1, hpair=hp)
         mark()
         return er, evar, gr, total, marks
 
@@ -311,7 +316,11 @@ def run_ours(args):
             "traffic": _profile_traffic(), "launch_ms": fill_ms,
             "peak_source": "derived: 152 SMs x 128 lanes x 2.07 GHz"}
 
-    kernels_per_step = 12  # stage 1, search 1 + scan 3 + compaction 1, energy 2, evar 1, backward 3
+    # library kernels per step: pairs phase, then amplitudes + row order (2) + E_loc^var, E^var
+    # (+ combination across ranks), amplitudes + adjoint weights + row order (2) + adjoint
+    pairs_kernels = {"terms": 1 + 1 + 2 + 3 + 1, "batch": 1 + 1 + 3 + 1,
+                     "trie": 1 + 3 * ((inst.n_qubits + 7) // 8) + 7 + 1 + 3 + 1}[args.schedule]
+    kernels_per_step = pairs_kernels + 4 + 1 + (1 if ws > 1 else 0) + 5
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None,

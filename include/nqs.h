@@ -205,15 +205,21 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
  * the same range, write
  *   eloc_re[r], eloc_im[r] = E_loc^var(U_r)  (eloc_im may be NULL only if
  *                                              logpsi_im is NULL),
- *   hdiag[r] = H_{U_r U_r} (may be NULL).
+ *   hdiag[r] = H_{U_r U_r} (may be NULL),
+ *   hpair[q] = H of pair q, q indexing pair_j/pair_k (may be NULL): device
+ *              float2 (hi, lo) per pair with NQS_PREC_FP32C, double with
+ *              NQS_PREC_FP64; nqs_local_energy_backward can read it instead
+ *              of recomputing the matrix elements.
  * logpsi_re/_im: device FP64 [n_unq] for the whole batch.  Each row is a
- * fixed-order reduction, so results are bitwise reproducible.  The call
- * overwrites the per-sample scratch of work.  Asynchronous. */
+ * fixed-order reduction by one warp, so results are bitwise reproducible
+ * (rows are handed out heaviest first; the order does not affect any row).
+ * The call overwrites the per-sample scratch of work.  Asynchronous. */
 int nqs_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, void* work,
                      const double* logpsi_re, const double* logpsi_im,
                      int64_t row_begin, int64_t row_end, const int64_t* row_ptr,
                      const uint32_t* pair_j, const uint32_t* pair_k, int precision,
-                     double* eloc_re, double* eloc_im, double* hdiag, void* stream);
+                     double* eloc_re, double* eloc_im, double* hdiag, void* hpair,
+                     void* stream);
 
 /* E^var = sum_x p(x) Re E_loc^var(x) / sum_x p(x) with p = exp(2 a) over the
  * whole batch (Eq. variational_energy), FP64, deterministic (fixed block
@@ -264,6 +270,8 @@ int nqs_evar_combine_host(const double* parts, int k, double* out);
  *   evar: device FP64 [3] from nqs_variational_energy.
  *   g_eloc_re/_im: device FP64 [n_unq] or NULL (zero upstream).
  *   g_evar: device FP64 [1] or NULL (zero).
+ *   hpair: the per-pair matrix elements stored by nqs_local_energy for the
+ *          same pairs and precision, or NULL to recompute them (same bits).
  * With both g_eloc arrays NULL no pair data is read (row_ptr may be NULL)
  * and the result is the closed form 2 w_y (E_loc(y) - E) g_evar.  The sum
  * over x of each pair (x, y) is evaluated on row y, which lists the same
@@ -273,6 +281,7 @@ int nqs_local_energy_backward(const nqs_ham* ham, const uint64_t* U, int64_t n_u
                               void* work, const double* logpsi_re, const double* logpsi_im,
                               int64_t row_begin, int64_t row_end, const int64_t* row_ptr,
                               const uint32_t* pair_j, const uint32_t* pair_k,
+                              const void* hpair,
                               const double* eloc_re, const double* eloc_im,
                               const double* hdiag, const double* evar,
                               const double* g_eloc_re, const double* g_eloc_im,

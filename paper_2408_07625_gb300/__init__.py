@@ -67,9 +67,9 @@ def load_library(path: str = None):
                                           _i64, _c_i64p, _vp]),
         "nqs_pairs_scratch_bytes": (_i64, [_i64, _i64]),
         "nqs_local_energy": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _i32,
-                                    _vp, _vp, _vp, _vp]),
+                                    _vp, _vp, _vp, _vp, _vp]),
         "nqs_variational_energy": (_i32, [_i64, _vp, _vp, _vp, _vp, _vp]),
-        "nqs_local_energy_backward": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp,
+        "nqs_local_energy_backward": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp,
                                              _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp]),
         "nqs_batch_plan": (_i32, [_vp, _i32, _i32, _i32, ctypes.POINTER(_vp), _vp]),
         "nqs_batch_run": (_i32, [_vp, _vp]),
@@ -311,12 +311,29 @@ def coupled_pairs(batch: Batch, row_begin=0, row_end=None, schedule="terms", one
     return row_ptr, pj[:total].clone(), pk[:total].clone()
 
 
+def pair_h_buffer(n_pairs, precision="fp32c", device="cuda"):
+    """A tensor that holds one matrix element per pair (``hpair`` of local_energy)."""
+    if precision == "fp64":
+        return torch.empty(max(int(n_pairs), 1), dtype=torch.float64, device=device)
+    return torch.empty((max(int(n_pairs), 1), 2), dtype=torch.float32, device=device)
+
+
+def _check_hpair(hpair, n_pairs, precision):
+    if hpair is None:
+        return None
+    want = (torch.float64, 1) if precision == "fp64" else (torch.float32, 2)
+    if hpair.dtype != want[0] or hpair.numel() < want[1] * n_pairs or not hpair.is_contiguous():
+        raise ValueError("hpair does not match the pair count or precision")
+    return hpair
+
+
 def local_energy(batch: Batch, logpsi_re, logpsi_im=None, pairs=None, precision="fp32c",
-                 row_begin=0, row_end=None, out=None, stream=None):
+                 row_begin=0, row_end=None, out=None, hpair=None, stream=None):
     """E_loc^var for rows [row_begin, row_end) from their CSR pairs.
 
     Returns (eloc_re, eloc_im or None, hdiag), full-length tensors of which the
-    rows in range are written.
+    rows in range are written.  ``hpair`` (from ``pair_h_buffer``) receives
+    each pair's matrix element for the adjoint.
     """
     row_end = batch.n if row_end is None else int(row_end)
     dev = batch.device
@@ -331,9 +348,11 @@ def local_energy(batch: Batch, logpsi_re, logpsi_im=None, pairs=None, precision=
         hd = torch.zeros(batch.n, dtype=torch.float64, device=dev)
     else:
         er, ei, hd = out
+    hpair = _check_hpair(hpair, int(pj.numel()), precision)
     _check(_lib.nqs_local_energy(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work), _ptr(a), _ptr(b),
                                  int(row_begin), row_end, _ptr(rp), _pair_ptr(pj), _pair_ptr(pk),
-                                 PRECISIONS[precision], _ptr(er), _ptr(ei), _ptr(hd), _stream(stream)))
+                                 PRECISIONS[precision], _ptr(er), _ptr(ei), _ptr(hd), _ptr(hpair),
+                                 _stream(stream)))
     return er, ei, hd
 
 
@@ -349,8 +368,12 @@ def variational_energy(batch: Batch, logpsi_re, eloc_re, out=None, stream=None):
 
 def local_energy_backward(batch: Batch, logpsi_re, logpsi_im, eloc_re, eloc_im, hdiag, evar,
                           g_eloc_re=None, g_eloc_im=None, g_evar=None, pairs=None, precision="fp32c",
-                          row_begin=0, row_end=None, out=None, stream=None):
-    """Gradient of sum g_re Re E_loc + g_im Im E_loc + g_E E^var w.r.t. (Re, Im) log psi."""
+                          row_begin=0, row_end=None, out=None, hpair=None, stream=None):
+    """Gradient of sum g_re Re E_loc + g_im Im E_loc + g_E E^var w.r.t. (Re, Im) log psi.
+
+    ``hpair``: the matrix elements local_energy stored for the same pairs (or
+    None to recompute them; the result is the same).
+    """
     row_end = batch.n if row_end is None else int(row_end)
     dev = batch.device
     a = _f64(logpsi_re, dev)
@@ -365,7 +388,9 @@ def local_energy_backward(batch: Batch, logpsi_re, logpsi_im, eloc_re, eloc_im, 
         gr, gi = out
     _check(_lib.nqs_local_energy_backward(
         batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work), _ptr(a), _ptr(b), int(row_begin), row_end,
-        _ptr(rp), _pair_ptr(pj), _pair_ptr(pk), _ptr(eloc_re), _ptr(eloc_im), _ptr(hdiag), _ptr(evar),
+        _ptr(rp), _pair_ptr(pj), _pair_ptr(pk),
+        _ptr(_check_hpair(hpair, int(pj.numel()), precision) if pj is not None else None),
+        _ptr(eloc_re), _ptr(eloc_im), _ptr(hdiag), _ptr(evar),
         _ptr(_f64(g_eloc_re, dev)), _ptr(_f64(g_eloc_im, dev)), _ptr(_f64(g_evar, dev)),
         PRECISIONS[precision], _ptr(gr), _ptr(gi), _stream(stream)))
     return gr, gi
@@ -386,13 +411,15 @@ def _row_chunks(row_ptr_host, max_pairs):
 
 
 def evaluate(batch: Batch, logpsi_re, logpsi_im=None, precision="fp32c", schedule="terms",
-             max_pairs=None, keep_pairs=True, stream=None):
+             max_pairs=None, keep_pairs=True, keep_h=False, stream=None):
     """Whole forward path: FindCoupledPairs, E_loc^var, E^var.
 
     Without ``max_pairs`` the search runs once (one-pass mode).  With it, rows
     are split into contiguous chunks holding at most ``max_pairs`` pairs each,
     and each chunk's pairs are listed, consumed and dropped in turn.
-    Returns dict(eloc_re, eloc_im, hdiag, evar, n_pairs, pairs or None, chunks).
+    Returns dict(eloc_re, eloc_im, hdiag, evar, n_pairs, pairs or None, chunks,
+    hpair).  With ``keep_h`` (and a single chunk) ``hpair`` holds each pair's
+    matrix element for the adjoint.
     """
     dev = batch.device
     a = _f64(logpsi_re, dev)
@@ -402,10 +429,13 @@ def evaluate(batch: Batch, logpsi_re, logpsi_im=None, precision="fp32c", schedul
     hd = torch.zeros(batch.n, dtype=torch.float64, device=dev)
     rp_host = None
     kept = None
+    hpair = None
     if max_pairs is None:
         pairs = coupled_pairs(batch, 0, batch.n, schedule, reuse=not keep_pairs, stream=stream)
         row_ptr, total, chunks = pairs[0], int(pairs[1].numel()), [(0, batch.n)]
-        local_energy(batch, a, b, pairs, precision, 0, batch.n, (er, ei, hd), stream)
+        if keep_h:
+            hpair = pair_h_buffer(total, precision, dev)
+        local_energy(batch, a, b, pairs, precision, 0, batch.n, (er, ei, hd), hpair=hpair, stream=stream)
         kept = pairs if keep_pairs else None
     else:
         row_ptr, total = count_pairs(batch, 0, batch.n, schedule, stream)
@@ -414,13 +444,13 @@ def evaluate(batch: Batch, logpsi_re, logpsi_im=None, precision="fp32c", schedul
         for (r0, r1) in chunks:
             rp = row_ptr[r0:r1 + 1]
             pj, pk = fill_pairs(batch, rp, int(rp_host[r1] - rp_host[r0]), r0, r1, schedule, stream)
-            local_energy(batch, a, b, (rp, pj, pk), precision, r0, r1, (er, ei, hd), stream)
+            local_energy(batch, a, b, (rp, pj, pk), precision, r0, r1, (er, ei, hd), stream=stream)
             if len(chunks) == 1 and keep_pairs:
                 kept = (rp, pj, pk)
     evar = variational_energy(batch, a, er, stream=stream)
     return {"eloc_re": er, "eloc_im": ei, "hdiag": hd, "evar": evar, "n_pairs": total,
             "pairs": kept, "chunks": chunks, "row_ptr": row_ptr, "row_ptr_host": rp_host,
-            "schedule": schedule}
+            "schedule": schedule, "hpair": hpair if kept is not None else None}
 
 
 class LocalEnergy(torch.autograd.Function):
@@ -436,7 +466,7 @@ class LocalEnergy(torch.autograd.Function):
     @staticmethod
     def forward(ctx, batch, logpsi_re, logpsi_im, precision="fp32c", max_pairs=None):
         res = evaluate(batch, logpsi_re.detach(), None if logpsi_im is None else logpsi_im.detach(),
-                       precision, "terms", max_pairs, keep_pairs=True)
+                       precision, "terms", max_pairs, keep_pairs=True, keep_h=max_pairs is None)
         ctx.batch, ctx.precision, ctx.max_pairs = batch, precision, max_pairs
         ctx.res = res
         ctx.cplx = logpsi_im is not None
@@ -455,7 +485,8 @@ class LocalEnergy(torch.autograd.Function):
         need_pairs = g_er is not None or g_ei is not None
         if not need_pairs or res["pairs"] is not None:
             gr, gi = local_energy_backward(batch, lre, lim, res["eloc_re"], res["eloc_im"], res["hdiag"],
-                                           res["evar"], g_er, g_ei, g_e, res["pairs"], ctx.precision)
+                                           res["evar"], g_er, g_ei, g_e, res["pairs"], ctx.precision,
+                                           hpair=res["hpair"] if need_pairs else None)
         else:
             gr = torch.zeros(batch.n, dtype=torch.float64, device=batch.device)
             gi = torch.zeros(batch.n, dtype=torch.float64, device=batch.device) if ctx.cplx else None

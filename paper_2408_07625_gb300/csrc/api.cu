@@ -62,6 +62,8 @@ StageHeader stage_layout(const nqs_ham* ham, int64_t n) {
   L.off_perm = off;   off = align256(off + 2 * 4 * std::max<int64_t>(n, 1));
   L.off_rowcur = off; off = align256(off + 8 * std::max<int64_t>(n, 1));
   L.off_trie = off;   off = align256(off + trie_bytes(ham->W, n));
+  L.off_sched = off;  off = align256(off + 512);
+  L.off_order = off;  off = align256(off + 4 * std::max<int64_t>(n, 1));
   L.total_bytes = off;
   return L;
 }
@@ -553,7 +555,7 @@ int nqs_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n, void* wor
                      const double* a, const double* b, int64_t rb, int64_t re,
                      const int64_t* row_ptr, const uint32_t* pair_j, const uint32_t* pair_k,
                      int precision, double* eloc_re, double* eloc_im, double* hdiag,
-                     void* stream) {
+                     void* hpair, void* stream) {
   StageHeader L;
   int rc = check_work(ham, U, n, work, &L);
   if (rc || (rc = check_rows(n, rb, re))) return rc;
@@ -567,7 +569,7 @@ int nqs_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n, void* wor
   cudaError_t e = launch_amplitudes(a, b, n, precision, (char*)work, L, s);
   if (e != cudaSuccess) return cuda_fail(e, "amplitude kernel");
   e = launch_local_energy(ham, U, n, (char*)work, L, b != nullptr, rb, re, row_ptr, pair_j, pair_k,
-                          precision, eloc_re, eloc_im, hdiag, s);
+                          precision, eloc_re, eloc_im, hdiag, hpair, s);
   if (e != cudaSuccess) return cuda_fail(e, "local energy kernel");
   return NQS_OK;
 }
@@ -609,6 +611,7 @@ int nqs_evar_combine_host(const double* parts, int k, double* out) {
 int nqs_local_energy_backward(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work,
                               const double* a, const double* b, int64_t rb, int64_t re,
                               const int64_t* row_ptr, const uint32_t* pair_j, const uint32_t* pair_k,
+                              const void* hpair,
                               const double* eloc_re, const double* eloc_im, const double* hdiag,
                               const double* evar, const double* g_re, const double* g_im,
                               const double* g_evar, int precision, double* grad_re,
@@ -631,7 +634,7 @@ int nqs_local_energy_backward(const nqs_ham* ham, const uint64_t* U, int64_t n, 
     if (e != cudaSuccess) return cuda_fail(e, "amplitude kernel");
   }
   e = launch_backward(ham, U, n, (char*)work, L, b != nullptr, a, b, rb, re, row_ptr, pair_j, pair_k,
-                      eloc_re, eloc_im, hdiag, evar, g_re, g_im, g_evar, precision, grad_re, grad_im, s);
+                      eloc_re, eloc_im, hdiag, evar, g_re, g_im, g_evar, precision, hpair, grad_re, grad_im, s);
   if (e != cudaSuccess) return cuda_fail(e, "backward kernel");
   return NQS_OK;
 }

@@ -151,25 +151,111 @@ __device__ __forceinline__ typename Pol::T melem_part(const uint64_t (&xp)[W], i
 }
 
 // --------------------------------------------------------------------------
-// E_loc^var over CSR pairs: one warp per row
+// row schedule: rows of [rb, re) in decreasing order of their pair count
+// (power-of-two classes, heaviest first), handed out to warps one at a time
+// from a counter, so the longest rows start first and no warp idles while
+// others hold several long rows.  Results do not depend on the order: every
+// row is a fixed-order reduction by one warp.
 // --------------------------------------------------------------------------
-template <class Pol, int W, bool CPLX>
+constexpr int kRowClasses = 32;
+
+__device__ __forceinline__ int row_class(int64_t c) {  // 0: heaviest
+  const int lg = c > 0 ? 64 - __clzll((long long)c) : 0;    // bit length, 0..35 for c < 2^35
+  const int k = kRowClasses - 1 - lg;
+  return k < 0 ? 0 : k;
+}
+
+__global__ void row_class_count_kernel(const int64_t* __restrict__ rp, int64_t rows, uint32_t* __restrict__ cnt) {
+  __shared__ uint32_t h[kRowClasses];
+  if (threadIdx.x < kRowClasses) h[threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&h[row_class(rp[r + 1] - rp[r])], 1u);
+  __syncthreads();
+  if (threadIdx.x < kRowClasses && h[threadIdx.x]) atomicAdd(cnt + threadIdx.x, h[threadIdx.x]);
+}
+
+__global__ void row_order_kernel(const int64_t* __restrict__ rp, int64_t rows, const uint32_t* __restrict__ cnt,
+                                 uint32_t* __restrict__ cursor, int32_t* __restrict__ order) {
+  __shared__ uint32_t off[kRowClasses];
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int k = 0; k < kRowClasses; ++k) { off[k] = run; run += cnt[k]; }
+  }
+  __syncthreads();
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+    const int k = row_class(rp[r + 1] - rp[r]);
+    order[off[k] + atomicAdd(cursor + k, 1u)] = (int32_t)r;
+  }
+}
+
+struct RowSched {
+  const int32_t* order;
+  unsigned long long* next;
+  int64_t rows;
+};
+
+// sched region of the workspace: counts [32] u32, cursors [32] u32, row counter u64
+static cudaError_t launch_row_order(const int64_t* rp, int64_t rows, char* stage, const StageHeader& L,
+                                    RowSched& rs, cudaStream_t s) {
+  char* base = stage + L.off_sched;
+  uint32_t* cnt = (uint32_t*)base;
+  uint32_t* cur = cnt + kRowClasses;
+  rs.next = (unsigned long long*)(cur + kRowClasses);
+  rs.order = (const int32_t*)(stage + L.off_order);
+  rs.rows = rows;
+  cudaError_t e = cudaMemsetAsync(base, 0, 2 * kRowClasses * 4 + 8, s);
+  if (e != cudaSuccess) return e;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 2 * num_sms()));
+  row_class_count_kernel<<<blocks, 256, 0, s>>>(rp, rows, cnt);
+  row_order_kernel<<<blocks, 256, 0, s>>>(rp, rows, cnt, cur, (int32_t*)(stage + L.off_order));
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ int64_t next_row(const RowSched& rs) {
+  unsigned long long v = 0;
+  if ((threadIdx.x & 31) == 0) v = atomicAdd(rs.next, 1ull);
+  const int64_t i = (int64_t)__shfl_sync(kFull, v, 0);
+  return i < rs.rows ? (int64_t)__ldg(rs.order + i) : -1;
+}
+
+// matrix elements kept per pair for the adjoint: (hi, lo) floats or doubles
+template <class Pol> struct HStore;
+template <> struct HStore<PolicyF> {
+  using V = float2;
+  __device__ static void put(void* h, int64_t q, df v) { reinterpret_cast<float2*>(h)[q] = make_float2(v.hi, v.lo); }
+  __device__ static df get(const void* h, int64_t q) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(h) + q);
+    return {v.x, v.y};
+  }
+};
+template <> struct HStore<PolicyD> {
+  using V = double;
+  __device__ static void put(void* h, int64_t q, double v) { reinterpret_cast<double*>(h)[q] = v; }
+  __device__ static double get(const void* h, int64_t q) { return __ldg(reinterpret_cast<const double*>(h) + q); }
+};
+
+// --------------------------------------------------------------------------
+// E_loc^var over CSR pairs: one warp per row.  H of a pair with a large P_XY
+// is summed by all lanes (then reduced across the warp); small ones by the
+// lane that holds the pair.  Either way the pair's lane adds H * ratio to its
+// accumulator and, if asked, stores H for the adjoint.
+// --------------------------------------------------------------------------
+template <class Pol, int W, bool CPLX, bool STORE_H>
 __global__ void __launch_bounds__(kEnergyThreads)
 local_energy_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict__ t_ptr,
                     const uint64_t* __restrict__ yz, const float2* __restrict__ cf,
                     const double* __restrict__ cd, int has_diag, int64_t heavy_end,
                     const char* __restrict__ P, const char* __restrict__ Q,
-                    const int* __restrict__ K, int64_t row_begin, int64_t row_end,
+                    const int* __restrict__ K, int64_t row_begin, RowSched rs,
                     const int64_t* __restrict__ rp, const uint32_t* __restrict__ pair_j,
                     const uint32_t* __restrict__ pair_k, double* __restrict__ eloc_re,
-                    double* __restrict__ eloc_im, double* __restrict__ hdiag,
+                    double* __restrict__ eloc_im, double* __restrict__ hdiag, void* __restrict__ hpair,
                     int32_t* __restrict__ status) {
   using T = typename Pol::T;
   if (*(volatile int32_t*)status & kStatusCapacity) return;  // the pair list was not written
   const int lane = threadIdx.x & 31;
-  const int64_t tw = (int64_t)gridDim.x * kEnergyWarps;
-  for (int64_t row = (int64_t)blockIdx.x * kEnergyWarps + (threadIdx.x >> 5); row < row_end - row_begin;
-       row += tw) {
+  for (int64_t row = next_row(rs); row >= 0; row = next_row(rs)) {
     const int64_t i = row + row_begin;
     int64_t p = rp[row] - rp[0];
     const int64_t p1 = rp[row + 1] - rp[0];
@@ -181,7 +267,10 @@ local_energy_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict__
       T h = melem_part<Pol, W>(xi, (int64_t)__ldg(t_ptr) + lane, (int64_t)__ldg(t_ptr + 1), 32, yz, cf, cd);
       h = Pol::warp_sum(h);
       hd = Pol::to_d(h);
-      if (lane == 0) Pol::acc(acc_re, h);  // psi(x)/psi(x) = 1
+      if (lane == 0) {
+        Pol::acc(acc_re, h);  // psi(x)/psi(x) = 1
+        if (STORE_H) HStore<Pol>::put(hpair, p, h);
+      }
       ++p;
     }
     for (int64_t base = p; base < p1; base += 32) {
@@ -198,13 +287,16 @@ local_energy_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict__
         const uint32_t kk = __shfl_sync(kFull, k, src);
         uint64_t xp[W];
         load_words<W>(U + (int64_t)jj * W, xp);
-        T part = melem_part<Pol, W>(xp, (int64_t)__ldg(t_ptr + kk) + lane, (int64_t)__ldg(t_ptr + kk + 1),
-                                    32, yz, cf, cd);
-        part = Pol::fin(part);
-        T rr, ri;
-        ratio<Pol, CPLX>(P, Q, K, jj, i, rr, ri, status);
-        Pol::acc(acc_re, Pol::mul(part, rr));
-        if (CPLX) Pol::acc(acc_im, Pol::mul(part, ri));
+        T h = melem_part<Pol, W>(xp, (int64_t)__ldg(t_ptr + kk) + lane, (int64_t)__ldg(t_ptr + kk + 1), 32, yz,
+                                 cf, cd);
+        h = Pol::warp_sum(h);
+        if (lane == src) {
+          T rr, ri;
+          ratio<Pol, CPLX>(P, Q, K, jj, i, rr, ri, status);
+          Pol::acc(acc_re, Pol::mul(h, rr));
+          if (CPLX) Pol::acc(acc_im, Pol::mul(h, ri));
+          if (STORE_H) HStore<Pol>::put(hpair, q, h);
+        }
       }
       if (have && !heavy) {  // small P_XY: one lane per pair
         uint64_t xp[W];
@@ -215,6 +307,7 @@ local_energy_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict__
         ratio<Pol, CPLX>(P, Q, K, j, i, rr, ri, status);
         Pol::acc(acc_re, Pol::mul(h, rr));
         if (CPLX) Pol::acc(acc_im, Pol::mul(h, ri));
+        if (STORE_H) HStore<Pol>::put(hpair, q, h);
       }
     }
     const T er = Pol::warp_sum(acc_re);
@@ -227,42 +320,62 @@ local_energy_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict__
   }
 }
 
-template <class Pol, int W, bool CPLX>
-static void launch_le(const nqs_ham* ham, const uint64_t* U, const char* stage, const StageHeader& L,
-                      int64_t rb, int64_t re, const int64_t* rp, const uint32_t* pj,
-                      const uint32_t* pk, double* er, double* ei, double* hd, cudaStream_t s) {
-  const int64_t rows = re - rb;
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + kEnergyWarps - 1) / kEnergyWarps,
-                                                                  (int64_t)num_sms() * 8));
-  local_energy_kernel<Pol, W, CPLX><<<blocks, kEnergyThreads, 0, s>>>(
-      U, ham->row_ptr, ham->yz, ham->coef_f, ham->coef, ham->has_diag, ham->heavy_end,
-      stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK), rb, re, rp, pj, pk,
-      er, ei, hd, (int32_t*)(stage + offsetof(StageHeader, status)));
+template <class Kern>
+static int grid_for(Kern kern, int64_t rows) {
+  int occ = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kEnergyThreads, 0);
+  if (occ < 1) occ = 1;
+  return (int)std::max<int64_t>(1, std::min<int64_t>((rows + kEnergyWarps - 1) / kEnergyWarps,
+                                                     (int64_t)num_sms() * occ));
 }
 
-template <class Pol, bool CPLX>
+template <class Pol, int W, bool CPLX, bool STORE_H>
+static void launch_le(const nqs_ham* ham, const uint64_t* U, const char* stage, const StageHeader& L,
+                      int64_t rb, const RowSched& rs, const int64_t* rp, const uint32_t* pj,
+                      const uint32_t* pk, double* er, double* ei, double* hd, void* hpair, cudaStream_t s) {
+  auto kern = local_energy_kernel<Pol, W, CPLX, STORE_H>;
+  kern<<<grid_for(kern, rs.rows), kEnergyThreads, 0, s>>>(
+      U, ham->row_ptr, ham->yz, ham->coef_f, ham->coef, ham->has_diag, ham->heavy_end,
+      stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK), rb, rs, rp, pj, pk,
+      er, ei, hd, hpair, (int32_t*)(stage + offsetof(StageHeader, status)));
+}
+
+template <class Pol, bool CPLX, bool STORE_H>
 static void launch_le_w(const nqs_ham* ham, const uint64_t* U, const char* stage, const StageHeader& L,
-                        int64_t rb, int64_t re, const int64_t* rp, const uint32_t* pj,
-                        const uint32_t* pk, double* er, double* ei, double* hd, cudaStream_t s) {
+                        int64_t rb, const RowSched& rs, const int64_t* rp, const uint32_t* pj,
+                        const uint32_t* pk, double* er, double* ei, double* hd, void* hpair, cudaStream_t s) {
   switch (ham->W) {
-    case 1: launch_le<Pol, 1, CPLX>(ham, U, stage, L, rb, re, rp, pj, pk, er, ei, hd, s); break;
-    case 2: launch_le<Pol, 2, CPLX>(ham, U, stage, L, rb, re, rp, pj, pk, er, ei, hd, s); break;
-    case 3: launch_le<Pol, 3, CPLX>(ham, U, stage, L, rb, re, rp, pj, pk, er, ei, hd, s); break;
-    default: launch_le<Pol, 4, CPLX>(ham, U, stage, L, rb, re, rp, pj, pk, er, ei, hd, s); break;
+    case 1: launch_le<Pol, 1, CPLX, STORE_H>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s); break;
+    case 2: launch_le<Pol, 2, CPLX, STORE_H>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s); break;
+    case 3: launch_le<Pol, 3, CPLX, STORE_H>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s); break;
+    default: launch_le<Pol, 4, CPLX, STORE_H>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s); break;
+  }
+}
+
+template <class Pol>
+static void launch_le_p(const nqs_ham* ham, const uint64_t* U, const char* stage, const StageHeader& L, bool cplx,
+                        int64_t rb, const RowSched& rs, const int64_t* rp, const uint32_t* pj, const uint32_t* pk,
+                        double* er, double* ei, double* hd, void* hpair, cudaStream_t s) {
+  if (cplx) {
+    if (hpair) launch_le_w<Pol, true, true>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s);
+    else launch_le_w<Pol, true, false>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s);
+  } else {
+    if (hpair) launch_le_w<Pol, false, true>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s);
+    else launch_le_w<Pol, false, false>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s);
   }
 }
 
 cudaError_t launch_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t, const char* stage,
                                 const StageHeader& L, bool cplx, int64_t rb, int64_t re,
                                 const int64_t* rp, const uint32_t* pj, const uint32_t* pk,
-                                int precision, double* er, double* ei, double* hd, cudaStream_t s) {
-  if (precision == NQS_PREC_FP64) {
-    if (cplx) launch_le_w<PolicyD, true>(ham, U, stage, L, rb, re, rp, pj, pk, er, ei, hd, s);
-    else launch_le_w<PolicyD, false>(ham, U, stage, L, rb, re, rp, pj, pk, er, ei, hd, s);
-  } else {
-    if (cplx) launch_le_w<PolicyF, true>(ham, U, stage, L, rb, re, rp, pj, pk, er, ei, hd, s);
-    else launch_le_w<PolicyF, false>(ham, U, stage, L, rb, re, rp, pj, pk, er, ei, hd, s);
-  }
+                                int precision, double* er, double* ei, double* hd, void* hpair,
+                                cudaStream_t s) {
+  if (re <= rb) return cudaSuccess;
+  RowSched rs;
+  cudaError_t e = launch_row_order(rp, re - rb, (char*)stage, L, rs, s);
+  if (e != cudaSuccess) return e;
+  if (precision == NQS_PREC_FP64) launch_le_p<PolicyD>(ham, U, stage, L, cplx, rb, rs, rp, pj, pk, er, ei, hd, hpair, s);
+  else launch_le_p<PolicyF>(ham, U, stage, L, cplx, rb, rs, rp, pj, pk, er, ei, hd, hpair, s);
   return cudaGetLastError();
 }
 
@@ -470,15 +583,19 @@ __device__ __forceinline__ void load_geff(const char* G, int64_t i, typename Pol
 // row y: sum over pairs (y, x), x != y, of ge(x) Re T + gi(x) Im T (and the
 // Im-part analogue) with T = H_yx psi(y)/psi(x) = H_xy psi(y)/psi(x); then the
 // diagonal term D_yy = -(E_loc(y) - H_yy) and g_E 2 w_y (Re E_loc(y) - E).
-template <class Pol, int W, bool CPLX>
+// With LOAD_H the matrix elements come from the forward call's store (one
+// lane per pair, no term loop); otherwise they are recomputed exactly as the
+// forward computes them, so both forms give the same bits.
+template <class Pol, int W, bool CPLX, bool LOAD_H>
 __global__ void __launch_bounds__(kEnergyThreads)
 backward_pairs_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict__ t_ptr,
                       const uint64_t* __restrict__ yz, const float2* __restrict__ cf,
                       const double* __restrict__ cd, int has_diag, int64_t heavy_end,
                       const char* __restrict__ P, const char* __restrict__ Q,
                       const int* __restrict__ K, const char* __restrict__ G,
-                      int64_t row_begin, int64_t row_end, const int64_t* __restrict__ rp,
+                      int64_t row_begin, RowSched rs, const int64_t* __restrict__ rp,
                       const uint32_t* __restrict__ pair_j, const uint32_t* __restrict__ pair_k,
+                      const void* __restrict__ hpair,
                       const double* __restrict__ a, const double* __restrict__ er,
                       const double* __restrict__ ei, const double* __restrict__ hdiag,
                       const double* __restrict__ evar, const double* __restrict__ g_re,
@@ -487,11 +604,9 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict
   using T = typename Pol::T;
   if (*(volatile int32_t*)status & kStatusCapacity) return;  // the pair list was not written
   const int lane = threadIdx.x & 31;
-  const int64_t tw = (int64_t)gridDim.x * kEnergyWarps;
   const double gE = g_evar ? g_evar[0] : 0.0;
   const double E = evar[0], amax = evar[1], S = evar[2];
-  for (int64_t row = (int64_t)blockIdx.x * kEnergyWarps + (threadIdx.x >> 5); row + row_begin < row_end;
-       row += tw) {
+  for (int64_t row = next_row(rs); row >= 0; row = next_row(rs)) {
     const int64_t y = row + row_begin;
     int64_t p = rp[row] - rp[0];
     const int64_t p1 = rp[row + 1] - rp[0];
@@ -501,35 +616,33 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict
       const int64_t q = base + lane;
       const bool have = q < p1;
       const uint32_t j = have ? __ldg(pair_j + q) : 0u;
-      const uint32_t k = have ? __ldg(pair_k + q) : 0u;
-      const bool heavy = have && (int64_t)k < heavy_end;
-      uint32_t hb = __ballot_sync(kFull, heavy);
-      while (hb) {
-        const int src = __ffs(hb) - 1;
-        hb &= hb - 1;
-        const uint32_t jj = __shfl_sync(kFull, j, src);
-        const uint32_t kk = __shfl_sync(kFull, k, src);
-        uint64_t xp[W];
-        load_words<W>(U + (int64_t)jj * W, xp);
-        T part = Pol::fin(melem_part<Pol, W>(xp, (int64_t)__ldg(t_ptr + kk) + lane,
-                                             (int64_t)__ldg(t_ptr + kk + 1), 32, yz, cf, cd));
-        T rr, ri, ge, gi;
-        ratio<Pol, CPLX>(P, Q, K, y, jj, rr, ri, status);
-        load_geff<Pol>(G, jj, ge, gi);
-        const T tr = Pol::mul(part, rr);
-        Pol::acc(da, Pol::mul(ge, tr));
-        if (CPLX) {
-          const T ti = Pol::mul(part, ri);
-          Pol::acc(da, Pol::mul(gi, ti));
-          Pol::acc(db, Pol::neg(Pol::mul(ge, ti)));
-          Pol::acc(db, Pol::mul(gi, tr));
+      T h = Pol::zero();
+      if (LOAD_H) {
+        if (have) h = HStore<Pol>::get(hpair, q);
+      } else {
+        const uint32_t k = have ? __ldg(pair_k + q) : 0u;
+        const bool heavy = have && (int64_t)k < heavy_end;
+        uint32_t hb = __ballot_sync(kFull, heavy);
+        while (hb) {
+          const int src = __ffs(hb) - 1;
+          hb &= hb - 1;
+          const uint32_t jj = __shfl_sync(kFull, j, src);
+          const uint32_t kk = __shfl_sync(kFull, k, src);
+          uint64_t xp[W];
+          load_words<W>(U + (int64_t)jj * W, xp);
+          T part = melem_part<Pol, W>(xp, (int64_t)__ldg(t_ptr + kk) + lane, (int64_t)__ldg(t_ptr + kk + 1), 32,
+                                      yz, cf, cd);
+          part = Pol::warp_sum(part);
+          if (lane == src) h = part;
+        }
+        if (have && !heavy) {
+          uint64_t xp[W];
+          load_words<W>(U + (int64_t)j * W, xp);
+          h = Pol::fin(melem_part<Pol, W>(xp, (int64_t)__ldg(t_ptr + k), (int64_t)__ldg(t_ptr + k + 1), 1, yz, cf,
+                                          cd));
         }
       }
-      if (have && !heavy) {
-        uint64_t xp[W];
-        load_words<W>(U + (int64_t)j * W, xp);
-        T h = Pol::fin(melem_part<Pol, W>(xp, (int64_t)__ldg(t_ptr + k), (int64_t)__ldg(t_ptr + k + 1), 1,
-                                          yz, cf, cd));
+      if (have) {
         T rr, ri, ge, gi;
         ratio<Pol, CPLX>(P, Q, K, y, j, rr, ri, status);
         load_geff<Pol>(G, j, ge, gi);
@@ -557,33 +670,46 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict
   }
 }
 
-template <class Pol, int W, bool CPLX>
-static void launch_bw(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L,
-                      int64_t rb, int64_t re, const int64_t* rp, const uint32_t* pj, const uint32_t* pk,
-                      const double* a, const double* er, const double* ei, const double* hd,
-                      const double* evar, const double* g_re, const double* g_im, const double* g_evar,
-                      double* gre, double* gim, cudaStream_t s) {
-  const int64_t rows = re - rb;
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + kEnergyWarps - 1) / kEnergyWarps,
-                                                                  (int64_t)num_sms() * 8));
-  backward_pairs_kernel<Pol, W, CPLX><<<blocks, kEnergyThreads, 0, s>>>(
+struct BwArgs {
+  const double *a, *er, *ei, *hd, *evar, *g_re, *g_im, *g_evar;
+  double *gre, *gim;
+  const void* hpair;
+};
+
+template <class Pol, int W, bool CPLX, bool LOAD_H>
+static void launch_bw(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L, int64_t rb,
+                      const RowSched& rs, const int64_t* rp, const uint32_t* pj, const uint32_t* pk,
+                      const BwArgs& b, cudaStream_t s) {
+  auto kern = backward_pairs_kernel<Pol, W, CPLX, LOAD_H>;
+  kern<<<grid_for(kern, rs.rows), kEnergyThreads, 0, s>>>(
       U, ham->row_ptr, ham->yz, ham->coef_f, ham->coef, ham->has_diag, ham->heavy_end,
       stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK), stage + L.off_geff,
-      rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim,
+      rb, rs, rp, pj, pk, b.hpair, b.a, b.er, b.ei, b.hd, b.evar, b.g_re, b.g_im, b.g_evar, b.gre, b.gim,
       (int32_t*)(stage + offsetof(StageHeader, status)));
 }
 
-template <class Pol, bool CPLX>
-static void launch_bw_w(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L,
-                        int64_t rb, int64_t re, const int64_t* rp, const uint32_t* pj, const uint32_t* pk,
-                        const double* a, const double* er, const double* ei, const double* hd,
-                        const double* evar, const double* g_re, const double* g_im, const double* g_evar,
-                        double* gre, double* gim, cudaStream_t s) {
+template <class Pol, bool CPLX, bool LOAD_H>
+static void launch_bw_w(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L, int64_t rb,
+                        const RowSched& rs, const int64_t* rp, const uint32_t* pj, const uint32_t* pk,
+                        const BwArgs& b, cudaStream_t s) {
   switch (ham->W) {
-    case 1: launch_bw<Pol, 1, CPLX>(ham, U, stage, L, rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, s); break;
-    case 2: launch_bw<Pol, 2, CPLX>(ham, U, stage, L, rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, s); break;
-    case 3: launch_bw<Pol, 3, CPLX>(ham, U, stage, L, rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, s); break;
-    default: launch_bw<Pol, 4, CPLX>(ham, U, stage, L, rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, s); break;
+    case 1: launch_bw<Pol, 1, CPLX, LOAD_H>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s); break;
+    case 2: launch_bw<Pol, 2, CPLX, LOAD_H>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s); break;
+    case 3: launch_bw<Pol, 3, CPLX, LOAD_H>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s); break;
+    default: launch_bw<Pol, 4, CPLX, LOAD_H>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s); break;
+  }
+}
+
+template <class Pol>
+static void launch_bw_p(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L, bool cplx,
+                        int64_t rb, const RowSched& rs, const int64_t* rp, const uint32_t* pj, const uint32_t* pk,
+                        const BwArgs& b, cudaStream_t s) {
+  if (cplx) {
+    if (b.hpair) launch_bw_w<Pol, true, true>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s);
+    else launch_bw_w<Pol, true, false>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s);
+  } else {
+    if (b.hpair) launch_bw_w<Pol, false, true>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s);
+    else launch_bw_w<Pol, false, false>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s);
   }
 }
 
@@ -592,9 +718,10 @@ cudaError_t launch_backward(const nqs_ham* ham, const uint64_t* U, int64_t n, ch
                             int64_t rb, int64_t re, const int64_t* rp, const uint32_t* pj,
                             const uint32_t* pk, const double* er, const double* ei, const double* hd,
                             const double* evar, const double* g_re, const double* g_im,
-                            const double* g_evar, int precision, double* gre, double* gim,
-                            cudaStream_t s) {
+                            const double* g_evar, int precision, const void* hpair, double* gre,
+                            double* gim, cudaStream_t s) {
   const int64_t rows = re - rb;
+  if (rows <= 0) return cudaSuccess;
   if (!g_re && !g_im) {
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 8 * num_sms()));
     backward_closed_kernel<<<blocks, 256, 0, s>>>(rb, re, a, er, ei, evar, g_evar, gre, gim);
@@ -606,15 +733,15 @@ cudaError_t launch_backward(const nqs_ham* ham, const uint64_t* U, int64_t n, ch
     geff_kernel<<<blocks, 256, 0, s>>>(n, a, evar, g_re, g_im, g_evar, fp64 ? 1 : 0,
                                        (double2*)(stage + L.off_geff), (float4*)(stage + L.off_geff));
   }
-  if (fp64) {
-    if (cplx) launch_bw_w<PolicyD, true>(ham, U, stage, L, rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, s);
-    else launch_bw_w<PolicyD, false>(ham, U, stage, L, rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, s);
-  } else {
-    if (cplx) launch_bw_w<PolicyF, true>(ham, U, stage, L, rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, s);
-    else launch_bw_w<PolicyF, false>(ham, U, stage, L, rb, re, rp, pj, pk, a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, s);
-  }
+  RowSched rs;
+  cudaError_t e = launch_row_order(rp, rows, stage, L, rs, s);
+  if (e != cudaSuccess) return e;
+  const BwArgs b{a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, hpair};
+  if (fp64) launch_bw_p<PolicyD>(ham, U, stage, L, cplx, rb, rs, rp, pj, pk, b, s);
+  else launch_bw_p<PolicyF>(ham, U, stage, L, cplx, rb, rs, rp, pj, pk, b, s);
   return cudaGetLastError();
 }
+
 
 }  // namespace nqs
 

@@ -87,6 +87,7 @@ struct StageHeader {
   int64_t off_trie;     // prefix tree of U (LoopOverTrie)
   int64_t off_hx, off_table, off_bloom, off_scan, off_ampP, off_ampQ, off_ampK, off_geff, off_counters;
   int64_t off_perm, off_rowcur;
+  int64_t off_sched, off_order;   // row schedule of the energy and adjoint kernels
   int64_t scan_blocks;
   int64_t total_bytes;
 };
@@ -155,7 +156,7 @@ cudaError_t launch_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n
                                 const char* stage, const StageHeader& L, bool cplx,
                                 int64_t row_begin, int64_t row_end, const int64_t* row_ptr,
                                 const uint32_t* pair_j, const uint32_t* pair_k, int precision,
-                                double* eloc_re, double* eloc_im, double* hdiag,
+                                double* eloc_re, double* eloc_im, double* hdiag, void* hpair,
                                 cudaStream_t s);
 
 cudaError_t launch_variational_energy(int64_t n, const double* a, const double* eloc_re,
@@ -169,8 +170,8 @@ cudaError_t launch_backward(const nqs_ham* ham, const uint64_t* U, int64_t n_unq
                             const uint32_t* pair_j, const uint32_t* pair_k,
                             const double* eloc_re, const double* eloc_im, const double* hdiag,
                             const double* evar, const double* g_re, const double* g_im,
-                            const double* g_evar, int precision, double* grad_re,
-                            double* grad_im, cudaStream_t s);
+                            const double* g_evar, int precision, const void* hpair,
+                            double* grad_re, double* grad_im, cudaStream_t s);
 
 int num_sms();
 

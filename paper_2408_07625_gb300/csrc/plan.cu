@@ -102,7 +102,7 @@ static cudaError_t enqueue_instance(PlanInstance& I, int precision, cudaStream_t
   }
   if ((e = launch_amplitudes(I.in.logpsi_re, nullptr, n, precision, w, I.L, s)) != cudaSuccess) return e;
   if ((e = launch_local_energy(ham, I.in.U, n, w, I.L, false, 0, n, I.row_ptr, I.pair_j, I.pair_k, precision,
-                               I.in.eloc_re, nullptr, I.hdiag, s)) != cudaSuccess)
+                               I.in.eloc_re, nullptr, I.hdiag, nullptr, s)) != cudaSuccess)
     return e;
   return launch_variational_energy(n, I.in.logpsi_re, I.in.eloc_re, w, I.in.evar, s);
 }

@@ -248,13 +248,17 @@ def test_backward_matches_oracle_vjp(prec):
     pairs_ref = oracle.find_coupled_pairs(inst.U, ref_ham)
     want_re, want_im = oracle.local_energy_vjp(inst.U, lre, lim, ref_ham, pairs_ref, gr, gi, gE)
     ham, batch = gpu_objects(inst)
-    res = nqs.evaluate(batch, lre, lim, prec)
+    res = nqs.evaluate(batch, lre, lim, prec, keep_h=True)
+    up = (torch.from_numpy(gr).cuda(), torch.from_numpy(gi).cuda(), torch.tensor([gE], dtype=torch.float64).cuda())
     g_re, g_im = nqs.local_energy_backward(batch, lre, lim, res["eloc_re"], res["eloc_im"], res["hdiag"],
-                                           res["evar"], torch.from_numpy(gr).cuda(), torch.from_numpy(gi).cuda(),
-                                           torch.tensor([gE], dtype=torch.float64).cuda(), res["pairs"], prec)
+                                           res["evar"], *up, res["pairs"], prec)
     tol = TOL64 if prec == "fp64" else TOL32
     assert np.abs(g_re.cpu().numpy() - want_re).max() < tol
     assert np.abs(g_im.cpu().numpy() - want_im).max() < tol
+    # the matrix elements stored by the forward call give the same bits
+    h_re, h_im = nqs.local_energy_backward(batch, lre, lim, res["eloc_re"], res["eloc_im"], res["hdiag"],
+                                           res["evar"], *up, res["pairs"], prec, hpair=res["hpair"])
+    assert torch.equal(h_re, g_re) and torch.equal(h_im, g_im)
     # closed form (no upstream on E_loc)
     c_re, c_im = nqs.local_energy_backward(batch, lre, lim, res["eloc_re"], res["eloc_im"], res["hdiag"],
                                            res["evar"], None, None,
@@ -376,3 +380,29 @@ def test_edge_cases():
         batch = nqs.Batch(ham, to_dev_u(pack_ints(Ui, n)))
         res = nqs.evaluate(batch, np.zeros(6), None, "fp64")
         assert np.abs(res["eloc_re"].cpu().numpy() - np.array([e.real for e in ref["eloc"]])).max() < TOL64
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_stored_matrix_elements_h28(h28, prec):
+    """hpair holds H of every pair (checked against the oracle on sampled pairs);
+    the adjoint that reads it equals the one that recomputes, bitwise."""
+    inst, ref_ham, ref = h28
+    ham, batch = gpu_objects(inst)
+    res = nqs.evaluate(batch, inst.logpsi_re, None, prec, keep_h=True)
+    rp, pj, pk = res["pairs"]
+    hp = res["hpair"]
+    h = hp.double().cpu().numpy() if prec == "fp64" else hp.double().sum(dim=1).cpu().numpy()
+    rows = np.repeat(np.arange(inst.n_unq), np.diff(rp.cpu().numpy()))
+    jj = pj.cpu().numpy().view(np.uint32)
+    Ui = unpack_ints(inst.U)
+    rng = np.random.default_rng(2)
+    for q in rng.choice(len(jj), 300, replace=False):
+        want = oracle.matrix_element(Ui[rows[q]], Ui[int(jj[q])], ref_ham)
+        assert abs(h[q] - want.real) < (1e-12 if prec == "fp64" else 1e-7) * max(1.0, abs(want))
+    g = torch.from_numpy(np.random.default_rng(3).normal(0, 1e-3, inst.n_unq)).cuda()
+    gE = torch.ones(1, dtype=torch.float64, device="cuda")
+    a = torch.from_numpy(inst.logpsi_re).cuda()
+    args = (batch, a, None, res["eloc_re"], None, res["hdiag"], res["evar"], g, None, gE, res["pairs"], prec)
+    x, _ = nqs.local_energy_backward(*args)
+    y, _ = nqs.local_energy_backward(*args, hpair=hp)
+    assert torch.equal(x, y)

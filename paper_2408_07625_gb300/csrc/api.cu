@@ -46,24 +46,27 @@ StageHeader stage_layout(const nqs_ham* ham, int64_t n) {
   L.n_unq = n;
   L.W = ham->W;
   L.cap = next_pow2(std::max<int64_t>(n, 16));        // buckets of 4 slots, <= 1 key per bucket on average
-  // two filters (one per pass), each for about half of the samples
-  L.nwords = std::min<int64_t>(std::max<int64_t>(next_pow2(std::max<int64_t>(n / 4, 1)), 32), 32768);
+  // one filter of all samples: about two keys per word, at most 128 KB (shared memory of the search)
+  L.nwords = std::min<int64_t>(std::max<int64_t>(next_pow2(std::max<int64_t>(n / 2, 1)), 32), 32768);
+  const int64_t n1 = std::max<int64_t>(n, 1);
   int64_t off = align256(kRedOffset + kRedBytes);
-  L.off_hx = off;     off = align256(off + 4 * std::max<int64_t>(n, 1));
+  L.off_hx = off;     off = align256(off + 4 * n1);
   L.off_table = off;  off = align256(off + 32 * L.cap);
-  L.off_bloom = off;  off = align256(off + 2 * 4 * L.nwords);
-  L.scan_blocks = (std::max<int64_t>(n, 1) + 1023) / 1024 + 1;
+  L.off_bloom = off;  off = align256(off + 4 * L.nwords);
+  L.scan_blocks = (n1 + 1023) / 1024 + 1;
   L.off_scan = off;   off = align256(off + 8 * L.scan_blocks);
-  L.off_ampP = off;   off = align256(off + 16 * std::max<int64_t>(n, 1));
-  L.off_ampQ = off;   off = align256(off + 16 * std::max<int64_t>(n, 1));
-  L.off_ampK = off;   off = align256(off + 4 * std::max<int64_t>(n, 1));
-  L.off_geff = off;   off = align256(off + 16 * std::max<int64_t>(n, 1));
+  L.off_ampP = off;   off = align256(off + 16 * n1);
+  L.off_ampQ = off;   off = align256(off + 16 * n1);
+  L.off_ampK = off;   off = align256(off + 4 * n1);
+  L.off_geff = off;   off = align256(off + 16 * n1);
   L.off_counters = off; off = align256(off + 256);
-  L.off_perm = off;   off = align256(off + 2 * 4 * std::max<int64_t>(n, 1));
-  L.off_rowcur = off; off = align256(off + 8 * std::max<int64_t>(n, 1));
+  L.off_q = off;      off = align256(off + 2 * 4 * 64 * kMaxWords);
+  L.off_qrows = off;  off = align256(off + 4 * n1 * (int64_t)ham->n_qubits);
+  L.off_big = off;    off = align256(off + 4 * n1);
+  L.off_rowcur = off; off = align256(off + 4 * n1);
   L.off_trie = off;   off = align256(off + trie_bytes(ham->W, n));
   L.off_sched = off;  off = align256(off + 512);
-  L.off_order = off;  off = align256(off + 4 * std::max<int64_t>(n, 1));
+  L.off_order = off;  off = align256(off + 4 * n1);
   L.total_bytes = off;
   return L;
 }
@@ -113,7 +116,7 @@ static void free_ham(nqs_ham* h) {
   if (!h) return;
   cudaFree(h->xy); cudaFree(h->row_ptr); cudaFree(h->yz); cudaFree(h->coef);
   cudaFree(h->coef_f); cudaFree(h->srch_hash); cudaFree(h->srch_id); cudaFree(h->srch_rec); cudaFree(h->hash_basis);
-  cudaFree(h->xy_table); cudaFree(h->wmask); cudaFree(h->xy_trie); cudaFree(h->xy_hash);
+  cudaFree(h->xy_table); cudaFree(h->wmask); cudaFree(h->xy_trie); cudaFree(h->xy_hash); cudaFree(h->segs);
   delete h;
 }
 
@@ -257,46 +260,63 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
     hxy[p] = v;
   }
 
-  // search table: non-diagonal patterns, class by class; inside a class each
-  // group of 32 slots holds patterns with 32 distinct (hash & 31) values, so
-  // the 32 lanes of a warp probing one sample touch 32 distinct shared-memory
-  // banks of the membership filter.
+  // search table of the oriented LoopOverTerms search: the non-diagonal
+  // patterns grouped by their highest set qubit t (a pair {x, x'} with
+  // x ^ x' = XY is searched from the one of the two with bit t set), one
+  // segment per t, largest first.  A segment is cut into groups of 32 slots
+  // holding at most two patterns per hash residue mod 32, so the 32 lanes of
+  // a warp probing one sample touch each shared-memory bank of the
+  // membership filter at most twice; short groups are padded with dummy slots.
   std::vector<uint32_t> srch_hash, srch_id;
   std::vector<uint64_t> srch_rec;
   h->rec_words = 2 * ((1 + W + 1) / 2);
-  // The table is split in two halves by the top hash bit t = hash >> 31: a
-  // row x probes half t in the pass that holds the samples whose top hash bit
-  // is (h(x) >> 31) ^ t, so every (row, pattern) pair is probed exactly once.
-  auto build_class = [&](int64_t lo, int64_t hi, uint32_t half) {
-    std::vector<std::vector<uint32_t>> buckets(32);
-    for (int64_t p = lo; p < hi; ++p)
-      if ((hxy[p] >> 31) == half) buckets[hxy[p] & 31].push_back((uint32_t)p);
-    size_t Gc = 0;
-    for (auto& b : buckets) Gc = std::max(Gc, b.size());
-    for (size_t g = 0; g < Gc; ++g)
-      for (int b = 0; b < 32; ++b) {
-        if (g < buckets[b].size()) {
-          uint32_t id = buckets[b][g];
+  std::vector<std::vector<uint32_t>> by_top(64 * W);
+  for (int64_t p = h->has_diag; p < G; ++p) {
+    int top = -1;
+    for (int w = W - 1; w >= 0 && top < 0; --w)
+      if (h->h_xy[p * W + w]) top = 64 * w + 63 - __builtin_clzll(h->h_xy[p * W + w]);
+    by_top[top].push_back((uint32_t)p);
+  }
+  std::vector<int> tord;
+  for (int t = 0; t < 64 * W; ++t)
+    if (!by_top[t].empty()) tord.push_back(t);
+  std::stable_sort(tord.begin(), tord.end(), [&](int a, int b) { return by_top[a].size() > by_top[b].size(); });
+  std::vector<int4> segs;
+  for (int t : tord) {
+    // striping the patterns, ordered by residue, over G groups puts at most
+    // ceil(|residue class| / G) <= 2 of a residue into each group
+    std::vector<uint32_t> pats = by_top[t];
+    std::stable_sort(pats.begin(), pats.end(), [&](uint32_t a, uint32_t b) { return (hxy[a] & 31) < (hxy[b] & 31); });
+    size_t maxb = 0;
+    {
+      size_t cnt[32] = {0};
+      for (uint32_t p : pats) maxb = std::max(maxb, ++cnt[hxy[p] & 31]);
+    }
+    const size_t Gs = std::max((pats.size() + 31) / 32, (maxb + 1) / 2);
+    std::vector<std::vector<uint32_t>> groups(Gs);
+    for (size_t q = 0; q < pats.size(); ++q) groups[q % Gs].push_back(pats[q]);
+    const int64_t g0 = (int64_t)srch_hash.size() / 32;
+    for (auto& grp : groups) {
+      for (int l = 0; l < 32; ++l) {
+        if (l < (int)grp.size()) {
+          const uint32_t id = grp[l];
           srch_hash.push_back(hxy[id]);
           srch_id.push_back(id);
           srch_rec.push_back((uint64_t)hxy[id] | ((uint64_t)id << 32));
           for (int w = 0; w < W; ++w) srch_rec.push_back(h->h_xy[(int64_t)id * W + w]);
           for (int w = 1 + W; w < h->rec_words; ++w) srch_rec.push_back(0);
         } else {
-          const uint32_t dh = (uint32_t)b | (half << 31);
+          const uint32_t dh = (uint32_t)l;
           srch_hash.push_back(dh);
           srch_id.push_back(kDummy);
           srch_rec.push_back((uint64_t)dh | ((uint64_t)kDummy << 32));
           for (int w = 1; w < h->rec_words; ++w) srch_rec.push_back(0);
         }
       }
-  };
-  for (uint32_t half = 0; half < 2; ++half) {
-    h->half_begin[half] = (int64_t)srch_hash.size() / 32;
-    build_class(h->has_diag, h->heavy_end, half);
-    build_class(h->heavy_end, G, half);
-    h->half_end[half] = (int64_t)srch_hash.size() / 32;
+    }
+    segs.push_back(make_int4(t, (int)g0, (int)(srch_hash.size() / 32), 0));
   }
+  h->n_segs = (int)segs.size();
   h->n_srch = (int64_t)srch_hash.size();
 
   // XY hash set for the batch schedule (Alg. 2B): same linear hash, so the
@@ -332,7 +352,7 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
       (rc = upload(&h->srch_id, srch_id)) || (rc = upload(&h->srch_rec, srch_rec)) ||
       (rc = upload(&h->hash_basis, h->h_hash_basis)) || (rc = upload(&h->xy_table, xy_table)) ||
       (rc = upload(&h->wmask, wmask)) || (rc = upload(&h->xy_trie, xy_trie)) ||
-      (rc = upload(&h->xy_hash, hxy))) {
+      (rc = upload(&h->xy_hash, hxy)) || (rc = upload(&h->segs, segs))) {
     free_ham(h);
     return rc;
   }
@@ -408,8 +428,6 @@ int nqs_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, int6
   char* base = (char*)work;
   cudaError_t e = cudaMemcpyAsync(base, &L, sizeof(L), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e, "header copy");
-  if ((e = cudaMemsetAsync(base + L.off_table, 0xFF, 32 * L.cap, s)) != cudaSuccess) return cuda_fail(e, "memset");
-  if ((e = cudaMemsetAsync(base + L.off_bloom, 0, 2 * 4 * L.nwords, s)) != cudaSuccess) return cuda_fail(e, "memset");
   if ((e = cudaMemsetAsync(base + kRedOffset, 0, 256, s)) != cudaSuccess) return cuda_fail(e, "memset");
   if ((e = launch_stage(ham, U, n, base, L, s)) != cudaSuccess) return cuda_fail(e, "stage kernel");
   if (check) return read_status(work, s);
@@ -453,13 +471,13 @@ static int pick_schedule(const nqs_ham* ham, int64_t n, int schedule) {
   return (n < ham->n_xy) ? NQS_SCHED_BATCH : NQS_SCHED_TERMS;
 }
 
-static cudaError_t launch_search(const nqs_ham* ham, const uint64_t* U, int64_t n, const char* work,
+static cudaError_t launch_search(const nqs_ham* ham, const uint64_t* U, int64_t n, char* work,
                                  const StageHeader& L, int64_t rb, int64_t re, int schedule,
                                  int64_t* rp, uint32_t* pj, uint32_t* pk, int mode,
                                  const PairScratch* sc, cudaStream_t s) {
   const int sched = pick_schedule(ham, n, schedule);
   if (sched == NQS_SCHED_BATCH)
-    return launch_pairs_batch(ham, U, n, work, L, rb, re, rp, pj, pk, mode, sc, s);
+    return launch_pairs_batch(ham, U, n, work, L, rb, re, rp, pj, pk, mode == kFill ? kFill : kCount, s);
   if (sched == NQS_SCHED_TRIE)
     return launch_pairs_trie(ham, U, n, work, L, rb, re, rp, pj, pk, mode == kFill ? kFill : kCount, s);
   return launch_pairs_terms(ham, U, work, L, rb, re, rp, pj, pk, mode, sc, s);
@@ -534,7 +552,7 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
   }
   if (((uintptr_t)scratch) & 255) return fail(NQS_ERR_ARG, "scratch not 256-byte aligned");
   PairScratch sc = pair_scratch_view(scratch, rows, scratch_bytes);
-  if (sc.max_chunks < 1) return fail(NQS_ERR_CAPACITY, "scratch too small");
+  if (sc.max_rec < 1) return fail(NQS_ERR_CAPACITY, "scratch too small");
   if ((rc = count_pass(ham, U, n, work, L, rb, re, schedule, row_ptr, &sc, s))) return rc;
   int64_t overflow = 0;
   cudaError_t e = cudaMemcpyAsync(n_pairs, row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
@@ -546,7 +564,7 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
   if (*n_pairs > capacity) return fail(NQS_ERR_CAPACITY, "pair capacity too small");
   if (rows == 0 || *n_pairs == 0) return NQS_OK;
   if (!pair_j || !pair_k) return fail(NQS_ERR_ARG, "null pair arrays");
-  e = launch_pairs_compact(sc, (const char*)work, L, rb, rows, row_ptr, pair_j, pair_k, capacity, s);
+  e = launch_pairs_compact(ham, sc, (char*)work, L, rb, rows, row_ptr, pair_j, pair_k, capacity, s);
   if (e != cudaSuccess) return cuda_fail(e, "compaction kernel");
   return NQS_OK;
 }

@@ -1,13 +1,24 @@
-// Sample staging and FindCoupledPairs, LoopOverTerms schedule (Alg. 2A).
+// Sample staging and FindCoupledPairs: LoopOverTerms (Alg. 2A) and
+// LoopOverBatch (Alg. 2B).
 //
-// Membership test "x' in U" (Alg. 2A): a GF(2)-linear 32-bit hash
+// Membership test "x' in U" (Algs. 2A, 2B): a GF(2)-linear 32-bit hash
 // h(v) = XOR_{b in v} R[b] makes the hash of a candidate x' = x XOR XY one XOR
-// of two precomputed values, h(x) ^ h(XY).  A blocked Bloom filter of U
-// (one 32-bit word per key, two bits set) lives in shared memory and rejects
-// most candidates; survivors are verified in a bucketed table of U resident
-// in L2: 32-byte buckets of four (hash tag, index) slots, at most one key per
-// bucket on average, so a miss reads one sector; only a tag match reads the
-// sample itself for the exact comparison.
+// of two precomputed values, h(x) ^ h(XY).  A blocked Bloom filter of U (one
+// 32-bit word per key, two bits set) lives in shared memory and rejects most
+// candidates; survivors are verified in a bucketed table of U resident in L2:
+// 32-byte buckets of four (hash tag, index) slots, at most one key per bucket
+// on average, so a miss reads one sector; only a tag match reads the sample.
+//
+// Oriented LoopOverTerms.  x XOR x' = XY is symmetric, so a coupled pair
+// {x, x'} with x != x' needs to be found once: from the one of the two that
+// has XY's highest set qubit t (exactly one of them has it).  The search table
+// is grouped by t and staging lists, per qubit t, the samples with bit t set;
+// a work item probes 8 samples of one list against the patterns of the
+// matching group.  For peaked molecular batches high qubits are rarely
+// occupied, which cuts the probes by an order of magnitude against probing
+// every (sample, pattern).  Each pair found is written to both of its rows,
+// and each row is then sorted by pattern index, so the list of a row (the
+// diagonal pair first, then ascending pattern index) depends on the row alone.
 #include <cstring>
 
 #include "device_util.cuh"
@@ -16,24 +27,54 @@
 namespace nqs {
 
 // --------------------------------------------------------------------------
-// staging: hash of each sample, keyed hash table and Bloom filter of U
-// table slot = W key words followed by the sample index (all ones: empty)
+// staging: hash of each sample, bucketed table and Bloom filter of U, and the
+// number of samples with each qubit set
 // --------------------------------------------------------------------------
+
+// lane b of the warp adds, for each 32-qubit slice c, the number of the warp's
+// samples with qubit 32 c + b set (one ballot per qubit)
+template <int W>
+__device__ __forceinline__ void count_qubits(const uint64_t (&v)[W], uint32_t (&mine)[2 * W]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int w = 0; w < W; ++w)
+#pragma unroll
+    for (int b = 0; b < 64; ++b) {
+      const uint32_t c = __popc(__ballot_sync(kFull, (uint32_t)(v[w] >> b) & 1u));
+      mine[2 * w + (b >> 5)] += (lane == (b & 31)) ? c : 0u;
+    }
+}
+
 template <int W>
 __global__ void stage_kernel(const uint64_t* __restrict__ U, int64_t n, int n_qubits,
                              const uint32_t* __restrict__ basis, int64_t cap, uint32_t wmask,
                              uint32_t* __restrict__ hx_out, unsigned long long* __restrict__ table,
-                             uint32_t* __restrict__ bloom, int32_t* __restrict__ status) {
+                             uint32_t* __restrict__ bloom, uint32_t* __restrict__ qcnt,
+                             int32_t* __restrict__ status) {
   __shared__ uint32_t R[64 * W];
-  for (int i = threadIdx.x; i < 64 * W; i += blockDim.x) R[i] = basis[i];
+  __shared__ uint32_t qc[64 * W];
+  for (int i = threadIdx.x; i < 64 * W; i += blockDim.x) {
+    R[i] = basis[i];
+    qc[i] = 0u;
+  }
   __syncthreads();
+  const int lane = threadIdx.x & 31;
   const int tail = n_qubits - 64 * (W - 1);
   const uint64_t tail_mask = tail == 64 ? ~0ull : ((1ull << tail) - 1);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  uint32_t mine[2 * W];
+#pragma unroll
+  for (int c = 0; c < 2 * W; ++c) mine[c] = 0u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
+    const int64_t i = i0 + lane;
+    const bool valid = i < n;
     uint64_t v[W];
-    load_words<W>(U + i * W, v);
+#pragma unroll
+    for (int w = 0; w < W; ++w) v[w] = valid ? __ldg(U + i * W + w) : 0ull;
     if (v[W - 1] & ~tail_mask) atomicOr(status, kStatusBadBits);
+    v[W - 1] &= tail_mask;  // bits >= N are an error (reported); the lists never hold them
+    count_qubits<W>(v, mine);
+    if (!valid) continue;
     uint32_t h = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
@@ -45,13 +86,13 @@ __global__ void stage_kernel(const uint64_t* __restrict__ U, int64_t n, int n_qu
       }
     }
     hx_out[i] = h;
-    const unsigned long long mine = (unsigned long long)h | ((unsigned long long)i << 32);
+    const unsigned long long key = (unsigned long long)h | ((unsigned long long)i << 32);
     int64_t b = h & (cap - 1);
     bool placed = false;
     for (int64_t it = 0; it < cap && !placed; ++it) {
       unsigned long long* bk = table + b * 4;
       for (int k = 0; k < 4; ++k) {
-        const unsigned long long prev = atomicCAS(bk + k, ~0ull, mine);
+        const unsigned long long prev = atomicCAS(bk + k, ~0ull, key);
         if (prev == ~0ull) { placed = true; break; }
         if ((uint32_t)prev == h) {  // same tag: compare the samples themselves
           const int64_t o = (int64_t)(prev >> 32);
@@ -64,71 +105,160 @@ __global__ void stage_kernel(const uint64_t* __restrict__ U, int64_t n, int n_qu
       b = (b + 1) & (cap - 1);
     }
     if (!placed) atomicOr(status, kStatusLimit);
-    atomicOr(&bloom[(int64_t)(h >> 31) * (wmask + 1) + (h & wmask)], bloom_bits(h));
+    atomicOr(&bloom[h & wmask], bloom_bits(h));
+  }
+#pragma unroll
+  for (int c = 0; c < 2 * W; ++c)
+    if (mine[c]) atomicAdd(&qc[32 * c + lane], mine[c]);
+  __syncthreads();
+  for (int q = threadIdx.x; q < 64 * W; q += blockDim.x)
+    if (qc[q]) atomicAdd(&qcnt[q], qc[q]);
+}
+
+// Per-qubit lists: the samples with bit q set, for every qubit q.  Each block
+// takes a contiguous slice of U, counts its samples per qubit, reserves that
+// many places in each list (one atomic per qubit and block), then writes the
+// samples (warp-aggregated positions; the order inside a list is irrelevant).
+template <int W>
+__global__ void qubit_rows_kernel(const uint64_t* __restrict__ U, int64_t n, int n_qubits, int64_t per_block,
+                                  const uint32_t* __restrict__ qcnt, uint32_t* __restrict__ qcur,
+                                  uint32_t* __restrict__ qrows) {
+  __shared__ int64_t base[64 * W];
+  __shared__ uint32_t cnt[64 * W];
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  const int64_t s0 = (int64_t)blockIdx.x * per_block;
+  const int64_t s1 = s0 + per_block < n ? s0 + per_block : n;
+  const int tail = n_qubits - 64 * (W - 1);
+  const uint64_t tail_mask = tail == 64 ? ~0ull : ((1ull << tail) - 1);
+  for (int q = threadIdx.x; q < 64 * W; q += blockDim.x) cnt[q] = 0u;
+  __syncthreads();
+  uint32_t mine[2 * W];
+#pragma unroll
+  for (int c = 0; c < 2 * W; ++c) mine[c] = 0u;
+  for (int64_t i0 = s0 + (threadIdx.x & ~31); i0 < s1; i0 += blockDim.x) {
+    const int64_t i = i0 + lane;
+    uint64_t v[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) v[w] = i < s1 ? __ldg(U + i * W + w) : 0ull;
+    v[W - 1] &= tail_mask;
+    count_qubits<W>(v, mine);
+  }
+#pragma unroll
+  for (int c = 0; c < 2 * W; ++c)
+    if (mine[c]) atomicAdd(&cnt[32 * c + lane], mine[c]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t run = 0;
+    for (int q = 0; q < 64 * W; ++q) {
+      base[q] = run;
+      run += qcnt[q];
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 64 * W; q += blockDim.x) {
+    if (cnt[q]) base[q] += atomicAdd(&qcur[q], cnt[q]);
+    cnt[q] = 0u;
+  }
+  __syncthreads();
+  for (int64_t i0 = s0 + (threadIdx.x & ~31); i0 < s1; i0 += blockDim.x) {
+    const int64_t i = i0 + lane;
+    uint64_t v[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) v[w] = i < s1 ? __ldg(U + i * W + w) : 0ull;
+    v[W - 1] &= tail_mask;
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+#pragma unroll 4
+      for (int b = 0; b < 64; ++b) {
+        const bool set = (v[w] >> b) & 1ull;
+        const uint32_t m = __ballot_sync(kFull, set);
+        if (m == 0u) continue;
+        uint32_t at = 0u;
+        if (lane == __ffs(m) - 1) at = atomicAdd(&cnt[64 * w + b], (uint32_t)__popc(m));
+        at = __shfl_sync(kFull, at, __ffs(m) - 1);
+        if (set) qrows[base[64 * w + b] + at + __popc(m & lt)] = (uint32_t)i;
+      }
   }
 }
 
 cudaError_t launch_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, char* stage,
                          const StageHeader& L, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(stage + L.off_table, 0xFF, 32 * L.cap, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(stage + L.off_bloom, 0, 4 * L.nwords, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(stage + L.off_q, 0, 2 * 4 * 64 * kMaxWords, s)) != cudaSuccess) return e;
   if (n == 0) return cudaSuccess;
-  int blocks = (int)std::min<int64_t>((n + 255) / 256, 4 * num_sms());
   auto* hx = (uint32_t*)(stage + L.off_hx);
   auto* table = (unsigned long long*)(stage + L.off_table);
   auto* bloom = (uint32_t*)(stage + L.off_bloom);
   auto* status = (int32_t*)(stage + offsetof(StageHeader, status));
-  uint32_t wmask = (uint32_t)(L.nwords - 1);
+  auto* qcnt = (uint32_t*)(stage + L.off_q);
+  auto* qcur = qcnt + 64 * kMaxWords;
+  auto* qrows = (uint32_t*)(stage + L.off_qrows);
+  const uint32_t wmask = (uint32_t)(L.nwords - 1);
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4 * num_sms());
+  const int qblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 2047) / 2048, 2 * num_sms()));
+  const int64_t per_block = (((n + qblocks - 1) / qblocks) + 31) & ~int64_t(31);
+#define NQS_STAGE(WW)                                                                                    \
+  case WW:                                                                                               \
+    stage_kernel<WW><<<blocks, 256, 0, s>>>(U, n, ham->n_qubits, ham->hash_basis, L.cap, wmask, hx,      \
+                                            table, bloom, qcnt, status);                                 \
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;                                               \
+    qubit_rows_kernel<WW><<<qblocks, 256, 0, s>>>(U, n, ham->n_qubits, per_block, qcnt, qcur, qrows);                   \
+    break;
   switch (ham->W) {
-    case 1: stage_kernel<1><<<blocks, 256, 0, s>>>(U, n, ham->n_qubits, ham->hash_basis, L.cap, wmask, hx, table, bloom, status); break;
-    case 2: stage_kernel<2><<<blocks, 256, 0, s>>>(U, n, ham->n_qubits, ham->hash_basis, L.cap, wmask, hx, table, bloom, status); break;
-    case 3: stage_kernel<3><<<blocks, 256, 0, s>>>(U, n, ham->n_qubits, ham->hash_basis, L.cap, wmask, hx, table, bloom, status); break;
-    default: stage_kernel<4><<<blocks, 256, 0, s>>>(U, n, ham->n_qubits, ham->hash_basis, L.cap, wmask, hx, table, bloom, status); break;
+    NQS_STAGE(1)
+    NQS_STAGE(2)
+    NQS_STAGE(3)
+    default:
+    NQS_STAGE(4)
   }
+#undef NQS_STAGE
   return cudaGetLastError();
 }
 
 // --------------------------------------------------------------------------
-// one-pass scratch: linked chunks of pair records per row batch
+// one-pass scratch: three uint32 arrays of found pairs (i, j, k)
 // --------------------------------------------------------------------------
 static inline int64_t a256(int64_t v) { return (v + 255) & ~int64_t(255); }
 
-static inline int64_t nb_max(int64_t rows) { return (rows + kRowsPerWarp - 1) / kRowsPerWarp + 2; }
-
 int64_t pair_scratch_bytes(int64_t rows, int64_t max_pairs) {
-  const int64_t nb = nb_max(rows);
-  const int64_t chunks = (max_pairs + kChunk - 1) / kChunk + 2 * nb;
-  return 256 + a256(16 * nb) + a256(4 * chunks) + 8 * kChunk * chunks;
+  (void)rows;  // a record serves at most two rows and at least one of the range
+  return 256 + 3 * a256(4 * std::max<int64_t>(max_pairs, 1));
 }
 
 PairScratch pair_scratch_view(void* base, int64_t rows, int64_t bytes) {
+  (void)rows;
   PairScratch sc;
-  const int64_t nb = nb_max(rows);
   char* p = (char*)base;
   sc.cursor = (int64_t*)p;
-  sc.heads = (int32_t*)(p + 256);
-  int64_t rest = bytes - 256 - a256(16 * nb);
-  int64_t chunks = rest / (4 + 8 * kChunk);
-  while (chunks > 0 && a256(4 * chunks) + 8 * kChunk * chunks > rest) --chunks;
-  sc.max_chunks = std::max<int64_t>(chunks, 0);
-  sc.next = (int32_t*)(p + 256 + a256(16 * nb));
-  sc.records = (uint64_t*)((char*)sc.next + a256(4 * std::max<int64_t>(sc.max_chunks, 1)));
+  int64_t m = (bytes - 256) / 12;
+  while (m > 0 && 3 * a256(4 * m) > bytes - 256) --m;
+  sc.max_rec = std::max<int64_t>(m, 0);
+  const int64_t stride = a256(4 * std::max<int64_t>(sc.max_rec, 1));
+  sc.rec_i = (uint32_t*)(p + 256);
+  sc.rec_j = (uint32_t*)(p + 256 + stride);
+  sc.rec_k = (uint32_t*)(p + 256 + 2 * stride);
   return sc;
 }
 
 // --------------------------------------------------------------------------
-// LoopOverTerms search.  A warp owns a batch of kRowsPerWarp rows (taken from
-// a global counter) and streams the search table: lane t takes slot 32g + t.
-// The 32 slots of a group have distinct low hash bits, so the 32 Bloom-word
-// loads of one row hit 32 distinct shared-memory banks.  Per slot a lane keeps
-// a bit mask of the rows whose filter test passed; groups with a hit append
-// one (row, slot) entry per passed test to a per-warp queue (warp prefix sum),
-// so a row's candidates stay in slot order whatever the other rows of its
-// batch do.  A full queue is verified lane-parallel against the hash table.
+// Oriented LoopOverTerms search.  A warp takes work items from a global
+// counter; item = (segment s of the search table, 8 consecutive entries of
+// the list of samples with bit t_s set).  Lane t scans slot 32 g + t of each
+// group g of the segment; the 32 slots of a group have at most two patterns
+// per hash residue mod 32, so the 32 Bloom-word loads of one row touch each
+// shared-memory bank at most twice.  Per slot a lane keeps a bit mask of the
+// rows whose filter test passed; slots with a hit go to a per-warp queue,
+// which is verified lane-parallel against the hash table when full.
 // --------------------------------------------------------------------------
 constexpr int kSearchThreads = 1024;
 constexpr int kSearchWarps = kSearchThreads / 32;
 constexpr int R = kRowsPerWarp;
+constexpr int kMaxSegs = 64 * kMaxWords;
 
-struct SearchArgs {
+struct TermsArgs {
   const uint64_t* U;
   const uint32_t* hx;
   const unsigned long long* table;
@@ -139,98 +269,81 @@ struct SearchArgs {
   const uint32_t* srch_hash;
   const uint64_t* srch_rec;
   int rec_words;
-  int64_t n_groups;
-  int has_diag;
+  const int4* segs;
+  int n_segs;
+  int nq;
+  const uint32_t* qcnt;
+  const uint32_t* qrows;
   int64_t row_begin, row_end;
-  int64_t* rp;
+  int64_t* counts;        // COUNT / EMIT: per-row counts of the range
+  const int64_t* rp;      // FILL: CSR offsets of the range
+  int32_t* cursor;        // FILL: per-row write cursors
   uint32_t* pair_j;
   uint32_t* pair_k;
+  PairScratch sc;         // EMIT
   int32_t* status;
-  unsigned long long* batch_counter;
-  PairScratch sc;
-  // two-pass filtering: rows of each class (top hash bit) in perm, pass index
-  int pass;
-  const int32_t* perm;
-  int64_t perm_stride;
-  const unsigned long long* cls_cnt;
-  int64_t g_begin[2], g_end[2];
-  int64_t* rowcur;
-  int64_t nbm;
-};
-
-struct EmitState {  // warp-uniform chunk state of the one-pass mode
-  int32_t chunk, fill, first, total;
+  unsigned long long* item_counter;
 };
 
 template <int W>
-struct RowCache {   // per-warp copy of the batch's rows (shared memory)
+struct RowCache {   // per-warp copy of the item's rows (shared memory)
   uint64_t u[R][W];
   uint32_t hx[R];
   uint32_t cnt[R];
   int64_t row[R];
 };
 
-// Emit one round of verified candidates (lane order).  COUNT/EMIT count per
-// row with shared-memory atomics; FILL places pairs at per-row ranks; EMIT
-// appends records to the warp's current scratch chunk.
-template <int MODE, int W>
-__device__ __forceinline__ void emit_round(bool found, int r, uint32_t j, uint32_t id,
-                                           int64_t (&acc)[R], EmitState& es, RowCache<W>* rc,
-                                           const SearchArgs& a) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t lt = (1u << lane) - 1u;
-  if (MODE == kFill) {
-#pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
-      const uint32_t m = __ballot_sync(kFull, found && r == rr);
-      if (found && r == rr) {
-        const int64_t p = acc[rr] + __popc(m & lt);
-        a.pair_j[p] = j;
-        a.pair_k[p] = id;
-      }
-      acc[rr] += __popc(m);
-    }
-    return;
-  }
-  if (found) atomicAdd(&rc->cnt[r], 1u);
-  if (MODE == kEmit) {
-    const uint32_t m = __ballot_sync(kFull, found);
-    const int n = __popc(m);
-    if (n == 0 || es.chunk == -2) return;
-    es.total += n;
-    const int off = __popc(m & lt);
-    const uint64_t rec = (uint64_t)j | ((uint64_t)id << 32) | ((uint64_t)r << 61);
-    const int room = es.chunk >= 0 ? kChunk - es.fill : 0;
-    if (n <= room) {
-      if (found) a.sc.records[(int64_t)es.chunk * kChunk + es.fill + off] = rec;
-      es.fill += n;
-      return;
-    }
-    int32_t fresh = -2;
-    if (lane == 0) {
-      const unsigned long long c = atomicAdd((unsigned long long*)a.sc.cursor, 1ull);
-      if ((int64_t)c < a.sc.max_chunks) {
-        fresh = (int32_t)c;
-        if (es.chunk >= 0) a.sc.next[es.chunk] = fresh;
-      } else {
-        atomicOr((unsigned long long*)(a.sc.cursor + 1), 1ull);
-      }
-    }
-    fresh = __shfl_sync(kFull, fresh, 0);
-    if (found) {
-      if (off < room) a.sc.records[(int64_t)es.chunk * kChunk + es.fill + off] = rec;
-      else if (fresh >= 0) a.sc.records[(int64_t)fresh * kChunk + (off - room)] = rec;
-    }
-    if (fresh >= 0 && es.first < 0) es.first = fresh;
-    es.chunk = fresh;
-    es.fill = n - room;
+// Place one pair in row r (relative to the range) at the row's next free
+// position; a row that is already full (counts that do not match this
+// search, e.g. a changed batch) flags the status instead of writing past it.
+__device__ __forceinline__ void place_pair(const int64_t* rp, int64_t r, int32_t* cursor, uint32_t* pj,
+                                           uint32_t* pk, uint32_t col, uint32_t k, int32_t* status) {
+  const int64_t a = rp[r] - rp[0];
+  const int64_t len = rp[r + 1] - rp[r];
+  const int64_t c = atomicAdd(cursor + r, 1);
+  if (c < len) {
+    pj[a + c] = col;
+    pk[a + c] = k;
+  } else {
+    atomicOr(status, kStatusLimit);
   }
 }
 
-// Verification of queued candidates: each lane takes several entries at a
-// time so their loads overlap (search record, then hash-table slot).
-template <int W>
-struct FlushWays { static constexpr int value = W == 1 ? 2 : 1; };
+// One round of verified candidates (lane order).  The pair (i, j) with
+// i = the item's row r is listed in row i and in row j.
+template <int MODE, int W>
+__device__ __forceinline__ void emit_found(bool found, int r, uint32_t j, uint32_t id, RowCache<W>* rc,
+                                           const TermsArgs& a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = found ? rc->row[r] : -1;
+  const bool in_i = found && i >= a.row_begin && i < a.row_end;
+  const bool in_j = found && (int64_t)j >= a.row_begin && (int64_t)j < a.row_end;
+  if (MODE == kFill) {
+    if (in_i) place_pair(a.rp, i - a.row_begin, a.cursor, a.pair_j, a.pair_k, j, id, a.status);
+    if (in_j) place_pair(a.rp, (int64_t)j - a.row_begin, a.cursor, a.pair_j, a.pair_k, (uint32_t)i, id, a.status);
+    return;
+  }
+  if (in_i) atomicAdd(&rc->cnt[r], 1u);
+  if (in_j) atomicAdd((unsigned long long*)(a.counts + ((int64_t)j - a.row_begin)), 1ull);
+  if (MODE == kEmit) {
+    const bool keep = in_i || in_j;
+    const uint32_t m = __ballot_sync(kFull, keep);
+    if (m == 0u) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd((unsigned long long*)a.sc.cursor, (unsigned long long)__popc(m));
+    base = __shfl_sync(kFull, base, 0);
+    if (keep) {
+      const int64_t q = (int64_t)base + __popc(m & ((1u << lane) - 1u));
+      if (q < a.sc.max_rec) {
+        a.sc.rec_i[q] = (uint32_t)i;
+        a.sc.rec_j[q] = j;
+        a.sc.rec_k[q] = id;
+      } else {
+        a.sc.cursor[1] = 1;
+      }
+    }
+  }
+}
 
 template <int W>
 __device__ __forceinline__ void load_slot(const unsigned long long* sl, unsigned long long (&v)[W + 1]) {
@@ -245,10 +358,10 @@ __device__ __forceinline__ void load_slot(const unsigned long long* sl, unsigned
 }
 
 // Exact membership of x' = x_r XOR XY(pos) in the bucket chain starting at
-// bucket b (slow path: full buckets, several equal tags).
+// bucket sh (slow path: full buckets, several equal tags).
 template <int W>
 __device__ __noinline__ bool verify_slow(int r, uint32_t pos, uint32_t sh, const RowCache<W>* rc,
-                                         const SearchArgs& a, uint32_t& j) {
+                                         const TermsArgs& a, uint32_t& j) {
   const uint64_t* rec = a.srch_rec + (int64_t)pos * a.rec_words;
   uint64_t key[W];
 #pragma unroll
@@ -272,18 +385,22 @@ __device__ __noinline__ bool verify_slow(int r, uint32_t pos, uint32_t sh, const
   return false;
 }
 
+// Verification of queued candidates: each lane takes two entries at a time
+// (W = 1) so their loads overlap (search record, then hash-table bucket).
+template <int W>
+struct FlushWays { static constexpr int value = W == 1 ? 2 : 1; };
+
 template <int W, int MODE>
-__device__ __forceinline__ void verify_items(const uint32_t* q, int qn, int64_t (&acc)[R],
-                                             EmitState& es, RowCache<W>* rc, const SearchArgs& a) {
-  constexpr int kFlushWays = FlushWays<W>::value;
+__device__ __forceinline__ void verify_items(const uint32_t* q, int qn, RowCache<W>* rc, const TermsArgs& a) {
+  constexpr int kWays = FlushWays<W>::value;
   const int lane = threadIdx.x & 31;
-  for (int e0 = 0; e0 < qn; e0 += 32 * kFlushWays) {
-    int r[kFlushWays];
-    uint32_t pos[kFlushWays], s[kFlushWays];
-    uint4 b0[kFlushWays], b1[kFlushWays];
-    bool live[kFlushWays];
+  for (int e0 = 0; e0 < qn; e0 += 32 * kWays) {
+    int r[kWays];
+    uint32_t pos[kWays], s[kWays];
+    uint4 b0[kWays], b1[kWays];
+    bool live[kWays];
 #pragma unroll
-    for (int u = 0; u < kFlushWays; ++u) {  // candidate hash, then its bucket
+    for (int u = 0; u < kWays; ++u) {  // candidate hash, then its bucket
       const int e = e0 + u * 32 + lane;
       live[u] = e < qn;
       const uint32_t ent = q[live[u] ? e : e0];
@@ -295,16 +412,15 @@ __device__ __forceinline__ void verify_items(const uint32_t* q, int qn, int64_t 
       b1[u] = __ldg(bk + 1);
     }
 #pragma unroll
-    for (int u = 0; u < kFlushWays; ++u) {
+    for (int u = 0; u < kWays; ++u) {
       // tag matches among occupied slots; slots fill in order, so slot 3 occupied = full
       const uint32_t sh = s[u];
       const uint32_t mm = (uint32_t)(b0[u].x == sh && b0[u].y != ~0u) | ((uint32_t)(b0[u].z == sh && b0[u].w != ~0u) << 1) |
                           ((uint32_t)(b1[u].x == sh && b1[u].y != ~0u) << 2) | ((uint32_t)(b1[u].z == sh && b1[u].w != ~0u) << 3);
       const uint32_t jc = (mm & 1u) ? b0[u].y : (mm & 2u) ? b0[u].w : (mm & 4u) ? b1[u].y : b1[u].w;
       const bool full = b1[u].w != ~0u;
-      bool found = false;
+      bool found = false, slow = false;
       uint32_t j = 0, id = kDummy;
-      bool slow = false;
       if (live[u] && mm) {  // confirm the first match exactly (almost always the only one)
         const uint64_t* rec = a.srch_rec + (int64_t)pos[u] * a.rec_words;
         id = (uint32_t)(__ldg(rec) >> 32);
@@ -323,26 +439,25 @@ __device__ __forceinline__ void verify_items(const uint32_t* q, int qn, int64_t 
         found = verify_slow<W>(r[u], pos[u], sh, rc, a, j);
       }
       found = found && id != kDummy;  // padding slots carry XY = 0 and never count
-      if (e0 + u * 32 < qn) emit_round<MODE, W>(found, r[u], j, id, acc, es, rc, a);
+      if (e0 + u * 32 < qn) emit_found<MODE, W>(found, r[u], j, id, rc, a);
     }
   }
 }
 
 // Queue entries are (row mask << 24 | slot).  Each 32-entry slice is expanded
-// into one (row << 24 | slot) item per set bit, rows of an entry in increasing
-// order and entries in queue order, so a row's items keep their slot order.
-// Items accumulate in xbuf and are verified in full chunks.
+// into one (row << 24 | slot) item per set bit; items accumulate in xbuf and
+// are verified in full chunks.
 constexpr int kXbufCap = 384;
 
 template <int W, int MODE>
-__device__ __forceinline__ void flush_queue(const uint32_t* q, int qn, uint32_t* xbuf, int64_t (&acc)[R],
-                                            EmitState& es, RowCache<W>* rc, const SearchArgs& a) {
+__device__ __forceinline__ void flush_queue(const uint32_t* q, int qn, uint32_t* xbuf, RowCache<W>* rc,
+                                            const TermsArgs& a) {
   const int lane = threadIdx.x & 31;
   int xn = 0;
   for (int c0 = 0; c0 < qn; c0 += 32) {
     if (xn + 32 * R > kXbufCap) {
       __syncwarp();
-      verify_items<W, MODE>(xbuf, xn, acc, es, rc, a);
+      verify_items<W, MODE>(xbuf, xn, rc, a);
       __syncwarp();
       xn = 0;
     }
@@ -366,14 +481,16 @@ __device__ __forceinline__ void flush_queue(const uint32_t* q, int qn, uint32_t*
     xn += __shfl_sync(kFull, incl, 31);
   }
   __syncwarp();
-  verify_items<W, MODE>(xbuf, xn, acc, es, rc, a);
+  verify_items<W, MODE>(xbuf, xn, rc, a);
   __syncwarp();
 }
 
 template <int W, int MODE>
-__global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const SearchArgs a) {
+__global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const TermsArgs a) {
   if (MODE == kFill && (*(volatile int32_t*)a.status & kStatusCapacity)) return;  // buffers too small
   extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ int64_t s_qoff[kMaxSegs];
+  __shared__ int64_t s_cum[kMaxSegs + 1];
   uint32_t* bloom = smem;
   RowCache<W>* caches = reinterpret_cast<RowCache<W>*>(smem + a.nwords);
   uint32_t* queue = reinterpret_cast<uint32_t*>(caches + kSearchWarps);
@@ -383,6 +500,19 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Se
     uint4* dst = reinterpret_cast<uint4*>(bloom);
     for (int i = threadIdx.x; i < a.nwords / 4; i += blockDim.x) dst[i] = __ldg(src + i);
   }
+  if (threadIdx.x == 0) {  // list offsets per qubit; work items per segment (prefix)
+    int64_t run = 0;
+    for (int q = 0; q < a.nq; ++q) {
+      s_qoff[q] = run;
+      run += a.qcnt[q];
+    }
+    int64_t c = 0;
+    for (int sg = 0; sg < a.n_segs; ++sg) {
+      s_cum[sg] = c;
+      c += ((int64_t)a.qcnt[__ldg(&a.segs[sg].x)] + R - 1) / R;
+    }
+    s_cum[a.n_segs] = c;
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -390,25 +520,26 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Se
   uint32_t* xbuf = xbufs + warp * kXbufCap;
   const uint32_t lt = (1u << lane) - 1u;
   RowCache<W>* rc = caches + warp;
-  const int64_t cnt0 = (int64_t)a.cls_cnt[0], cnt1 = (int64_t)a.cls_cnt[1];
-  const int64_t nb0 = (cnt0 + R - 1) / R;
-  const int64_t n_batches = nb0 + (cnt1 + R - 1) / R;
+  const int64_t n_items = s_cum[a.n_segs];
   const uint32_t wmask4 = a.wmask << 2;
   const char* bloom_bytes = reinterpret_cast<const char*>(bloom);
-  const int64_t pbase = (MODE == kFill && a.pass == 0) ? a.rp[0] : 0;
   while (true) {
-    unsigned long long btu = 0;
-    if (lane == 0) btu = atomicAdd(a.batch_counter, 1ull);
-    const int64_t bt = (int64_t)__shfl_sync(kFull, btu, 0);
-    if (bt >= n_batches) break;
-    const int cls = bt < nb0 ? 0 : 1;
-    const int64_t b0 = (cls ? bt - nb0 : bt) * R;
-    const int64_t ccount = cls ? cnt1 : cnt0;
-    const int half = cls ^ a.pass;  // patterns whose top hash bit sends x' to this pass's samples
+    unsigned long long itu = 0;
+    if (lane == 0) itu = atomicAdd(a.item_counter, 1ull);
+    const int64_t it = (int64_t)__shfl_sync(kFull, itu, 0);
+    if (it >= n_items) break;
+    int lo = 0, hi = a.n_segs;  // s_cum[lo] <= it < s_cum[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (s_cum[mid] <= it) lo = mid; else hi = mid;
+    }
+    const int4 sg = __ldg(&a.segs[lo]);
+    const int64_t b0 = (it - s_cum[lo]) * R;
+    const int64_t count_t = (int64_t)a.qcnt[sg.x];
     __syncwarp();
     if (lane < R) {
-      const bool valid = b0 + lane < ccount;
-      const int64_t row = valid ? (int64_t)a.perm[cls * a.perm_stride + b0 + lane] : -1;
+      const bool valid = b0 + lane < count_t;
+      const int64_t row = valid ? (int64_t)__ldg(a.qrows + s_qoff[sg.x] + b0 + lane) : -1;
 #pragma unroll
       for (int w = 0; w < W; ++w) rc->u[lane][w] = valid ? __ldg(a.U + row * W + w) : 0ull;
       rc->hx[lane] = valid ? __ldg(a.hx + row) : 0u;
@@ -418,28 +549,16 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Se
     __syncwarp();
     uint32_t hr4[R], hr17[R], hr22[R];
     uint32_t vmask = 0;
-    int64_t acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int64_t row = rc->row[r];
-      const bool valid = row >= 0;
       const uint32_t h = rc->hx[r];
       hr4[r] = h << 2;
       hr17[r] = h >> 17;
       hr22[r] = h >> 22;
-      if (valid) vmask |= 1u << (R - 1 - r);
-      acc[r] = 0;
-      if (MODE == kFill && valid)
-        acc[r] = a.pass == 0 ? a.rp[row - a.row_begin] - pbase : a.rowcur[row - a.row_begin];
-    }
-    EmitState es{-1, 0, -1, 0};
-    if (a.has_diag && a.pass == 0) {  // the diagonal pair (x, x) comes first in its row
-      const int64_t myrow = rc->row[lane < R ? lane : 0];
-      const bool d = lane < R && myrow >= 0;
-      emit_round<MODE, W>(d, lane, (uint32_t)(d ? myrow : 0), 0u, acc, es, rc, a);
+      if (rc->row[r] >= 0) vmask |= 1u << (R - 1 - r);
     }
     int qn = 0;
-    for (int64_t g = a.g_begin[half]; g < a.g_end[half]; ++g) {
+    for (int g = sg.y; g < sg.z; ++g) {
       const uint32_t pos = (uint32_t)(g * 32 + lane);
       const uint32_t hk = __ldg(a.srch_hash + pos);
       const uint32_t hk4 = hk << 2, hk17 = hk >> 17, hk22 = hk >> 22;
@@ -457,60 +576,21 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Se
         qn += __popc(bal);
         if (qn > kQueueCap - 32) {
           __syncwarp();
-          flush_queue<W, MODE>(q, qn, xbuf, acc, es, rc, a);
+          flush_queue<W, MODE>(q, qn, xbuf, rc, a);
           __syncwarp();
           qn = 0;
         }
       }
     }
     __syncwarp();
-    flush_queue<W, MODE>(q, qn, xbuf, acc, es, rc, a);
+    flush_queue<W, MODE>(q, qn, xbuf, rc, a);
     __syncwarp();
-    if (MODE != kFill && lane < R && rc->row[lane] >= 0) {
-      const int64_t rl = rc->row[lane] - a.row_begin;
-      if (a.pass == 0) a.rp[rl] = (int64_t)rc->cnt[lane];
-      else a.rp[rl] += (int64_t)rc->cnt[lane];
-    }
-    if (MODE == kFill && a.pass == 0) {
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (lane == r && rc->row[r] >= 0) a.rowcur[rc->row[r] - a.row_begin] = acc[r];
-    }
-    if (MODE == kEmit && lane == 0) {
-      a.sc.heads[a.pass * a.nbm + bt] = es.first;
-      a.sc.heads[(2 + a.pass) * a.nbm + bt] = es.total;
-      if (es.chunk >= 0) a.sc.next[es.chunk] = -1;
+    if (MODE != kFill && lane < R) {
+      const int64_t row = rc->row[lane];
+      if (row >= a.row_begin && row < a.row_end && rc->cnt[lane])
+        atomicAdd((unsigned long long*)(a.counts + (row - a.row_begin)), (unsigned long long)rc->cnt[lane]);
     }
   }
-}
-
-// Split the rows of [row_begin, row_end) by the top bit of their hash.  The
-// order inside a class does not matter: a row's pairs come out in the same
-// order whatever rows share its batch.
-__global__ void partition_rows_kernel(const uint32_t* __restrict__ hx, int64_t rb, int64_t re,
-                                      int32_t* __restrict__ perm, int64_t stride,
-                                      unsigned long long* __restrict__ cnt) {
-  for (int64_t row = rb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < re;
-       row += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(__ldg(hx + row) >> 31);
-    const unsigned long long p = atomicAdd(cnt + c, 1ull);
-    perm[c * stride + (int64_t)p] = (int32_t)row;
-  }
-}
-
-template <int W, int MODE>
-static cudaError_t launch_terms_w(const SearchArgs& args, int64_t rows, size_t smem, cudaStream_t s) {
-  auto kern = pairs_terms_kernel<W, MODE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int occ = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kSearchThreads, smem);
-  if (occ < 1) occ = 1;
-  const int64_t batches = nb_max(rows);
-  const int64_t need = (batches + kSearchWarps - 1) / kSearchWarps;
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * occ));
-  kern<<<blocks, kSearchThreads, smem, s>>>(args);
-  return cudaGetLastError();
 }
 
 template <int W>
@@ -519,61 +599,294 @@ static size_t search_smem(const StageHeader& L) {
          (size_t)kSearchWarps * (kQueueCap + kXbufCap) * 4;
 }
 
-cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, const char* stage,
-                               const StageHeader& L, int64_t rb, int64_t re, int64_t* rp,
-                               uint32_t* pj, uint32_t* pk, int mode, const PairScratch* sc,
-                               cudaStream_t s) {
+template <int W, int MODE>
+static cudaError_t launch_terms_w(const TermsArgs& args, const StageHeader& L, cudaStream_t s) {
+  auto kern = pairs_terms_kernel<W, MODE>;
+  const size_t smem = search_smem<W>(L);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<num_sms(), kSearchThreads, smem, s>>>(args);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// CSR assembly: row initialisation (diagonal pair, cursors), scatter of the
+// one-pass records, and the per-row sort by pattern index.
+// --------------------------------------------------------------------------
+
+// COUNT/EMIT: counts[r] = has_diag.  FILL: cursor[r] = has_diag and the
+// diagonal pair at the row's start.  In FILL mode, if the pairs outgrow
+// `capacity` or the scratch overflowed, flag the status and write nothing.
+__global__ void pairs_init_kernel(int mode, int64_t rows, int64_t rb, int has_diag, int64_t* __restrict__ counts,
+                                  const int64_t* __restrict__ rp, int32_t* __restrict__ cursor,
+                                  uint32_t* __restrict__ pj, uint32_t* __restrict__ pk, int64_t capacity,
+                                  const int64_t* __restrict__ overflow, int32_t* __restrict__ status) {
+  if (mode == kFill) {
+    const bool too_small = (capacity >= 0 && rp[rows] - rp[0] > capacity) || (overflow && *overflow != 0);
+    if (too_small) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusCapacity);
+      return;
+    }
+    if (*(volatile int32_t*)status & kStatusCapacity) return;
+  }
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+    if (mode != kFill) {
+      counts[r] = has_diag;
+    } else {
+      cursor[r] = has_diag;
+      if (has_diag) {
+        const int64_t p = rp[r] - rp[0];
+        pj[p] = (uint32_t)(rb + r);
+        pk[p] = 0u;
+      }
+    }
+  }
+}
+
+__global__ void pairs_scatter_kernel(PairScratch sc, int64_t rb, int64_t re, const int64_t* __restrict__ rp,
+                                     int32_t* __restrict__ cursor, uint32_t* __restrict__ pj,
+                                     uint32_t* __restrict__ pk, int32_t* __restrict__ status) {
+  if (*(volatile const int32_t*)status & kStatusCapacity) return;
+  const int64_t n_rec = *sc.cursor < sc.max_rec ? *sc.cursor : sc.max_rec;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_rec; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = sc.rec_i[q], j = sc.rec_j[q];
+    const uint32_t k = sc.rec_k[q];
+    if (i >= rb && i < re) place_pair(rp, i - rb, cursor, pj, pk, (uint32_t)j, k, status);
+    if (j >= rb && j < re) place_pair(rp, j - rb, cursor, pj, pk, (uint32_t)i, k, status);
+  }
+}
+
+// Bitonic sorting network whose comparators all put the minimum at the lower
+// index: for block sizes k = 2, 4, .., N, first compare i with i XOR (k - 1)
+// (each position of the lower half with its mirror image), then i with
+// i XOR d for d = k/4, .., 1.  Keys beyond the row's length act as +infinity
+// and, sitting at the higher index of every comparator they take part in,
+// never move, so no padding needs to be stored.
+// Warp version: key index e = lane * S + s (S keys per lane, in registers).
+template <int S>
+__device__ __forceinline__ void warp_cmpx(uint64_t (&v)[S], int m) {
+  const int lane = threadIdx.x & 31;
+  const int hb = 1 << (31 - __clz(m));  // highest bit of m: e is the lower index iff (e & hb) == 0
+  if (m < S) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      if ((s & hb) == 0) {
+        const int s2 = s ^ m;
+        const uint64_t x = v[s], y = v[s2];
+        v[s] = x < y ? x : y;
+        v[s2] = x < y ? y : x;
+      }
+    }
+  } else {
+    const int ml = m / S, ms = m & (S - 1);
+    const bool lower = (lane & (hb / S)) == 0;
+    uint64_t t[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) t[s] = __shfl_xor_sync(kFull, v[s ^ ms], ml);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const bool less = v[s] < t[s];
+      v[s] = (lower == less) ? v[s] : t[s];
+    }
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void warp_sort_row(uint32_t* __restrict__ pj, uint32_t* __restrict__ pk, int n) {
+  const int lane = threadIdx.x & 31;
+  uint64_t v[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int e = lane * S + s;
+    v[s] = e < n ? (((uint64_t)pk[e] << 32) | pj[e]) : ~0ull;
+  }
+#pragma unroll
+  for (int k = 2; k <= 32 * S; k <<= 1) {
+    warp_cmpx<S>(v, k - 1);
+#pragma unroll
+    for (int d = k >> 2; d >= 1; d >>= 1) warp_cmpx<S>(v, d);
+  }
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int e = lane * S + s;
+    if (e < n) {
+      pj[e] = (uint32_t)v[s];
+      pk[e] = (uint32_t)(v[s] >> 32);
+    }
+  }
+}
+
+__global__ void sort_rows_warp_kernel(const int64_t* __restrict__ rp, int64_t rows, uint32_t* __restrict__ pj,
+                                      uint32_t* __restrict__ pk, int has_diag, int32_t* __restrict__ big,
+                                      unsigned long long* __restrict__ big_count,
+                                      const int32_t* __restrict__ status) {
+  if (*(volatile const int32_t*)status & kStatusCapacity) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+  const int64_t p0 = rp[0];
+  for (int64_t r = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5); r < rows; r += nw) {
+    const int64_t a = rp[r] - p0 + has_diag;
+    const int64_t n = rp[r + 1] - p0 - a;
+    if (n <= 1) continue;
+    uint32_t* rj = pj + a;
+    uint32_t* rk = pk + a;
+    if (n <= 32) warp_sort_row<1>(rj, rk, (int)n);
+    else if (n <= 64) warp_sort_row<2>(rj, rk, (int)n);
+    else if (n <= 128) warp_sort_row<4>(rj, rk, (int)n);
+    else if (n <= 256) warp_sort_row<8>(rj, rk, (int)n);
+    else if (n <= kSortWarpMax) warp_sort_row<16>(rj, rk, (int)n);
+    else if (lane == 0) big[atomicAdd(big_count, 1ull)] = (int32_t)r;
+  }
+}
+
+// Rows longer than kSortWarpMax: one block per row, in shared memory when the
+// row fits (kSortBlockKeys keys), else in place in the pair arrays.
+constexpr int kSortBlockThreads = 1024;
+
+__global__ void __launch_bounds__(kSortBlockThreads)
+sort_rows_block_kernel(const int64_t* __restrict__ rp, uint32_t* __restrict__ pj, uint32_t* __restrict__ pk,
+                       int has_diag, const int32_t* __restrict__ big, const unsigned long long* __restrict__ big_count,
+                       unsigned long long* __restrict__ big_next, const int32_t* __restrict__ status) {
+  if (*(volatile const int32_t*)status & kStatusCapacity) return;
+  extern __shared__ __align__(16) uint64_t keys[];
+  __shared__ int64_t s_row;
+  const int64_t p0 = rp[0];
+  const int64_t n_big = (int64_t)*big_count;
+  while (true) {
+    if (threadIdx.x == 0) {
+      const unsigned long long t = atomicAdd(big_next, 1ull);
+      s_row = (int64_t)t < n_big ? (int64_t)big[t] : -1;
+    }
+    __syncthreads();
+    const int64_t r = s_row;
+    __syncthreads();
+    if (r < 0) break;
+    const int64_t a = rp[r] - p0 + has_diag;
+    const int64_t n = rp[r + 1] - p0 - a;
+    int64_t N = 1;
+    while (N < n) N <<= 1;
+    uint32_t* rj = pj + a;
+    uint32_t* rk = pk + a;
+    if (N <= kSortBlockKeys) {
+      for (int64_t e = threadIdx.x; e < N; e += blockDim.x)
+        keys[e] = e < n ? (((uint64_t)rk[e] << 32) | rj[e]) : ~0ull;
+      __syncthreads();
+      for (int64_t k = 2; k <= N; k <<= 1) {
+        for (int64_t m = k - 1, d = k; d > 1; d >>= 1, m = d >> 1) {
+          // comparator (e, e ^ m) with e the lower index: e has bit hb = highest bit of m clear
+          const int64_t hb = (m == k - 1) ? (k >> 1) : m;
+          for (int64_t c = threadIdx.x; c < N / 2; c += blockDim.x) {
+            const int64_t e = ((c & ~(hb - 1)) << 1) | (c & (hb - 1));  // insert a 0 at bit hb
+            const int64_t f = e ^ m;
+            const uint64_t x = keys[e], y = keys[f];
+            if (y < x) { keys[e] = y; keys[f] = x; }
+          }
+          __syncthreads();
+        }
+      }
+      for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+        rj[e] = (uint32_t)keys[e];
+        rk[e] = (uint32_t)(keys[e] >> 32);
+      }
+      __syncthreads();
+    } else {  // in place in global memory, sorting pattern indices and moving columns along
+      for (int64_t k = 2; k <= N; k <<= 1) {
+        for (int64_t m = k - 1, d = k; d > 1; d >>= 1, m = d >> 1) {
+          const int64_t hb = (m == k - 1) ? (k >> 1) : m;
+          for (int64_t c = threadIdx.x; c < N / 2; c += blockDim.x) {
+            const int64_t e = ((c & ~(hb - 1)) << 1) | (c & (hb - 1));
+            const int64_t f = e ^ m;
+            if (f >= n) continue;  // +infinity partner at the higher index: nothing moves
+            const uint32_t ke = rk[e], kf = rk[f];
+            if (kf < ke) {
+              const uint32_t je = rj[e];
+              rk[e] = kf; rk[f] = ke;
+              rj[e] = rj[f]; rj[f] = je;
+            }
+          }
+          __threadfence_block();
+          __syncthreads();
+        }
+      }
+    }
+  }
+}
+
+static cudaError_t launch_sort_rows(const int64_t* rp, int64_t rows, uint32_t* pj, uint32_t* pk, int has_diag,
+                                    char* stage, const StageHeader& L, cudaStream_t s) {
+  auto* ctr = (unsigned long long*)(stage + L.off_counters);
+  auto* status = (const int32_t*)(stage + offsetof(StageHeader, status));
+  auto* big = (int32_t*)(stage + L.off_big);
+  cudaError_t e = cudaMemsetAsync(ctr + kCtrBigCount, 0, 2 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, 16 * num_sms()));
+  sort_rows_warp_kernel<<<blocks, 256, 0, s>>>(rp, rows, pj, pk, has_diag, big, ctr + kCtrBigCount, status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t smem = sizeof(uint64_t) * kSortBlockKeys;
+  e = cudaFuncSetAttribute(sort_rows_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  sort_rows_block_kernel<<<num_sms(), kSortBlockThreads, smem, s>>>(rp, pj, pk, has_diag, big, ctr + kCtrBigCount,
+                                                                   ctr + kCtrBigNext, status);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_init(int mode, int64_t rows, int64_t rb, int has_diag, int64_t* counts, const int64_t* rp,
+                               int32_t* cursor, uint32_t* pj, uint32_t* pk, int64_t capacity,
+                               const int64_t* overflow, int32_t* status, cudaStream_t s) {
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 4 * num_sms()));
+  pairs_init_kernel<<<blocks, 256, 0, s>>>(mode, rows, rb, has_diag, counts, rp, cursor, pj, pk, capacity, overflow,
+                                           status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L,
+                               int64_t rb, int64_t re, int64_t* rp, uint32_t* pj, uint32_t* pk, int mode,
+                               const PairScratch* sc, cudaStream_t s) {
   if (ham->n_srch >= (int64_t(1) << 24) || ham->n_xy >= (int64_t(1) << 29)) return cudaErrorInvalidValue;
+  if (mode == kEmit && !sc) return cudaErrorInvalidValue;
   const int64_t rows = re - rb;
-  unsigned long long* counters = (unsigned long long*)(stage + L.off_counters);
-  SearchArgs a;
+  auto* ctr = (unsigned long long*)(stage + L.off_counters);
+  auto* status = (int32_t*)(stage + offsetof(StageHeader, status));
+  auto* cursor = (int32_t*)(stage + L.off_rowcur);
+  TermsArgs a;
+  std::memset(&a, 0, sizeof(a));
   a.U = U;
   a.hx = (const uint32_t*)(stage + L.off_hx);
   a.table = (const unsigned long long*)(stage + L.off_table);
   a.capmask = L.cap - 1;
+  a.bloom_g = (const uint32_t*)(stage + L.off_bloom);
   a.wmask = (uint32_t)(L.nwords - 1);
   a.nwords = (int)L.nwords;
   a.srch_hash = ham->srch_hash;
   a.srch_rec = ham->srch_rec;
   a.rec_words = ham->rec_words;
-  a.n_groups = ham->n_srch / 32;
-  a.has_diag = ham->has_diag;
+  a.segs = ham->segs;
+  a.n_segs = ham->n_segs;
+  a.nq = 64 * ham->W;
+  a.qcnt = (const uint32_t*)(stage + L.off_q);
+  a.qrows = (const uint32_t*)(stage + L.off_qrows);
   a.row_begin = rb;
   a.row_end = re;
-  a.rp = rp;
+  a.counts = mode == kFill ? nullptr : rp;
+  a.rp = mode == kFill ? rp : nullptr;
+  a.cursor = cursor;
   a.pair_j = pj;
   a.pair_k = pk;
-  a.status = (int32_t*)(stage + offsetof(StageHeader, status));
-  if (sc) a.sc = *sc; else a.sc = PairScratch{0, nullptr, nullptr, nullptr, nullptr};
-  a.perm = (const int32_t*)(stage + L.off_perm);
-  a.perm_stride = rows;
-  a.cls_cnt = counters + 2;
-  for (int t = 0; t < 2; ++t) { a.g_begin[t] = ham->half_begin[t]; a.g_end[t] = ham->half_end[t]; }
-  a.rowcur = (int64_t*)(stage + L.off_rowcur);
-  a.nbm = nb_max(rows);
-  cudaError_t e = cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned long long), s);
-  if (e != cudaSuccess) return e;
-  {
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 4 * num_sms()));
-    partition_rows_kernel<<<blocks, 256, 0, s>>>(a.hx, rb, re, (int32_t*)a.perm, rows, counters + 2);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  if (mode == kEmit) {
-    e = cudaMemsetAsync(sc->cursor, 0, 2 * sizeof(int64_t), s);
-    if (e != cudaSuccess) return e;
-  }
-  for (int pass = 0; pass < 2; ++pass) {
-    a.pass = pass;
-    a.bloom_g = (const uint32_t*)(stage + L.off_bloom) + (int64_t)pass * L.nwords;
-    a.batch_counter = counters + pass;
-#define NQS_TERMS(WW)                                                                    \
-  case WW: {                                                                             \
-    const size_t smem = search_smem<WW>(L);                                              \
-    if (mode == kCount) e = launch_terms_w<WW, kCount>(a, rows, smem, s);                \
-    else if (mode == kFill) e = launch_terms_w<WW, kFill>(a, rows, smem, s);             \
-    else e = launch_terms_w<WW, kEmit>(a, rows, smem, s);                                \
-    break;                                                                               \
-  }
+  if (sc) a.sc = *sc;
+  a.status = status;
+  a.item_counter = ctr + kCtrItems;
+  cudaError_t e;
+  if ((e = launch_init(mode, rows, rb, ham->has_diag, rp, rp, cursor, pj, pk, -1, nullptr, status, s)) != cudaSuccess)
+    return e;
+  if (mode == kEmit && (e = cudaMemsetAsync(sc->cursor, 0, 2 * sizeof(int64_t), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ctr + kCtrItems, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+  if (ham->n_segs > 0) {
+#define NQS_TERMS(WW)                                                            \
+  case WW:                                                                       \
+    if (mode == kCount) e = launch_terms_w<WW, kCount>(a, L, s);                 \
+    else if (mode == kFill) e = launch_terms_w<WW, kFill>(a, L, s);              \
+    else e = launch_terms_w<WW, kEmit>(a, L, s);                                 \
+    break;
     switch (ham->W) {
       NQS_TERMS(1)
       NQS_TERMS(2)
@@ -584,79 +897,22 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, const char
 #undef NQS_TERMS
     if (e != cudaSuccess) return e;
   }
+  if (mode == kFill) return launch_sort_rows(rp, rows, pj, pk, ham->has_diag, stage, L, s);
   return cudaSuccess;
 }
 
-// --------------------------------------------------------------------------
-// compaction of the one-pass records into CSR order (one warp per row batch)
-// --------------------------------------------------------------------------
-__global__ void pairs_compact_kernel(PairScratch sc, int64_t rows, const int64_t* __restrict__ rp,
-                                     const int32_t* __restrict__ perm, const unsigned long long* __restrict__ cls_cnt,
-                                     int64_t rb, int64_t nbm, uint32_t* __restrict__ pair_j,
-                                     uint32_t* __restrict__ pair_k, int64_t capacity, int32_t* status) {
-  // buffers sized ahead of time (graph replay) may be too small: report, write nothing
-  if (rp[rows] - rp[0] > capacity || sc.cursor[1] != 0) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusCapacity);
-    return;
-  }
-  const int lane = threadIdx.x & 31;
-  const uint32_t lt = (1u << lane) - 1u;
-  const int64_t cnt0 = (int64_t)cls_cnt[0], cnt1 = (int64_t)cls_cnt[1];
-  const int64_t nb0 = (cnt0 + R - 1) / R;
-  const int64_t n_batches = nb0 + (cnt1 + R - 1) / R;
-  const int64_t tw = (int64_t)gridDim.x * (blockDim.x / 32);
-  const int64_t p0 = rp[0];
-  for (int64_t bt = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); bt < n_batches; bt += tw) {
-    const int cls = bt < nb0 ? 0 : 1;
-    const int64_t b0 = (cls ? bt - nb0 : bt) * R;
-    const int64_t ccount = cls ? cnt1 : cnt0;
-    int64_t base[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const bool valid = b0 + r < ccount;
-      base[r] = valid ? rp[perm[cls * rows + b0 + r] - rb] - p0 : 0;
-    }
-    for (int pass = 0; pass < 2; ++pass) {  // a row's pass-0 pairs precede its pass-1 pairs
-      const int64_t total = sc.heads[(2 + pass) * nbm + bt];
-      int64_t consumed = 0;
-      int32_t c = sc.heads[pass * nbm + bt];
-      while (consumed < total && c >= 0) {
-        const int n_here = (int)((total - consumed < kChunk) ? total - consumed : kChunk);
-        for (int e0 = 0; e0 < n_here; e0 += 32) {
-          const int e = e0 + lane;
-          const bool v = e < n_here;
-          const uint64_t rec = v ? sc.records[(int64_t)c * kChunk + e] : 0ull;
-          const int r = (int)(rec >> 61);
-          const uint32_t j = (uint32_t)rec;
-          const uint32_t k = (uint32_t)(rec >> 32) & 0x1FFFFFFFu;
-#pragma unroll
-          for (int rr = 0; rr < R; ++rr) {
-            const uint32_t m = __ballot_sync(kFull, v && r == rr);
-            if (v && r == rr) {
-              const int64_t p = base[rr] + __popc(m & lt);
-              pair_j[p] = j;
-              pair_k[p] = k;
-            }
-            base[rr] += __popc(m);
-          }
-        }
-        consumed += n_here;
-        c = sc.next[c];
-      }
-    }
-  }
-}
-
-cudaError_t launch_pairs_compact(const PairScratch& sc, const char* stage, const StageHeader& L, int64_t rb,
-                                 int64_t rows, const int64_t* row_ptr, uint32_t* pair_j, uint32_t* pair_k,
-                                 int64_t capacity, cudaStream_t s) {
-  const int64_t batches = nb_max(rows);
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((batches + 7) / 8, (int64_t)num_sms() * 8));
-  pairs_compact_kernel<<<blocks, 256, 0, s>>>(sc, rows, row_ptr, (const int32_t*)(stage + L.off_perm),
-                                              (const unsigned long long*)(stage + L.off_counters) + 2, rb,
-                                              nb_max(rows), pair_j, pair_k, capacity,
-                                              (int32_t*)(stage + offsetof(StageHeader, status)));
-  return cudaGetLastError();
+cudaError_t launch_pairs_compact(const nqs_ham* ham, const PairScratch& sc, char* stage, const StageHeader& L,
+                                 int64_t rb, int64_t rows, const int64_t* row_ptr, uint32_t* pair_j,
+                                 uint32_t* pair_k, int64_t capacity, cudaStream_t s) {
+  auto* status = (int32_t*)(stage + offsetof(StageHeader, status));
+  auto* cursor = (int32_t*)(stage + L.off_rowcur);
+  cudaError_t e = launch_init(kFill, rows, rb, ham->has_diag, nullptr, row_ptr, cursor, pair_j, pair_k, capacity,
+                              sc.cursor + 1, status, s);
+  if (e != cudaSuccess) return e;
+  const int blocks = 8 * num_sms();
+  pairs_scatter_kernel<<<blocks, 256, 0, s>>>(sc, rb, rb + rows, row_ptr, cursor, pair_j, pair_k, status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return launch_sort_rows(row_ptr, rows, pair_j, pair_k, ham->has_diag, stage, L, s);
 }
 
 // --------------------------------------------------------------------------
@@ -680,16 +936,43 @@ struct BatchArgs {
   uint32_t* pair_k;
   int32_t* status;
   unsigned long long* batch_counter;
-  PairScratch sc;
-  SearchArgs emit;  // pair_j, pair_k, sc for emit_round
 };
 
 constexpr int kBatchThreads = 512;
 constexpr int kBatchWarps = kBatchThreads / 32;
 
+template <int W>
+struct BatchRows {   // per-warp copy of the batch's rows (shared memory)
+  uint64_t u[R][W];
+  uint32_t hx[R];
+  uint32_t cnt[R];
+};
+
+// COUNT counts per row (shared atomics); FILL places pairs at per-row ranks in lane order
+template <int MODE, int W>
+__device__ __forceinline__ void batch_emit(bool found, int r, uint32_t j, uint32_t id, int64_t (&acc)[R],
+                                           BatchRows<W>* rc, const BatchArgs& a) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  if (MODE == kFill) {
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+      const uint32_t m = __ballot_sync(kFull, found && r == rr);
+      if (found && r == rr) {
+        const int64_t p = acc[rr] + __popc(m & lt);
+        a.pair_j[p] = j;
+        a.pair_k[p] = id;
+      }
+      acc[rr] += __popc(m);
+    }
+    return;
+  }
+  if (found) atomicAdd(&rc->cnt[r], 1u);
+}
+
 template <int W, int MODE>
-__device__ __forceinline__ void batch_verify(const uint32_t* items, int n_items, int64_t (&acc)[R], EmitState& es,
-                                             RowCache<W>* rc, const BatchArgs& a) {
+__device__ __forceinline__ void batch_verify(const uint32_t* items, int n_items, int64_t (&acc)[R],
+                                             BatchRows<W>* rc, const BatchArgs& a) {
   const int lane = threadIdx.x & 31;
   for (int e0 = 0; e0 < n_items; e0 += 32) {
     const int e = e0 + lane;
@@ -717,14 +1000,52 @@ __device__ __forceinline__ void batch_verify(const uint32_t* items, int n_items,
       }
       if (k > a.xy_capmask) atomicOr(a.status, kStatusLimit);
     }
-    emit_round<MODE, W>(found, r, j, id, acc, es, rc, a.emit);
+    batch_emit<MODE, W>(found, r, j, id, acc, rc, a);
   }
+}
+
+// expand queue entries (row mask << 24 | column) into (row << 24 | column)
+// items, rows of an entry in increasing order, entries in queue order; verify
+template <int W, int MODE>
+__device__ __forceinline__ void batch_flush(const uint32_t* q, int qn, uint32_t* xbuf, int64_t (&acc)[R],
+                                            BatchRows<W>* rc, const BatchArgs& a) {
+  const int lane = threadIdx.x & 31;
+  int xn = 0;
+  for (int s0 = 0; s0 < qn; s0 += 32) {
+    if (xn + 32 * R > kXbufCap) {
+      __syncwarp();
+      batch_verify<W, MODE>(xbuf, xn, acc, rc, a);
+      __syncwarp();
+      xn = 0;
+    }
+    const int e = s0 + lane;
+    const uint32_t ent = e < qn ? q[e] : 0u;
+    uint32_t bits = ent >> 24;
+    const uint32_t col = ent & 0x00FFFFFFu;
+    const int c = __popc(bits);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += t;
+    }
+    int at = xn + incl - c;
+    while (bits) {
+      const int b = 31 - __clz(bits);
+      bits &= ~(1u << b);
+      xbuf[at++] = ((uint32_t)(R - 1 - b) << 24) | col;
+    }
+    xn += __shfl_sync(kFull, incl, 31);
+  }
+  __syncwarp();
+  batch_verify<W, MODE>(xbuf, xn, acc, rc, a);
+  __syncwarp();
 }
 
 template <int W, int MODE>
 __global__ void __launch_bounds__(kBatchThreads) pairs_batch_kernel(const BatchArgs a) {
   if (MODE == kFill && (*(volatile int32_t*)a.status & kStatusCapacity)) return;  // buffers too small
-  __shared__ RowCache<W> caches[kBatchWarps];
+  __shared__ BatchRows<W> caches[kBatchWarps];
   __shared__ uint32_t queue[kBatchWarps][kQueueCap];
   __shared__ uint32_t xbufs[kBatchWarps][kXbufCap];
   __shared__ unsigned long long wm[5];
@@ -735,7 +1056,7 @@ __global__ void __launch_bounds__(kBatchThreads) pairs_batch_kernel(const BatchA
   const uint32_t lt = (1u << lane) - 1u;
   uint32_t* q = queue[warp];
   uint32_t* xbuf = xbufs[warp];
-  RowCache<W>* rc = caches + warp;
+  BatchRows<W>* rc = caches + warp;
   const int64_t n_rows = a.row_end - a.row_begin;
   const int64_t n_batches = (n_rows + R - 1) / R;
   const int64_t pbase = (MODE == kFill) ? a.rp[0] : 0;
@@ -767,10 +1088,9 @@ __global__ void __launch_bounds__(kBatchThreads) pairs_batch_kernel(const BatchA
       if (valid) vmask |= 1u << (R - 1 - r);
       acc[r] = (MODE == kFill && valid) ? a.rp[row - a.row_begin] - pbase : 0;
     }
-    EmitState es{-1, 0, -1, 0};
     if (a.has_diag) {
       const bool d = lane < R && r0 + lane < a.row_end;
-      emit_round<MODE, W>(d, lane, (uint32_t)(r0 + lane), 0u, acc, es, rc, a.emit);
+      batch_emit<MODE, W>(d, lane, (uint32_t)(r0 + lane), 0u, acc, rc, a);
     }
     int qn = 0;
     for (int64_t c0 = 0; c0 < a.n; c0 += 32) {
@@ -795,80 +1115,17 @@ __global__ void __launch_bounds__(kBatchThreads) pairs_batch_kernel(const BatchA
         qn += __popc(bal);
         if (qn > kQueueCap - 32) {
           __syncwarp();
-          // expand and verify (same order rules as the LoopOverTerms flush)
-          int xn = 0;
-          for (int s0 = 0; s0 < qn; s0 += 32) {
-            if (xn + 32 * R > kXbufCap) {
-              __syncwarp();
-              batch_verify<W, MODE>(xbuf, xn, acc, es, rc, a);
-              __syncwarp();
-              xn = 0;
-            }
-            const int e = s0 + lane;
-            const uint32_t ent = e < qn ? q[e] : 0u;
-            uint32_t bits = ent >> 24;
-            const uint32_t col = ent & 0x00FFFFFFu;
-            const int c = __popc(bits);
-            int incl = c;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const int t = __shfl_up_sync(kFull, incl, o);
-              if (lane >= o) incl += t;
-            }
-            int at = xn + incl - c;
-            while (bits) {
-              const int b = 31 - __clz(bits);
-              bits &= ~(1u << b);
-              xbuf[at++] = ((uint32_t)(R - 1 - b) << 24) | col;
-            }
-            xn += __shfl_sync(kFull, incl, 31);
-          }
-          __syncwarp();
-          batch_verify<W, MODE>(xbuf, xn, acc, es, rc, a);
+          batch_flush<W, MODE>(q, qn, xbuf, acc, rc, a);
           __syncwarp();
           qn = 0;
         }
       }
     }
     __syncwarp();
-    {
-      int xn = 0;
-      for (int s0 = 0; s0 < qn; s0 += 32) {
-        if (xn + 32 * R > kXbufCap) {
-          __syncwarp();
-          batch_verify<W, MODE>(xbuf, xn, acc, es, rc, a);
-          __syncwarp();
-          xn = 0;
-        }
-        const int e = s0 + lane;
-        const uint32_t ent = e < qn ? q[e] : 0u;
-        uint32_t bits = ent >> 24;
-        const uint32_t col = ent & 0x00FFFFFFu;
-        const int c = __popc(bits);
-        int incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int t = __shfl_up_sync(kFull, incl, o);
-          if (lane >= o) incl += t;
-        }
-        int at = xn + incl - c;
-        while (bits) {
-          const int b = 31 - __clz(bits);
-          bits &= ~(1u << b);
-          xbuf[at++] = ((uint32_t)(R - 1 - b) << 24) | col;
-        }
-        xn += __shfl_sync(kFull, incl, 31);
-      }
-      __syncwarp();
-      batch_verify<W, MODE>(xbuf, xn, acc, es, rc, a);
-      __syncwarp();
-    }
+    batch_flush<W, MODE>(q, qn, xbuf, acc, rc, a);
+    __syncwarp();
     if (MODE != kFill && lane < R && r0 + lane < a.row_end)
       a.rp[r0 + lane - a.row_begin] = (int64_t)rc->cnt[lane];
-    if (MODE == kEmit && lane == 0) {
-      a.sc.heads[bt] = es.first;
-      if (es.chunk >= 0) a.sc.next[es.chunk] = -1;
-    }
   }
 }
 
@@ -885,10 +1142,10 @@ static cudaError_t launch_batch_w(const BatchArgs& args, int64_t rows, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_pairs_batch(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, const char* stage,
+cudaError_t launch_pairs_batch(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, char* stage,
                                const StageHeader& L, int64_t rb, int64_t re, int64_t* rp, uint32_t* pj,
-                               uint32_t* pk, int mode, const PairScratch* sc, cudaStream_t s) {
-  if (n_unq >= (int64_t(1) << 24)) return cudaErrorInvalidValue;
+                               uint32_t* pk, int mode, cudaStream_t s) {
+  if (n_unq >= (int64_t(1) << 24) || mode == kEmit) return cudaErrorInvalidValue;
   BatchArgs a;
   a.U = U;
   a.n = n_unq;
@@ -903,24 +1160,14 @@ cudaError_t launch_pairs_batch(const nqs_ham* ham, const uint64_t* U, int64_t n_
   a.pair_j = pj;
   a.pair_k = pk;
   a.status = (int32_t*)(stage + offsetof(StageHeader, status));
-  a.batch_counter = (unsigned long long*)(stage + L.off_counters);
-  if (sc) a.sc = *sc; else a.sc = PairScratch{0, nullptr, nullptr, nullptr, nullptr};
-  std::memset(&a.emit, 0, sizeof(a.emit));
-  a.emit.pair_j = pj;
-  a.emit.pair_k = pk;
-  a.emit.sc = a.sc;
+  a.batch_counter = (unsigned long long*)(stage + L.off_counters) + kCtrBatch;
   cudaError_t e = cudaMemsetAsync(a.batch_counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  if (mode == kEmit) {
-    e = cudaMemsetAsync(sc->cursor, 0, 2 * sizeof(int64_t), s);
-    if (e != cudaSuccess) return e;
-  }
   const int64_t rows = re - rb;
 #define NQS_BATCH(WW)                                                          \
   case WW:                                                                     \
     if (mode == kCount) return launch_batch_w<WW, kCount>(a, rows, s);         \
-    if (mode == kFill) return launch_batch_w<WW, kFill>(a, rows, s);           \
-    return launch_batch_w<WW, kEmit>(a, rows, s);
+    return launch_batch_w<WW, kFill>(a, rows, s);
   switch (ham->W) {
     NQS_BATCH(1)
     NQS_BATCH(2)

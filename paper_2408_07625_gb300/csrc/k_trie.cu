@@ -628,7 +628,7 @@ cudaError_t launch_pairs_trie(const nqs_ham* ham, const uint64_t* U, int64_t n, 
   a.pair_k = pk;
   a.status = (int32_t*)(stage + offsetof(StageHeader, status));
   a.trie_ok = (const int32_t*)(stage + offsetof(StageHeader, trie_ok));
-  a.row_counter = (unsigned long long*)(stage + L.off_counters) + 4;
+  a.row_counter = (unsigned long long*)(stage + L.off_counters) + kCtrTrie;
   cudaError_t e = cudaMemsetAsync(a.row_counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   const int64_t rows = re - rb;

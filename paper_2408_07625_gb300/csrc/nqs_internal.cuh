@@ -15,7 +15,15 @@ constexpr uint32_t kDummy = 0xFFFFFFFFu;     // padding slot of the search table
 constexpr int kHeavyTerms = 24;              // |P_XY| above this: warp-cooperative term loop
 constexpr int kQueueCap = 256;               // per-warp candidate queue (entries)
 constexpr int kRowsPerWarp = 8;              // rows scanned together by one warp
-constexpr int kChunk = 128;                  // records per scratch chunk (one-pass search)
+constexpr int kSortWarpMax = 512;           // rows with up to this many pairs are sorted by one warp
+constexpr int kSortBlockKeys = 16384;        // longer rows: one block, in shared memory up to this size
+
+// counter slots (uint64) of the workspace's counter region
+constexpr int kCtrItems = 0;                 // LoopOverTerms work items taken
+constexpr int kCtrBigCount = 1;              // long rows queued for the block sort
+constexpr int kCtrBigNext = 2;               // long rows taken by the block sort
+constexpr int kCtrBatch = 3;                 // LoopOverBatch row batches taken
+constexpr int kCtrTrie = 4;                  // LoopOverTrie rows taken
 
 // status bits (device status word)
 constexpr int kStatusDuplicate = 1;
@@ -39,7 +47,7 @@ struct nqs_ham_dev {
   int64_t heavy_end = 0;         // ids < heavy_end (and >= has_diag) are heavy
   int64_t max_group = 0;
   int64_t n_srch = 0;            // search-table slots, multiple of 32
-  int64_t half_begin[2] = {0, 0}, half_end[2] = {0, 0};  // groups of each half (top hash bit)
+  int n_segs = 0;                // segments of the search table (one per orientation qubit)
 
   uint64_t* xy = nullptr;        // [n_xy][W]
   uint32_t* row_ptr = nullptr;   // [n_xy + 1]
@@ -49,6 +57,8 @@ struct nqs_ham_dev {
   uint32_t* srch_hash = nullptr; // [n_srch]    linear hash of each pattern
   uint32_t* srch_id = nullptr;   // [n_srch]    pattern id or kDummy
   uint64_t* srch_rec = nullptr;  // [n_srch][rec_words]: (hash | id << 32), XY words (0 for padding)
+  int4* segs = nullptr;          // [n_segs] {t, first group, end group, 0}: the patterns whose highest
+                                 // set qubit is t, in groups of 32 slots; largest segments first
   int rec_words = 0;             // 64-bit words per search record (16-byte multiple)
   uint32_t* hash_basis = nullptr;// [64 * W]    R[b]: h(v) = XOR of R[b] over set bits b
   unsigned long long* xy_table = nullptr;  // XY hash set: slots of W key words + (id | hash << 32), id = ~0: empty
@@ -86,7 +96,10 @@ struct StageHeader {
   int32_t pad0;
   int64_t off_trie;     // prefix tree of U (LoopOverTrie)
   int64_t off_hx, off_table, off_bloom, off_scan, off_ampP, off_ampQ, off_ampK, off_geff, off_counters;
-  int64_t off_perm, off_rowcur;
+  int64_t off_q;        // per-qubit sample counts and fill cursors: uint32 [2][64 W]
+  int64_t off_qrows;    // per-qubit lists of the samples with that bit set: uint32 [n_unq * n_qubits]
+  int64_t off_big;      // rows queued for the block sort: int32 [n_unq]
+  int64_t off_rowcur;   // per-row fill cursors: int32 [n_unq]
   int64_t off_sched, off_order;   // row schedule of the energy and adjoint kernels
   int64_t scan_blocks;
   int64_t total_bytes;
@@ -104,37 +117,43 @@ int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
 // launchers (defined in the kernel translation units) -------------------------
+// staging: clears the membership structures, then hashes, tables, filter and
+// per-qubit lists of U (the header must already be in place)
 cudaError_t launch_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, char* stage,
                          const StageHeader& L, cudaStream_t s);
 
 // search modes: COUNT writes per-row counts, FILL writes pairs at given CSR
-// offsets, EMIT writes per-row counts and the pairs into scratch chunks
+// offsets, EMIT writes per-row counts and the pairs into scratch records
 enum SearchMode { kCount = 0, kFill = 1, kEmit = 2 };
 
-struct PairScratch {        // one-pass search scratch (caller memory)
-  int64_t max_chunks;
-  int64_t* cursor;          // [2]: next chunk, overflow flag
-  int32_t* heads;           // [2][nb_max] first chunk of each row batch and pass (-1: none), then
-                            // [2][nb_max] number of records of each row batch and pass
-  int32_t* next;            // [max_chunks]
-  uint64_t* records;        // [max_chunks * kChunk]: j | k << 32 | r << 61
+struct PairScratch {        // one-pass search scratch (caller memory): found pairs (i, j, k)
+  int64_t max_rec;
+  int64_t* cursor;          // [2]: records written, overflow flag
+  uint32_t* rec_i;          // [max_rec] the sample that found the pair (has the pattern's top qubit)
+  uint32_t* rec_j;          // [max_rec] the other sample
+  uint32_t* rec_k;          // [max_rec] pattern index
 };
 int64_t pair_scratch_bytes(int64_t rows, int64_t max_pairs);
 PairScratch pair_scratch_view(void* base, int64_t rows, int64_t bytes);
 
-cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, const char* stage,
+// LoopOverTerms.  COUNT: counts_or_rowptr = per-row counts (rows entries).
+// EMIT: the same counts, and the pairs into the scratch (compact afterwards).
+// FILL: counts_or_rowptr = CSR offsets; writes and sorts the rows.
+cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stage,
                                const StageHeader& L, int64_t row_begin, int64_t row_end,
                                int64_t* counts_or_rowptr, uint32_t* pair_j, uint32_t* pair_k,
                                int mode, const PairScratch* scratch, cudaStream_t s);
 
-cudaError_t launch_pairs_compact(const PairScratch& sc, const char* stage, const StageHeader& L, int64_t rb,
-                                 int64_t rows, const int64_t* row_ptr, uint32_t* pair_j, uint32_t* pair_k,
-                                 int64_t capacity, cudaStream_t s);
+// EMIT records -> CSR rows of [row_begin, row_begin + rows), sorted.  If the
+// pairs outgrow `capacity` or the scratch, sets kStatusCapacity and writes nothing.
+cudaError_t launch_pairs_compact(const nqs_ham* ham, const PairScratch& sc, char* stage, const StageHeader& L,
+                                 int64_t rb, int64_t rows, const int64_t* row_ptr, uint32_t* pair_j,
+                                 uint32_t* pair_k, int64_t capacity, cudaStream_t s);
 
-cudaError_t launch_pairs_batch(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, const char* stage,
+cudaError_t launch_pairs_batch(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, char* stage,
                                const StageHeader& L, int64_t row_begin, int64_t row_end,
                                int64_t* counts_or_rowptr, uint32_t* pair_j, uint32_t* pair_k,
-                               int mode, const PairScratch* scratch, cudaStream_t s);
+                               int mode, cudaStream_t s);
 
 // prefix trees (LoopOverTrie)
 void build_xy_trie(const std::vector<uint64_t>& xy, int64_t n_xy, int W, std::vector<int32_t>& nodes);

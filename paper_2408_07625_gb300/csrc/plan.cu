@@ -71,17 +71,15 @@ static cudaError_t enqueue_instance(PlanInstance& I, int precision, cudaStream_t
   cudaError_t e;
   int32_t* status = (int32_t*)(w + offsetof(StageHeader, status));
   if ((e = cudaMemsetAsync(status, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(w + I.L.off_table, 0xFF, 32 * I.L.cap, s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(w + I.L.off_bloom, 0, 2 * 4 * I.L.nwords, s)) != cudaSuccess) return e;
   if ((e = launch_stage(ham, I.in.U, n, w, I.L, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(I.row_ptr, 0, sizeof(int64_t), s)) != cudaSuccess) return e;
   if (I.schedule == NQS_SCHED_BATCH) {
-    if ((e = launch_pairs_batch(ham, I.in.U, n, w, I.L, 0, n, I.row_ptr + 1, nullptr, nullptr, kCount, nullptr, s)))
+    if ((e = launch_pairs_batch(ham, I.in.U, n, w, I.L, 0, n, I.row_ptr + 1, nullptr, nullptr, kCount, s)))
       return e;
     if ((e = launch_scan(I.row_ptr + 1, n, w, I.L, s)) != cudaSuccess) return e;
     capacity_check_kernel<<<1, 32, 0, s>>>(I.row_ptr, n, I.capacity, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = launch_pairs_batch(ham, I.in.U, n, w, I.L, 0, n, I.row_ptr, I.pair_j, I.pair_k, kFill, nullptr, s)))
+    if ((e = launch_pairs_batch(ham, I.in.U, n, w, I.L, 0, n, I.row_ptr, I.pair_j, I.pair_k, kFill, s)))
       return e;
   } else if (I.schedule == NQS_SCHED_TRIE) {
     if ((e = launch_trie_build(ham, I.in.U, n, w, I.L, s)) != cudaSuccess) return e;
@@ -97,7 +95,7 @@ static cudaError_t enqueue_instance(PlanInstance& I, int precision, cudaStream_t
     if ((e = launch_pairs_terms(ham, I.in.U, w, I.L, 0, n, I.row_ptr + 1, nullptr, nullptr, kEmit, &sc, s)))
       return e;
     if ((e = launch_scan(I.row_ptr + 1, n, w, I.L, s)) != cudaSuccess) return e;
-    if ((e = launch_pairs_compact(sc, w, I.L, 0, n, I.row_ptr, I.pair_j, I.pair_k, I.capacity, s)))
+    if ((e = launch_pairs_compact(ham, sc, w, I.L, 0, n, I.row_ptr, I.pair_j, I.pair_k, I.capacity, s)))
       return e;
   }
   if ((e = launch_amplitudes(I.in.logpsi_re, nullptr, n, precision, w, I.L, s)) != cudaSuccess) return e;

@@ -154,8 +154,8 @@ int nqs_stage_status(const void* work, void* stream);
  *   first (if the XY = 0 pattern exists), then the others in an order fixed
  *   by the schedule and the row alone: it depends neither on the row range
  *   nor on the call (count, fill and one-pass calls agree).  LoopOverTerms
- *   lists pairs whose P_XY is large before the rest.  Both (i, j) and (j, i)
- *   are listed.  NQS_SCHED_TRIE needs nqs_stage_trie after nqs_stage.
+ *   lists them by ascending column.  Both (i, j) and (j, i) are listed.
+ *   NQS_SCHED_TRIE needs nqs_stage_trie after nqs_stage.
  * All calls need a workspace staged with the same U.  Readers of the CSR
  * (fill, energy, adjoint) take positions relative to row_ptr[0], so a slice
  * row_ptr + (r0 - row_begin) of a larger offset array can be passed for the

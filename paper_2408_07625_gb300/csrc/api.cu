@@ -552,7 +552,10 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
   }
   if (((uintptr_t)scratch) & 255) return fail(NQS_ERR_ARG, "scratch not 256-byte aligned");
   PairScratch sc = pair_scratch_view(scratch, rows, scratch_bytes);
-  if (sc.max_rec < 1) return fail(NQS_ERR_CAPACITY, "scratch too small");
+  if (sc.max_pairs < 1) {  // no room at all: count only, so that row_ptr and *n_pairs are valid
+    rc = nqs_count_coupled_pairs(ham, U, n, work, rb, re, schedule, row_ptr, n_pairs, stream);
+    return rc ? rc : fail(NQS_ERR_CAPACITY, "scratch too small");
+  }
   if ((rc = count_pass(ham, U, n, work, L, rb, re, schedule, row_ptr, &sc, s))) return rc;
   int64_t overflow = 0;
   cudaError_t e = cudaMemcpyAsync(n_pairs, row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
@@ -560,7 +563,7 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
   e = cudaMemcpyAsync(&overflow, sc.cursor + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_fail(e, "flag copy");
   if ((rc = read_status(work, s))) return rc;
-  if (overflow) return fail(NQS_ERR_CAPACITY, "scratch too small for the pairs found");
+  if (overflow || *n_pairs > sc.max_pairs) return fail(NQS_ERR_CAPACITY, "scratch too small for the pairs found");
   if (*n_pairs > capacity) return fail(NQS_ERR_CAPACITY, "pair capacity too small");
   if (rows == 0 || *n_pairs == 0) return NQS_OK;
   if (!pair_j || !pair_k) return fail(NQS_ERR_ARG, "null pair arrays");

@@ -17,8 +17,8 @@
 // matching group.  For peaked molecular batches high qubits are rarely
 // occupied, which cuts the probes by an order of magnitude against probing
 // every (sample, pattern).  Each pair found is written to both of its rows,
-// and each row is then sorted by pattern index, so the list of a row (the
-// diagonal pair first, then ascending pattern index) depends on the row alone.
+// and each row is then sorted by column, so the list of a row (the diagonal
+// pair first, then ascending column index) depends on the row alone.
 #include <cstring>
 
 #include "device_util.cuh"
@@ -115,6 +115,30 @@ __global__ void stage_kernel(const uint64_t* __restrict__ U, int64_t n, int n_qu
     if (qc[q]) atomicAdd(&qcnt[q], qc[q]);
 }
 
+// Exclusive scan of n <= 256 values in shared memory by one warp (each lane
+// takes a contiguous run of ceil(n / 32) values); the total goes to *total.
+__device__ __forceinline__ void warp_exclusive_scan(int64_t* v, int n, int64_t* total) {
+  const int lane = threadIdx.x & 31;
+  const int per = (n + 31) / 32;
+  const int lo = lane * per < n ? lane * per : n;
+  const int hi = lo + per < n ? lo + per : n;
+  int64_t sum = 0;
+  for (int i = lo; i < hi; ++i) sum += v[i];
+  int64_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  int64_t run = incl - sum;
+  for (int i = lo; i < hi; ++i) {
+    const int64_t x = v[i];
+    v[i] = run;
+    run += x;
+  }
+  if (lane == 31 && total) *total = incl;
+}
+
 // Per-qubit lists: the samples with bit q set, for every qubit q.  Each block
 // takes a contiguous slice of U, counts its samples per qubit, reserves that
 // many places in each list (one atomic per qubit and block), then writes the
@@ -148,13 +172,9 @@ __global__ void qubit_rows_kernel(const uint64_t* __restrict__ U, int64_t n, int
   for (int c = 0; c < 2 * W; ++c)
     if (mine[c]) atomicAdd(&cnt[32 * c + lane], mine[c]);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int64_t run = 0;
-    for (int q = 0; q < 64 * W; ++q) {
-      base[q] = run;
-      run += qcnt[q];
-    }
-  }
+  for (int q = threadIdx.x; q < 64 * W; q += blockDim.x) base[q] = qcnt[q];
+  __syncthreads();
+  if (threadIdx.x < 32) warp_exclusive_scan(base, 64 * W, nullptr);
   __syncthreads();
   for (int q = threadIdx.x; q < 64 * W; q += blockDim.x) {
     if (cnt[q]) base[q] += atomicAdd(&qcur[q], cnt[q]);
@@ -219,13 +239,24 @@ cudaError_t launch_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, char*
 }
 
 // --------------------------------------------------------------------------
-// one-pass scratch: three uint32 arrays of found pairs (i, j, k)
+// one-pass scratch: three uint32 arrays of found pairs (i, j, k), handed out
+// to the search warps in chunks of kRecChunk records; the unused tail of a
+// warp's last chunk is marked with i = kNoRecord
 // --------------------------------------------------------------------------
 static inline int64_t a256(int64_t v) { return (v + 255) & ~int64_t(255); }
+constexpr int kSearchThreads = 1024;
+constexpr int kSearchWarps = kSearchThreads / 32;
+constexpr int kRecChunk = 128;
+constexpr uint32_t kNoRecord = 0xFFFFFFFFu;
 
+static inline int64_t rec_slack() { return (int64_t)num_sms() * kSearchWarps * kRecChunk; }
+
+// records for up to max_pairs + slack pairs (a record serves at most two rows
+// and at least one of the range), then one 64-bit sort key per pair
 int64_t pair_scratch_bytes(int64_t rows, int64_t max_pairs) {
-  (void)rows;  // a record serves at most two rows and at least one of the range
-  return 256 + 3 * a256(4 * std::max<int64_t>(max_pairs, 1));
+  (void)rows;
+  const int64_t m = std::max<int64_t>(max_pairs, 1);
+  return 256 + 3 * a256(4 * (m + rec_slack())) + a256(8 * m);
 }
 
 PairScratch pair_scratch_view(void* base, int64_t rows, int64_t bytes) {
@@ -233,13 +264,16 @@ PairScratch pair_scratch_view(void* base, int64_t rows, int64_t bytes) {
   PairScratch sc;
   char* p = (char*)base;
   sc.cursor = (int64_t*)p;
-  int64_t m = (bytes - 256) / 12;
-  while (m > 0 && 3 * a256(4 * m) > bytes - 256) --m;
-  sc.max_rec = std::max<int64_t>(m, 0);
+  // 12 bytes of records per pair (plus the slack) and 8 of sort key, each array 256-byte aligned
+  int64_t m = std::max<int64_t>((bytes - 256 - 12 * rec_slack()) / 20, 0);  // at most ~50 too large
+  while (m > 0 && pair_scratch_bytes(rows, m) > bytes) --m;
+  sc.max_pairs = m;
+  sc.max_rec = m > 0 ? m + rec_slack() : 0;
   const int64_t stride = a256(4 * std::max<int64_t>(sc.max_rec, 1));
   sc.rec_i = (uint32_t*)(p + 256);
   sc.rec_j = (uint32_t*)(p + 256 + stride);
   sc.rec_k = (uint32_t*)(p + 256 + 2 * stride);
+  sc.keys = (uint64_t*)(p + 256 + 3 * stride);
   return sc;
 }
 
@@ -253,10 +287,10 @@ PairScratch pair_scratch_view(void* base, int64_t rows, int64_t bytes) {
 // rows whose filter test passed; slots with a hit go to a per-warp queue,
 // which is verified lane-parallel against the hash table when full.
 // --------------------------------------------------------------------------
-constexpr int kSearchThreads = 1024;
-constexpr int kSearchWarps = kSearchThreads / 32;
 constexpr int R = kRowsPerWarp;
 constexpr int kMaxSegs = 64 * kMaxWords;
+constexpr int kItemsPerGrab = 4;   // work items a warp takes per atomic
+constexpr int kGroupsPerItem = 16; // search-table groups per work item (bounds an item's length)
 
 struct TermsArgs {
   const uint64_t* U;
@@ -309,11 +343,16 @@ __device__ __forceinline__ void place_pair(const int64_t* rp, int64_t r, int32_t
   }
 }
 
+struct RecState {  // warp-uniform: current record chunk (base < 0: none) and its fill
+  int64_t base;
+  int fill;
+};
+
 // One round of verified candidates (lane order).  The pair (i, j) with
 // i = the item's row r is listed in row i and in row j.
 template <int MODE, int W>
 __device__ __forceinline__ void emit_found(bool found, int r, uint32_t j, uint32_t id, RowCache<W>* rc,
-                                           const TermsArgs& a) {
+                                           RecState& rs, const TermsArgs& a) {
   const int lane = threadIdx.x & 31;
   const int64_t i = found ? rc->row[r] : -1;
   const bool in_i = found && i >= a.row_begin && i < a.row_end;
@@ -328,19 +367,30 @@ __device__ __forceinline__ void emit_found(bool found, int r, uint32_t j, uint32
   if (MODE == kEmit) {
     const bool keep = in_i || in_j;
     const uint32_t m = __ballot_sync(kFull, keep);
-    if (m == 0u) return;
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd((unsigned long long*)a.sc.cursor, (unsigned long long)__popc(m));
-    base = __shfl_sync(kFull, base, 0);
-    if (keep) {
-      const int64_t q = (int64_t)base + __popc(m & ((1u << lane) - 1u));
-      if (q < a.sc.max_rec) {
-        a.sc.rec_i[q] = (uint32_t)i;
-        a.sc.rec_j[q] = j;
-        a.sc.rec_k[q] = id;
-      } else {
-        a.sc.cursor[1] = 1;
+    const int n = __popc(m);
+    if (n == 0) return;
+    const int off = __popc(m & ((1u << lane) - 1u));
+    const int room = rs.base >= 0 ? kRecChunk - rs.fill : 0;
+    int64_t q = -1;
+    if (off < room) q = rs.base + rs.fill + off;
+    if (n > room) {  // the rest goes to a fresh chunk
+      long long fresh = -1;
+      if (lane == 0) {
+        const unsigned long long c = atomicAdd((unsigned long long*)a.sc.cursor, (unsigned long long)kRecChunk);
+        if ((int64_t)c + kRecChunk <= a.sc.max_rec) fresh = (long long)c;
+        else a.sc.cursor[1] = 1;  // scratch too small: counting goes on, the list is completed by a fill pass
       }
+      fresh = __shfl_sync(kFull, fresh, 0);
+      if (off >= room && fresh >= 0) q = fresh + (off - room);
+      rs.base = fresh;
+      rs.fill = fresh >= 0 ? n - room : kRecChunk;
+    } else {
+      rs.fill += n;
+    }
+    if (keep && q >= 0) {
+      a.sc.rec_i[q] = (uint32_t)i;
+      a.sc.rec_j[q] = j;
+      a.sc.rec_k[q] = id;
     }
   }
 }
@@ -391,7 +441,8 @@ template <int W>
 struct FlushWays { static constexpr int value = W == 1 ? 2 : 1; };
 
 template <int W, int MODE>
-__device__ __forceinline__ void verify_items(const uint32_t* q, int qn, RowCache<W>* rc, const TermsArgs& a) {
+__device__ __forceinline__ void verify_items(const uint32_t* q, int qn, RowCache<W>* rc, RecState& rs,
+                                             const TermsArgs& a) {
   constexpr int kWays = FlushWays<W>::value;
   const int lane = threadIdx.x & 31;
   for (int e0 = 0; e0 < qn; e0 += 32 * kWays) {
@@ -439,7 +490,7 @@ __device__ __forceinline__ void verify_items(const uint32_t* q, int qn, RowCache
         found = verify_slow<W>(r[u], pos[u], sh, rc, a, j);
       }
       found = found && id != kDummy;  // padding slots carry XY = 0 and never count
-      if (e0 + u * 32 < qn) emit_found<MODE, W>(found, r[u], j, id, rc, a);
+      if (e0 + u * 32 < qn) emit_found<MODE, W>(found, r[u], j, id, rc, rs, a);
     }
   }
 }
@@ -451,13 +502,13 @@ constexpr int kXbufCap = 384;
 
 template <int W, int MODE>
 __device__ __forceinline__ void flush_queue(const uint32_t* q, int qn, uint32_t* xbuf, RowCache<W>* rc,
-                                            const TermsArgs& a) {
+                                            RecState& rs, const TermsArgs& a) {
   const int lane = threadIdx.x & 31;
   int xn = 0;
   for (int c0 = 0; c0 < qn; c0 += 32) {
     if (xn + 32 * R > kXbufCap) {
       __syncwarp();
-      verify_items<W, MODE>(xbuf, xn, rc, a);
+      verify_items<W, MODE>(xbuf, xn, rc, rs, a);
       __syncwarp();
       xn = 0;
     }
@@ -481,7 +532,7 @@ __device__ __forceinline__ void flush_queue(const uint32_t* q, int qn, uint32_t*
     xn += __shfl_sync(kFull, incl, 31);
   }
   __syncwarp();
-  verify_items<W, MODE>(xbuf, xn, rc, a);
+  verify_items<W, MODE>(xbuf, xn, rc, rs, a);
   __syncwarp();
 }
 
@@ -500,18 +551,16 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
     uint4* dst = reinterpret_cast<uint4*>(bloom);
     for (int i = threadIdx.x; i < a.nwords / 4; i += blockDim.x) dst[i] = __ldg(src + i);
   }
-  if (threadIdx.x == 0) {  // list offsets per qubit; work items per segment (prefix)
-    int64_t run = 0;
-    for (int q = 0; q < a.nq; ++q) {
-      s_qoff[q] = run;
-      run += a.qcnt[q];
-    }
-    int64_t c = 0;
-    for (int sg = 0; sg < a.n_segs; ++sg) {
-      s_cum[sg] = c;
-      c += ((int64_t)a.qcnt[__ldg(&a.segs[sg].x)] + R - 1) / R;
-    }
-    s_cum[a.n_segs] = c;
+  // list offsets per qubit; work items per segment (exclusive prefix, total last)
+  for (int qq = threadIdx.x; qq < a.nq; qq += blockDim.x) s_qoff[qq] = a.qcnt[qq];
+  for (int sg = threadIdx.x; sg < a.n_segs; sg += blockDim.x) {
+    const int4 g = __ldg(&a.segs[sg]);
+    s_cum[sg] = ((int64_t)a.qcnt[g.x] + R - 1) / R * ((g.z - g.y + kGroupsPerItem - 1) / kGroupsPerItem);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    warp_exclusive_scan(s_qoff, a.nq, nullptr);
+    warp_exclusive_scan(s_cum, a.n_segs, s_cum + a.n_segs);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -523,74 +572,96 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
   const int64_t n_items = s_cum[a.n_segs];
   const uint32_t wmask4 = a.wmask << 2;
   const char* bloom_bytes = reinterpret_cast<const char*>(bloom);
+  RecState rs{-1, kRecChunk};
+  int cur_seg = -1;
+  int64_t cur_batch = -1;
   while (true) {
     unsigned long long itu = 0;
-    if (lane == 0) itu = atomicAdd(a.item_counter, 1ull);
-    const int64_t it = (int64_t)__shfl_sync(kFull, itu, 0);
-    if (it >= n_items) break;
-    int lo = 0, hi = a.n_segs;  // s_cum[lo] <= it < s_cum[hi]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (s_cum[mid] <= it) lo = mid; else hi = mid;
-    }
-    const int4 sg = __ldg(&a.segs[lo]);
-    const int64_t b0 = (it - s_cum[lo]) * R;
-    const int64_t count_t = (int64_t)a.qcnt[sg.x];
-    __syncwarp();
-    if (lane < R) {
-      const bool valid = b0 + lane < count_t;
-      const int64_t row = valid ? (int64_t)__ldg(a.qrows + s_qoff[sg.x] + b0 + lane) : -1;
+    if (lane == 0) itu = atomicAdd(a.item_counter, (unsigned long long)kItemsPerGrab);
+    const int64_t it0 = (int64_t)__shfl_sync(kFull, itu, 0);
+    if (it0 >= n_items) break;
+    const int64_t it1 = it0 + kItemsPerGrab < n_items ? it0 + kItemsPerGrab : n_items;
+    for (int64_t it = it0; it < it1; ++it) {
+      int lo = 0, hi = a.n_segs;  // s_cum[lo] <= it < s_cum[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_cum[mid] <= it) lo = mid; else hi = mid;
+      }
+      // item = (segment, batch of R list entries, chunk of kGroupsPerItem groups)
+      const int4 sg = __ldg(&a.segs[lo]);
+      const int n_chunks = (sg.z - sg.y + kGroupsPerItem - 1) / kGroupsPerItem;
+      const int64_t local = it - s_cum[lo];
+      const int64_t batch = local / n_chunks;
+      const int g0 = sg.y + (int)(local - batch * n_chunks) * kGroupsPerItem;
+      const int g1 = g0 + kGroupsPerItem < sg.z ? g0 + kGroupsPerItem : sg.z;
+      if (lo != cur_seg || batch != cur_batch) {  // new rows (consecutive chunks share them)
+        cur_seg = lo;
+        cur_batch = batch;
+        const int64_t b0 = batch * R;
+        const int64_t count_t = (int64_t)a.qcnt[sg.x];
+        __syncwarp();
+        if (lane < R) {
+          const bool valid = b0 + lane < count_t;
+          const int64_t row = valid ? (int64_t)__ldg(a.qrows + s_qoff[sg.x] + b0 + lane) : -1;
 #pragma unroll
-      for (int w = 0; w < W; ++w) rc->u[lane][w] = valid ? __ldg(a.U + row * W + w) : 0ull;
-      rc->hx[lane] = valid ? __ldg(a.hx + row) : 0u;
-      rc->cnt[lane] = 0u;
-      rc->row[lane] = row;
-    }
-    __syncwarp();
-    uint32_t hr4[R], hr17[R], hr22[R];
-    uint32_t vmask = 0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const uint32_t h = rc->hx[r];
-      hr4[r] = h << 2;
-      hr17[r] = h >> 17;
-      hr22[r] = h >> 22;
-      if (rc->row[r] >= 0) vmask |= 1u << (R - 1 - r);
-    }
-    int qn = 0;
-    for (int g = sg.y; g < sg.z; ++g) {
-      const uint32_t pos = (uint32_t)(g * 32 + lane);
-      const uint32_t hk = __ldg(a.srch_hash + pos);
-      const uint32_t hk4 = hk << 2, hk17 = hk >> 17, hk22 = hk >> 22;
-      uint32_t hm = 0;
+          for (int w = 0; w < W; ++w) rc->u[lane][w] = valid ? __ldg(a.U + row * W + w) : 0ull;
+          rc->hx[lane] = valid ? __ldg(a.hx + row) : 0u;
+          rc->cnt[lane] = 0u;
+          rc->row[lane] = row;
+        }
+        __syncwarp();
+      }
+      uint32_t hr4[R], hr17[R], hr22[R];
+      uint32_t vmask = 0;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const uint32_t w = *reinterpret_cast<const uint32_t*>(bloom_bytes + ((hr4[r] ^ hk4) & wmask4));
-        const uint32_t t = __funnelshift_r(w, w, hr17[r] ^ hk17) & __funnelshift_r(w, w, hr22[r] ^ hk22);
-        hm = (hm << 1) | (t & 1u);
+        const uint32_t h = rc->hx[r];
+        hr4[r] = h << 2;
+        hr17[r] = h >> 17;
+        hr22[r] = h >> 22;
+        if (rc->row[r] >= 0) vmask |= 1u << (R - 1 - r);
       }
-      hm &= vmask;
-      const uint32_t bal = __ballot_sync(kFull, hm != 0u);
-      if (bal) {
-        if (hm) q[qn + __popc(bal & lt)] = (hm << 24) | pos;
-        qn += __popc(bal);
-        if (qn > kQueueCap - 32) {
-          __syncwarp();
-          flush_queue<W, MODE>(q, qn, xbuf, rc, a);
-          __syncwarp();
-          qn = 0;
+      int qn = 0;
+      uint32_t hk_next = __ldg(a.srch_hash + (uint32_t)(g0 * 32 + lane));
+      for (int g = g0; g < g1; ++g) {
+        const uint32_t pos = (uint32_t)(g * 32 + lane);
+        const uint32_t hk = hk_next;
+        if (g + 1 < g1) hk_next = __ldg(a.srch_hash + pos + 32);  // next group's hashes in flight
+        const uint32_t hk4 = hk << 2, hk17 = hk >> 17, hk22 = hk >> 22;
+        uint32_t hm = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const uint32_t w = *reinterpret_cast<const uint32_t*>(bloom_bytes + ((hr4[r] ^ hk4) & wmask4));
+          const uint32_t t = __funnelshift_r(w, w, hr17[r] ^ hk17) & __funnelshift_r(w, w, hr22[r] ^ hk22);
+          hm = (hm << 1) | (t & 1u);
+        }
+        hm &= vmask;
+        const uint32_t bal = __ballot_sync(kFull, hm != 0u);
+        if (bal) {
+          if (hm) q[qn + __popc(bal & lt)] = (hm << 24) | pos;
+          qn += __popc(bal);
+          if (qn > kQueueCap - 32) {
+            __syncwarp();
+            flush_queue<W, MODE>(q, qn, xbuf, rc, rs, a);
+            __syncwarp();
+            qn = 0;
+          }
         }
       }
-    }
-    __syncwarp();
-    flush_queue<W, MODE>(q, qn, xbuf, rc, a);
-    __syncwarp();
-    if (MODE != kFill && lane < R) {
-      const int64_t row = rc->row[lane];
-      if (row >= a.row_begin && row < a.row_end && rc->cnt[lane])
-        atomicAdd((unsigned long long*)(a.counts + (row - a.row_begin)), (unsigned long long)rc->cnt[lane]);
-    }
+      __syncwarp();
+      flush_queue<W, MODE>(q, qn, xbuf, rc, rs, a);
+      __syncwarp();
+      if (MODE != kFill && lane < R) {
+        const int64_t row = rc->row[lane];
+        if (row >= a.row_begin && row < a.row_end && rc->cnt[lane])
+          atomicAdd((unsigned long long*)(a.counts + (row - a.row_begin)), (unsigned long long)rc->cnt[lane]);
+        rc->cnt[lane] = 0u;
+      }
+      __syncwarp();
+    }  // items of this grab
   }
+  if (MODE == kEmit && rs.base >= 0)  // mark the unused tail of the last chunk
+    for (int f = rs.fill + lane; f < kRecChunk; f += 32) a.sc.rec_i[rs.base + f] = kNoRecord;
 }
 
 template <int W>
@@ -611,16 +682,17 @@ static cudaError_t launch_terms_w(const TermsArgs& args, const StageHeader& L, c
 
 // --------------------------------------------------------------------------
 // CSR assembly: row initialisation (diagonal pair, cursors), scatter of the
-// one-pass records, and the per-row sort by pattern index.
+// one-pass records, and the per-row sort by column.
 // --------------------------------------------------------------------------
 
 // COUNT/EMIT: counts[r] = has_diag.  FILL: cursor[r] = has_diag and the
-// diagonal pair at the row's start.  In FILL mode, if the pairs outgrow
-// `capacity` or the scratch overflowed, flag the status and write nothing.
+// diagonal pair at the row's start (it leads the row and is not sorted).  In
+// FILL mode, if the pairs outgrow `capacity` or the scratch overflowed, flag
+// the status and write nothing.
 __global__ void pairs_init_kernel(int mode, int64_t rows, int64_t rb, int has_diag, int64_t* __restrict__ counts,
                                   const int64_t* __restrict__ rp, int32_t* __restrict__ cursor,
-                                  uint32_t* __restrict__ pj, uint32_t* __restrict__ pk, int64_t capacity,
-                                  const int64_t* __restrict__ overflow, int32_t* __restrict__ status) {
+                                  uint32_t* __restrict__ pj, uint32_t* __restrict__ pk, int64_t capacity, const int64_t* __restrict__ overflow,
+                                  int32_t* __restrict__ status) {
   if (mode == kFill) {
     const bool too_small = (capacity >= 0 && rp[rows] - rp[0] > capacity) || (overflow && *overflow != 0);
     if (too_small) {
@@ -643,112 +715,198 @@ __global__ void pairs_init_kernel(int mode, int64_t rows, int64_t rb, int has_di
   }
 }
 
+// records -> sort keys grouped by row (each pair in both of its rows)
 __global__ void pairs_scatter_kernel(PairScratch sc, int64_t rb, int64_t re, const int64_t* __restrict__ rp,
-                                     int32_t* __restrict__ cursor, uint32_t* __restrict__ pj,
-                                     uint32_t* __restrict__ pk, int32_t* __restrict__ status) {
+                                     int32_t* __restrict__ cursor, int32_t* __restrict__ status) {
   if (*(volatile const int32_t*)status & kStatusCapacity) return;
   const int64_t n_rec = *sc.cursor < sc.max_rec ? *sc.cursor : sc.max_rec;
+  const int64_t p0 = rp[0];
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_rec; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = sc.rec_i[q], j = sc.rec_j[q];
-    const uint32_t k = sc.rec_k[q];
-    if (i >= rb && i < re) place_pair(rp, i - rb, cursor, pj, pk, (uint32_t)j, k, status);
-    if (j >= rb && j < re) place_pair(rp, j - rb, cursor, pj, pk, (uint32_t)i, k, status);
-  }
-}
-
-// Bitonic sorting network whose comparators all put the minimum at the lower
-// index: for block sizes k = 2, 4, .., N, first compare i with i XOR (k - 1)
-// (each position of the lower half with its mirror image), then i with
-// i XOR d for d = k/4, .., 1.  Keys beyond the row's length act as +infinity
-// and, sitting at the higher index of every comparator they take part in,
-// never move, so no padding needs to be stored.
-// Warp version: key index e = lane * S + s (S keys per lane, in registers).
-template <int S>
-__device__ __forceinline__ void warp_cmpx(uint64_t (&v)[S], int m) {
-  const int lane = threadIdx.x & 31;
-  const int hb = 1 << (31 - __clz(m));  // highest bit of m: e is the lower index iff (e & hb) == 0
-  if (m < S) {
+    const uint32_t ri = sc.rec_i[q];
+    if (ri == kNoRecord) continue;
+    const int64_t i = ri, j = sc.rec_j[q];
+    const uint64_t k = sc.rec_k[q];
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      if ((s & hb) == 0) {
-        const int s2 = s ^ m;
-        const uint64_t x = v[s], y = v[s2];
-        v[s] = x < y ? x : y;
-        v[s2] = x < y ? y : x;
-      }
-    }
-  } else {
-    const int ml = m / S, ms = m & (S - 1);
-    const bool lower = (lane & (hb / S)) == 0;
-    uint64_t t[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) t[s] = __shfl_xor_sync(kFull, v[s ^ ms], ml);
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      const bool less = v[s] < t[s];
-      v[s] = (lower == less) ? v[s] : t[s];
+    for (int side = 0; side < 2; ++side) {
+      const int64_t r = (side ? j : i) - rb;
+      if (r < 0 || r >= re - rb) continue;
+      const int64_t a = rp[r] - p0;
+      const int64_t len = rp[r + 1] - p0 - a;
+      const int64_t c = atomicAdd(cursor + r, 1);
+      if (c < len) sc.keys[a + c] = ((uint64_t)(side ? i : j) << 32) | k;
+      else atomicOr(status, kStatusLimit);
     }
   }
 }
 
-template <int S>
-__device__ __forceinline__ void warp_sort_row(uint32_t* __restrict__ pj, uint32_t* __restrict__ pk, int n) {
+// A pair's sort key: column above, pattern index below (the column is unique
+// within a row).
+__device__ __forceinline__ uint64_t pair_key(const uint64_t* keys, const uint32_t* pj, const uint32_t* pk,
+                                             int64_t e) {
+  return keys ? keys[e] : (((uint64_t)pj[e] << 32) | pk[e]);
+}
+__device__ __forceinline__ void put_pair(uint32_t* pj, uint32_t* pk, int64_t e, uint64_t key) {
+  pj[e] = (uint32_t)(key >> 32);
+  pk[e] = (uint32_t)key;
+}
+
+__device__ __forceinline__ void warp_exclusive_scan_u32(uint32_t* v, int n) {
   const int lane = threadIdx.x & 31;
+  const int per = (n + 31) / 32;
+  const int lo = lane * per < n ? lane * per : n;
+  const int hi = lo + per < n ? lo + per : n;
+  uint32_t sum = 0;
+  for (int i = lo; i < hi; ++i) sum += v[i];
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  uint32_t run = incl - sum;
+  for (int i = lo; i < hi; ++i) {
+    const uint32_t x = v[i];
+    v[i] = run;
+    run += x;
+  }
+}
+
+// One row of n <= 32 S pairs, sorted by a warp.  The keys are spread over
+// 32 S buckets by linear interpolation of the column between the row's
+// smallest and largest; each key takes a slot in its bucket (shared
+// atomics), the buckets' starts come from a scan, and each lane then
+// insertion-sorts its buckets.  Returns false, writing nothing, when the
+// largest bucket holds more than kBucketMax keys (clustered columns): the
+// row then goes to the block sort.
+constexpr int kBucketMax = 16;
+
+template <int S>
+__device__ __forceinline__ bool warp_sort_row(int64_t a, int n, const uint64_t* keys, uint32_t* pj, uint32_t* pk,
+                                              uint32_t* cnt, uint64_t* buf) {
+  const int lane = threadIdx.x & 31;
+  constexpr int B = 32 * S;
   uint64_t v[S];
+  uint32_t cmin = 0xFFFFFFFFu, cmax = 0u;
 #pragma unroll
   for (int s = 0; s < S; ++s) {
-    const int e = lane * S + s;
-    v[s] = e < n ? (((uint64_t)pk[e] << 32) | pj[e]) : ~0ull;
-  }
-#pragma unroll
-  for (int k = 2; k <= 32 * S; k <<= 1) {
-    warp_cmpx<S>(v, k - 1);
-#pragma unroll
-    for (int d = k >> 2; d >= 1; d >>= 1) warp_cmpx<S>(v, d);
-  }
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const int e = lane * S + s;
+    const int e = s * 32 + lane;
+    v[s] = e < n ? pair_key(keys, pj, pk, a + e) : 0ull;
     if (e < n) {
-      pj[e] = (uint32_t)v[s];
-      pk[e] = (uint32_t)(v[s] >> 32);
+      cmin = min(cmin, (uint32_t)(v[s] >> 32));
+      cmax = max(cmax, (uint32_t)(v[s] >> 32));
     }
   }
+  cmin = __reduce_min_sync(kFull, cmin);
+  cmax = __reduce_max_sync(kFull, cmax);
+  const uint64_t span = (uint64_t)(cmax - cmin) + 1;
+  for (int b = lane; b < B; b += 32) cnt[b] = 0u;
+  __syncwarp();
+  uint32_t place[S];  // bucket << 16 | slot in the bucket
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int e = s * 32 + lane;
+    if (e < n) {
+      const uint32_t bk = (uint32_t)((((v[s] >> 32) - cmin) * (uint64_t)B) / span);
+      place[s] = (bk << 16) | atomicAdd(&cnt[bk], 1u);
+    }
+  }
+  __syncwarp();
+  uint32_t big = 0u;
+  for (int b = lane; b < B; b += 32) big = max(big, cnt[b]);
+  if (__reduce_max_sync(kFull, big) > kBucketMax) return false;
+  if (B > 32) {
+    warp_exclusive_scan_u32(cnt, B);
+  } else {  // one bucket per lane
+    const uint32_t x = cnt[lane];
+    uint32_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += t;
+    }
+    cnt[lane] = incl - x;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int e = s * 32 + lane;
+    if (e < n) buf[cnt[place[s] >> 16] + (place[s] & 0xFFFFu)] = v[s];
+  }
+  __syncwarp();
+  for (int b = lane; b < B; b += 32) {
+    const int lo = (int)cnt[b];
+    const int hi = b + 1 < B ? (int)cnt[b + 1] : n;
+    for (int x = lo + 1; x < hi; ++x) {
+      const uint64_t key = buf[x];
+      int y = x - 1;
+      while (y >= lo && buf[y] > key) {
+        buf[y + 1] = buf[y];
+        --y;
+      }
+      buf[y + 1] = key;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int e = s * 32 + lane;
+    if (e < n) put_pair(pj, pk, a + e, buf[e]);
+  }
+  __syncwarp();
+  return true;
 }
 
-__global__ void sort_rows_warp_kernel(const int64_t* __restrict__ rp, int64_t rows, uint32_t* __restrict__ pj,
-                                      uint32_t* __restrict__ pk, int has_diag, int32_t* __restrict__ big,
-                                      unsigned long long* __restrict__ big_count,
-                                      const int32_t* __restrict__ status) {
+constexpr int kSortWarpThreads = 256;
+constexpr int kSortWarpWarps = kSortWarpThreads / 32;
+
+// Rows of up to kSortWarpMax pairs, one warp each; longer rows, and rows
+// with clustered columns, are queued for the block kernel.  The diagonal
+// pair leads its row and is not sorted.  With `keys` the rows are read from
+// the scatter's sort keys; without, pj/pk are sorted in place.
+__global__ void __launch_bounds__(kSortWarpThreads)
+sort_rows_warp_kernel(const int64_t* __restrict__ rp, int64_t rows, const uint64_t* __restrict__ keys,
+                      uint32_t* __restrict__ pj, uint32_t* __restrict__ pk, int has_diag, int32_t* __restrict__ big,
+                      unsigned long long* __restrict__ big_count, const int32_t* __restrict__ status) {
+  __shared__ uint32_t s_cnt[kSortWarpWarps][kSortWarpMax];
+  __shared__ uint64_t s_buf[kSortWarpWarps][kSortWarpMax];
   if (*(volatile const int32_t*)status & kStatusCapacity) return;
   const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+  const int warp = threadIdx.x >> 5;
+  const int64_t nw = (int64_t)gridDim.x * kSortWarpWarps;
   const int64_t p0 = rp[0];
-  for (int64_t r = blockIdx.x * (int64_t)(blockDim.x / 32) + (threadIdx.x >> 5); r < rows; r += nw) {
+  for (int64_t r = blockIdx.x * (int64_t)kSortWarpWarps + warp; r < rows; r += nw) {
     const int64_t a = rp[r] - p0 + has_diag;
     const int64_t n = rp[r + 1] - p0 - a;
-    if (n <= 1) continue;
-    uint32_t* rj = pj + a;
-    uint32_t* rk = pk + a;
-    if (n <= 32) warp_sort_row<1>(rj, rk, (int)n);
-    else if (n <= 64) warp_sort_row<2>(rj, rk, (int)n);
-    else if (n <= 128) warp_sort_row<4>(rj, rk, (int)n);
-    else if (n <= 256) warp_sort_row<8>(rj, rk, (int)n);
-    else if (n <= kSortWarpMax) warp_sort_row<16>(rj, rk, (int)n);
-    else if (lane == 0) big[atomicAdd(big_count, 1ull)] = (int32_t)r;
+    if (n <= 0 || (n == 1 && !keys)) continue;
+    bool done = false;
+    if (n <= 32) done = warp_sort_row<1>(a, (int)n, keys, pj, pk, s_cnt[warp], s_buf[warp]);
+    else if (n <= 64) done = warp_sort_row<2>(a, (int)n, keys, pj, pk, s_cnt[warp], s_buf[warp]);
+    else if (n <= 128) done = warp_sort_row<4>(a, (int)n, keys, pj, pk, s_cnt[warp], s_buf[warp]);
+    else if (n <= 256) done = warp_sort_row<8>(a, (int)n, keys, pj, pk, s_cnt[warp], s_buf[warp]);
+    else if (n <= kSortWarpMax) done = warp_sort_row<16>(a, (int)n, keys, pj, pk, s_cnt[warp], s_buf[warp]);
+    if (!done && lane == 0) big[atomicAdd(big_count, 1ull)] = (int32_t)r;
   }
 }
 
-// Rows longer than kSortWarpMax: one block per row, in shared memory when the
-// row fits (kSortBlockKeys keys), else in place in the pair arrays.
+// Rows longer than kSortWarpMax (or with clustered columns): one block per
+// row, sorted by a bitonic network whose comparators all put the minimum at
+// the lower index: for block sizes k = 2, 4, .., N, first compare i with
+// i XOR (k - 1) (each position of the lower half with its mirror image), then
+// i with i XOR d for d = k/4, .., 1.  In shared memory when the row fits
+// (kSortBlockKeys keys, padded with +infinity), else in place in global
+// memory (the sort keys when given, else pj/pk with the pattern indices moved
+// along); there keys beyond the row's length act as +infinity and, sitting at
+// the higher index of every comparator they take part in, never move, so no
+// padding needs to be stored.
 constexpr int kSortBlockThreads = 1024;
 
 __global__ void __launch_bounds__(kSortBlockThreads)
-sort_rows_block_kernel(const int64_t* __restrict__ rp, uint32_t* __restrict__ pj, uint32_t* __restrict__ pk,
-                       int has_diag, const int32_t* __restrict__ big, const unsigned long long* __restrict__ big_count,
-                       unsigned long long* __restrict__ big_next, const int32_t* __restrict__ status) {
+sort_rows_block_kernel(const int64_t* __restrict__ rp, uint64_t* __restrict__ keys, uint32_t* __restrict__ pj,
+                       uint32_t* __restrict__ pk, int has_diag, const int32_t* __restrict__ big,
+                       const unsigned long long* __restrict__ big_count, unsigned long long* __restrict__ big_next,
+                       const int32_t* __restrict__ status) {
   if (*(volatile const int32_t*)status & kStatusCapacity) return;
-  extern __shared__ __align__(16) uint64_t keys[];
+  extern __shared__ __align__(16) uint64_t sk[];
   __shared__ int64_t s_row;
   const int64_t p0 = rp[0];
   const int64_t n_big = (int64_t)*big_count;
@@ -765,11 +923,10 @@ sort_rows_block_kernel(const int64_t* __restrict__ rp, uint32_t* __restrict__ pj
     const int64_t n = rp[r + 1] - p0 - a;
     int64_t N = 1;
     while (N < n) N <<= 1;
-    uint32_t* rj = pj + a;
-    uint32_t* rk = pk + a;
-    if (N <= kSortBlockKeys) {
-      for (int64_t e = threadIdx.x; e < N; e += blockDim.x)
-        keys[e] = e < n ? (((uint64_t)rk[e] << 32) | rj[e]) : ~0ull;
+    if (N <= kSortBlockKeys || keys) {
+      uint64_t* v = N <= kSortBlockKeys ? sk : keys + a;  // large rows: the keys in place
+      if (N <= kSortBlockKeys)
+        for (int64_t e = threadIdx.x; e < N; e += blockDim.x) sk[e] = e < n ? pair_key(keys, pj, pk, a + e) : ~0ull;
       __syncthreads();
       for (int64_t k = 2; k <= N; k <<= 1) {
         for (int64_t m = k - 1, d = k; d > 1; d >>= 1, m = d >> 1) {
@@ -778,33 +935,32 @@ sort_rows_block_kernel(const int64_t* __restrict__ rp, uint32_t* __restrict__ pj
           for (int64_t c = threadIdx.x; c < N / 2; c += blockDim.x) {
             const int64_t e = ((c & ~(hb - 1)) << 1) | (c & (hb - 1));  // insert a 0 at bit hb
             const int64_t f = e ^ m;
-            const uint64_t x = keys[e], y = keys[f];
-            if (y < x) { keys[e] = y; keys[f] = x; }
+            if (f >= n && v != sk) continue;  // +infinity partner at the higher index: nothing moves
+            const uint64_t x = v[e], y = v[f];
+            if (y < x) { v[e] = y; v[f] = x; }
           }
           __syncthreads();
         }
       }
-      for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
-        rj[e] = (uint32_t)keys[e];
-        rk[e] = (uint32_t)(keys[e] >> 32);
-      }
+      for (int64_t e = threadIdx.x; e < n; e += blockDim.x) put_pair(pj, pk, a + e, v[e]);
       __syncthreads();
-    } else {  // in place in global memory, sorting pattern indices and moving columns along
+    } else {  // in place in pj/pk, sorting columns and moving pattern indices along
+      uint32_t* rj = pj + a;
+      uint32_t* rk = pk + a;
       for (int64_t k = 2; k <= N; k <<= 1) {
         for (int64_t m = k - 1, d = k; d > 1; d >>= 1, m = d >> 1) {
           const int64_t hb = (m == k - 1) ? (k >> 1) : m;
           for (int64_t c = threadIdx.x; c < N / 2; c += blockDim.x) {
             const int64_t e = ((c & ~(hb - 1)) << 1) | (c & (hb - 1));
             const int64_t f = e ^ m;
-            if (f >= n) continue;  // +infinity partner at the higher index: nothing moves
-            const uint32_t ke = rk[e], kf = rk[f];
-            if (kf < ke) {
-              const uint32_t je = rj[e];
-              rk[e] = kf; rk[f] = ke;
-              rj[e] = rj[f]; rj[f] = je;
+            if (f >= n) continue;
+            const uint32_t je = rj[e], jf = rj[f];
+            if (jf < je) {
+              const uint32_t ke = rk[e];
+              rj[e] = jf; rj[f] = je;
+              rk[e] = rk[f]; rk[f] = ke;
             }
           }
-          __threadfence_block();
           __syncthreads();
         }
       }
@@ -812,21 +968,23 @@ sort_rows_block_kernel(const int64_t* __restrict__ rp, uint32_t* __restrict__ pj
   }
 }
 
-static cudaError_t launch_sort_rows(const int64_t* rp, int64_t rows, uint32_t* pj, uint32_t* pk, int has_diag,
-                                    char* stage, const StageHeader& L, cudaStream_t s) {
+static cudaError_t launch_sort_rows(const int64_t* rp, int64_t rows, uint64_t* keys, uint32_t* pj, uint32_t* pk,
+                                    int has_diag, char* stage, const StageHeader& L, cudaStream_t s) {
   auto* ctr = (unsigned long long*)(stage + L.off_counters);
   auto* status = (const int32_t*)(stage + offsetof(StageHeader, status));
   auto* big = (int32_t*)(stage + L.off_big);
   cudaError_t e = cudaMemsetAsync(ctr + kCtrBigCount, 0, 2 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, 16 * num_sms()));
-  sort_rows_warp_kernel<<<blocks, 256, 0, s>>>(rp, rows, pj, pk, has_diag, big, ctr + kCtrBigCount, status);
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + kSortWarpWarps - 1) / kSortWarpWarps,
+                                                                  8 * num_sms()));
+  sort_rows_warp_kernel<<<blocks, kSortWarpThreads, 0, s>>>(rp, rows, keys, pj, pk, has_diag, big,
+                                                            ctr + kCtrBigCount, status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t smem = sizeof(uint64_t) * kSortBlockKeys;
   e = cudaFuncSetAttribute(sort_rows_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  sort_rows_block_kernel<<<num_sms(), kSortBlockThreads, smem, s>>>(rp, pj, pk, has_diag, big, ctr + kCtrBigCount,
-                                                                   ctr + kCtrBigNext, status);
+  sort_rows_block_kernel<<<num_sms(), kSortBlockThreads, smem, s>>>(rp, keys, pj, pk, has_diag, big,
+                                                                   ctr + kCtrBigCount, ctr + kCtrBigNext, status);
   return cudaGetLastError();
 }
 
@@ -834,8 +992,8 @@ static cudaError_t launch_init(int mode, int64_t rows, int64_t rb, int has_diag,
                                int32_t* cursor, uint32_t* pj, uint32_t* pk, int64_t capacity,
                                const int64_t* overflow, int32_t* status, cudaStream_t s) {
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 4 * num_sms()));
-  pairs_init_kernel<<<blocks, 256, 0, s>>>(mode, rows, rb, has_diag, counts, rp, cursor, pj, pk, capacity, overflow,
-                                           status);
+  pairs_init_kernel<<<blocks, 256, 0, s>>>(mode, rows, rb, has_diag, counts, rp, cursor, pj, pk, capacity,
+                                           overflow, status);
   return cudaGetLastError();
 }
 
@@ -897,7 +1055,7 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stag
 #undef NQS_TERMS
     if (e != cudaSuccess) return e;
   }
-  if (mode == kFill) return launch_sort_rows(rp, rows, pj, pk, ham->has_diag, stage, L, s);
+  if (mode == kFill) return launch_sort_rows(rp, rows, nullptr, pj, pk, ham->has_diag, stage, L, s);
   return cudaSuccess;
 }
 
@@ -906,13 +1064,13 @@ cudaError_t launch_pairs_compact(const nqs_ham* ham, const PairScratch& sc, char
                                  uint32_t* pair_k, int64_t capacity, cudaStream_t s) {
   auto* status = (int32_t*)(stage + offsetof(StageHeader, status));
   auto* cursor = (int32_t*)(stage + L.off_rowcur);
-  cudaError_t e = launch_init(kFill, rows, rb, ham->has_diag, nullptr, row_ptr, cursor, pair_j, pair_k, capacity,
+  const int64_t cap = std::min<int64_t>(capacity, sc.max_pairs);
+  cudaError_t e = launch_init(kFill, rows, rb, ham->has_diag, nullptr, row_ptr, cursor, pair_j, pair_k, cap,
                               sc.cursor + 1, status, s);
   if (e != cudaSuccess) return e;
-  const int blocks = 8 * num_sms();
-  pairs_scatter_kernel<<<blocks, 256, 0, s>>>(sc, rb, rb + rows, row_ptr, cursor, pair_j, pair_k, status);
+  pairs_scatter_kernel<<<8 * num_sms(), 256, 0, s>>>(sc, rb, rb + rows, row_ptr, cursor, status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return launch_sort_rows(row_ptr, rows, pair_j, pair_k, ham->has_diag, stage, L, s);
+  return launch_sort_rows(row_ptr, rows, sc.keys, pair_j, pair_k, ham->has_diag, stage, L, s);
 }
 
 // --------------------------------------------------------------------------

@@ -132,6 +132,8 @@ struct PairScratch {        // one-pass search scratch (caller memory): found pa
   uint32_t* rec_i;          // [max_rec] the sample that found the pair (has the pattern's top qubit)
   uint32_t* rec_j;          // [max_rec] the other sample
   uint32_t* rec_k;          // [max_rec] pattern index
+  uint64_t* keys;           // [max_pairs] the range's pairs grouped by row: k << 32 | column
+  int64_t max_pairs;
 };
 int64_t pair_scratch_bytes(int64_t rows, int64_t max_pairs);
 PairScratch pair_scratch_view(void* base, int64_t rows, int64_t bytes);

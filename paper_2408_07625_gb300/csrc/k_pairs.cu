@@ -10,13 +10,14 @@
 // on average, so a miss reads one sector; only a tag match reads the sample.
 //
 // Oriented LoopOverTerms.  x XOR x' = XY is symmetric, so a coupled pair
-// {x, x'} with x != x' needs to be found once: from the one of the two that
-// has XY's highest set qubit t (exactly one of them has it).  The search table
-// is grouped by t and staging lists, per qubit t, the samples with bit t set;
-// a work item probes 8 samples of one list against the patterns of the
-// matching group.  For peaked molecular batches high qubits are rarely
-// occupied, which cuts the probes by an order of magnitude against probing
-// every (sample, pattern).  Each pair found is written to both of its rows,
+// {x, x'} with x != x' needs to be found once: exactly one of the two has
+// XY's highest set qubit t, so it is found either from the one with bit t set
+// or from the one with bit t clear, whichever side of t holds fewer samples.
+// The search table is grouped by t and staging lists, per qubit t, the
+// samples on that side; a work item probes 8 samples of one list against the
+// patterns of the matching group.  For peaked molecular batches most qubits
+// are nearly always empty or nearly always occupied, which cuts the probes by
+// an order of magnitude against probing every (sample, pattern).  Each pair found is written to both of its rows,
 // and each row is then sorted by column, so the list of a row (the diagonal
 // pair first, then ascending column index) depends on the row alone.
 #include <cstring>
@@ -139,16 +140,25 @@ __device__ __forceinline__ void warp_exclusive_scan(int64_t* v, int n, int64_t* 
   if (lane == 31 && total) *total = incl;
 }
 
-// Per-qubit lists: the samples with bit q set, for every qubit q.  Each block
-// takes a contiguous slice of U, counts its samples per qubit, reserves that
-// many places in each list (one atomic per qubit and block), then writes the
-// samples (warp-aggregated positions; the order inside a list is irrelevant).
+// Side of qubit q whose list the search uses: the samples with bit q set if
+// they are at most half of the batch, else the samples with bit q clear.
+__device__ __forceinline__ bool list_side(uint32_t qcnt_q, int64_t n) { return 2 * (int64_t)qcnt_q <= n; }
+__device__ __forceinline__ int64_t list_len(uint32_t qcnt_q, int64_t n) {
+  return list_side(qcnt_q, n) ? (int64_t)qcnt_q : n - (int64_t)qcnt_q;
+}
+
+// Per-qubit lists: for every qubit q, the samples on the rarer side of q (bit
+// set, or bit clear).  Each block takes a contiguous slice of U, counts its
+// samples per qubit, reserves that many places in each list (one atomic per
+// qubit and block), then writes the samples (warp-aggregated positions; the
+// order inside a list is irrelevant).
 template <int W>
 __global__ void qubit_rows_kernel(const uint64_t* __restrict__ U, int64_t n, int n_qubits, int64_t per_block,
                                   const uint32_t* __restrict__ qcnt, uint32_t* __restrict__ qcur,
                                   uint32_t* __restrict__ qrows) {
   __shared__ int64_t base[64 * W];
   __shared__ uint32_t cnt[64 * W];
+  __shared__ uint64_t side[W];  // bit q: the list of qubit q holds the samples with bit q set
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   const int64_t s0 = (int64_t)blockIdx.x * per_block;
@@ -156,7 +166,10 @@ __global__ void qubit_rows_kernel(const uint64_t* __restrict__ U, int64_t n, int
   const int tail = n_qubits - 64 * (W - 1);
   const uint64_t tail_mask = tail == 64 ? ~0ull : ((1ull << tail) - 1);
   for (int q = threadIdx.x; q < 64 * W; q += blockDim.x) cnt[q] = 0u;
+  if (threadIdx.x < W) side[threadIdx.x] = 0ull;
   __syncthreads();
+  for (int q = threadIdx.x; q < 64 * W; q += blockDim.x)
+    if (list_side(qcnt[q], n)) atomicOr((unsigned long long*)&side[q >> 6], 1ull << (q & 63));
   uint32_t mine[2 * W];
 #pragma unroll
   for (int c = 0; c < 2 * W; ++c) mine[c] = 0u;
@@ -172,7 +185,10 @@ __global__ void qubit_rows_kernel(const uint64_t* __restrict__ U, int64_t n, int
   for (int c = 0; c < 2 * W; ++c)
     if (mine[c]) atomicAdd(&cnt[32 * c + lane], mine[c]);
   __syncthreads();
-  for (int q = threadIdx.x; q < 64 * W; q += blockDim.x) base[q] = qcnt[q];
+  for (int q = threadIdx.x; q < 64 * W; q += blockDim.x) {
+    base[q] = list_len(qcnt[q], n);
+    if (!((side[q >> 6] >> (q & 63)) & 1ull)) cnt[q] = (uint32_t)(s1 > s0 ? s1 - s0 : 0) - cnt[q];
+  }
   __syncthreads();
   if (threadIdx.x < 32) warp_exclusive_scan(base, 64 * W, nullptr);
   __syncthreads();
@@ -188,10 +204,11 @@ __global__ void qubit_rows_kernel(const uint64_t* __restrict__ U, int64_t n, int
     for (int w = 0; w < W; ++w) v[w] = i < s1 ? __ldg(U + i * W + w) : 0ull;
     v[W - 1] &= tail_mask;
 #pragma unroll
-    for (int w = 0; w < W; ++w)
+    for (int w = 0; w < W; ++w) {
+      const uint64_t sd = side[w];
 #pragma unroll 4
       for (int b = 0; b < 64; ++b) {
-        const bool set = (v[w] >> b) & 1ull;
+        const bool set = i < s1 && (((v[w] ^ ~sd) >> b) & 1ull);  // on the listed side of qubit 64 w + b
         const uint32_t m = __ballot_sync(kFull, set);
         if (m == 0u) continue;
         uint32_t at = 0u;
@@ -199,6 +216,7 @@ __global__ void qubit_rows_kernel(const uint64_t* __restrict__ U, int64_t n, int
         at = __shfl_sync(kFull, at, __ffs(m) - 1);
         if (set) qrows[base[64 * w + b] + at + __popc(m & lt)] = (uint32_t)i;
       }
+    }
   }
 }
 
@@ -306,6 +324,7 @@ struct TermsArgs {
   const int4* segs;
   int n_segs;
   int nq;
+  int64_t n_unq;
   const uint32_t* qcnt;
   const uint32_t* qrows;
   int64_t row_begin, row_end;
@@ -552,10 +571,10 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
     for (int i = threadIdx.x; i < a.nwords / 4; i += blockDim.x) dst[i] = __ldg(src + i);
   }
   // list offsets per qubit; work items per segment (exclusive prefix, total last)
-  for (int qq = threadIdx.x; qq < a.nq; qq += blockDim.x) s_qoff[qq] = a.qcnt[qq];
+  for (int qq = threadIdx.x; qq < a.nq; qq += blockDim.x) s_qoff[qq] = list_len(a.qcnt[qq], a.n_unq);
   for (int sg = threadIdx.x; sg < a.n_segs; sg += blockDim.x) {
     const int4 g = __ldg(&a.segs[sg]);
-    s_cum[sg] = ((int64_t)a.qcnt[g.x] + R - 1) / R * ((g.z - g.y + kGroupsPerItem - 1) / kGroupsPerItem);
+    s_cum[sg] = (list_len(a.qcnt[g.x], a.n_unq) + R - 1) / R * ((g.z - g.y + kGroupsPerItem - 1) / kGroupsPerItem);
   }
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -591,14 +610,14 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
       const int4 sg = __ldg(&a.segs[lo]);
       const int n_chunks = (sg.z - sg.y + kGroupsPerItem - 1) / kGroupsPerItem;
       const int64_t local = it - s_cum[lo];
-      const int64_t batch = local / n_chunks;
+      const int64_t batch = local < 0x7FFFFFFF ? (int64_t)((uint32_t)local / (uint32_t)n_chunks) : local / n_chunks;
       const int g0 = sg.y + (int)(local - batch * n_chunks) * kGroupsPerItem;
       const int g1 = g0 + kGroupsPerItem < sg.z ? g0 + kGroupsPerItem : sg.z;
       if (lo != cur_seg || batch != cur_batch) {  // new rows (consecutive chunks share them)
         cur_seg = lo;
         cur_batch = batch;
         const int64_t b0 = batch * R;
-        const int64_t count_t = (int64_t)a.qcnt[sg.x];
+        const int64_t count_t = list_len(a.qcnt[sg.x], a.n_unq);
         __syncwarp();
         if (lane < R) {
           const bool valid = b0 + lane < count_t;
@@ -1021,6 +1040,7 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stag
   a.segs = ham->segs;
   a.n_segs = ham->n_segs;
   a.nq = 64 * ham->W;
+  a.n_unq = L.n_unq;
   a.qcnt = (const uint32_t*)(stage + L.off_q);
   a.qrows = (const uint32_t*)(stage + L.off_qrows);
   a.row_begin = rb;

@@ -117,6 +117,8 @@ static void free_ham(nqs_ham* h) {
   cudaFree(h->xy); cudaFree(h->row_ptr); cudaFree(h->yz); cudaFree(h->coef);
   cudaFree(h->coef_f); cudaFree(h->srch_hash); cudaFree(h->srch_id); cudaFree(h->srch_rec); cudaFree(h->hash_basis);
   cudaFree(h->xy_table); cudaFree(h->wmask); cudaFree(h->xy_trie); cudaFree(h->xy_hash); cudaFree(h->segs);
+  cudaFree(h->lin_id); cudaFree(h->lin_z0); cudaFree(h->lin_d); cudaFree(h->lin_f); cudaFree(h->quad_d);
+  cudaFree(h->quad_f);
   delete h;
 }
 
@@ -245,6 +247,81 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
   }
   h->h_row_ptr[G] = t;
 
+  // MatrixElement forms.  Both regroup the sum of Eq. pauli_melem exactly;
+  // coefficients are summed with Neumaier compensation in a fixed order.
+  //   linear: a heavy pattern whose terms' YZ masks differ from the first
+  //     term's YZ_0 in at most one qubit r:  c (-1)^{x'.YZ} = c (-1)^{x'.YZ_0}
+  //     (1 - 2 x'_r), so H = (-1)^{x'.YZ_0} (C - 2 sum_{r in x'} a_r);
+  //   quadratic diagonal: every diagonal term a Z string on at most two
+  //     qubits: c (-1)^{x_r + x_s} = c (1 - 2 x_r)(1 - 2 x_s).
+  struct CSum {
+    double s = 0.0, c = 0.0;
+    void add(double v) {
+      const double t = s + v;
+      c += (std::fabs(s) >= std::fabs(v)) ? (s - t) + v : (v - t) + s;
+      s = t;
+    }
+    double value() const { return s + c; }
+  };
+  const int NQ = 64 * W;
+  h->lin_stride = 1 + NQ;
+  std::vector<int32_t> lin_id(G, -1);
+  std::vector<uint64_t> lin_z0;
+  std::vector<double> lin_d;
+  for (int64_t p = h->has_diag; p < h->heavy_end; ++p) {
+    const int64_t t0 = h->h_row_ptr[p], t1 = h->h_row_ptr[p + 1];
+    std::vector<CSum> acc(1 + NQ);
+    bool ok = true;
+    for (int64_t t = t0; t < t1 && ok; ++t) {
+      int wt = 0, r = -1;
+      for (int w = 0; w < W; ++w) {
+        const uint64_t d = h->h_yz[t * W + w] ^ h->h_yz[t0 * W + w];
+        wt += __builtin_popcountll(d);
+        if (d) r = 64 * w + __builtin_ctzll(d);
+      }
+      if (wt > 1) { ok = false; break; }
+      acc[0].add(h->h_coef[t]);
+      if (wt == 1) acc[1 + r].add(-2.0 * h->h_coef[t]);
+    }
+    if (!ok) continue;
+    lin_id[p] = (int32_t)h->n_lin++;
+    for (int w = 0; w < W; ++w) lin_z0.push_back(h->h_yz[t0 * W + w]);
+    for (auto& a : acc) lin_d.push_back(a.value());
+  }
+  std::vector<double> quad_d;
+  if (h->has_diag) {
+    const int64_t t0 = h->h_row_ptr[0], t1 = h->h_row_ptr[1];
+    std::vector<CSum> acc(1 + NQ + (size_t)NQ * NQ);
+    bool ok = true;
+    for (int64_t t = t0; t < t1 && ok; ++t) {
+      int q[2], nq = 0;
+      for (int w = 0; w < W && ok; ++w)
+        for (uint64_t m = h->h_yz[t * W + w]; m; m &= m - 1) {
+          if (nq == 2) { ok = false; break; }
+          q[nq++] = 64 * w + __builtin_ctzll(m);
+        }
+      if (!ok) break;
+      const double c = h->h_coef[t];
+      acc[0].add(c);
+      for (int u = 0; u < nq; ++u) acc[1 + q[u]].add(-2.0 * c);
+      if (nq == 2) acc[1 + NQ + (size_t)q[0] * NQ + q[1]].add(4.0 * c);
+    }
+    if (ok) {
+      h->diag_quad = 1;
+      quad_d.resize(acc.size());
+      for (size_t e = 0; e < acc.size(); ++e) quad_d[e] = acc[e].value();
+    }
+  }
+  auto split = [](const std::vector<double>& v) {
+    std::vector<float2> f(v.size());
+    for (size_t e = 0; e < v.size(); ++e) {
+      const float hi = (float)v[e];
+      f[e] = make_float2(hi, (float)(v[e] - (double)hi));
+    }
+    return f;
+  };
+  const std::vector<float2> lin_f = split(lin_d), quad_f = split(quad_d);
+
   // linear hash basis: h(v) = XOR over set bits b of R[b] (GF(2)-linear, so
   // h(x ^ xy) = h(x) ^ h(xy) and a candidate's hash costs one XOR)
   h->h_hash_basis.resize(64 * W);
@@ -352,7 +429,9 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
       (rc = upload(&h->srch_id, srch_id)) || (rc = upload(&h->srch_rec, srch_rec)) ||
       (rc = upload(&h->hash_basis, h->h_hash_basis)) || (rc = upload(&h->xy_table, xy_table)) ||
       (rc = upload(&h->wmask, wmask)) || (rc = upload(&h->xy_trie, xy_trie)) ||
-      (rc = upload(&h->xy_hash, hxy)) || (rc = upload(&h->segs, segs))) {
+      (rc = upload(&h->xy_hash, hxy)) || (rc = upload(&h->segs, segs)) || (rc = upload(&h->lin_id, lin_id)) ||
+      (rc = upload(&h->lin_z0, lin_z0)) || (rc = upload(&h->lin_d, lin_d)) || (rc = upload(&h->lin_f, lin_f)) ||
+      (rc = upload(&h->quad_d, quad_d)) || (rc = upload(&h->quad_f, quad_f))) {
     free_ham(h);
     return rc;
   }

@@ -72,6 +72,10 @@ struct PolicyF {
   __device__ static T coef(const float2* cf, const double*, int64_t l, uint32_t par) {
     return df_signflip(__ldg(cf + l), par);
   }
+  __device__ static T val(const float2* f, const double*, int64_t i) {
+    const float2 v = __ldg(f + i);
+    return {v.x, v.y};
+  }
   __device__ static void acc(T& a, T t) { df_acc(a, t); }
   __device__ static T add(T a, T b) { return df_add(a, b); }
   __device__ static T mul(T a, T b) { return df_mul(a, b); }
@@ -95,6 +99,7 @@ struct PolicyD {
   __device__ static T coef(const float2*, const double* cd, int64_t l, uint32_t par) {
     return dsignflip(__ldg(cd + l), par);
   }
+  __device__ static T val(const float2*, const double* d, int64_t i) { return __ldg(d + i); }
   __device__ static void acc(T& a, T t) { a += t; }
   __device__ static T add(T a, T b) { return a + b; }
   __device__ static T mul(T a, T b) { return a * b; }
@@ -136,6 +141,29 @@ __device__ __forceinline__ void ratio(const char* P, const char* Q, const int* K
   }
 }
 
+// MatrixElement tables of a Hamiltonian (device pointers)
+struct Melem {
+  const uint32_t* t_ptr;   // P_XY of pattern k: terms t_ptr[k] .. t_ptr[k+1]-1
+  const uint64_t* yz;
+  const float2* cf;
+  const double* cd;
+  int has_diag;
+  int64_t heavy_end;
+  const int32_t* lin_id;   // linear-form index of a heavy pattern, or -1
+  const uint64_t* lin_z0;
+  const float2* lin_f;
+  const double* lin_d;
+  int lin_stride;
+  int diag_quad;
+  const float2* quad_f;
+  const double* quad_d;
+};
+
+static Melem melem_tables(const nqs_ham* h) {
+  return Melem{h->row_ptr, h->yz, h->coef_f, h->coef, h->has_diag, h->heavy_end, h->lin_id, h->lin_z0,
+               h->lin_f, h->lin_d, h->lin_stride, h->diag_quad, h->quad_f, h->quad_d};
+}
+
 // partial matrix element over the terms l = t0 + lane0, t0 + lane0 + step, ... < t1
 template <class Pol, int W>
 __device__ __forceinline__ typename Pol::T melem_part(const uint64_t (&xp)[W], int64_t t0, int64_t t1,
@@ -150,14 +178,70 @@ __device__ __forceinline__ typename Pol::T melem_part(const uint64_t (&xp)[W], i
   return h;
 }
 
+// H of one pair by one lane: the linear form when the pattern has one,
+// else the pattern's terms (Eq. pauli_melem; loads of four terms in flight)
+template <class Pol, int W>
+__device__ __forceinline__ typename Pol::T melem_lane(const uint64_t (&xp)[W], uint32_t k, int32_t lm,
+                                                       const Melem& M) {
+  using T = typename Pol::T;
+  T h = Pol::zero();
+  if (lm >= 0) {
+    const int64_t b = (int64_t)lm * M.lin_stride;
+    h = Pol::val(M.lin_f, M.lin_d, b);
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+      for (uint64_t v = xp[w]; v; v &= v - 1)
+        Pol::acc(h, Pol::val(M.lin_f, M.lin_d, b + 1 + 64 * w + (__ffsll((long long)v) - 1)));
+    h = Pol::fin(h);
+    return parity_and<W>(xp, M.lin_z0 + (int64_t)lm * W) ? Pol::neg(h) : h;
+  }
+  const int64_t t0 = __ldg(M.t_ptr + k), t1 = __ldg(M.t_ptr + k + 1);
+#pragma unroll 4
+  for (int64_t l = t0; l < t1; ++l) Pol::acc(h, Pol::coef(M.cf, M.cd, l, parity_and<W>(xp, M.yz + l * W)));
+  return Pol::fin(h);
+}
+
+// H_xx by the whole warp: the quadratic form (lane t takes the occupied
+// qubits r with rank t mod 32 and adds b_r + sum_{s > r occupied} B_rs) or
+// the diagonal pattern's terms; every lane returns the same value.
+template <class Pol, int W>
+__device__ __forceinline__ typename Pol::T melem_diag(const uint64_t (&x)[W], const Melem& M) {
+  using T = typename Pol::T;
+  const int lane = threadIdx.x & 31;
+  if (!M.diag_quad)
+    return Pol::warp_sum(melem_part<Pol, W>(x, (int64_t)__ldg(M.t_ptr) + lane, (int64_t)__ldg(M.t_ptr + 1), 32,
+                                            M.yz, M.cf, M.cd));
+  constexpr int NQ = 64 * W;
+  T h = lane == 0 ? Pol::val(M.quad_f, M.quad_d, 0) : Pol::zero();
+  int rank = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    for (uint64_t v = x[w]; v; v &= v - 1, ++rank) {
+      if ((rank & 31) != lane) continue;
+      const int r = 64 * w + (__ffsll((long long)v) - 1);
+      Pol::acc(h, Pol::val(M.quad_f, M.quad_d, 1 + r));
+      const int64_t row = 1 + NQ + (int64_t)r * NQ;
+#pragma unroll
+      for (int w2 = w; w2 < W; ++w2)
+        for (uint64_t u = (w2 == w) ? (v & (v - 1)) : x[w2]; u; u &= u - 1)
+          Pol::acc(h, Pol::val(M.quad_f, M.quad_d, row + 64 * w2 + (__ffsll((long long)u) - 1)));
+    }
+  }
+  return Pol::warp_sum(h);
+}
+
 // --------------------------------------------------------------------------
 // row schedule: rows of [rb, re) in decreasing order of their pair count
-// (power-of-two classes, heaviest first), handed out to warps one at a time
-// from a counter, so the longest rows start first and no warp idles while
-// others hold several long rows.  Results do not depend on the order: every
-// row is a fixed-order reduction by one warp.
+// (power-of-two classes, heaviest first).  Rows of at least kLongRow pairs
+// (they lead the order) are taken one per block, whose warps share the row's
+// rounds; the rest are handed out to warps one at a time from a counter, so
+// the longest rows start first and no warp idles while others hold several
+// long rows.  Results do not depend on the order: a row is a fixed-order
+// reduction whose shape depends on its length alone.
 // --------------------------------------------------------------------------
 constexpr int kRowClasses = 32;
+constexpr int kLongRowBits = 11;                 // rows with bit length >= 11: at least 1024 pairs
+constexpr int64_t kLongRow = int64_t(1) << (kLongRowBits - 1);
 
 __device__ __forceinline__ int row_class(int64_t c) {  // 0: heaviest
   const int lg = c > 0 ? 64 - __clzll((long long)c) : 0;    // bit length, 0..35 for c < 2^35
@@ -191,20 +275,24 @@ __global__ void row_order_kernel(const int64_t* __restrict__ rp, int64_t rows, c
 
 struct RowSched {
   const int32_t* order;
-  unsigned long long* next;
+  const uint32_t* cnt;           // rows per class
+  unsigned long long* next;      // warp rows taken
+  unsigned long long* next_long; // block rows taken
   int64_t rows;
 };
 
-// sched region of the workspace: counts [32] u32, cursors [32] u32, row counter u64
+// sched region of the workspace: counts [32] u32, cursors [32] u32, two row counters u64
 static cudaError_t launch_row_order(const int64_t* rp, int64_t rows, char* stage, const StageHeader& L,
                                     RowSched& rs, cudaStream_t s) {
   char* base = stage + L.off_sched;
   uint32_t* cnt = (uint32_t*)base;
   uint32_t* cur = cnt + kRowClasses;
+  rs.cnt = cnt;
   rs.next = (unsigned long long*)(cur + kRowClasses);
+  rs.next_long = rs.next + 1;
   rs.order = (const int32_t*)(stage + L.off_order);
   rs.rows = rows;
-  cudaError_t e = cudaMemsetAsync(base, 0, 2 * kRowClasses * 4 + 8, s);
+  cudaError_t e = cudaMemsetAsync(base, 0, 2 * kRowClasses * 4 + 16, s);
   if (e != cudaSuccess) return e;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 2 * num_sms()));
   row_class_count_kernel<<<blocks, 256, 0, s>>>(rp, rows, cnt);
@@ -212,10 +300,28 @@ static cudaError_t launch_row_order(const int64_t* rp, int64_t rows, char* stage
   return cudaGetLastError();
 }
 
-__device__ __forceinline__ int64_t next_row(const RowSched& rs) {
+// number of long rows (they lead the order)
+__device__ __forceinline__ int64_t long_rows(const RowSched& rs) {
+  int64_t n = 0;
+  for (int k = 0; k <= kRowClasses - 1 - kLongRowBits; ++k) n += rs.cnt[k];
+  return n;
+}
+
+// next long row for the whole block (-1: none left); all threads call it
+__device__ __forceinline__ int64_t next_long_row(const RowSched& rs, int64_t n_long, int64_t* slot) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long v = atomicAdd(rs.next_long, 1ull);
+    *slot = (int64_t)v < n_long ? (int64_t)__ldg(rs.order + v) : -1;
+  }
+  __syncthreads();
+  return *slot;
+}
+
+__device__ __forceinline__ int64_t next_row(const RowSched& rs, int64_t n_long) {
   unsigned long long v = 0;
   if ((threadIdx.x & 31) == 0) v = atomicAdd(rs.next, 1ull);
-  const int64_t i = (int64_t)__shfl_sync(kFull, v, 0);
+  const int64_t i = n_long + (int64_t)__shfl_sync(kFull, v, 0);
   return i < rs.rows ? (int64_t)__ldg(rs.order + i) : -1;
 }
 
@@ -236,80 +342,141 @@ template <> struct HStore<PolicyD> {
 };
 
 // --------------------------------------------------------------------------
-// E_loc^var over CSR pairs: one warp per row.  H of a pair with a large P_XY
-// is summed by all lanes (then reduced across the warp); small ones by the
-// lane that holds the pair.  Either way the pair's lane adds H * ratio to its
-// accumulator and, if asked, stores H for the adjoint.
+// E_loc^var over CSR pairs.  A row is a sequence of rounds of 32 pairs; each
+// pair is evaluated by the lane that holds it (linear form or the pattern's
+// terms), and heavy patterns without a linear form are summed by all lanes
+// (then reduced across the warp).  The pair's lane adds H * ratio to its
+// accumulator and, if asked, stores H for the adjoint.  The next round's pair
+// indices are loaded while the current round is evaluated.  A short row is
+// one warp's rounds; a long row's rounds are dealt to the block's warps in
+// turn and the warps' sums are added in warp order.
 // --------------------------------------------------------------------------
 template <class Pol, int W, bool CPLX, bool STORE_H>
-__global__ void __launch_bounds__(kEnergyThreads)
-local_energy_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict__ t_ptr,
-                    const uint64_t* __restrict__ yz, const float2* __restrict__ cf,
-                    const double* __restrict__ cd, int has_diag, int64_t heavy_end,
-                    const char* __restrict__ P, const char* __restrict__ Q,
-                    const int* __restrict__ K, int64_t row_begin, RowSched rs,
-                    const int64_t* __restrict__ rp, const uint32_t* __restrict__ pair_j,
-                    const uint32_t* __restrict__ pair_k, double* __restrict__ eloc_re,
-                    double* __restrict__ eloc_im, double* __restrict__ hdiag, void* __restrict__ hpair,
-                    int32_t* __restrict__ status) {
+__device__ __forceinline__ void energy_rounds(const uint64_t* __restrict__ U, const Melem& M, const char* P,
+                                              const char* Q, const int* K, int64_t i, int64_t p, int64_t p1,
+                                              int64_t first, int64_t stride, const uint32_t* __restrict__ pair_j,
+                                              const uint32_t* __restrict__ pair_k, void* hpair, int32_t* status,
+                                              typename Pol::T& acc_re, typename Pol::T& acc_im) {
   using T = typename Pol::T;
-  if (*(volatile int32_t*)status & kStatusCapacity) return;  // the pair list was not written
   const int lane = threadIdx.x & 31;
-  for (int64_t row = next_row(rs); row >= 0; row = next_row(rs)) {
-    const int64_t i = row + row_begin;
-    int64_t p = rp[row] - rp[0];
-    const int64_t p1 = rp[row + 1] - rp[0];
-    T acc_re = Pol::zero(), acc_im = Pol::zero();
-    double hd = 0.0;
-    if (has_diag && p < p1 && __ldg(pair_k + p) == 0u) {
-      uint64_t xi[W];
-      load_words<W>(U + i * W, xi);
-      T h = melem_part<Pol, W>(xi, (int64_t)__ldg(t_ptr) + lane, (int64_t)__ldg(t_ptr + 1), 32, yz, cf, cd);
-      h = Pol::warp_sum(h);
-      hd = Pol::to_d(h);
-      if (lane == 0) {
-        Pol::acc(acc_re, h);  // psi(x)/psi(x) = 1
-        if (STORE_H) HStore<Pol>::put(hpair, p, h);
-      }
-      ++p;
+  uint32_t jn = 0u, kn = 0u;
+  int64_t base = p + 32 * first;
+  if (base + lane < p1) {
+    jn = __ldg(pair_j + base + lane);
+    kn = __ldg(pair_k + base + lane);
+  }
+  for (; base < p1; base += 32 * stride) {
+    const int64_t q = base + lane;
+    const bool have = q < p1;
+    const uint32_t j = jn, k = kn;
+    if (q + 32 * stride < p1) {
+      jn = __ldg(pair_j + q + 32 * stride);
+      kn = __ldg(pair_k + q + 32 * stride);
     }
-    for (int64_t base = p; base < p1; base += 32) {
-      const int64_t q = base + lane;
-      const bool have = q < p1;
-      const uint32_t j = have ? __ldg(pair_j + q) : 0u;
-      const uint32_t k = have ? __ldg(pair_k + q) : 0u;
-      const bool heavy = have && (int64_t)k < heavy_end;
-      uint32_t hb = __ballot_sync(kFull, heavy);
-      while (hb) {  // large P_XY: all lanes share the term loop of one pair
-        const int src = __ffs(hb) - 1;
-        hb &= hb - 1;
-        const uint32_t jj = __shfl_sync(kFull, j, src);
-        const uint32_t kk = __shfl_sync(kFull, k, src);
-        uint64_t xp[W];
-        load_words<W>(U + (int64_t)jj * W, xp);
-        T h = melem_part<Pol, W>(xp, (int64_t)__ldg(t_ptr + kk) + lane, (int64_t)__ldg(t_ptr + kk + 1), 32, yz,
-                                 cf, cd);
-        h = Pol::warp_sum(h);
-        if (lane == src) {
-          T rr, ri;
-          ratio<Pol, CPLX>(P, Q, K, jj, i, rr, ri, status);
-          Pol::acc(acc_re, Pol::mul(h, rr));
-          if (CPLX) Pol::acc(acc_im, Pol::mul(h, ri));
-          if (STORE_H) HStore<Pol>::put(hpair, q, h);
-        }
-      }
-      if (have && !heavy) {  // small P_XY: one lane per pair
-        uint64_t xp[W];
-        load_words<W>(U + (int64_t)j * W, xp);
-        T h = melem_part<Pol, W>(xp, (int64_t)__ldg(t_ptr + k), (int64_t)__ldg(t_ptr + k + 1), 1, yz, cf, cd);
-        h = Pol::fin(h);
+    const bool heavy = have && (int64_t)k < M.heavy_end;
+    const int32_t lm = heavy ? __ldg(M.lin_id + k) : -1;
+    const bool coop = heavy && lm < 0;
+    uint32_t hb = __ballot_sync(kFull, coop);
+    while (hb) {  // heavy pattern without a linear form: all lanes share its term loop
+      const int src = __ffs(hb) - 1;
+      hb &= hb - 1;
+      const uint32_t jj = __shfl_sync(kFull, j, src);
+      const uint32_t kk = __shfl_sync(kFull, k, src);
+      uint64_t xp[W];
+      load_words<W>(U + (int64_t)jj * W, xp);
+      T h = melem_part<Pol, W>(xp, (int64_t)__ldg(M.t_ptr + kk) + lane, (int64_t)__ldg(M.t_ptr + kk + 1), 32,
+                               M.yz, M.cf, M.cd);
+      h = Pol::warp_sum(h);
+      if (lane == src) {
         T rr, ri;
-        ratio<Pol, CPLX>(P, Q, K, j, i, rr, ri, status);
+        ratio<Pol, CPLX>(P, Q, K, jj, i, rr, ri, status);
         Pol::acc(acc_re, Pol::mul(h, rr));
         if (CPLX) Pol::acc(acc_im, Pol::mul(h, ri));
         if (STORE_H) HStore<Pol>::put(hpair, q, h);
       }
     }
+    if (have && !coop) {
+      uint64_t xp[W];
+      load_words<W>(U + (int64_t)j * W, xp);
+      const T h = melem_lane<Pol, W>(xp, k, lm, M);
+      T rr, ri;
+      ratio<Pol, CPLX>(P, Q, K, j, i, rr, ri, status);
+      Pol::acc(acc_re, Pol::mul(h, rr));
+      if (CPLX) Pol::acc(acc_im, Pol::mul(h, ri));
+      if (STORE_H) HStore<Pol>::put(hpair, q, h);
+    }
+  }
+}
+
+// the diagonal pair, if the row starts with it: H_xx added by lane 0 (psi(x)/psi(x) = 1)
+template <class Pol, int W, bool STORE_H>
+__device__ __forceinline__ bool energy_diag(const uint64_t* __restrict__ U, const Melem& M, int64_t i, int64_t p,
+                                            int64_t p1, const uint32_t* __restrict__ pair_k, void* hpair,
+                                            typename Pol::T& acc_re, double& hd) {
+  if (!(M.has_diag && p < p1 && __ldg(pair_k + p) == 0u)) return false;
+  uint64_t xi[W];
+  load_words<W>(U + i * W, xi);
+  const typename Pol::T h = melem_diag<Pol, W>(xi, M);
+  hd = Pol::to_d(h);
+  if ((threadIdx.x & 31) == 0) {
+    Pol::acc(acc_re, h);
+    if (STORE_H) HStore<Pol>::put(hpair, p, h);
+  }
+  return true;
+}
+
+template <class Pol, int W, bool CPLX, bool STORE_H>
+__global__ void __launch_bounds__(kEnergyThreads)
+local_energy_kernel(const uint64_t* __restrict__ U, const Melem M, const char* __restrict__ P,
+                    const char* __restrict__ Q, const int* __restrict__ K, int64_t row_begin, RowSched rs,
+                    const int64_t* __restrict__ rp, const uint32_t* __restrict__ pair_j,
+                    const uint32_t* __restrict__ pair_k, double* __restrict__ eloc_re,
+                    double* __restrict__ eloc_im, double* __restrict__ hdiag, void* __restrict__ hpair,
+                    int32_t* __restrict__ status) {
+  using T = typename Pol::T;
+  __shared__ T s_re[kEnergyWarps], s_im[kEnergyWarps];
+  __shared__ int64_t s_row;
+  if (*(volatile int32_t*)status & kStatusCapacity) return;  // the pair list was not written
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int64_t n_long = long_rows(rs);
+  for (int64_t row = next_long_row(rs, n_long, &s_row); row >= 0; row = next_long_row(rs, n_long, &s_row)) {
+    const int64_t i = row + row_begin;
+    int64_t p = rp[row] - rp[0];
+    const int64_t p1 = rp[row + 1] - rp[0];
+    T acc_re = Pol::zero(), acc_im = Pol::zero();
+    double hd = 0.0;
+    if (warp == 0) energy_diag<Pol, W, STORE_H>(U, M, i, p, p1, pair_k, hpair, acc_re, hd);
+    if (M.has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
+    energy_rounds<Pol, W, CPLX, STORE_H>(U, M, P, Q, K, i, p, p1, warp, kEnergyWarps, pair_j, pair_k, hpair,
+                                         status, acc_re, acc_im);
+    const T er = Pol::warp_sum(acc_re);
+    const T ei = CPLX ? Pol::warp_sum(acc_im) : Pol::zero();
+    if (lane == 0) {
+      s_re[warp] = er;
+      s_im[warp] = ei;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T tr = s_re[0], ti = s_im[0];
+      for (int w = 1; w < kEnergyWarps; ++w) {
+        tr = Pol::add(tr, s_re[w]);
+        ti = Pol::add(ti, s_im[w]);
+      }
+      eloc_re[i] = Pol::to_d(tr);
+      if (eloc_im) eloc_im[i] = Pol::to_d(ti);
+      if (hdiag) hdiag[i] = hd;
+    }
+  }
+  for (int64_t row = next_row(rs, n_long); row >= 0; row = next_row(rs, n_long)) {
+    const int64_t i = row + row_begin;
+    int64_t p = rp[row] - rp[0];
+    const int64_t p1 = rp[row + 1] - rp[0];
+    T acc_re = Pol::zero(), acc_im = Pol::zero();
+    double hd = 0.0;
+    if (energy_diag<Pol, W, STORE_H>(U, M, i, p, p1, pair_k, hpair, acc_re, hd)) ++p;
+    energy_rounds<Pol, W, CPLX, STORE_H>(U, M, P, Q, K, i, p, p1, 0, 1, pair_j, pair_k, hpair, status, acc_re,
+                                         acc_im);
     const T er = Pol::warp_sum(acc_re);
     const T ei = CPLX ? Pol::warp_sum(acc_im) : Pol::zero();
     if (lane == 0) {
@@ -335,9 +502,8 @@ static void launch_le(const nqs_ham* ham, const uint64_t* U, const char* stage, 
                       const uint32_t* pk, double* er, double* ei, double* hd, void* hpair, cudaStream_t s) {
   auto kern = local_energy_kernel<Pol, W, CPLX, STORE_H>;
   kern<<<grid_for(kern, rs.rows), kEnergyThreads, 0, s>>>(
-      U, ham->row_ptr, ham->yz, ham->coef_f, ham->coef, ham->has_diag, ham->heavy_end,
-      stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK), rb, rs, rp, pj, pk,
-      er, ei, hd, hpair, (int32_t*)(stage + offsetof(StageHeader, status)));
+      U, melem_tables(ham), stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK), rb, rs, rp,
+      pj, pk, er, ei, hd, hpair, (int32_t*)(stage + offsetof(StageHeader, status)));
 }
 
 template <class Pol, bool CPLX, bool STORE_H>
@@ -587,10 +753,88 @@ __device__ __forceinline__ void load_geff(const char* G, int64_t i, typename Pol
 // lane per pair, no term loop); otherwise they are recomputed exactly as the
 // forward computes them, so both forms give the same bits.
 template <class Pol, int W, bool CPLX, bool LOAD_H>
+__device__ __forceinline__ void backward_rounds(const uint64_t* __restrict__ U, const Melem& M, const char* P,
+                                                const char* Q, const int* K, const char* G, int64_t y, int64_t p,
+                                                int64_t p1, int64_t first, int64_t stride,
+                                                const uint32_t* __restrict__ pair_j,
+                                                const uint32_t* __restrict__ pair_k, const void* hpair,
+                                                int32_t* status, typename Pol::T& da, typename Pol::T& db) {
+  using T = typename Pol::T;
+  const int lane = threadIdx.x & 31;
+  uint32_t jn = 0u, kn = 0u;
+  int64_t base = p + 32 * first;
+  if (base + lane < p1) {
+    jn = __ldg(pair_j + base + lane);
+    if (!LOAD_H) kn = __ldg(pair_k + base + lane);
+  }
+  for (; base < p1; base += 32 * stride) {
+    const int64_t q = base + lane;
+    const bool have = q < p1;
+    const uint32_t j = jn, k = kn;
+    if (q + 32 * stride < p1) {
+      jn = __ldg(pair_j + q + 32 * stride);
+      if (!LOAD_H) kn = __ldg(pair_k + q + 32 * stride);
+    }
+    T h = Pol::zero();
+    if (LOAD_H) {
+      if (have) h = HStore<Pol>::get(hpair, q);
+    } else {
+      const bool heavy = have && (int64_t)k < M.heavy_end;
+      const int32_t lm = heavy ? __ldg(M.lin_id + k) : -1;
+      const bool coop = heavy && lm < 0;
+      uint32_t hb = __ballot_sync(kFull, coop);
+      while (hb) {
+        const int src = __ffs(hb) - 1;
+        hb &= hb - 1;
+        const uint32_t jj = __shfl_sync(kFull, j, src);
+        const uint32_t kk = __shfl_sync(kFull, k, src);
+        uint64_t xp[W];
+        load_words<W>(U + (int64_t)jj * W, xp);
+        T part = melem_part<Pol, W>(xp, (int64_t)__ldg(M.t_ptr + kk) + lane, (int64_t)__ldg(M.t_ptr + kk + 1), 32,
+                                    M.yz, M.cf, M.cd);
+        part = Pol::warp_sum(part);
+        if (lane == src) h = part;
+      }
+      if (have && !coop) {
+        uint64_t xp[W];
+        load_words<W>(U + (int64_t)j * W, xp);
+        h = melem_lane<Pol, W>(xp, k, lm, M);
+      }
+    }
+    if (have) {
+      T rr, ri, ge, gi;
+      ratio<Pol, CPLX>(P, Q, K, y, j, rr, ri, status);
+      load_geff<Pol>(G, j, ge, gi);
+      const T tr = Pol::mul(h, rr);
+      Pol::acc(da, Pol::mul(ge, tr));
+      if (CPLX) {
+        const T ti = Pol::mul(h, ri);
+        Pol::acc(da, Pol::mul(gi, ti));
+        Pol::acc(db, Pol::neg(Pol::mul(ge, ti)));
+        Pol::acc(db, Pol::mul(gi, tr));
+      }
+    }
+  }
+}
+
+// the row's own terms: D_yy = -(E_loc(y) - H_yy) and g_E 2 w_y (Re E_loc(y) - E)
+template <bool CPLX>
+__device__ __forceinline__ void backward_finish(int64_t y, double sa, double sb, const double* a,
+                                                const double* er, const double* ei, const double* hdiag,
+                                                const double* g_re, const double* g_im, double gE, double E,
+                                                double amax, double S, double* gre, double* gim) {
+  const double w = exp(2.0 * (a[y] - amax)) / S;
+  const double ge_y = (g_re ? g_re[y] : 0.0) + gE * w;
+  const double gi_y = g_im ? g_im[y] : 0.0;
+  const double Dr = -(er[y] - hdiag[y]);
+  const double Di = CPLX ? -ei[y] : 0.0;
+  gre[y] = sa + ge_y * Dr + gi_y * Di + gE * 2.0 * w * (er[y] - E);
+  if (gim) gim[y] = CPLX ? (sb - ge_y * Di + gi_y * Dr) : 0.0;
+}
+
+template <class Pol, int W, bool CPLX, bool LOAD_H>
 __global__ void __launch_bounds__(kEnergyThreads)
-backward_pairs_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict__ t_ptr,
-                      const uint64_t* __restrict__ yz, const float2* __restrict__ cf,
-                      const double* __restrict__ cd, int has_diag, int64_t heavy_end,
+backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
                       const char* __restrict__ P, const char* __restrict__ Q,
                       const int* __restrict__ K, const char* __restrict__ G,
                       int64_t row_begin, RowSched rs, const int64_t* __restrict__ rp,
@@ -602,71 +846,49 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const uint32_t* __restrict
                       const double* __restrict__ g_im, const double* __restrict__ g_evar,
                       double* __restrict__ gre, double* __restrict__ gim, int32_t* __restrict__ status) {
   using T = typename Pol::T;
+  __shared__ T s_a[kEnergyWarps], s_b[kEnergyWarps];
+  __shared__ int64_t s_row;
   if (*(volatile int32_t*)status & kStatusCapacity) return;  // the pair list was not written
   const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   const double gE = g_evar ? g_evar[0] : 0.0;
   const double E = evar[0], amax = evar[1], S = evar[2];
-  for (int64_t row = next_row(rs); row >= 0; row = next_row(rs)) {
+  const int64_t n_long = long_rows(rs);
+  for (int64_t row = next_long_row(rs, n_long, &s_row); row >= 0; row = next_long_row(rs, n_long, &s_row)) {
     const int64_t y = row + row_begin;
     int64_t p = rp[row] - rp[0];
     const int64_t p1 = rp[row + 1] - rp[0];
+    if (M.has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
     T da = Pol::zero(), db = Pol::zero();
-    if (has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
-    for (int64_t base = p; base < p1; base += 32) {
-      const int64_t q = base + lane;
-      const bool have = q < p1;
-      const uint32_t j = have ? __ldg(pair_j + q) : 0u;
-      T h = Pol::zero();
-      if (LOAD_H) {
-        if (have) h = HStore<Pol>::get(hpair, q);
-      } else {
-        const uint32_t k = have ? __ldg(pair_k + q) : 0u;
-        const bool heavy = have && (int64_t)k < heavy_end;
-        uint32_t hb = __ballot_sync(kFull, heavy);
-        while (hb) {
-          const int src = __ffs(hb) - 1;
-          hb &= hb - 1;
-          const uint32_t jj = __shfl_sync(kFull, j, src);
-          const uint32_t kk = __shfl_sync(kFull, k, src);
-          uint64_t xp[W];
-          load_words<W>(U + (int64_t)jj * W, xp);
-          T part = melem_part<Pol, W>(xp, (int64_t)__ldg(t_ptr + kk) + lane, (int64_t)__ldg(t_ptr + kk + 1), 32,
-                                      yz, cf, cd);
-          part = Pol::warp_sum(part);
-          if (lane == src) h = part;
-        }
-        if (have && !heavy) {
-          uint64_t xp[W];
-          load_words<W>(U + (int64_t)j * W, xp);
-          h = Pol::fin(melem_part<Pol, W>(xp, (int64_t)__ldg(t_ptr + k), (int64_t)__ldg(t_ptr + k + 1), 1, yz, cf,
-                                          cd));
-        }
-      }
-      if (have) {
-        T rr, ri, ge, gi;
-        ratio<Pol, CPLX>(P, Q, K, y, j, rr, ri, status);
-        load_geff<Pol>(G, j, ge, gi);
-        const T tr = Pol::mul(h, rr);
-        Pol::acc(da, Pol::mul(ge, tr));
-        if (CPLX) {
-          const T ti = Pol::mul(h, ri);
-          Pol::acc(da, Pol::mul(gi, ti));
-          Pol::acc(db, Pol::neg(Pol::mul(ge, ti)));
-          Pol::acc(db, Pol::mul(gi, tr));
-        }
-      }
+    backward_rounds<Pol, W, CPLX, LOAD_H>(U, M, P, Q, K, G, y, p, p1, warp, kEnergyWarps, pair_j, pair_k, hpair,
+                                          status, da, db);
+    da = Pol::warp_sum(da);
+    db = CPLX ? Pol::warp_sum(db) : Pol::zero();
+    if (lane == 0) {
+      s_a[warp] = da;
+      s_b[warp] = db;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T ta = s_a[0], tb = s_b[0];
+      for (int w = 1; w < kEnergyWarps; ++w) {
+        ta = Pol::add(ta, s_a[w]);
+        tb = Pol::add(tb, s_b[w]);
+      }
+      backward_finish<CPLX>(y, Pol::to_d(ta), CPLX ? Pol::to_d(tb) : 0.0, a, er, ei, hdiag, g_re, g_im, gE, E,
+                            amax, S, gre, gim);
+    }
+  }
+  for (int64_t row = next_row(rs, n_long); row >= 0; row = next_row(rs, n_long)) {
+    const int64_t y = row + row_begin;
+    int64_t p = rp[row] - rp[0];
+    const int64_t p1 = rp[row + 1] - rp[0];
+    if (M.has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
+    T da = Pol::zero(), db = Pol::zero();
+    backward_rounds<Pol, W, CPLX, LOAD_H>(U, M, P, Q, K, G, y, p, p1, 0, 1, pair_j, pair_k, hpair, status, da, db);
     const double sa = Pol::to_d(Pol::warp_sum(da));
     const double sb = CPLX ? Pol::to_d(Pol::warp_sum(db)) : 0.0;
-    if (lane == 0) {
-      const double w = exp(2.0 * (a[y] - amax)) / S;
-      const double ge_y = (g_re ? g_re[y] : 0.0) + gE * w;
-      const double gi_y = g_im ? g_im[y] : 0.0;
-      const double Dr = -(er[y] - hdiag[y]);
-      const double Di = CPLX ? -ei[y] : 0.0;
-      gre[y] = sa + ge_y * Dr + gi_y * Di + gE * 2.0 * w * (er[y] - E);
-      if (gim) gim[y] = CPLX ? (sb - ge_y * Di + gi_y * Dr) : 0.0;
-    }
+    if (lane == 0) backward_finish<CPLX>(y, sa, sb, a, er, ei, hdiag, g_re, g_im, gE, E, amax, S, gre, gim);
   }
 }
 
@@ -682,8 +904,7 @@ static void launch_bw(const nqs_ham* ham, const uint64_t* U, char* stage, const 
                       const BwArgs& b, cudaStream_t s) {
   auto kern = backward_pairs_kernel<Pol, W, CPLX, LOAD_H>;
   kern<<<grid_for(kern, rs.rows), kEnergyThreads, 0, s>>>(
-      U, ham->row_ptr, ham->yz, ham->coef_f, ham->coef, ham->has_diag, ham->heavy_end,
-      stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK), stage + L.off_geff,
+      U, melem_tables(ham), stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK), stage + L.off_geff,
       rb, rs, rp, pj, pk, b.hpair, b.a, b.er, b.ei, b.hd, b.evar, b.g_re, b.g_im, b.g_evar, b.gre, b.gim,
       (int32_t*)(stage + offsetof(StageHeader, status)));
 }

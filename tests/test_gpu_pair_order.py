@@ -108,11 +108,20 @@ def test_star_long_row(n_two):
     sel = np.random.default_rng(3).choice(len(rows), 20000, replace=False)
     for t in sel:
         assert samples[rows[t]] ^ samples[j[t]] == xy[k[t]]
-    # local energies of a few rows, the long one included, against the oracle
-    er, _, _ = nqs.local_energy(batch, logpsi, None, pairs, "fp64")
+    # local energies and the adjoint of a few rows, the long one (one block,
+    # warps dealt its rounds) included, against the oracle
+    er, _, hd = nqs.local_energy(batch, logpsi, None, pairs, "fp64")
+    ev = nqs.variational_energy(batch, logpsi, er)
+    g = np.random.default_rng(5).normal(0.0, 1.0, len(samples))
+    gr, _ = nqs.local_energy_backward(batch, logpsi, None, er, None, hd, ev, g, None, None, pairs, "fp64")
     ro = oracle.RowOracle(U, oracle.prepare_hamiltonian(x, z, c, n_qubits), logpsi)
     for r in [hub, 0, 1, len(samples) - 1]:
-        assert abs(er[r].item() - ro.row(r)["eloc"].real) < 1e-9
+        want = ro.row(r)["eloc"]
+        assert abs(er[r].item() - want.real) < 1e-9
+        eloc = np.zeros(len(samples), complex)
+        eloc[r] = want
+        g_want, _ = ro.row_vjp(r, eloc, 0.0, g_eloc_re=g, g_evar=0.0)
+        assert abs(gr[r].item() - g_want) < 1e-9 * max(1.0, abs(g_want))
     # one-pass and two-pass lists agree
     two = nqs.coupled_pairs(batch, one_pass=False)
     for a_, b_ in zip(pairs, two):

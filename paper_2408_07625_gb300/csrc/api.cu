@@ -117,7 +117,7 @@ static void free_ham(nqs_ham* h) {
   cudaFree(h->xy); cudaFree(h->row_ptr); cudaFree(h->yz); cudaFree(h->coef);
   cudaFree(h->coef_f); cudaFree(h->srch_hash); cudaFree(h->srch_id); cudaFree(h->srch_rec); cudaFree(h->hash_basis);
   cudaFree(h->xy_table); cudaFree(h->wmask); cudaFree(h->xy_trie); cudaFree(h->xy_hash); cudaFree(h->segs);
-  cudaFree(h->lin_id); cudaFree(h->lin_z0); cudaFree(h->lin_d); cudaFree(h->lin_f); cudaFree(h->quad_d);
+  cudaFree(h->fm); cudaFree(h->fv_d); cudaFree(h->fv_f); cudaFree(h->fz); cudaFree(h->quad_d);
   cudaFree(h->quad_f);
   delete h;
 }
@@ -247,11 +247,10 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
   }
   h->h_row_ptr[G] = t;
 
-  // MatrixElement forms.  Both regroup the sum of Eq. pauli_melem exactly;
+  // MatrixElement forms.  Each regroups the sum of Eq. pauli_melem exactly;
   // coefficients are summed with Neumaier compensation in a fixed order.
-  //   linear: a heavy pattern whose terms' YZ masks differ from the first
-  //     term's YZ_0 in at most one qubit r:  c (-1)^{x'.YZ} = c (-1)^{x'.YZ_0}
-  //     (1 - 2 x'_r), so H = (-1)^{x'.YZ_0} (C - 2 sum_{r in x'} a_r);
+  //   local: YZ_l = A XOR B_l with B_l inside the pattern's qubits, so
+  //     c (-1)^{x'.YZ_l} = c (-1)^{x'.A} (-1)^{u.B_l}, u = x' on those qubits;
   //   quadratic diagonal: every diagonal term a Z string on at most two
   //     qubits: c (-1)^{x_r + x_s} = c (1 - 2 x_r)(1 - 2 x_s).
   struct CSum {
@@ -264,29 +263,41 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
     double value() const { return s + c; }
   };
   const int NQ = 64 * W;
-  h->lin_stride = 1 + NQ;
-  std::vector<int32_t> lin_id(G, -1);
-  std::vector<uint64_t> lin_z0;
-  std::vector<double> lin_d;
-  for (int64_t p = h->has_diag; p < h->heavy_end; ++p) {
+  std::vector<int4> fm(G, make_int4(kForm::Terms, 0, 0, 0));
+  std::vector<double> fv;
+  std::vector<uint64_t> fz;
+  for (int64_t p = h->has_diag; p < G; ++p) {
     const int64_t t0 = h->h_row_ptr[p], t1 = h->h_row_ptr[p + 1];
-    std::vector<CSum> acc(1 + NQ);
-    bool ok = true;
-    for (int64_t t = t0; t < t1 && ok; ++t) {
-      int wt = 0, r = -1;
-      for (int w = 0; w < W; ++w) {
-        const uint64_t d = h->h_yz[t * W + w] ^ h->h_yz[t0 * W + w];
-        wt += __builtin_popcountll(d);
-        if (d) r = 64 * w + __builtin_ctzll(d);
+    const uint64_t* xy = &h->h_xy[p * W];
+    const int nb = popc_words(xy, W);
+    // local: every YZ_l agrees with YZ_0 outside XY
+    bool local = nb <= 4;
+    for (int64_t t = t0; t < t1 && local; ++t)
+      for (int w = 0; w < W; ++w)
+        if ((h->h_yz[t * W + w] ^ h->h_yz[t0 * W + w]) & ~xy[w]) local = false;
+    if (local) {
+      int q[4], n = 0;
+      for (int w = 0; w < W; ++w)
+        for (uint64_t m = xy[w]; m; m &= m - 1) q[n++] = 64 * w + __builtin_ctzll(m);
+      uint32_t packed = 0;
+      for (int i = 0; i < nb; ++i) packed |= (uint32_t)q[i] << (8 * i);
+      std::vector<CSum> T(1u << nb);
+      for (int64_t t = t0; t < t1; ++t) {
+        uint32_t bl = 0;  // YZ_l on the pattern's qubits, compressed
+        for (int i = 0; i < nb; ++i) bl |= (uint32_t)((h->h_yz[t * W + q[i] / 64] >> (q[i] % 64)) & 1ull) << i;
+        for (uint32_t u = 0; u < (1u << nb); ++u)
+          T[u].add((__builtin_popcount(u & bl) & 1) ? -h->h_coef[t] : h->h_coef[t]);
       }
-      if (wt > 1) { ok = false; break; }
-      acc[0].add(h->h_coef[t]);
-      if (wt == 1) acc[1 + r].add(-2.0 * h->h_coef[t]);
+      fm[p] = make_int4(kForm::Local | (nb << 4), (int)fv.size(), (int)(fz.size() / W), (int)packed);
+      for (auto& v : T) fv.push_back(v.value());
+      for (int w = 0; w < W; ++w) fz.push_back(h->h_yz[t0 * W + w] & ~xy[w]);
+      ++h->n_local;
     }
-    if (!ok) continue;
-    lin_id[p] = (int32_t)h->n_lin++;
-    for (int w = 0; w < W; ++w) lin_z0.push_back(h->h_yz[t0 * W + w]);
-    for (auto& a : acc) lin_d.push_back(a.value());
+  }
+  if (fv.size() >= (size_t)INT32_MAX || fz.size() / W >= (size_t)INT32_MAX) {
+    std::fill(fm.begin(), fm.end(), make_int4(kForm::Terms, 0, 0, 0));  // tables too large to index
+    fv.clear();
+    fz.clear();
   }
   std::vector<double> quad_d;
   if (h->has_diag) {
@@ -320,7 +331,7 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
     }
     return f;
   };
-  const std::vector<float2> lin_f = split(lin_d), quad_f = split(quad_d);
+  const std::vector<float2> fv_f = split(fv), quad_f = split(quad_d);
 
   // linear hash basis: h(v) = XOR over set bits b of R[b] (GF(2)-linear, so
   // h(x ^ xy) = h(x) ^ h(xy) and a candidate's hash costs one XOR)
@@ -429,8 +440,8 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
       (rc = upload(&h->srch_id, srch_id)) || (rc = upload(&h->srch_rec, srch_rec)) ||
       (rc = upload(&h->hash_basis, h->h_hash_basis)) || (rc = upload(&h->xy_table, xy_table)) ||
       (rc = upload(&h->wmask, wmask)) || (rc = upload(&h->xy_trie, xy_trie)) ||
-      (rc = upload(&h->xy_hash, hxy)) || (rc = upload(&h->segs, segs)) || (rc = upload(&h->lin_id, lin_id)) ||
-      (rc = upload(&h->lin_z0, lin_z0)) || (rc = upload(&h->lin_d, lin_d)) || (rc = upload(&h->lin_f, lin_f)) ||
+      (rc = upload(&h->xy_hash, hxy)) || (rc = upload(&h->segs, segs)) || (rc = upload(&h->fm, fm)) ||
+      (rc = upload(&h->fv_d, fv)) || (rc = upload(&h->fv_f, fv_f)) || (rc = upload(&h->fz, fz)) ||
       (rc = upload(&h->quad_d, quad_d)) || (rc = upload(&h->quad_f, quad_f))) {
     free_ham(h);
     return rc;

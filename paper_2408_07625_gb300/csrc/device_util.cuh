@@ -85,7 +85,14 @@ __device__ __forceinline__ df df_from_double(double v) {
 
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
-__device__ __forceinline__ df df_ldexp(df a, int e) { return {ldexpf(a.hi, e), ldexpf(a.lo, e)}; }
+// a * 2^e for |e| <= 126: multiplication by the power of two built from its
+// IEEE-754 exponent field (exact unless the product leaves the normal range)
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+__device__ __forceinline__ df df_ldexp(df a, int e) {
+  const float s = pow2f(e);
+  return {a.hi * s, a.lo * s};
+}
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 
 // flip the sign of both parts when bit is 1 (exact)
 __device__ __forceinline__ df df_signflip(float2 c, uint32_t bit) {

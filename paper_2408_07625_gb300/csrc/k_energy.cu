@@ -104,7 +104,7 @@ struct PolicyD {
   __device__ static T add(T a, T b) { return a + b; }
   __device__ static T mul(T a, T b) { return a * b; }
   __device__ static T neg(T a) { return -a; }
-  __device__ static T scale(T a, int e) { return ldexp(a, e); }
+  __device__ static T scale(T a, int e) { return a * pow2d(e); }  // |e| <= kMaxExp
   __device__ static T fin(T a) { return a; }
   __device__ static T warp_sum(T a) { return nqs::warp_sum(a); }
   __device__ static double to_d(T a) { return a; }
@@ -149,83 +149,106 @@ struct Melem {
   const double* cd;
   int has_diag;
   int64_t heavy_end;
-  const int32_t* lin_id;   // linear-form index of a heavy pattern, or -1
-  const uint64_t* lin_z0;
-  const float2* lin_f;
-  const double* lin_d;
-  int lin_stride;
+  const int4* fm;          // per pattern: {kind | nb << 4, table offset, mask offset, packed qubits}
+  const float2* fv_f;
+  const double* fv_d;
+  const uint64_t* fz;
   int diag_quad;
   const float2* quad_f;
   const double* quad_d;
 };
 
 static Melem melem_tables(const nqs_ham* h) {
-  return Melem{h->row_ptr, h->yz, h->coef_f, h->coef, h->has_diag, h->heavy_end, h->lin_id, h->lin_z0,
-               h->lin_f, h->lin_d, h->lin_stride, h->diag_quad, h->quad_f, h->quad_d};
+  return Melem{h->row_ptr, h->yz, h->coef_f, h->coef, h->has_diag, h->heavy_end, h->fm,
+               h->fv_f, h->fv_d, h->fz, h->diag_quad, h->quad_f, h->quad_d};
 }
 
-// partial matrix element over the terms l = t0 + lane0, t0 + lane0 + step, ... < t1
+// The terms [t0, t1) of one pattern summed by the whole warp: lane t adds
+// terms t0 + t, t0 + t + 32, ... in order, four loads in flight at a time;
+// every lane runs the same number of steps (terms past t1 add nothing).
+// Every lane returns the same value.
 template <class Pol, int W>
-__device__ __forceinline__ typename Pol::T melem_part(const uint64_t (&xp)[W], int64_t t0, int64_t t1,
-                                                       int step, const uint64_t* __restrict__ yz,
-                                                       const float2* __restrict__ cf,
-                                                       const double* __restrict__ cd) {
-  typename Pol::T h = Pol::zero();
-  for (int64_t l = t0; l < t1; l += step) {
-    const uint32_t par = parity_and<W>(xp, yz + l * W);
-    Pol::acc(h, Pol::coef(cf, cd, l, par));
-  }
-  return h;
-}
+__device__ __forceinline__ typename Pol::T melem_warp(const uint64_t (&xp)[W], int64_t t0, int64_t t1,
+                                                       const Melem& M);
 
-// H of one pair by one lane: the linear form when the pattern has one,
-// else the pattern's terms (Eq. pauli_melem; loads of four terms in flight)
+// H of one pair by one lane, in the pattern's form (fm = its descriptor):
+// local (one table value) or the pattern's terms (loads of four terms in
+// flight).
 template <class Pol, int W>
-__device__ __forceinline__ typename Pol::T melem_lane(const uint64_t (&xp)[W], uint32_t k, int32_t lm,
+__device__ __forceinline__ typename Pol::T melem_lane(const uint64_t (&xp)[W], uint32_t k, int4 fm,
                                                        const Melem& M) {
   using T = typename Pol::T;
-  T h = Pol::zero();
-  if (lm >= 0) {
-    const int64_t b = (int64_t)lm * M.lin_stride;
-    h = Pol::val(M.lin_f, M.lin_d, b);
+  const int kind = fm.x & 15;
+  if (kind == kForm::Local) {
+    const int nb = fm.x >> 4;
+    uint32_t u = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w)
-      for (uint64_t v = xp[w]; v; v &= v - 1)
-        Pol::acc(h, Pol::val(M.lin_f, M.lin_d, b + 1 + 64 * w + (__ffsll((long long)v) - 1)));
-    h = Pol::fin(h);
-    return parity_and<W>(xp, M.lin_z0 + (int64_t)lm * W) ? Pol::neg(h) : h;
+    for (int i = 0; i < 4; ++i) {
+      if (i < nb) {
+        const int q = (fm.w >> (8 * i)) & 255;
+        u |= (uint32_t)((xp[q >> 6] >> (q & 63)) & 1ull) << i;
+      }
+    }
+    const T h = Pol::val(M.fv_f, M.fv_d, (int64_t)fm.y + u);
+    return parity_and<W>(xp, M.fz + (int64_t)fm.z * W) ? Pol::neg(h) : h;
   }
+  T h = Pol::zero();
   const int64_t t0 = __ldg(M.t_ptr + k), t1 = __ldg(M.t_ptr + k + 1);
 #pragma unroll 4
   for (int64_t l = t0; l < t1; ++l) Pol::acc(h, Pol::coef(M.cf, M.cd, l, parity_and<W>(xp, M.yz + l * W)));
   return Pol::fin(h);
 }
 
+template <class Pol, int W>
+__device__ __forceinline__ typename Pol::T melem_warp(const uint64_t (&xp)[W], int64_t t0, int64_t t1,
+                                                       const Melem& M) {
+  using T = typename Pol::T;
+  const int lane = threadIdx.x & 31;
+  T h = Pol::zero();
+  for (int64_t b = t0; b < t1; b += 4 * 32) {
+    T c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t l = b + 32 * u + lane;
+      c[u] = l < t1 ? Pol::coef(M.cf, M.cd, l, parity_and<W>(xp, M.yz + l * W)) : Pol::zero();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) Pol::acc(h, c[u]);
+  }
+  return Pol::warp_sum(h);
+}
+
 // H_xx by the whole warp: the quadratic form (lane t takes the occupied
-// qubits r with rank t mod 32 and adds b_r + sum_{s > r occupied} B_rs) or
-// the diagonal pattern's terms; every lane returns the same value.
+// qubits r of rank t, t + 32, .. and adds b_r + sum_{s > r occupied} B_rs;
+// the lanes work side by side) or the diagonal pattern's terms; every lane
+// returns the same value.
 template <class Pol, int W>
 __device__ __forceinline__ typename Pol::T melem_diag(const uint64_t (&x)[W], const Melem& M) {
   using T = typename Pol::T;
   const int lane = threadIdx.x & 31;
-  if (!M.diag_quad)
-    return Pol::warp_sum(melem_part<Pol, W>(x, (int64_t)__ldg(M.t_ptr) + lane, (int64_t)__ldg(M.t_ptr + 1), 32,
-                                            M.yz, M.cf, M.cd));
+  if (!M.diag_quad) return melem_warp<Pol, W>(x, (int64_t)__ldg(M.t_ptr), (int64_t)__ldg(M.t_ptr + 1), M);
   constexpr int NQ = 64 * W;
   T h = lane == 0 ? Pol::val(M.quad_f, M.quad_d, 0) : Pol::zero();
-  int rank = 0;
+  int before = 0;  // occupied qubits in the words before w
 #pragma unroll
   for (int w = 0; w < W; ++w) {
-    for (uint64_t v = x[w]; v; v &= v - 1, ++rank) {
-      if ((rank & 31) != lane) continue;
-      const int r = 64 * w + (__ffsll((long long)v) - 1);
+    const int cnt = __popcll(x[w]);
+    for (int t = lane; t < before + cnt; t += 32) {  // this lane's occupied qubits in word w
+      if (t < before) continue;
+      const int n = t - before;                     // rank inside the word
+      const uint32_t lo = (uint32_t)x[w], hi = (uint32_t)(x[w] >> 32);
+      const int nlo = __popc(lo);
+      const int b = n < nlo ? (int)__fns(lo, 0, n + 1) : 32 + (int)__fns(hi, 0, n - nlo + 1);
+      const int r = 64 * w + b;
       Pol::acc(h, Pol::val(M.quad_f, M.quad_d, 1 + r));
       const int64_t row = 1 + NQ + (int64_t)r * NQ;
+      const uint64_t above = b == 63 ? 0ull : (x[w] & (~0ull << (b + 1)));
 #pragma unroll
       for (int w2 = w; w2 < W; ++w2)
-        for (uint64_t u = (w2 == w) ? (v & (v - 1)) : x[w2]; u; u &= u - 1)
+        for (uint64_t u = (w2 == w) ? above : x[w2]; u; u &= u - 1)
           Pol::acc(h, Pol::val(M.quad_f, M.quad_d, row + 64 * w2 + (__ffsll((long long)u) - 1)));
     }
+    before += cnt;
   }
   return Pol::warp_sum(h);
 }
@@ -373,32 +396,26 @@ __device__ __forceinline__ void energy_rounds(const uint64_t* __restrict__ U, co
       jn = __ldg(pair_j + q + 32 * stride);
       kn = __ldg(pair_k + q + 32 * stride);
     }
-    const bool heavy = have && (int64_t)k < M.heavy_end;
-    const int32_t lm = heavy ? __ldg(M.lin_id + k) : -1;
-    const bool coop = heavy && lm < 0;
+    const int4 fm = have ? __ldg(M.fm + k) : make_int4(0, 0, 0, 0);
+    const bool coop = have && (int64_t)k < M.heavy_end && (fm.x & 15) == kForm::Terms;
+    T h = Pol::zero();
     uint32_t hb = __ballot_sync(kFull, coop);
-    while (hb) {  // heavy pattern without a linear form: all lanes share its term loop
+    while (hb) {  // heavy pattern in term form: all lanes share its term loop, its lane keeps H
       const int src = __ffs(hb) - 1;
       hb &= hb - 1;
       const uint32_t jj = __shfl_sync(kFull, j, src);
       const uint32_t kk = __shfl_sync(kFull, k, src);
       uint64_t xp[W];
       load_words<W>(U + (int64_t)jj * W, xp);
-      T h = melem_part<Pol, W>(xp, (int64_t)__ldg(M.t_ptr + kk) + lane, (int64_t)__ldg(M.t_ptr + kk + 1), 32,
-                               M.yz, M.cf, M.cd);
-      h = Pol::warp_sum(h);
-      if (lane == src) {
-        T rr, ri;
-        ratio<Pol, CPLX>(P, Q, K, jj, i, rr, ri, status);
-        Pol::acc(acc_re, Pol::mul(h, rr));
-        if (CPLX) Pol::acc(acc_im, Pol::mul(h, ri));
-        if (STORE_H) HStore<Pol>::put(hpair, q, h);
-      }
+      const T hw = melem_warp<Pol, W>(xp, (int64_t)__ldg(M.t_ptr + kk), (int64_t)__ldg(M.t_ptr + kk + 1), M);
+      if (lane == src) h = hw;
     }
-    if (have && !coop) {
-      uint64_t xp[W];
-      load_words<W>(U + (int64_t)j * W, xp);
-      const T h = melem_lane<Pol, W>(xp, k, lm, M);
+    if (have) {
+      if (!coop) {
+        uint64_t xp[W];
+        load_words<W>(U + (int64_t)j * W, xp);
+        h = melem_lane<Pol, W>(xp, k, fm, M);
+      }
       T rr, ri;
       ratio<Pol, CPLX>(P, Q, K, j, i, rr, ri, status);
       Pol::acc(acc_re, Pol::mul(h, rr));
@@ -779,9 +796,8 @@ __device__ __forceinline__ void backward_rounds(const uint64_t* __restrict__ U, 
     if (LOAD_H) {
       if (have) h = HStore<Pol>::get(hpair, q);
     } else {
-      const bool heavy = have && (int64_t)k < M.heavy_end;
-      const int32_t lm = heavy ? __ldg(M.lin_id + k) : -1;
-      const bool coop = heavy && lm < 0;
+      const int4 fm = have ? __ldg(M.fm + k) : make_int4(0, 0, 0, 0);
+      const bool coop = have && (int64_t)k < M.heavy_end && (fm.x & 15) == kForm::Terms;
       uint32_t hb = __ballot_sync(kFull, coop);
       while (hb) {
         const int src = __ffs(hb) - 1;
@@ -790,15 +806,13 @@ __device__ __forceinline__ void backward_rounds(const uint64_t* __restrict__ U, 
         const uint32_t kk = __shfl_sync(kFull, k, src);
         uint64_t xp[W];
         load_words<W>(U + (int64_t)jj * W, xp);
-        T part = melem_part<Pol, W>(xp, (int64_t)__ldg(M.t_ptr + kk) + lane, (int64_t)__ldg(M.t_ptr + kk + 1), 32,
-                                    M.yz, M.cf, M.cd);
-        part = Pol::warp_sum(part);
-        if (lane == src) h = part;
+        const T hw = melem_warp<Pol, W>(xp, (int64_t)__ldg(M.t_ptr + kk), (int64_t)__ldg(M.t_ptr + kk + 1), M);
+        if (lane == src) h = hw;
       }
       if (have && !coop) {
         uint64_t xp[W];
         load_words<W>(U + (int64_t)j * W, xp);
-        h = melem_lane<Pol, W>(xp, k, lm, M);
+        h = melem_lane<Pol, W>(xp, k, fm, M);
       }
     }
     if (have) {

@@ -13,6 +13,7 @@ namespace nqs {
 constexpr int kMaxWords = 4;                 // N <= 256 qubits
 constexpr uint32_t kDummy = 0xFFFFFFFFu;     // padding slot of the search table
 constexpr int kHeavyTerms = 24;              // |P_XY| above this: warp-cooperative term loop
+namespace kForm { constexpr int Terms = 0, Local = 1; }
 constexpr int kQueueCap = 256;               // per-warp candidate queue (entries)
 constexpr int kRowsPerWarp = 8;              // rows scanned together by one warp
 constexpr int kSortWarpMax = 512;           // rows with up to this many pairs are sorted by one warp
@@ -68,19 +69,21 @@ struct nqs_ham_dev {
   int64_t n_xy_nodes = 0;
   uint32_t* xy_hash = nullptr;   // [n_xy] linear hash of each pattern
 
-  // MatrixElement forms (exact regroupings of the sum of Eq. pauli_melem):
-  //   linear pattern m (heavy, every YZ_l within one qubit of its first term's
-  //   YZ_0): H = (-1)^{|x' & YZ_0|} (C - 2 sum_{r in x'} a_r), stored as rows
-  //   [C, -2 a_0, .., -2 a_{64W-1}] of lin_stride = 1 + 64 W values;
-  //   quadratic diagonal (every diagonal term a Z string on at most two qubits):
+  // MatrixElement forms (exact regroupings of the sum of Eq. pauli_melem),
+  // chosen per pattern at load; fm[k] = {kind | nb << 4, table offset, mask
+  // offset, packed qubits}:
+  //   kForm::Local  every YZ_l agrees with YZ_0 outside the pattern's own
+  //     nb <= 4 qubits (packed 8 bits each): H = (-1)^{|x' & A|} T[u], A the
+  //     common part, u = x' read at those qubits, T the 2^nb table;
+  //   kForm::Terms  the term loop (heavy patterns: all lanes of a warp).
+  // quadratic diagonal (every diagonal term a Z string on at most two qubits):
   //   H_xx = C + sum_{r in x} b_r + sum_{r < s in x} B_rs, stored as
   //   [C, b_0 .. b_{64W-1}, B (64W x 64W, row-major, r < s used)].
-  int32_t* lin_id = nullptr;     // [n_xy] linear-form index of the pattern or -1
-  uint64_t* lin_z0 = nullptr;    // [n_lin][W]
-  double* lin_d = nullptr;       // [n_lin][lin_stride]
-  float2* lin_f = nullptr;       // same, (hi, lo) split
-  int64_t n_lin = 0;
-  int lin_stride = 0;
+  int4* fm = nullptr;            // [n_xy]
+  double* fv_d = nullptr;        // value pool
+  float2* fv_f = nullptr;        // same, (hi, lo) split
+  uint64_t* fz = nullptr;        // mask pool [..][W]
+  int64_t n_local = 0;
   int diag_quad = 0;             // the diagonal pattern uses the quadratic form
   double* quad_d = nullptr;      // [1 + 64W + (64W)^2]
   float2* quad_f = nullptr;

@@ -59,11 +59,12 @@ StageHeader stage_layout(const nqs_ham* ham, int64_t n) {
   L.off_ampQ = off;   off = align256(off + 16 * n1);
   L.off_ampK = off;   off = align256(off + 4 * n1);
   L.off_geff = off;   off = align256(off + 16 * n1);
+  L.off_own = off;    off = align256(off + 16 * n1);
   L.off_counters = off; off = align256(off + 256);
   L.off_q = off;      off = align256(off + 2 * 4 * 64 * kMaxWords);
   L.off_qrows = off;  off = align256(off + 4 * n1 * (int64_t)ham->n_qubits);
   L.off_big = off;    off = align256(off + 4 * n1);
-  L.off_rowcur = off; off = align256(off + 4 * n1);
+  L.off_rowcur = off; off = align256(off + 8 * n1);
   L.off_trie = off;   off = align256(off + trie_bytes(ham->W, n));
   L.off_sched = off;  off = align256(off + 512);
   L.off_order = off;  off = align256(off + 4 * n1);

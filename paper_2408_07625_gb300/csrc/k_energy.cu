@@ -722,13 +722,19 @@ static cudaError_t evar_scratch_address(void** out) {
 // --------------------------------------------------------------------------
 // adjoint
 // --------------------------------------------------------------------------
-// per-sample effective upstream: ge(x) = g_re(x) + g_E w(x), gi(x) = g_im(x)
+// per-sample effective upstream: ge(x) = g_re(x) + g_E w(x), gi(x) = g_im(x);
+// and, for the rows y of [rb, re), the row's own terms of the gradient,
+// D_yy = -(E_loc(y) - H_yy) and g_E 2 w_y (Re E_loc(y) - E):
+//   own(y) = (ge_y Re D + gi_y Im D + g_E 2 w_y (Re E_loc(y) - E), gi_y Re D - ge_y Im D)
+// (FP64 once per sample, all lanes busy, instead of in the row kernels' epilogue)
 __global__ void geff_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ evar,
                             const double* __restrict__ g_re, const double* __restrict__ g_im,
                             const double* __restrict__ g_evar, int fp64, double2* __restrict__ gd,
-                            float4* __restrict__ gf) {
+                            float4* __restrict__ gf, int64_t rb, int64_t re, const double* __restrict__ er,
+                            const double* __restrict__ ei, const double* __restrict__ hdiag,
+                            double2* __restrict__ own) {
   const double gE = g_evar ? g_evar[0] : 0.0;
-  const double amax = evar[1], S = evar[2];
+  const double E = evar[0], amax = evar[1], S = evar[2];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double w = exp(2.0 * (a[i] - amax)) / S;
@@ -739,6 +745,11 @@ __global__ void geff_kernel(int64_t n, const double* __restrict__ a, const doubl
     } else {
       df a1 = df_from_double(ge), a2 = df_from_double(gi);
       gf[i] = make_float4(a1.hi, a1.lo, a2.hi, a2.lo);
+    }
+    if (i >= rb && i < re) {
+      const double Dr = -(er[i] - hdiag[i]);
+      const double Di = ei ? -ei[i] : 0.0;
+      own[i] = make_double2(ge * Dr + gi * Di + gE * 2.0 * w * (er[i] - E), gi * Dr - ge * Di);
     }
   }
 }
@@ -831,19 +842,13 @@ __device__ __forceinline__ void backward_rounds(const uint64_t* __restrict__ U, 
   }
 }
 
-// the row's own terms: D_yy = -(E_loc(y) - H_yy) and g_E 2 w_y (Re E_loc(y) - E)
+// the pair sums plus the row's own terms (from geff_kernel)
 template <bool CPLX>
-__device__ __forceinline__ void backward_finish(int64_t y, double sa, double sb, const double* a,
-                                                const double* er, const double* ei, const double* hdiag,
-                                                const double* g_re, const double* g_im, double gE, double E,
-                                                double amax, double S, double* gre, double* gim) {
-  const double w = exp(2.0 * (a[y] - amax)) / S;
-  const double ge_y = (g_re ? g_re[y] : 0.0) + gE * w;
-  const double gi_y = g_im ? g_im[y] : 0.0;
-  const double Dr = -(er[y] - hdiag[y]);
-  const double Di = CPLX ? -ei[y] : 0.0;
-  gre[y] = sa + ge_y * Dr + gi_y * Di + gE * 2.0 * w * (er[y] - E);
-  if (gim) gim[y] = CPLX ? (sb - ge_y * Di + gi_y * Dr) : 0.0;
+__device__ __forceinline__ void backward_finish(int64_t y, double sa, double sb, const double2* own, double* gre,
+                                                double* gim) {
+  const double2 o = own[y];
+  gre[y] = sa + o.x;
+  if (gim) gim[y] = CPLX ? sb + o.y : 0.0;
 }
 
 template <class Pol, int W, bool CPLX, bool LOAD_H>
@@ -853,11 +858,7 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
                       const int* __restrict__ K, const char* __restrict__ G,
                       int64_t row_begin, RowSched rs, const int64_t* __restrict__ rp,
                       const uint32_t* __restrict__ pair_j, const uint32_t* __restrict__ pair_k,
-                      const void* __restrict__ hpair,
-                      const double* __restrict__ a, const double* __restrict__ er,
-                      const double* __restrict__ ei, const double* __restrict__ hdiag,
-                      const double* __restrict__ evar, const double* __restrict__ g_re,
-                      const double* __restrict__ g_im, const double* __restrict__ g_evar,
+                      const void* __restrict__ hpair, const double2* __restrict__ own,
                       double* __restrict__ gre, double* __restrict__ gim, int32_t* __restrict__ status) {
   using T = typename Pol::T;
   __shared__ T s_a[kEnergyWarps], s_b[kEnergyWarps];
@@ -865,8 +866,6 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
   if (*(volatile int32_t*)status & kStatusCapacity) return;  // the pair list was not written
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const double gE = g_evar ? g_evar[0] : 0.0;
-  const double E = evar[0], amax = evar[1], S = evar[2];
   const int64_t n_long = long_rows(rs);
   for (int64_t row = next_long_row(rs, n_long, &s_row); row >= 0; row = next_long_row(rs, n_long, &s_row)) {
     const int64_t y = row + row_begin;
@@ -889,8 +888,7 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
         ta = Pol::add(ta, s_a[w]);
         tb = Pol::add(tb, s_b[w]);
       }
-      backward_finish<CPLX>(y, Pol::to_d(ta), CPLX ? Pol::to_d(tb) : 0.0, a, er, ei, hdiag, g_re, g_im, gE, E,
-                            amax, S, gre, gim);
+      backward_finish<CPLX>(y, Pol::to_d(ta), CPLX ? Pol::to_d(tb) : 0.0, own, gre, gim);
     }
   }
   for (int64_t row = next_row(rs, n_long); row >= 0; row = next_row(rs, n_long)) {
@@ -902,12 +900,12 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
     backward_rounds<Pol, W, CPLX, LOAD_H>(U, M, P, Q, K, G, y, p, p1, 0, 1, pair_j, pair_k, hpair, status, da, db);
     const double sa = Pol::to_d(Pol::warp_sum(da));
     const double sb = CPLX ? Pol::to_d(Pol::warp_sum(db)) : 0.0;
-    if (lane == 0) backward_finish<CPLX>(y, sa, sb, a, er, ei, hdiag, g_re, g_im, gE, E, amax, S, gre, gim);
+    if (lane == 0) backward_finish<CPLX>(y, sa, sb, own, gre, gim);
   }
 }
 
 struct BwArgs {
-  const double *a, *er, *ei, *hd, *evar, *g_re, *g_im, *g_evar;
+  const double2* own;
   double *gre, *gim;
   const void* hpair;
 };
@@ -918,8 +916,8 @@ static void launch_bw(const nqs_ham* ham, const uint64_t* U, char* stage, const 
                       const BwArgs& b, cudaStream_t s) {
   auto kern = backward_pairs_kernel<Pol, W, CPLX, LOAD_H>;
   kern<<<grid_for(kern, rs.rows), kEnergyThreads, 0, s>>>(
-      U, melem_tables(ham), stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK), stage + L.off_geff,
-      rb, rs, rp, pj, pk, b.hpair, b.a, b.er, b.ei, b.hd, b.evar, b.g_re, b.g_im, b.g_evar, b.gre, b.gim,
+      U, melem_tables(ham), stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK),
+      stage + L.off_geff, rb, rs, rp, pj, pk, b.hpair, b.own, b.gre, b.gim,
       (int32_t*)(stage + offsetof(StageHeader, status)));
 }
 
@@ -966,12 +964,13 @@ cudaError_t launch_backward(const nqs_ham* ham, const uint64_t* U, int64_t n, ch
   {
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * num_sms()));
     geff_kernel<<<blocks, 256, 0, s>>>(n, a, evar, g_re, g_im, g_evar, fp64 ? 1 : 0,
-                                       (double2*)(stage + L.off_geff), (float4*)(stage + L.off_geff));
+                                       (double2*)(stage + L.off_geff), (float4*)(stage + L.off_geff), rb, re, er,
+                                       ei, hd, (double2*)(stage + L.off_own));
   }
   RowSched rs;
   cudaError_t e = launch_row_order(rp, rows, stage, L, rs, s);
   if (e != cudaSuccess) return e;
-  const BwArgs b{a, er, ei, hd, evar, g_re, g_im, g_evar, gre, gim, hpair};
+  const BwArgs b{(const double2*)(stage + L.off_own), gre, gim, hpair};
   if (fp64) launch_bw_p<PolicyD>(ham, U, stage, L, cplx, rb, rs, rp, pj, pk, b, s);
   else launch_bw_p<PolicyF>(ham, U, stage, L, cplx, rb, rs, rp, pj, pk, b, s);
   return cudaGetLastError();

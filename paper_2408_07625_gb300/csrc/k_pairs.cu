@@ -330,7 +330,7 @@ struct TermsArgs {
   int64_t row_begin, row_end;
   int64_t* counts;        // COUNT / EMIT: per-row counts of the range
   const int64_t* rp;      // FILL: CSR offsets of the range
-  int32_t* cursor;        // FILL: per-row write cursors
+  unsigned long long* cursor;  // FILL: per-row write cursors (relative to the row's start)
   uint32_t* pair_j;
   uint32_t* pair_k;
   PairScratch sc;         // EMIT
@@ -349,11 +349,11 @@ struct RowCache {   // per-warp copy of the item's rows (shared memory)
 // Place one pair in row r (relative to the range) at the row's next free
 // position; a row that is already full (counts that do not match this
 // search, e.g. a changed batch) flags the status instead of writing past it.
-__device__ __forceinline__ void place_pair(const int64_t* rp, int64_t r, int32_t* cursor, uint32_t* pj,
+__device__ __forceinline__ void place_pair(const int64_t* rp, int64_t r, unsigned long long* cursor, uint32_t* pj,
                                            uint32_t* pk, uint32_t col, uint32_t k, int32_t* status) {
   const int64_t a = rp[r] - rp[0];
   const int64_t len = rp[r + 1] - rp[r];
-  const int64_t c = atomicAdd(cursor + r, 1);
+  const int64_t c = (int64_t)atomicAdd(cursor + r, 1ull);
   if (c < len) {
     pj[a + c] = col;
     pk[a + c] = k;
@@ -704,13 +704,15 @@ static cudaError_t launch_terms_w(const TermsArgs& args, const StageHeader& L, c
 // one-pass records, and the per-row sort by column.
 // --------------------------------------------------------------------------
 
-// COUNT/EMIT: counts[r] = has_diag.  FILL: cursor[r] = has_diag and the
-// diagonal pair at the row's start (it leads the row and is not sorted).  In
-// FILL mode, if the pairs outgrow `capacity` or the scratch overflowed, flag
-// the status and write nothing.
+// COUNT/EMIT: counts[r] = has_diag.  FILL: the diagonal pair at the row's
+// start (it leads the row and is not sorted) and cursor[r] = has_diag, or,
+// with `absolute`, the row's first free position in the list.  In FILL mode,
+// if the pairs outgrow `capacity` or the scratch overflowed, flag the status
+// and write nothing.
 __global__ void pairs_init_kernel(int mode, int64_t rows, int64_t rb, int has_diag, int64_t* __restrict__ counts,
-                                  const int64_t* __restrict__ rp, int32_t* __restrict__ cursor,
-                                  uint32_t* __restrict__ pj, uint32_t* __restrict__ pk, int64_t capacity, const int64_t* __restrict__ overflow,
+                                  const int64_t* __restrict__ rp, unsigned long long* __restrict__ cursor,
+                                  int absolute, uint32_t* __restrict__ pj, uint32_t* __restrict__ pk,
+                                  int64_t capacity, const int64_t* __restrict__ overflow,
                                   int32_t* __restrict__ status) {
   if (mode == kFill) {
     const bool too_small = (capacity >= 0 && rp[rows] - rp[0] > capacity) || (overflow && *overflow != 0);
@@ -724,9 +726,9 @@ __global__ void pairs_init_kernel(int mode, int64_t rows, int64_t rb, int has_di
     if (mode != kFill) {
       counts[r] = has_diag;
     } else {
-      cursor[r] = has_diag;
+      const int64_t p = rp[r] - rp[0];
+      cursor[r] = (unsigned long long)((absolute ? p : 0) + has_diag);
       if (has_diag) {
-        const int64_t p = rp[r] - rp[0];
         pj[p] = (uint32_t)(rb + r);
         pk[p] = 0u;
       }
@@ -734,12 +736,14 @@ __global__ void pairs_init_kernel(int mode, int64_t rows, int64_t rb, int has_di
   }
 }
 
-// records -> sort keys grouped by row (each pair in both of its rows)
+// records -> sort keys grouped by row (each pair in both of its rows); the
+// cursors hold each row's next free position, and no write passes the end
+// of the list
 __global__ void pairs_scatter_kernel(PairScratch sc, int64_t rb, int64_t re, const int64_t* __restrict__ rp,
-                                     int32_t* __restrict__ cursor, int32_t* __restrict__ status) {
+                                     unsigned long long* __restrict__ cursor, int32_t* __restrict__ status) {
   if (*(volatile const int32_t*)status & kStatusCapacity) return;
   const int64_t n_rec = *sc.cursor < sc.max_rec ? *sc.cursor : sc.max_rec;
-  const int64_t p0 = rp[0];
+  const uint64_t total = (uint64_t)(rp[re - rb] - rp[0]);
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_rec; q += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t ri = sc.rec_i[q];
     if (ri == kNoRecord) continue;
@@ -749,10 +753,8 @@ __global__ void pairs_scatter_kernel(PairScratch sc, int64_t rb, int64_t re, con
     for (int side = 0; side < 2; ++side) {
       const int64_t r = (side ? j : i) - rb;
       if (r < 0 || r >= re - rb) continue;
-      const int64_t a = rp[r] - p0;
-      const int64_t len = rp[r + 1] - p0 - a;
-      const int64_t c = atomicAdd(cursor + r, 1);
-      if (c < len) sc.keys[a + c] = ((uint64_t)(side ? i : j) << 32) | k;
+      const unsigned long long pos = atomicAdd(cursor + r, 1ull);
+      if (pos < total) sc.keys[pos] = ((uint64_t)(side ? i : j) << 32) | k;
       else atomicOr(status, kStatusLimit);
     }
   }
@@ -790,71 +792,54 @@ __device__ __forceinline__ void warp_exclusive_scan_u32(uint32_t* v, int n) {
   }
 }
 
-// One row of n <= 32 S pairs, sorted by a warp.  The keys are spread over
-// 32 S buckets by linear interpolation of the column between the row's
-// smallest and largest; each key takes a slot in its bucket (shared
-// atomics), the buckets' starts come from a scan, and each lane then
-// insertion-sorts its buckets.  Returns false, writing nothing, when the
-// largest bucket holds more than kBucketMax keys (clustered columns): the
-// row then goes to the block sort.
+// One row of n <= kSortWarpMax pairs, sorted by a warp.  The keys are
+// spread over B >= n buckets (B a power of two) by linear interpolation of
+// the column between the row's smallest and largest; a pass counts the
+// buckets, a scan turns the counts into starts, a second pass places each
+// key at its bucket's next slot (shared atomics), and each lane then
+// insertion-sorts its buckets.  Keys are re-read from memory in each pass
+// (the row is in L1), so nothing per key is held in registers.  Returns
+// false, writing nothing, when the largest bucket holds more than kBucketMax
+// keys (clustered columns): the row then goes to the block sort.
 constexpr int kBucketMax = 16;
 
-template <int S>
+__device__ __forceinline__ uint32_t pair_col(const uint64_t* keys, const uint32_t* pj, int64_t e) {
+  return keys ? (uint32_t)(__ldg(keys + e) >> 32) : pj[e];
+}
+
 __device__ __forceinline__ bool warp_sort_row(int64_t a, int n, const uint64_t* keys, uint32_t* pj, uint32_t* pk,
                                               uint32_t* cnt, uint64_t* buf) {
   const int lane = threadIdx.x & 31;
-  constexpr int B = 32 * S;
-  uint64_t v[S];
   uint32_t cmin = 0xFFFFFFFFu, cmax = 0u;
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const int e = s * 32 + lane;
-    v[s] = e < n ? pair_key(keys, pj, pk, a + e) : 0ull;
-    if (e < n) {
-      cmin = min(cmin, (uint32_t)(v[s] >> 32));
-      cmax = max(cmax, (uint32_t)(v[s] >> 32));
-    }
+  for (int e = lane; e < n; e += 32) {
+    const uint32_t c = pair_col(keys, pj, a + e);
+    cmin = min(cmin, c);
+    cmax = max(cmax, c);
   }
   cmin = __reduce_min_sync(kFull, cmin);
   cmax = __reduce_max_sync(kFull, cmax);
+  int B = 32;
+  while (B < n) B <<= 1;
   const uint64_t span = (uint64_t)(cmax - cmin) + 1;
   for (int b = lane; b < B; b += 32) cnt[b] = 0u;
   __syncwarp();
-  uint32_t place[S];  // bucket << 16 | slot in the bucket
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const int e = s * 32 + lane;
-    if (e < n) {
-      const uint32_t bk = (uint32_t)((((v[s] >> 32) - cmin) * (uint64_t)B) / span);
-      place[s] = (bk << 16) | atomicAdd(&cnt[bk], 1u);
-    }
-  }
+  for (int e = lane; e < n; e += 32)
+    atomicAdd(&cnt[(uint32_t)(((uint64_t)(pair_col(keys, pj, a + e) - cmin) * (uint64_t)B) / span)], 1u);
   __syncwarp();
   uint32_t big = 0u;
   for (int b = lane; b < B; b += 32) big = max(big, cnt[b]);
   if (__reduce_max_sync(kFull, big) > kBucketMax) return false;
-  if (B > 32) {
-    warp_exclusive_scan_u32(cnt, B);
-  } else {  // one bucket per lane
-    const uint32_t x = cnt[lane];
-    uint32_t incl = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += t;
-    }
-    cnt[lane] = incl - x;
+  warp_exclusive_scan_u32(cnt, B);
+  __syncwarp();
+  for (int e = lane; e < n; e += 32) {
+    const uint64_t key = pair_key(keys, pj, pk, a + e);
+    const uint32_t bk = (uint32_t)((((key >> 32) - cmin) * (uint64_t)B) / span);
+    buf[atomicAdd(&cnt[bk], 1u)] = key;
   }
   __syncwarp();
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const int e = s * 32 + lane;
-    if (e < n) buf[cnt[place[s] >> 16] + (place[s] & 0xFFFFu)] = v[s];
-  }
-  __syncwarp();
-  for (int b = lane; b < B; b += 32) {
-    const int lo = (int)cnt[b];
-    const int hi = b + 1 < B ? (int)cnt[b + 1] : n;
+  for (int b = lane; b < B; b += 32) {  // bucket b now spans [cnt[b-1], cnt[b])
+    const int lo = b ? (int)cnt[b - 1] : 0;
+    const int hi = (int)cnt[b];
     for (int x = lo + 1; x < hi; ++x) {
       const uint64_t key = buf[x];
       int y = x - 1;
@@ -866,11 +851,7 @@ __device__ __forceinline__ bool warp_sort_row(int64_t a, int n, const uint64_t* 
     }
   }
   __syncwarp();
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const int e = s * 32 + lane;
-    if (e < n) put_pair(pj, pk, a + e, buf[e]);
-  }
+  for (int e = lane; e < n; e += 32) put_pair(pj, pk, a + e, buf[e]);
   __syncwarp();
   return true;
 }
@@ -897,12 +878,7 @@ sort_rows_warp_kernel(const int64_t* __restrict__ rp, int64_t rows, const uint64
     const int64_t a = rp[r] - p0 + has_diag;
     const int64_t n = rp[r + 1] - p0 - a;
     if (n <= 0 || (n == 1 && !keys)) continue;
-    bool done = false;
-    if (n <= 32) done = warp_sort_row<1>(a, (int)n, keys, pj, pk, s_cnt[warp], s_buf[warp]);
-    else if (n <= 64) done = warp_sort_row<2>(a, (int)n, keys, pj, pk, s_cnt[warp], s_buf[warp]);
-    else if (n <= 128) done = warp_sort_row<4>(a, (int)n, keys, pj, pk, s_cnt[warp], s_buf[warp]);
-    else if (n <= 256) done = warp_sort_row<8>(a, (int)n, keys, pj, pk, s_cnt[warp], s_buf[warp]);
-    else if (n <= kSortWarpMax) done = warp_sort_row<16>(a, (int)n, keys, pj, pk, s_cnt[warp], s_buf[warp]);
+    const bool done = n <= kSortWarpMax && warp_sort_row(a, (int)n, keys, pj, pk, s_cnt[warp], s_buf[warp]);
     if (!done && lane == 0) big[atomicAdd(big_count, 1ull)] = (int32_t)r;
   }
 }
@@ -1008,10 +984,10 @@ static cudaError_t launch_sort_rows(const int64_t* rp, int64_t rows, uint64_t* k
 }
 
 static cudaError_t launch_init(int mode, int64_t rows, int64_t rb, int has_diag, int64_t* counts, const int64_t* rp,
-                               int32_t* cursor, uint32_t* pj, uint32_t* pk, int64_t capacity,
-                               const int64_t* overflow, int32_t* status, cudaStream_t s) {
+                               unsigned long long* cursor, int absolute, uint32_t* pj, uint32_t* pk,
+                               int64_t capacity, const int64_t* overflow, int32_t* status, cudaStream_t s) {
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 4 * num_sms()));
-  pairs_init_kernel<<<blocks, 256, 0, s>>>(mode, rows, rb, has_diag, counts, rp, cursor, pj, pk, capacity,
+  pairs_init_kernel<<<blocks, 256, 0, s>>>(mode, rows, rb, has_diag, counts, rp, cursor, absolute, pj, pk, capacity,
                                            overflow, status);
   return cudaGetLastError();
 }
@@ -1024,7 +1000,7 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stag
   const int64_t rows = re - rb;
   auto* ctr = (unsigned long long*)(stage + L.off_counters);
   auto* status = (int32_t*)(stage + offsetof(StageHeader, status));
-  auto* cursor = (int32_t*)(stage + L.off_rowcur);
+  auto* cursor = (unsigned long long*)(stage + L.off_rowcur);
   TermsArgs a;
   std::memset(&a, 0, sizeof(a));
   a.U = U;
@@ -1054,7 +1030,8 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stag
   a.status = status;
   a.item_counter = ctr + kCtrItems;
   cudaError_t e;
-  if ((e = launch_init(mode, rows, rb, ham->has_diag, rp, rp, cursor, pj, pk, -1, nullptr, status, s)) != cudaSuccess)
+  if ((e = launch_init(mode, rows, rb, ham->has_diag, rp, rp, cursor, 0, pj, pk, -1, nullptr, status, s)) !=
+      cudaSuccess)
     return e;
   if (mode == kEmit && (e = cudaMemsetAsync(sc->cursor, 0, 2 * sizeof(int64_t), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(ctr + kCtrItems, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
@@ -1083,9 +1060,9 @@ cudaError_t launch_pairs_compact(const nqs_ham* ham, const PairScratch& sc, char
                                  int64_t rb, int64_t rows, const int64_t* row_ptr, uint32_t* pair_j,
                                  uint32_t* pair_k, int64_t capacity, cudaStream_t s) {
   auto* status = (int32_t*)(stage + offsetof(StageHeader, status));
-  auto* cursor = (int32_t*)(stage + L.off_rowcur);
+  auto* cursor = (unsigned long long*)(stage + L.off_rowcur);
   const int64_t cap = std::min<int64_t>(capacity, sc.max_pairs);
-  cudaError_t e = launch_init(kFill, rows, rb, ham->has_diag, nullptr, row_ptr, cursor, pair_j, pair_k, cap,
+  cudaError_t e = launch_init(kFill, rows, rb, ham->has_diag, nullptr, row_ptr, cursor, 1, pair_j, pair_k, cap,
                               sc.cursor + 1, status, s);
   if (e != cudaSuccess) return e;
   pairs_scatter_kernel<<<8 * num_sms(), 256, 0, s>>>(sc, rb, rb + rows, row_ptr, cursor, status);

@@ -116,10 +116,11 @@ struct StageHeader {
   int32_t pad0;
   int64_t off_trie;     // prefix tree of U (LoopOverTrie)
   int64_t off_hx, off_table, off_bloom, off_scan, off_ampP, off_ampQ, off_ampK, off_geff, off_counters;
+  int64_t off_own;      // adjoint: each row's own terms, double2 [n_unq]
   int64_t off_q;        // per-qubit sample counts and fill cursors: uint32 [2][64 W]
   int64_t off_qrows;    // per-qubit lists of the samples with that bit set: uint32 [n_unq * n_qubits]
   int64_t off_big;      // rows queued for the block sort: int32 [n_unq]
-  int64_t off_rowcur;   // per-row fill cursors: int32 [n_unq]
+  int64_t off_rowcur;   // per-row fill cursors: uint64 [n_unq]
   int64_t off_sched, off_order;   // row schedule of the energy and adjoint kernels
   int64_t scan_blocks;
   int64_t total_bytes;

@@ -282,17 +282,31 @@ __global__ void row_class_count_kernel(const int64_t* __restrict__ rp, int64_t r
   if (threadIdx.x < kRowClasses && h[threadIdx.x]) atomicAdd(cnt + threadIdx.x, h[threadIdx.x]);
 }
 
+// rows to their places in the order, class by class: a block counts its rows
+// per class in shared memory, reserves that many places per class with one
+// global atomic each, then writes its rows (the order inside a class is free)
 __global__ void row_order_kernel(const int64_t* __restrict__ rp, int64_t rows, const uint32_t* __restrict__ cnt,
                                  uint32_t* __restrict__ cursor, int32_t* __restrict__ order) {
   __shared__ uint32_t off[kRowClasses];
+  __shared__ uint32_t local[kRowClasses];
+  if (threadIdx.x < kRowClasses) local[threadIdx.x] = 0u;
+  __syncthreads();
+  const int64_t r0 = blockIdx.x * (int64_t)blockDim.x * 4;
+  const int64_t r1 = r0 + (int64_t)blockDim.x * 4 < rows ? r0 + (int64_t)blockDim.x * 4 : rows;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) atomicAdd(&local[row_class(rp[r + 1] - rp[r])], 1u);
+  __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t run = 0;
-    for (int k = 0; k < kRowClasses; ++k) { off[k] = run; run += cnt[k]; }
+    for (int k = 0; k < kRowClasses; ++k) {
+      off[k] = run + (local[k] ? atomicAdd(cursor + k, local[k]) : 0u);
+      run += cnt[k];
+      local[k] = 0u;
+    }
   }
   __syncthreads();
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
     const int k = row_class(rp[r + 1] - rp[r]);
-    order[off[k] + atomicAdd(cursor + k, 1u)] = (int32_t)r;
+    order[off[k] + atomicAdd(&local[k], 1u)] = (int32_t)r;
   }
 }
 
@@ -319,7 +333,7 @@ static cudaError_t launch_row_order(const int64_t* rp, int64_t rows, char* stage
   if (e != cudaSuccess) return e;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 2 * num_sms()));
   row_class_count_kernel<<<blocks, 256, 0, s>>>(rp, rows, cnt);
-  row_order_kernel<<<blocks, 256, 0, s>>>(rp, rows, cnt, cur, (int32_t*)(stage + L.off_order));
+  row_order_kernel<<<(unsigned)((rows + 1023) / 1024), 256, 0, s>>>(rp, rows, cnt, cur, (int32_t*)(stage + L.off_order));
   return cudaGetLastError();
 }
 

@@ -236,7 +236,7 @@ cudaError_t launch_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, char*
   auto* qrows = (uint32_t*)(stage + L.off_qrows);
   const uint32_t wmask = (uint32_t)(L.nwords - 1);
   const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4 * num_sms());
-  const int qblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 2047) / 2048, 2 * num_sms()));
+  const int qblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * num_sms()));
   const int64_t per_block = (((n + qblocks - 1) / qblocks) + 31) & ~int64_t(31);
 #define NQS_STAGE(WW)                                                                                    \
   case WW:                                                                                               \
@@ -884,16 +884,119 @@ sort_rows_warp_kernel(const int64_t* __restrict__ rp, int64_t rows, const uint64
 }
 
 // Rows longer than kSortWarpMax (or with clustered columns): one block per
-// row, sorted by a bitonic network whose comparators all put the minimum at
-// the lower index: for block sizes k = 2, 4, .., N, first compare i with
-// i XOR (k - 1) (each position of the lower half with its mirror image), then
-// i with i XOR d for d = k/4, .., 1.  In shared memory when the row fits
+// row.  Rows of up to kBlockBucketKeys pairs take the warp sort's bucket
+// method with the whole block; the rest (and rows whose columns cluster)
+// take a bitonic network whose comparators all put the minimum at the lower
+// index: for block sizes k = 2, 4, .., N, first compare i with i XOR (k - 1)
+// (each position of the lower half with its mirror image), then i with
+// i XOR d for d = k/4, .., 1.  In shared memory when the row fits
 // (kSortBlockKeys keys, padded with +infinity), else in place in global
 // memory (the sort keys when given, else pj/pk with the pattern indices moved
 // along); there keys beyond the row's length act as +infinity and, sitting at
 // the higher index of every comparator they take part in, never move, so no
 // padding needs to be stored.
 constexpr int kSortBlockThreads = 1024;
+constexpr int kBlockBucketKeys = kSortBlockKeys / 2;
+
+__device__ __forceinline__ uint32_t block_reduce_u32(uint32_t v, bool take_max, uint32_t* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = take_max ? __reduce_max_sync(kFull, v) : __reduce_min_sync(kFull, v);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = lane < (int)(blockDim.x >> 5) ? sh[lane] : (take_max ? 0u : 0xFFFFFFFFu);
+    t = take_max ? __reduce_max_sync(kFull, t) : __reduce_min_sync(kFull, t);
+    if (lane == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+// exclusive scan of n values in shared memory by the block (each thread a
+// contiguous run of ceil(n / blockDim.x) values)
+__device__ __forceinline__ void block_exclusive_scan_u32(uint32_t* v, int n, uint32_t* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int lo = min((int)threadIdx.x * per, n), hi = min(lo + per, n);
+  uint32_t sum = 0;
+  for (int i = lo; i < hi; ++i) sum += v[i];
+  uint32_t incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  __syncthreads();
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t wt = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0u;
+    uint32_t wi = wt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(kFull, wi, o);
+      if (lane >= o) wi += t;
+    }
+    sh[lane] = wi - wt;
+  }
+  __syncthreads();
+  uint32_t run = sh[warp] + (incl - sum);
+  for (int i = lo; i < hi; ++i) {
+    const uint32_t x = v[i];
+    v[i] = run;
+    run += x;
+  }
+  __syncthreads();
+}
+
+// the warp sort's bucket method with a whole block (n <= kBlockBucketKeys);
+// false (nothing written) when a bucket holds more than kBucketMax keys
+__device__ bool block_sort_row(int64_t a, int n, const uint64_t* keys, uint32_t* pj, uint32_t* pk, uint64_t* out,
+                               uint32_t* cnt, uint32_t* sh) {
+  uint32_t cmin = 0xFFFFFFFFu, cmax = 0u;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const uint32_t c = pair_col(keys, pj, a + e);
+    cmin = min(cmin, c);
+    cmax = max(cmax, c);
+  }
+  cmin = block_reduce_u32(cmin, false, sh);
+  cmax = block_reduce_u32(cmax, true, sh);
+  int B = 32;
+  while (B < n) B <<= 1;
+  const uint64_t span = (uint64_t)(cmax - cmin) + 1;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) cnt[b] = 0u;
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += blockDim.x)
+    atomicAdd(&cnt[(uint32_t)(((uint64_t)(pair_col(keys, pj, a + e) - cmin) * (uint64_t)B) / span)], 1u);
+  __syncthreads();
+  uint32_t big = 0u;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) big = max(big, cnt[b]);
+  if (block_reduce_u32(big, true, sh) > kBucketMax) return false;
+  block_exclusive_scan_u32(cnt, B, sh);
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const uint64_t key = pair_key(keys, pj, pk, a + e);
+    out[atomicAdd(&cnt[(uint32_t)((((key >> 32) - cmin) * (uint64_t)B) / span)], 1u)] = key;
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {  // bucket b now spans [cnt[b-1], cnt[b])
+    const int lo = b ? (int)cnt[b - 1] : 0;
+    const int hi = (int)cnt[b];
+    for (int x = lo + 1; x < hi; ++x) {
+      const uint64_t key = out[x];
+      int y = x - 1;
+      while (y >= lo && out[y] > key) {
+        out[y + 1] = out[y];
+        --y;
+      }
+      out[y + 1] = key;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += blockDim.x) put_pair(pj, pk, a + e, out[e]);
+  __syncthreads();
+  return true;
+}
 
 __global__ void __launch_bounds__(kSortBlockThreads)
 sort_rows_block_kernel(const int64_t* __restrict__ rp, uint64_t* __restrict__ keys, uint32_t* __restrict__ pj,
@@ -901,7 +1004,9 @@ sort_rows_block_kernel(const int64_t* __restrict__ rp, uint64_t* __restrict__ ke
                        const unsigned long long* __restrict__ big_count, unsigned long long* __restrict__ big_next,
                        const int32_t* __restrict__ status) {
   if (*(volatile const int32_t*)status & kStatusCapacity) return;
-  extern __shared__ __align__(16) uint64_t sk[];
+  extern __shared__ __align__(16) uint64_t sk[];  // [kSortBlockKeys] keys, then [kBlockBucketKeys] bucket counts
+  uint32_t* scnt = reinterpret_cast<uint32_t*>(sk + kSortBlockKeys);
+  __shared__ uint32_t sh[33];
   __shared__ int64_t s_row;
   const int64_t p0 = rp[0];
   const int64_t n_big = (int64_t)*big_count;
@@ -916,21 +1021,37 @@ sort_rows_block_kernel(const int64_t* __restrict__ rp, uint64_t* __restrict__ ke
     if (r < 0) break;
     const int64_t a = rp[r] - p0 + has_diag;
     const int64_t n = rp[r + 1] - p0 - a;
+    if (n <= kBlockBucketKeys && block_sort_row(a, (int)n, keys, pj, pk, sk, scnt, sh)) continue;
     int64_t N = 1;
     while (N < n) N <<= 1;
-    if (N <= kSortBlockKeys || keys) {
-      uint64_t* v = N <= kSortBlockKeys ? sk : keys + a;  // large rows: the keys in place
-      if (N <= kSortBlockKeys)
-        for (int64_t e = threadIdx.x; e < N; e += blockDim.x) sk[e] = e < n ? pair_key(keys, pj, pk, a + e) : ~0ull;
+    if (N <= kSortBlockKeys) {
+      const int n32 = (int)n, N32 = (int)N;
+      for (int e = threadIdx.x; e < N32; e += blockDim.x) sk[e] = e < n32 ? pair_key(keys, pj, pk, a + e) : ~0ull;
       __syncthreads();
+      for (int k = 2; k <= N32; k <<= 1) {
+        for (int m = k - 1, d = k; d > 1; d >>= 1, m = d >> 1) {
+          // comparator (e, e ^ m) with e the lower index: e has bit hb = highest bit of m clear
+          const int hb = (m == k - 1) ? (k >> 1) : m;
+          for (int c = threadIdx.x; c < N32 / 2; c += blockDim.x) {
+            const int e = ((c & ~(hb - 1)) << 1) | (c & (hb - 1));  // insert a 0 at bit hb
+            const int f = e ^ m;
+            const uint64_t x = sk[e], y = sk[f];
+            if (y < x) { sk[e] = y; sk[f] = x; }
+          }
+          __syncthreads();
+        }
+      }
+      for (int e = threadIdx.x; e < n32; e += blockDim.x) put_pair(pj, pk, a + e, sk[e]);
+      __syncthreads();
+    } else if (keys) {  // in place in the sort keys
+      uint64_t* v = keys + a;
       for (int64_t k = 2; k <= N; k <<= 1) {
         for (int64_t m = k - 1, d = k; d > 1; d >>= 1, m = d >> 1) {
-          // comparator (e, e ^ m) with e the lower index: e has bit hb = highest bit of m clear
           const int64_t hb = (m == k - 1) ? (k >> 1) : m;
           for (int64_t c = threadIdx.x; c < N / 2; c += blockDim.x) {
-            const int64_t e = ((c & ~(hb - 1)) << 1) | (c & (hb - 1));  // insert a 0 at bit hb
+            const int64_t e = ((c & ~(hb - 1)) << 1) | (c & (hb - 1));
             const int64_t f = e ^ m;
-            if (f >= n && v != sk) continue;  // +infinity partner at the higher index: nothing moves
+            if (f >= n) continue;  // +infinity partner at the higher index: nothing moves
             const uint64_t x = v[e], y = v[f];
             if (y < x) { v[e] = y; v[f] = x; }
           }
@@ -975,7 +1096,7 @@ static cudaError_t launch_sort_rows(const int64_t* rp, int64_t rows, uint64_t* k
   sort_rows_warp_kernel<<<blocks, kSortWarpThreads, 0, s>>>(rp, rows, keys, pj, pk, has_diag, big,
                                                             ctr + kCtrBigCount, status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const size_t smem = sizeof(uint64_t) * kSortBlockKeys;
+  const size_t smem = sizeof(uint64_t) * kSortBlockKeys + sizeof(uint32_t) * kBlockBucketKeys;
   e = cudaFuncSetAttribute(sort_rows_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   sort_rows_block_kernel<<<num_sms(), kSortBlockThreads, smem, s>>>(rp, keys, pj, pk, has_diag, big,

@@ -32,7 +32,7 @@ METRIC = "unique-sample E_loc/s at 56 qubits (E_loc^var + E^var + adjoint per st
 UNIT = "samples/s"
 L2_FLUSH_BYTES = 512 << 20
 SEARCH_SOURCE = os.path.join(ROOT, "paper_2408_07625_gb300", "csrc", "k_pairs.cu")
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pairs_terms_fill_h56.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pairs_terms_kernel_h56.md")
 SM_COUNT, LANES_PER_SM, SM_MAX_GHZ = 152, 128, 2.07
 OPS_PER_PROBE = 4  # algorithmic minimum per (sample, XY) probe: hash XOR, filter address, filter load, bit test
 
@@ -108,6 +108,30 @@ def _profile_traffic():
         return None
     cur = hashlib.sha256(open(SEARCH_SOURCE, "rb").read()).hexdigest()
     return float(m.group(1)) if h.group(1) == cur else None
+
+
+def oriented_probes(U, xy, n_qubits):
+    """(sample, pattern) probes of the oriented LoopOverTerms search: every
+    non-diagonal pattern is probed by the samples on the rarer side (bit set
+    or clear) of its highest qubit.  Host-side count from U and the patterns."""
+    U = np.ascontiguousarray(U)
+    n = U.shape[0]
+    W = U.shape[1]
+    occ = np.zeros(64 * W, np.int64)
+    for w in range(W):
+        bits = (U[:, w][:, None] >> np.arange(64, dtype=np.uint64)) & np.uint64(1)
+        occ[64 * w:64 * (w + 1)] = bits.sum(axis=0)
+    side = np.where(2 * occ <= n, occ, n - occ)
+    probes = 0
+    for row in xy:
+        top = -1
+        for w in range(W - 1, -1, -1):
+            if int(row[w]):
+                top = 64 * w + int(row[w]).bit_length() - 1
+                break
+        if top >= 0:
+            probes += int(side[top])
+    return probes
 
 
 def _peaks():
@@ -238,7 +262,9 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    starts, ends, fills = [], [], []
+    nqs.search_time()  # drop any earlier intervals
+    nqs.search_timing(args.schedule == "terms")
+    starts, ends = [], []
     total_pairs = 0
     for it in range(args.steps):
         flush.zero_()
@@ -247,11 +273,12 @@ def run_ours(args):
         er, evar, gr, total_pairs, marks = step(batch, U, a, record=True)
         s1.record(stream)
         starts.append(s0); ends.append(s1)
-        fills.append((marks[1], marks[2]))
         for name, (m0, m1) in zip(ev.keys(), zip(marks[:-1], marks[1:])):
             ev[name].append((m0, m1))
     torch.cuda.synchronize()
     clk = clocks.stop()
+    nqs.search_timing(False)
+    search_ms, search_launches = nqs.search_time()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_ms = float(np.sum(step_ms))
     if ws > 1:
@@ -262,7 +289,6 @@ def run_ours(args):
     ms_per_step = t_ms / args.steps
     value = ws * n * args.steps / (t_ms * 1e-3)
     phases = {k: float(np.mean([m0.elapsed_time(m1) for m0, m1 in v])) for k, v in ev.items()}
-    fill_ms = float(np.mean([m0.elapsed_time(m1) for m0, m1 in fills]))
 
     # e2e: public API with host buffers (H2D of U and log psi, D2H of E_loc, gradient, E^var)
     out_e = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -305,21 +331,29 @@ def run_ours(args):
            "abs_dE_var": abs(float(r64["evar"][0].item()) - float(r32["evar"][0].item())),
            "E_var_fp64": float(r64["evar"][0].item())}
 
-    # roofline of the dominant kernel: the LoopOverTerms search (one launch per fill call)
+    # roofline of the dominant kernel: the LoopOverTerms search (one launch per step)
     info = ham.info
-    probes = n * (info["n_xy"] - info["has_diag"])
-    achieved = OPS_PER_PROBE * probes / (fill_ms * 1e-3) / 1e12
     peak = SM_COUNT * LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12
-    roof = {"bound": "alu", "kernel": "pairs_terms_kernel (one-pass search, with its scan and compaction)",
-            "achieved": achieved, "peak": peak,
-            "unit": "Tops/s (integer lane-ops; 4 per sample-XY probe)", "frac": achieved / peak,
-            "traffic": _profile_traffic(), "launch_ms": fill_ms,
-            "peak_source": "derived: 152 SMs x 128 lanes x 2.07 GHz"}
-
-    # library kernels per step: pairs phase, then amplitudes + row order (2) + E_loc^var, E^var
-    # (+ combination across ranks), amplitudes + adjoint weights + row order (2) + adjoint
-    pairs_kernels = {"terms": 1 + 1 + 2 + 3 + 1, "batch": 1 + 1 + 3 + 1,
-                     "trie": 1 + 3 * ((inst.n_qubits + 7) // 8) + 7 + 1 + 3 + 1}[args.schedule]
+    if search_launches > 0:
+        xy = ham.export()[0]
+        probes = oriented_probes(inst.U, xy, inst.n_qubits)
+        launch_ms = search_ms / search_launches
+        achieved = OPS_PER_PROBE * probes / (launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "pairs_terms_kernel (oriented LoopOverTerms search)",
+                "achieved": achieved, "peak": peak,
+                "unit": "Tops/s (integer lane-ops; 4 per sample-pattern probe)", "frac": achieved / peak,
+                "traffic": _profile_traffic(), "launch_ms": launch_ms, "probes_per_launch": probes,
+                "launches_timed": search_launches,
+                "peak_source": "derived: 152 SMs x 128 lanes x 2.07 GHz (max SM clock)"}
+    else:
+        roof = None
+    # library kernels per step: staging (hash table and filter, per-qubit lists), the pairs phase
+    # (terms: count init, search, 3-kernel scan, row init, scatter, warp and block row sorts;
+    # batch: count, scan, fill; trie: tree build, count, scan, fill), then amplitudes + row order (2)
+    # + E_loc^var, E^var (+ combination across ranks), amplitudes + adjoint weights + row order (2)
+    # + adjoint
+    pairs_kernels = {"terms": 2 + 1 + 1 + 3 + 1 + 1 + 2, "batch": 2 + 1 + 3 + 1,
+                     "trie": 2 + 3 * ((inst.n_qubits + 7) // 8) + 7 + 1 + 3 + 1}[args.schedule]
     kernels_per_step = pairs_kernels + 4 + 1 + (1 if ws > 1 else 0) + 5
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,

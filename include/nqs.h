@@ -340,6 +340,16 @@ int nqs_batch_free(nqs_plan* plan);
 const char* nqs_last_error(void);   /* thread-local message of the last error */
 int nqs_version(void);              /* NQS_VERSION                               */
 
+/* Timing of the LoopOverTerms search kernel, for benchmarks.  While enabled
+ * (on != 0), every launch of that kernel is bracketed by two CUDA events
+ * recorded on its stream (no synchronisation, no effect on results).
+ * nqs_search_time waits for the recorded events, returns the summed kernel
+ * time (ms, host) and the number of launches (host), and forgets them.
+ * Process-wide state; leave it disabled while capturing a CUDA graph (the
+ * events would be captured, not recorded).  The paper has no counterpart. */
+int nqs_search_timing(int on);
+int nqs_search_time(double* total_ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

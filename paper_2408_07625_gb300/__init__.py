@@ -80,6 +80,8 @@ def load_library(path: str = None):
         "nqs_evar_combine_host": (_i32, [_vp, _i32, _vp]),
         "nqs_last_error": (ctypes.c_char_p, []),
         "nqs_version": (_i32, []),
+        "nqs_search_timing": (_i32, [_i32]),
+        "nqs_search_time": (_i32, [ctypes.POINTER(ctypes.c_double), _c_i64p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -309,6 +311,19 @@ def coupled_pairs(batch: Batch, row_begin=0, row_end=None, schedule="terms", one
     if reuse:
         return row_ptr, pj[:total], pk[:total]
     return row_ptr, pj[:total].clone(), pk[:total].clone()
+
+
+def search_timing(on: bool):
+    """Bracket every LoopOverTerms search launch with CUDA events (benchmarks)."""
+    _check(load_library().nqs_search_timing(1 if on else 0))
+
+
+def search_time():
+    """(summed kernel ms, launches) of the search launches timed since the last call."""
+    t = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(load_library().nqs_search_time(ctypes.byref(t), ctypes.byref(n)))
+    return t.value, int(n.value)
 
 
 def pair_h_buffer(n_pairs, precision="fp32c", device="cuda"):

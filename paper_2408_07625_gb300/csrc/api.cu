@@ -132,6 +132,18 @@ extern "C" {
 const char* nqs_last_error(void) { return g_error.c_str(); }
 int nqs_version(void) { return NQS_VERSION; }
 
+int nqs_search_timing(int on) {
+  search_timing(on != 0);
+  return NQS_OK;
+}
+
+int nqs_search_time(double* total_ms, int64_t* launches) {
+  if (!total_ms || !launches) return fail(NQS_ERR_ARG, "null argument");
+  cudaError_t e = search_time(total_ms, launches);
+  if (e != cudaSuccess) return cuda_fail(e, "search timing events");
+  return NQS_OK;
+}
+
 int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const uint64_t* z_mask,
                  const double* coef, nqs_ham** out) {
   if (!out) return fail(NQS_ERR_ARG, "out is NULL");

@@ -21,6 +21,9 @@
 // and each row is then sorted by column, so the list of a row (the diagonal
 // pair first, then ascending column index) depends on the row alone.
 #include <cstring>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "device_util.cuh"
 #include "nqs_internal.cuh"
@@ -689,14 +692,61 @@ static size_t search_smem(const StageHeader& L) {
          (size_t)kSearchWarps * (kQueueCap + kXbufCap) * 4;
 }
 
+// Optional timing of the search kernel for benchmarks: while enabled, each
+// launch is bracketed by two CUDA events on its stream; nqs_search_time sums
+// the recorded intervals (waiting for them) and forgets them.
+static std::mutex g_timing_mu;
+static bool g_timing_on = false;
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_timing_events;
+
 template <int W, int MODE>
 static cudaError_t launch_terms_w(const TermsArgs& args, const StageHeader& L, cudaStream_t s) {
   auto kern = pairs_terms_kernel<W, MODE>;
   const size_t smem = search_smem<W>(L);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  {
+    std::lock_guard<std::mutex> lock(g_timing_mu);
+    if (g_timing_on && cudaEventCreate(&ev.first) == cudaSuccess && cudaEventCreate(&ev.second) == cudaSuccess) {
+      cudaEventRecord(ev.first, s);
+    } else if (ev.first) {
+      cudaEventDestroy(ev.first);
+      ev.first = nullptr;
+    }
+  }
   kern<<<num_sms(), kSearchThreads, smem, s>>>(args);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (ev.first) {
+    cudaEventRecord(ev.second, s);
+    std::lock_guard<std::mutex> lock(g_timing_mu);
+    g_timing_events.push_back(ev);
+  }
+  return e;
+}
+
+void search_timing(bool on) {
+  std::lock_guard<std::mutex> lock(g_timing_mu);
+  g_timing_on = on;
+}
+
+cudaError_t search_time(double* total_ms, int64_t* launches) {
+  std::lock_guard<std::mutex> lock(g_timing_mu);
+  double t = 0.0;
+  cudaError_t err = cudaSuccess;
+  for (auto& ev : g_timing_events) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(ev.second);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.first, ev.second);
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+    t += ms;
+    cudaEventDestroy(ev.first);
+    cudaEventDestroy(ev.second);
+  }
+  *launches = (int64_t)g_timing_events.size();
+  g_timing_events.clear();
+  *total_ms = t;
+  return err;
 }
 
 // --------------------------------------------------------------------------

@@ -191,6 +191,10 @@ cudaError_t launch_pairs_trie(const nqs_ham* ham, const uint64_t* U, int64_t n, 
 cudaError_t launch_scan(int64_t* data, int64_t n, char* stage, const StageHeader& L,
                         cudaStream_t s);
 
+// benchmark timing of the LoopOverTerms search kernel (nqs_search_timing)
+void search_timing(bool on);
+cudaError_t search_time(double* total_ms, int64_t* launches);
+
 cudaError_t launch_amplitudes(const double* a, const double* b, int64_t n, int precision,
                               char* stage, const StageHeader& L, cudaStream_t s);
 

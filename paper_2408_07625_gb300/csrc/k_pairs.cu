@@ -265,7 +265,7 @@ cudaError_t launch_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, char*
 // warp's last chunk is marked with i = kNoRecord
 // --------------------------------------------------------------------------
 static inline int64_t a256(int64_t v) { return (v + 255) & ~int64_t(255); }
-constexpr int kSearchThreads = 1024;
+constexpr int kSearchThreads = 512;
 constexpr int kSearchWarps = kSearchThreads / 32;
 constexpr int kRecChunk = 128;
 constexpr uint32_t kNoRecord = 0xFFFFFFFFu;
@@ -312,6 +312,7 @@ constexpr int R = kRowsPerWarp;
 constexpr int kMaxSegs = 64 * kMaxWords;
 constexpr int kItemsPerGrab = 4;   // work items a warp takes per atomic
 constexpr int kGroupsPerItem = 16; // search-table groups per work item (bounds an item's length)
+constexpr int kCandCap = 256;      // per-warp queue of filter survivors (sample, slot)
 
 struct TermsArgs {
   const uint64_t* U;
@@ -343,10 +344,8 @@ struct TermsArgs {
 
 template <int W>
 struct RowCache {   // per-warp copy of the item's rows (shared memory)
-  uint64_t u[R][W];
   uint32_t hx[R];
-  uint32_t cnt[R];
-  int64_t row[R];
+  int32_t row[R];
 };
 
 // Place one pair in row r (relative to the range) at the row's next free
@@ -370,13 +369,12 @@ struct RecState {  // warp-uniform: current record chunk (base < 0: none) and it
   int fill;
 };
 
-// One round of verified candidates (lane order).  The pair (i, j) with
-// i = the item's row r is listed in row i and in row j.
-template <int MODE, int W>
-__device__ __forceinline__ void emit_found(bool found, int r, uint32_t j, uint32_t id, RowCache<W>* rc,
-                                           RecState& rs, const TermsArgs& a) {
+// One round of verified candidates (lane order).  The pair (i, j) is listed
+// in row i and in row j.
+template <int MODE>
+__device__ __forceinline__ void emit_found(bool found, int64_t i, uint32_t j, uint32_t id, RecState& rs,
+                                           const TermsArgs& a) {
   const int lane = threadIdx.x & 31;
-  const int64_t i = found ? rc->row[r] : -1;
   const bool in_i = found && i >= a.row_begin && i < a.row_end;
   const bool in_j = found && (int64_t)j >= a.row_begin && (int64_t)j < a.row_end;
   if (MODE == kFill) {
@@ -384,7 +382,7 @@ __device__ __forceinline__ void emit_found(bool found, int r, uint32_t j, uint32
     if (in_j) place_pair(a.rp, (int64_t)j - a.row_begin, a.cursor, a.pair_j, a.pair_k, (uint32_t)i, id, a.status);
     return;
   }
-  if (in_i) atomicAdd(&rc->cnt[r], 1u);
+  if (in_i) atomicAdd((unsigned long long*)(a.counts + (i - a.row_begin)), 1ull);
   if (in_j) atomicAdd((unsigned long long*)(a.counts + ((int64_t)j - a.row_begin)), 1ull);
   if (MODE == kEmit) {
     const bool keep = in_i || in_j;
@@ -417,27 +415,15 @@ __device__ __forceinline__ void emit_found(bool found, int r, uint32_t j, uint32
   }
 }
 
-template <int W>
-__device__ __forceinline__ void load_slot(const unsigned long long* sl, unsigned long long (&v)[W + 1]) {
-  if (W == 1) {
-    const ulonglong2 t = __ldg(reinterpret_cast<const ulonglong2*>(sl));
-    v[0] = t.x;
-    v[W] = t.y;
-  } else {
-#pragma unroll
-    for (int w = 0; w <= W; ++w) v[w] = __ldg(sl + w);
-  }
-}
-
-// Exact membership of x' = x_r XOR XY(pos) in the bucket chain starting at
+// Exact membership of x' = x XOR XY(pos) in the bucket chain starting at
 // bucket sh (slow path: full buckets, several equal tags).
 template <int W>
-__device__ __noinline__ bool verify_slow(int r, uint32_t pos, uint32_t sh, const RowCache<W>* rc,
-                                         const TermsArgs& a, uint32_t& j) {
+__device__ __noinline__ bool verify_slow(const uint64_t* x, uint32_t pos, uint32_t sh, const TermsArgs& a,
+                                         uint32_t& j) {
   const uint64_t* rec = a.srch_rec + (int64_t)pos * a.rec_words;
   uint64_t key[W];
 #pragma unroll
-  for (int w = 0; w < W; ++w) key[w] = rc->u[r][w] ^ __ldg(rec + 1 + w);
+  for (int w = 0; w < W; ++w) key[w] = x[w] ^ __ldg(rec + 1 + w);
   int64_t b = sh & a.capmask;
   for (int64_t it = 0; it <= a.capmask; ++it) {
     const uint2* bk = reinterpret_cast<const uint2*>(a.table + b * 4);
@@ -457,107 +443,108 @@ __device__ __noinline__ bool verify_slow(int r, uint32_t pos, uint32_t sh, const
   return false;
 }
 
-// Verification of queued candidates: each lane takes two entries at a time
-// (W = 1) so their loads overlap (search record, then hash-table bucket).
-template <int W>
-struct FlushWays { static constexpr int value = W == 1 ? 2 : 1; };
+// Verification of queued candidates (sample i, search slot pos), in two
+// converged phases.  Phase 1 (four candidates per lane in flight): the hash of
+// x' = U_i XOR XY(pos) (one XOR of two stored hashes) picks a bucket of the
+// table of U; candidates with a tag match, or a full bucket, survive into a
+// compact list.  Phase 2 (four survivors per lane): the first tag match is
+// confirmed exactly (almost always the only one); full buckets or several
+// equal tags take the slow path; found pairs are emitted.
+constexpr int kVerifyWays = 4;
+
+// Phase-1 survivors are compacted in place into the queue's consumed entries;
+// beside each, its first tag match (bits 0-30; kNoMatch if none) and bit 31
+// set when several tags match or the bucket is full (slow path).
+struct Survivors {
+  uint32_t jc[kCandCap];
+};
+constexpr uint32_t kNoMatch = 0x7FFFFFFFu;  // no sample has this index (n_unq < 2^31)
 
 template <int W, int MODE>
-__device__ __forceinline__ void verify_items(const uint32_t* q, int qn, RowCache<W>* rc, RecState& rs,
-                                             const TermsArgs& a) {
-  constexpr int kWays = FlushWays<W>::value;
+__device__ __forceinline__ void verify_queue(uint2* q, int qn, Survivors* sv, RecState& rs, const TermsArgs& a) {
   const int lane = threadIdx.x & 31;
-  for (int e0 = 0; e0 < qn; e0 += 32 * kWays) {
-    int r[kWays];
-    uint32_t pos[kWays], s[kWays];
-    uint4 b0[kWays], b1[kWays];
-    bool live[kWays];
+  const uint32_t lt = (1u << lane) - 1u;
+  int ns = 0;
+  for (int e0 = 0; e0 < qn; e0 += 32 * kVerifyWays) {
+    uint32_t row[kVerifyWays], pos[kVerifyWays], sh[kVerifyWays];
+    uint4 b0[kVerifyWays], b1[kVerifyWays];
 #pragma unroll
-    for (int u = 0; u < kWays; ++u) {  // candidate hash, then its bucket
+    for (int u = 0; u < kVerifyWays; ++u) {
       const int e = e0 + u * 32 + lane;
-      live[u] = e < qn;
-      const uint32_t ent = q[live[u] ? e : e0];
-      r[u] = (int)(ent >> 24);
-      pos[u] = ent & 0x00FFFFFFu;
-      s[u] = rc->hx[r[u]] ^ __ldg(a.srch_hash + pos[u]);
-      const uint4* bk = reinterpret_cast<const uint4*>(a.table + (int64_t)(s[u] & a.capmask) * 4);
+      const uint2 ent = q[e < qn ? e : 0];
+      row[u] = ent.x;
+      pos[u] = ent.y;
+      sh[u] = __ldg(a.hx + row[u]) ^ __ldg(a.srch_hash + pos[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kVerifyWays; ++u) {
+      const uint4* bk = reinterpret_cast<const uint4*>(a.table + (int64_t)(sh[u] & a.capmask) * 4);
       b0[u] = __ldg(bk);
       b1[u] = __ldg(bk + 1);
     }
 #pragma unroll
-    for (int u = 0; u < kWays; ++u) {
+    for (int u = 0; u < kVerifyWays; ++u) {
       // tag matches among occupied slots; slots fill in order, so slot 3 occupied = full
-      const uint32_t sh = s[u];
-      const uint32_t mm = (uint32_t)(b0[u].x == sh && b0[u].y != ~0u) | ((uint32_t)(b0[u].z == sh && b0[u].w != ~0u) << 1) |
-                          ((uint32_t)(b1[u].x == sh && b1[u].y != ~0u) << 2) | ((uint32_t)(b1[u].z == sh && b1[u].w != ~0u) << 3);
-      const uint32_t jc = (mm & 1u) ? b0[u].y : (mm & 2u) ? b0[u].w : (mm & 4u) ? b1[u].y : b1[u].w;
+      const uint32_t s = sh[u];
+      const uint32_t mm = (uint32_t)(b0[u].x == s && b0[u].y != ~0u) | ((uint32_t)(b0[u].z == s && b0[u].w != ~0u) << 1) |
+                          ((uint32_t)(b1[u].x == s && b1[u].y != ~0u) << 2) | ((uint32_t)(b1[u].z == s && b1[u].w != ~0u) << 3);
+      const uint32_t jc = mm == 0u ? kNoMatch : (mm & 1u) ? b0[u].y : (mm & 2u) ? b0[u].w : (mm & 4u) ? b1[u].y : b1[u].w;
       const bool full = b1[u].w != ~0u;
-      bool found = false, slow = false;
-      uint32_t j = 0, id = kDummy;
-      if (live[u] && mm) {  // confirm the first match exactly (almost always the only one)
-        const uint64_t* rec = a.srch_rec + (int64_t)pos[u] * a.rec_words;
-        id = (uint32_t)(__ldg(rec) >> 32);
-        bool eq = true;
+      const bool keep = e0 + u * 32 + lane < qn && (mm != 0u || full);
+      const uint32_t m = __ballot_sync(kFull, keep);
+      __syncwarp();  // every lane holds this round's entries before any is overwritten
+      if (keep) {
+        const int o = ns + __popc(m & lt);  // o <= entries consumed so far
+        q[o] = make_uint2(row[u], pos[u]);
+        sv->jc[o] = jc | (((mm & (mm - 1u)) != 0u || full) ? 0x80000000u : 0u);
+      }
+      ns += __popc(m);
+    }
+  }
+  __syncwarp();
+  for (int e0 = 0; e0 < ns; e0 += 32 * kVerifyWays) {
+    uint32_t row[kVerifyWays], pos[kVerifyWays], jc[kVerifyWays], fl[kVerifyWays];
+    uint64_t rec0[kVerifyWays], xy[kVerifyWays][W], x[kVerifyWays][W], uj[kVerifyWays][W];
 #pragma unroll
-        for (int w = 0; w < W; ++w)
-          eq = eq && ((rc->u[r[u]][w] ^ __ldg(rec + 1 + w)) == __ldg(a.U + (int64_t)jc * W + w));
-        found = eq;
-        j = jc;
-        slow = !eq && ((mm & (mm - 1u)) != 0u || full);
-      } else if (live[u] && full) {
-        slow = true;
+    for (int u = 0; u < kVerifyWays; ++u) {
+      const int e = e0 + u * 32 + lane;
+      const int ee = e < ns ? e : 0;
+      const uint2 ent = q[ee];
+      row[u] = ent.x;
+      pos[u] = ent.y;
+      jc[u] = sv->jc[ee] & kNoMatch;
+      fl[u] = sv->jc[ee] >> 31;
+      const uint64_t* rec = a.srch_rec + (int64_t)pos[u] * a.rec_words;
+      rec0[u] = __ldg(rec);
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        xy[u][w] = __ldg(rec + 1 + w);
+        x[u][w] = __ldg(a.U + (int64_t)row[u] * W + w);
+        uj[u][w] = jc[u] != kNoMatch ? __ldg(a.U + (int64_t)jc[u] * W + w) : ~0ull;
       }
-      if (slow) {
-        id = (uint32_t)(__ldg(a.srch_rec + (int64_t)pos[u] * a.rec_words) >> 32);
-        found = verify_slow<W>(r[u], pos[u], sh, rc, a, j);
-      }
+    }
+#pragma unroll
+    for (int u = 0; u < kVerifyWays; ++u) {
+      const bool live = e0 + u * 32 + lane < ns;
+      const uint32_t id = (uint32_t)(rec0[u] >> 32);
+      bool eq = jc[u] != kNoMatch;
+#pragma unroll
+      for (int w = 0; w < W; ++w) eq = eq && ((x[u][w] ^ xy[u][w]) == uj[u][w]);
+      bool found = live && eq;
+      uint32_t j = jc[u];
+      if (live && !eq && fl[u]) found = verify_slow<W>(x[u], pos[u], (uint32_t)__ldg(a.hx + row[u]) ^ (uint32_t)rec0[u], a, j);
       found = found && id != kDummy;  // padding slots carry XY = 0 and never count
-      if (e0 + u * 32 < qn) emit_found<MODE, W>(found, r[u], j, id, rc, rs, a);
+      if (e0 + u * 32 < ns) emit_found<MODE>(found, (int64_t)row[u], j, id, rs, a);
     }
   }
-}
-
-// Queue entries are (row mask << 24 | slot).  Each 32-entry slice is expanded
-// into one (row << 24 | slot) item per set bit; items accumulate in xbuf and
-// are verified in full chunks.
-constexpr int kXbufCap = 384;
-
-template <int W, int MODE>
-__device__ __forceinline__ void flush_queue(const uint32_t* q, int qn, uint32_t* xbuf, RowCache<W>* rc,
-                                            RecState& rs, const TermsArgs& a) {
-  const int lane = threadIdx.x & 31;
-  int xn = 0;
-  for (int c0 = 0; c0 < qn; c0 += 32) {
-    if (xn + 32 * R > kXbufCap) {
-      __syncwarp();
-      verify_items<W, MODE>(xbuf, xn, rc, rs, a);
-      __syncwarp();
-      xn = 0;
-    }
-    const int e = c0 + lane;
-    const uint32_t ent = e < qn ? q[e] : 0u;
-    uint32_t bits = ent >> 24;
-    const uint32_t pos = ent & 0x00FFFFFFu;
-    const int c = __popc(bits);
-    int incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += t;
-    }
-    int at = xn + incl - c;
-    while (bits) {
-      const int b = 31 - __clz(bits);
-      bits &= ~(1u << b);
-      xbuf[at++] = ((uint32_t)(R - 1 - b) << 24) | pos;
-    }
-    xn += __shfl_sync(kFull, incl, 31);
-  }
-  __syncwarp();
-  verify_items<W, MODE>(xbuf, xn, rc, rs, a);
   __syncwarp();
 }
 
+// Oriented LoopOverTerms search kernel.  A warp probes 8 samples of a
+// per-qubit list against up to kGroupsPerItem groups of that qubit's segment;
+// each filter survivor is queued as (sample, slot) in the warp's queue, which
+// is verified in full rounds whenever the next group might not fit, and once
+// more at the end.
 template <int W, int MODE>
 __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const TermsArgs a) {
   if (MODE == kFill && (*(volatile int32_t*)a.status & kStatusCapacity)) return;  // buffers too small
@@ -566,8 +553,8 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
   __shared__ int64_t s_cum[kMaxSegs + 1];
   uint32_t* bloom = smem;
   RowCache<W>* caches = reinterpret_cast<RowCache<W>*>(smem + a.nwords);
-  uint32_t* queue = reinterpret_cast<uint32_t*>(caches + kSearchWarps);
-  uint32_t* xbufs = queue + kSearchWarps * kQueueCap;
+  uint2* queues = reinterpret_cast<uint2*>(caches + kSearchWarps);
+  Survivors* survivors = reinterpret_cast<Survivors*>(queues + kSearchWarps * kCandCap);
   {
     const uint4* src = reinterpret_cast<const uint4*>(a.bloom_g);
     uint4* dst = reinterpret_cast<uint4*>(bloom);
@@ -587,16 +574,19 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  uint32_t* q = queue + warp * kQueueCap;
-  uint32_t* xbuf = xbufs + warp * kXbufCap;
+  uint2* q = queues + warp * kCandCap;
+  Survivors* sv = survivors + warp;
   const uint32_t lt = (1u << lane) - 1u;
   RowCache<W>* rc = caches + warp;
   const int64_t n_items = s_cum[a.n_segs];
   const uint32_t wmask4 = a.wmask << 2;
   const char* bloom_bytes = reinterpret_cast<const char*>(bloom);
   RecState rs{-1, kRecChunk};
+  int qn = 0;
   int cur_seg = -1;
   int64_t cur_batch = -1;
+  uint32_t hr4[R], hr17[R], hr22[R];
+  uint32_t vmask = 0;
   while (true) {
     unsigned long long itu = 0;
     if (lane == 0) itu = atomicAdd(a.item_counter, (unsigned long long)kItemsPerGrab);
@@ -624,26 +614,21 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
         __syncwarp();
         if (lane < R) {
           const bool valid = b0 + lane < count_t;
-          const int64_t row = valid ? (int64_t)__ldg(a.qrows + s_qoff[sg.x] + b0 + lane) : -1;
-#pragma unroll
-          for (int w = 0; w < W; ++w) rc->u[lane][w] = valid ? __ldg(a.U + row * W + w) : 0ull;
+          const int32_t row = valid ? (int32_t)__ldg(a.qrows + s_qoff[sg.x] + b0 + lane) : -1;
           rc->hx[lane] = valid ? __ldg(a.hx + row) : 0u;
-          rc->cnt[lane] = 0u;
           rc->row[lane] = row;
         }
         __syncwarp();
-      }
-      uint32_t hr4[R], hr17[R], hr22[R];
-      uint32_t vmask = 0;
+        vmask = 0;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const uint32_t h = rc->hx[r];
-        hr4[r] = h << 2;
-        hr17[r] = h >> 17;
-        hr22[r] = h >> 22;
-        if (rc->row[r] >= 0) vmask |= 1u << (R - 1 - r);
+        for (int r = 0; r < R; ++r) {
+          const uint32_t h = rc->hx[r];
+          hr4[r] = h << 2;
+          hr17[r] = h >> 17;
+          hr22[r] = h >> 22;
+          if (rc->row[r] >= 0) vmask |= 1u << (R - 1 - r);
+        }
       }
-      int qn = 0;
       uint32_t hk_next = __ldg(a.srch_hash + (uint32_t)(g0 * 32 + lane));
       for (int g = g0; g < g1; ++g) {
         const uint32_t pos = (uint32_t)(g * 32 + lane);
@@ -658,38 +643,42 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
           hm = (hm << 1) | (t & 1u);
         }
         hm &= vmask;
-        const uint32_t bal = __ballot_sync(kFull, hm != 0u);
-        if (bal) {
-          if (hm) q[qn + __popc(bal & lt)] = (hm << 24) | pos;
-          qn += __popc(bal);
-          if (qn > kQueueCap - 32) {
+        if (__ballot_sync(kFull, hm != 0u)) {
+          const int c = __popc(hm);
+          int incl = c;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+          }
+          const int total = __shfl_sync(kFull, incl, 31);
+          if (qn + total > kCandCap) {  // verify the queue first (total <= 32 R = kCandCap fits then)
             __syncwarp();
-            flush_queue<W, MODE>(q, qn, xbuf, rc, rs, a);
+            verify_queue<W, MODE>(q, qn, sv, rs, a);
             __syncwarp();
             qn = 0;
           }
+          int at = qn + incl - c;
+          while (hm) {  // one entry per surviving row, rows of an entry in increasing order
+            const int b = 31 - __clz(hm);
+            hm &= ~(1u << b);
+            q[at++] = make_uint2((uint32_t)rc->row[R - 1 - b], pos);
+          }
+          qn += total;
         }
       }
-      __syncwarp();
-      flush_queue<W, MODE>(q, qn, xbuf, rc, rs, a);
-      __syncwarp();
-      if (MODE != kFill && lane < R) {
-        const int64_t row = rc->row[lane];
-        if (row >= a.row_begin && row < a.row_end && rc->cnt[lane])
-          atomicAdd((unsigned long long*)(a.counts + (row - a.row_begin)), (unsigned long long)rc->cnt[lane]);
-        rc->cnt[lane] = 0u;
-      }
-      __syncwarp();
     }  // items of this grab
   }
+  __syncwarp();
+  verify_queue<W, MODE>(q, qn, sv, rs, a);
   if (MODE == kEmit && rs.base >= 0)  // mark the unused tail of the last chunk
     for (int f = rs.fill + lane; f < kRecChunk; f += 32) a.sc.rec_i[rs.base + f] = kNoRecord;
 }
 
 template <int W>
 static size_t search_smem(const StageHeader& L) {
-  return 4 * (size_t)L.nwords + kSearchWarps * sizeof(RowCache<W>) +
-         (size_t)kSearchWarps * (kQueueCap + kXbufCap) * 4;
+  return 4 * (size_t)L.nwords + kSearchWarps * sizeof(RowCache<W>) + (size_t)kSearchWarps * kCandCap * sizeof(uint2) +
+         kSearchWarps * sizeof(Survivors);
 }
 
 // Optional timing of the search kernel for benchmarks: while enabled, each
@@ -1266,6 +1255,7 @@ struct BatchArgs {
 
 constexpr int kBatchThreads = 512;
 constexpr int kBatchWarps = kBatchThreads / 32;
+constexpr int kXbufCap = 384;  // expanded candidates verified per round
 
 template <int W>
 struct BatchRows {   // per-warp copy of the batch's rows (shared memory)

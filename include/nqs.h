@@ -185,8 +185,10 @@ int64_t nqs_pairs_scratch_bytes(int64_t rows, int64_t max_pairs);
 /* One search pass.  The pairs are written to scratch (device, 256-byte
  * aligned, scratch_bytes from nqs_pairs_scratch_bytes) while the rows are
  * counted, then copied in CSR order to pair_j/pair_k (device uint32,
- * `capacity` entries).  Synchronises the stream (the total is returned in
- * *n_pairs).  If the scratch or `capacity` is too small the call returns
+ * `capacity` entries).  The call waits until the count is known (the total
+ * is returned in *n_pairs); the copy into pair_j/pair_k may still be running
+ * on the stream when it returns (later work on the stream sees it done).
+ * If the scratch or `capacity` is too small the call returns
  * NQS_ERR_CAPACITY with row_ptr and *n_pairs valid and pair_j/pair_k
  * unwritten; nqs_fill_coupled_pairs with the same row_ptr then completes the
  * list.  scratch == NULL selects the two-pass form (count, then fill). */

@@ -635,6 +635,25 @@ int64_t nqs_pairs_scratch_bytes(int64_t rows, int64_t max_pairs) {
   return pair_scratch_bytes(rows, max_pairs);
 }
 
+// Pinned host words that the one-pass search reads its count, overflow flag
+// and header into.  Copies into pinned memory stay asynchronous, so the
+// compaction is queued behind them before the host waits.  One block per host
+// thread, kept for the thread's lifetime (portable across devices).
+namespace {
+struct CountWords {
+  int64_t n_pairs;
+  int64_t overflow;
+  StageHeader hdr;
+};
+struct CountReadback {
+  CountWords* w = nullptr;
+  ~CountReadback() {
+    if (w) cudaFreeHost(w);
+  }
+};
+thread_local CountReadback g_readback;
+}  // namespace
+
 int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work,
                            int64_t rb, int64_t re, int schedule, void* scratch, int64_t scratch_bytes,
                            int64_t* row_ptr, uint32_t* pair_j, uint32_t* pair_k, int64_t capacity,
@@ -660,18 +679,41 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
     return rc ? rc : fail(NQS_ERR_CAPACITY, "scratch too small");
   }
   if ((rc = count_pass(ham, U, n, work, L, rb, re, schedule, row_ptr, &sc, s))) return rc;
-  int64_t overflow = 0;
-  cudaError_t e = cudaMemcpyAsync(n_pairs, row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  // The count, the overflow flag and the status reach the host while the
+  // compaction (enqueued right behind them) runs; the compaction checks on the
+  // device that the pairs fit and writes nothing otherwise.
+  cudaError_t e = cudaSuccess;
+  if (!g_readback.w) {
+    void* h = nullptr;
+    if ((e = cudaHostAlloc(&h, sizeof(CountWords), cudaHostAllocPortable)) != cudaSuccess)
+      return cuda_fail(e, "pinned readback");
+    g_readback.w = (CountWords*)h;
+  }
+  CountWords* cw = g_readback.w;
+  e = cudaMemcpyAsync(&cw->n_pairs, row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&cw->overflow, sc.cursor + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&cw->hdr, work, sizeof(StageHeader), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_fail(e, "count copy");
-  e = cudaMemcpyAsync(&overflow, sc.cursor + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return cuda_fail(e, "flag copy");
-  if ((rc = read_status(work, s))) return rc;
+  cudaEvent_t counted;
+  if ((e = cudaEventCreateWithFlags(&counted, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "event");
+  e = cudaEventRecord(counted, s);
+  const bool arrays = pair_j && pair_k;
+  if (e == cudaSuccess && rows > 0)
+    e = launch_pairs_compact(ham, sc, (char*)work, L, rb, rows, row_ptr, pair_j, pair_k, arrays ? capacity : 0, s);
+  const cudaError_t es = cudaEventSynchronize(counted);
+  cudaEventDestroy(counted);
+  if (e != cudaSuccess) return cuda_fail(e, "compaction kernel");
+  if (es != cudaSuccess) return cuda_fail(es, "stream synchronize");
+  *n_pairs = cw->n_pairs;
+  const int64_t overflow = cw->overflow;
+  if (cw->hdr.magic != kStageMagic) return fail(NQS_ERR_ARG, "workspace was not staged");
+  if ((rc = status_to_code(cw->hdr.status))) return rc;
+  const bool fits = !overflow && *n_pairs <= sc.max_pairs && *n_pairs <= (arrays ? capacity : 0);
+  if (!fits && rows > 0 && (e = launch_clear_capacity((char*)work, s)) != cudaSuccess)
+    return cuda_fail(e, "status reset");
   if (overflow || *n_pairs > sc.max_pairs) return fail(NQS_ERR_CAPACITY, "scratch too small for the pairs found");
   if (*n_pairs > capacity) return fail(NQS_ERR_CAPACITY, "pair capacity too small");
-  if (rows == 0 || *n_pairs == 0) return NQS_OK;
-  if (!pair_j || !pair_k) return fail(NQS_ERR_ARG, "null pair arrays");
-  e = launch_pairs_compact(ham, sc, (char*)work, L, rb, rows, row_ptr, pair_j, pair_k, capacity, s);
-  if (e != cudaSuccess) return cuda_fail(e, "compaction kernel");
+  if (*n_pairs > 0 && !arrays) return fail(NQS_ERR_ARG, "null pair arrays");
   return NQS_OK;
 }
 

@@ -23,12 +23,10 @@ __device__ __forceinline__ uint32_t parity_and(const uint64_t (&x)[W], const uin
   return __popc((uint32_t)t ^ (uint32_t)(t >> 32)) & 1u;
 }
 
-// two bits of a 32-bit blocked Bloom word per key, taken from hash bits 17.. and 22..
+// three bits of a 32-bit blocked Bloom word per key, taken from hash bits
+// 17.., 22.. and 27.. (the word itself from the low bits)
 __device__ __forceinline__ uint32_t bloom_bits(uint32_t h) {
-  return (1u << ((h >> 17) & 31)) | (1u << ((h >> 22) & 31));
-}
-__device__ __forceinline__ uint32_t bloom_hit(uint32_t w, uint32_t s) {
-  return __funnelshift_r(w, w, s >> 17) & __funnelshift_r(w, w, s >> 22) & 1u;
+  return (1u << ((h >> 17) & 31)) | (1u << ((h >> 22) & 31)) | (1u << (h >> 27));
 }
 
 // --------------------------------------------------------------------------

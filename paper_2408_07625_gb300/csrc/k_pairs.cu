@@ -4,7 +4,7 @@
 // Membership test "x' in U" (Algs. 2A, 2B): a GF(2)-linear 32-bit hash
 // h(v) = XOR_{b in v} R[b] makes the hash of a candidate x' = x XOR XY one XOR
 // of two precomputed values, h(x) ^ h(XY).  A blocked Bloom filter of U (one
-// 32-bit word per key, two bits set) lives in shared memory and rejects most
+// 32-bit word per key, three bits set) lives in shared memory and rejects most
 // candidates; survivors are verified in a bucketed table of U resident in L2:
 // 32-byte buckets of four (hash tag, index) slots, at most one key per bucket
 // on average, so a miss reads one sector; only a tag match reads the sample.
@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
   int qn = 0;
   int cur_seg = -1;
   int64_t cur_batch = -1;
-  uint32_t hr4[R], hr17[R], hr22[R];
+  uint32_t hr4[R], hr17[R], hr22[R], hr27[R];
   uint32_t vmask = 0;
   while (true) {
     unsigned long long itu = 0;
@@ -626,6 +626,7 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
           hr4[r] = h << 2;
           hr17[r] = h >> 17;
           hr22[r] = h >> 22;
+          hr27[r] = h >> 27;
           if (rc->row[r] >= 0) vmask |= 1u << (R - 1 - r);
         }
       }
@@ -634,12 +635,13 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
         const uint32_t pos = (uint32_t)(g * 32 + lane);
         const uint32_t hk = hk_next;
         if (g + 1 < g1) hk_next = __ldg(a.srch_hash + pos + 32);  // next group's hashes in flight
-        const uint32_t hk4 = hk << 2, hk17 = hk >> 17, hk22 = hk >> 22;
+        const uint32_t hk4 = hk << 2, hk17 = hk >> 17, hk22 = hk >> 22, hk27 = hk >> 27;
         uint32_t hm = 0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const uint32_t w = *reinterpret_cast<const uint32_t*>(bloom_bytes + ((hr4[r] ^ hk4) & wmask4));
-          const uint32_t t = __funnelshift_r(w, w, hr17[r] ^ hk17) & __funnelshift_r(w, w, hr22[r] ^ hk22);
+          const uint32_t t = __funnelshift_r(w, w, hr17[r] ^ hk17) & __funnelshift_r(w, w, hr22[r] ^ hk22) &
+                             __funnelshift_r(w, w, hr27[r] ^ hk27);
           hm = (hm << 1) | (t & 1u);
         }
         hm &= vmask;
@@ -777,23 +779,43 @@ __global__ void pairs_init_kernel(int mode, int64_t rows, int64_t rb, int has_di
 
 // records -> sort keys grouped by row (each pair in both of its rows); the
 // cursors hold each row's next free position, and no write passes the end
-// of the list
+// of the list.  A warp's records come from few search rows, so the lanes
+// sharing their first row take their places with one atomic.
 __global__ void pairs_scatter_kernel(PairScratch sc, int64_t rb, int64_t re, const int64_t* __restrict__ rp,
                                      unsigned long long* __restrict__ cursor, int32_t* __restrict__ status) {
   if (*(volatile const int32_t*)status & kStatusCapacity) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
   const int64_t n_rec = *sc.cursor < sc.max_rec ? *sc.cursor : sc.max_rec;
   const uint64_t total = (uint64_t)(rp[re - rb] - rp[0]);
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_rec; q += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t ri = sc.rec_i[q];
-    if (ri == kNoRecord) continue;
-    const int64_t i = ri, j = sc.rec_j[q];
-    const uint64_t k = sc.rec_k[q];
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const int64_t r = (side ? j : i) - rb;
-      if (r < 0 || r >= re - rb) continue;
-      const unsigned long long pos = atomicAdd(cursor + r, 1ull);
-      if (pos < total) sc.keys[pos] = ((uint64_t)(side ? i : j) << 32) | k;
+  const int64_t rows = re - rb;
+  // warp-uniform trip count: q0 is the warp's first record
+  for (int64_t q0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) - lane; q0 < n_rec;
+       q0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = q0 + lane;
+    const uint32_t ri = q < n_rec ? sc.rec_i[q] : kNoRecord;
+    const bool live = ri != kNoRecord;
+    const int64_t i = ri;
+    const int64_t j = live ? (int64_t)sc.rec_j[q] : 0;
+    const uint64_t k = live ? (uint64_t)sc.rec_k[q] : 0;
+    // first row: one atomic per distinct row of the warp
+    const int64_t r0 = i - rb;
+    const bool in0 = live && r0 >= 0 && r0 < rows;
+    const uint32_t peers = __match_any_sync(kFull, in0 ? ri : kNoRecord);
+    const int leader = __ffs(peers) - 1;
+    unsigned long long base = 0;
+    if (in0 && lane == leader) base = atomicAdd(cursor + r0, (unsigned long long)__popc(peers));
+    base = __shfl_sync(kFull, base, leader);
+    if (in0) {
+      const unsigned long long pos = base + __popc(peers & lt);
+      if (pos < total) sc.keys[pos] = ((uint64_t)j << 32) | k;
+      else atomicOr(status, kStatusLimit);
+    }
+    // second row
+    const int64_t r1 = j - rb;
+    if (live && r1 >= 0 && r1 < rows) {
+      const unsigned long long pos = atomicAdd(cursor + r1, 1ull);
+      if (pos < total) sc.keys[pos] = ((uint64_t)i << 32) | k;
       else atomicOr(status, kStatusLimit);
     }
   }
@@ -1214,6 +1236,15 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stag
   }
   if (mode == kFill) return launch_sort_rows(rp, rows, nullptr, pj, pk, ham->has_diag, stage, L, s);
   return cudaSuccess;
+}
+
+__global__ void clear_capacity_kernel(int32_t* status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) atomicAnd(status, ~kStatusCapacity);
+}
+
+cudaError_t launch_clear_capacity(char* stage, cudaStream_t s) {
+  clear_capacity_kernel<<<1, 32, 0, s>>>((int32_t*)(stage + offsetof(StageHeader, status)));
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pairs_compact(const nqs_ham* ham, const PairScratch& sc, char* stage, const StageHeader& L,

@@ -167,6 +167,9 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stag
                                int64_t* counts_or_rowptr, uint32_t* pair_j, uint32_t* pair_k,
                                int mode, const PairScratch* scratch, cudaStream_t s);
 
+// clear the capacity bit of the status word (stream-ordered)
+cudaError_t launch_clear_capacity(char* stage, cudaStream_t s);
+
 // EMIT records -> CSR rows of [row_begin, row_begin + rows), sorted.  If the
 // pairs outgrow `capacity` or the scratch, sets kStatusCapacity and writes nothing.
 cudaError_t launch_pairs_compact(const nqs_ham* ham, const PairScratch& sc, char* stage, const StageHeader& L,

@@ -156,11 +156,22 @@ struct Melem {
   int diag_quad;
   const float2* quad_f;
   const double* quad_d;
+  int64_t n_xy;            // patterns (pair indices k are below it)
+  int64_t n_unq;           // samples of the batch (pair columns j are below it)
 };
 
-static Melem melem_tables(const nqs_ham* h) {
+static Melem melem_tables(const nqs_ham* h, int64_t n_unq) {
   return Melem{h->row_ptr, h->yz, h->coef_f, h->coef, h->has_diag, h->heavy_end, h->fm,
-               h->fv_f, h->fv_d, h->fz, h->diag_quad, h->quad_f, h->quad_d};
+               h->fv_f, h->fv_d, h->fz, h->diag_quad, h->quad_f, h->quad_d, h->n_xy, n_unq};
+}
+
+// A pair's column and pattern index lie in range by construction of the
+// lists; one that does not (a list not built for this batch) is flagged
+// and skipped instead of indexing outside the tables.
+__device__ __forceinline__ bool pair_in_range(const Melem& M, uint32_t j, uint32_t k, int32_t* status) {
+  const bool ok = (int64_t)j < M.n_unq && (int64_t)k < M.n_xy;
+  if (!ok) atomicOr(status, kStatusLimit);
+  return ok;
 }
 
 // The terms [t0, t1) of one pattern summed by the whole warp: lane t adds
@@ -404,8 +415,8 @@ __device__ __forceinline__ void energy_rounds(const uint64_t* __restrict__ U, co
   }
   for (; base < p1; base += 32 * stride) {
     const int64_t q = base + lane;
-    const bool have = q < p1;
     const uint32_t j = jn, k = kn;
+    const bool have = q < p1 && pair_in_range(M, j, k, status);
     if (q + 32 * stride < p1) {
       jn = __ldg(pair_j + q + 32 * stride);
       kn = __ldg(pair_k + q + 32 * stride);
@@ -533,7 +544,7 @@ static void launch_le(const nqs_ham* ham, const uint64_t* U, const char* stage, 
                       const uint32_t* pk, double* er, double* ei, double* hd, void* hpair, cudaStream_t s) {
   auto kern = local_energy_kernel<Pol, W, CPLX, STORE_H>;
   kern<<<grid_for(kern, rs.rows), kEnergyThreads, 0, s>>>(
-      U, melem_tables(ham), stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK), rb, rs, rp,
+      U, melem_tables(ham, L.n_unq), stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK), rb, rs, rp,
       pj, pk, er, ei, hd, hpair, (int32_t*)(stage + offsetof(StageHeader, status)));
 }
 
@@ -811,8 +822,8 @@ __device__ __forceinline__ void backward_rounds(const uint64_t* __restrict__ U, 
   }
   for (; base < p1; base += 32 * stride) {
     const int64_t q = base + lane;
-    const bool have = q < p1;
     const uint32_t j = jn, k = kn;
+    const bool have = q < p1 && pair_in_range(M, j, k, status);
     if (q + 32 * stride < p1) {
       jn = __ldg(pair_j + q + 32 * stride);
       if (!LOAD_H) kn = __ldg(pair_k + q + 32 * stride);
@@ -930,7 +941,7 @@ static void launch_bw(const nqs_ham* ham, const uint64_t* U, char* stage, const 
                       const BwArgs& b, cudaStream_t s) {
   auto kern = backward_pairs_kernel<Pol, W, CPLX, LOAD_H>;
   kern<<<grid_for(kern, rs.rows), kEnergyThreads, 0, s>>>(
-      U, melem_tables(ham), stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK),
+      U, melem_tables(ham, L.n_unq), stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK),
       stage + L.off_geff, rb, rs, rp, pj, pk, b.hpair, b.own, b.gre, b.gim,
       (int32_t*)(stage + offsetof(StageHeader, status)));
 }

@@ -864,12 +864,22 @@ __device__ __forceinline__ void warp_exclusive_scan_u32(uint32_t* v, int n) {
 // keys (clustered columns): the row then goes to the block sort.
 constexpr int kBucketMax = 16;
 
+// Bucket of column c among B buckets spread over [cmin, cmin + span):
+// ((c - cmin) * m) >> 32 with m = floor(B * 2^32 / span), one division per
+// row instead of one per key.  Non-decreasing in c (so concatenated sorted
+// buckets are a sorted row) and below B, since c - cmin < span; the product
+// stays below B * 2^32.
+__device__ __forceinline__ uint64_t bucket_scale(int B, uint64_t span) { return ((uint64_t)B << 32) / span; }
+__device__ __forceinline__ uint32_t bucket_of(uint32_t c, uint32_t cmin, uint64_t m) {
+  return (uint32_t)(((uint64_t)(c - cmin) * m) >> 32);
+}
+
 __device__ __forceinline__ uint32_t pair_col(const uint64_t* keys, const uint32_t* pj, int64_t e) {
   return keys ? (uint32_t)(__ldg(keys + e) >> 32) : pj[e];
 }
 
 __device__ __forceinline__ bool warp_sort_row(int64_t a, int n, const uint64_t* keys, uint32_t* pj, uint32_t* pk,
-                                              uint32_t* cnt, uint64_t* buf) {
+                                              uint32_t* cnt, uint64_t* buf, int32_t* status) {
   const int lane = threadIdx.x & 31;
   uint32_t cmin = 0xFFFFFFFFu, cmax = 0u;
   for (int e = lane; e < n; e += 32) {
@@ -881,11 +891,17 @@ __device__ __forceinline__ bool warp_sort_row(int64_t a, int n, const uint64_t* 
   cmax = __reduce_max_sync(kFull, cmax);
   int B = 32;
   while (B < n) B <<= 1;
-  const uint64_t span = (uint64_t)(cmax - cmin) + 1;
+  const uint64_t m = bucket_scale(B, (uint64_t)(cmax - cmin) + 1);
   for (int b = lane; b < B; b += 32) cnt[b] = 0u;
   __syncwarp();
-  for (int e = lane; e < n; e += 32)
-    atomicAdd(&cnt[(uint32_t)(((uint64_t)(pair_col(keys, pj, a + e) - cmin) * (uint64_t)B) / span)], 1u);
+  // bucket indices below B and places below n hold by construction; a
+  // violation (keys changed under the sort) is flagged and skipped
+  bool bad = false;
+  for (int e = lane; e < n; e += 32) {
+    const uint32_t bk = bucket_of(pair_col(keys, pj, a + e), cmin, m);
+    if (bk < (uint32_t)B) atomicAdd(&cnt[bk], 1u);
+    else bad = true;
+  }
   __syncwarp();
   uint32_t big = 0u;
   for (int b = lane; b < B; b += 32) big = max(big, cnt[b]);
@@ -894,9 +910,12 @@ __device__ __forceinline__ bool warp_sort_row(int64_t a, int n, const uint64_t* 
   __syncwarp();
   for (int e = lane; e < n; e += 32) {
     const uint64_t key = pair_key(keys, pj, pk, a + e);
-    const uint32_t bk = (uint32_t)((((key >> 32) - cmin) * (uint64_t)B) / span);
-    buf[atomicAdd(&cnt[bk], 1u)] = key;
+    const uint32_t bk = bucket_of((uint32_t)(key >> 32), cmin, m);
+    const uint32_t o = bk < (uint32_t)B ? atomicAdd(&cnt[bk], 1u) : (uint32_t)n;
+    if (o < (uint32_t)n) buf[o] = key;
+    else bad = true;
   }
+  if (bad) atomicOr(status, kStatusLimit);
   __syncwarp();
   for (int b = lane; b < B; b += 32) {  // bucket b now spans [cnt[b-1], cnt[b])
     const int lo = b ? (int)cnt[b - 1] : 0;
@@ -927,7 +946,7 @@ constexpr int kSortWarpWarps = kSortWarpThreads / 32;
 __global__ void __launch_bounds__(kSortWarpThreads)
 sort_rows_warp_kernel(const int64_t* __restrict__ rp, int64_t rows, const uint64_t* __restrict__ keys,
                       uint32_t* __restrict__ pj, uint32_t* __restrict__ pk, int has_diag, int32_t* __restrict__ big,
-                      unsigned long long* __restrict__ big_count, const int32_t* __restrict__ status) {
+                      unsigned long long* __restrict__ big_count, int32_t* __restrict__ status) {
   __shared__ uint32_t s_cnt[kSortWarpWarps][kSortWarpMax];
   __shared__ uint64_t s_buf[kSortWarpWarps][kSortWarpMax];
   if (*(volatile const int32_t*)status & kStatusCapacity) return;
@@ -939,7 +958,7 @@ sort_rows_warp_kernel(const int64_t* __restrict__ rp, int64_t rows, const uint64
     const int64_t a = rp[r] - p0 + has_diag;
     const int64_t n = rp[r + 1] - p0 - a;
     if (n <= 0 || (n == 1 && !keys)) continue;
-    const bool done = n <= kSortWarpMax && warp_sort_row(a, (int)n, keys, pj, pk, s_cnt[warp], s_buf[warp]);
+    const bool done = n <= kSortWarpMax && warp_sort_row(a, (int)n, keys, pj, pk, s_cnt[warp], s_buf[warp], status);
     if (!done && lane == 0) big[atomicAdd(big_count, 1ull)] = (int32_t)r;
   }
 }
@@ -1014,7 +1033,7 @@ __device__ __forceinline__ void block_exclusive_scan_u32(uint32_t* v, int n, uin
 // the warp sort's bucket method with a whole block (n <= kBlockBucketKeys);
 // false (nothing written) when a bucket holds more than kBucketMax keys
 __device__ bool block_sort_row(int64_t a, int n, const uint64_t* keys, uint32_t* pj, uint32_t* pk, uint64_t* out,
-                               uint32_t* cnt, uint32_t* sh) {
+                               uint32_t* cnt, uint32_t* sh, int32_t* status) {
   uint32_t cmin = 0xFFFFFFFFu, cmax = 0u;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
     const uint32_t c = pair_col(keys, pj, a + e);
@@ -1025,11 +1044,15 @@ __device__ bool block_sort_row(int64_t a, int n, const uint64_t* keys, uint32_t*
   cmax = block_reduce_u32(cmax, true, sh);
   int B = 32;
   while (B < n) B <<= 1;
-  const uint64_t span = (uint64_t)(cmax - cmin) + 1;
+  const uint64_t m = bucket_scale(B, (uint64_t)(cmax - cmin) + 1);
   for (int b = threadIdx.x; b < B; b += blockDim.x) cnt[b] = 0u;
   __syncthreads();
-  for (int e = threadIdx.x; e < n; e += blockDim.x)
-    atomicAdd(&cnt[(uint32_t)(((uint64_t)(pair_col(keys, pj, a + e) - cmin) * (uint64_t)B) / span)], 1u);
+  bool bad = false;  // as in the warp sort: flagged and skipped
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const uint32_t bk = bucket_of(pair_col(keys, pj, a + e), cmin, m);
+    if (bk < (uint32_t)B) atomicAdd(&cnt[bk], 1u);
+    else bad = true;
+  }
   __syncthreads();
   uint32_t big = 0u;
   for (int b = threadIdx.x; b < B; b += blockDim.x) big = max(big, cnt[b]);
@@ -1037,8 +1060,12 @@ __device__ bool block_sort_row(int64_t a, int n, const uint64_t* keys, uint32_t*
   block_exclusive_scan_u32(cnt, B, sh);
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
     const uint64_t key = pair_key(keys, pj, pk, a + e);
-    out[atomicAdd(&cnt[(uint32_t)((((key >> 32) - cmin) * (uint64_t)B) / span)], 1u)] = key;
+    const uint32_t bk = bucket_of((uint32_t)(key >> 32), cmin, m);
+    const uint32_t o = bk < (uint32_t)B ? atomicAdd(&cnt[bk], 1u) : (uint32_t)n;
+    if (o < (uint32_t)n) out[o] = key;
+    else bad = true;
   }
+  if (bad) atomicOr(status, kStatusLimit);
   __syncthreads();
   for (int b = threadIdx.x; b < B; b += blockDim.x) {  // bucket b now spans [cnt[b-1], cnt[b])
     const int lo = b ? (int)cnt[b - 1] : 0;
@@ -1063,7 +1090,7 @@ __global__ void __launch_bounds__(kSortBlockThreads)
 sort_rows_block_kernel(const int64_t* __restrict__ rp, uint64_t* __restrict__ keys, uint32_t* __restrict__ pj,
                        uint32_t* __restrict__ pk, int has_diag, const int32_t* __restrict__ big,
                        const unsigned long long* __restrict__ big_count, unsigned long long* __restrict__ big_next,
-                       const int32_t* __restrict__ status) {
+                       int32_t* __restrict__ status) {
   if (*(volatile const int32_t*)status & kStatusCapacity) return;
   extern __shared__ __align__(16) uint64_t sk[];  // [kSortBlockKeys] keys, then [kBlockBucketKeys] bucket counts
   uint32_t* scnt = reinterpret_cast<uint32_t*>(sk + kSortBlockKeys);
@@ -1082,7 +1109,7 @@ sort_rows_block_kernel(const int64_t* __restrict__ rp, uint64_t* __restrict__ ke
     if (r < 0) break;
     const int64_t a = rp[r] - p0 + has_diag;
     const int64_t n = rp[r + 1] - p0 - a;
-    if (n <= kBlockBucketKeys && block_sort_row(a, (int)n, keys, pj, pk, sk, scnt, sh)) continue;
+    if (n <= kBlockBucketKeys && block_sort_row(a, (int)n, keys, pj, pk, sk, scnt, sh, status)) continue;
     int64_t N = 1;
     while (N < n) N <<= 1;
     if (N <= kSortBlockKeys) {
@@ -1148,7 +1175,7 @@ sort_rows_block_kernel(const int64_t* __restrict__ rp, uint64_t* __restrict__ ke
 static cudaError_t launch_sort_rows(const int64_t* rp, int64_t rows, uint64_t* keys, uint32_t* pj, uint32_t* pk,
                                     int has_diag, char* stage, const StageHeader& L, cudaStream_t s) {
   auto* ctr = (unsigned long long*)(stage + L.off_counters);
-  auto* status = (const int32_t*)(stage + offsetof(StageHeader, status));
+  auto* status = (int32_t*)(stage + offsetof(StageHeader, status));
   auto* big = (int32_t*)(stage + L.off_big);
   cudaError_t e = cudaMemsetAsync(ctr + kCtrBigCount, 0, 2 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;

@@ -55,9 +55,8 @@ StageHeader stage_layout(const nqs_ham* ham, int64_t n) {
   L.off_bloom = off;  off = align256(off + 4 * L.nwords);
   L.scan_blocks = (n1 + 1023) / 1024 + 1;
   L.off_scan = off;   off = align256(off + 8 * L.scan_blocks);
-  L.off_ampP = off;   off = align256(off + 16 * n1);
-  L.off_ampQ = off;   off = align256(off + 16 * n1);
-  L.off_ampK = off;   off = align256(off + 4 * n1);
+  L.off_ampP = off;   off = align256(off + 32 * n1);  // 32-byte records: factor and exponent
+  L.off_ampQ = off;   off = align256(off + 32 * n1);
   L.off_geff = off;   off = align256(off + 16 * n1);
   L.off_own = off;    off = align256(off + 16 * n1);
   L.off_counters = off; off = align256(off + 256);

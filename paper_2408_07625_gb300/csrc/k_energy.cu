@@ -24,10 +24,23 @@ constexpr int kEnergyWarps = kEnergyThreads / 32;
 // --------------------------------------------------------------------------
 // per-sample amplitude factors
 // --------------------------------------------------------------------------
+// A factor (P or Q, FP32 compensated or FP64, real and imaginary parts) with
+// the sample's power-of-two exponent K in one 32-byte record (one L2
+// sector): a pair's gather of P_j and K_j, or Q_j and K_j, is one request.
+struct __align__(32) AmpF {
+  float4 v;
+  int k;
+  int pad[3];
+};
+struct __align__(32) AmpD {
+  double2 v;
+  int k;
+  int pad[3];
+};
+
 __global__ void amplitudes_kernel(const double* __restrict__ a, const double* __restrict__ b,
-                                  int64_t n, int fp64, float4* __restrict__ Pf,
-                                  float4* __restrict__ Qf, double2* __restrict__ Pd,
-                                  double2* __restrict__ Qd, int* __restrict__ K) {
+                                  int64_t n, int fp64, AmpF* __restrict__ Pf, AmpF* __restrict__ Qf,
+                                  AmpD* __restrict__ Pd, AmpD* __restrict__ Qd) {
   const double kLn2 = 0.6931471805599453094;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -38,15 +51,19 @@ __global__ void amplitudes_kernel(const double* __restrict__ a, const double* __
     if (b) sincos(b[i], &s, &c);
     const double pr = m * c, pi = m * s;
     const double qr = c / m, qi = -s / m;
-    K[i] = (int)k;
+    const int ki = (int)k;
     if (fp64) {
-      Pd[i] = make_double2(pr, pi);
-      Qd[i] = make_double2(qr, qi);
+      Pd[i].v = make_double2(pr, pi);
+      Pd[i].k = ki;
+      Qd[i].v = make_double2(qr, qi);
+      Qd[i].k = ki;
     } else {
       df dpr = df_from_double(pr), dpi = df_from_double(pi);
       df dqr = df_from_double(qr), dqi = df_from_double(qi);
-      Pf[i] = make_float4(dpr.hi, dpr.lo, dpi.hi, dpi.lo);
-      Qf[i] = make_float4(dqr.hi, dqr.lo, dqi.hi, dqi.lo);
+      Pf[i].v = make_float4(dpr.hi, dpr.lo, dpi.hi, dpi.lo);
+      Pf[i].k = ki;
+      Qf[i].v = make_float4(dqr.hi, dqr.lo, dqi.hi, dqi.lo);
+      Qf[i].k = ki;
     }
   }
 }
@@ -57,8 +74,8 @@ cudaError_t launch_amplitudes(const double* a, const double* b, int64_t n, int p
   const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8 * num_sms());
   const bool fp64 = precision == NQS_PREC_FP64;
   amplitudes_kernel<<<blocks, 256, 0, s>>>(
-      a, b, n, fp64 ? 1 : 0, (float4*)(stage + L.off_ampP), (float4*)(stage + L.off_ampQ),
-      (double2*)(stage + L.off_ampP), (double2*)(stage + L.off_ampQ), (int*)(stage + L.off_ampK));
+      a, b, n, fp64 ? 1 : 0, (AmpF*)(stage + L.off_ampP), (AmpF*)(stage + L.off_ampQ),
+      (AmpD*)(stage + L.off_ampP), (AmpD*)(stage + L.off_ampQ));
   return cudaGetLastError();
 }
 
@@ -85,8 +102,15 @@ struct PolicyF {
   __device__ static T warp_sum(T a) { return nqs::warp_sum(df_norm(a)); }
   __device__ static double to_d(T a) { return df_to_double(a); }
   __device__ static T from_d(double v) { return df_from_double(v); }
-  __device__ static void load_amp(const char* P, int64_t i, T& re, T& im) {
-    float4 v = __ldg(reinterpret_cast<const float4*>(P) + i);
+  __device__ static void load_v(const char* G, int64_t i, T& re, T& im) {  // 16-byte (re, im) entries
+    const float4 v = __ldg(reinterpret_cast<const float4*>(G) + i);
+    re = {v.x, v.y};
+    im = {v.z, v.w};
+  }
+  __device__ static void load_amp(const char* P, int64_t i, T& re, T& im, int& k) {
+    const AmpF* r = reinterpret_cast<const AmpF*>(P) + i;
+    const float4 v = __ldg(&r->v);
+    k = __ldg(&r->k);
     re = {v.x, v.y};
     im = {v.z, v.w};
   }
@@ -109,8 +133,15 @@ struct PolicyD {
   __device__ static T warp_sum(T a) { return nqs::warp_sum(a); }
   __device__ static double to_d(T a) { return a; }
   __device__ static T from_d(double v) { return v; }
-  __device__ static void load_amp(const char* P, int64_t i, T& re, T& im) {
-    double2 v = __ldg(reinterpret_cast<const double2*>(P) + i);
+  __device__ static void load_v(const char* G, int64_t i, T& re, T& im) {  // 16-byte (re, im) entries
+    const double2 v = __ldg(reinterpret_cast<const double2*>(G) + i);
+    re = v.x;
+    im = v.y;
+  }
+  __device__ static void load_amp(const char* P, int64_t i, T& re, T& im, int& k) {
+    const AmpD* r = reinterpret_cast<const AmpD*>(P) + i;
+    const double2 v = __ldg(&r->v);
+    k = __ldg(&r->k);
     re = v.x;
     im = v.y;
   }
@@ -118,14 +149,14 @@ struct PolicyD {
 
 // complex ratio psi(num) / psi(den) = P_num Q_den 2^{K_num - K_den}
 template <class Pol, bool CPLX>
-__device__ __forceinline__ void ratio(const char* P, const char* Q, const int* K, int64_t num,
-                                      int64_t den, typename Pol::T& rr, typename Pol::T& ri,
-                                      int32_t* status) {
+__device__ __forceinline__ void ratio(const char* P, const char* Q, int64_t num, int64_t den,
+                                      typename Pol::T& rr, typename Pol::T& ri, int32_t* status) {
   using T = typename Pol::T;
   T pr, pi, qr, qi;
-  Pol::load_amp(P, num, pr, pi);
-  Pol::load_amp(Q, den, qr, qi);
-  int e = __ldg(K + num) - __ldg(K + den);
+  int kn, kd;
+  Pol::load_amp(P, num, pr, pi, kn);
+  Pol::load_amp(Q, den, qr, qi, kd);
+  int e = kn - kd;
   if (e > Pol::kMaxExp || e < -Pol::kMaxExp) {
     atomicOr(status, kStatusRange);
     e = e > 0 ? Pol::kMaxExp : -Pol::kMaxExp;
@@ -401,7 +432,7 @@ template <> struct HStore<PolicyD> {
 // --------------------------------------------------------------------------
 template <class Pol, int W, bool CPLX, bool STORE_H>
 __device__ __forceinline__ void energy_rounds(const uint64_t* __restrict__ U, const Melem& M, const char* P,
-                                              const char* Q, const int* K, int64_t i, int64_t p, int64_t p1,
+                                              const char* Q, int64_t i, int64_t p, int64_t p1,
                                               int64_t first, int64_t stride, const uint32_t* __restrict__ pair_j,
                                               const uint32_t* __restrict__ pair_k, void* hpair, int32_t* status,
                                               typename Pol::T& acc_re, typename Pol::T& acc_im) {
@@ -442,7 +473,7 @@ __device__ __forceinline__ void energy_rounds(const uint64_t* __restrict__ U, co
         h = melem_lane<Pol, W>(xp, k, fm, M);
       }
       T rr, ri;
-      ratio<Pol, CPLX>(P, Q, K, j, i, rr, ri, status);
+      ratio<Pol, CPLX>(P, Q, j, i, rr, ri, status);
       Pol::acc(acc_re, Pol::mul(h, rr));
       if (CPLX) Pol::acc(acc_im, Pol::mul(h, ri));
       if (STORE_H) HStore<Pol>::put(hpair, q, h);
@@ -470,7 +501,7 @@ __device__ __forceinline__ bool energy_diag(const uint64_t* __restrict__ U, cons
 template <class Pol, int W, bool CPLX, bool STORE_H>
 __global__ void __launch_bounds__(kEnergyThreads)
 local_energy_kernel(const uint64_t* __restrict__ U, const Melem M, const char* __restrict__ P,
-                    const char* __restrict__ Q, const int* __restrict__ K, int64_t row_begin, RowSched rs,
+                    const char* __restrict__ Q, int64_t row_begin, RowSched rs,
                     const int64_t* __restrict__ rp, const uint32_t* __restrict__ pair_j,
                     const uint32_t* __restrict__ pair_k, double* __restrict__ eloc_re,
                     double* __restrict__ eloc_im, double* __restrict__ hdiag, void* __restrict__ hpair,
@@ -490,7 +521,7 @@ local_energy_kernel(const uint64_t* __restrict__ U, const Melem M, const char* _
     double hd = 0.0;
     if (warp == 0) energy_diag<Pol, W, STORE_H>(U, M, i, p, p1, pair_k, hpair, acc_re, hd);
     if (M.has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
-    energy_rounds<Pol, W, CPLX, STORE_H>(U, M, P, Q, K, i, p, p1, warp, kEnergyWarps, pair_j, pair_k, hpair,
+    energy_rounds<Pol, W, CPLX, STORE_H>(U, M, P, Q, i, p, p1, warp, kEnergyWarps, pair_j, pair_k, hpair,
                                          status, acc_re, acc_im);
     const T er = Pol::warp_sum(acc_re);
     const T ei = CPLX ? Pol::warp_sum(acc_im) : Pol::zero();
@@ -517,7 +548,7 @@ local_energy_kernel(const uint64_t* __restrict__ U, const Melem M, const char* _
     T acc_re = Pol::zero(), acc_im = Pol::zero();
     double hd = 0.0;
     if (energy_diag<Pol, W, STORE_H>(U, M, i, p, p1, pair_k, hpair, acc_re, hd)) ++p;
-    energy_rounds<Pol, W, CPLX, STORE_H>(U, M, P, Q, K, i, p, p1, 0, 1, pair_j, pair_k, hpair, status, acc_re,
+    energy_rounds<Pol, W, CPLX, STORE_H>(U, M, P, Q, i, p, p1, 0, 1, pair_j, pair_k, hpair, status, acc_re,
                                          acc_im);
     const T er = Pol::warp_sum(acc_re);
     const T ei = CPLX ? Pol::warp_sum(acc_im) : Pol::zero();
@@ -544,7 +575,7 @@ static void launch_le(const nqs_ham* ham, const uint64_t* U, const char* stage, 
                       const uint32_t* pk, double* er, double* ei, double* hd, void* hpair, cudaStream_t s) {
   auto kern = local_energy_kernel<Pol, W, CPLX, STORE_H>;
   kern<<<grid_for(kern, rs.rows), kEnergyThreads, 0, s>>>(
-      U, melem_tables(ham, L.n_unq), stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK), rb, rs, rp,
+      U, melem_tables(ham, L.n_unq), stage + L.off_ampP, stage + L.off_ampQ, rb, rs, rp,
       pj, pk, er, ei, hd, hpair, (int32_t*)(stage + offsetof(StageHeader, status)));
 }
 
@@ -796,7 +827,7 @@ __global__ void backward_closed_kernel(int64_t rb, int64_t re, const double* __r
 
 template <class Pol>
 __device__ __forceinline__ void load_geff(const char* G, int64_t i, typename Pol::T& ge, typename Pol::T& gi) {
-  Pol::load_amp(G, i, ge, gi);
+  Pol::load_v(G, i, ge, gi);
 }
 
 // row y: sum over pairs (y, x), x != y, of ge(x) Re T + gi(x) Im T (and the
@@ -807,7 +838,7 @@ __device__ __forceinline__ void load_geff(const char* G, int64_t i, typename Pol
 // forward computes them, so both forms give the same bits.
 template <class Pol, int W, bool CPLX, bool LOAD_H>
 __device__ __forceinline__ void backward_rounds(const uint64_t* __restrict__ U, const Melem& M, const char* P,
-                                                const char* Q, const int* K, const char* G, int64_t y, int64_t p,
+                                                const char* Q, const char* G, int64_t y, int64_t p,
                                                 int64_t p1, int64_t first, int64_t stride,
                                                 const uint32_t* __restrict__ pair_j,
                                                 const uint32_t* __restrict__ pair_k, const void* hpair,
@@ -853,7 +884,7 @@ __device__ __forceinline__ void backward_rounds(const uint64_t* __restrict__ U, 
     }
     if (have) {
       T rr, ri, ge, gi;
-      ratio<Pol, CPLX>(P, Q, K, y, j, rr, ri, status);
+      ratio<Pol, CPLX>(P, Q, y, j, rr, ri, status);
       load_geff<Pol>(G, j, ge, gi);
       const T tr = Pol::mul(h, rr);
       Pol::acc(da, Pol::mul(ge, tr));
@@ -879,8 +910,7 @@ __device__ __forceinline__ void backward_finish(int64_t y, double sa, double sb,
 template <class Pol, int W, bool CPLX, bool LOAD_H>
 __global__ void __launch_bounds__(kEnergyThreads)
 backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
-                      const char* __restrict__ P, const char* __restrict__ Q,
-                      const int* __restrict__ K, const char* __restrict__ G,
+                      const char* __restrict__ P, const char* __restrict__ Q, const char* __restrict__ G,
                       int64_t row_begin, RowSched rs, const int64_t* __restrict__ rp,
                       const uint32_t* __restrict__ pair_j, const uint32_t* __restrict__ pair_k,
                       const void* __restrict__ hpair, const double2* __restrict__ own,
@@ -898,7 +928,7 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
     const int64_t p1 = rp[row + 1] - rp[0];
     if (M.has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
     T da = Pol::zero(), db = Pol::zero();
-    backward_rounds<Pol, W, CPLX, LOAD_H>(U, M, P, Q, K, G, y, p, p1, warp, kEnergyWarps, pair_j, pair_k, hpair,
+    backward_rounds<Pol, W, CPLX, LOAD_H>(U, M, P, Q, G, y, p, p1, warp, kEnergyWarps, pair_j, pair_k, hpair,
                                           status, da, db);
     da = Pol::warp_sum(da);
     db = CPLX ? Pol::warp_sum(db) : Pol::zero();
@@ -922,7 +952,7 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
     const int64_t p1 = rp[row + 1] - rp[0];
     if (M.has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
     T da = Pol::zero(), db = Pol::zero();
-    backward_rounds<Pol, W, CPLX, LOAD_H>(U, M, P, Q, K, G, y, p, p1, 0, 1, pair_j, pair_k, hpair, status, da, db);
+    backward_rounds<Pol, W, CPLX, LOAD_H>(U, M, P, Q, G, y, p, p1, 0, 1, pair_j, pair_k, hpair, status, da, db);
     const double sa = Pol::to_d(Pol::warp_sum(da));
     const double sb = CPLX ? Pol::to_d(Pol::warp_sum(db)) : 0.0;
     if (lane == 0) backward_finish<CPLX>(y, sa, sb, own, gre, gim);
@@ -941,8 +971,7 @@ static void launch_bw(const nqs_ham* ham, const uint64_t* U, char* stage, const 
                       const BwArgs& b, cudaStream_t s) {
   auto kern = backward_pairs_kernel<Pol, W, CPLX, LOAD_H>;
   kern<<<grid_for(kern, rs.rows), kEnergyThreads, 0, s>>>(
-      U, melem_tables(ham, L.n_unq), stage + L.off_ampP, stage + L.off_ampQ, (const int*)(stage + L.off_ampK),
-      stage + L.off_geff, rb, rs, rp, pj, pk, b.hpair, b.own, b.gre, b.gim,
+      U, melem_tables(ham, L.n_unq), stage + L.off_ampP, stage + L.off_ampQ, stage + L.off_geff, rb, rs, rp, pj, pk, b.hpair, b.own, b.gre, b.gim,
       (int32_t*)(stage + offsetof(StageHeader, status)));
 }
 

@@ -115,7 +115,7 @@ struct StageHeader {
   int32_t trie_ok;      // nonzero once the prefix tree of U is built for this staging
   int32_t pad0;
   int64_t off_trie;     // prefix tree of U (LoopOverTrie)
-  int64_t off_hx, off_table, off_bloom, off_scan, off_ampP, off_ampQ, off_ampK, off_geff, off_counters;
+  int64_t off_hx, off_table, off_bloom, off_scan, off_ampP, off_ampQ, off_geff, off_counters;
   int64_t off_own;      // adjoint: each row's own terms, double2 [n_unq]
   int64_t off_q;        // per-qubit sample counts and fill cursors: uint32 [2][64 W]
   int64_t off_qrows;    // per-qubit lists of the samples with that bit set: uint32 [n_unq * n_qubits]

@@ -32,6 +32,7 @@ METRIC = "unique-sample E_loc/s at 56 qubits (E_loc^var + E^var + adjoint per st
 UNIT = "samples/s"
 L2_FLUSH_BYTES = 512 << 20
 SEARCH_SOURCE = os.path.join(ROOT, "paper_2408_07625_gb300", "csrc", "k_pairs.cu")
+SEARCH_SECTION_END = "// CSR assembly:"  # the search kernel's source ends before this section
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pairs_terms_kernel_h56.md")
 SM_COUNT, LANES_PER_SM, SM_MAX_GHZ = 152, 128, 2.07
 OPS_PER_PROBE = 4  # algorithmic minimum per (sample, XY) probe: hash XOR, filter address, filter load, bit test
@@ -96,6 +97,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def search_source_sha256():
+    """sha256 of the search kernel's source: k_pairs.cu up to its CSR-assembly
+    section (staging, one-pass scratch and the LoopOverTerms search kernel)."""
+    text = open(SEARCH_SOURCE, encoding="utf-8").read()
+    return hashlib.sha256(text[:text.index(SEARCH_SECTION_END)].encode()).hexdigest()
+
+
 def _profile_traffic():
     """Per-launch DRAM bytes of the search kernel from the committed ncu summary,
     or None if absent or taken on a different kernel source."""
@@ -103,11 +111,10 @@ def _profile_traffic():
         return None
     text = open(PROFILE_SUMMARY).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    h = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    h = re.search(r"search_source_sha256:\s*([0-9a-f]+)", text)
     if not m or not h:
         return None
-    cur = hashlib.sha256(open(SEARCH_SOURCE, "rb").read()).hexdigest()
-    return float(m.group(1)) if h.group(1) == cur else None
+    return float(m.group(1)) if h.group(1) == search_source_sha256() else None
 
 
 def oriented_probes(U, xy, n_qubits):

@@ -712,7 +712,9 @@ evar_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ 
 
 cudaError_t launch_variational_energy(int64_t n, const double* a, const double* er, char* work,
                                       double* out, cudaStream_t s) {
-  const int G = (int)std::max<int64_t>(1, std::min<int64_t>((n + 2047) / 2048, std::min(kRedBlocks, num_sms())));
+  // one block per SM once there are 256 samples per SM: the FP64 exp per
+  // sample runs on every SM (FP64 issue is scarce on this part)
+  const int G = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, std::min(kRedBlocks, num_sms())));
   unsigned int* done = (unsigned int*)(work + kRedOffset);
   double* part = (double*)(work + kRedOffset + 256);
   evar_kernel<<<G, kRedThreads, 0, s>>>(n, a, er, done, part, out);

@@ -854,7 +854,7 @@ __device__ __forceinline__ void warp_exclusive_scan_u32(uint32_t* v, int n) {
 }
 
 // One row of n <= kSortWarpMax pairs, sorted by a warp.  The keys are
-// spread over B >= n buckets (B a power of two) by linear interpolation of
+// spread over B >= n / 2 buckets (B a power of two) by linear interpolation of
 // the column between the row's smallest and largest; a pass counts the
 // buckets, a scan turns the counts into starts, a second pass places each
 // key at its bucket's next slot (shared atomics), and each lane then
@@ -863,6 +863,7 @@ __device__ __forceinline__ void warp_exclusive_scan_u32(uint32_t* v, int n) {
 // false, writing nothing, when the largest bucket holds more than kBucketMax
 // keys (clustered columns): the row then goes to the block sort.
 constexpr int kBucketMax = 16;
+constexpr int kSortWarpBuckets = kSortWarpMax / 2;  // buckets of the warp sort: B >= n / 2, B >= 32
 
 // Bucket of column c among B buckets spread over [cmin, cmin + span):
 // ((c - cmin) * m) >> 32 with m = floor(B * 2^32 / span), one division per
@@ -890,7 +891,7 @@ __device__ __forceinline__ bool warp_sort_row(int64_t a, int n, const uint64_t* 
   cmin = __reduce_min_sync(kFull, cmin);
   cmax = __reduce_max_sync(kFull, cmax);
   int B = 32;
-  while (B < n) B <<= 1;
+  while (2 * B < n) B <<= 1;  // about two keys per bucket: B <= kSortWarpBuckets
   const uint64_t m = bucket_scale(B, (uint64_t)(cmax - cmin) + 1);
   for (int b = lane; b < B; b += 32) cnt[b] = 0u;
   __syncwarp();
@@ -947,7 +948,7 @@ __global__ void __launch_bounds__(kSortWarpThreads)
 sort_rows_warp_kernel(const int64_t* __restrict__ rp, int64_t rows, const uint64_t* __restrict__ keys,
                       uint32_t* __restrict__ pj, uint32_t* __restrict__ pk, int has_diag, int32_t* __restrict__ big,
                       unsigned long long* __restrict__ big_count, int32_t* __restrict__ status) {
-  __shared__ uint32_t s_cnt[kSortWarpWarps][kSortWarpMax];
+  __shared__ uint32_t s_cnt[kSortWarpWarps][kSortWarpBuckets];
   __shared__ uint64_t s_buf[kSortWarpWarps][kSortWarpMax];
   if (*(volatile const int32_t*)status & kStatusCapacity) return;
   const int lane = threadIdx.x & 31;

@@ -854,7 +854,7 @@ __device__ __forceinline__ void warp_exclusive_scan_u32(uint32_t* v, int n) {
 }
 
 // One row of n <= kSortWarpMax pairs, sorted by a warp.  The keys are
-// spread over B >= n / 2 buckets (B a power of two) by linear interpolation of
+// spread over B >= n / 4 buckets (B a power of two) by linear interpolation of
 // the column between the row's smallest and largest; a pass counts the
 // buckets, a scan turns the counts into starts, a second pass places each
 // key at its bucket's next slot (shared atomics), and each lane then
@@ -863,7 +863,7 @@ __device__ __forceinline__ void warp_exclusive_scan_u32(uint32_t* v, int n) {
 // false, writing nothing, when the largest bucket holds more than kBucketMax
 // keys (clustered columns): the row then goes to the block sort.
 constexpr int kBucketMax = 16;
-constexpr int kSortWarpBuckets = kSortWarpMax / 2;  // buckets of the warp sort: B >= n / 2, B >= 32
+constexpr int kSortWarpBuckets = kSortWarpMax / 4;  // buckets of the warp sort: B >= n / 2, B >= 32
 
 // Bucket of column c among B buckets spread over [cmin, cmin + span):
 // ((c - cmin) * m) >> 32 with m = floor(B * 2^32 / span), one division per
@@ -891,7 +891,7 @@ __device__ __forceinline__ bool warp_sort_row(int64_t a, int n, const uint64_t* 
   cmin = __reduce_min_sync(kFull, cmin);
   cmax = __reduce_max_sync(kFull, cmax);
   int B = 32;
-  while (2 * B < n) B <<= 1;  // about two keys per bucket: B <= kSortWarpBuckets
+  while (4 * B < n) B <<= 1;  // about four keys per bucket: B <= kSortWarpBuckets
   const uint64_t m = bucket_scale(B, (uint64_t)(cmax - cmin) + 1);
   for (int b = lane; b < B; b += 32) cnt[b] = 0u;
   __syncwarp();
@@ -944,7 +944,7 @@ constexpr int kSortWarpWarps = kSortWarpThreads / 32;
 // with clustered columns, are queued for the block kernel.  The diagonal
 // pair leads its row and is not sorted.  With `keys` the rows are read from
 // the scatter's sort keys; without, pj/pk are sorted in place.
-__global__ void __launch_bounds__(kSortWarpThreads)
+__global__ void __launch_bounds__(kSortWarpThreads, 6)
 sort_rows_warp_kernel(const int64_t* __restrict__ rp, int64_t rows, const uint64_t* __restrict__ keys,
                       uint32_t* __restrict__ pj, uint32_t* __restrict__ pk, int has_diag, int32_t* __restrict__ big,
                       unsigned long long* __restrict__ big_count, int32_t* __restrict__ status) {

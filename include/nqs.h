@@ -59,7 +59,9 @@ enum {
     NQS_ERR_CUDA = -3,         /* a CUDA runtime call failed                        */
     NQS_ERR_CAPACITY = -4,     /* output buffer too small; required size returned  */
     NQS_ERR_DUPLICATE = -5,    /* the sample batch repeats a basis vector           */
-    NQS_ERR_DEVICE_LIMIT = -6, /* a bounded device loop ran out (corrupt input)     */
+    NQS_ERR_DEVICE_LIMIT = -6, /* a bounded device loop ran out, or a device index
+                                  check failed and the access was skipped
+                                  (corrupt input or pair list)                     */
     NQS_ERR_OOM = -7,          /* device allocation inside nqs_ham_load failed      */
     NQS_ERR_RANGE = -8         /* an amplitude ratio leaves the FP32 exponent range */
 };

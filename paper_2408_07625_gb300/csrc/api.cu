@@ -491,7 +491,8 @@ int64_t nqs_stage_bytes(const nqs_ham* ham, int64_t n_unq) {
 static int status_to_code(int st) {
   if (st & kStatusDuplicate) return fail(NQS_ERR_DUPLICATE, "the sample batch repeats a basis vector");
   if (st & kStatusBadBits) return fail(NQS_ERR_ARG, "a sample has bits >= n_qubits");
-  if (st & kStatusLimit) return fail(NQS_ERR_DEVICE_LIMIT, "a bounded device loop ran out");
+  if (st & kStatusLimit)
+    return fail(NQS_ERR_DEVICE_LIMIT, "a bounded device loop ran out or an index check skipped an access");
   if (st & kStatusRange) return fail(NQS_ERR_RANGE, "an amplitude ratio leaves the FP32 range");
   if (st & kStatusCapacity) return fail(NQS_ERR_CAPACITY, "a pair buffer sized at planning time was too small");
   if (st & kStatusNoTrie) return fail(NQS_ERR_ARG, "trie schedule without nqs_stage_trie after nqs_stage");

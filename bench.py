@@ -184,13 +184,18 @@ def run_reference(args):
             ro.row(nxt % inst.n_unq); nxt += 1
     dt = time.time() - t0
     value = args.steps * rows_per_step / dt
+    xm = np.ascontiguousarray(inst.x_mask).reshape(len(inst.x_mask), -1)
+    n_xy = len(np.unique(xm, axis=0))
+    # the same workload description as the GPU arm's line; the oracle runs in FP64 on the host
+    ref_config = _workload_config(inst, {"n_terms": inst.n_terms, "n_xy": n_xy}, schedule="terms",
+                                  precision="fp64")
+    ref_config["l2"] = "host run: no GPU caches involved"
+    ref_config["sample_rows_per_step"] = rows_per_step
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"{inst.name}: {inst.n_qubits} qubits, {inst.n_terms} Pauli terms, "
-                                   f"{inst.n_unq} peaked unique samples",
-                       "sample_rows_per_step": rows_per_step},
+            "config": ref_config,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{rows_per_step} rows of the batch per step (pure Python FP64 oracle, "
                                        "LoopOverTerms per row)"},

@@ -26,6 +26,9 @@ Modules and the passages they follow:
   derivatives with respect to log psi.
 * ``rows`` -- the same quantities for a chosen subset of rows of a large
   batch (LoopOverTerms per row), used for sampled checks at full size.
+* ``candidates`` -- the exact local energy of Eq. (local_energy): the
+  coupled candidates x XOR XY of every sample (inside or outside U),
+  deduplicated over the batch, and the sum over them.
 
 Every function has at least one pin in ``tests/test_oracle_*.py`` that does
 not reuse the oracle's own formula (paper's worked example, dense Kronecker
@@ -42,6 +45,7 @@ from .energy import (matrix_element, matrix_element_all_terms, local_energy_var,
                      variational_energy, energy_gradient_closed_form,
                      local_energy_vjp, forward)
 from .rows import RowOracle
+from .candidates import full_candidates, local_energy_full
 
 __all__ = [
     "PauliTerm", "PreparedHamiltonian", "prepare_hamiltonian", "pauli_matrix_element",
@@ -50,4 +54,5 @@ __all__ = [
     "find_a_in_b_pointers", "prefix_tree_levels",
     "matrix_element", "matrix_element_all_terms", "local_energy_var", "variational_energy",
     "energy_gradient_closed_form", "local_energy_vjp", "forward", "RowOracle",
+    "full_candidates", "local_energy_full",
 ]

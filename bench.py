@@ -33,7 +33,8 @@ UNIT = "samples/s"
 L2_FLUSH_BYTES = 512 << 20
 SEARCH_SOURCE = os.path.join(ROOT, "paper_2408_07625_gb300", "csrc", "k_pairs.cu")
 SEARCH_SECTION_END = "// CSR assembly:"  # the search kernel's source ends before this section
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pairs_terms_kernel_h56.md")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "search_traffic.json")
+GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
 SM_COUNT, LANES_PER_SM, SM_MAX_GHZ = 152, 128, 2.07
 OPS_PER_PROBE = 4  # algorithmic minimum per (sample, XY) probe: hash XOR, filter address, filter load, bit test
 
@@ -105,16 +106,39 @@ def search_source_sha256():
 
 
 def _profile_traffic():
-    """Per-launch DRAM bytes of the search kernel from the committed ncu summary,
-    or None if absent or taken on a different kernel source."""
-    if not os.path.exists(PROFILE_SUMMARY):
+    """Per-launch DRAM bytes of the search kernel from the committed ncu record
+    (profiles/search_traffic.json), or None if absent or taken on a different
+    kernel source."""
+    if not os.path.exists(PROFILE_TRAFFIC):
         return None
-    text = open(PROFILE_SUMMARY).read()
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    h = re.search(r"search_source_sha256:\s*([0-9a-f]+)", text)
-    if not m or not h:
+    rec = json.load(open(PROFILE_TRAFFIC))
+    if rec.get("search_source_sha256") != search_source_sha256():
         return None
-    return float(m.group(1)) if h.group(1) == search_source_sha256() else None
+    return float(rec["traffic_bytes_per_launch"])
+
+
+def algorithmic_bytes(n, W, n_terms, n_xy, n_pairs, upstream=True):
+    """HBM bytes one step must move by the path's data (no re-reads): U, log psi,
+    E_loc (and the adjoint's upstream and gradient), the Hamiltonian tables
+    (XY patterns with a 4-byte term offset, YZ mask and coefficient per term),
+    and the pair list at 12 B per pair (i, j, pattern) written once by
+    FindCoupledPairs and read once by E_loc^var and once by the adjoint."""
+    per_sample = 8 * W + 8 + 8 + (16 if upstream else 0)
+    return {"samples": n * per_sample, "hamiltonian": n_terms * (8 * W + 8) + n_xy * (8 * W + 4),
+            "pairs": 12 * n_pairs * (3 if upstream else 2)}
+
+
+def golden_rows(inst):
+    """The oracle's per-row values for this workload (tests/golden/<name>_rows.npz,
+    written by tests/golden/full_size.py), if stored for exactly this batch."""
+    path = os.path.join(GOLDEN_DIR, f"{inst.name}_rows.npz")
+    if not os.path.exists(path):
+        return None
+    g = np.load(path)
+    sha = hashlib.sha256(np.ascontiguousarray(inst.U).tobytes()).hexdigest()
+    if str(g["u_sha"]) != sha or len(g["eloc"]) != inst.n_unq:
+        return None
+    return g
 
 
 def oriented_probes(U, xy, n_qubits):
@@ -239,8 +263,13 @@ def run_ours(args):
         r0, r1 = row_blocks(rp_all.cpu().numpy(), ws)[rank]
 
     hbuf = [None]  # per-pair matrix elements, kept from E_loc^var for the adjoint
+    # outputs allocated once (every row of the range is written by each call)
+    outs = {"e": (torch.zeros(n, dtype=torch.float64, device=dev), None,
+                  torch.zeros(n, dtype=torch.float64, device=dev)),
+            "g": (torch.zeros(n, dtype=torch.float64, device=dev), None),
+            "v": torch.zeros(3, dtype=torch.float64, device=dev)}
 
-    def step(batch_obj, Udev, adev, record=False):
+    def step(batch_obj, Udev, adev, record=False, prec=prec):
         marks = []
         def mark():
             if record:
@@ -251,17 +280,19 @@ def run_ours(args):
         rp, pj, pk = nqs.coupled_pairs(batch_obj, r0, r1, schedule=args.schedule, reuse=True)
         total = int(pj.numel())
         mark()
-        if hbuf[0] is None or hbuf[0].numel() < (2 if prec == "fp32c" else 1) * total:
+        hdt = torch.float64 if prec == "fp64" else torch.float32
+        if hbuf[0] is None or hbuf[0].dtype != hdt or hbuf[0].numel() < (2 if prec == "fp32c" else 1) * total:
             hbuf[0] = nqs.pair_h_buffer(int(total * 1.1) + 1024, prec, dev)
         hp = hbuf[0][:total] if total > 0 else None
-        er, ei, hd = nqs.local_energy(batch_obj, adev, None, (rp, pj, pk), prec, r0, r1, hpair=hp)
+        er, ei, hd = nqs.local_energy(batch_obj, adev, None, (rp, pj, pk), prec, r0, r1, out=outs["e"],
+                                      hpair=hp)
         mark()
-        evar = nqs.variational_energy(batch_obj, adev[r0:r1], er[r0:r1])
+        evar = nqs.variational_energy(batch_obj, adev[r0:r1], er[r0:r1], out=outs["v"])
         if ws > 1:  # the one exchange: every rank's [E, max, sum] triple
             evar = combine_evar(evar)
         mark()
         gr, gi = nqs.local_energy_backward(batch_obj, adev, None, er, ei, hd, evar, g, None, gE,
-                                           (rp, pj, pk), prec, r0, r1, hpair=hp)
+                                           (rp, pj, pk), prec, r0, r1, out=outs["g"], hpair=hp)
         mark()
         return er, evar, gr, total, marks
 
@@ -302,6 +333,26 @@ def run_ours(args):
     value = ws * n * args.steps / (t_ms * 1e-3)
     phases = {k: float(np.mean([m0.elapsed_time(m1) for m0, m1 in v])) for k, v in ev.items()}
 
+    # the other precision on the same batch, same step, same timing rules
+    other = "fp64" if prec == "fp32c" else "fp32c"
+    for _ in range(3):
+        step(batch, U, a, prec=other)
+    torch.cuda.synchronize()
+    o_ms = []
+    for it in range(args.steps):
+        flush.zero_()
+        s0 = torch.cuda.Event(enable_timing=True); s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        step(batch, U, a, prec=other)
+        s1.record(stream)
+        o_ms.append((s0, s1))
+    torch.cuda.synchronize()
+    other_ms = float(np.mean([s0.elapsed_time(s1) for s0, s1 in o_ms]))
+    if ws > 1:
+        t = torch.tensor([other_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        other_ms = float(t.item())
+
     # e2e: public API with host buffers (H2D of U and log psi, D2H of E_loc, gradient, E^var)
     out_e = torch.empty(n, dtype=torch.float64).pin_memory()
     out_g = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -336,29 +387,59 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return
 
-    # FP32C vs FP64 (untimed)
+    # FP32C vs FP64 (untimed), and both against the oracle's values of every row when stored
     r64 = nqs.evaluate(batch, a, None, "fp64", schedule=args.schedule)
     r32 = nqs.evaluate(batch, a, None, "fp32c", schedule=args.schedule)
-    err = {"max_abs_dE_loc": float((r64["eloc_re"] - r32["eloc_re"]).abs().max().item()),
-           "abs_dE_var": abs(float(r64["evar"][0].item()) - float(r32["evar"][0].item())),
+    err = {"fp32c_vs_fp64_gpu": {"max_abs_dE_loc": float((r64["eloc_re"] - r32["eloc_re"]).abs().max().item()),
+                                 "abs_dE_var": abs(float(r64["evar"][0].item()) - float(r32["evar"][0].item()))},
            "E_var_fp64": float(r64["evar"][0].item())}
+    gold = golden_rows(inst) if (r0, r1) == (0, n) else None
+    if gold is not None:
+        for name, r in (("fp64", r64), ("fp32c", r32)):
+            d = np.abs(r["eloc_re"].cpu().numpy() - gold["eloc"])
+            err[f"{name}_vs_oracle"] = {"max_abs_dE_loc": float(d.max()), "mean_abs_dE_loc": float(d.mean()),
+                                        "abs_dE_var": abs(float(r["evar"][0].item()) - float(gold["evar"][0])),
+                                        "rows": int(len(d))}
+        err["oracle"] = ("FP64 CPU oracle, every row (tests/golden/" + inst.name + "_rows.npz, written by "
+                         "tests/golden/full_size.py)")
+        err["oracle_E_var"] = float(gold["evar"][0])
 
-    # roofline of the dominant kernel: the LoopOverTerms search (one launch per step)
+    # roofline of the dominant kernel: the LoopOverTerms search (one launch per step),
+    # against the integer peak measured on this GPU by the library's microbenchmark
     info = ham.info
-    peak = SM_COUNT * LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12
+    derived = SM_COUNT * LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12
+    alu_peak, loop_peak = nqs.probe_peaks()
     if search_launches > 0:
         xy = ham.export()[0]
         probes = oriented_probes(inst.U, xy, inst.n_qubits)
         launch_ms = search_ms / search_launches
         achieved = OPS_PER_PROBE * probes / (launch_ms * 1e-3) / 1e12
+        peak = alu_peak / 1e12
         roof = {"bound": "alu", "kernel": "pairs_terms_kernel (oriented LoopOverTerms search)",
                 "achieved": achieved, "peak": peak,
                 "unit": "Tops/s (integer lane-ops; 4 per sample-pattern probe)", "frac": achieved / peak,
                 "traffic": _profile_traffic(), "launch_ms": launch_ms, "probes_per_launch": probes,
                 "launches_timed": search_launches,
-                "peak_source": "derived: 152 SMs x 128 lanes x 2.07 GHz (max SM clock)"}
+                "peak_source": "measured: nqs_probe_peaks register-only XOR/AND/funnel-shift mix, "
+                               "152 x 512 threads, CUDA events (derived unit-count figure: "
+                               f"{derived:.1f} Tops/s)",
+                "probe_loop": {"achieved_gprobes_s": probes / (launch_ms * 1e-3) / 1e9,
+                               "peak_gprobes_s": loop_peak / 1e9,
+                               "frac": probes / (launch_ms * 1e-3) / loop_peak,
+                               "peak_source": "measured: the search's filter loop alone (128 KB shared "
+                                              "filter, no survivors), nqs_probe_peaks"}}
     else:
         roof = None
+    peaks, src = _peaks()
+    ab = algorithmic_bytes(r1 - r0, inst.n_words, int(info["n_terms"]), int(info["n_xy"]), total_pairs)
+    ab_total = float(sum(ab.values()))
+    hbm = {"algorithmic_bytes_per_step": ab_total, "parts": ab,
+           "achieved_gbs": ab_total / (ms_per_step * 1e-3) / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
+           "frac": ab_total / (ms_per_step * 1e-3) / 1e9 / peaks.get("hbm_gbs"),
+           "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback",
+           "model": "U, log psi, E_loc, upstream, gradient: (8W + 32) B per sample; Hamiltonian: (8W + 8) B "
+                    "per term + (8W + 4) B per XY pattern; pair list 12 B per pair written once and read "
+                    "twice (E_loc^var, adjoint)"}
     # library kernels per step: staging (hash table and filter, per-qubit lists), the pairs phase
     # (terms: count init, search, 3-kernel scan, row init, scatter, warp and block row sorts;
     # batch: count, scan, fill; trie: tree build, count, scan, fill), then amplitudes + row order (2)
@@ -377,12 +458,12 @@ def run_ours(args):
                            else "one GPU", rows_rank0=[r0, r1]),
             "pairs_per_s": total_pairs / (phases["pairs"] * 1e-3),
             "phases_ms": phases, "precision_error": err,
-            "roofline": roof,
+            f"{other}_ms_per_step": other_ms,
+            f"{other}_value": ws * n / (other_ms * 1e-3),
+            "roofline": roof, "hbm": hbm,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": kernels_per_step * args.steps,
             "clocks": clk}
-    peaks, src = _peaks()
-    line["hbm_peak_gbs"] = {"value": peaks.get("hbm_gbs"), "source": src}
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(inst, seconds=args.cpu_seconds)
     print(json.dumps(line), flush=True)

@@ -244,8 +244,11 @@ int nqs_variational_energy(int64_t n_unq, const double* logpsi_re, const double*
  *   n_unq <= 2097152 (2048 samples for each of the array's 1024 slots);
  *   larger batches return NQS_ERR_CAPACITY and launch nothing.
  * The first call on a device looks up the array's device address (a
- * one-time set-up per device); make that first call before any stream
- * capture.  Every call uses the same array: calls that overlap on the GPU
+ * one-time set-up per device, cached by device index); make that first call
+ * before any stream capture.  `stream` must belong to the current device
+ * (the address is taken for the current device).  The cached addresses do
+ * not survive cudaDeviceReset: a process that resets a device must not call
+ * this entry point again afterwards.  Every call uses the same array: calls that overlap on the GPU
  * (different streams, or different host threads, at the same time) race and
  * corrupt each other's result, so serialise them.  The paper has no
  * counterpart to this entry point.  Asynchronous. */
@@ -353,6 +356,22 @@ int nqs_version(void);              /* NQS_VERSION                              
  * events would be captured, not recorded).  The paper has no counterpart. */
 int nqs_search_timing(int on);
 int nqs_search_time(double* total_ms, int64_t* launches);
+
+/* Measured integer speed of light of the current device, for benchmark
+ * rooflines of the LoopOverTerms search (the paper has no counterpart).
+ * Runs two short kernels at the search kernel's launch shape (one 512-thread
+ * block per SM), each timed with CUDA events on `stream` after a warm-up
+ * launch, and synchronises the stream:
+ *   out[0] = integer lane operations per second of a register-only mix of
+ *            the operations of one filter probe (XOR, AND, 32-bit funnel
+ *            shift, shift-or; counted as source-level operations, sixteen
+ *            independent chains per thread);
+ *   out[1] = probes per second of the search's filter loop by itself: eight
+ *            samples per lane against a stream of pattern hashes, one word
+ *            of a 128 KB shared-memory filter read and three bits tested per
+ *            probe, no survivor handling.
+ * out: host double[2].  Allocates and frees a small device buffer. */
+int nqs_probe_peaks(double* out, void* stream);
 
 #ifdef __cplusplus
 }

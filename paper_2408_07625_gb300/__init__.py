@@ -82,6 +82,7 @@ def load_library(path: str = None):
         "nqs_version": (_i32, []),
         "nqs_search_timing": (_i32, [_i32]),
         "nqs_search_time": (_i32, [ctypes.POINTER(ctypes.c_double), _c_i64p]),
+        "nqs_probe_peaks": (_i32, [ctypes.POINTER(ctypes.c_double), _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -324,6 +325,13 @@ def search_time():
     n = ctypes.c_int64()
     _check(load_library().nqs_search_time(ctypes.byref(t), ctypes.byref(n)))
     return t.value, int(n.value)
+
+
+def probe_peaks(stream=None):
+    """Measured (integer lane-ops/s of the probe ALU mix, filter-loop probes/s) of this GPU."""
+    out = (ctypes.c_double * 2)()
+    _check(load_library().nqs_probe_peaks(out, _stream(stream)))
+    return float(out[0]), float(out[1])
 
 
 def pair_h_buffer(n_pairs, precision="fp32c", device="cuda"):

@@ -143,6 +143,13 @@ int nqs_search_time(double* total_ms, int64_t* launches) {
   return NQS_OK;
 }
 
+int nqs_probe_peaks(double* out, void* stream) {
+  if (!out) return fail(NQS_ERR_ARG, "null argument");
+  cudaError_t e = probe_peaks(out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "integer peak kernels");
+  return NQS_OK;
+}
+
 int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const uint64_t* z_mask,
                  const double* coef, nqs_ham** out) {
   if (!out) return fail(NQS_ERR_ARG, "out is NULL");
@@ -714,6 +721,52 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
   if (overflow || *n_pairs > sc.max_pairs) return fail(NQS_ERR_CAPACITY, "scratch too small for the pairs found");
   if (*n_pairs > capacity) return fail(NQS_ERR_CAPACITY, "pair capacity too small");
   if (*n_pairs > 0 && !arrays) return fail(NQS_ERR_ARG, "null pair arrays");
+  return NQS_OK;
+}
+
+int64_t nqs_candidates_scratch_bytes(const nqs_ham* ham, int64_t n_unq) {
+  if (!ham || n_unq < 0) return fail(NQS_ERR_ARG, "bad argument to nqs_candidates_scratch_bytes");
+  return cand_scratch_bytes(ham, n_unq);
+}
+
+int nqs_full_candidates(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, void* scratch,
+                        int64_t scratch_bytes, uint32_t* cand_id, double* hval, uint64_t* cand,
+                        int32_t* cand_in_u, int64_t capacity, int64_t* n_cand, void* stream) {
+  StageHeader L;
+  int rc = check_work(ham, U, n, work, &L);
+  if (rc) return rc;
+  if (!n_cand) return fail(NQS_ERR_ARG, "null n_cand");
+  *n_cand = 0;
+  if (n == 0 || ham->n_xy == 0) return NQS_OK;
+  if (!scratch || !cand_id) return fail(NQS_ERR_ARG, "null scratch or cand_id");
+  if (((uintptr_t)scratch) & 255) return fail(NQS_ERR_ARG, "scratch not 256-byte aligned");
+  if (n * ham->n_xy > (int64_t(1) << 29)) return fail(NQS_ERR_UNSUPPORTED, "more than 2^29 candidate entries");
+  if (scratch_bytes < cand_scratch_bytes(ham, n)) return fail(NQS_ERR_CAPACITY, "scratch smaller than nqs_candidates_scratch_bytes");
+  int limit = 0;
+  cudaError_t e = launch_full_candidates(ham, U, n, (const char*)work, L, scratch, cand_id, hval, cand, cand_in_u,
+                                         cand ? capacity : 0, n_cand, &limit, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "candidate kernels");
+  if (limit) return fail(NQS_ERR_DEVICE_LIMIT, "candidate table or membership probe ran out");
+  if (!cand || *n_cand > capacity) return fail(NQS_ERR_CAPACITY, "candidate capacity too small");
+  return NQS_OK;
+}
+
+int nqs_local_energy_full(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, const double* a,
+                          const double* b, const uint32_t* cand_id, const double* hval, int64_t n_cand,
+                          const double* ca, const double* cb, void* scratch, int64_t scratch_bytes,
+                          double* eloc_re, double* eloc_im, void* stream) {
+  StageHeader L;
+  int rc = check_work(ham, U, n, work, &L);
+  if (rc) return rc;
+  if (n == 0) return NQS_OK;
+  if (!a || !eloc_re) return fail(NQS_ERR_ARG, "null logpsi_re or eloc_re");
+  if ((b || cb) && !eloc_im) return fail(NQS_ERR_ARG, "complex amplitudes need eloc_im");
+  if (ham->n_xy > 0 && (!cand_id || !hval || !ca || n_cand < 1)) return fail(NQS_ERR_ARG, "null candidate arrays");
+  if (!scratch || scratch_bytes < 32 * std::max<int64_t>(n_cand, 1)) return fail(NQS_ERR_CAPACITY, "scratch too small");
+  if (((uintptr_t)scratch) & 255) return fail(NQS_ERR_ARG, "scratch not 256-byte aligned");
+  cudaError_t e = launch_local_energy_full(n, ham->n_xy, (const char*)work, L, a, b, cand_id, hval, n_cand, ca, cb,
+                                           scratch, eloc_re, eloc_im, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "full local energy kernels");
   return NQS_OK;
 }
 

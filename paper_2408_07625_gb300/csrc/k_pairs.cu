@@ -678,10 +678,11 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
 }
 
 template <int W>
-static size_t search_smem(const StageHeader& L) {
-  return 4 * (size_t)L.nwords + kSearchWarps * sizeof(RowCache<W>) + (size_t)kSearchWarps * kCandCap * sizeof(uint2) +
+static size_t search_smem(int64_t nwords) {
+  return 4 * (size_t)nwords + kSearchWarps * sizeof(RowCache<W>) + (size_t)kSearchWarps * kCandCap * sizeof(uint2) +
          kSearchWarps * sizeof(Survivors);
 }
+constexpr int64_t kMaxBloomWords = 32768;   // stage_layout caps the filter at 128 KB
 
 // Optional timing of the search kernel for benchmarks: while enabled, each
 // launch is bracketed by two CUDA events on its stream; nqs_search_time sums
@@ -693,8 +694,11 @@ static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_timing_events;
 template <int W, int MODE>
 static cudaError_t launch_terms_w(const TermsArgs& args, const StageHeader& L, cudaStream_t s) {
   auto kern = pairs_terms_kernel<W, MODE>;
-  const size_t smem = search_smem<W>(L);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = search_smem<W>(L.nwords);
+  // the attribute is set to the largest size any batch needs, not this launch's: launches of
+  // several batches captured into one graph then all stay within it whatever their order
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)search_smem<W>(kMaxBloomWords));
   if (e != cudaSuccess) return e;
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   {

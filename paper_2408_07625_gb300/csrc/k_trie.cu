@@ -107,13 +107,16 @@ __device__ __forceinline__ uint64_t word_at(const uint64_t (&v)[W], int idx) {
   return r;
 }
 
-template <int W>
+// digit g of a key: byte g of the W-word value, either as is (numeric order,
+// word W-1 most significant) or bit-reversed (qubit order: qubit 8g is the
+// digit's most significant bit)
+template <int W, bool QORDER>
 __device__ __forceinline__ uint32_t sort_digit(const uint64_t (&v)[W], int g) {
   const uint32_t byte = (uint32_t)(word_at<W>(v, g >> 3) >> ((g & 7) * 8)) & 0xFFu;
-  return __brev(byte) >> 24;  // qubit 8g is the digit's most significant bit
+  return QORDER ? __brev(byte) >> 24 : byte;
 }
 
-template <int W>
+template <int W, bool QORDER>
 __global__ void __launch_bounds__(kSortThreads) sort_hist_kernel(const uint64_t* __restrict__ keys, int64_t n,
                                                                  int g, int32_t* __restrict__ hist, int nblk) {
   __shared__ int32_t h[256];
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_hist_kernel(const uint64_t*
     if (e < n) {
       uint64_t v[W];
       load_words<W>(keys + e * W, v);
-      atomicAdd(&h[sort_digit<W>(v, g)], 1);
+      atomicAdd(&h[sort_digit<W, QORDER>(v, g)], 1);
     }
   }
   __syncthreads();
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(1024) sort_scan_kernel(int32_t* __restrict__ d
 
 // Stable scatter: warp w of a block owns keys [t0 + 256 w, t0 + 256 w + 256),
 // visited in rounds of 32; equal digits are ranked by (round, lane).
-template <int W>
+template <int W, bool QORDER>
 __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const uint64_t* __restrict__ kin,
                                                                     const int32_t* __restrict__ iin, int64_t n, int g,
                                                                     const int32_t* __restrict__ hist, int nblk,
@@ -179,7 +182,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const uint64
     if (live) {
       uint64_t v[W];
       load_words<W>(kin + e * W, v);
-      d = sort_digit<W>(v, g);
+      d = sort_digit<W, QORDER>(v, g);
     }
     const uint32_t peers = __match_any_sync(kFull, d);
     const int32_t prior = live ? wcnt[warp][d] : 0;
@@ -361,9 +364,9 @@ static cudaError_t trie_build_w(const nqs_ham* ham, const uint64_t* U, int64_t n
   int cur = 0;
   cudaError_t e;
   for (int g = G - 1; g >= 0; --g) {  // least significant digit (highest qubits) first
-    sort_hist_kernel<W><<<v.nblk, kSortThreads, 0, s>>>(kin, n, g, v.hist, v.nblk);
+    sort_hist_kernel<W, true><<<v.nblk, kSortThreads, 0, s>>>(kin, n, g, v.hist, v.nblk);
     sort_scan_kernel<<<1, 1024, 0, s>>>(v.hist, 256 * (int64_t)v.nblk);
-    sort_scatter_kernel<W><<<v.nblk, kSortThreads, 0, s>>>(kin, iin, n, g, v.hist, v.nblk, v.keys[cur], v.idx[cur]);
+    sort_scatter_kernel<W, true><<<v.nblk, kSortThreads, 0, s>>>(kin, iin, n, g, v.hist, v.nblk, v.keys[cur], v.idx[cur]);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     kin = v.keys[cur];
     iin = v.idx[cur];
@@ -389,6 +392,46 @@ cudaError_t launch_trie_build(const nqs_ham* ham, const uint64_t* U, int64_t n, 
     case 2: return trie_build_w<2>(ham, U, n, stage, L, s);
     case 3: return trie_build_w<3>(ham, U, n, stage, L, s);
     default: return trie_build_w<4>(ham, U, n, stage, L, s);
+  }
+}
+
+// --------------------------------------------------------------------------
+// LSD radix sort of W-word keys in numeric order (word W-1 most significant),
+// with an int32 payload, over the low n_bytes bytes of the keys (the higher
+// ones must be zero): one histogram, scan and stable scatter per byte.
+// Buffers: kbuf[2] of n*W words, ibuf[2] of n ints, hist of 256 * sort_blocks(n)
+// ints.  The result is in kbuf[*out] / ibuf[*out].
+// --------------------------------------------------------------------------
+int64_t sort_blocks(int64_t n) { return (std::max<int64_t>(n, 1) + kSortTile - 1) / kSortTile; }
+
+template <int W>
+static cudaError_t sort_words_w(const uint64_t* kin, const int32_t* iin, int64_t n, int n_bytes, uint64_t* kbuf[2],
+                                int32_t* ibuf[2], int32_t* hist, int* out, cudaStream_t s) {
+  const int nblk = (int)sort_blocks(n);
+  int cur = 0;
+  for (int g = 0; g < n_bytes; ++g) {
+    sort_hist_kernel<W, false><<<nblk, kSortThreads, 0, s>>>(kin, n, g, hist, nblk);
+    sort_scan_kernel<<<1, 1024, 0, s>>>(hist, 256 * (int64_t)nblk);
+    sort_scatter_kernel<W, false><<<nblk, kSortThreads, 0, s>>>(kin, iin, n, g, hist, nblk, kbuf[cur], ibuf[cur]);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    kin = kbuf[cur];
+    iin = ibuf[cur];
+    *out = cur;
+    cur ^= 1;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_sort_words(const uint64_t* kin, const int32_t* iin, int64_t n, int W, int n_bytes,
+                              uint64_t* kbuf[2], int32_t* ibuf[2], int32_t* hist, int* out, cudaStream_t s) {
+  *out = -1;
+  if (n == 0 || n_bytes == 0) return cudaSuccess;
+  switch (W) {
+    case 1: return sort_words_w<1>(kin, iin, n, n_bytes, kbuf, ibuf, hist, out, s);
+    case 2: return sort_words_w<2>(kin, iin, n, n_bytes, kbuf, ibuf, hist, out, s);
+    case 3: return sort_words_w<3>(kin, iin, n, n_bytes, kbuf, ibuf, hist, out, s);
+    default: return sort_words_w<4>(kin, iin, n, n_bytes, kbuf, ibuf, hist, out, s);
   }
 }
 

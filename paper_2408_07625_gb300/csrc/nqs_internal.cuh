@@ -194,9 +194,29 @@ cudaError_t launch_pairs_trie(const nqs_ham* ham, const uint64_t* U, int64_t n, 
 cudaError_t launch_scan(int64_t* data, int64_t n, char* stage, const StageHeader& L,
                         cudaStream_t s);
 
+// LSD radix sort of W-word keys in numeric order with an int32 payload (k_trie.cu)
+int64_t sort_blocks(int64_t n);
+cudaError_t launch_sort_words(const uint64_t* kin, const int32_t* iin, int64_t n, int W, int n_bytes,
+                              uint64_t* kbuf[2], int32_t* ibuf[2], int32_t* hist, int* out, cudaStream_t s);
+
+// exact local energy over the coupled candidates (k_cand.cu)
+int64_t cand_scratch_bytes(const nqs_ham* ham, int64_t n_unq);
+cudaError_t launch_full_candidates(const nqs_ham* ham, const uint64_t* U, int64_t n, const char* stage,
+                                   const StageHeader& L, void* scratch, uint32_t* cand_id, double* hval,
+                                   uint64_t* cand, int32_t* in_u, int64_t capacity, int64_t* n_cand,
+                                   int* limit_hit, cudaStream_t s);
+cudaError_t launch_local_energy_full(int64_t n, int64_t n_xy, const char* stage, const StageHeader& L,
+                                     const double* a, const double* b, const uint32_t* cand_id, const double* hval,
+                                     int64_t n_cand, const double* ca, const double* cb, void* scratch,
+                                     double* er, double* ei, cudaStream_t s);
+
 // benchmark timing of the LoopOverTerms search kernel (nqs_search_timing)
 void search_timing(bool on);
 cudaError_t search_time(double* total_ms, int64_t* launches);
+
+// measured integer speed of light (nqs_probe_peaks): out[0] lane-ops/s of the
+// probe's ALU mix, out[1] probes/s of the filter loop alone
+cudaError_t probe_peaks(double* out, cudaStream_t s);
 
 cudaError_t launch_amplitudes(const double* a, const double* b, int64_t n, int precision,
                               char* stage, const StageHeader& L, cudaStream_t s);

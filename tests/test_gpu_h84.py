@@ -1,6 +1,7 @@
 """84 qubits (two 64-bit words per sample), 1.15e6 Pauli terms, 2e5 peaked samples.
 
-Forward E^var in FP32C and FP64; sampled rows against the oracle; the adjoint
+Forward E^var in FP32C and FP64; sampled rows against the oracle (every row
+is compared in test_gpu_full_parity.py); the adjoint
 through the autograd function with the pair list recomputed in row chunks,
 checked against central finite differences (h = 1e-4) at full size and against
 the oracle's gradient on a 300-sample batch of the same Hamiltonian.
@@ -42,7 +43,7 @@ def test_h84_forward_rows_and_precision(h84):
     for i in rng.choice(inst.n_unq, size=12, replace=False):
         rr = ro.row(int(i))
         assert sorted(j[rp[i]:rp[i + 1]].tolist()) == sorted(rr["j"])
-        assert abs(r64["eloc_re"][i].item() - rr["eloc"].real) < 1e-8
+        assert abs(r64["eloc_re"][i].item() - rr["eloc"].real) < 1e-9
         assert abs(r32["eloc_re"][i].item() - rr["eloc"].real) < 1e-6
 
 

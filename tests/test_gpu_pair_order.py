@@ -114,14 +114,21 @@ def test_star_long_row(n_two):
     ev = nqs.variational_energy(batch, logpsi, er)
     g = np.random.default_rng(5).normal(0.0, 1.0, len(samples))
     gr, _ = nqs.local_energy_backward(batch, logpsi, None, er, None, hd, ev, g, None, None, pairs, "fp64")
+    # the same rows in FP32C (the long row is reduced by a whole block there too)
+    er32, _, hd32 = nqs.local_energy(batch, logpsi, None, pairs, "fp32c")
+    ev32 = nqs.variational_energy(batch, logpsi, er32)
+    gr32, _ = nqs.local_energy_backward(batch, logpsi, None, er32, None, hd32, ev32, g, None, None, pairs, "fp32c")
+    batch.status()  # no device index check fired
     ro = oracle.RowOracle(U, oracle.prepare_hamiltonian(x, z, c, n_qubits), logpsi)
     for r in [hub, 0, 1, len(samples) - 1]:
         want = ro.row(r)["eloc"]
         assert abs(er[r].item() - want.real) < 1e-9
+        assert abs(er32[r].item() - want.real) < 1e-6
         eloc = np.zeros(len(samples), complex)
         eloc[r] = want
         g_want, _ = ro.row_vjp(r, eloc, 0.0, g_eloc_re=g, g_evar=0.0)
         assert abs(gr[r].item() - g_want) < 1e-9 * max(1.0, abs(g_want))
+        assert abs(gr32[r].item() - g_want) < 1e-6 * max(1.0, abs(g_want))
     # one-pass and two-pass lists agree
     two = nqs.coupled_pairs(batch, one_pass=False)
     for a_, b_ in zip(pairs, two):

@@ -318,14 +318,17 @@ def test_fp32c_vs_fp64_h56_full_size():
         rr = ro.row(int(i))
         got = sorted(j[rp[i]:rp[i + 1]].tolist())
         assert got == sorted(rr["j"])
-        assert abs(r64["eloc_re"][i].item() - rr["eloc"].real) < TOL64 * 10
+        assert abs(r64["eloc_re"][i].item() - rr["eloc"].real) < TOL64
         assert abs(r32["eloc_re"][i].item() - rr["eloc"].real) < TOL32
     # pair symmetry over the whole list
     key = rows * inst.n_unq + j
     key_t = j * inst.n_unq + rows
     assert np.array_equal(np.sort(key), np.sort(key_t))
+    # the reduction alone (E^var of the GPU's own E_loc by the oracle's formula); E^var against the
+    # oracle's own E_loc of every row is checked in test_gpu_full_parity.py
     ev_ref = oracle.variational_energy(inst.logpsi_re, [complex(v) for v in r64["eloc_re"].cpu().numpy()])
     assert abs(ev_ref.real - r64["evar"][0].item()) < TOL64
+    batch.status()
 
 
 def test_error_paths():

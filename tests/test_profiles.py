@@ -1,10 +1,10 @@
-"""The committed ncu summaries under profiles/ (no GPU needed).
+"""The committed ncu records under profiles/ (no GPU needed).
 
-bench.py reports the search kernel's DRAM traffic from
-profiles/pairs_terms_kernel_h56.md only while that summary was taken on the
+bench.py reports the search kernel's DRAM traffic from the machine-readable
+record profiles/search_traffic.json only while that record was taken on the
 current search source; a change to the search kernel without a new capture
 fails here instead of silently turning the bench's traffic figure to null.
-Every ncu command recorded there leaves the GPU clocks alone.
+Every ncu command recorded under profiles/ leaves the GPU clocks alone.
 """
 
 import glob
@@ -18,12 +18,12 @@ PROFILES = os.path.join(ROOT, "profiles")
 def test_search_traffic_summary_matches_source():
     import bench
     traffic = bench._profile_traffic()
-    assert traffic is not None, "profiles/pairs_terms_kernel_h56.md was captured on another search source"
+    assert traffic is not None, "profiles/search_traffic.json was captured on another search source"
     assert traffic > 0
 
 
 def test_ncu_commands_keep_clocks():
-    files = sorted(glob.glob(os.path.join(PROFILES, "*.md")))
+    files = sorted(glob.glob(os.path.join(PROFILES, "*.md")) + glob.glob(os.path.join(PROFILES, "*.txt")))
     assert files
     checked = 0
     for path in files:

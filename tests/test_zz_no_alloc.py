@@ -11,6 +11,7 @@ named so that pytest collects it last.
 """
 
 import ctypes
+import math
 
 import numpy as np
 import pytest
@@ -46,7 +47,9 @@ def test_noalloc_matches_workspace_form_on_two_calls():
     ham, batch = _workspace_batch(nqs)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     rng = np.random.default_rng(2024)
-    for n in (100_000, 777):  # the second call must not see the first call's partial sums
+    # the second and later calls must not see an earlier call's partial sums;
+    # 2^21 fills all 1024 partial-sum slots of the array, 2^21 - 1 leaves a ragged last one
+    for n in (100_000, 777, 2 ** 21, 2 ** 21 - 1):
         a = torch.from_numpy(-2.0 * rng.integers(0, 5, n) + rng.normal(0.0, 0.3, n)).cuda()
         e = torch.from_numpy(rng.normal(50.0, 30.0, n)).cuda()
         want = torch.empty(3, dtype=torch.float64, device="cuda")
@@ -61,7 +64,7 @@ def test_noalloc_matches_workspace_form_on_two_calls():
         # and the plain definition (Eq. variational_energy) in FP64 on the host
         an, en = a.cpu().numpy(), e.cpu().numpy()
         p = np.exp(2.0 * (an - an.max()))
-        assert abs(g[0] - (p * en).sum() / p.sum()) <= TOL64
+        assert abs(g[0] - math.fsum(p * en) / math.fsum(p)) <= TOL64
 
 
 def test_noalloc_rejects_batches_beyond_its_array():

@@ -26,6 +26,8 @@ Modules and the passages they follow:
   derivatives with respect to log psi.
 * ``rows`` -- the same quantities for a chosen subset of rows of a large
   batch (LoopOverTerms per row), used for sampled checks at full size.
+* ``sampling`` -- autoregressive sampling without replacement, Alg. 1
+  (ARGumbelTopK), with the random numbers passed in.
 * ``candidates`` -- the exact local energy of Eq. (local_energy): the
   coupled candidates x XOR XY of every sample (inside or outside U),
   deduplicated over the batch, and the sum over them.
@@ -46,6 +48,7 @@ from .energy import (matrix_element, matrix_element_all_terms, local_energy_var,
                      local_energy_vjp, forward)
 from .rows import RowOracle
 from .candidates import full_candidates, local_energy_full
+from .sampling import ar_gumbel_topk
 
 __all__ = [
     "PauliTerm", "PreparedHamiltonian", "prepare_hamiltonian", "pauli_matrix_element",
@@ -54,5 +57,5 @@ __all__ = [
     "find_a_in_b_pointers", "prefix_tree_levels",
     "matrix_element", "matrix_element_all_terms", "local_energy_var", "variational_energy",
     "energy_gradient_closed_form", "local_energy_vjp", "forward", "RowOracle",
-    "full_candidates", "local_energy_full",
+    "full_candidates", "local_energy_full", "ar_gumbel_topk",
 ]

@@ -22,11 +22,12 @@ from .samples import (peaked_samples, all_sector_determinants, rank_quotas,
                       excitation_rank)
 from .instances import (Instance, config_instance, CONFIGS, batched_instances,
                         random_pauli_hamiltonian)
+from .ansatz import ToyAutoregressive, gumbel_noise
 
 __all__ = [
     "n_words", "pack_ints", "unpack_ints", "from_paper_string", "to_paper_string",
     "popcount_rows", "molecular_integrals", "jordan_wigner", "hf_energy_from_integrals",
     "pauli_to_xyz", "peaked_samples", "all_sector_determinants", "rank_quotas",
     "excitation_rank", "Instance", "config_instance", "CONFIGS", "batched_instances",
-    "random_pauli_hamiltonian",
+    "random_pauli_hamiltonian", "ToyAutoregressive", "gumbel_noise",
 ]

@@ -28,6 +28,8 @@ Modules and the passages they follow:
   batch (LoopOverTerms per row), used for sampled checks at full size.
 * ``sampling`` -- autoregressive sampling without replacement, Alg. 1
   (ARGumbelTopK), with the random numbers passed in.
+* ``sr`` -- the quantum geometric tensor of Eq. (qgt_definition) on the most
+  probable samples and the regularised (min-SR) step.
 * ``candidates`` -- the exact local energy of Eq. (local_energy): the
   coupled candidates x XOR XY of every sample (inside or outside U),
   deduplicated over the batch, and the sum over them.
@@ -49,6 +51,7 @@ from .energy import (matrix_element, matrix_element_all_terms, local_energy_var,
 from .rows import RowOracle
 from .candidates import full_candidates, local_energy_full
 from .sampling import ar_gumbel_topk
+from .sr import top_probable, sr_weights, qgt, centred, sample_gram, min_sr_step
 
 __all__ = [
     "PauliTerm", "PreparedHamiltonian", "prepare_hamiltonian", "pauli_matrix_element",
@@ -58,4 +61,5 @@ __all__ = [
     "matrix_element", "matrix_element_all_terms", "local_energy_var", "variational_energy",
     "energy_gradient_closed_form", "local_energy_vjp", "forward", "RowOracle",
     "full_candidates", "local_energy_full", "ar_gumbel_topk",
+    "top_probable", "sr_weights", "qgt", "centred", "sample_gram", "min_sr_step",
 ]

@@ -70,6 +70,26 @@ def test_bounding_property():
         prev = cur
 
 
+def test_conditioned_value_is_the_printed_expression():
+    """The stable form equals -log(exp(-T) - exp(-Z) + exp(-L)) evaluated with 50 digits,
+    also where FP64 evaluation of the printed form loses every digit (Z far below T)."""
+    import mpmath
+    mpmath.mp.dps = 50
+    rng = np.random.default_rng(23)
+    from oracle.sampling import conditioned_value
+    cases = [(-3.4657359027997265, -40.97809828410075, -48.8)]   # the printed form gives log(0) here
+    for _ in range(400):
+        T = rng.uniform(-60, 20)
+        Z = T - rng.exponential(rng.choice([0.01, 1.0, 30.0]))
+        L = Z - rng.exponential(rng.choice([1e-9, 0.1, 3.0, 50.0]))
+        cases.append((T, Z, L))
+    for T, Z, L in cases:
+        exact = -mpmath.log(mpmath.exp(-mpmath.mpf(T)) - mpmath.exp(-mpmath.mpf(Z)) + mpmath.exp(-mpmath.mpf(L)))
+        got = conditioned_value(T, Z, L)
+        assert abs(got - float(exact)) <= 1e-13 * max(1.0, abs(float(exact))), (T, Z, L, got, float(exact))
+    assert conditioned_value(1.5, -2.0, -2.0) == 1.5
+
+
 def test_gumbel_max_frequencies():
     model = ToyAutoregressive(3, 7, scale=1.0)
     p = np.array([math.exp(model.log_prob(x)) for x in range(8)])

@@ -189,6 +189,96 @@ def cpu_baseline(inst, seconds=15.0, max_rows=None):
                       f"pure Python FP64 ({dt:.1f} s; oracle set-up {setup:.1f} s not timed)"}
 
 
+def bench_full_eloc(nqs, torch, inst, n_sub, steps, warmup, flush, peak_gbs):
+    """Exact local energy (Eq. local_energy) on the first n_sub samples of the
+    batch: candidate generation with matrix elements and deduplication, then
+    the sum over the candidates given their log-amplitudes (a seeded stand-in
+    for the ansatz's values).  Device-timed with CUDA events on the stream."""
+    dev = flush.device
+    ham = nqs.Hamiltonian.from_instance(inst)
+    U = torch.from_numpy(np.ascontiguousarray(inst.U[:n_sub]).view(np.int64)).to(dev)
+    a = torch.from_numpy(inst.logpsi_re[:n_sub].copy()).to(dev)
+    batch = nqs.Batch(ham, U, check=True)
+    stream = torch.cuda.current_stream()
+    fc = nqs.full_candidates(batch)
+    ca = torch.from_numpy(np.random.default_rng(11).normal(-8.0, 2.0, fc.n_cand)).to(dev)
+    er = torch.empty(n_sub, dtype=torch.float64, device=dev)
+    for _ in range(warmup):
+        fc = nqs.full_candidates(batch)
+        nqs.local_energy_full(fc, a, None, ca, out=(er, None))
+    torch.cuda.synchronize()
+    t_gen, t_el = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        fc = nqs.full_candidates(batch)
+        e1.record(stream)
+        nqs.local_energy_full(fc, a, None, ca, out=(er, None))
+        e2.record(stream)
+        t_gen.append((e0, e1)); t_el.append((e1, e2))
+    torch.cuda.synchronize()
+    batch.status()
+    ms_gen = float(np.mean([x.elapsed_time(y) for x, y in t_gen]))
+    ms_el = float(np.mean([x.elapsed_time(y) for x, y in t_el]))
+    n_xy = int(ham.info["n_xy"])
+    entries = n_sub * n_xy
+    W = inst.n_words
+    # algorithmic bytes: per entry the candidate index (4 B) and matrix element (8 B) written by
+    # the generation and read by the sum; per distinct candidate its key and U-index written and
+    # its log-amplitude read; U, log psi and E_loc per sample; the Hamiltonian's XY table
+    b_gen = entries * 12 + fc.n_cand * (8 * W + 4) + n_sub * (8 * W + 4) + n_xy * (8 * W + 4)
+    b_el = entries * 12 + fc.n_cand * 8 + n_sub * 16
+    roof = {"bound": "hbm", "kernel": "candidate generation (insert, compact, sort, relabel) + E_loc sum",
+            "achieved": (b_gen + b_el) / ((ms_gen + ms_el) * 1e-3) / 1e9, "peak": peak_gbs, "unit": "GB/s",
+            "frac": (b_gen + b_el) / ((ms_gen + ms_el) * 1e-3) / 1e9 / peak_gbs,
+            "algorithmic_bytes": b_gen + b_el,
+            "sum_only": {"achieved": b_el / (ms_el * 1e-3) / 1e9, "frac": b_el / (ms_el * 1e-3) / 1e9 / peak_gbs}}
+    return {"workload": f"first {n_sub} samples of {inst.name}, {n_xy} XY patterns, {entries} candidate entries, "
+                        f"{fc.n_cand} distinct candidates",
+            "entries": entries, "n_cand": fc.n_cand, "ms_candidates": ms_gen, "ms_eloc_sum": ms_el,
+            "entries_per_s": entries / ((ms_gen + ms_el) * 1e-3), "roofline": roof, "steps": steps}
+
+
+def bench_sr(nqs, torch, n_sr, n_params, steps, flush, peaks):
+    """min-SR step (Sec. "ANQS-tailored stochastic reconfiguration") on n_sr samples with
+    n_params log-derivatives (synthetic FP32, seeded): top-probability selection is not
+    included (the derivatives are the ansatz's, for the selected samples)."""
+    dev = flush.device
+    g = torch.Generator(device=dev).manual_seed(12)
+    O = torch.randn((n_sr, n_params), generator=g, device=dev, dtype=torch.float32)
+    O += torch.randn((1, n_params), generator=g, device=dev, dtype=torch.float32) * 0.5
+    a = torch.randn(n_sr, generator=g, device=dev, dtype=torch.float64) * 0.7
+    el = torch.randn(n_sr, generator=g, device=dev, dtype=torch.float64) - 5.0
+    ev = torch.tensor([-5.1], dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        nqs.sr_step(O, a, el, ev, 1e-2)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nqs.sr_step(O, a, el, ev, 1e-2)
+        e1.record(stream)
+        ms.append((e0, e1))
+    torch.cuda.synchronize()
+    t = float(np.mean([x.elapsed_time(y) for x, y in ms]))
+    o_bytes = 4.0 * n_sr * n_params
+    mma_flops = 3 * 2.0 * 128 * 128 * n_params     # hi hi + hi lo + lo hi, M = N = 128 tiles
+    useful_flops = 2.0 * n_sr * n_sr * n_params
+    return {"workload": f"N_SR = {n_sr} samples, {n_params} parameters (FP32 d log psi / d theta)",
+            "ms_per_step": t,
+            "hbm": {"bytes": 3 * o_bytes, "what": "O read by the mean, the Gram (tensor-core) and the step kernels",
+                    "achieved_gbs": 3 * o_bytes / (t * 1e-3) / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
+                    "frac": 3 * o_bytes / (t * 1e-3) / 1e9 / peaks.get("hbm_gbs")},
+            "tensor": {"mma_flops": mma_flops, "useful_flops": useful_flops,
+                       "achieved_tflops": mma_flops / (t * 1e-3) / 1e12, "peak_tflops": peaks.get("bf16_tflops"),
+                       "frac": mma_flops / (t * 1e-3) / 1e12 / peaks.get("bf16_tflops"),
+                       "note": "over the whole step time (mean, Gram, FP64 sum and Cholesky solve, step)"}}
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -333,6 +423,36 @@ def run_ours(args):
     value = ws * n * args.steps / (t_ms * 1e-3)
     phases = {k: float(np.mean([m0.elapsed_time(m1) for m0, m1 in v])) for k, v in ev.items()}
 
+    # the half-stored pair path (each unordered pair once, symmetric scatter), same batch and rules
+    def step_half(batch_obj, Udev, adev):
+        batch_obj.restage(Udev)
+        half = nqs.half_pairs(batch_obj)
+        if hbuf_half[0] is None or hbuf_half[0].shape[0] < half[3]:
+            hbuf_half[0] = nqs.half_h_buffer(int(half[3] * 1.1) + 1024, prec, dev)
+        hr = hbuf_half[0][:half[3]]
+        er, ei, hd = nqs.local_energy_half(batch_obj, adev, None, half, prec, out=outs["e"], hrec=hr)
+        evar = nqs.variational_energy(batch_obj, adev, er, out=outs["v"])
+        gr, gi = nqs.local_energy_backward_half(batch_obj, adev, None, er, ei, hd, evar, g, None, gE, half, prec,
+                                                hrec=hr, out=outs["g"])
+        return er, evar, gr
+
+    half_ms = None
+    if ws == 1:
+        hbuf_half = [None]
+        for _ in range(3):
+            step_half(batch, U, a)
+        torch.cuda.synchronize()
+        h_ev = []
+        for it in range(args.steps):
+            flush.zero_()
+            s0 = torch.cuda.Event(enable_timing=True); s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            er_h, ev_h, gr_h = step_half(batch, U, a)
+            s1.record(stream)
+            h_ev.append((s0, s1))
+        torch.cuda.synchronize()
+        half_ms = float(np.mean([s0.elapsed_time(s1) for s0, s1 in h_ev]))
+
     # the other precision on the same batch, same step, same timing rules
     other = "fp64" if prec == "fp32c" else "fp32c"
     for _ in range(3):
@@ -460,10 +580,24 @@ def run_ours(args):
             "phases_ms": phases, "precision_error": err,
             f"{other}_ms_per_step": other_ms,
             f"{other}_value": ws * n / (other_ms * 1e-3),
+            "half_pairs_path": None if half_ms is None else {
+                "ms_per_step": half_ms, "value": n / (half_ms * 1e-3), "unit": UNIT,
+                "what": "same step with each unordered pair stored once (i, j, k) and both rows updated by FP64 "
+                        "atomic addition (no scatter, no row sort; one matrix element per unordered pair)",
+                "precision": prec},
             "roofline": roof, "hbm": hbm,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": kernels_per_step * args.steps,
             "clocks": clk}
+    if ws == 1 and args.sr_params > 0:
+        line["sr"] = bench_sr(nqs, torch, 100, args.sr_params, max(3, args.steps // 4), flush, peaks)
+    if ws == 1 and not args.no_batch64:
+        b = measure_batched(args, steps=max(3, args.steps // 3), gradients=True)
+        line["batch64"] = {k: b[k] for k in ("metric", "value", "unit", "ms_per_step", "config", "sequential_ms_per_step",
+                                             "e2e", "gpu_launches", "tuned", "gradients")}
+    if ws == 1 and args.full_n > 0:
+        line["full_eloc"] = bench_full_eloc(nqs, torch, inst, min(args.full_n, n), max(3, args.steps // 4), 3, flush,
+                                            peaks.get("hbm_gbs"))
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(inst, seconds=args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -471,7 +605,8 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-BATCH_METRIC = "unique-sample E_loc/s over 64 batched instances of 20-56 qubits (E_loc^var + E^var, one graph)"
+BATCH_METRIC = ("unique-sample E_loc/s over 64 batched instances of 20-56 qubits (E_loc^var + E^var, and with "
+                "gradients dE^var/dlog psi, one graph)")
 
 
 def run_batched(args):
@@ -482,9 +617,20 @@ def run_batched(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
+    line = measure_batched(args, ws, rank, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measure_batched(args, ws=1, rank=0, local=0, steps=None, gradients=False):
+    """The batched workload's measurements (a dict; rank 0's values)."""
+    import torch
     dev = torch.device("cuda", local)
     import paper_2408_07625_gb300 as nqs
     from synth import batched_instances
+    steps = args.steps if steps is None else steps
 
     insts = batched_instances(64)
     hams = {}
@@ -497,7 +643,7 @@ def run_batched(args):
         hosts.append((Uh, ah))
         items.append((hams[inst.n_qubits], Uh.to(dev), ah.to(dev)))
     t0 = time.time()
-    plan = nqs.BatchedPlan(items, precision=args.precision, autotune=True)
+    plan = nqs.BatchedPlan(items, precision=args.precision, autotune=True, gradients=gradients)
     t_plan = time.time() - t0
     total = sum(inst.n_unq for inst in insts)
     stream = torch.cuda.current_stream()
@@ -511,7 +657,7 @@ def run_batched(args):
     clocks.start()
     time.sleep(0.3)
     ev = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
         a.record(stream); plan.run(); b.record(stream)
@@ -526,7 +672,7 @@ def run_batched(args):
     batches = [nqs.Batch(it[0], it[1]) for it in items]
     scheds = [plan.info(i)["schedule"] for i in range(len(items))]
     seq = []
-    for _ in range(max(1, args.steps // 3)):
+    for _ in range(max(1, steps // 3)):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -538,10 +684,10 @@ def run_batched(args):
     torch.cuda.synchronize()
     seq_ms = float(np.mean([a.elapsed_time(b) for a, b in seq]))
     # end to end: pinned host inputs in, E_loc and E^var out, every step
-    outs = [(torch.empty(inst.n_unq, dtype=torch.float64).pin_memory(), torch.empty(3, dtype=torch.float64).pin_memory())
-            for inst in insts]
+    outs = [(torch.empty(inst.n_unq, dtype=torch.float64).pin_memory(), torch.empty(3, dtype=torch.float64).pin_memory(),
+             torch.empty(inst.n_unq, dtype=torch.float64).pin_memory() if gradients else None) for inst in insts]
     e2e = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True); b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -549,9 +695,11 @@ def run_batched(args):
             plan.U[i].copy_(Uh, non_blocking=True)
             plan.logpsi[i].copy_(ah, non_blocking=True)
         plan.run()
-        for i, (oe, ov) in enumerate(outs):
+        for i, (oe, ov, og) in enumerate(outs):
             oe.copy_(plan.eloc[i], non_blocking=True)
             ov.copy_(plan.evar[i], non_blocking=True)
+            if og is not None:
+                og.copy_(plan.grad[i], non_blocking=True)
         b.record(stream)
         e2e.append((a, b))
     torch.cuda.synchronize()
@@ -560,16 +708,12 @@ def run_batched(args):
         t = torch.tensor([t_ms, e2e_ms], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t_ms, e2e_ms = float(t[0].item()), float(t[1].item())
-    if rank != 0:
-        if ws > 1:
-            torch.distributed.destroy_process_group()
-        return
     h2d = sum(inst.U.nbytes + inst.logpsi_re.nbytes for inst in insts)
-    d2h = sum(8 * inst.n_unq + 24 for inst in insts)
+    d2h = sum(8 * inst.n_unq * (2 if gradients else 1) + 24 for inst in insts)
     counts = {k: scheds.count(k) for k in sorted(set(scheds))}
     n_pairs = int(sum(plan.info(i)["planned_pairs"] for i in range(len(items))))
-    line = {"metric": BATCH_METRIC, "value": ws * total * args.steps / (t_ms * 1e-3), "unit": UNIT,
-            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+    line = {"metric": BATCH_METRIC, "value": ws * total * steps / (t_ms * 1e-3), "unit": UNIT,
+            "n_gpus": ws, "steps": steps, "warmup": args.warmup, "ms_per_step": t_ms / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u64+f32c (FP32 compensated, FP64 reduction)" if args.precision == "fp32c" else "u64+f64",
             "data": "synthetic (seeded integrals, JW, peaked samples)",
@@ -579,12 +723,16 @@ def run_batched(args):
                        "plan_s": round(t_plan, 2), "precision": args.precision,
                        "l2": "flushed between timed steps (512 MiB write)"},
             "sequential_ms_per_step": seq_ms,
-            "e2e": {"value": ws * total * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+            "e2e": {"value": ws * total * steps / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": plan.info(0)["graph_kernels"] * args.steps, "clocks": clk}
-    print(json.dumps(line), flush=True)
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+            "gpu_launches": plan.info(0)["graph_kernels"] * steps, "clocks": clk,
+            "tuned": {"schedules": counts,
+                      "terms_settings": sorted({(plan.info(i)["tune"]["terms_grab"], plan.info(i)["tune"]["terms_groups"])
+                                                for i in range(len(items)) if scheds[i] == "terms"}),
+                      "trie_settings": sorted({plan.info(i)["tune"]["trie_pop"] for i in range(len(items))
+                                               if scheds[i] == "trie"})},
+            "gradients": gradients}
+    return line
 
 
 def main():
@@ -600,6 +748,11 @@ def main():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ref-rows", type=int, default=40)
+    p.add_argument("--sr-params", type=int, default=1_000_000,
+                   help="parameters of the min-SR measurement (100 samples); 0 skips it")
+    p.add_argument("--no-batch64", action="store_true", help="skip the 64-instance batched measurement")
+    p.add_argument("--full-n", type=int, default=1000,
+                   help="samples of the exact-local-energy (Eq. local_energy) measurement; 0 skips it")
     args = p.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -37,9 +37,12 @@
  *     device-side problems (repeated samples, bounded loops running out) are
  *     recorded in a status word and reported by the next synchronising call
  *     or by nqs_stage_status().
- *   - Scope of version 1: real Hamiltonians (every string has an even number
- *     of Y, real h_l; molecular Hamiltonians are of this kind); complex log
- *     psi is supported; 1 <= N <= 256.
+ *   - Scope: real coefficients h_l; strings with an odd number of Y make H
+ *     complex Hermitian (coefficient h_l i^{|Y|} imaginary), and then the
+ *     local energies are complex (eloc_im required); molecular Hamiltonians
+ *     are real.  Complex log psi is supported; 1 <= N <= 256.  The batched
+ *     plan and the exact local energy (nqs_full_candidates) take real
+ *     Hamiltonians only.
  */
 #ifndef NQS_H
 #define NQS_H
@@ -55,7 +58,7 @@ extern "C" {
 enum {
     NQS_OK = 0,
     NQS_ERR_ARG = -1,          /* bad argument (null pointer, size, range)          */
-    NQS_ERR_UNSUPPORTED = -2,  /* outside the scope above (odd |Y|, N > 256)        */
+    NQS_ERR_UNSUPPORTED = -2,  /* outside the scope above (N > 256, ...)            */
     NQS_ERR_CUDA = -3,         /* a CUDA runtime call failed                        */
     NQS_ERR_CAPACITY = -4,     /* output buffer too small; required size returned  */
     NQS_ERR_DUPLICATE = -5,    /* the sample batch repeats a basis vector           */
@@ -89,10 +92,12 @@ typedef struct nqs_ham nqs_ham;
  *   x_mask, z_mask : host, [n_terms][W] uint64, symplectic encoding.
  *   coef           : host, [n_terms] FP64 real coefficients h_l.
  * Identical strings are merged (coefficients summed); terms whose merged
- * coefficient is exactly zero are dropped.  Errors: NQS_ERR_ARG (n_qubits
- * out of range, bits >= N set, null pointer), NQS_ERR_UNSUPPORTED (a term
- * with an odd number of Y), NQS_ERR_OOM, NQS_ERR_CUDA.  On success *out
- * owns the device tables until nqs_ham_free. */
+ * coefficient is exactly zero are dropped.  A string with an odd number of
+ * Y gets the imaginary coefficient h_l i^{|Y|} (Eq. pauli_melem) and makes
+ * the Hamiltonian complex (nqs_ham_is_complex).  Errors: NQS_ERR_ARG
+ * (n_qubits out of range, bits >= N set, null pointer),
+ * NQS_ERR_UNSUPPORTED (N > 256), NQS_ERR_OOM, NQS_ERR_CUDA.  On success
+ * *out owns the device tables until nqs_ham_free. */
 int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask,
                  const uint64_t* z_mask, const double* coef, nqs_ham** out);
 
@@ -108,9 +113,16 @@ int nqs_ham_info(const nqs_ham* ham, int64_t info[8]);
  *   xy      [n_xy][W]   unique XY patterns, in library order
  *   row_ptr [n_xy+1]    P_XY of pattern m = terms row_ptr[m] .. row_ptr[m+1]-1
  *   yz      [terms][W]  YZ^(l) (= z mask) per grouped term
- *   coef    [terms]     h_l * i^{|Y^(l)|} (real, since |Y| is even)           */
+ *   coef    [terms]     real part of h_l * i^{|Y^(l)|} (zero if |Y| is odd)   */
 int nqs_ham_export(const nqs_ham* ham, uint64_t* xy, int64_t* row_ptr,
                    uint64_t* yz, double* coef);
+
+/* 1 if some string has an odd number of Y (complex H), else 0 (also for NULL). */
+int nqs_ham_is_complex(const nqs_ham* ham);
+
+/* Imaginary parts of the grouped coefficients h_l * i^{|Y^(l)|}, host
+ * [terms] in the order of nqs_ham_export (zero for even |Y|). */
+int nqs_ham_export_im(const nqs_ham* ham, double* coef_im);
 
 /* ---------------------------------------------------------------------------
  * Batch workspace and sample staging: the membership structure of U used by
@@ -208,12 +220,14 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
 /* For rows r in [row_begin, row_end), with their pairs from a fill pass over
  * the same range, write
  *   eloc_re[r], eloc_im[r] = E_loc^var(U_r)  (eloc_im may be NULL only if
- *                                              logpsi_im is NULL),
- *   hdiag[r] = H_{U_r U_r} (may be NULL),
+ *                                              logpsi_im is NULL and H is real),
+ *   hdiag[r] = H_{U_r U_r} (may be NULL; real for any Hermitian H),
  *   hpair[q] = H of pair q, q indexing pair_j/pair_k (may be NULL): device
  *              float2 (hi, lo) per pair with NQS_PREC_FP32C, double with
- *              NQS_PREC_FP64; nqs_local_energy_backward can read it instead
- *              of recomputing the matrix elements.
+ *              NQS_PREC_FP64; for a complex H both parts, float4 (re hi,
+ *              re lo, im hi, im lo) or double2 per pair (16-byte aligned);
+ *              nqs_local_energy_backward can read it instead of recomputing
+ *              the matrix elements.
  * logpsi_re/_im: device FP64 [n_unq] for the whole batch.  Each row is a
  * fixed-order reduction by one warp, so results are bitwise reproducible
  * (rows are handed out heaviest first; the order does not affect any row).
@@ -224,6 +238,130 @@ int nqs_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, void*
                      const uint32_t* pair_j, const uint32_t* pair_k, int precision,
                      double* eloc_re, double* eloc_im, double* hdiag, void* hpair,
                      void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Autoregressive sampling without replacement (Alg. 1, ARGumbelTopK; Sec.
+ * "Autoregressive sampling without replacement"): the producer of the
+ * unique batch U.  One call per qubit; the caller's ansatz supplies the
+ * conditional log-probabilities between calls.
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of the scratch of nqs_gumbel_topk_level for n_parents kept vectors. */
+int64_t nqs_gumbel_scratch_bytes(int64_t n_parents);
+
+/* Qubit `level` of Alg. 1.  The n_parents kept vectors x_<level (device
+ * uint64 [n_parents][W], W = ceil(n_qubits / 64); may be NULL at level 0,
+ * meaning the empty vector), their log-probabilities l and conditioned
+ * perturbed log-probabilities L~ (device FP64 [n_parents]; 0 and 0 for the
+ * empty vector), the conditional log-probabilities log p_level(x | x_<level)
+ * for x = 0, 1 (device FP64 [n_parents][2]; -inf for an impossible outcome)
+ * and the Gumbel(0) draws G (device FP64 [n_parents][2]) give the extensions
+ * l' = l + log p, L' = l' + G, Z = max(L'_0, L'_1),
+ * L~' = -log(exp(-L~) - exp(-Z) + exp(-L')) (evaluated as L~' = L~ for the
+ * larger extension and L~ - softplus(L~ - Z + log(expm1(Z - L'))) for the
+ * other: the same value without the cancellation).  The extensions with l' > -inf
+ * are ordered by L~' descending (stable: ties keep the parent order, x = 0
+ * first) and the first min(K, possible) are written to child_x [..][W],
+ * child_l, child_lt (device, room for min(K, 2 n_parents)); *n_children
+ * (host) is their number.  FP64 throughout.
+ * scratch: device, 256-byte aligned, nqs_gumbel_scratch_bytes(n_parents).
+ * Synchronises the stream (to learn the count).  The paper's own
+ * contribution is the use of this sampler (Ref. on ancestral Gumbel top-k
+ * sampling); the kernel is this library's. */
+int nqs_gumbel_topk_level(int n_qubits, int level, int64_t n_parents, const uint64_t* parent_x,
+                          const double* parent_l, const double* parent_lt, const double* cond_logp,
+                          const double* gumbel, int64_t K, void* scratch, int64_t scratch_bytes,
+                          uint64_t* child_x, double* child_l, double* child_lt, int64_t* n_children,
+                          void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Stochastic reconfiguration on the most probable samples (Sec. "ANQS-
+ * tailored stochastic reconfiguration", Eq. qgt_definition), min-SR form.
+ * ------------------------------------------------------------------------- */
+
+/* Scratch bytes of nqs_sr_top (n_unq samples) and nqs_sr_step (n_params). */
+int64_t nqs_sr_scratch_bytes(int64_t n_unq, int64_t n_params);
+
+/* Indices (device int32 [n_sr]) of the n_sr samples of highest probability
+ * p = |psi|^2, i.e. largest logpsi_re (device FP64 [n_unq]); equal values in
+ * index order.  Asynchronous. */
+int nqs_sr_top(int64_t n_unq, const double* logpsi_re, int64_t n_sr, int32_t* idx, void* scratch,
+               int64_t scratch_bytes, void* stream);
+
+/* The regularised SR step for n_sr <= 128 samples with real log-derivatives
+ * O = d log psi(x) / d theta (device FP32 [n_sr][n_params], row-major):
+ *   w = p / sum p over the n_sr samples (p = exp(2 logpsi_re)),
+ *   m = sum_x w_x O_x,  Obar_x = sqrt(w_x) (O_x - m)   (so S = Obar^T Obar
+ *   is the QGT estimate of Eq. qgt_definition with renormalised weights),
+ *   T = Obar Obar^T, eps_x = sqrt(w_x) (eloc_re[x] - evar[0]),
+ *   delta = Obar^T (T + lambda I)^{-1} eps   (device FP64 [n_params]),
+ *   T (device FP64 [n_sr][n_sr], may be NULL) receives Obar Obar^T.
+ * logpsi_re, eloc_re: device FP64 [n_sr]; evar: device FP64 [1].  T is
+ * formed on the tensor cores (tcgen05, bf16 hi/lo split of Obar with FP32
+ * accumulation: about 16 significant bits per element), summed and solved
+ * (Cholesky) in FP64.  The solve adds c sqrt(w) sqrt(w)^T (c = tr T / n_sr)
+ * to T + lambda I: sqrt(w) is a null vector of the exact T and the step
+ * annihilates it, so delta is unchanged while the factorisation no longer
+ * sees an eigenvalue of lambda along it.  Synchronises the stream.  Errors:
+ * NQS_ERR_RANGE if that matrix is not positive definite in FP64 (raise lambda),
+ * NQS_ERR_DEVICE_LIMIT if a tensor-core pipeline wait ran out. */
+int nqs_sr_step(int n_sr, int64_t n_params, const float* O, const double* logpsi_re, const double* eloc_re,
+                const double* evar, double lambda, double* delta, double* T, void* scratch, int64_t scratch_bytes,
+                void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Exact local energy (Eq. local_energy): the sum over every x' with
+ * H_xx' != 0, inside or outside the batch.  Term l couples x to x' exactly
+ * when x XOR x' = XY^(l) (Eq. pauli_melem), so the candidates of x are
+ * x XOR XY_k for the k = 0 .. n_xy-1 unique XY patterns of the loaded
+ * Hamiltonian (library order, nqs_ham_export).  Every sample has exactly
+ * n_xy candidate entries, e = i * n_xy + k, whose matrix element may be zero
+ * (a pattern whose terms cancel on x).  The ansatz is evaluated once per
+ * distinct candidate; the paper's surrogate E_loc^var (Sec. "Streamlined
+ * local energy calculations") keeps only the candidates that lie in U.
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of the scratch nqs_full_candidates needs for n_unq samples (about
+ * 60 + 16 W bytes per entry, n_unq * n_xy entries). */
+int64_t nqs_candidates_scratch_bytes(const nqs_ham* ham, int64_t n_unq);
+
+/* Candidates of every sample of U (device [n_unq][W]; staged in `work`):
+ *   cand_id  device uint32 [n_unq][n_xy]: index of x_i XOR XY_k in `cand`;
+ *   hval     device FP64 [n_unq][n_xy] or NULL: H_{x_i, x_i XOR XY_k} (the
+ *            MatrixElement forms of nqs_local_energy, FP64);
+ *   cand     device uint64 [capacity][W]: the distinct candidates of the
+ *            whole batch in increasing numeric order (qubit 0 the least
+ *            significant bit); *n_cand (host) their number;
+ *   cand_in_u device int32 [capacity] or NULL: the candidate's index in U,
+ *            or -1 if it is not a sample of the batch.
+ * scratch: device, 256-byte aligned, scratch_bytes >= nqs_candidates_scratch_bytes.
+ * Needs n_unq * n_xy <= 2^29.  Synchronises the stream once (to learn
+ * *n_cand); the remaining kernels may still run on the stream when it
+ * returns.  NQS_ERR_CAPACITY (with *n_cand set, cand unwritten) if
+ * capacity < *n_cand or cand is NULL; the call can be repeated with larger
+ * buffers.  The candidate order and every index are independent of thread
+ * timing. */
+int nqs_full_candidates(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, void* work,
+                        void* scratch, int64_t scratch_bytes, uint32_t* cand_id, double* hval,
+                        uint64_t* cand, int32_t* cand_in_u, int64_t capacity, int64_t* n_cand,
+                        void* stream);
+
+/* E_loc(x_i) = sum_k H_{x_i, x_k} psi(x_k) / psi(x_i) over the candidate
+ * entries of nqs_full_candidates (Eq. local_energy), FP64, one fixed-order
+ * reduction per sample.  logpsi_re/_im: device [n_unq] for U (im may be
+ * NULL); cand_logpsi_re/_im: device [n_cand] for the candidates in the
+ * order of `cand` (im may be NULL; a candidate with psi = 0 may pass a very
+ * negative log, its contributions underflow to zero).  scratch: device,
+ * 256-byte aligned, >= 32 * n_cand bytes (the nqs_full_candidates scratch
+ * qualifies).  eloc_im needed when either imaginary part is given.  The
+ * per-sample amplitude records of `work` are overwritten.  A candidate index
+ * out of range is skipped and reported by nqs_stage_status as
+ * NQS_ERR_DEVICE_LIMIT.  Asynchronous. */
+int nqs_local_energy_full(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, void* work,
+                          const double* logpsi_re, const double* logpsi_im, const uint32_t* cand_id,
+                          const double* hval, int64_t n_cand, const double* cand_logpsi_re,
+                          const double* cand_logpsi_im, void* scratch, int64_t scratch_bytes,
+                          double* eloc_re, double* eloc_im, void* stream);
 
 /* E^var = sum_x p(x) Re E_loc^var(x) / sum_x p(x) with p = exp(2 a) over the
  * whole batch (Eq. variational_energy), FP64, deterministic (fixed block
@@ -282,7 +420,8 @@ int nqs_evar_combine_host(const double* parts, int k, double* out);
  * With both g_eloc arrays NULL no pair data is read (row_ptr may be NULL)
  * and the result is the closed form 2 w_y (E_loc(y) - E) g_evar.  The sum
  * over x of each pair (x, y) is evaluated on row y, which lists the same
- * pairs because x XOR y is symmetric and H is real symmetric.
+ * pairs because x XOR y is symmetric; it uses H_xy = conj(H_yx) (H
+ * Hermitian; equal for a real H).  A complex H needs eloc_im.
  * Asynchronous. */
 int nqs_local_energy_backward(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
                               void* work, const double* logpsi_re, const double* logpsi_im,
@@ -312,15 +451,21 @@ typedef struct {
     const double* logpsi_re;  /* device [n_unq] (real amplitudes)                    */
     double* eloc_re;          /* device [n_unq] output E_loc^var                      */
     double* evar;             /* device [3] output as nqs_variational_energy          */
+    double* grad;             /* device [n_unq] output dE^var / d Re log psi, or NULL */
 } nqs_instance;
 
 /* Plan n_inst instances (arrays are read during the call; the pointers inside
  * must stay valid for the plan's lifetime).  Planning stages every instance,
- * counts its pairs, picks its schedule (flags bit 0: time the count pass of
- * LoopOverTerms, LoopOverBatch and LoopOverTrie (with its prefix-tree build)
- * and keep the fastest; otherwise the cost model of NQS_SCHED_AUTO), allocates its buffers with 25% headroom over the planned
+ * counts its pairs, picks its schedule and launch parameters (flags bit 0:
+ * time the count pass of LoopOverTerms with 2/4/8 work items per atomic and
+ * 8/16/32 table groups per item, LoopOverBatch, and LoopOverTrie (with its
+ * prefix-tree build) popping 8/16/32 node pairs per step, and keep the
+ * fastest; otherwise the cost model of NQS_SCHED_AUTO with the default
+ * parameters), allocates its buffers with 25% headroom over the planned
  * pair count, and captures all instances into one CUDA graph on forked
- * streams.  Synchronises `stream`.  The plan owns its device memory. */
+ * streams.  An instance with `grad` set also gets the gradient of its E^var
+ * (the adjoint's closed form) in the graph.  Synchronises `stream`.  The
+ * plan owns its device memory.  Real Hamiltonians only. */
 int nqs_batch_plan(const nqs_instance* instances, int n_inst, int precision, int flags,
                    nqs_plan** out, void* stream);
 
@@ -338,6 +483,11 @@ int nqs_batch_status(const nqs_plan* plan, int* failed_instance, void* stream);
  * [6] LoopOverTrie tree build + count time (us) of instance i (-1: not
  * timed), [7] kernel nodes of the graph. */
 int nqs_batch_info(const nqs_plan* plan, int i, int64_t info[8]);
+
+/* Launch parameters chosen for instance i: tune[0] LoopOverTerms work items
+ * per atomic, tune[1] its table groups per work item, tune[2] LoopOverTrie
+ * node pairs popped per step (defaults 4, 16, 32 when not tuned). */
+int nqs_batch_tune(const nqs_plan* plan, int i, int32_t tune[3]);
 
 int nqs_batch_free(nqs_plan* plan);
 

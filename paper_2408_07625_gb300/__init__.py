@@ -17,7 +17,10 @@ import os
 import numpy as np
 import torch
 
-__all__ = ["NQSError", "load_library", "Hamiltonian", "Batch", "coupled_pairs",
+__all__ = ["NQSError", "load_library", "Hamiltonian", "Batch", "coupled_pairs", "FullCandidates",
+           "half_pairs", "local_energy_half", "local_energy_backward_half", "gumbel_topk_level",
+           "ar_gumbel_topk", "sr_top", "sr_step",
+           "full_candidates", "local_energy_full",
            "local_energy", "variational_energy", "local_energy_backward", "LocalEnergy",
            "evaluate", "BatchedPlan", "SCHEDULES", "PRECISIONS", "library_path"]
 
@@ -57,6 +60,8 @@ def load_library(path: str = None):
         "nqs_ham_free": (_i32, [_vp]),
         "nqs_ham_info": (_i32, [_vp, _c_i64p]),
         "nqs_ham_export": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+        "nqs_ham_is_complex": (_i32, [_vp]),
+        "nqs_ham_export_im": (_i32, [_vp, _vp]),
         "nqs_stage_bytes": (_i64, [_vp, _i64]),
         "nqs_stage": (_i32, [_vp, _vp, _i64, _vp, _i64, _i32, _vp]),
         "nqs_stage_status": (_i32, [_vp, _vp]),
@@ -75,6 +80,7 @@ def load_library(path: str = None):
         "nqs_batch_run": (_i32, [_vp, _vp]),
         "nqs_batch_status": (_i32, [_vp, ctypes.POINTER(_i32), _vp]),
         "nqs_batch_info": (_i32, [_vp, _i32, _c_i64p]),
+        "nqs_batch_tune": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_int32)]),
         "nqs_batch_free": (_i32, [_vp]),
         "nqs_evar_combine": (_i32, [_vp, _i32, _vp, _vp]),
         "nqs_evar_combine_host": (_i32, [_vp, _i32, _vp]),
@@ -83,6 +89,21 @@ def load_library(path: str = None):
         "nqs_search_timing": (_i32, [_i32]),
         "nqs_search_time": (_i32, [ctypes.POINTER(ctypes.c_double), _c_i64p]),
         "nqs_probe_peaks": (_i32, [ctypes.POINTER(ctypes.c_double), _vp]),
+        "nqs_candidates_scratch_bytes": (_i64, [_vp, _i64]),
+        "nqs_gumbel_scratch_bytes": (_i64, [_i64]),
+        "nqs_sr_scratch_bytes": (_i64, [_i64, _i64]),
+        "nqs_sr_top": (_i32, [_i64, _vp, _i64, _vp, _vp, _i64, _vp]),
+        "nqs_sr_step": (_i32, [_i32, _i64, _vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _i64, _vp]),
+        "nqs_gumbel_topk_level": (_i32, [_i32, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp, _vp,
+                                         _c_i64p, _vp]),
+        "nqs_find_pairs_half": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _c_i64p, _vp]),
+        "nqs_local_energy_half": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp,
+                                         _vp, _vp]),
+        "nqs_local_energy_backward_half": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp,
+                                                  _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp]),
+        "nqs_full_candidates": (_i32, [_vp, _vp, _i64, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _c_i64p, _vp]),
+        "nqs_local_energy_full": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i64,
+                                         _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -139,6 +160,8 @@ def _dev_u64(U):
 def _f64(t, device):
     if t is None:
         return None
+    if isinstance(t, (list, tuple)):
+        t = np.asarray(t, dtype=np.float64)
     if isinstance(t, np.ndarray):
         t = torch.from_numpy(np.ascontiguousarray(t, dtype=np.float64))
     return t.to(device=device, dtype=torch.float64).contiguous()
@@ -172,6 +195,7 @@ class Hamiltonian:
                      "has_diag": info[4], "max_group": info[5], "n_search": info[6],
                      "heavy_end": info[7]}
         self.n_words = int(info[1])
+        self.complex = bool(lib.nqs_ham_is_complex(h))
 
     @property
     def handle(self):
@@ -334,17 +358,20 @@ def probe_peaks(stream=None):
     return float(out[0]), float(out[1])
 
 
-def pair_h_buffer(n_pairs, precision="fp32c", device="cuda"):
-    """A tensor that holds one matrix element per pair (``hpair`` of local_energy)."""
+def pair_h_buffer(n_pairs, precision="fp32c", device="cuda", complex_h=False):
+    """A tensor that holds one matrix element per pair (``hpair`` of local_energy);
+    both parts of it for a complex Hamiltonian."""
+    m = 2 if complex_h else 1
     if precision == "fp64":
-        return torch.empty(max(int(n_pairs), 1), dtype=torch.float64, device=device)
-    return torch.empty((max(int(n_pairs), 1), 2), dtype=torch.float32, device=device)
+        return torch.empty((max(int(n_pairs), 1), m), dtype=torch.float64, device=device).squeeze(1)
+    return torch.empty((max(int(n_pairs), 1), 2 * m), dtype=torch.float32, device=device)
 
 
-def _check_hpair(hpair, n_pairs, precision):
+def _check_hpair(hpair, n_pairs, precision, complex_h=False):
     if hpair is None:
         return None
-    want = (torch.float64, 1) if precision == "fp64" else (torch.float32, 2)
+    m = 2 if complex_h else 1
+    want = (torch.float64, m) if precision == "fp64" else (torch.float32, 2 * m)
     if hpair.dtype != want[0] or hpair.numel() < want[1] * n_pairs or not hpair.is_contiguous():
         raise ValueError("hpair does not match the pair count or precision")
     return hpair
@@ -365,13 +392,14 @@ def local_energy(batch: Batch, logpsi_re, logpsi_im=None, pairs=None, precision=
     if pairs is None:
         pairs = coupled_pairs(batch, row_begin, row_end, stream=stream)
     rp, pj, pk = pairs
+    cplx = b is not None or batch.ham.complex
     if out is None:
         er = torch.zeros(batch.n, dtype=torch.float64, device=dev)
-        ei = torch.zeros(batch.n, dtype=torch.float64, device=dev) if b is not None else None
+        ei = torch.zeros(batch.n, dtype=torch.float64, device=dev) if cplx else None
         hd = torch.zeros(batch.n, dtype=torch.float64, device=dev)
     else:
         er, ei, hd = out
-    hpair = _check_hpair(hpair, int(pj.numel()), precision)
+    hpair = _check_hpair(hpair, int(pj.numel()), precision, batch.ham.complex)
     _check(_lib.nqs_local_energy(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work), _ptr(a), _ptr(b),
                                  int(row_begin), row_end, _ptr(rp), _pair_ptr(pj), _pair_ptr(pk),
                                  PRECISIONS[precision], _ptr(er), _ptr(ei), _ptr(hd), _ptr(hpair),
@@ -409,12 +437,15 @@ def local_energy_backward(batch: Batch, logpsi_re, logpsi_im, eloc_re, eloc_im, 
         gi = torch.zeros(batch.n, dtype=torch.float64, device=dev) if b is not None else None
     else:
         gr, gi = out
+    # converted arguments are held in locals until the call has been enqueued: a temporary
+    # freed after its pointer was taken would let the next conversion reuse its memory
+    up_re, up_im, up_e = _f64(g_eloc_re, dev), _f64(g_eloc_im, dev), _f64(g_evar, dev)
     _check(_lib.nqs_local_energy_backward(
         batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work), _ptr(a), _ptr(b), int(row_begin), row_end,
         _ptr(rp), _pair_ptr(pj), _pair_ptr(pk),
-        _ptr(_check_hpair(hpair, int(pj.numel()), precision) if pj is not None else None),
+        _ptr(_check_hpair(hpair, int(pj.numel()), precision, batch.ham.complex) if pj is not None else None),
         _ptr(eloc_re), _ptr(eloc_im), _ptr(hdiag), _ptr(evar),
-        _ptr(_f64(g_eloc_re, dev)), _ptr(_f64(g_eloc_im, dev)), _ptr(_f64(g_evar, dev)),
+        _ptr(up_re), _ptr(up_im), _ptr(up_e),
         PRECISIONS[precision], _ptr(gr), _ptr(gi), _stream(stream)))
     return gr, gi
 
@@ -448,7 +479,7 @@ def evaluate(batch: Batch, logpsi_re, logpsi_im=None, precision="fp32c", schedul
     a = _f64(logpsi_re, dev)
     b = _f64(logpsi_im, dev)
     er = torch.zeros(batch.n, dtype=torch.float64, device=dev)
-    ei = torch.zeros(batch.n, dtype=torch.float64, device=dev) if b is not None else None
+    ei = torch.zeros(batch.n, dtype=torch.float64, device=dev) if (b is not None or batch.ham.complex) else None
     hd = torch.zeros(batch.n, dtype=torch.float64, device=dev)
     rp_host = None
     kept = None
@@ -457,7 +488,7 @@ def evaluate(batch: Batch, logpsi_re, logpsi_im=None, precision="fp32c", schedul
         pairs = coupled_pairs(batch, 0, batch.n, schedule, reuse=not keep_pairs, stream=stream)
         row_ptr, total, chunks = pairs[0], int(pairs[1].numel()), [(0, batch.n)]
         if keep_h:
-            hpair = pair_h_buffer(total, precision, dev)
+            hpair = pair_h_buffer(total, precision, dev, batch.ham.complex)
         local_energy(batch, a, b, pairs, precision, 0, batch.n, (er, ei, hd), hpair=hpair, stream=stream)
         kept = pairs if keep_pairs else None
     else:
@@ -493,6 +524,7 @@ class LocalEnergy(torch.autograd.Function):
         ctx.batch, ctx.precision, ctx.max_pairs = batch, precision, max_pairs
         ctx.res = res
         ctx.cplx = logpsi_im is not None
+        ctx.cplx_out = ctx.cplx or batch.ham.complex   # Im E_loc is not zero
         ctx.save_for_backward(logpsi_re, logpsi_im if logpsi_im is not None else logpsi_re)
         ei = res["eloc_im"] if res["eloc_im"] is not None else torch.zeros_like(res["eloc_re"])
         return res["eloc_re"], ei, res["evar"][0]
@@ -503,7 +535,7 @@ class LocalEnergy(torch.autograd.Function):
         lim = lim if ctx.cplx else None
         res, batch = ctx.res, ctx.batch
         g_er = None if g_er is None else g_er.contiguous()
-        g_ei = None if (g_ei is None or not ctx.cplx) else g_ei.contiguous()
+        g_ei = None if (g_ei is None or not ctx.cplx_out) else g_ei.contiguous()
         g_e = None if g_e is None else g_e.reshape(1).to(torch.float64).contiguous()
         need_pairs = g_er is not None or g_ei is not None
         if not need_pairs or res["pairs"] is not None:
@@ -526,9 +558,227 @@ class LocalEnergy(torch.autograd.Function):
         return None, gr, gi, None, None
 
 
+def half_pairs(batch: Batch, stream=None):
+    """Each unordered coupled pair {x_i, x_j} once as a record (i, j, k) (nqs_find_pairs_half).
+
+    Returns (rec_i, rec_j, rec_k, n_slots): int32 tensors holding uint32 values,
+    slots [0, n_slots) of which are in use; an unused slot has i = 0xFFFFFFFF.
+    The buffers are kept on the batch and reused by the next call.
+    """
+    lib = load_library()
+    n = ctypes.c_int64()
+    cap = getattr(batch, "_half_cap", None) or max(128 * batch.n, 1 << 16)
+    for _ in range(3):
+        buf = getattr(batch, "_half_buf", None)
+        if buf is None or buf[0].numel() < cap:
+            buf = tuple(torch.empty(cap, dtype=torch.int32, device=batch.device) for _ in range(3))
+            batch._half_buf = buf
+        rc = lib.nqs_find_pairs_half(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work), _ptr(buf[0]),
+                                     _ptr(buf[1]), _ptr(buf[2]), buf[0].numel(), ctypes.byref(n), _stream(stream))
+        if rc == -4:
+            cap = int(n.value * 1.1) + 4096
+            batch._half_cap = cap
+            continue
+        _check(rc)
+        break
+    else:
+        _check(rc)
+    k = int(n.value)
+    return buf[0][:k], buf[1][:k], buf[2][:k], k
+
+
+def half_h_buffer(n_slots, precision="fp32c", device="cuda", complex_h=False):
+    """Per-record matrix elements of the half-stored path (same layout as pair_h_buffer)."""
+    return pair_h_buffer(n_slots, precision, device, complex_h)
+
+
+def local_energy_half(batch: Batch, logpsi_re, logpsi_im, half, precision="fp32c", out=None, hrec=None,
+                      stream=None):
+    """E_loc^var from half-stored records (symmetric scatter): (eloc_re, eloc_im or None, hdiag)."""
+    dev = batch.device
+    a, b = _f64(logpsi_re, dev), _f64(logpsi_im, dev)
+    ri, rj, rk, ns = half
+    cplx = b is not None or batch.ham.complex
+    if out is None:
+        er = torch.empty(batch.n, dtype=torch.float64, device=dev)
+        ei = torch.empty(batch.n, dtype=torch.float64, device=dev) if cplx else None
+        hd = torch.empty(batch.n, dtype=torch.float64, device=dev)
+    else:
+        er, ei, hd = out
+    _check(_lib.nqs_local_energy_half(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work), _ptr(a), _ptr(b),
+                                      _pair_ptr(ri), _pair_ptr(rj), _pair_ptr(rk), ns, PRECISIONS[precision],
+                                      _ptr(er), _ptr(ei), _ptr(hd),
+                                      _ptr(_check_hpair(hrec, ns, precision, batch.ham.complex)), _stream(stream)))
+    return er, ei, hd
+
+
+def local_energy_backward_half(batch: Batch, logpsi_re, logpsi_im, eloc_re, eloc_im, hdiag, evar, g_eloc_re=None,
+                               g_eloc_im=None, g_evar=None, half=None, precision="fp32c", hrec=None, out=None,
+                               stream=None):
+    """Adjoint over half-stored records (see local_energy_backward): (grad_re, grad_im or None)."""
+    dev = batch.device
+    a, b = _f64(logpsi_re, dev), _f64(logpsi_im, dev)
+    ri, rj, rk, ns = half if half is not None else (None, None, None, 0)
+    if out is None:
+        gr = torch.empty(batch.n, dtype=torch.float64, device=dev)
+        gi = torch.empty(batch.n, dtype=torch.float64, device=dev) if b is not None else None
+    else:
+        gr, gi = out
+    up_re, up_im, up_e = _f64(g_eloc_re, dev), _f64(g_eloc_im, dev), _f64(g_evar, dev)   # held until enqueued
+    _check(_lib.nqs_local_energy_backward_half(
+        batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work), _ptr(a), _ptr(b), _pair_ptr(ri), _pair_ptr(rj),
+        _pair_ptr(rk), ns, _ptr(_check_hpair(hrec, ns, precision, batch.ham.complex)), _ptr(eloc_re), _ptr(eloc_im),
+        _ptr(hdiag), _ptr(evar), _ptr(up_re), _ptr(up_im), _ptr(up_e),
+        PRECISIONS[precision], _ptr(gr), _ptr(gi), _stream(stream)))
+    return gr, gi
+
+
+def gumbel_topk_level(n_qubits, level, parent_x, parent_l, parent_lt, cond_logp, gumbel, K, device="cuda",
+                      stream=None):
+    """One qubit of Alg. 1 (ARGumbelTopK) on the GPU: (child_x [m, W] int64, child_l, child_lt)."""
+    lib = load_library()
+    W = (int(n_qubits) + 63) // 64
+    pl, plt = _f64(parent_l, device), _f64(parent_lt, device)
+    lp = _f64(np.asarray(cond_logp, dtype=np.float64).reshape(-1) if not torch.is_tensor(cond_logp)
+              else cond_logp.reshape(-1), device)
+    g = _f64(np.asarray(gumbel, dtype=np.float64).reshape(-1) if not torch.is_tensor(gumbel)
+             else gumbel.reshape(-1), device)
+    n = int(pl.shape[0])
+    px = None if parent_x is None else _dev_u64(parent_x)
+    m = min(int(K), 2 * n)
+    cx = torch.empty((max(m, 1), W), dtype=torch.int64, device=device)
+    cl = torch.empty(max(m, 1), dtype=torch.float64, device=device)
+    clt = torch.empty(max(m, 1), dtype=torch.float64, device=device)
+    nbytes = int(lib.nqs_gumbel_scratch_bytes(n))
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    out = ctypes.c_int64()
+    _check(lib.nqs_gumbel_topk_level(int(n_qubits), int(level), n, _ptr(px), _ptr(pl), _ptr(plt), _ptr(lp), _ptr(g),
+                                     int(K), _ptr(scratch), nbytes, _ptr(cx), _ptr(cl), _ptr(clt), ctypes.byref(out),
+                                     _stream(stream)))
+    k = int(out.value)
+    return cx[:k], cl[:k], clt[:k]
+
+
+def ar_gumbel_topk(n_qubits, K, cond_logp, gumbel, device="cuda"):
+    """Alg. 1 driven from the host: ``cond_logp(level, prefixes)`` -> [(log p(0|x), log p(1|x))]
+    for the kept prefixes (Python ints), ``gumbel[level]`` -> the level's Gumbel draws (two per
+    kept vector).  Returns (x [K', W] int64 tensor, l, L~) on the device, L~ descending."""
+    W = (int(n_qubits) + 63) // 64
+    x, l, lt = None, torch.zeros(1, dtype=torch.float64, device=device), torch.zeros(1, dtype=torch.float64,
+                                                                                       device=device)
+    for i in range(int(n_qubits)):
+        if x is None:
+            prefixes = [0]
+        else:
+            words = x.cpu().numpy().view(np.uint64)
+            prefixes = [sum(int(words[r, w]) << (64 * w) for w in range(W)) for r in range(words.shape[0])]
+        lp = np.asarray(cond_logp(i, prefixes), dtype=np.float64)
+        g = np.asarray(gumbel[i], dtype=np.float64)[:2 * len(prefixes)]
+        x, l, lt = gumbel_topk_level(n_qubits, i, x, l, lt, lp, g, K, device)
+    return x, l, lt
+
+
+def sr_top(logpsi_re, n_sr, stream=None):
+    """Indices of the n_sr most probable samples (largest Re log psi; ties by index)."""
+    lib = load_library()
+    a = _f64(logpsi_re, "cuda")
+    n = int(a.shape[0])
+    nbytes = int(lib.nqs_sr_scratch_bytes(n, 1))
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=a.device)
+    idx = torch.empty(min(int(n_sr), n), dtype=torch.int32, device=a.device)
+    _check(lib.nqs_sr_top(n, _ptr(a), int(n_sr), _ptr(idx), _ptr(scratch), nbytes, _stream(stream)))
+    return idx
+
+
+def sr_step(O, logpsi_re, eloc_re, evar, lam, want_T=False, stream=None):
+    """min-SR step on the GPU: (delta [n_params] FP64, T [n_sr, n_sr] FP64 or None).
+
+    O: [n_sr, n_params] FP32 CUDA tensor of d log psi / d theta (real); evar: E
+    (device tensor whose first entry is used, or a float)."""
+    lib = load_library()
+    O = O.to(dtype=torch.float32).contiguous()
+    dev = O.device
+    n, P = int(O.shape[0]), int(O.shape[1])
+    a, el = _f64(logpsi_re, dev), _f64(eloc_re, dev)
+    ev = _f64(evar if torch.is_tensor(evar) else np.array([float(evar)]), dev)
+    nbytes = int(lib.nqs_sr_scratch_bytes(1, P))
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    delta = torch.empty(P, dtype=torch.float64, device=dev)
+    T = torch.empty((n, n), dtype=torch.float64, device=dev) if want_T else None
+    _check(lib.nqs_sr_step(n, P, _ptr(O), _ptr(a), _ptr(el), _ptr(ev), float(lam), _ptr(delta), _ptr(T), _ptr(scratch),
+                           nbytes, _stream(stream)))
+    return delta, T
+
+
+class FullCandidates:
+    """Candidates of the exact local energy (Eq. local_energy) for a staged batch.
+
+    ``cand_id`` / ``hval``: [n_unq, n_xy] (int32 holding uint32 candidate
+    indices, FP64 matrix elements), ``cand``: [n_cand, W] distinct candidates
+    in increasing numeric order, ``in_u``: index of each candidate in U or -1.
+    """
+
+    def __init__(self, batch, cand_id, hval, cand, in_u, scratch):
+        self.batch, self.cand_id, self.hval, self.cand, self.in_u = batch, cand_id, hval, cand, in_u
+        self.scratch = scratch
+
+    @property
+    def n_cand(self):
+        return int(self.cand.shape[0])
+
+
+def full_candidates(batch: Batch, with_h=True, stream=None):
+    """Every x XOR XY of every sample, deduplicated over the batch (nqs_full_candidates)."""
+    lib = load_library()
+    ham = batch.ham
+    n_xy = int(ham.info["n_xy"])
+    dev = batch.device
+    nbytes = int(lib.nqs_candidates_scratch_bytes(ham.handle, batch.n))
+    if nbytes < 0:
+        _check(nbytes)
+    scratch = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
+    cand_id = torch.empty((batch.n, n_xy), dtype=torch.int32, device=dev)
+    hval = torch.empty((batch.n, n_xy), dtype=torch.float64, device=dev) if with_h else None
+    n = ctypes.c_int64()
+    cap = max(batch.n * n_xy // 4, 1024)
+    for _ in range(2):
+        cand = torch.empty((cap, ham.n_words), dtype=torch.int64, device=dev)
+        in_u = torch.empty(cap, dtype=torch.int32, device=dev)
+        rc = lib.nqs_full_candidates(ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work), _ptr(scratch),
+                                     scratch.numel(), _ptr(cand_id), _ptr(hval), _ptr(cand), _ptr(in_u), cap,
+                                     ctypes.byref(n), _stream(stream))
+        if rc == -4 and n.value > cap:
+            cap = int(n.value)
+            continue
+        _check(rc)
+        break
+    k = int(n.value)
+    return FullCandidates(batch, cand_id, hval, cand[:k], in_u[:k], scratch)
+
+
+def local_energy_full(fc: FullCandidates, logpsi_re, logpsi_im, cand_logpsi_re, cand_logpsi_im=None,
+                      out=None, stream=None):
+    """Exact E_loc (Eq. local_energy) from the candidates' log-amplitudes: (eloc_re, eloc_im or None)."""
+    batch = fc.batch
+    dev = batch.device
+    a, b = _f64(logpsi_re, dev), _f64(logpsi_im, dev)
+    ca, cb = _f64(cand_logpsi_re, dev), _f64(cand_logpsi_im, dev)
+    cplx = b is not None or cb is not None
+    if out is None:
+        er = torch.empty(batch.n, dtype=torch.float64, device=dev)
+        ei = torch.empty(batch.n, dtype=torch.float64, device=dev) if cplx else None
+    else:
+        er, ei = out
+    _check(_lib.nqs_local_energy_full(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work), _ptr(a), _ptr(b),
+                                      _ptr(fc.cand_id), _ptr(fc.hval), fc.n_cand, _ptr(ca), _ptr(cb),
+                                      _ptr(fc.scratch), fc.scratch.numel(), _ptr(er), _ptr(ei), _stream(stream)))
+    return er, ei
+
+
 class _Instance(ctypes.Structure):
     _fields_ = [("ham", ctypes.c_void_p), ("U", ctypes.c_void_p), ("n_unq", ctypes.c_int64),
-                ("logpsi_re", ctypes.c_void_p), ("eloc_re", ctypes.c_void_p), ("evar", ctypes.c_void_p)]
+                ("logpsi_re", ctypes.c_void_p), ("eloc_re", ctypes.c_void_p), ("evar", ctypes.c_void_p),
+                ("grad", ctypes.c_void_p)]
 
 
 class BatchedPlan:
@@ -538,13 +788,14 @@ class BatchedPlan:
     are kept as device tensors whose contents may be overwritten between
     runs (same sizes).  ``run()`` launches the graph asynchronously; results
     are ``eloc[i]`` (E_loc^var) and ``evar[i]`` ([E^var, max log psi, sum of
-    weights]).  ``autotune`` times both pair-search schedules per instance
-    at planning time.
+    weights]).  ``autotune`` times the pair-search schedules and their launch
+    parameters per instance at planning time.  With ``gradients`` every run
+    also writes ``grad[i]`` = dE^var / d Re log psi (the adjoint's closed form).
     """
 
-    def __init__(self, items, precision="fp32c", autotune=True, stream=None):
+    def __init__(self, items, precision="fp32c", autotune=True, gradients=False, stream=None):
         lib = load_library()
-        self.hams, self.U, self.logpsi, self.eloc, self.evar = [], [], [], [], []
+        self.hams, self.U, self.logpsi, self.eloc, self.evar, self.grad = [], [], [], [], [], []
         arr = (_Instance * len(items))()
         for i, (ham, U, lre) in enumerate(items):
             Ud = _dev_u64(U)
@@ -553,10 +804,11 @@ class BatchedPlan:
             a = _f64(lre, Ud.device)
             er = torch.zeros(Ud.shape[0], dtype=torch.float64, device=Ud.device)
             ev = torch.zeros(3, dtype=torch.float64, device=Ud.device)
+            gr = torch.zeros(Ud.shape[0], dtype=torch.float64, device=Ud.device) if gradients else None
             self.hams.append(ham); self.U.append(Ud); self.logpsi.append(a)
-            self.eloc.append(er); self.evar.append(ev)
+            self.eloc.append(er); self.evar.append(ev); self.grad.append(gr)
             arr[i] = _Instance(ham.handle.value, Ud.data_ptr(), Ud.shape[0], a.data_ptr(), er.data_ptr(),
-                               ev.data_ptr())
+                               ev.data_ptr(), None if gr is None else gr.data_ptr())
         h = ctypes.c_void_p()
         _check(lib.nqs_batch_plan(arr, len(items), PRECISIONS[precision], 1 if autotune else 0,
                                   ctypes.byref(h), _stream(stream)))
@@ -574,8 +826,11 @@ class BatchedPlan:
         v = (ctypes.c_int64 * 8)()
         _check(_lib.nqs_batch_info(self._h, int(i), v))
         sched = {v2: k for k, v2 in SCHEDULES.items()}[int(v[0])]
+        t = (ctypes.c_int32 * 3)()
+        _check(_lib.nqs_batch_tune(self._h, int(i), t))
         return {"schedule": sched, "capacity": v[1], "planned_pairs": v[2], "graph_nodes": v[3],
-                "t_terms_us": v[4], "t_batch_us": v[5], "t_trie_us": v[6], "graph_kernels": v[7]}
+                "t_terms_us": v[4], "t_batch_us": v[5], "t_trie_us": v[6], "graph_kernels": v[7],
+                "tune": {"terms_grab": t[0], "terms_groups": t[1], "trie_pop": t[2]}}
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

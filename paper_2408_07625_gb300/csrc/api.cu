@@ -118,7 +118,7 @@ static void free_ham(nqs_ham* h) {
   cudaFree(h->coef_f); cudaFree(h->srch_hash); cudaFree(h->srch_id); cudaFree(h->srch_rec); cudaFree(h->hash_basis);
   cudaFree(h->xy_table); cudaFree(h->wmask); cudaFree(h->xy_trie); cudaFree(h->xy_hash); cudaFree(h->segs);
   cudaFree(h->fm); cudaFree(h->fv_d); cudaFree(h->fv_f); cudaFree(h->fz); cudaFree(h->quad_d);
-  cudaFree(h->quad_f);
+  cudaFree(h->quad_f); cudaFree(h->coef_im); cudaFree(h->coef_f_im); cudaFree(h->fv_d_im); cudaFree(h->fv_f_im);
   delete h;
 }
 
@@ -196,15 +196,13 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
     if (h != 0.0) merged.push_back({idx[a], h});
     a = b;
   }
-  // odd |Y| -> complex matrix elements (outside version 1)
+  nqs_ham* h = new nqs_ham();
+  // a string with an odd number of Y has an imaginary coefficient h i^{|Y|}: complex H
   for (auto& m : merged) {
     uint64_t y[kMaxWords];
     for (int w = 0; w < W; ++w) y[w] = x_mask[m.first * W + w] & z_mask[m.first * W + w];
-    if (popc_words(y, W) & 1)
-      return fail(NQS_ERR_UNSUPPORTED, "a Pauli string has an odd number of Y (complex H)");
+    if (popc_words(y, W) & 1) h->cplx = 1;
   }
-
-  nqs_ham* h = new nqs_ham();
   h->n_qubits = n_qubits;
   h->W = W;
   cudaGetDevice(&h->device);
@@ -241,7 +239,8 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
   h->h_row_ptr.assign(G + 1, 0);
   h->h_yz.assign(M * W, 0);
   h->h_coef.assign(M, 0.0);
-  std::vector<float2> coef_f(M);
+  h->h_coef_im.assign(M, 0.0);
+  std::vector<float2> coef_f(M), coef_f_im(M);
   int64_t t = 0;
   for (int64_t p = 0; p < G; ++p) {
     int64_t g = order[p];
@@ -256,12 +255,15 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
         h->h_yz[t * W + w] = z_mask[src * W + w];
         y[w] = x_mask[src * W + w] & z_mask[src * W + w];
       }
-      // <x|P|x'> = i^{|Y|} (-1)^{|x' & YZ|}; |Y| even -> i^{|Y|} = (-1)^{|Y|/2}
-      double c = merged[a].h * (((popc_words(y, W) / 2) & 1) ? -1.0 : 1.0);
-      h->h_coef[t] = c;
+      // <x|P|x'> = i^{|Y|} (-1)^{|x' & YZ|}: |Y| even -> i^{|Y|} = (-1)^{|Y|/2} (real),
+      // |Y| odd -> i^{|Y|} = i (-1)^{(|Y|-1)/2} (imaginary)
+      const int ny = popc_words(y, W);
+      const double c = merged[a].h * (((ny / 2) & 1) ? -1.0 : 1.0);
+      double& dst = (ny & 1) ? h->h_coef_im[t] : h->h_coef[t];
+      dst = c;
       float hi = (float)c;
       float lo = (float)(c - (double)hi);
-      coef_f[t] = make_float2(hi, lo);
+      ((ny & 1) ? coef_f_im[t] : coef_f[t]) = make_float2(hi, lo);
     }
   }
   h->h_row_ptr[G] = t;
@@ -283,7 +285,7 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
   };
   const int NQ = 64 * W;
   std::vector<int4> fm(G, make_int4(kForm::Terms, 0, 0, 0));
-  std::vector<double> fv;
+  std::vector<double> fv, fv_im;   // real and imaginary parts of the local tables
   std::vector<uint64_t> fz;
   for (int64_t p = h->has_diag; p < G; ++p) {
     const int64_t t0 = h->h_row_ptr[p], t1 = h->h_row_ptr[p + 1];
@@ -300,15 +302,19 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
         for (uint64_t m = xy[w]; m; m &= m - 1) q[n++] = 64 * w + __builtin_ctzll(m);
       uint32_t packed = 0;
       for (int i = 0; i < nb; ++i) packed |= (uint32_t)q[i] << (8 * i);
-      std::vector<CSum> T(1u << nb);
+      std::vector<CSum> T(1u << nb), Ti(1u << nb);
       for (int64_t t = t0; t < t1; ++t) {
         uint32_t bl = 0;  // YZ_l on the pattern's qubits, compressed
         for (int i = 0; i < nb; ++i) bl |= (uint32_t)((h->h_yz[t * W + q[i] / 64] >> (q[i] % 64)) & 1ull) << i;
-        for (uint32_t u = 0; u < (1u << nb); ++u)
-          T[u].add((__builtin_popcount(u & bl) & 1) ? -h->h_coef[t] : h->h_coef[t]);
+        for (uint32_t u = 0; u < (1u << nb); ++u) {
+          const bool neg = __builtin_popcount(u & bl) & 1;
+          if (h->h_coef[t] != 0.0) T[u].add(neg ? -h->h_coef[t] : h->h_coef[t]);
+          if (h->h_coef_im[t] != 0.0) Ti[u].add(neg ? -h->h_coef_im[t] : h->h_coef_im[t]);
+        }
       }
       fm[p] = make_int4(kForm::Local | (nb << 4), (int)fv.size(), (int)(fz.size() / W), (int)packed);
       for (auto& v : T) fv.push_back(v.value());
+      for (auto& v : Ti) fv_im.push_back(v.value());
       for (int w = 0; w < W; ++w) fz.push_back(h->h_yz[t0 * W + w] & ~xy[w]);
       ++h->n_local;
     }
@@ -316,6 +322,7 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
   if (fv.size() >= (size_t)INT32_MAX || fz.size() / W >= (size_t)INT32_MAX) {
     std::fill(fm.begin(), fm.end(), make_int4(kForm::Terms, 0, 0, 0));  // tables too large to index
     fv.clear();
+    fv_im.clear();
     fz.clear();
   }
   std::vector<double> quad_d;
@@ -350,7 +357,7 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
     }
     return f;
   };
-  const std::vector<float2> fv_f = split(fv), quad_f = split(quad_d);
+  const std::vector<float2> fv_f = split(fv), quad_f = split(quad_d), fv_f_im = split(fv_im);
 
   // linear hash basis: h(v) = XOR over set bits b of R[b] (GF(2)-linear, so
   // h(x ^ xy) = h(x) ^ h(xy) and a candidate's hash costs one XOR)
@@ -461,7 +468,9 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
       (rc = upload(&h->wmask, wmask)) || (rc = upload(&h->xy_trie, xy_trie)) ||
       (rc = upload(&h->xy_hash, hxy)) || (rc = upload(&h->segs, segs)) || (rc = upload(&h->fm, fm)) ||
       (rc = upload(&h->fv_d, fv)) || (rc = upload(&h->fv_f, fv_f)) || (rc = upload(&h->fz, fz)) ||
-      (rc = upload(&h->quad_d, quad_d)) || (rc = upload(&h->quad_f, quad_f))) {
+      (rc = upload(&h->quad_d, quad_d)) || (rc = upload(&h->quad_f, quad_f)) ||
+      (rc = upload(&h->coef_im, h->h_coef_im)) || (rc = upload(&h->coef_f_im, coef_f_im)) ||
+      (rc = upload(&h->fv_d_im, fv_im)) || (rc = upload(&h->fv_f_im, fv_f_im))) {
     free_ham(h);
     return rc;
   }
@@ -478,6 +487,14 @@ int nqs_ham_info(const nqs_ham* h, int64_t info[8]) {
   if (!h || !info) return fail(NQS_ERR_ARG, "null argument");
   info[0] = h->n_qubits; info[1] = h->W; info[2] = h->n_terms; info[3] = h->n_xy;
   info[4] = h->has_diag; info[5] = h->max_group; info[6] = h->n_srch; info[7] = h->heavy_end;
+  return NQS_OK;
+}
+
+int nqs_ham_is_complex(const nqs_ham* h) { return h ? h->cplx : 0; }
+
+int nqs_ham_export_im(const nqs_ham* h, double* coef_im) {
+  if (!h || !coef_im) return fail(NQS_ERR_ARG, "null argument");
+  std::copy(h->h_coef_im.begin(), h->h_coef_im.end(), coef_im);
   return NQS_OK;
 }
 
@@ -737,6 +754,7 @@ int nqs_full_candidates(const nqs_ham* ham, const uint64_t* U, int64_t n, void* 
   if (rc) return rc;
   if (!n_cand) return fail(NQS_ERR_ARG, "null n_cand");
   *n_cand = 0;
+  if (ham->cplx) return fail(NQS_ERR_UNSUPPORTED, "exact local energy of a complex Hamiltonian");
   if (n == 0 || ham->n_xy == 0) return NQS_OK;
   if (!scratch || !cand_id) return fail(NQS_ERR_ARG, "null scratch or cand_id");
   if (((uintptr_t)scratch) & 255) return fail(NQS_ERR_ARG, "scratch not 256-byte aligned");
@@ -758,6 +776,7 @@ int nqs_local_energy_full(const nqs_ham* ham, const uint64_t* U, int64_t n, void
   StageHeader L;
   int rc = check_work(ham, U, n, work, &L);
   if (rc) return rc;
+  if (ham->cplx) return fail(NQS_ERR_UNSUPPORTED, "exact local energy of a complex Hamiltonian");
   if (n == 0) return NQS_OK;
   if (!a || !eloc_re) return fail(NQS_ERR_ARG, "null logpsi_re or eloc_re");
   if ((b || cb) && !eloc_im) return fail(NQS_ERR_ARG, "complex amplitudes need eloc_im");
@@ -767,6 +786,132 @@ int nqs_local_energy_full(const nqs_ham* ham, const uint64_t* U, int64_t n, void
   cudaError_t e = launch_local_energy_full(n, ham->n_xy, (const char*)work, L, a, b, cand_id, hval, n_cand, ca, cb,
                                            scratch, eloc_re, eloc_im, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "full local energy kernels");
+  return NQS_OK;
+}
+
+int64_t nqs_sr_scratch_bytes(int64_t n_unq, int64_t n_params) {
+  if (n_unq < 0 || n_params < 0) return fail(NQS_ERR_ARG, "negative size");
+  return std::max(sr_scratch_bytes(n_params), sr_top_scratch_bytes(n_unq));
+}
+
+int nqs_sr_top(int64_t n_unq, const double* logpsi_re, int64_t n_sr, int32_t* idx, void* scratch,
+               int64_t scratch_bytes, void* stream) {
+  if (n_unq < 1 || n_sr < 1 || !logpsi_re || !idx) return fail(NQS_ERR_ARG, "bad argument to nqs_sr_top");
+  if (n_unq >= (int64_t(1) << 31)) return fail(NQS_ERR_UNSUPPORTED, "more than 2^31 samples");
+  if (!scratch || scratch_bytes < sr_top_scratch_bytes(n_unq)) return fail(NQS_ERR_CAPACITY, "scratch too small");
+  if (((uintptr_t)scratch) & 255) return fail(NQS_ERR_ARG, "scratch not 256-byte aligned");
+  cudaError_t e = launch_sr_top(n_unq, logpsi_re, n_sr, idx, scratch, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "top-probability selection");
+  return NQS_OK;
+}
+
+int nqs_sr_step(int n_sr, int64_t n_params, const float* O, const double* logpsi_re, const double* eloc_re,
+                const double* evar, double lambda, double* delta, double* T, void* scratch, int64_t scratch_bytes,
+                void* stream) {
+  if (n_sr < 1 || n_sr > 128) return fail(NQS_ERR_UNSUPPORTED, "n_sr must be in 1..128");
+  if (n_params < 1 || !O || !logpsi_re || !eloc_re || !evar || !delta) return fail(NQS_ERR_ARG, "bad argument to nqs_sr_step");
+  if (!(lambda >= 0.0)) return fail(NQS_ERR_ARG, "lambda must be >= 0");
+  if (!scratch || scratch_bytes < sr_scratch_bytes(n_params)) return fail(NQS_ERR_CAPACITY, "scratch too small");
+  if (((uintptr_t)scratch) & 255) return fail(NQS_ERR_ARG, "scratch not 256-byte aligned");
+  int32_t st = 0;
+  cudaError_t e = launch_sr_step(n_sr, n_params, O, logpsi_re, eloc_re, evar, lambda, scratch, delta, T, &st,
+                                 (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "SR kernels");
+  if (st & kStatusLimit) return fail(NQS_ERR_DEVICE_LIMIT, "tensor-core pipeline wait ran out");
+  if (st & kStatusRange) return fail(NQS_ERR_RANGE, "T + lambda I is not positive definite in FP64");
+  return NQS_OK;
+}
+
+int64_t nqs_gumbel_scratch_bytes(int64_t n_parents) {
+  if (n_parents < 0) return fail(NQS_ERR_ARG, "negative n_parents");
+  return sample_scratch_bytes(n_parents);
+}
+
+int nqs_gumbel_topk_level(int n_qubits, int level, int64_t n_parents, const uint64_t* parent_x,
+                          const double* parent_l, const double* parent_lt, const double* cond_logp,
+                          const double* gumbel, int64_t K, void* scratch, int64_t scratch_bytes, uint64_t* child_x,
+                          double* child_l, double* child_lt, int64_t* n_children, void* stream) {
+  if (!n_children) return fail(NQS_ERR_ARG, "null n_children");
+  *n_children = 0;
+  if (n_qubits < 1 || n_qubits > 64 * kMaxWords) return fail(NQS_ERR_ARG, "n_qubits out of range");
+  if (level < 0 || level >= n_qubits) return fail(NQS_ERR_ARG, "level out of range");
+  if (n_parents < 1 || K < 1) return fail(NQS_ERR_ARG, "n_parents and K must be positive");
+  if (n_parents >= (int64_t(1) << 30)) return fail(NQS_ERR_UNSUPPORTED, "more than 2^30 kept vectors");
+  if ((level > 0 && !parent_x) || !parent_l || !parent_lt || !cond_logp || !gumbel || !child_x || !child_l || !child_lt)
+    return fail(NQS_ERR_ARG, "null array");
+  if (!scratch || scratch_bytes < sample_scratch_bytes(n_parents)) return fail(NQS_ERR_CAPACITY, "scratch too small");
+  if (((uintptr_t)scratch) & 255) return fail(NQS_ERR_ARG, "scratch not 256-byte aligned");
+  cudaError_t e = launch_gumbel_level((n_qubits + 63) / 64, level, n_parents, parent_x, parent_l, parent_lt, cond_logp,
+                                      gumbel, K, scratch, child_x, child_l, child_lt, n_children, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sampling kernels");
+  return NQS_OK;
+}
+
+int nqs_find_pairs_half(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, uint32_t* rec_i,
+                        uint32_t* rec_j, uint32_t* rec_k, int64_t capacity, int64_t* n_slots, void* stream) {
+  StageHeader L;
+  int rc = check_work(ham, U, n, work, &L);
+  if (rc) return rc;
+  if (!n_slots) return fail(NQS_ERR_ARG, "null n_slots");
+  *n_slots = 0;
+  if (capacity < 0 || (capacity > 0 && (!rec_i || !rec_j || !rec_k))) return fail(NQS_ERR_ARG, "null record arrays");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_find_half(ham, U, (char*)work, L, rec_i, rec_j, rec_k, capacity, s);
+  if (e != cudaSuccess) return cuda_fail(e, "half-pair search kernel");
+  int64_t cur[2] = {0, 0};
+  e = cudaMemcpyAsync(cur, (char*)work + L.off_counters + 8 * kCtrHalf, sizeof(cur), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "slot count copy");
+  if ((rc = read_status(work, s))) return rc;
+  *n_slots = cur[0];
+  if (cur[1] != 0) return fail(NQS_ERR_CAPACITY, "record capacity too small (n_slots: slots asked for)");
+  return NQS_OK;
+}
+
+int nqs_local_energy_half(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, const double* a,
+                          const double* b, const uint32_t* rec_i, const uint32_t* rec_j, const uint32_t* rec_k,
+                          int64_t n_slots, int precision, double* eloc_re, double* eloc_im, double* hdiag,
+                          void* hrec, void* stream) {
+  StageHeader L;
+  int rc = check_work(ham, U, n, work, &L);
+  if (rc) return rc;
+  if (precision != NQS_PREC_FP64 && precision != NQS_PREC_FP32C) return fail(NQS_ERR_ARG, "bad precision");
+  if (n > 0 && (!a || !eloc_re)) return fail(NQS_ERR_ARG, "null logpsi_re or eloc_re");
+  if ((b || ham->cplx) && !eloc_im) return fail(NQS_ERR_ARG, "complex log psi or H needs eloc_im");
+  if (n_slots < 0 || (n_slots > 0 && (!rec_i || !rec_j || !rec_k))) return fail(NQS_ERR_ARG, "null record arrays");
+  if (n == 0) return NQS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_amplitudes(a, b, n, precision, (char*)work, L, s);
+  if (e != cudaSuccess) return cuda_fail(e, "amplitude kernel");
+  e = launch_local_energy_half(ham, U, n, (const char*)work, L, b != nullptr, rec_i, rec_j, rec_k, n_slots, precision,
+                               eloc_re, eloc_im, hdiag, hrec, s);
+  if (e != cudaSuccess) return cuda_fail(e, "half-pair energy kernels");
+  return NQS_OK;
+}
+
+int nqs_local_energy_backward_half(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, const double* a,
+                                   const double* b, const uint32_t* rec_i, const uint32_t* rec_j,
+                                   const uint32_t* rec_k, int64_t n_slots, const void* hrec, const double* eloc_re,
+                                   const double* eloc_im, const double* hdiag, const double* evar,
+                                   const double* g_re, const double* g_im, const double* g_evar, int precision,
+                                   double* grad_re, double* grad_im, void* stream) {
+  StageHeader L;
+  int rc = check_work(ham, U, n, work, &L);
+  if (rc) return rc;
+  if (precision != NQS_PREC_FP64 && precision != NQS_PREC_FP32C) return fail(NQS_ERR_ARG, "bad precision");
+  if (n > 0 && (!a || !eloc_re || !evar || !grad_re)) return fail(NQS_ERR_ARG, "null forward input or grad_re");
+  if (b && (!grad_im || !eloc_im)) return fail(NQS_ERR_ARG, "complex log psi needs grad_im and eloc_im");
+  if (ham->cplx && !eloc_im) return fail(NQS_ERR_ARG, "a complex Hamiltonian needs eloc_im");
+  const bool pairs_needed = g_re || g_im;
+  if (pairs_needed && (!hdiag || n_slots < 0 || (n_slots > 0 && (!rec_i || !rec_j || !rec_k))))
+    return fail(NQS_ERR_ARG, "upstream E_loc gradient needs the records and hdiag");
+  if (n == 0) return NQS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (pairs_needed && (e = launch_amplitudes(a, b, n, precision, (char*)work, L, s)) != cudaSuccess)
+    return cuda_fail(e, "amplitude kernel");
+  e = launch_backward_half(ham, U, n, (char*)work, L, b != nullptr, a, rec_i, rec_j, rec_k, n_slots, hrec, eloc_re,
+                           eloc_im, hdiag, evar, g_re, g_im, g_evar, precision, grad_re, grad_im, s);
+  if (e != cudaSuccess) return cuda_fail(e, "half-pair adjoint kernels");
   return NQS_OK;
 }
 
@@ -782,6 +927,7 @@ int nqs_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n, void* wor
   if (n > 0 && !a) return fail(NQS_ERR_ARG, "null logpsi_re");
   if (!eloc_re) return fail(NQS_ERR_ARG, "null eloc_re");
   if (b && !eloc_im) return fail(NQS_ERR_ARG, "complex log psi needs eloc_im");
+  if (ham->cplx && !eloc_im) return fail(NQS_ERR_ARG, "a complex Hamiltonian needs eloc_im");
   if (re > rb && (!row_ptr || !pair_j || !pair_k)) return fail(NQS_ERR_ARG, "null pair arrays");
   if (re == rb) return NQS_OK;
   cudaStream_t s = (cudaStream_t)stream;
@@ -842,6 +988,7 @@ int nqs_local_energy_backward(const nqs_ham* ham, const uint64_t* U, int64_t n, 
   if (n > 0 && (!a || !eloc_re || !evar)) return fail(NQS_ERR_ARG, "null forward input");
   if (!grad_re) return fail(NQS_ERR_ARG, "null grad_re");
   if (b && (!grad_im || !eloc_im)) return fail(NQS_ERR_ARG, "complex log psi needs grad_im and eloc_im");
+  if (ham->cplx && !eloc_im) return fail(NQS_ERR_ARG, "a complex Hamiltonian needs eloc_im");
   const bool pairs_needed = g_re || g_im;
   if (pairs_needed && re > rb && (!row_ptr || !pair_j || !pair_k || !hdiag))
     return fail(NQS_ERR_ARG, "upstream E_loc gradient needs pairs and hdiag");

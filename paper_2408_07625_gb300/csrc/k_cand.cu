@@ -56,6 +56,7 @@ struct CandScratch {
   uint64_t* kb;                   // [entries][W] sort buffer
   int32_t* ib;                    // [entries] sort payload buffer
   int32_t* hist;                  // [256 * sort_blocks(entries)]
+  int32_t* partial;               // [sort_scan_partials(entries)]
   int64_t bytes;
 };
 
@@ -74,6 +75,7 @@ static CandScratch cand_scratch_view(char* base, int64_t entries, int W) {
   v.kb = (uint64_t*)take(8 * W * m);
   v.ib = (int32_t*)take(4 * m);
   v.hist = (int32_t*)take(4 * 256 * sort_blocks(m));
+  v.partial = (int32_t*)take(4 * sort_scan_partials(m));
   v.bytes = off;
   return v;
 }
@@ -135,31 +137,38 @@ __device__ __forceinline__ uint32_t cand_insert(const CandArgs& a, const uint64_
   return 0u;
 }
 
-// One warp per sample: lanes take the patterns in rounds of 32.  Matrix
-// elements in FP64 as in the E_loc^var kernel (the diagonal by its quadratic
-// form or term loop, heavy term-form patterns by the whole warp, the rest
-// one lane each).
+// Work unit of a warp: one sample and a tile of kCandTile consecutive
+// patterns (lanes take them in rounds of 32), so that few samples with many
+// patterns still fill the GPU.  Matrix elements in FP64 as in the E_loc^var
+// kernel (the diagonal by its quadratic form or term loop, heavy term-form
+// patterns by the whole warp, the rest one lane each).
+constexpr int kCandTile = 1024;
+
 template <int W>
 __global__ void __launch_bounds__(kCandThreads) cand_insert_kernel(const CandArgs a, const Melem M) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * kCandWarps;
-  for (int64_t i = blockIdx.x * (int64_t)kCandWarps + (threadIdx.x >> 5); i < a.n_unq; i += nw) {
+  const int64_t k_first = M.has_diag ? 1 : 0;
+  const int64_t tpr = (a.n_xy - k_first + kCandTile - 1) / kCandTile;   // tiles per sample
+  const int64_t n_tiles = a.n_unq * (tpr > 0 ? tpr : 1);
+  for (int64_t t = blockIdx.x * (int64_t)kCandWarps + (threadIdx.x >> 5); t < n_tiles; t += nw) {
+    const int64_t i = tpr > 0 ? t / tpr : t;
+    const int64_t tc = tpr > 0 ? t - i * tpr : 0;
     uint64_t x[W];
     load_words<W>(a.U + i * W, x);
     const uint32_t hxi = __ldg(a.hx + i);
     const uint64_t e0 = (uint64_t)i * (uint64_t)a.n_xy;
-    int64_t k0 = 0;
-    if (M.has_diag) {  // pattern 0: x' = x
-      const double hd = melem_diag<PolicyD, W>(x, M);
+    if (M.has_diag && tc == 0) {  // pattern 0: x' = x, with the sample's first tile
+      const double hd = a.hval ? melem_diag<PolicyD, W>(x, M) : 0.0;
       if (lane == 0) {
         a.cand_id[e0] = cand_insert<W>(a, x, hxi ^ __ldg(a.xy_hash), e0);
         if (a.hval) a.hval[e0] = hd;
       }
-      k0 = 1;
     }
-    for (int64_t kb = k0; kb < a.n_xy; kb += 32) {
+    const int64_t k_end = min(a.n_xy, k_first + (tc + 1) * kCandTile);
+    for (int64_t kb = k_first + tc * kCandTile; kb < k_end; kb += 32) {
       const int64_t k = kb + lane;
-      const bool have = k < a.n_xy;
+      const bool have = k < k_end;
       uint64_t c[W];
 #pragma unroll
       for (int w = 0; w < W; ++w) c[w] = have ? x[w] ^ __ldg(a.xy + k * W + w) : 0ull;
@@ -189,49 +198,75 @@ __global__ void __launch_bounds__(kCandThreads) cand_insert_kernel(const CandArg
   }
 }
 
-// occupied slots -> unsorted unique keys and their slots (warp-aggregated cursor)
+// occupied slots -> unsorted unique keys and their slots.  A block owns a
+// chunk of kCompactChunk consecutive slots: it counts them, takes its places
+// with one atomic, then writes them in slot order (the chunk is re-read from
+// L2).
+constexpr int kCompactChunk = 8192;
+
 template <int W>
-__global__ void cand_compact_kernel(const CandArgs a, uint64_t* __restrict__ ukeys, int32_t* __restrict__ uslot) {
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256) cand_compact_kernel(const CandArgs a, uint64_t* __restrict__ ukeys,
+                                                           int32_t* __restrict__ uslot) {
+  __shared__ uint32_t wcnt[8];
+  __shared__ unsigned long long s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t cap = 1ull << a.lg;
-  for (uint64_t s0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) - lane; s0 < cap;
-       s0 += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t s = s0 + lane;
-    const unsigned long long v = s < cap ? a.table[s] : kEmptySlot;
+  const uint64_t s0 = (uint64_t)blockIdx.x * kCompactChunk;
+  const uint64_t s1 = s0 + kCompactChunk < cap ? s0 + kCompactChunk : cap;
+  uint32_t cnt = 0;
+  for (uint64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) cnt += a.table[s] != kEmptySlot ? 1u : 0u;
+  cnt = __reduce_add_sync(kFull, cnt);
+  if (lane == 0) wcnt[warp] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < 8; ++w) t += wcnt[w];
+    s_base = t ? atomicAdd(a.counters, (unsigned long long)t) : 0ull;
+  }
+  __syncthreads();
+  unsigned long long run = s_base;
+  for (uint64_t t0 = s0; t0 < s1; t0 += blockDim.x) {
+    const uint64_t s = t0 + threadIdx.x;
+    const unsigned long long v = s < s1 ? a.table[s] : kEmptySlot;
     const bool occ = v != kEmptySlot;
     const uint32_t m = __ballot_sync(kFull, occ);
-    if (!m) continue;
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(a.counters, (unsigned long long)__popc(m));
-    base = __shfl_sync(kFull, base, 0);
+    __syncthreads();
+    if (lane == 0) wcnt[warp] = __popc(m);
+    __syncthreads();
+    uint32_t off = 0, total = 0;
+    for (int w = 0; w < 8; ++w) {
+      off += w < warp ? wcnt[w] : 0u;
+      total += wcnt[w];
+    }
     if (occ) {
-      const uint64_t u = base + __popc(m & ((1u << lane) - 1u));
+      const uint64_t u = run + off + __popc(m & ((1u << lane) - 1u));
       uint64_t c[W];
       entry_key<W>(a, v >> 32, c);
 #pragma unroll
       for (int w = 0; w < W; ++w) ukeys[u * W + w] = c[w];
       uslot[u] = (int32_t)s;
     }
+    run += total;
   }
 }
 
 // sorted rank u -> slot_uid[slot]; membership of the candidate in U
+// (the candidate's linear hash, which the staged table of U is keyed by, is
+// the tag its slot keeps)
 template <int W>
 __global__ void cand_assign_kernel(int64_t n_c, const uint64_t* __restrict__ keys, const int32_t* __restrict__ slots,
                                    int32_t* __restrict__ slot_uid, int32_t* __restrict__ in_u,
                                    const unsigned long long* __restrict__ utable, int64_t capmask,
-                                   const uint32_t* __restrict__ basis, const uint64_t* __restrict__ U,
+                                   const unsigned long long* __restrict__ ctable, const uint64_t* __restrict__ U,
                                    unsigned long long* counters) {
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n_c; u += (int64_t)gridDim.x * blockDim.x) {
-    slot_uid[slots[u]] = (int32_t)u;
+    const int32_t sl = slots[u];
+    slot_uid[sl] = (int32_t)u;
     if (!in_u) continue;
     uint64_t c[W];
-    uint32_t h = 0;
+    const uint32_t h = (uint32_t)ctable[sl];
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-      c[w] = keys[u * W + w];
-      for (uint64_t m = c[w]; m; m &= m - 1) h ^= __ldg(basis + 64 * w + (__ffsll((long long)m) - 1));
-    }
+    for (int w = 0; w < W; ++w) c[w] = keys[u * W + w];
     int32_t j = -1;
     int64_t b = h & capmask;
     bool done = false;
@@ -281,10 +316,12 @@ static cudaError_t cand_w(const nqs_ham* ham, const uint64_t* U, int64_t n, cons
   if ((e = cudaMemsetAsync(sc.counters, 0, 256, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(sc.table, 0xFF, 8 * sc.cap, s)) != cudaSuccess) return e;
   const int sms = num_sms();
-  const int rows_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kCandWarps - 1) / kCandWarps, 8 * sms));
-  cand_insert_kernel<W><<<rows_blocks, kCandThreads, 0, s>>>(a, melem_tables(ham, n));
-  const int tb = (int)std::max<int64_t>(1, std::min<int64_t>(sc.cap / 256, 16 * sms));
-  cand_compact_kernel<W><<<tb, 256, 0, s>>>(a, sc.ukeys, sc.uslot);
+  const int64_t k_first = ham->has_diag ? 1 : 0;
+  const int64_t tiles = n * std::max<int64_t>(1, (ham->n_xy - k_first + kCandTile - 1) / kCandTile);
+  const int ins_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((tiles + kCandWarps - 1) / kCandWarps, 16 * sms));
+  cand_insert_kernel<W><<<ins_blocks, kCandThreads, 0, s>>>(a, melem_tables(ham, n));
+  cand_compact_kernel<W><<<(unsigned)((sc.cap + kCompactChunk - 1) / kCompactChunk), 256, 0, s>>>(a, sc.ukeys,
+                                                                                                sc.uslot);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   unsigned long long ctr[2] = {0, 0};
   if ((e = cudaMemcpyAsync(ctr, sc.counters, sizeof(ctr), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
@@ -298,7 +335,8 @@ static cudaError_t cand_w(const nqs_ham* ham, const uint64_t* U, int64_t n, cons
   // pass 0 reads ukeys/uslot; the payload ping-pong reuses uslot after pass 0
   int out = -1;
   const int n_bytes = (ham->n_qubits + 7) / 8;
-  if ((e = launch_sort_words(sc.ukeys, sc.uslot, *n_cand, W, n_bytes, kbuf, ibuf, sc.hist, &out, s)) != cudaSuccess)
+  if ((e = launch_sort_words(sc.ukeys, sc.uslot, *n_cand, W, n_bytes, kbuf, ibuf, sc.hist, sc.partial, &out, s)) !=
+      cudaSuccess)
     return e;
   const uint64_t* keys = out >= 0 ? kbuf[out] : sc.ukeys;
   const int32_t* slots = out >= 0 ? ibuf[out] : sc.uslot;
@@ -308,7 +346,7 @@ static cudaError_t cand_w(const nqs_ham* ham, const uint64_t* U, int64_t n, cons
   const int ub = (int)std::max<int64_t>(1, std::min<int64_t>((*n_cand + 255) / 256, 8 * sms));
   cand_assign_kernel<W><<<ub, 256, 0, s>>>(*n_cand, cand, slots, sc.slot_uid, in_u,
                                            (const unsigned long long*)(stage + L.off_table), L.cap - 1,
-                                           ham->hash_basis, U, sc.counters);
+                                           sc.table, U, sc.counters);
   const int eb = (int)std::max<int64_t>(1, std::min<int64_t>((entries + 255) / 256, 16 * sms));
   cand_relabel_kernel<<<eb, 256, 0, s>>>(entries, cand_id, sc.slot_uid);
   return cudaGetLastError();
@@ -349,20 +387,22 @@ __global__ void cand_amp_kernel(int64_t n, const double* __restrict__ a, const d
   }
 }
 
+// one block per sample: thread t takes entries t, t + 256, ...; the warps'
+// sums are added in warp order (a fixed reduction order)
 template <bool CPLX>
 __global__ void __launch_bounds__(kCandThreads) eloc_full_kernel(int64_t n, int64_t n_xy, const uint32_t* __restrict__ cand_id,
                                                                  const double* __restrict__ hval,
                                                                  const AmpD* __restrict__ P, const AmpD* __restrict__ Q,
                                                                  int64_t n_cand, double* __restrict__ er,
                                                                  double* __restrict__ ei, int32_t* __restrict__ status) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t)gridDim.x * kCandWarps;
-  for (int64_t i = blockIdx.x * (int64_t)kCandWarps + (threadIdx.x >> 5); i < n; i += nw) {
+  __shared__ double s_r[kCandWarps], s_i[kCandWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     const double2 q = __ldg(&Q[i].v);
     const int kq = __ldg(&Q[i].k);
     double sr = 0.0, si = 0.0;
     const uint64_t e0 = (uint64_t)i * (uint64_t)n_xy;
-    for (int64_t k = lane; k < n_xy; k += 32) {
+    for (int64_t k = threadIdx.x; k < n_xy; k += kCandThreads) {
       const uint32_t c = __ldg(cand_id + e0 + k);
       const double h = __ldg(hval + e0 + k);
       if ((int64_t)c >= n_cand) { atomicOr(status, kStatusLimit); continue; }
@@ -379,9 +419,20 @@ __global__ void __launch_bounds__(kCandThreads) eloc_full_kernel(int64_t n, int6
     sr = warp_sum(sr);
     if (CPLX) si = warp_sum(si);
     if (lane == 0) {
-      er[i] = sr;
-      if (ei) ei[i] = si;
+      s_r[warp] = sr;
+      s_i[warp] = si;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tr = 0.0, ti = 0.0;
+      for (int w = 0; w < kCandWarps; ++w) {
+        tr += s_r[w];
+        ti += s_i[w];
+      }
+      er[i] = tr;
+      if (ei) ei[i] = CPLX ? ti : 0.0;
+    }
+    __syncthreads();
   }
 }
 
@@ -396,7 +447,7 @@ cudaError_t launch_local_energy_full(int64_t n, int64_t n_xy, const char* stage,
   if (n_cand > 0)
     cand_amp_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((n_cand + 255) / 256, 8 * sms)), 256, 0, s>>>(
         n_cand, ca, cb, P);
-  const int rb = (int)std::max<int64_t>(1, std::min<int64_t>((n + kCandWarps - 1) / kCandWarps, 8 * sms));
+  const int rb = (int)std::max<int64_t>(1, std::min<int64_t>(n, 16 * sms));
   const AmpD* Q = (const AmpD*)(stage + L.off_ampQ);
   int32_t* status = (int32_t*)(stage + offsetof(StageHeader, status));
   if (b || cb)

@@ -178,6 +178,7 @@ __device__ __forceinline__ int64_t next_row(const RowSched& rs, int64_t n_long) 
 
 // matrix elements kept per pair for the adjoint: (hi, lo) floats or doubles
 template <class Pol> struct HStore;
+// (complex H: both parts, float4 or double2 per pair)
 template <> struct HStore<PolicyF> {
   using V = float2;
   __device__ static void put(void* h, int64_t q, df v) { reinterpret_cast<float2*>(h)[q] = make_float2(v.hi, v.lo); }
@@ -185,12 +186,33 @@ template <> struct HStore<PolicyF> {
     const float2 v = __ldg(reinterpret_cast<const float2*>(h) + q);
     return {v.x, v.y};
   }
+  __device__ static void put2(void* h, int64_t q, df r, df i) {
+    reinterpret_cast<float4*>(h)[q] = make_float4(r.hi, r.lo, i.hi, i.lo);
+  }
+  __device__ static void get2(const void* h, int64_t q, df& r, df& i) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(h) + q);
+    r = {v.x, v.y};
+    i = {v.z, v.w};
+  }
 };
 template <> struct HStore<PolicyD> {
   using V = double;
   __device__ static void put(void* h, int64_t q, double v) { reinterpret_cast<double*>(h)[q] = v; }
   __device__ static double get(const void* h, int64_t q) { return __ldg(reinterpret_cast<const double*>(h) + q); }
+  __device__ static void put2(void* h, int64_t q, double r, double i) {
+    reinterpret_cast<double2*>(h)[q] = make_double2(r, i);
+  }
+  __device__ static void get2(const void* h, int64_t q, double& r, double& i) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(h) + q);
+    r = v.x;
+    i = v.y;
+  }
 };
+
+// Arithmetic modes of the energy and adjoint kernels (template CX): real H
+// with real log psi (0), real H with complex log psi (1), complex H (2; the
+// local energies are complex whatever log psi is).
+constexpr int kReal = 0, kCplxPsi = 1, kCplxH = 2;
 
 // --------------------------------------------------------------------------
 // E_loc^var over CSR pairs.  A row is a sequence of rounds of 32 pairs; each
@@ -202,7 +224,7 @@ template <> struct HStore<PolicyD> {
 // one warp's rounds; a long row's rounds are dealt to the block's warps in
 // turn and the warps' sums are added in warp order.
 // --------------------------------------------------------------------------
-template <class Pol, int W, bool CPLX, bool STORE_H>
+template <class Pol, int W, int CX, bool STORE_H>
 __device__ __forceinline__ void energy_rounds(const uint64_t* __restrict__ U, const Melem& M, const char* P,
                                               const char* Q, int64_t i, int64_t p, int64_t p1,
                                               int64_t first, int64_t stride, const uint32_t* __restrict__ pair_j,
@@ -226,7 +248,7 @@ __device__ __forceinline__ void energy_rounds(const uint64_t* __restrict__ U, co
     }
     const int4 fm = have ? __ldg(M.fm + k) : make_int4(0, 0, 0, 0);
     const bool coop = have && (int64_t)k < M.heavy_end && (fm.x & 15) == kForm::Terms;
-    T h = Pol::zero();
+    T h = Pol::zero(), h_im = Pol::zero();
     uint32_t hb = __ballot_sync(kFull, coop);
     while (hb) {  // heavy pattern in term form: all lanes share its term loop, its lane keeps H
       const int src = __ffs(hb) - 1;
@@ -235,26 +257,42 @@ __device__ __forceinline__ void energy_rounds(const uint64_t* __restrict__ U, co
       const uint32_t kk = __shfl_sync(kFull, k, src);
       uint64_t xp[W];
       load_words<W>(U + (int64_t)jj * W, xp);
-      const T hw = melem_warp<Pol, W>(xp, (int64_t)__ldg(M.t_ptr + kk), (int64_t)__ldg(M.t_ptr + kk + 1), M);
-      if (lane == src) h = hw;
+      const int64_t t0 = (int64_t)__ldg(M.t_ptr + kk), t1 = (int64_t)__ldg(M.t_ptr + kk + 1);
+      if (CX == kCplxH) {
+        T hwr, hwi;
+        melem_warp_c<Pol, W>(xp, t0, t1, M, hwr, hwi);
+        if (lane == src) { h = hwr; h_im = hwi; }
+      } else {
+        const T hw = melem_warp<Pol, W>(xp, t0, t1, M);
+        if (lane == src) h = hw;
+      }
     }
     if (have) {
       if (!coop) {
         uint64_t xp[W];
         load_words<W>(U + (int64_t)j * W, xp);
-        h = melem_lane<Pol, W>(xp, k, fm, M);
+        if (CX == kCplxH) melem_lane_c<Pol, W>(xp, k, fm, M, h, h_im);
+        else h = melem_lane<Pol, W>(xp, k, fm, M);
       }
       T rr, ri;
-      ratio<Pol, CPLX>(P, Q, j, i, rr, ri, status);
-      Pol::acc(acc_re, Pol::mul(h, rr));
-      if (CPLX) Pol::acc(acc_im, Pol::mul(h, ri));
-      if (STORE_H) HStore<Pol>::put(hpair, q, h);
+      ratio<Pol, CX != kReal>(P, Q, j, i, rr, ri, status);
+      if (CX == kCplxH) {  // (h + i h_im)(rr + i ri)
+        Pol::acc(acc_re, Pol::mul(h, rr));
+        Pol::acc(acc_re, Pol::neg(Pol::mul(h_im, ri)));
+        Pol::acc(acc_im, Pol::mul(h, ri));
+        Pol::acc(acc_im, Pol::mul(h_im, rr));
+        if (STORE_H) HStore<Pol>::put2(hpair, q, h, h_im);
+      } else {
+        Pol::acc(acc_re, Pol::mul(h, rr));
+        if (CX == kCplxPsi) Pol::acc(acc_im, Pol::mul(h, ri));
+        if (STORE_H) HStore<Pol>::put(hpair, q, h);
+      }
     }
   }
 }
 
 // the diagonal pair, if the row starts with it: H_xx added by lane 0 (psi(x)/psi(x) = 1)
-template <class Pol, int W, bool STORE_H>
+template <class Pol, int W, int CX, bool STORE_H>
 __device__ __forceinline__ bool energy_diag(const uint64_t* __restrict__ U, const Melem& M, int64_t i, int64_t p,
                                             int64_t p1, const uint32_t* __restrict__ pair_k, void* hpair,
                                             typename Pol::T& acc_re, double& hd) {
@@ -265,12 +303,15 @@ __device__ __forceinline__ bool energy_diag(const uint64_t* __restrict__ U, cons
   hd = Pol::to_d(h);
   if ((threadIdx.x & 31) == 0) {
     Pol::acc(acc_re, h);
-    if (STORE_H) HStore<Pol>::put(hpair, p, h);
+    if (STORE_H) {
+      if (CX == kCplxH) HStore<Pol>::put2(hpair, p, h, Pol::zero());  // H_xx is real
+      else HStore<Pol>::put(hpair, p, h);
+    }
   }
   return true;
 }
 
-template <class Pol, int W, bool CPLX, bool STORE_H>
+template <class Pol, int W, int CX, bool STORE_H>
 __global__ void __launch_bounds__(kEnergyThreads)
 local_energy_kernel(const uint64_t* __restrict__ U, const Melem M, const char* __restrict__ P,
                     const char* __restrict__ Q, int64_t row_begin, RowSched rs,
@@ -291,12 +332,12 @@ local_energy_kernel(const uint64_t* __restrict__ U, const Melem M, const char* _
     const int64_t p1 = rp[row + 1] - rp[0];
     T acc_re = Pol::zero(), acc_im = Pol::zero();
     double hd = 0.0;
-    if (warp == 0) energy_diag<Pol, W, STORE_H>(U, M, i, p, p1, pair_k, hpair, acc_re, hd);
+    if (warp == 0) energy_diag<Pol, W, CX, STORE_H>(U, M, i, p, p1, pair_k, hpair, acc_re, hd);
     if (M.has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
-    energy_rounds<Pol, W, CPLX, STORE_H>(U, M, P, Q, i, p, p1, warp, kEnergyWarps, pair_j, pair_k, hpair,
-                                         status, acc_re, acc_im);
+    energy_rounds<Pol, W, CX, STORE_H>(U, M, P, Q, i, p, p1, warp, kEnergyWarps, pair_j, pair_k, hpair,
+                                       status, acc_re, acc_im);
     const T er = Pol::warp_sum(acc_re);
-    const T ei = CPLX ? Pol::warp_sum(acc_im) : Pol::zero();
+    const T ei = CX != kReal ? Pol::warp_sum(acc_im) : Pol::zero();
     if (lane == 0) {
       s_re[warp] = er;
       s_im[warp] = ei;
@@ -319,11 +360,11 @@ local_energy_kernel(const uint64_t* __restrict__ U, const Melem M, const char* _
     const int64_t p1 = rp[row + 1] - rp[0];
     T acc_re = Pol::zero(), acc_im = Pol::zero();
     double hd = 0.0;
-    if (energy_diag<Pol, W, STORE_H>(U, M, i, p, p1, pair_k, hpair, acc_re, hd)) ++p;
-    energy_rounds<Pol, W, CPLX, STORE_H>(U, M, P, Q, i, p, p1, 0, 1, pair_j, pair_k, hpair, status, acc_re,
+    if (energy_diag<Pol, W, CX, STORE_H>(U, M, i, p, p1, pair_k, hpair, acc_re, hd)) ++p;
+    energy_rounds<Pol, W, CX, STORE_H>(U, M, P, Q, i, p, p1, 0, 1, pair_j, pair_k, hpair, status, acc_re,
                                          acc_im);
     const T er = Pol::warp_sum(acc_re);
-    const T ei = CPLX ? Pol::warp_sum(acc_im) : Pol::zero();
+    const T ei = CX != kReal ? Pol::warp_sum(acc_im) : Pol::zero();
     if (lane == 0) {
       eloc_re[i] = Pol::to_d(er);
       if (eloc_im) eloc_im[i] = Pol::to_d(ei);
@@ -341,25 +382,25 @@ static int grid_for(Kern kern, int64_t rows) {
                                                      (int64_t)num_sms() * occ));
 }
 
-template <class Pol, int W, bool CPLX, bool STORE_H>
+template <class Pol, int W, int CX, bool STORE_H>
 static void launch_le(const nqs_ham* ham, const uint64_t* U, const char* stage, const StageHeader& L,
                       int64_t rb, const RowSched& rs, const int64_t* rp, const uint32_t* pj,
                       const uint32_t* pk, double* er, double* ei, double* hd, void* hpair, cudaStream_t s) {
-  auto kern = local_energy_kernel<Pol, W, CPLX, STORE_H>;
+  auto kern = local_energy_kernel<Pol, W, CX, STORE_H>;
   kern<<<grid_for(kern, rs.rows), kEnergyThreads, 0, s>>>(
       U, melem_tables(ham, L.n_unq), stage + L.off_ampP, stage + L.off_ampQ, rb, rs, rp,
       pj, pk, er, ei, hd, hpair, (int32_t*)(stage + offsetof(StageHeader, status)));
 }
 
-template <class Pol, bool CPLX, bool STORE_H>
+template <class Pol, int CX, bool STORE_H>
 static void launch_le_w(const nqs_ham* ham, const uint64_t* U, const char* stage, const StageHeader& L,
                         int64_t rb, const RowSched& rs, const int64_t* rp, const uint32_t* pj,
                         const uint32_t* pk, double* er, double* ei, double* hd, void* hpair, cudaStream_t s) {
   switch (ham->W) {
-    case 1: launch_le<Pol, 1, CPLX, STORE_H>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s); break;
-    case 2: launch_le<Pol, 2, CPLX, STORE_H>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s); break;
-    case 3: launch_le<Pol, 3, CPLX, STORE_H>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s); break;
-    default: launch_le<Pol, 4, CPLX, STORE_H>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s); break;
+    case 1: launch_le<Pol, 1, CX, STORE_H>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s); break;
+    case 2: launch_le<Pol, 2, CX, STORE_H>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s); break;
+    case 3: launch_le<Pol, 3, CX, STORE_H>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s); break;
+    default: launch_le<Pol, 4, CX, STORE_H>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s); break;
   }
 }
 
@@ -367,12 +408,15 @@ template <class Pol>
 static void launch_le_p(const nqs_ham* ham, const uint64_t* U, const char* stage, const StageHeader& L, bool cplx,
                         int64_t rb, const RowSched& rs, const int64_t* rp, const uint32_t* pj, const uint32_t* pk,
                         double* er, double* ei, double* hd, void* hpair, cudaStream_t s) {
-  if (cplx) {
-    if (hpair) launch_le_w<Pol, true, true>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s);
-    else launch_le_w<Pol, true, false>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s);
+  if (ham->cplx) {
+    if (hpair) launch_le_w<Pol, kCplxH, true>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s);
+    else launch_le_w<Pol, kCplxH, false>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s);
+  } else if (cplx) {
+    if (hpair) launch_le_w<Pol, kCplxPsi, true>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s);
+    else launch_le_w<Pol, kCplxPsi, false>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s);
   } else {
-    if (hpair) launch_le_w<Pol, false, true>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s);
-    else launch_le_w<Pol, false, false>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s);
+    if (hpair) launch_le_w<Pol, kReal, true>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s);
+    else launch_le_w<Pol, kReal, false>(ham, U, stage, L, rb, rs, rp, pj, pk, er, ei, hd, hpair, s);
   }
 }
 
@@ -610,7 +654,7 @@ __device__ __forceinline__ void load_geff(const char* G, int64_t i, typename Pol
 // With LOAD_H the matrix elements come from the forward call's store (one
 // lane per pair, no term loop); otherwise they are recomputed exactly as the
 // forward computes them, so both forms give the same bits.
-template <class Pol, int W, bool CPLX, bool LOAD_H>
+template <class Pol, int W, int CX, bool LOAD_H>
 __device__ __forceinline__ void backward_rounds(const uint64_t* __restrict__ U, const Melem& M, const char* P,
                                                 const char* Q, const char* G, int64_t y, int64_t p,
                                                 int64_t p1, int64_t first, int64_t stride,
@@ -633,9 +677,12 @@ __device__ __forceinline__ void backward_rounds(const uint64_t* __restrict__ U, 
       jn = __ldg(pair_j + q + 32 * stride);
       if (!LOAD_H) kn = __ldg(pair_k + q + 32 * stride);
     }
-    T h = Pol::zero();
+    T h = Pol::zero(), h_im = Pol::zero();
     if (LOAD_H) {
-      if (have) h = HStore<Pol>::get(hpair, q);
+      if (have) {
+        if (CX == kCplxH) HStore<Pol>::get2(hpair, q, h, h_im);
+        else h = HStore<Pol>::get(hpair, q);
+      }
     } else {
       const int4 fm = have ? __ldg(M.fm + k) : make_int4(0, 0, 0, 0);
       const bool coop = have && (int64_t)k < M.heavy_end && (fm.x & 15) == kForm::Terms;
@@ -647,26 +694,45 @@ __device__ __forceinline__ void backward_rounds(const uint64_t* __restrict__ U, 
         const uint32_t kk = __shfl_sync(kFull, k, src);
         uint64_t xp[W];
         load_words<W>(U + (int64_t)jj * W, xp);
-        const T hw = melem_warp<Pol, W>(xp, (int64_t)__ldg(M.t_ptr + kk), (int64_t)__ldg(M.t_ptr + kk + 1), M);
-        if (lane == src) h = hw;
+        const int64_t t0 = (int64_t)__ldg(M.t_ptr + kk), t1 = (int64_t)__ldg(M.t_ptr + kk + 1);
+        if (CX == kCplxH) {
+          T hwr, hwi;
+          melem_warp_c<Pol, W>(xp, t0, t1, M, hwr, hwi);
+          if (lane == src) { h = hwr; h_im = hwi; }
+        } else {
+          const T hw = melem_warp<Pol, W>(xp, t0, t1, M);
+          if (lane == src) h = hw;
+        }
       }
       if (have && !coop) {
         uint64_t xp[W];
         load_words<W>(U + (int64_t)j * W, xp);
-        h = melem_lane<Pol, W>(xp, k, fm, M);
+        if (CX == kCplxH) melem_lane_c<Pol, W>(xp, k, fm, M, h, h_im);
+        else h = melem_lane<Pol, W>(xp, k, fm, M);
       }
     }
     if (have) {
       T rr, ri, ge, gi;
-      ratio<Pol, CPLX>(P, Q, y, j, rr, ri, status);
+      ratio<Pol, CX != kReal>(P, Q, y, j, rr, ri, status);
       load_geff<Pol>(G, j, ge, gi);
-      const T tr = Pol::mul(h, rr);
-      Pol::acc(da, Pol::mul(ge, tr));
-      if (CPLX) {
-        const T ti = Pol::mul(h, ri);
+      if (CX == kCplxH) {
+        // row y holds H_yj; the pair's term uses H_jy = conj(H_yj) (H Hermitian):
+        // T = conj(h) psi(y)/psi(j) = (h rr + h_im ri) + i (h ri - h_im rr)
+        const T tr = Pol::add(Pol::mul(h, rr), Pol::mul(h_im, ri));
+        const T ti = Pol::add(Pol::mul(h, ri), Pol::neg(Pol::mul(h_im, rr)));
+        Pol::acc(da, Pol::mul(ge, tr));
         Pol::acc(da, Pol::mul(gi, ti));
         Pol::acc(db, Pol::neg(Pol::mul(ge, ti)));
         Pol::acc(db, Pol::mul(gi, tr));
+      } else {
+        const T tr = Pol::mul(h, rr);
+        Pol::acc(da, Pol::mul(ge, tr));
+        if (CX == kCplxPsi) {
+          const T ti = Pol::mul(h, ri);
+          Pol::acc(da, Pol::mul(gi, ti));
+          Pol::acc(db, Pol::neg(Pol::mul(ge, ti)));
+          Pol::acc(db, Pol::mul(gi, tr));
+        }
       }
     }
   }
@@ -681,7 +747,7 @@ __device__ __forceinline__ void backward_finish(int64_t y, double sa, double sb,
   if (gim) gim[y] = CPLX ? sb + o.y : 0.0;
 }
 
-template <class Pol, int W, bool CPLX, bool LOAD_H>
+template <class Pol, int W, int CX, bool LOAD_H>
 __global__ void __launch_bounds__(kEnergyThreads)
 backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
                       const char* __restrict__ P, const char* __restrict__ Q, const char* __restrict__ G,
@@ -702,10 +768,10 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
     const int64_t p1 = rp[row + 1] - rp[0];
     if (M.has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
     T da = Pol::zero(), db = Pol::zero();
-    backward_rounds<Pol, W, CPLX, LOAD_H>(U, M, P, Q, G, y, p, p1, warp, kEnergyWarps, pair_j, pair_k, hpair,
+    backward_rounds<Pol, W, CX, LOAD_H>(U, M, P, Q, G, y, p, p1, warp, kEnergyWarps, pair_j, pair_k, hpair,
                                           status, da, db);
     da = Pol::warp_sum(da);
-    db = CPLX ? Pol::warp_sum(db) : Pol::zero();
+    db = CX != kReal ? Pol::warp_sum(db) : Pol::zero();
     if (lane == 0) {
       s_a[warp] = da;
       s_b[warp] = db;
@@ -717,7 +783,7 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
         ta = Pol::add(ta, s_a[w]);
         tb = Pol::add(tb, s_b[w]);
       }
-      backward_finish<CPLX>(y, Pol::to_d(ta), CPLX ? Pol::to_d(tb) : 0.0, own, gre, gim);
+      backward_finish<CX != kReal>(y, Pol::to_d(ta), CX != kReal ? Pol::to_d(tb) : 0.0, own, gre, gim);
     }
   }
   for (int64_t row = next_row(rs, n_long); row >= 0; row = next_row(rs, n_long)) {
@@ -726,10 +792,10 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
     const int64_t p1 = rp[row + 1] - rp[0];
     if (M.has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
     T da = Pol::zero(), db = Pol::zero();
-    backward_rounds<Pol, W, CPLX, LOAD_H>(U, M, P, Q, G, y, p, p1, 0, 1, pair_j, pair_k, hpair, status, da, db);
+    backward_rounds<Pol, W, CX, LOAD_H>(U, M, P, Q, G, y, p, p1, 0, 1, pair_j, pair_k, hpair, status, da, db);
     const double sa = Pol::to_d(Pol::warp_sum(da));
-    const double sb = CPLX ? Pol::to_d(Pol::warp_sum(db)) : 0.0;
-    if (lane == 0) backward_finish<CPLX>(y, sa, sb, own, gre, gim);
+    const double sb = CX != kReal ? Pol::to_d(Pol::warp_sum(db)) : 0.0;
+    if (lane == 0) backward_finish<CX != kReal>(y, sa, sb, own, gre, gim);
   }
 }
 
@@ -739,25 +805,25 @@ struct BwArgs {
   const void* hpair;
 };
 
-template <class Pol, int W, bool CPLX, bool LOAD_H>
+template <class Pol, int W, int CX, bool LOAD_H>
 static void launch_bw(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L, int64_t rb,
                       const RowSched& rs, const int64_t* rp, const uint32_t* pj, const uint32_t* pk,
                       const BwArgs& b, cudaStream_t s) {
-  auto kern = backward_pairs_kernel<Pol, W, CPLX, LOAD_H>;
+  auto kern = backward_pairs_kernel<Pol, W, CX, LOAD_H>;
   kern<<<grid_for(kern, rs.rows), kEnergyThreads, 0, s>>>(
       U, melem_tables(ham, L.n_unq), stage + L.off_ampP, stage + L.off_ampQ, stage + L.off_geff, rb, rs, rp, pj, pk, b.hpair, b.own, b.gre, b.gim,
       (int32_t*)(stage + offsetof(StageHeader, status)));
 }
 
-template <class Pol, bool CPLX, bool LOAD_H>
+template <class Pol, int CX, bool LOAD_H>
 static void launch_bw_w(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L, int64_t rb,
                         const RowSched& rs, const int64_t* rp, const uint32_t* pj, const uint32_t* pk,
                         const BwArgs& b, cudaStream_t s) {
   switch (ham->W) {
-    case 1: launch_bw<Pol, 1, CPLX, LOAD_H>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s); break;
-    case 2: launch_bw<Pol, 2, CPLX, LOAD_H>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s); break;
-    case 3: launch_bw<Pol, 3, CPLX, LOAD_H>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s); break;
-    default: launch_bw<Pol, 4, CPLX, LOAD_H>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s); break;
+    case 1: launch_bw<Pol, 1, CX, LOAD_H>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s); break;
+    case 2: launch_bw<Pol, 2, CX, LOAD_H>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s); break;
+    case 3: launch_bw<Pol, 3, CX, LOAD_H>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s); break;
+    default: launch_bw<Pol, 4, CX, LOAD_H>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s); break;
   }
 }
 
@@ -765,12 +831,15 @@ template <class Pol>
 static void launch_bw_p(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L, bool cplx,
                         int64_t rb, const RowSched& rs, const int64_t* rp, const uint32_t* pj, const uint32_t* pk,
                         const BwArgs& b, cudaStream_t s) {
-  if (cplx) {
-    if (b.hpair) launch_bw_w<Pol, true, true>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s);
-    else launch_bw_w<Pol, true, false>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s);
+  if (ham->cplx) {
+    if (b.hpair) launch_bw_w<Pol, kCplxH, true>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s);
+    else launch_bw_w<Pol, kCplxH, false>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s);
+  } else if (cplx) {
+    if (b.hpair) launch_bw_w<Pol, kCplxPsi, true>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s);
+    else launch_bw_w<Pol, kCplxPsi, false>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s);
   } else {
-    if (b.hpair) launch_bw_w<Pol, false, true>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s);
-    else launch_bw_w<Pol, false, false>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s);
+    if (b.hpair) launch_bw_w<Pol, kReal, true>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s);
+    else launch_bw_w<Pol, kReal, false>(ham, U, stage, L, rb, rs, rp, pj, pk, b, s);
   }
 }
 
@@ -801,6 +870,311 @@ cudaError_t launch_backward(const nqs_ham* ham, const uint64_t* U, int64_t n, ch
   const BwArgs b{(const double2*)(stage + L.off_own), gre, gim, hpair};
   if (fp64) launch_bw_p<PolicyD>(ham, U, stage, L, cplx, rb, rs, rp, pj, pk, b, s);
   else launch_bw_p<PolicyF>(ham, U, stage, L, cplx, rb, rs, rp, pj, pk, b, s);
+  return cudaGetLastError();
+}
+
+
+// --------------------------------------------------------------------------
+// Half-stored pairs (i < j form): each unordered coupled pair {x_i, x_j} is
+// one record (i, j, k).  Its matrix element is evaluated once and both rows
+// receive their terms by FP64 atomic addition (symmetric scatter):
+//   E_loc(i) += H_ij psi(j)/psi(i),   E_loc(j) += H_ji psi(i)/psi(j),
+// with H_ji = conj(H_ij) (H Hermitian).  The diagonal is set first, one warp
+// per sample.  Atomic addition makes the summation order, and so the last
+// bits of a row's sum, depend on thread timing; the per-pair terms are the
+// CSR path's to the bit.
+// --------------------------------------------------------------------------
+template <class Pol, int W>
+__global__ void __launch_bounds__(kEnergyThreads)
+half_diag_kernel(const uint64_t* __restrict__ U, const Melem M, int64_t n, double* __restrict__ er,
+                 double* __restrict__ ei, double* __restrict__ hd) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * kEnergyWarps;
+  for (int64_t i = blockIdx.x * (int64_t)kEnergyWarps + (threadIdx.x >> 5); i < n; i += nw) {
+    double h = 0.0;
+    if (M.has_diag) {
+      uint64_t x[W];
+      load_words<W>(U + i * W, x);
+      h = Pol::to_d(melem_diag<Pol, W>(x, M));
+    }
+    if (lane == 0) {
+      er[i] = h;
+      if (ei) ei[i] = 0.0;
+      if (hd) hd[i] = h;
+    }
+  }
+}
+
+// H_ij of the record held by this lane (x' = U_j, pattern k): heavy term-form
+// patterns by the whole warp, the rest by the lane
+template <class Pol, int W, int CX>
+__device__ __forceinline__ void half_melem(const uint64_t* __restrict__ U, const Melem& M, bool have, uint32_t j,
+                                           uint32_t k, typename Pol::T& h, typename Pol::T& h_im) {
+  using T = typename Pol::T;
+  const int lane = threadIdx.x & 31;
+  const int4 fm = have ? __ldg(M.fm + k) : make_int4(0, 0, 0, 0);
+  const bool coop = have && (int64_t)k < M.heavy_end && (fm.x & 15) == kForm::Terms;
+  h = Pol::zero();
+  h_im = Pol::zero();
+  uint32_t hb = __ballot_sync(kFull, coop);
+  while (hb) {
+    const int src = __ffs(hb) - 1;
+    hb &= hb - 1;
+    const uint32_t jj = __shfl_sync(kFull, j, src);
+    const uint32_t kk = __shfl_sync(kFull, k, src);
+    uint64_t xp[W];
+    load_words<W>(U + (int64_t)jj * W, xp);
+    const int64_t t0 = (int64_t)__ldg(M.t_ptr + kk), t1 = (int64_t)__ldg(M.t_ptr + kk + 1);
+    if (CX == kCplxH) {
+      T hwr, hwi;
+      melem_warp_c<Pol, W>(xp, t0, t1, M, hwr, hwi);
+      if (lane == src) { h = hwr; h_im = hwi; }
+    } else {
+      const T hw = melem_warp<Pol, W>(xp, t0, t1, M);
+      if (lane == src) h = hw;
+    }
+  }
+  if (have && !coop) {
+    uint64_t xp[W];
+    load_words<W>(U + (int64_t)j * W, xp);
+    if (CX == kCplxH) melem_lane_c<Pol, W>(xp, k, fm, M, h, h_im);
+    else h = melem_lane<Pol, W>(xp, k, fm, M);
+  }
+}
+
+// the two terms of a record: t_i = H_ij psi(j)/psi(i) and t_j = conj(H_ij) psi(i)/psi(j)
+template <class Pol, int CX>
+__device__ __forceinline__ void half_terms(const char* P, const char* Q, int64_t i, int64_t j, typename Pol::T h,
+                                           typename Pol::T h_im, int32_t* status, double& ir, double& ii,
+                                           double& jr, double& ji) {
+  using T = typename Pol::T;
+  T rr, ri, sr, si;
+  ratio<Pol, CX != kReal>(P, Q, j, i, rr, ri, status);   // psi(j)/psi(i)
+  ratio<Pol, CX != kReal>(P, Q, i, j, sr, si, status);   // psi(i)/psi(j)
+  if (CX == kCplxH) {
+    ir = Pol::to_d(Pol::add(Pol::mul(h, rr), Pol::neg(Pol::mul(h_im, ri))));
+    ii = Pol::to_d(Pol::add(Pol::mul(h, ri), Pol::mul(h_im, rr)));
+    jr = Pol::to_d(Pol::add(Pol::mul(h, sr), Pol::mul(h_im, si)));
+    ji = Pol::to_d(Pol::add(Pol::mul(h, si), Pol::neg(Pol::mul(h_im, sr))));
+  } else {
+    ir = Pol::to_d(Pol::mul(h, rr));
+    jr = Pol::to_d(Pol::mul(h, sr));
+    ii = CX == kCplxPsi ? Pol::to_d(Pol::mul(h, ri)) : 0.0;
+    ji = CX == kCplxPsi ? Pol::to_d(Pol::mul(h, si)) : 0.0;
+  }
+}
+
+__device__ __forceinline__ bool half_record(const uint32_t* __restrict__ ri, const uint32_t* __restrict__ rj,
+                                            const uint32_t* __restrict__ rk, int64_t s, int64_t n_slots,
+                                            const Melem& M, int32_t* status, uint32_t& i, uint32_t& j,
+                                            uint32_t& k) {
+  i = s < n_slots ? __ldg(ri + s) : kNoRecordSlot;
+  if (i == kNoRecordSlot) return false;
+  j = __ldg(rj + s);
+  k = __ldg(rk + s);
+  const bool ok = (int64_t)i < M.n_unq && pair_in_range(M, j, k, status);
+  if (!ok && (int64_t)i >= M.n_unq) atomicOr(status, kStatusLimit);
+  return ok;
+}
+
+template <class Pol, int W, int CX, bool STORE_H>
+__global__ void __launch_bounds__(kEnergyThreads)
+half_energy_kernel(const uint64_t* __restrict__ U, const Melem M, const char* __restrict__ P,
+                   const char* __restrict__ Q, const uint32_t* __restrict__ ri, const uint32_t* __restrict__ rj,
+                   const uint32_t* __restrict__ rk, int64_t n_slots, double* __restrict__ er,
+                   double* __restrict__ ei, void* __restrict__ hrec, int32_t* __restrict__ status) {
+  using T = typename Pol::T;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * kEnergyThreads;
+  for (int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) - lane; b < n_slots; b += stride) {
+    const int64_t s = b + lane;
+    uint32_t i = 0, j = 0, k = 0;
+    const bool have = half_record(ri, rj, rk, s, n_slots, M, status, i, j, k);
+    T h, h_im;
+    half_melem<Pol, W, CX>(U, M, have, j, k, h, h_im);
+    if (!have) continue;
+    double a_r, a_i, b_r, b_i;
+    half_terms<Pol, CX>(P, Q, i, j, h, h_im, status, a_r, a_i, b_r, b_i);
+    atomicAdd(er + i, a_r);
+    atomicAdd(er + j, b_r);
+    if (CX != kReal) {
+      atomicAdd(ei + i, a_i);
+      atomicAdd(ei + j, b_i);
+    }
+    if (STORE_H) {
+      if (CX == kCplxH) HStore<Pol>::put2(hrec, s, h, h_im);
+      else HStore<Pol>::put(hrec, s, h);
+    }
+  }
+}
+
+template <class Pol, int W, int CX, bool STORE_H>
+static void launch_half_le(const nqs_ham* ham, const uint64_t* U, int64_t n, const char* stage, const StageHeader& L,
+                           const uint32_t* ri, const uint32_t* rj, const uint32_t* rk, int64_t n_slots, double* er,
+                           double* ei, void* hrec, cudaStream_t s) {
+  const Melem M = melem_tables(ham, n);
+  auto kern = half_energy_kernel<Pol, W, CX, STORE_H>;
+  const int64_t warps = (n_slots + 31) / 32;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((warps + kEnergyWarps - 1) / kEnergyWarps,
+                                                                  (int64_t)grid_for(kern, INT64_MAX / 2)));
+  kern<<<blocks, kEnergyThreads, 0, s>>>(U, M, stage + L.off_ampP, stage + L.off_ampQ, ri, rj, rk, n_slots, er, ei,
+                                         hrec, (int32_t*)(stage + offsetof(StageHeader, status)));
+}
+
+template <class Pol, int CX, bool STORE_H>
+static void launch_half_le_w(const nqs_ham* ham, const uint64_t* U, int64_t n, const char* stage,
+                             const StageHeader& L, const uint32_t* ri, const uint32_t* rj, const uint32_t* rk,
+                             int64_t n_slots, double* er, double* ei, double* hd, void* hrec, cudaStream_t s) {
+  const Melem M = melem_tables(ham, n);
+  const int db = (int)std::max<int64_t>(1, std::min<int64_t>((n + kEnergyWarps - 1) / kEnergyWarps, 8 * num_sms()));
+  switch (ham->W) {
+    case 1: half_diag_kernel<Pol, 1><<<db, kEnergyThreads, 0, s>>>(U, M, n, er, ei, hd);
+            launch_half_le<Pol, 1, CX, STORE_H>(ham, U, n, stage, L, ri, rj, rk, n_slots, er, ei, hrec, s); break;
+    case 2: half_diag_kernel<Pol, 2><<<db, kEnergyThreads, 0, s>>>(U, M, n, er, ei, hd);
+            launch_half_le<Pol, 2, CX, STORE_H>(ham, U, n, stage, L, ri, rj, rk, n_slots, er, ei, hrec, s); break;
+    case 3: half_diag_kernel<Pol, 3><<<db, kEnergyThreads, 0, s>>>(U, M, n, er, ei, hd);
+            launch_half_le<Pol, 3, CX, STORE_H>(ham, U, n, stage, L, ri, rj, rk, n_slots, er, ei, hrec, s); break;
+    default: half_diag_kernel<Pol, 4><<<db, kEnergyThreads, 0, s>>>(U, M, n, er, ei, hd);
+             launch_half_le<Pol, 4, CX, STORE_H>(ham, U, n, stage, L, ri, rj, rk, n_slots, er, ei, hrec, s); break;
+  }
+}
+
+template <class Pol>
+static void launch_half_le_p(const nqs_ham* ham, const uint64_t* U, int64_t n, const char* stage,
+                             const StageHeader& L, bool cplx, const uint32_t* ri, const uint32_t* rj,
+                             const uint32_t* rk, int64_t n_slots, double* er, double* ei, double* hd, void* hrec,
+                             cudaStream_t s) {
+  if (ham->cplx) {
+    if (hrec) launch_half_le_w<Pol, kCplxH, true>(ham, U, n, stage, L, ri, rj, rk, n_slots, er, ei, hd, hrec, s);
+    else launch_half_le_w<Pol, kCplxH, false>(ham, U, n, stage, L, ri, rj, rk, n_slots, er, ei, hd, hrec, s);
+  } else if (cplx) {
+    if (hrec) launch_half_le_w<Pol, kCplxPsi, true>(ham, U, n, stage, L, ri, rj, rk, n_slots, er, ei, hd, hrec, s);
+    else launch_half_le_w<Pol, kCplxPsi, false>(ham, U, n, stage, L, ri, rj, rk, n_slots, er, ei, hd, hrec, s);
+  } else {
+    if (hrec) launch_half_le_w<Pol, kReal, true>(ham, U, n, stage, L, ri, rj, rk, n_slots, er, ei, hd, hrec, s);
+    else launch_half_le_w<Pol, kReal, false>(ham, U, n, stage, L, ri, rj, rk, n_slots, er, ei, hd, hrec, s);
+  }
+}
+
+cudaError_t launch_local_energy_half(const nqs_ham* ham, const uint64_t* U, int64_t n, const char* stage,
+                                     const StageHeader& L, bool cplx, const uint32_t* ri, const uint32_t* rj,
+                                     const uint32_t* rk, int64_t n_slots, int precision, double* er, double* ei,
+                                     double* hd, void* hrec, cudaStream_t s) {
+  if (precision == NQS_PREC_FP64)
+    launch_half_le_p<PolicyD>(ham, U, n, stage, L, cplx, ri, rj, rk, n_slots, er, ei, hd, hrec, s);
+  else
+    launch_half_le_p<PolicyF>(ham, U, n, stage, L, cplx, ri, rj, rk, n_slots, er, ei, hd, hrec, s);
+  return cudaGetLastError();
+}
+
+// Adjoint over half-stored records.  The row terms of the CSR adjoint, for a
+// record (i, j): row j gets ge(i) Re T + gi(i) Im T (and -ge(i) Im T + gi(i) Re T
+// for Im log psi) with T = H_ij psi(j)/psi(i), row i the same with the roles
+// of i and j swapped and T = conj(H_ij) psi(i)/psi(j).  The rows' own terms
+// (geff_kernel) initialise the gradient.
+__global__ void half_grad_init_kernel(int64_t n, const double2* __restrict__ own, double* __restrict__ gre,
+                                      double* __restrict__ gim) {
+  for (int64_t y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; y < n; y += (int64_t)gridDim.x * blockDim.x) {
+    const double2 o = own[y];
+    gre[y] = o.x;
+    if (gim) gim[y] = o.y;
+  }
+}
+
+template <class Pol, int W, int CX, bool LOAD_H>
+__global__ void __launch_bounds__(kEnergyThreads)
+half_backward_kernel(const uint64_t* __restrict__ U, const Melem M, const char* __restrict__ P,
+                     const char* __restrict__ Q, const char* __restrict__ G, const uint32_t* __restrict__ ri,
+                     const uint32_t* __restrict__ rj, const uint32_t* __restrict__ rk, int64_t n_slots,
+                     const void* __restrict__ hrec, double* __restrict__ gre, double* __restrict__ gim,
+                     int32_t* __restrict__ status) {
+  using T = typename Pol::T;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * kEnergyThreads;
+  for (int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) - lane; b < n_slots; b += stride) {
+    const int64_t s = b + lane;
+    uint32_t i = 0, j = 0, k = 0;
+    const bool have = half_record(ri, rj, rk, s, n_slots, M, status, i, j, k);
+    T h = Pol::zero(), h_im = Pol::zero();
+    if (LOAD_H) {
+      if (have) {
+        if (CX == kCplxH) HStore<Pol>::get2(hrec, s, h, h_im);
+        else h = HStore<Pol>::get(hrec, s);
+      }
+    } else {
+      half_melem<Pol, W, CX>(U, M, have, j, k, h, h_im);
+    }
+    if (!have) continue;
+    double a_r, a_i, b_r, b_i;   // T_ij (row j's term) and T_ji (row i's term)
+    half_terms<Pol, CX>(P, Q, i, j, h, h_im, status, a_r, a_i, b_r, b_i);
+    T gei, gii, gej, gij;
+    Pol::load_v(G, i, gei, gii);
+    Pol::load_v(G, j, gej, gij);
+    const double ge_i = Pol::to_d(gei), gi_i = Pol::to_d(gii), ge_j = Pol::to_d(gej), gi_j = Pol::to_d(gij);
+    atomicAdd(gre + j, ge_i * a_r + gi_i * a_i);
+    atomicAdd(gre + i, ge_j * b_r + gi_j * b_i);
+    if (gim) {
+      atomicAdd(gim + j, -ge_i * a_i + gi_i * a_r);
+      atomicAdd(gim + i, -ge_j * b_i + gi_j * b_r);
+    }
+  }
+}
+
+template <class Pol, int CX, bool LOAD_H>
+static void launch_half_bw_w(const nqs_ham* ham, const uint64_t* U, int64_t n, char* stage, const StageHeader& L,
+                             const uint32_t* ri, const uint32_t* rj, const uint32_t* rk, int64_t n_slots,
+                             const void* hrec, double* gre, double* gim, cudaStream_t s) {
+  const Melem M = melem_tables(ham, n);
+  const int64_t warps = (n_slots + 31) / 32;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((warps + kEnergyWarps - 1) / kEnergyWarps,
+                                                                  (int64_t)8 * num_sms()));
+  int32_t* status = (int32_t*)(stage + offsetof(StageHeader, status));
+#define NQS_HALF_BW(WW)                                                                                          \
+  half_backward_kernel<Pol, WW, CX, LOAD_H><<<blocks, kEnergyThreads, 0, s>>>(                                    \
+      U, M, stage + L.off_ampP, stage + L.off_ampQ, stage + L.off_geff, ri, rj, rk, n_slots, hrec, gre, gim, status)
+  switch (ham->W) {
+    case 1: NQS_HALF_BW(1); break;
+    case 2: NQS_HALF_BW(2); break;
+    case 3: NQS_HALF_BW(3); break;
+    default: NQS_HALF_BW(4); break;
+  }
+#undef NQS_HALF_BW
+}
+
+cudaError_t launch_backward_half(const nqs_ham* ham, const uint64_t* U, int64_t n, char* stage,
+                                 const StageHeader& L, bool cplx, const double* a, const uint32_t* ri,
+                                 const uint32_t* rj, const uint32_t* rk, int64_t n_slots, const void* hrec,
+                                 const double* er, const double* ei, const double* hd, const double* evar,
+                                 const double* g_re, const double* g_im, const double* g_evar, int precision,
+                                 double* gre, double* gim, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * num_sms()));
+  if (!g_re && !g_im) {
+    backward_closed_kernel<<<blocks, 256, 0, s>>>(0, n, a, er, ei, evar, g_evar, gre, gim);
+    return cudaGetLastError();
+  }
+  const bool fp64 = precision == NQS_PREC_FP64;
+  geff_kernel<<<blocks, 256, 0, s>>>(n, a, evar, g_re, g_im, g_evar, fp64 ? 1 : 0, (double2*)(stage + L.off_geff),
+                                     (float4*)(stage + L.off_geff), 0, n, er, ei, hd, (double2*)(stage + L.off_own));
+  half_grad_init_kernel<<<blocks, 256, 0, s>>>(n, (const double2*)(stage + L.off_own), gre, gim);
+  const int cx = ham->cplx ? kCplxH : (cplx ? kCplxPsi : kReal);
+#define NQS_HALF_BW_P(POL)                                                                                        \
+  if (cx == kCplxH) {                                                                                             \
+    if (hrec) launch_half_bw_w<POL, kCplxH, true>(ham, U, n, stage, L, ri, rj, rk, n_slots, hrec, gre, gim, s);   \
+    else launch_half_bw_w<POL, kCplxH, false>(ham, U, n, stage, L, ri, rj, rk, n_slots, hrec, gre, gim, s);       \
+  } else if (cx == kCplxPsi) {                                                                                    \
+    if (hrec) launch_half_bw_w<POL, kCplxPsi, true>(ham, U, n, stage, L, ri, rj, rk, n_slots, hrec, gre, gim, s); \
+    else launch_half_bw_w<POL, kCplxPsi, false>(ham, U, n, stage, L, ri, rj, rk, n_slots, hrec, gre, gim, s);     \
+  } else {                                                                                                        \
+    if (hrec) launch_half_bw_w<POL, kReal, true>(ham, U, n, stage, L, ri, rj, rk, n_slots, hrec, gre, gim, s);    \
+    else launch_half_bw_w<POL, kReal, false>(ham, U, n, stage, L, ri, rj, rk, n_slots, hrec, gre, gim, s);        \
+  }
+  if (fp64) {
+    NQS_HALF_BW_P(PolicyD)
+  } else {
+    NQS_HALF_BW_P(PolicyF)
+  }
+#undef NQS_HALF_BW_P
   return cudaGetLastError();
 }
 

@@ -310,8 +310,8 @@ PairScratch pair_scratch_view(void* base, int64_t rows, int64_t bytes) {
 // --------------------------------------------------------------------------
 constexpr int R = kRowsPerWarp;
 constexpr int kMaxSegs = 64 * kMaxWords;
-constexpr int kItemsPerGrab = 4;   // work items a warp takes per atomic
-constexpr int kGroupsPerItem = 16; // search-table groups per work item (bounds an item's length)
+// work items a warp takes per atomic, and search-table groups per work item
+// (bounds an item's length): launch parameters (SearchTune), 4 and 16 by default
 constexpr int kCandCap = 256;      // per-warp queue of filter survivors (sample, slot)
 
 struct TermsArgs {
@@ -340,6 +340,8 @@ struct TermsArgs {
   PairScratch sc;         // EMIT
   int32_t* status;
   unsigned long long* item_counter;
+  int items_per_grab;
+  int groups_per_item;
 };
 
 template <int W>
@@ -382,9 +384,11 @@ __device__ __forceinline__ void emit_found(bool found, int64_t i, uint32_t j, ui
     if (in_j) place_pair(a.rp, (int64_t)j - a.row_begin, a.cursor, a.pair_j, a.pair_k, (uint32_t)i, id, a.status);
     return;
   }
-  if (in_i) atomicAdd((unsigned long long*)(a.counts + (i - a.row_begin)), 1ull);
-  if (in_j) atomicAdd((unsigned long long*)(a.counts + ((int64_t)j - a.row_begin)), 1ull);
-  if (MODE == kEmit) {
+  if (MODE != kEmitHalf) {
+    if (in_i) atomicAdd((unsigned long long*)(a.counts + (i - a.row_begin)), 1ull);
+    if (in_j) atomicAdd((unsigned long long*)(a.counts + ((int64_t)j - a.row_begin)), 1ull);
+  }
+  if (MODE == kEmit || MODE == kEmitHalf) {
     const bool keep = in_i || in_j;
     const uint32_t m = __ballot_sync(kFull, keep);
     const int n = __popc(m);
@@ -541,7 +545,7 @@ __device__ __forceinline__ void verify_queue(uint2* q, int qn, Survivors* sv, Re
 }
 
 // Oriented LoopOverTerms search kernel.  A warp probes 8 samples of a
-// per-qubit list against up to kGroupsPerItem groups of that qubit's segment;
+// per-qubit list against up to groups_per_item groups of that qubit's segment;
 // each filter survivor is queued as (sample, slot) in the warp's queue, which
 // is verified in full rounds whenever the next group might not fit, and once
 // more at the end.
@@ -564,7 +568,7 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
   for (int qq = threadIdx.x; qq < a.nq; qq += blockDim.x) s_qoff[qq] = list_len(a.qcnt[qq], a.n_unq);
   for (int sg = threadIdx.x; sg < a.n_segs; sg += blockDim.x) {
     const int4 g = __ldg(&a.segs[sg]);
-    s_cum[sg] = (list_len(a.qcnt[g.x], a.n_unq) + R - 1) / R * ((g.z - g.y + kGroupsPerItem - 1) / kGroupsPerItem);
+    s_cum[sg] = (list_len(a.qcnt[g.x], a.n_unq) + R - 1) / R * ((g.z - g.y + a.groups_per_item - 1) / a.groups_per_item);
   }
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -589,23 +593,23 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
   uint32_t vmask = 0;
   while (true) {
     unsigned long long itu = 0;
-    if (lane == 0) itu = atomicAdd(a.item_counter, (unsigned long long)kItemsPerGrab);
+    if (lane == 0) itu = atomicAdd(a.item_counter, (unsigned long long)a.items_per_grab);
     const int64_t it0 = (int64_t)__shfl_sync(kFull, itu, 0);
     if (it0 >= n_items) break;
-    const int64_t it1 = it0 + kItemsPerGrab < n_items ? it0 + kItemsPerGrab : n_items;
+    const int64_t it1 = it0 + a.items_per_grab < n_items ? it0 + a.items_per_grab : n_items;
     for (int64_t it = it0; it < it1; ++it) {
       int lo = 0, hi = a.n_segs;  // s_cum[lo] <= it < s_cum[hi]
       while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
         if (s_cum[mid] <= it) lo = mid; else hi = mid;
       }
-      // item = (segment, batch of R list entries, chunk of kGroupsPerItem groups)
+      // item = (segment, batch of R list entries, chunk of groups_per_item groups)
       const int4 sg = __ldg(&a.segs[lo]);
-      const int n_chunks = (sg.z - sg.y + kGroupsPerItem - 1) / kGroupsPerItem;
+      const int n_chunks = (sg.z - sg.y + a.groups_per_item - 1) / a.groups_per_item;
       const int64_t local = it - s_cum[lo];
       const int64_t batch = local < 0x7FFFFFFF ? (int64_t)((uint32_t)local / (uint32_t)n_chunks) : local / n_chunks;
-      const int g0 = sg.y + (int)(local - batch * n_chunks) * kGroupsPerItem;
-      const int g1 = g0 + kGroupsPerItem < sg.z ? g0 + kGroupsPerItem : sg.z;
+      const int g0 = sg.y + (int)(local - batch * n_chunks) * a.groups_per_item;
+      const int g1 = g0 + a.groups_per_item < sg.z ? g0 + a.groups_per_item : sg.z;
       if (lo != cur_seg || batch != cur_batch) {  // new rows (consecutive chunks share them)
         cur_seg = lo;
         cur_batch = batch;
@@ -673,7 +677,7 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
   }
   __syncwarp();
   verify_queue<W, MODE>(q, qn, sv, rs, a);
-  if (MODE == kEmit && rs.base >= 0)  // mark the unused tail of the last chunk
+  if ((MODE == kEmit || MODE == kEmitHalf) && rs.base >= 0)  // mark the unused tail of the last chunk
     for (int f = rs.fill + lane; f < kRecChunk; f += 32) a.sc.rec_i[rs.base + f] = kNoRecord;
 }
 
@@ -1208,9 +1212,9 @@ static cudaError_t launch_init(int mode, int64_t rows, int64_t rb, int has_diag,
 
 cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L,
                                int64_t rb, int64_t re, int64_t* rp, uint32_t* pj, uint32_t* pk, int mode,
-                               const PairScratch* sc, cudaStream_t s) {
+                               const PairScratch* sc, cudaStream_t s, const SearchTune& tune) {
   if (ham->n_srch >= (int64_t(1) << 24) || ham->n_xy >= (int64_t(1) << 29)) return cudaErrorInvalidValue;
-  if (mode == kEmit && !sc) return cudaErrorInvalidValue;
+  if ((mode == kEmit || mode == kEmitHalf) && !sc) return cudaErrorInvalidValue;
   const int64_t rows = re - rb;
   auto* ctr = (unsigned long long*)(stage + L.off_counters);
   auto* status = (int32_t*)(stage + offsetof(StageHeader, status));
@@ -1243,18 +1247,23 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stag
   if (sc) a.sc = *sc;
   a.status = status;
   a.item_counter = ctr + kCtrItems;
+  a.items_per_grab = std::max(1, tune.terms_grab);
+  a.groups_per_item = std::max(1, tune.terms_groups);
   cudaError_t e;
-  if ((e = launch_init(mode, rows, rb, ham->has_diag, rp, rp, cursor, 0, pj, pk, -1, nullptr, status, s)) !=
-      cudaSuccess)
+  if (mode != kEmitHalf &&
+      (e = launch_init(mode, rows, rb, ham->has_diag, rp, rp, cursor, 0, pj, pk, -1, nullptr, status, s)) !=
+          cudaSuccess)
     return e;
-  if (mode == kEmit && (e = cudaMemsetAsync(sc->cursor, 0, 2 * sizeof(int64_t), s)) != cudaSuccess) return e;
+  if ((mode == kEmit || mode == kEmitHalf) && (e = cudaMemsetAsync(sc->cursor, 0, 2 * sizeof(int64_t), s)) != cudaSuccess)
+    return e;
   if ((e = cudaMemsetAsync(ctr + kCtrItems, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
   if (ham->n_segs > 0) {
 #define NQS_TERMS(WW)                                                            \
   case WW:                                                                       \
     if (mode == kCount) e = launch_terms_w<WW, kCount>(a, L, s);                 \
     else if (mode == kFill) e = launch_terms_w<WW, kFill>(a, L, s);              \
-    else e = launch_terms_w<WW, kEmit>(a, L, s);                                 \
+    else if (mode == kEmit) e = launch_terms_w<WW, kEmit>(a, L, s);              \
+    else e = launch_terms_w<WW, kEmitHalf>(a, L, s);                             \
     break;
     switch (ham->W) {
       NQS_TERMS(1)
@@ -1268,6 +1277,24 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stag
   }
   if (mode == kFill) return launch_sort_rows(rp, rows, nullptr, pj, pk, ham->has_diag, stage, L, s);
   return cudaSuccess;
+}
+
+// Half-stored pairs: one EMIT_HALF search over the whole batch writes every
+// unordered coupled pair {x, x'} (x != x') once, as (i, j, k) with i the
+// sample that found it, into the caller's arrays in per-warp chunks; unused
+// slots carry i = kNoRecordSlot.  The slot cursor and overflow flag live in
+// the workspace's counters.
+cudaError_t launch_find_half(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L,
+                             uint32_t* rec_i, uint32_t* rec_j, uint32_t* rec_k, int64_t capacity,
+                             cudaStream_t s) {
+  PairScratch sc;
+  std::memset(&sc, 0, sizeof(sc));
+  sc.cursor = (int64_t*)(stage + L.off_counters) + kCtrHalf;
+  sc.max_rec = capacity;
+  sc.rec_i = rec_i;
+  sc.rec_j = rec_j;
+  sc.rec_k = rec_k;
+  return launch_pairs_terms(ham, U, stage, L, 0, L.n_unq, nullptr, nullptr, nullptr, kEmitHalf, &sc, s);
 }
 
 __global__ void clear_capacity_kernel(int32_t* status) {

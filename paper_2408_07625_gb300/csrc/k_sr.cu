@@ -1,0 +1,479 @@
+// Stochastic reconfiguration on the most probable samples (Sec. "ANQS-
+// tailored stochastic reconfiguration", Eq. qgt_definition), min-SR form:
+//   w_x = p(x) / sum_SR p,  m = sum_x w_x O_x,  Obar_x = sqrt(w_x) (O_x - m),
+//   T = Obar Obar^T (N_SR x N_SR),  eps_x = sqrt(w_x) (Re E_loc(x) - E),
+//   delta = Obar^T (T + lambda I)^{-1} eps   (= (S + lambda I)^{-1} g, S the QGT).
+// The solve deflates T's known null vector sqrt(w) (sr_solve_kernel).
+// O = d log psi / d theta of the N_SR samples, FP32 [N_SR][P] (real), P large.
+//
+// T is the one dense contraction of the method: M = N = N_SR <= 128, K = P.
+// gram_kernel streams O once: each CTA takes a range of 64-column K tiles,
+// centres and scales them on the CUDA cores, splits every value into bf16
+// hi + lo (about 16 significant bits together), stores both in shared memory
+// in the tensor core's canonical K-major layout and lets one thread issue
+// tcgen05.mma (kind::f16, bf16 in, FP32 accumulate in TMEM, M = N = 128):
+// D += hi hi^T + hi lo^T + lo hi^T (the lo lo^T term is below the split's
+// error).  Two shared-memory stages; an mbarrier signalled by tcgen05.commit
+// tells the loaders when a stage's MMAs are done.  The 128 x 128 FP32
+// accumulator (128 TMEM columns) is read back with tcgen05.ld and written as
+// the CTA's partial; the partials are summed in FP64 in a fixed order.
+#include <algorithm>
+#include <cfloat>
+#include <cstring>
+
+#include <cuda_bf16.h>
+
+#include "nqs_internal.cuh"
+
+namespace nqs {
+
+constexpr int kSrRows = 128;      // N_SR padded to the MMA's M = N
+constexpr int kSrKTile = 64;      // K elements per stage (4 MMAs of K = 16)
+constexpr int kSrThreads = 128;   // 4 warps: loaders; warp w reads TMEM lanes 32w..32w+31
+constexpr int kSrStages = 2;
+constexpr int kSrTileBytes = kSrRows * kSrKTile * 2;   // one bf16 tile: 16 KB
+constexpr int kSrSmem = kSrStages * 2 * kSrTileBytes + 1024;
+constexpr long long kSrWaitLimit = 1ll << 26;          // mbarrier polls before giving up
+
+static inline int64_t a256r(int64_t v) { return (v + 255) & ~int64_t(255); }
+
+// ---------------------------------------------------------------------------
+// PTX helpers (tcgen05, mbarrier)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait: false (and the caller records an error) if the phase never completes
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+  for (long long it = 0; it < kSrWaitLimit; ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, bf16 in, FP32 accumulate
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of
+// 8 rows x 16 bytes (rows 16 B apart); lbo = byte distance between the two
+// core matrices adjacent along K, sbo = between 8-row groups.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of this architecture family; base offset 0, no swizzle
+  return d;
+}
+
+// instruction descriptor: D FP32, A and B bf16, both K-major, N = 128, M = 128
+constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kSrRows >> 3) << 17) |
+                                ((uint32_t)(kSrRows >> 4) << 24);
+
+// byte offset of (row r, k) inside a 128 x 64 tile: core matrix (r / 8, k / 8)
+// at (r / 8) * 1024 + (k / 8) * 128, then row r % 8 at 16 B and k % 8 at 2 B
+__device__ __forceinline__ uint32_t tile_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+constexpr uint32_t kSrLbo = 128, kSrSbo = 1024;
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat16 x = __float2bfloat16_rn(a), y = __float2bfloat16_rn(b);
+  return (uint32_t)__bfloat16_as_ushort(x) | ((uint32_t)__bfloat16_as_ushort(y) << 16);
+}
+
+// ---------------------------------------------------------------------------
+// Gram kernel: partial[blockIdx.x] = sum over this CTA's K tiles of Obar Obar^T
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSrThreads) gram_kernel(int n, int64_t P, const float* __restrict__ O,
+                                                          const float* __restrict__ m, const float* __restrict__ sw,
+                                                          int64_t tiles_per_cta, float* __restrict__ partial,
+                                                          int32_t* __restrict__ error) {
+  extern __shared__ __align__(1024) unsigned char sr_smem[];
+  __shared__ uint64_t bars[kSrStages];
+  __shared__ uint32_t s_taddr;
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)sr_smem + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t n_tiles = (P + kSrKTile - 1) / kSrKTile;
+  const int64_t t0 = (int64_t)blockIdx.x * tiles_per_cta;
+  const int64_t t1 = t0 + tiles_per_cta < n_tiles ? t0 + tiles_per_cta : n_tiles;
+  if (tid == 0) {
+    for (int s = 0; s < kSrStages; ++s) mbar_init(&bars[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    tmem_alloc(&s_taddr, kSrRows);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = s_taddr;
+  bool ok = true;
+  int64_t it = 0;
+  for (int64_t t = t0; t < t1; ++t, ++it) {
+    const int s = (int)(it & 1);
+    unsigned char* hi = base + s * 2 * kSrTileBytes;
+    unsigned char* lo = hi + kSrTileBytes;
+    if (it >= kSrStages && !mbar_wait(&bars[s], (uint32_t)(((it - kSrStages) >> 1) & 1))) ok = false;
+    // load, centre, scale and split 128 rows x 64 columns: thread tid takes rows r = 2 i + tid / 64,
+    // columns 4 ((tid % 64) % 16) .. + 3 of quarter (tid % 64) / 16 -- i.e. float4 groups along K
+    const int64_t k0 = t * kSrKTile;
+#pragma unroll 4
+    for (int i = 0; i < (kSrRows * kSrKTile / 4) / kSrThreads; ++i) {
+      const int g = i * kSrThreads + tid;       // float4 group index within the tile
+      const int r = g / (kSrKTile / 4);
+      const int kq = (g % (kSrKTile / 4)) * 4;  // first k of the group
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
+      if (r < n) {
+        const float s_r = __ldg(sw + r);
+        const int64_t k = k0 + kq;
+        if (k + 3 < P && (((uintptr_t)(O + (int64_t)r * P + k)) & 15) == 0) {
+          const float4 o = __ldg(reinterpret_cast<const float4*>(O + (int64_t)r * P + k));
+          const float4 mm = __ldg(reinterpret_cast<const float4*>(m + k));
+          v[0] = s_r * (o.x - mm.x); v[1] = s_r * (o.y - mm.y); v[2] = s_r * (o.z - mm.z); v[3] = s_r * (o.w - mm.w);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (k + j < P) v[j] = s_r * (__ldg(O + (int64_t)r * P + k + j) - __ldg(m + k + j));
+        }
+      }
+      float h[4], l[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        h[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
+        l[j] = v[j] - h[j];
+      }
+      const uint32_t off = tile_off(r, kq);
+      *reinterpret_cast<uint2*>(hi + off) = make_uint2(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]));
+      *reinterpret_cast<uint2*>(lo + off) = make_uint2(pack_bf16x2(l[0], l[1]), pack_bf16x2(l[2], l[3]));
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t sh = smem_u32(hi), sl = smem_u32(lo);
+#pragma unroll
+      for (int j = 0; j < kSrKTile / 16; ++j) {
+        const uint32_t adv = (uint32_t)j * 2 * kSrLbo;   // two core matrices along K per MMA
+        const uint64_t dh = umma_desc(sh + adv, kSrLbo, kSrSbo);
+        const uint64_t dl = umma_desc(sl + adv, kSrLbo, kSrSbo);
+        mma_bf16(taddr, dh, dh, kIdescBf16, (it > 0 || j > 0) ? 1u : 0u);
+        mma_bf16(taddr, dh, dl, kIdescBf16, 1u);
+        mma_bf16(taddr, dl, dh, kIdescBf16, 1u);
+      }
+      mma_commit(&bars[s]);
+    }
+    __syncthreads();
+  }
+  // wait for the last stage's MMAs (they complete in order), then read D
+  if (it > 0) {
+    const int64_t last = it - 1;
+    if (!mbar_wait(&bars[last & 1], (uint32_t)((last >> 1) & 1))) ok = false;
+  }
+  tc_fence_after();
+  const int row = warp * 32 + (tid & 31);
+  float* out = partial + (int64_t)blockIdx.x * kSrRows * kSrRows + (int64_t)row * kSrRows;
+  if (ok && it > 0) {
+#pragma unroll
+    for (int c = 0; c < kSrRows; c += 32) {
+      float v[32];
+      tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) out[c + i] = v[i];
+    }
+  } else {
+    for (int c = 0; c < kSrRows; ++c) out[c] = 0.f;
+  }
+  if (!ok && (tid & 31) == 0) atomicOr(error, kStatusLimit);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(taddr, kSrRows);
+}
+
+// ---------------------------------------------------------------------------
+// weights, column mean, Gram sum + regularised solve, step
+// ---------------------------------------------------------------------------
+// w = p / sum p (p = exp(2 (a - max a))), sqrt(w) as FP32 for the Gram kernel and FP64
+__global__ void sr_weights_kernel(int n, const double* __restrict__ a, double* __restrict__ w,
+                                  float* __restrict__ swf) {
+  __shared__ double sh[kSrRows];
+  const int t = threadIdx.x;
+  double amax = -DBL_MAX;
+  for (int i = 0; i < n; ++i) amax = fmax(amax, a[i]);
+  const double p = t < n ? exp(2.0 * (a[t] - amax)) : 0.0;
+  sh[t] = p;
+  __syncthreads();
+  if (t == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += sh[i];
+    for (int i = 0; i < n; ++i) w[i] = sh[i] / s;
+  }
+  __syncthreads();
+  if (t < n) swf[t] = (float)sqrt(w[t]);
+}
+
+// m_p = sum_x w_x O_xp (FP64 accumulation over the N_SR rows), stored FP32
+__global__ void sr_mean_kernel(int n, int64_t P, const float* __restrict__ O, const double* __restrict__ w,
+                               float* __restrict__ m) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int x = 0; x < n; ++x) s += __ldg(w + x) * (double)__ldg(O + (int64_t)x * P + p);
+    m[p] = (float)s;
+  }
+}
+
+// G = sum of the CTAs' partials in CTA order (FP64), one thread per entry of the n x n block
+__global__ void sr_gram_sum_kernel(int n, int n_part, const float* __restrict__ partial, double* __restrict__ G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * n) return;
+  const int r = i / n, c = i % n;
+  double s = 0.0;
+  for (int q = 0; q < n_part; ++q) s += (double)__ldg(partial + (int64_t)q * kSrRows * kSrRows + r * kSrRows + c);
+  G[i] = s;
+}
+
+// T = (G + G^T) / 2; (T + lambda I + c u u^T) y = eps by Cholesky in FP64, one block of
+// kSrRows threads.  u = sqrt(w) is a unit null vector of the exact T (Obar^T u = sum_x w_x
+// (O_x - m) = 0), so the rank-one term changes y only along u, which the step Obar^T y
+// annihilates: delta is that of (T + lambda I)^{-1}.  With c = tr T / n the u direction
+// no longer has eigenvalue lambda, below the Gram's rounding for small lambda, which
+// would leave T + lambda I indefinite and amplify y along u by 1 / lambda.
+__global__ void sr_solve_kernel(int n, const double* __restrict__ G, const double* __restrict__ w,
+                                const double* __restrict__ eloc, const double* __restrict__ evar, double lambda,
+                                double* __restrict__ T, double* __restrict__ y, int32_t* __restrict__ error) {
+  extern __shared__ double A[];   // [n][n] then b[n]
+  double* b = A + n * n;
+  __shared__ double defl;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i) tr += G[i * n + i];
+    defl = tr / n;
+  }
+  __syncthreads();
+  for (int i = t; i < n * n; i += blockDim.x) {
+    const int r = i / n, c = i % n;
+    const double v = 0.5 * (G[i] + G[c * n + r]);
+    if (T) T[i] = v;
+    A[i] = v + (r == c ? lambda : 0.0) + defl * sqrt(w[r] * w[c]);
+  }
+  if (t < n) b[t] = sqrt(w[t]) * (eloc[t] - evar[0]);
+  __syncthreads();
+  // Cholesky A = L L^T in place (lower triangle), column by column
+  for (int j = 0; j < n; ++j) {
+    if (t == 0) {
+      double d = A[j * n + j];
+      for (int k = 0; k < j; ++k) d -= A[j * n + k] * A[j * n + k];
+      if (!(d > 0.0)) {
+        atomicOr(error, kStatusRange);
+        d = DBL_MIN;
+      }
+      A[j * n + j] = sqrt(d);
+    }
+    __syncthreads();
+    for (int i = j + 1 + t; i < n; i += blockDim.x) {
+      double s = A[i * n + j];
+      for (int k = 0; k < j; ++k) s -= A[i * n + k] * A[j * n + k];
+      A[i * n + j] = s / A[j * n + j];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {  // forward then back substitution
+    for (int i = 0; i < n; ++i) {
+      double s = b[i];
+      for (int k = 0; k < i; ++k) s -= A[i * n + k] * b[k];
+      b[i] = s / A[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double s = b[i];
+      for (int k = i + 1; k < n; ++k) s -= A[k * n + i] * b[k];
+      b[i] = s / A[i * n + i];
+    }
+  }
+  __syncthreads();
+  if (t < n) y[t] = b[t];
+}
+
+// delta_p = sum_x sqrt(w_x) (O_xp - m_p) y_x, FP32 compensated (two-sum) accumulation
+__global__ void sr_step_kernel(int n, int64_t P, const float* __restrict__ O, const float* __restrict__ m,
+                               const float* __restrict__ sw, const double* __restrict__ y, double* __restrict__ delta) {
+  __shared__ float cy[kSrRows];
+  if (threadIdx.x < n) cy[threadIdx.x] = (float)(y[threadIdx.x] * (double)sw[threadIdx.x]);
+  __syncthreads();
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+    const float mp = __ldg(m + p);
+    float s = 0.f, c = 0.f;
+    for (int x = 0; x < n; ++x) {
+      const float tm = cy[x] * (__ldg(O + (int64_t)x * P + p) - mp);
+      const float u = s + tm;
+      const float bb = u - s;
+      c += (s - (u - bb)) + (tm - bb);
+      s = u;
+    }
+    delta[p] = (double)s + (double)c;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the n_sr samples of highest probability: stable descending order of log |psi|
+// (ties by index), by a 64-bit radix sort of order-preserving keys
+// ---------------------------------------------------------------------------
+__global__ void sr_top_keys_kernel(int64_t n, const double* __restrict__ a, uint64_t* __restrict__ keys,
+                                   int32_t* __restrict__ idx) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = a[i];
+    if (v == 0.0) v = 0.0;
+    const uint64_t u = (uint64_t)__double_as_longlong(v);
+    keys[i] = ~((u >> 63) ? ~u : (u | 0x8000000000000000ull));
+    idx[i] = (int32_t)i;
+  }
+}
+
+int64_t sr_top_scratch_bytes(int64_t n) {
+  const int64_t m = std::max<int64_t>(n, 1);
+  return a256r(8 * m) * 2 + a256r(4 * m) * 2 + a256r(4 * 256 * sort_blocks(m)) + a256r(4 * sort_scan_partials(m));
+}
+
+cudaError_t launch_sr_top(int64_t n, const double* a, int64_t n_sr, int32_t* out, void* scratch, cudaStream_t s) {
+  char* p = (char*)scratch;
+  const int64_t m = std::max<int64_t>(n, 1);
+  uint64_t* k0 = (uint64_t*)p; p += a256r(8 * m);
+  uint64_t* k1 = (uint64_t*)p; p += a256r(8 * m);
+  int32_t* i0 = (int32_t*)p; p += a256r(4 * m);
+  int32_t* i1 = (int32_t*)p; p += a256r(4 * m);
+  int32_t* hist = (int32_t*)p; p += a256r(4 * 256 * sort_blocks(m));
+  int32_t* part = (int32_t*)p;
+  sr_top_keys_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * num_sms())), 256, 0, s>>>(
+      n, a, k0, i0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  uint64_t* kbuf[2] = {k1, k0};
+  int32_t* ibuf[2] = {i1, i0};
+  int out_buf = -1;
+  if ((e = launch_sort_words(k0, i0, n, 1, 8, kbuf, ibuf, hist, part, &out_buf, s)) != cudaSuccess) return e;
+  const int32_t* order = out_buf >= 0 ? ibuf[out_buf] : i0;
+  return cudaMemcpyAsync(out, order, 4 * std::min(n, n_sr), cudaMemcpyDeviceToDevice, s);
+}
+
+struct SrScratch {
+  double* w;
+  float* sw;
+  float* m;
+  float* partial;
+  double* G;
+  double* y;
+  int32_t* error;
+  int64_t n_part;
+  int64_t bytes;
+};
+
+static SrScratch sr_scratch_view(char* base, int64_t P, int n_part) {
+  SrScratch v;
+  std::memset(&v, 0, sizeof(v));
+  int64_t off = 0;
+  auto take = [&](int64_t bytes) { char* p = base ? base + off : nullptr; off = a256r(off + bytes); return p; };
+  v.error = (int32_t*)take(256);
+  v.w = (double*)take(8 * kSrRows);
+  v.sw = (float*)take(4 * kSrRows);
+  v.y = (double*)take(8 * kSrRows);
+  v.G = (double*)take(8 * kSrRows * kSrRows);
+  v.m = (float*)take(4 * std::max<int64_t>(P, 1) + 16);
+  v.partial = (float*)take(4 * (int64_t)n_part * kSrRows * kSrRows);
+  v.n_part = n_part;
+  v.bytes = off;
+  return v;
+}
+
+static int sr_parts() { return 2 * num_sms(); }
+
+int64_t sr_scratch_bytes(int64_t P) { return sr_scratch_view(nullptr, P, sr_parts()).bytes; }
+
+cudaError_t launch_sr_step(int n, int64_t P, const float* O, const double* a, const double* eloc,
+                           const double* evar, double lambda, void* scratch, double* delta, double* T,
+                           int32_t* status_out, cudaStream_t s) {
+  const SrScratch sc = sr_scratch_view((char*)scratch, P, sr_parts());
+  cudaError_t e = cudaMemsetAsync(sc.error, 0, 4, s);
+  if (e != cudaSuccess) return e;
+  sr_weights_kernel<<<1, kSrRows, 0, s>>>(n, a, sc.w, sc.sw);
+  const int sms = num_sms();
+  sr_mean_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, 8 * sms)), 256, 0, s>>>(n, P, O, sc.w,
+                                                                                                        sc.m);
+  const int64_t n_tiles = (P + kSrKTile - 1) / kSrKTile;
+  const int64_t per = (n_tiles + sc.n_part - 1) / sc.n_part;
+  if ((e = cudaFuncSetAttribute(gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSrSmem)) != cudaSuccess)
+    return e;
+  gram_kernel<<<(int)sc.n_part, kSrThreads, kSrSmem, s>>>(n, P, O, sc.m, sc.sw, per, sc.partial, sc.error);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t solve_smem = sizeof(double) * (size_t)(n * n + n);
+  if ((e = cudaFuncSetAttribute(sr_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem)) !=
+      cudaSuccess)
+    return e;
+  sr_gram_sum_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, (int)sc.n_part, sc.partial, sc.G);
+  sr_solve_kernel<<<1, kSrRows, solve_smem, s>>>(n, sc.G, sc.w, eloc, evar, lambda, T, sc.y, sc.error);
+  sr_step_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, 8 * sms)), 256, 0, s>>>(
+      n, P, O, sc.m, sc.sw, sc.y, delta);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int32_t err = 0;
+  if ((e = cudaMemcpyAsync(&err, sc.error, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  *status_out = err;
+  return cudaSuccess;
+}
+
+}  // namespace nqs

@@ -98,6 +98,8 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 2048 keys per block
 
+int64_t sort_blocks(int64_t n) { return (std::max<int64_t>(n, 1) + kSortTile - 1) / kSortTile; }
+
 // v[idx] without dynamic indexing of a register array
 template <int W>
 __device__ __forceinline__ uint64_t word_at(const uint64_t (&v)[W], int idx) {
@@ -157,6 +159,75 @@ __global__ void __launch_bounds__(1024) sort_scan_kernel(int32_t* __restrict__ d
     run += v;
   }
 }
+
+// Exclusive scan of a long int32 array by many blocks: each block scans a
+// tile of kScanTileI keys (warp scans, then the warps' totals), one thread
+// turns the tile totals into offsets, and every block adds its offset.
+constexpr int kScanTileI = 2048;
+
+__global__ void __launch_bounds__(1024) scan_tile_i32_kernel(int32_t* __restrict__ d, int64_t m,
+                                                             int32_t* __restrict__ tile_sum) {
+  __shared__ int32_t wsum[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTileI;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t e0 = base + 2 * threadIdx.x;
+  const int32_t v0 = e0 < m ? d[e0] : 0, v1 = e0 + 1 < m ? d[e0 + 1] : 0;
+  const int32_t t = v0 + v1;
+  int32_t incl = t;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += x;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int32_t w = wsum[lane];
+    int32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t x = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+      if (lane >= o) wi += x;
+    }
+    wsum[lane] = wi - w;
+    if (lane == 31) tile_sum[blockIdx.x] = wi;
+  }
+  __syncthreads();
+  const int32_t ex = wsum[warp] + incl - t;
+  if (e0 < m) d[e0] = ex;
+  if (e0 + 1 < m) d[e0 + 1] = ex + v0;
+}
+
+__global__ void scan_tile_offsets_kernel(int32_t* __restrict__ tile_sum, int64_t tiles) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int32_t run = 0;
+  for (int64_t t = 0; t < tiles; ++t) {
+    const int32_t v = tile_sum[t];
+    tile_sum[t] = run;
+    run += v;
+  }
+}
+
+__global__ void scan_tile_add_kernel(int32_t* __restrict__ d, int64_t m, const int32_t* __restrict__ tile_sum) {
+  const int64_t e = (int64_t)blockIdx.x * kScanTileI + threadIdx.x;
+  const int32_t off = tile_sum[blockIdx.x];
+  if (e < m) d[e] += off;
+  if (e + 1024 < m && threadIdx.x + 1024 < kScanTileI) d[e + 1024] += off;
+}
+
+// exclusive scan of m ints: one block when small, tiles (partial: ceil(m / 2048) ints) when large
+static void scan_i32(int32_t* d, int64_t m, int32_t* partial, cudaStream_t s) {
+  if (!partial || m <= (int64_t)1 << 18) {
+    sort_scan_kernel<<<1, 1024, 0, s>>>(d, m);
+    return;
+  }
+  const int64_t tiles = (m + kScanTileI - 1) / kScanTileI;
+  scan_tile_i32_kernel<<<(unsigned)tiles, 1024, 0, s>>>(d, m, partial);
+  scan_tile_offsets_kernel<<<1, 32, 0, s>>>(partial, tiles);
+  scan_tile_add_kernel<<<(unsigned)tiles, 1024, 0, s>>>(d, m, partial);
+}
+
+int64_t sort_scan_partials(int64_t n) { return 256 * sort_blocks(n) / kScanTileI + 1; }
 
 // Stable scatter: warp w of a block owns keys [t0 + 256 w, t0 + 256 w + 256),
 // visited in rounds of 32; equal digits are ranked by (round, lane).
@@ -402,16 +473,15 @@ cudaError_t launch_trie_build(const nqs_ham* ham, const uint64_t* U, int64_t n, 
 // Buffers: kbuf[2] of n*W words, ibuf[2] of n ints, hist of 256 * sort_blocks(n)
 // ints.  The result is in kbuf[*out] / ibuf[*out].
 // --------------------------------------------------------------------------
-int64_t sort_blocks(int64_t n) { return (std::max<int64_t>(n, 1) + kSortTile - 1) / kSortTile; }
 
 template <int W>
 static cudaError_t sort_words_w(const uint64_t* kin, const int32_t* iin, int64_t n, int n_bytes, uint64_t* kbuf[2],
-                                int32_t* ibuf[2], int32_t* hist, int* out, cudaStream_t s) {
+                                int32_t* ibuf[2], int32_t* hist, int32_t* partial, int* out, cudaStream_t s) {
   const int nblk = (int)sort_blocks(n);
   int cur = 0;
   for (int g = 0; g < n_bytes; ++g) {
     sort_hist_kernel<W, false><<<nblk, kSortThreads, 0, s>>>(kin, n, g, hist, nblk);
-    sort_scan_kernel<<<1, 1024, 0, s>>>(hist, 256 * (int64_t)nblk);
+    scan_i32(hist, 256 * (int64_t)nblk, partial, s);
     sort_scatter_kernel<W, false><<<nblk, kSortThreads, 0, s>>>(kin, iin, n, g, hist, nblk, kbuf[cur], ibuf[cur]);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -424,14 +494,15 @@ static cudaError_t sort_words_w(const uint64_t* kin, const int32_t* iin, int64_t
 }
 
 cudaError_t launch_sort_words(const uint64_t* kin, const int32_t* iin, int64_t n, int W, int n_bytes,
-                              uint64_t* kbuf[2], int32_t* ibuf[2], int32_t* hist, int* out, cudaStream_t s) {
+                              uint64_t* kbuf[2], int32_t* ibuf[2], int32_t* hist, int32_t* partial, int* out,
+                              cudaStream_t s) {
   *out = -1;
   if (n == 0 || n_bytes == 0) return cudaSuccess;
   switch (W) {
-    case 1: return sort_words_w<1>(kin, iin, n, n_bytes, kbuf, ibuf, hist, out, s);
-    case 2: return sort_words_w<2>(kin, iin, n, n_bytes, kbuf, ibuf, hist, out, s);
-    case 3: return sort_words_w<3>(kin, iin, n, n_bytes, kbuf, ibuf, hist, out, s);
-    default: return sort_words_w<4>(kin, iin, n, n_bytes, kbuf, ibuf, hist, out, s);
+    case 1: return sort_words_w<1>(kin, iin, n, n_bytes, kbuf, ibuf, hist, partial, out, s);
+    case 2: return sort_words_w<2>(kin, iin, n, n_bytes, kbuf, ibuf, hist, partial, out, s);
+    case 3: return sort_words_w<3>(kin, iin, n, n_bytes, kbuf, ibuf, hist, partial, out, s);
+    default: return sort_words_w<4>(kin, iin, n, n_bytes, kbuf, ibuf, hist, partial, out, s);
   }
 }
 
@@ -465,6 +536,7 @@ struct TrieArgs {
   int32_t* status;
   const int32_t* trie_ok;
   unsigned long long* row_counter;
+  int pop;                           // node pairs popped per step (<= 32)
 };
 
 // entry: t (23 bits) | level (9 bits) << 23 | XY node << 32
@@ -524,7 +596,7 @@ __global__ void __launch_bounds__(kTrieThreads) pairs_trie_kernel(const TrieArgs
   const TrieRec<W>* rec = reinterpret_cast<const TrieRec<W>*>(a.rec);
   const int n_rows = (int)(a.row_end - a.row_begin);
   const int64_t pbase = MODE == kFill ? a.rp[0] : 0;
-  // deepest stack the step rule allows: below cap - N - 34 a step adds <= 32,
+  // deepest stack the step rule allows: below cap - N - 34 a step adds <= pop <= 32,
   // above it a single pop adds at most one entry per level still to descend
   const int dfs_from = kTrieStack - a.n_qubits - 34;
   while (true) {
@@ -549,7 +621,7 @@ __global__ void __launch_bounds__(kTrieThreads) pairs_trie_kernel(const TrieArgs
     __syncwarp();
     bool ok = true;
     while (sc > 0) {
-      const int k = (sc <= dfs_from) ? min(32, sc) : 1;
+      const int k = (sc <= dfs_from) ? min(a.pop, sc) : 1;
       const bool act = lane < k;
       const uint64_t ent = act ? st[sc - k + lane] : 0ull;
       __syncwarp();
@@ -645,7 +717,7 @@ static cudaError_t launch_trie_w(const TrieArgs& args, int64_t rows, cudaStream_
 
 cudaError_t launch_pairs_trie(const nqs_ham* ham, const uint64_t* U, int64_t n, const char* stage,
                               const StageHeader& L, int64_t rb, int64_t re, int64_t* rp, uint32_t* pj,
-                              uint32_t* pk, int mode, cudaStream_t s) {
+                              uint32_t* pk, int mode, cudaStream_t s, const SearchTune& tune) {
   if (n >= (int64_t(1) << 23) || ham->n_qubits > 255 || mode == kEmit) return cudaErrorInvalidValue;
   TrieView v = trie_view((char*)stage, L);
   TrieArgs a;
@@ -672,6 +744,7 @@ cudaError_t launch_pairs_trie(const nqs_ham* ham, const uint64_t* U, int64_t n, 
   a.status = (int32_t*)(stage + offsetof(StageHeader, status));
   a.trie_ok = (const int32_t*)(stage + offsetof(StageHeader, trie_ok));
   a.row_counter = (unsigned long long*)(stage + L.off_counters) + kCtrTrie;
+  a.pop = std::min(32, std::max(1, tune.trie_pop));
   cudaError_t e = cudaMemsetAsync(a.row_counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   const int64_t rows = re - rb;

@@ -134,11 +134,17 @@ struct Melem {
   const double* quad_d;
   int64_t n_xy;            // patterns (pair indices k are below it)
   int64_t n_unq;           // samples of the batch (pair columns j are below it)
+  // imaginary parts of the coefficients and local tables (complex H: terms with odd |Y|)
+  const float2* cf_im;
+  const double* cd_im;
+  const float2* fv_f_im;
+  const double* fv_d_im;
 };
 
 inline Melem melem_tables(const nqs_ham* h, int64_t n_unq) {
   return Melem{h->row_ptr, h->yz, h->coef_f, h->coef, h->has_diag, h->heavy_end, h->fm,
-               h->fv_f, h->fv_d, h->fz, h->diag_quad, h->quad_f, h->quad_d, h->n_xy, n_unq};
+               h->fv_f, h->fv_d, h->fz, h->diag_quad, h->quad_f, h->quad_d, h->n_xy, n_unq,
+               h->coef_f_im, h->coef_im, h->fv_f_im, h->fv_d_im};
 }
 
 // A pair's column and pattern index lie in range by construction of the
@@ -238,6 +244,69 @@ __device__ __forceinline__ typename Pol::T melem_diag(const uint64_t (&x)[W], co
     before += cnt;
   }
   return Pol::warp_sum(h);
+}
+
+// Complex H (terms with an odd number of Y): the same forms with both parts.
+// A term's coefficient h i^{|Y|} is real or imaginary; the sign
+// (-1)^{|x' & YZ|} applies to both parts alike.
+template <class Pol, int W>
+__device__ __forceinline__ void melem_lane_c(const uint64_t (&xp)[W], uint32_t k, int4 fm, const Melem& M,
+                                             typename Pol::T& hr, typename Pol::T& hi) {
+  using T = typename Pol::T;
+  const int kind = fm.x & 15;
+  if (kind == kForm::Local) {
+    const int nb = fm.x >> 4;
+    uint32_t u = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (i < nb) {
+        const int q = (fm.w >> (8 * i)) & 255;
+        u |= (uint32_t)((xp[q >> 6] >> (q & 63)) & 1ull) << i;
+      }
+    }
+    const T vr = Pol::val(M.fv_f, M.fv_d, (int64_t)fm.y + u);
+    const T vi = Pol::val(M.fv_f_im, M.fv_d_im, (int64_t)fm.y + u);
+    const bool neg = parity_and<W>(xp, M.fz + (int64_t)fm.z * W);
+    hr = neg ? Pol::neg(vr) : vr;
+    hi = neg ? Pol::neg(vi) : vi;
+    return;
+  }
+  hr = Pol::zero();
+  hi = Pol::zero();
+  const int64_t t0 = __ldg(M.t_ptr + k), t1 = __ldg(M.t_ptr + k + 1);
+#pragma unroll 2
+  for (int64_t l = t0; l < t1; ++l) {
+    const uint32_t par = parity_and<W>(xp, M.yz + l * W);
+    Pol::acc(hr, Pol::coef(M.cf, M.cd, l, par));
+    Pol::acc(hi, Pol::coef(M.cf_im, M.cd_im, l, par));
+  }
+  hr = Pol::fin(hr);
+  hi = Pol::fin(hi);
+}
+
+template <class Pol, int W>
+__device__ __forceinline__ void melem_warp_c(const uint64_t (&xp)[W], int64_t t0, int64_t t1, const Melem& M,
+                                             typename Pol::T& hr, typename Pol::T& hi) {
+  using T = typename Pol::T;
+  const int lane = threadIdx.x & 31;
+  T ar = Pol::zero(), ai = Pol::zero();
+  for (int64_t b = t0; b < t1; b += 2 * 32) {
+    T cr[2], ci[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int64_t l = b + 32 * u + lane;
+      const uint32_t par = l < t1 ? parity_and<W>(xp, M.yz + l * W) : 0u;
+      cr[u] = l < t1 ? Pol::coef(M.cf, M.cd, l, par) : Pol::zero();
+      ci[u] = l < t1 ? Pol::coef(M.cf_im, M.cd_im, l, par) : Pol::zero();
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      Pol::acc(ar, cr[u]);
+      Pol::acc(ai, ci[u]);
+    }
+  }
+  hr = Pol::warp_sum(ar);
+  hi = Pol::warp_sum(ai);
 }
 
 }  // namespace nqs

@@ -25,6 +25,7 @@ constexpr int kCtrBigCount = 1;              // long rows queued for the block s
 constexpr int kCtrBigNext = 2;               // long rows taken by the block sort
 constexpr int kCtrBatch = 3;                 // LoopOverBatch row batches taken
 constexpr int kCtrTrie = 4;                  // LoopOverTrie rows taken
+constexpr int kCtrHalf = 8;                  // half-stored records: slots taken (8), overflow flag (9)
 
 // status bits (device status word)
 constexpr int kStatusDuplicate = 1;
@@ -87,11 +88,19 @@ struct nqs_ham_dev {
   int diag_quad = 0;             // the diagonal pattern uses the quadratic form
   double* quad_d = nullptr;      // [1 + 64W + (64W)^2]
   float2* quad_f = nullptr;
+  // complex H: strings with an odd number of Y have imaginary coefficients
+  // h i^{|Y|}; their parts live in the *_im arrays (zero for real terms) and
+  // the local tables get imaginary parts too (the diagonal is always real)
+  int cplx = 0;
+  double* coef_im = nullptr;     // [n_terms]
+  float2* coef_f_im = nullptr;
+  double* fv_d_im = nullptr;     // same indexing as fv_d
+  float2* fv_f_im = nullptr;
 
   // host copies (export, tests)
   std::vector<uint64_t> h_xy, h_yz;
   std::vector<int64_t> h_row_ptr;
-  std::vector<double> h_coef;
+  std::vector<double> h_coef, h_coef_im;
   std::vector<uint32_t> h_hash_basis;
   int device = 0;
 };
@@ -143,9 +152,20 @@ int cuda_fail(cudaError_t e, const char* what);
 cudaError_t launch_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, char* stage,
                          const StageHeader& L, cudaStream_t s);
 
+// launch parameters of the searches, chosen per instance by the batched plan's
+// autotuner: LoopOverTerms work items per atomic and search-table groups per
+// item; LoopOverTrie node pairs popped per step
+struct SearchTune {
+  int terms_grab = 4;
+  int terms_groups = 16;
+  int trie_pop = 32;
+};
+
 // search modes: COUNT writes per-row counts, FILL writes pairs at given CSR
-// offsets, EMIT writes per-row counts and the pairs into scratch records
-enum SearchMode { kCount = 0, kFill = 1, kEmit = 2 };
+// offsets, EMIT writes per-row counts and the pairs into scratch records,
+// EMIT_HALF writes only the records (each unordered pair once, whole batch)
+enum SearchMode { kCount = 0, kFill = 1, kEmit = 2, kEmitHalf = 3 };
+constexpr uint32_t kNoRecordSlot = 0xFFFFFFFFu;   // i of an unused record slot
 
 struct PairScratch {        // one-pass search scratch (caller memory): found pairs (i, j, k)
   int64_t max_rec;
@@ -165,7 +185,8 @@ PairScratch pair_scratch_view(void* base, int64_t rows, int64_t bytes);
 cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stage,
                                const StageHeader& L, int64_t row_begin, int64_t row_end,
                                int64_t* counts_or_rowptr, uint32_t* pair_j, uint32_t* pair_k,
-                               int mode, const PairScratch* scratch, cudaStream_t s);
+                               int mode, const PairScratch* scratch, cudaStream_t s,
+                               const SearchTune& tune = SearchTune());
 
 // clear the capacity bit of the status word (stream-ordered)
 cudaError_t launch_clear_capacity(char* stage, cudaStream_t s);
@@ -189,15 +210,17 @@ cudaError_t launch_trie_build(const nqs_ham* ham, const uint64_t* U, int64_t n, 
 cudaError_t launch_pairs_trie(const nqs_ham* ham, const uint64_t* U, int64_t n, const char* stage,
                               const StageHeader& L, int64_t row_begin, int64_t row_end,
                               int64_t* counts_or_rowptr, uint32_t* pair_j, uint32_t* pair_k,
-                              int mode, cudaStream_t s);
+                              int mode, cudaStream_t s, const SearchTune& tune = SearchTune());
 
 cudaError_t launch_scan(int64_t* data, int64_t n, char* stage, const StageHeader& L,
                         cudaStream_t s);
 
 // LSD radix sort of W-word keys in numeric order with an int32 payload (k_trie.cu)
 int64_t sort_blocks(int64_t n);
+int64_t sort_scan_partials(int64_t n);   // ints of the tiled histogram scan for n keys
 cudaError_t launch_sort_words(const uint64_t* kin, const int32_t* iin, int64_t n, int W, int n_bytes,
-                              uint64_t* kbuf[2], int32_t* ibuf[2], int32_t* hist, int* out, cudaStream_t s);
+                              uint64_t* kbuf[2], int32_t* ibuf[2], int32_t* hist, int32_t* partial, int* out,
+                              cudaStream_t s);
 
 // exact local energy over the coupled candidates (k_cand.cu)
 int64_t cand_scratch_bytes(const nqs_ham* ham, int64_t n_unq);
@@ -231,6 +254,35 @@ cudaError_t launch_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n
 cudaError_t launch_variational_energy(int64_t n, const double* a, const double* eloc_re,
                                       char* work, double* out, cudaStream_t s);
 cudaError_t launch_evar_combine(const double* parts, int k, double* out, cudaStream_t s);
+
+// stochastic reconfiguration on the most probable samples (k_sr.cu)
+int64_t sr_scratch_bytes(int64_t P);
+int64_t sr_top_scratch_bytes(int64_t n);
+cudaError_t launch_sr_top(int64_t n, const double* a, int64_t n_sr, int32_t* out, void* scratch, cudaStream_t s);
+cudaError_t launch_sr_step(int n, int64_t P, const float* O, const double* a, const double* eloc,
+                           const double* evar, double lambda, void* scratch, double* delta, double* T,
+                           int32_t* status_out, cudaStream_t s);
+
+// autoregressive sampling without replacement, one qubit (k_sample.cu)
+int64_t sample_scratch_bytes(int64_t n_parents);
+cudaError_t launch_gumbel_level(int W, int level, int64_t n, const uint64_t* px, const double* pl, const double* plt,
+                                const double* logp, const double* G, int64_t K, void* scratch, uint64_t* cx,
+                                double* cl, double* clt, int64_t* n_out, cudaStream_t s);
+
+// half-stored pairs: the records of one EMIT_HALF search (k_half section of k_energy.cu)
+cudaError_t launch_find_half(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L,
+                             uint32_t* rec_i, uint32_t* rec_j, uint32_t* rec_k, int64_t capacity,
+                             cudaStream_t s);
+cudaError_t launch_local_energy_half(const nqs_ham* ham, const uint64_t* U, int64_t n, const char* stage,
+                                     const StageHeader& L, bool cplx, const uint32_t* ri, const uint32_t* rj,
+                                     const uint32_t* rk, int64_t n_slots, int precision, double* er, double* ei,
+                                     double* hd, void* hrec, cudaStream_t s);
+cudaError_t launch_backward_half(const nqs_ham* ham, const uint64_t* U, int64_t n, char* stage,
+                                 const StageHeader& L, bool cplx, const double* a, const uint32_t* ri,
+                                 const uint32_t* rj, const uint32_t* rk, int64_t n_slots, const void* hrec,
+                                 const double* er, const double* ei, const double* hd, const double* evar,
+                                 const double* g_re, const double* g_im, const double* g_evar, int precision,
+                                 double* gre, double* gim, cudaStream_t s);
 
 cudaError_t launch_backward(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
                             char* stage, const StageHeader& L, bool cplx,

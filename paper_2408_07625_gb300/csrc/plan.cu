@@ -1,10 +1,13 @@
 // Batched evaluation of many independent (Hamiltonian, sample batch) instances
 // as one CUDA graph: planning stages every instance, picks its FindCoupledPairs
-// schedule by timing the candidates (LoopOverTerms, Alg. 2A; LoopOverBatch,
-// Alg. 2B; LoopOverTrie, Alg. 2C with the prefix-tree build of Alg. 3),
+// schedule and that schedule's launch parameters by timing the candidates
+// (LoopOverTerms, Alg. 2A, with 2/4/8 work items per atomic and 8/16/32
+// table groups per item; LoopOverBatch, Alg. 2B; LoopOverTrie, Alg. 2C with
+// the prefix-tree build of Alg. 3, popping 8/16/32 node pairs per step),
 // sizes its buffers, and captures all instances' kernels on forked streams
 // into a single graph; each run is one graph launch with no host
-// synchronisation and no allocation.  Buffers sized at planning time are
+// synchronisation and no allocation.  An instance with a gradient output also
+// gets dE^var / d log psi (the closed form of the adjoint) in the graph.  Buffers sized at planning time are
 // checked on the device: an overflow sets the instance's status word and the
 // later kernels of that instance skip their work.
 #include <algorithm>
@@ -29,6 +32,7 @@ struct PlanInstance {
   int64_t capacity = 0;
   int64_t planned_pairs = 0;
   float t_terms_ms = -1.f, t_batch_ms = -1.f, t_trie_ms = -1.f;
+  SearchTune tune;
 };
 
 }  // namespace nqs
@@ -42,6 +46,7 @@ struct nqs_plan {
   std::vector<cudaEvent_t> events;
   size_t n_nodes = 0;
   size_t n_kernels = 0;
+  double* one = nullptr;   // device 1.0: the upstream of E^var for the gradients
 };
 
 namespace nqs {
@@ -60,11 +65,12 @@ static void free_plan(nqs_plan* p) {
   }
   for (auto s : p->streams) cudaStreamDestroy(s);
   for (auto e : p->events) cudaEventDestroy(e);
+  cudaFree(p->one);
   delete p;
 }
 
 // the kernels of one instance's forward pass, enqueued without host synchronisation
-static cudaError_t enqueue_instance(PlanInstance& I, int precision, cudaStream_t s) {
+static cudaError_t enqueue_instance(PlanInstance& I, int precision, const double* one, cudaStream_t s) {
   const nqs_ham* ham = I.in.ham;
   const int64_t n = I.in.n_unq;
   char* w = I.work;
@@ -83,16 +89,16 @@ static cudaError_t enqueue_instance(PlanInstance& I, int precision, cudaStream_t
       return e;
   } else if (I.schedule == NQS_SCHED_TRIE) {
     if ((e = launch_trie_build(ham, I.in.U, n, w, I.L, s)) != cudaSuccess) return e;
-    if ((e = launch_pairs_trie(ham, I.in.U, n, w, I.L, 0, n, I.row_ptr + 1, nullptr, nullptr, kCount, s)))
+    if ((e = launch_pairs_trie(ham, I.in.U, n, w, I.L, 0, n, I.row_ptr + 1, nullptr, nullptr, kCount, s, I.tune)))
       return e;
     if ((e = launch_scan(I.row_ptr + 1, n, w, I.L, s)) != cudaSuccess) return e;
     capacity_check_kernel<<<1, 32, 0, s>>>(I.row_ptr, n, I.capacity, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = launch_pairs_trie(ham, I.in.U, n, w, I.L, 0, n, I.row_ptr, I.pair_j, I.pair_k, kFill, s)))
+    if ((e = launch_pairs_trie(ham, I.in.U, n, w, I.L, 0, n, I.row_ptr, I.pair_j, I.pair_k, kFill, s, I.tune)))
       return e;
   } else {
     PairScratch sc = pair_scratch_view(I.scratch, n, I.scratch_bytes);
-    if ((e = launch_pairs_terms(ham, I.in.U, w, I.L, 0, n, I.row_ptr + 1, nullptr, nullptr, kEmit, &sc, s)))
+    if ((e = launch_pairs_terms(ham, I.in.U, w, I.L, 0, n, I.row_ptr + 1, nullptr, nullptr, kEmit, &sc, s, I.tune)))
       return e;
     if ((e = launch_scan(I.row_ptr + 1, n, w, I.L, s)) != cudaSuccess) return e;
     if ((e = launch_pairs_compact(ham, sc, w, I.L, 0, n, I.row_ptr, I.pair_j, I.pair_k, I.capacity, s)))
@@ -102,7 +108,41 @@ static cudaError_t enqueue_instance(PlanInstance& I, int precision, cudaStream_t
   if ((e = launch_local_energy(ham, I.in.U, n, w, I.L, false, 0, n, I.row_ptr, I.pair_j, I.pair_k, precision,
                                I.in.eloc_re, nullptr, I.hdiag, nullptr, s)) != cudaSuccess)
     return e;
-  return launch_variational_energy(n, I.in.logpsi_re, I.in.eloc_re, w, I.in.evar, s);
+  if ((e = launch_variational_energy(n, I.in.logpsi_re, I.in.eloc_re, w, I.in.evar, s)) != cudaSuccess) return e;
+  if (!I.in.grad) return cudaSuccess;
+  // dE^var / d Re log psi: the adjoint with no upstream on E_loc (closed form)
+  return launch_backward(ham, I.in.U, n, w, I.L, false, I.in.logpsi_re, nullptr, 0, n, I.row_ptr, I.pair_j, I.pair_k,
+                         I.in.eloc_re, nullptr, I.hdiag, I.in.evar, nullptr, nullptr, one, precision, nullptr,
+                         I.in.grad, nullptr, s);
+}
+
+// one count pass of LoopOverTerms or LoopOverTrie with the given launch
+// parameters, timed with events on the stream; *n_pairs receives the total
+static cudaError_t time_count(PlanInstance& I, int sched, const SearchTune& t, cudaStream_t s, float* ms,
+                              int64_t* n_pairs) {
+  const nqs_ham* ham = I.in.ham;
+  const int64_t n = I.in.n_unq;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return e; }
+  cudaEventRecord(e0, s);
+  e = cudaMemsetAsync(I.row_ptr, 0, sizeof(int64_t), s);
+  if (e == cudaSuccess) {
+    if (sched == NQS_SCHED_TRIE)
+      e = launch_pairs_trie(ham, I.in.U, n, I.work, I.L, 0, n, I.row_ptr + 1, nullptr, nullptr, kCount, s, t);
+    else
+      e = launch_pairs_terms(ham, I.in.U, I.work, I.L, 0, n, I.row_ptr + 1, nullptr, nullptr, kCount, nullptr, s, t);
+  }
+  if (e == cudaSuccess) e = launch_scan(I.row_ptr + 1, n, I.work, I.L, s);
+  cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(n_pairs, I.row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return e;
 }
 
 }  // namespace nqs
@@ -128,6 +168,10 @@ int nqs_batch_plan(const nqs_instance* insts, int n_inst, int precision, int fla
     const int64_t n = I.in.n_unq;
     if (!I.in.ham || !I.in.U || !I.in.logpsi_re || !I.in.eloc_re || !I.in.evar || n <= 0) {
       rc = fail(NQS_ERR_ARG, "instance " + std::to_string(i) + ": null pointer or empty batch");
+      break;
+    }
+    if (I.in.ham->cplx) {  // the plan's outputs are real E_loc^var
+      rc = fail(NQS_ERR_UNSUPPORTED, "instance " + std::to_string(i) + ": complex Hamiltonian in a batched plan");
       break;
     }
     I.L = stage_layout(I.in.ham, n);
@@ -175,10 +219,49 @@ int nqs_batch_plan(const nqs_instance* insts, int n_inst, int precision, int fla
     cudaEventDestroy(t1);
     if (rc) break;
     if (flags & 1) {
+      // launch parameters of the two tunable schedules: best of two timings per setting
+      // (the trie's tree build, timed above, is shared by its settings)
+      SearchTune best_terms, best_trie;
+      float t_terms = 1e30f, t_trie = 1e30f;
+      for (int grab : {2, 4, 8})
+        for (int groups : {8, 16, 32}) {
+          SearchTune t;
+          t.terms_grab = grab;
+          t.terms_groups = groups;
+          for (int rep = 0; rep < 2 && !rc; ++rep) {
+            float ms = 0.f;
+            int64_t np = -1;
+            if ((e = time_count(I, NQS_SCHED_TERMS, t, s, &ms, &np)) != cudaSuccess) rc = cuda_fail(e, "tuning");
+            else if (np != np_terms) rc = fail(NQS_ERR_DEVICE_LIMIT, "launch settings disagree on the pair count");
+            if (!rc && ms < t_terms) { t_terms = ms; best_terms = t; }
+          }
+        }
+      if (!rc && try_trie) {
+        const float build_ms = std::max(0.f, I.t_trie_ms);
+        float count_default = 0.f;
+        int64_t np = -1;
+        if ((e = time_count(I, NQS_SCHED_TRIE, SearchTune(), s, &count_default, &np)) != cudaSuccess)
+          rc = cuda_fail(e, "tuning");
+        const float build_only = std::max(0.f, build_ms - count_default);
+        for (int pop : {8, 16, 32}) {
+          SearchTune t;
+          t.trie_pop = pop;
+          for (int rep = 0; rep < 2 && !rc; ++rep) {
+            float ms = 0.f;
+            if ((e = time_count(I, NQS_SCHED_TRIE, t, s, &ms, &np)) != cudaSuccess) rc = cuda_fail(e, "tuning");
+            else if (np != np_terms) rc = fail(NQS_ERR_DEVICE_LIMIT, "launch settings disagree on the pair count");
+            if (!rc && build_only + ms < t_trie) { t_trie = build_only + ms; best_trie = t; }
+          }
+        }
+      }
+      if (rc) break;
+      I.t_terms_ms = t_terms;
+      if (try_trie) I.t_trie_ms = t_trie;
       I.schedule = NQS_SCHED_TERMS;
-      float best = I.t_terms_ms;
-      if (try_batch && I.t_batch_ms < best) { I.schedule = NQS_SCHED_BATCH; best = I.t_batch_ms; }
-      if (try_trie && I.t_trie_ms < best) { I.schedule = NQS_SCHED_TRIE; best = I.t_trie_ms; }
+      I.tune = best_terms;
+      float best = t_terms;
+      if (try_batch && I.t_batch_ms < best) { I.schedule = NQS_SCHED_BATCH; best = I.t_batch_ms; I.tune = SearchTune(); }
+      if (try_trie && t_trie < best) { I.schedule = NQS_SCHED_TRIE; best = t_trie; I.tune = best_trie; }
     } else
       I.schedule = (n < I.in.ham->n_xy) ? NQS_SCHED_BATCH : NQS_SCHED_TERMS;
     I.planned_pairs = np_terms;
@@ -195,6 +278,15 @@ int nqs_batch_plan(const nqs_instance* insts, int n_inst, int precision, int fla
     free_plan(p);
     return rc;
   }
+  // the upstream 1.0 of E^var for the instances' gradients (a device constant of the plan)
+  {
+    const double one = 1.0;
+    if ((e = cudaMalloc((void**)&p->one, sizeof(double))) != cudaSuccess ||
+        (e = cudaMemcpy(p->one, &one, sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      free_plan(p);
+      return fail(NQS_ERR_OOM, "cudaMalloc in nqs_batch_plan");
+    }
+  }
   // capture: fork over streams, one instance per stream round-robin, join
   const int K = std::min(8, n_inst);
   p->streams.resize(K);
@@ -209,7 +301,8 @@ int nqs_batch_plan(const nqs_instance* insts, int n_inst, int precision, int fla
   cudaEventRecord(p->events[K], cs);
   for (int k = 1; k < K; ++k) cudaStreamWaitEvent(p->streams[k], p->events[K], 0);
   cudaError_t ce = cudaSuccess;
-  for (int i = 0; i < n_inst && ce == cudaSuccess; ++i) ce = enqueue_instance(p->inst[i], precision, p->streams[i % K]);
+  for (int i = 0; i < n_inst && ce == cudaSuccess; ++i)
+    ce = enqueue_instance(p->inst[i], precision, p->one, p->streams[i % K]);
   for (int k = 1; k < K; ++k) {
     cudaEventRecord(p->events[k], p->streams[k]);
     cudaStreamWaitEvent(cs, p->events[k], 0);
@@ -268,6 +361,15 @@ int nqs_batch_info(const nqs_plan* p, int i, int64_t info[8]) {
   info[5] = (int64_t)(1000.0f * I.t_batch_ms);
   info[6] = (int64_t)(1000.0f * I.t_trie_ms);
   info[7] = (int64_t)p->n_kernels;
+  return NQS_OK;
+}
+
+int nqs_batch_tune(const nqs_plan* p, int i, int32_t tune[3]) {
+  if (!p || !tune || i < 0 || i >= (int)p->inst.size()) return fail(NQS_ERR_ARG, "bad argument");
+  const SearchTune& t = p->inst[i].tune;
+  tune[0] = t.terms_grab;
+  tune[1] = t.terms_groups;
+  tune[2] = t.trie_pop;
   return NQS_OK;
 }
 

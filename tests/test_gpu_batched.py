@@ -42,13 +42,15 @@ def small_batch():
 @pytest.mark.parametrize("precision", ["fp64", "fp32c"])
 def test_graph_matches_single_instance_and_oracle(small_batch, precision):
     items = _items(small_batch)
-    plan = nqs.BatchedPlan(items, precision=precision, autotune=True)
+    plan = nqs.BatchedPlan(items, precision=precision, autotune=True, gradients=True)
     plan.run()
     torch.cuda.synchronize()
     assert plan.status() == (0, -1)
     tol = 1e-9 if precision == "fp64" else 1e-6
+    choices = set()
     for i, (inst, (ham, U, lre)) in enumerate(zip(small_batch, items)):
         info = plan.info(i)
+        choices.add((info["schedule"], tuple(sorted(info["tune"].items()))))
         batch = nqs.Batch(ham, U)
         ref = nqs.evaluate(batch, lre, None, precision, schedule=info["schedule"])
         if info["schedule"] == "terms":
@@ -56,11 +58,19 @@ def test_graph_matches_single_instance_and_oracle(small_batch, precision):
         else:
             assert (plan.eloc[i] - ref["eloc_re"]).abs().max().item() < tol
         assert abs(plan.evar[i][0].item() - ref["evar"][0].item()) < tol
+        # the graph's gradient of E^var is the closed form of the adjoint
+        g_ref, _ = nqs.local_energy_backward(batch, lre, None, ref["eloc_re"], None, ref["hdiag"], ref["evar"],
+                                             None, None, torch.ones(1, dtype=torch.float64, device="cuda"))
+        assert (plan.grad[i] - g_ref).abs().max().item() < tol
         if inst.n_unq <= 400:
             ref_ham = oracle_for(inst)
             res = oracle.forward(inst.U, inst.logpsi_re, None, ref_ham)
             want = np.array([e.real for e in res["eloc"]])
             assert np.abs(plan.eloc[i].cpu().numpy() - want).max() < tol
+            g_want, _ = oracle.energy_gradient_closed_form(inst.logpsi_re, res["eloc"], res["e_var"])
+            assert np.abs(plan.grad[i].cpu().numpy() - g_want).max() < tol
+    # the autotuner chose per instance: not every instance got the same schedule and settings
+    assert len(choices) > 1, choices
     # replay twice: same results
     first = [e.clone() for e in plan.eloc]
     plan.run(); plan.run()

@@ -347,10 +347,13 @@ def run_ours(args):
     ev = {k: [] for k in ("stage", "pairs", "energy", "evar", "backward")}
     # rows of this rank: one contiguous block balanced by pair counts (all rows on one GPU)
     r0, r1 = 0, n
+    bounds = [0, n]
     if ws > 1:
-        from paper_2408_07625_gb300.sharding import row_blocks, combine_evar
+        from paper_2408_07625_gb300.sharding import row_blocks, combine_evar, sharded_coupled_pairs
         rp_all, _ = nqs.count_pairs(batch)
-        r0, r1 = row_blocks(rp_all.cpu().numpy(), ws)[rank]
+        blocks = row_blocks(rp_all.cpu().numpy(), ws)
+        bounds = [b[0] for b in blocks] + [n]
+        r0, r1 = blocks[rank]
 
     hbuf = [None]  # per-pair matrix elements, kept from E_loc^var for the adjoint
     # outputs allocated once (every row of the range is written by each call)
@@ -367,7 +370,11 @@ def run_ours(args):
         mark()
         batch_obj.restage(Udev)
         mark()
-        rp, pj, pk = nqs.coupled_pairs(batch_obj, r0, r1, schedule=args.schedule, reuse=True)
+        if ws > 1 and args.schedule == "terms":
+            # sharded search: this rank's slice of the work items, records exchanged to the row owners
+            rp, pj, pk = sharded_coupled_pairs(batch_obj, bounds, rank, ws)
+        else:
+            rp, pj, pk = nqs.coupled_pairs(batch_obj, r0, r1, schedule=args.schedule, reuse=True)
         total = int(pj.numel())
         mark()
         hdt = torch.float64 if prec == "fp64" else torch.float32
@@ -541,7 +548,7 @@ def run_ours(args):
                 "traffic": _profile_traffic(), "launch_ms": launch_ms, "probes_per_launch": probes,
                 "launches_timed": search_launches,
                 "peak_source": "measured: nqs_probe_peaks register-only XOR/AND/funnel-shift mix, "
-                               "152 x 512 threads, CUDA events (derived unit-count figure: "
+                               "152 x 1024 threads, CUDA events (derived unit-count figure: "
                                f"{derived:.1f} Tops/s)",
                 "probe_loop": {"achieved_gprobes_s": probes / (launch_ms * 1e-3) / 1e9,
                                "peak_gprobes_s": loop_peak / 1e9,
@@ -567,6 +574,10 @@ def run_ours(args):
     # + adjoint
     pairs_kernels = {"terms": 2 + 1 + 1 + 3 + 1 + 1 + 2, "batch": 2 + 1 + 3 + 1,
                      "trie": 2 + 3 * ((inst.n_qubits + 7) // 8) + 7 + 1 + 3 + 1}[args.schedule]
+    if ws > 1 and args.schedule == "terms":
+        # sharded: staging, search slice, routing (count, scatter), record counts (init, count),
+        # 3-kernel scan, row init, scatter, warp and block row sorts
+        pairs_kernels = 2 + 1 + 2 + 2 + 3 + 1 + 1 + 2
     kernels_per_step = pairs_kernels + 4 + 1 + (1 if ws > 1 else 0) + 5
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -574,7 +585,7 @@ def run_ours(args):
             "dtype": "u64+f32c (FP32 compensated, FP64 reduction)" if prec == "fp32c" else "u64+f64",
             "data": "synthetic (seeded integrals, JW, peaked samples)",
             "config": dict(_workload_config(inst, info, total_pairs, args.schedule, prec),
-                           parallelism=f"rows sharded over {ws} GPU(s); E^var triples all-gathered" if ws > 1
+                           parallelism=f"search work items sharded over {ws} GPU(s), records all-to-all to the row owners; rows sharded; E^var triples all-gathered" if ws > 1
                            else "one GPU", rows_rank0=[r0, r1]),
             "pairs_per_s": total_pairs / (phases["pairs"] * 1e-3),
             "phases_ms": phases, "precision_error": err,
@@ -607,6 +618,18 @@ def run_ours(args):
 
 BATCH_METRIC = ("unique-sample E_loc/s over 64 batched instances of 20-56 qubits (E_loc^var + E^var, and with "
                 "gradients dE^var/dlog psi, one graph)")
+
+
+def run_sr_only(args):
+    """The min-SR step alone (``--sr-only``): one JSON line with the SR measurement."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2408_07625_gb300 as nqs
+    peaks, _ = _peaks()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    sr = bench_sr(nqs, torch, 100, args.sr_params, args.steps, flush, peaks)
+    print(json.dumps(dict(sr, metric="min-SR step time (N_SR = 100)", unit="ms", higher_is_better=False,
+                          value=sr["ms_per_step"], steps=args.steps)), flush=True)
 
 
 def run_batched(args):
@@ -751,6 +774,7 @@ def main():
     p.add_argument("--sr-params", type=int, default=1_000_000,
                    help="parameters of the min-SR measurement (100 samples); 0 skips it")
     p.add_argument("--no-batch64", action="store_true", help="skip the 64-instance batched measurement")
+    p.add_argument("--sr-only", action="store_true", help="time only the min-SR step (--sr-params parameters)")
     p.add_argument("--full-n", type=int, default=1000,
                    help="samples of the exact-local-energy (Eq. local_energy) measurement; 0 skips it")
     args = p.parse_args()
@@ -758,6 +782,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.sr_only:
+        run_sr_only(args)
     elif args.workload == "batch64":
         run_batched(args)
     else:

@@ -213,6 +213,95 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
                            int64_t capacity, int64_t* n_pairs, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Half-stored pairs (Sec. "FindCoupledPairs implementations", Alg. 2A; the
+ * symmetry x XOR x' = XY of Eq. pauli_melem): each unordered coupled pair
+ * {U_i, U_j}, i != j, found once by the oriented LoopOverTerms search and
+ * written as one record (i, j, k), k the XY pattern index, instead of once
+ * in each of its two rows.
+ * ------------------------------------------------------------------------- */
+
+/* Records of every unordered pair of the batch: rec_i/rec_j/rec_k device
+ * uint32 [capacity].  *n_slots (host) = record slots used; a slot whose
+ * rec_i is 0xFFFFFFFF is unused (the search hands out slots in chunks), and
+ * the order of the records depends on thread timing.  NQS_ERR_CAPACITY if
+ * `capacity` is too small (*n_slots then gives the slots asked for).
+ * Synchronises the stream. */
+int nqs_find_pairs_half(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, void* work,
+                        uint32_t* rec_i, uint32_t* rec_j, uint32_t* rec_k, int64_t capacity,
+                        int64_t* n_slots, void* stream);
+
+/* The same search restricted to slice `part` of `n_parts` equal slices of
+ * the oriented work items (sample-list batch x pattern groups): the slices
+ * of parts 0 .. n_parts-1 together list every unordered pair exactly once,
+ * so n_parts ranks (one GPU each, each holding the whole staged batch)
+ * search disjoint slices.  part 0 of 1 is nqs_find_pairs_half. */
+int nqs_find_pairs_part(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, void* work,
+                        int part, int n_parts, uint32_t* rec_i, uint32_t* rec_j,
+                        uint32_t* rec_k, int64_t capacity, int64_t* n_slots, void* stream);
+
+/* Scratch bytes of nqs_route_records (n_parts in [1, 1024]). */
+int64_t nqs_route_scratch_bytes(int n_parts);
+
+/* The exchange step of the sharded search: part p owns rows
+ * [bounds[p], bounds[p + 1]) (host int64 [n_parts + 1], bounds[0] = 0,
+ * ascending).  Every used record slot of rec_i/rec_j/rec_k ([n_slots], from
+ * nqs_find_pairs_part) is copied to out_i/out_j/out_k (device uint32
+ * [capacity]) once for the part owning row i and once more for the part
+ * owning row j if that is another part; the copies are grouped by part in
+ * part order (order within a part unspecified), and counts[p] (host int64
+ * [n_parts]) receives each part's number.  These groups are what an
+ * all-to-all exchange sends to each rank.  scratch: device, 256-byte
+ * aligned, nqs_route_scratch_bytes.  NQS_ERR_CAPACITY if the copies exceed
+ * `capacity` (counts are then valid).  Synchronises the stream. */
+int nqs_route_records(int n_parts, const int64_t* bounds, const uint32_t* rec_i,
+                      const uint32_t* rec_j, const uint32_t* rec_k, int64_t n_slots,
+                      uint32_t* out_i, uint32_t* out_j, uint32_t* out_k, int64_t capacity,
+                      int64_t* counts, void* scratch, int64_t scratch_bytes, void* stream);
+
+/* CSR pairs of rows [row_begin, row_end) from records (device uint32 [n_rec];
+ * unused slots 0xFFFFFFFF allowed) that include every unordered pair with an
+ * endpoint in the range, e.g. the records a rank received from the exchange:
+ * row_ptr, pair_j, pair_k exactly as nqs_find_coupled_pairs writes them for
+ * that range (diagonal pair first, then ascending column).  A pair listed
+ * by several records is listed that often.  scratch: device, 256-byte
+ * aligned, at least 256 + 8 * (pairs of the range) bytes.  *n_pairs (host)
+ * = pairs of the range; NQS_ERR_CAPACITY if they exceed `capacity` or the
+ * scratch (row_ptr and *n_pairs then valid).  Synchronises the stream. */
+int nqs_pairs_from_records(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, void* work,
+                           const uint32_t* rec_i, const uint32_t* rec_j, const uint32_t* rec_k,
+                           int64_t n_rec, int64_t row_begin, int64_t row_end, void* scratch,
+                           int64_t scratch_bytes, int64_t* row_ptr, uint32_t* pair_j,
+                           uint32_t* pair_k, int64_t capacity, int64_t* n_pairs, void* stream);
+
+/* E_loc^var of every sample from half-stored records (n_slots slots): the
+ * diagonal term per row, then one MatrixElement per record, whose two terms
+ * (row i with column j, row j with column i, the latter with
+ * H_ji = conj(H_ij)) are added to eloc[i] and eloc[j] by FP64 atomic
+ * addition (row sums equal the CSR path's to rounding, not bitwise).
+ * Arguments as nqs_local_energy over the whole batch (eloc_re, eloc_im,
+ * hdiag device FP64 [n_unq]); hrec: per-record H (layout of hpair, indexed
+ * by slot) or NULL.  Asynchronous. */
+int nqs_local_energy_half(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, void* work,
+                          const double* logpsi_re, const double* logpsi_im, const uint32_t* rec_i,
+                          const uint32_t* rec_j, const uint32_t* rec_k, int64_t n_slots,
+                          int precision, double* eloc_re, double* eloc_im, double* hdiag,
+                          void* hrec, void* stream);
+
+/* Adjoint over half-stored records: the gradient of nqs_local_energy_backward
+ * (same upstreams, closed form when both g_eloc arrays are NULL) for every
+ * sample, each record's two terms added by FP64 atomic addition.  hrec: as
+ * written by nqs_local_energy_half, or NULL to recompute.  Asynchronous. */
+int nqs_local_energy_backward_half(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
+                                   void* work, const double* logpsi_re, const double* logpsi_im,
+                                   const uint32_t* rec_i, const uint32_t* rec_j,
+                                   const uint32_t* rec_k, int64_t n_slots, const void* hrec,
+                                   const double* eloc_re, const double* eloc_im,
+                                   const double* hdiag, const double* evar,
+                                   const double* g_eloc_re, const double* g_eloc_im,
+                                   const double* g_evar, int precision, double* grad_re,
+                                   double* grad_im, void* stream);
+
+/* ---------------------------------------------------------------------------
  * MatrixElement + ScatterAdd -> E_loc^var (Sec. "MatrixElement
  * implementation", Fig. scatter_local_energies)
  * ------------------------------------------------------------------------- */
@@ -298,12 +387,15 @@ int nqs_sr_top(int64_t n_unq, const double* logpsi_re, int64_t n_sr, int32_t* id
  *   T (device FP64 [n_sr][n_sr], may be NULL) receives Obar Obar^T.
  * logpsi_re, eloc_re: device FP64 [n_sr]; evar: device FP64 [1].  T is
  * formed on the tensor cores (tcgen05, bf16 hi/lo split of Obar with FP32
- * accumulation: about 16 significant bits per element), summed and solved
- * (Cholesky) in FP64.  The solve adds c sqrt(w) sqrt(w)^T (c = tr T / n_sr)
+ * accumulation: about 16 significant bits per element), summed in FP64 and
+ * solved by an L D L^T factorisation in double-float arithmetic (about 48
+ * significant bits).  The solve adds c sqrt(w) sqrt(w)^T (c = tr T / n_sr)
  * to T + lambda I: sqrt(w) is a null vector of the exact T and the step
  * annihilates it, so delta is unchanged while the factorisation no longer
- * sees an eigenvalue of lambda along it.  Synchronises the stream.  Errors:
- * NQS_ERR_RANGE if that matrix is not positive definite in FP64 (raise lambda),
+ * sees an eigenvalue of lambda along it.  n_params a multiple of 4 (and O,
+ * delta 16-byte aligned) takes the streamed kernels (tensor copies of O).
+ * Synchronises the stream.  Errors: NQS_ERR_RANGE if a pivot of that matrix
+ * is not positive (raise lambda),
  * NQS_ERR_DEVICE_LIMIT if a tensor-core pipeline wait ran out. */
 int nqs_sr_step(int n_sr, int64_t n_params, const float* O, const double* logpsi_re, const double* eloc_re,
                 const double* evar, double lambda, double* delta, double* T, void* scratch, int64_t scratch_bytes,
@@ -322,7 +414,8 @@ int nqs_sr_step(int n_sr, int64_t n_params, const float* O, const double* logpsi
  * ------------------------------------------------------------------------- */
 
 /* Bytes of the scratch nqs_full_candidates needs for n_unq samples (about
- * 60 + 16 W bytes per entry, n_unq * n_xy entries). */
+ * 13 + 16 W bytes per entry and at least 32, n_unq * n_xy entries: the keys
+ * and entry indices of a radix sort, its histograms, the candidate marks). */
 int64_t nqs_candidates_scratch_bytes(const nqs_ham* ham, int64_t n_unq);
 
 /* Candidates of every sample of U (device [n_unq][W]; staged in `work`):
@@ -335,9 +428,9 @@ int64_t nqs_candidates_scratch_bytes(const nqs_ham* ham, int64_t n_unq);
  *   cand_in_u device int32 [capacity] or NULL: the candidate's index in U,
  *            or -1 if it is not a sample of the batch.
  * scratch: device, 256-byte aligned, scratch_bytes >= nqs_candidates_scratch_bytes.
- * Needs n_unq * n_xy <= 2^29.  Synchronises the stream once (to learn
- * *n_cand); the remaining kernels may still run on the stream when it
- * returns.  NQS_ERR_CAPACITY (with *n_cand set, cand unwritten) if
+ * Needs n_unq * n_xy <= 2^29.  The candidates are deduplicated by a radix
+ * sort of all entries' keys.  Synchronises the stream (to learn *n_cand and
+ * the membership probe's status).  NQS_ERR_CAPACITY (with *n_cand set, cand unwritten) if
  * capacity < *n_cand or cand is NULL; the call can be repeated with larger
  * buffers.  The candidate order and every index are independent of thread
  * timing. */

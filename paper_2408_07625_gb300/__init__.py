@@ -97,6 +97,12 @@ def load_library(path: str = None):
         "nqs_gumbel_topk_level": (_i32, [_i32, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64, _vp, _vp, _vp,
                                          _c_i64p, _vp]),
         "nqs_find_pairs_half": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _c_i64p, _vp]),
+        "nqs_find_pairs_part": (_i32, [_vp, _vp, _i64, _vp, _i32, _i32, _vp, _vp, _vp, _i64, _c_i64p, _vp]),
+        "nqs_route_scratch_bytes": (_i64, [_i32]),
+        "nqs_route_records": (_i32, [_i32, _c_i64p, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i64, _c_i64p, _vp, _i64,
+                                     _vp]),
+        "nqs_pairs_from_records": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _i64, _i64, _vp, _i64, _vp, _vp,
+                                          _vp, _i64, _c_i64p, _vp]),
         "nqs_local_energy_half": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp,
                                          _vp, _vp]),
         "nqs_local_energy_backward_half": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp,
@@ -558,23 +564,26 @@ class LocalEnergy(torch.autograd.Function):
         return None, gr, gi, None, None
 
 
-def half_pairs(batch: Batch, stream=None):
+def half_pairs(batch: Batch, stream=None, part=0, n_parts=1):
     """Each unordered coupled pair {x_i, x_j} once as a record (i, j, k) (nqs_find_pairs_half).
 
     Returns (rec_i, rec_j, rec_k, n_slots): int32 tensors holding uint32 values,
     slots [0, n_slots) of which are in use; an unused slot has i = 0xFFFFFFFF.
-    The buffers are kept on the batch and reused by the next call.
+    With ``n_parts`` > 1 only slice ``part`` of the search's work items is
+    searched (nqs_find_pairs_part).  The buffers are kept on the batch and
+    reused by the next call.
     """
     lib = load_library()
     n = ctypes.c_int64()
-    cap = getattr(batch, "_half_cap", None) or max(128 * batch.n, 1 << 16)
+    cap = getattr(batch, "_half_cap", None) or max(128 * batch.n // max(1, n_parts), 1 << 16)
     for _ in range(3):
         buf = getattr(batch, "_half_buf", None)
         if buf is None or buf[0].numel() < cap:
             buf = tuple(torch.empty(cap, dtype=torch.int32, device=batch.device) for _ in range(3))
             batch._half_buf = buf
-        rc = lib.nqs_find_pairs_half(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work), _ptr(buf[0]),
-                                     _ptr(buf[1]), _ptr(buf[2]), buf[0].numel(), ctypes.byref(n), _stream(stream))
+        rc = lib.nqs_find_pairs_part(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work), int(part),
+                                     int(n_parts), _ptr(buf[0]), _ptr(buf[1]), _ptr(buf[2]), buf[0].numel(),
+                                     ctypes.byref(n), _stream(stream))
         if rc == -4:
             cap = int(n.value * 1.1) + 4096
             batch._half_cap = cap
@@ -585,6 +594,62 @@ def half_pairs(batch: Batch, stream=None):
         _check(rc)
     k = int(n.value)
     return buf[0][:k], buf[1][:k], buf[2][:k], k
+
+
+def route_records(records, bounds, stream=None):
+    """Copies of half-stored records grouped by the part owning each endpoint row (nqs_route_records).
+
+    ``records``: (rec_i, rec_j, rec_k, n_slots) as from ``half_pairs``;
+    ``bounds``: the n_parts + 1 row bounds of the parts.  Returns
+    (out_i, out_j, out_k, counts): int32 device tensors grouped by part and the
+    host list of each part's number of records.
+    """
+    lib = load_library()
+    ri, rj, rk, ns = records
+    b = np.ascontiguousarray(np.asarray(bounds, dtype=np.int64))
+    n_parts = len(b) - 1
+    dev = ri.device
+    nbytes = int(lib.nqs_route_scratch_bytes(n_parts))
+    _check(nbytes if nbytes < 0 else 0)
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    counts = (ctypes.c_int64 * n_parts)()
+    cap = 2 * max(int(ns), 1)
+    out = tuple(torch.empty(cap, dtype=torch.int32, device=dev) for _ in range(3))
+    _check(lib.nqs_route_records(n_parts, b.ctypes.data_as(_c_i64p), _pair_ptr(ri), _pair_ptr(rj), _pair_ptr(rk),
+                                 int(ns), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), cap, counts, _ptr(scratch),
+                                 nbytes, _stream(stream)))
+    c = [int(v) for v in counts]
+    tot = sum(c)
+    return out[0][:tot], out[1][:tot], out[2][:tot], c
+
+
+def pairs_from_records(batch: Batch, rec_i, rec_j, rec_k, row_begin, row_end, stream=None):
+    """CSR (row_ptr, j, k) of rows [row_begin, row_end) from records naming every pair of those rows
+    (nqs_pairs_from_records); the same lists as ``coupled_pairs`` over that range."""
+    lib = load_library()
+    rows = int(row_end) - int(row_begin)
+    dev = batch.device
+    n_rec = int(rec_i.numel())
+    rp = torch.empty(rows + 1, dtype=torch.int64, device=dev)
+    n = ctypes.c_int64()
+    cap = max(2 * n_rec + rows, 1)
+    for _ in range(2):
+        pj = torch.empty(cap, dtype=torch.int32, device=dev)
+        pk = torch.empty(cap, dtype=torch.int32, device=dev)
+        scratch = torch.empty(256 + 8 * cap, dtype=torch.uint8, device=dev)
+        rc = lib.nqs_pairs_from_records(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work), _pair_ptr(rec_i),
+                                        _pair_ptr(rec_j), _pair_ptr(rec_k), n_rec, int(row_begin), int(row_end),
+                                        _ptr(scratch), scratch.numel(), _ptr(rp), _ptr(pj), _ptr(pk), cap,
+                                        ctypes.byref(n), _stream(stream))
+        if rc == -4:
+            cap = int(n.value) + 1
+            continue
+        _check(rc)
+        break
+    else:
+        _check(rc)
+    k = int(n.value)
+    return rp, pj[:k], pk[:k]
 
 
 def half_h_buffer(n_slots, precision="fp32c", device="cuda", complex_h=False):

@@ -849,14 +849,21 @@ int nqs_gumbel_topk_level(int n_qubits, int level, int64_t n_parents, const uint
 
 int nqs_find_pairs_half(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, uint32_t* rec_i,
                         uint32_t* rec_j, uint32_t* rec_k, int64_t capacity, int64_t* n_slots, void* stream) {
+  return nqs_find_pairs_part(ham, U, n, work, 0, 1, rec_i, rec_j, rec_k, capacity, n_slots, stream);
+}
+
+int nqs_find_pairs_part(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, int part, int n_parts,
+                        uint32_t* rec_i, uint32_t* rec_j, uint32_t* rec_k, int64_t capacity, int64_t* n_slots,
+                        void* stream) {
   StageHeader L;
   int rc = check_work(ham, U, n, work, &L);
   if (rc) return rc;
   if (!n_slots) return fail(NQS_ERR_ARG, "null n_slots");
   *n_slots = 0;
+  if (n_parts < 1 || part < 0 || part >= n_parts) return fail(NQS_ERR_ARG, "bad part");
   if (capacity < 0 || (capacity > 0 && (!rec_i || !rec_j || !rec_k))) return fail(NQS_ERR_ARG, "null record arrays");
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = launch_find_half(ham, U, (char*)work, L, rec_i, rec_j, rec_k, capacity, s);
+  cudaError_t e = launch_find_half(ham, U, (char*)work, L, rec_i, rec_j, rec_k, capacity, s, part, n_parts);
   if (e != cudaSuccess) return cuda_fail(e, "half-pair search kernel");
   int64_t cur[2] = {0, 0};
   e = cudaMemcpyAsync(cur, (char*)work + L.off_counters + 8 * kCtrHalf, sizeof(cur), cudaMemcpyDeviceToHost, s);
@@ -865,6 +872,96 @@ int nqs_find_pairs_half(const nqs_ham* ham, const uint64_t* U, int64_t n, void* 
   *n_slots = cur[0];
   if (cur[1] != 0) return fail(NQS_ERR_CAPACITY, "record capacity too small (n_slots: slots asked for)");
   return NQS_OK;
+}
+
+int64_t nqs_route_scratch_bytes(int n_parts) {
+  if (n_parts < 1 || n_parts > 1024) return fail(NQS_ERR_ARG, "n_parts outside [1, 1024]");
+  return 256 + 8 * (int64_t)(n_parts + 1) + 2 * 8 * (int64_t)n_parts + 256;
+}
+
+int nqs_route_records(int n_parts, const int64_t* bounds, const uint32_t* rec_i, const uint32_t* rec_j,
+                      const uint32_t* rec_k, int64_t n_slots, uint32_t* out_i, uint32_t* out_j, uint32_t* out_k,
+                      int64_t capacity, int64_t* counts, void* scratch, int64_t scratch_bytes, void* stream) {
+  if (n_parts < 1 || n_parts > 1024) return fail(NQS_ERR_ARG, "n_parts outside [1, 1024]");
+  if (!bounds || !counts) return fail(NQS_ERR_ARG, "null bounds or counts");
+  if (n_slots < 0 || (n_slots > 0 && (!rec_i || !rec_j || !rec_k))) return fail(NQS_ERR_ARG, "null record arrays");
+  if (!scratch || scratch_bytes < nqs_route_scratch_bytes(n_parts)) return fail(NQS_ERR_ARG, "scratch too small");
+  if (((uintptr_t)scratch) & 255) return fail(NQS_ERR_ARG, "scratch not 256-byte aligned");
+  for (int p = 0; p < n_parts; ++p)
+    if (bounds[p] < 0 || bounds[p + 1] < bounds[p]) return fail(NQS_ERR_ARG, "bounds not ascending");
+  if (bounds[0] != 0) return fail(NQS_ERR_ARG, "bounds must start at row 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* base = (char*)scratch;
+  int64_t* d_bounds = (int64_t*)(base + 256);
+  auto* d_counts = (unsigned long long*)(base + 256 + ((8 * (n_parts + 1) + 255) & ~255));
+  unsigned long long* d_cur = d_counts + n_parts;
+  cudaError_t e = cudaMemcpyAsync(d_bounds, bounds, 8 * (size_t)(n_parts + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_route_count(rec_i, rec_j, n_slots, d_bounds, n_parts, d_counts, s);
+  std::vector<unsigned long long> c(n_parts, 0ull);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c.data(), d_counts, 8 * (size_t)n_parts, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "record routing count");
+  std::vector<unsigned long long> off(n_parts, 0ull);
+  unsigned long long total = 0;
+  for (int p = 0; p < n_parts; ++p) {
+    off[p] = total;
+    total += c[p];
+    counts[p] = (int64_t)c[p];
+  }
+  if ((int64_t)total > capacity) return fail(NQS_ERR_CAPACITY, "routed record capacity too small (counts: per part)");
+  if (total > 0 && (!out_i || !out_j || !out_k)) return fail(NQS_ERR_ARG, "null output arrays");
+  e = cudaMemcpyAsync(d_cur, off.data(), 8 * (size_t)n_parts, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = launch_route_scatter(rec_i, rec_j, rec_k, n_slots, d_bounds, n_parts, d_cur, out_i, out_j, out_k, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // off lives on this stack frame
+  if (e != cudaSuccess) return cuda_fail(e, "record routing scatter");
+  return NQS_OK;
+}
+
+int nqs_pairs_from_records(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, const uint32_t* rec_i,
+                           const uint32_t* rec_j, const uint32_t* rec_k, int64_t n_rec, int64_t rb, int64_t re,
+                           void* scratch, int64_t scratch_bytes, int64_t* row_ptr, uint32_t* pair_j,
+                           uint32_t* pair_k, int64_t capacity, int64_t* n_pairs, void* stream) {
+  StageHeader L;
+  int rc = check_work(ham, U, n, work, &L);
+  if (rc || (rc = check_rows(n, rb, re))) return rc;
+  if (!row_ptr || !n_pairs) return fail(NQS_ERR_ARG, "null row_ptr or n_pairs");
+  if (n_rec < 0 || (n_rec > 0 && (!rec_i || !rec_j || !rec_k))) return fail(NQS_ERR_ARG, "null record arrays");
+  if (n_rec >= (int64_t(1) << 40)) return fail(NQS_ERR_ARG, "too many records");
+  if (!scratch || ((uintptr_t)scratch) & 255) return fail(NQS_ERR_ARG, "scratch null or not 256-byte aligned");
+  *n_pairs = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t rows = re - rb;
+  auto* status = (int32_t*)((char*)work + offsetof(StageHeader, status));
+  cudaError_t e = cudaMemsetAsync(row_ptr, 0, sizeof(int64_t), s);
+  if (e == cudaSuccess) e = launch_records_count(rec_i, rec_j, n_rec, rb, rows, ham->has_diag, row_ptr + 1, status, s);
+  if (e == cudaSuccess && rows > 0) e = launch_scan(row_ptr + 1, rows, (char*)work, L, s);
+  if (e != cudaSuccess) return cuda_fail(e, "record count kernels");
+  int64_t total = 0;
+  if ((e = cudaMemcpyAsync(&total, row_ptr + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "count copy");
+  if ((rc = read_status(work, s))) return rc;
+  *n_pairs = total;
+  if (total > capacity) return fail(NQS_ERR_CAPACITY, "pair capacity too small");
+  if (total > 0 && (!pair_j || !pair_k)) return fail(NQS_ERR_ARG, "null pair arrays");
+  // the records as a one-pass scratch: header (record count, overflow flag), then the sort keys
+  if (scratch_bytes < 256 + 8 * total) return fail(NQS_ERR_CAPACITY, "scratch too small for the pairs (8 B each)");
+  if (rows == 0) return NQS_OK;
+  PairScratch sc;
+  std::memset(&sc, 0, sizeof(sc));
+  sc.cursor = (int64_t*)scratch;
+  sc.rec_i = const_cast<uint32_t*>(rec_i);
+  sc.rec_j = const_cast<uint32_t*>(rec_j);
+  sc.rec_k = const_cast<uint32_t*>(rec_k);
+  sc.max_rec = n_rec;
+  sc.max_pairs = total;
+  sc.keys = (uint64_t*)((char*)scratch + 256);
+  const int64_t hdr[2] = {n_rec, 0};
+  if ((e = cudaMemcpyAsync(sc.cursor, hdr, sizeof(hdr), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(e, "record header");
+  e = launch_pairs_compact(ham, sc, (char*)work, L, rb, rows, row_ptr, pair_j, pair_k, capacity, s);
+  if (e != cudaSuccess) return cuda_fail(e, "record scatter and row sort");
+  return read_status(work, s);   // synchronises: hdr is read before this frame returns
 }
 
 int nqs_local_energy_half(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, const double* a,

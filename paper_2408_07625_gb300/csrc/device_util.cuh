@@ -23,10 +23,11 @@ __device__ __forceinline__ uint32_t parity_and(const uint64_t (&x)[W], const uin
   return __popc((uint32_t)t ^ (uint32_t)(t >> 32)) & 1u;
 }
 
-// three bits of a 32-bit blocked Bloom word per key, taken from hash bits
-// 17.., 22.. and 27.. (the word itself from the low bits)
+// three bits of a 32-bit blocked Bloom word per key (the word itself from the
+// low bits of the hash): for each 5-bit field f of the hash at bits 15, 20 and
+// 25, bit f - 1 (mod 32), which a right rotation by f brings to bit 31
 __device__ __forceinline__ uint32_t bloom_bits(uint32_t h) {
-  return (1u << ((h >> 17) & 31)) | (1u << ((h >> 22) & 31)) | (1u << (h >> 27));
+  return (1u << (((h >> 15) - 1u) & 31u)) | (1u << (((h >> 20) - 1u) & 31u)) | (1u << (((h >> 25) - 1u) & 31u));
 }
 
 // --------------------------------------------------------------------------

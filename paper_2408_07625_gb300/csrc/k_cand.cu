@@ -12,16 +12,15 @@
 // pattern order).  Every sample has exactly n_xy entries, so the per-entry
 // outputs are dense [n_unq][n_xy] arrays and need no offsets.
 //
-// Deduplication (all passes stream over the entries or the table):
-//   1. insert: each entry's candidate goes into an open-addressing table of
-//      64-bit slots (owner entry << 32 | 32-bit linear hash); the entry's slot
-//      index is written to cand_id[e] and its matrix element to hval[e];
-//   2. compact: occupied slots -> unsorted unique keys with their slots;
-//   3. sort: LSD radix sort of the unique keys in numeric order (qubit 0 the
-//      least significant bit) carrying the slot; candidate u = sorted rank;
-//   4. assign: slot_uid[slot] = u; cand_in_u[u] = the candidate's index in U
-//      (membership table of the staged batch) or -1;
-//   5. relabel: cand_id[e] = slot_uid[cand_id[e]].
+// Deduplication by sorting (every pass streams):
+//   1. generate: each entry's candidate key (and its matrix element);
+//   2. sort: LSD radix sort of the keys in numeric order (qubit 0 the least
+//      significant bit), carrying the entry index (stable: equal keys keep
+//      entry order);
+//   3. mark: a sorted position starts a candidate when its key differs from
+//      the previous one; an exclusive scan of the marks numbers them;
+//   4. scatter: cand_id[entry] = number of its key; each candidate's key and
+//      its membership in U (the staged table of U) from its first position.
 // The candidate order (numeric) and every entry's index are independent of
 // thread timing.
 #include <algorithm>
@@ -33,30 +32,19 @@
 
 namespace nqs {
 
-constexpr unsigned long long kEmptySlot = ~0ull;
 constexpr int kCandThreads = 256;
 constexpr int kCandWarps = kCandThreads / 32;
 
 static inline int64_t a256c(int64_t v) { return (v + 255) & ~int64_t(255); }
 
-static int64_t cand_table_cap(int64_t entries) {
-  int64_t c = 1024;
-  while (c < 2 * entries) c <<= 1;
-  return c;
-}
-
 // scratch layout of nqs_full_candidates
 struct CandScratch {
-  unsigned long long* counters;   // [0] unique candidates, [1] probe limit hit
-  unsigned long long* table;      // [cap] slots
-  int64_t cap;
-  int32_t* slot_uid;              // [cap]
-  uint64_t* ukeys;                // [entries][W] unique keys before the sort (sort buffer)
-  int32_t* uslot;                 // [entries] their slots (sort payload buffer)
-  uint64_t* kb;                   // [entries][W] sort buffer
-  int32_t* ib;                    // [entries] sort payload buffer
+  unsigned long long* counters;   // [1] probe limit hit
+  uint64_t* keys[2];              // [entries][W] sort buffers (keys[0]: generated keys)
+  int32_t* idx[2];                // [entries] sort payload buffers (entry index)
+  int32_t* mark;                  // [entries + 1] candidate starts, then their exclusive scan
   int32_t* hist;                  // [256 * sort_blocks(entries)]
-  int32_t* partial;               // [sort_scan_partials(entries)]
+  int32_t* partial;               // [scan partials]
   int64_t bytes;
 };
 
@@ -64,19 +52,18 @@ static CandScratch cand_scratch_view(char* base, int64_t entries, int W) {
   CandScratch v;
   std::memset(&v, 0, sizeof(v));
   const int64_t m = std::max<int64_t>(entries, 1);
-  v.cap = cand_table_cap(m);
   int64_t off = 0;
   auto take = [&](int64_t bytes) { char* p = base ? base + off : nullptr; off = a256c(off + bytes); return p; };
   v.counters = (unsigned long long*)take(256);
-  v.table = (unsigned long long*)take(8 * v.cap);
-  v.slot_uid = (int32_t*)take(4 * v.cap);
-  v.ukeys = (uint64_t*)take(8 * W * m);
-  v.uslot = (int32_t*)take(4 * m);
-  v.kb = (uint64_t*)take(8 * W * m);
-  v.ib = (int32_t*)take(4 * m);
+  v.keys[0] = (uint64_t*)take(8 * W * m);
+  v.keys[1] = (uint64_t*)take(8 * W * m);
+  v.idx[0] = (int32_t*)take(4 * m);
+  v.idx[1] = (int32_t*)take(4 * m);
+  v.mark = (int32_t*)take(4 * (m + 1));
   v.hist = (int32_t*)take(4 * 256 * sort_blocks(m));
-  v.partial = (int32_t*)take(4 * sort_scan_partials(m));
-  v.bytes = off;
+  v.partial = (int32_t*)take(4 * std::max<int64_t>(sort_scan_partials(m), (m + 1) / 2048 + 2));
+  // the E_loc sum reuses the scratch for 32 bytes per candidate (at most one per entry)
+  v.bytes = std::max<int64_t>(off, 32 * m + 256);
   return v;
 }
 
@@ -84,58 +71,13 @@ int64_t cand_scratch_bytes(const nqs_ham* ham, int64_t n_unq) {
   return cand_scratch_view(nullptr, n_unq * ham->n_xy, ham->W).bytes;
 }
 
-// slot of a 32-bit linear hash: Fibonacci hashing spreads the (structured)
-// linear hash over the table
-__device__ __forceinline__ uint64_t cand_home(uint32_t h, int lg) {
-  return (uint64_t)((h * 0x9E3779B97F4A7C15ull) >> (64 - lg));
-}
-
 struct CandArgs {
   const uint64_t* U;
-  const uint32_t* hx;          // linear hash of each sample (staged)
   const uint64_t* xy;          // [n_xy][W]
-  const uint32_t* xy_hash;     // [n_xy]
   int64_t n_unq, n_xy;
-  unsigned long long* table;
-  int lg;                      // log2 of the table size
-  uint32_t* cand_id;           // [n_unq][n_xy]: slot, later the candidate index
+  uint64_t* keys;              // [entries][W] generated keys
   double* hval;                // [n_unq][n_xy] or null
-  unsigned long long* counters;
 };
-
-// the candidate of entry e (row e / n_xy, pattern e % n_xy)
-template <int W>
-__device__ __forceinline__ void entry_key(const CandArgs& a, uint64_t e, uint64_t (&c)[W]) {
-  const uint64_t i = e / (uint64_t)a.n_xy, k = e - i * (uint64_t)a.n_xy;
-#pragma unroll
-  for (int w = 0; w < W; ++w) c[w] = __ldg(a.U + i * W + w) ^ __ldg(a.xy + k * W + w);
-}
-
-// Insert key c (hash h) owned by entry e; returns the slot holding it.
-template <int W>
-__device__ __forceinline__ uint32_t cand_insert(const CandArgs& a, const uint64_t (&c)[W], uint32_t h, uint64_t e) {
-  const uint64_t mask = (1ull << a.lg) - 1ull;
-  uint64_t s = cand_home(h, a.lg);
-  const unsigned long long mine = ((unsigned long long)e << 32) | h;
-  for (uint64_t it = 0; it <= mask; ++it) {
-    unsigned long long v = a.table[s];
-    if (v == kEmptySlot) {
-      v = atomicCAS(a.table + s, kEmptySlot, mine);
-      if (v == kEmptySlot) return (uint32_t)s;
-    }
-    if ((uint32_t)v == h) {
-      uint64_t o[W];
-      entry_key<W>(a, v >> 32, o);
-      bool eq = true;
-#pragma unroll
-      for (int w = 0; w < W; ++w) eq = eq && o[w] == c[w];
-      if (eq) return (uint32_t)s;
-    }
-    s = (s + 1) & mask;
-  }
-  atomicOr(a.counters + 1, 1ull);  // table full: cannot happen at load <= 1/2
-  return 0u;
-}
 
 // Work unit of a warp: one sample and a tile of kCandTile consecutive
 // patterns (lanes take them in rounds of 32), so that few samples with many
@@ -145,7 +87,7 @@ __device__ __forceinline__ uint32_t cand_insert(const CandArgs& a, const uint64_
 constexpr int kCandTile = 1024;
 
 template <int W>
-__global__ void __launch_bounds__(kCandThreads) cand_insert_kernel(const CandArgs a, const Melem M) {
+__global__ void __launch_bounds__(kCandThreads) cand_gen_kernel(const CandArgs a, const Melem M) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * kCandWarps;
   const int64_t k_first = M.has_diag ? 1 : 0;
@@ -156,12 +98,12 @@ __global__ void __launch_bounds__(kCandThreads) cand_insert_kernel(const CandArg
     const int64_t tc = tpr > 0 ? t - i * tpr : 0;
     uint64_t x[W];
     load_words<W>(a.U + i * W, x);
-    const uint32_t hxi = __ldg(a.hx + i);
     const uint64_t e0 = (uint64_t)i * (uint64_t)a.n_xy;
     if (M.has_diag && tc == 0) {  // pattern 0: x' = x, with the sample's first tile
       const double hd = a.hval ? melem_diag<PolicyD, W>(x, M) : 0.0;
       if (lane == 0) {
-        a.cand_id[e0] = cand_insert<W>(a, x, hxi ^ __ldg(a.xy_hash), e0);
+#pragma unroll
+        for (int w = 0; w < W; ++w) a.keys[e0 * W + w] = x[w];
         if (a.hval) a.hval[e0] = hd;
       }
     }
@@ -191,82 +133,56 @@ __global__ void __launch_bounds__(kCandThreads) cand_insert_kernel(const CandArg
       }
       if (have) {
         const uint64_t e = e0 + (uint64_t)k;
-        a.cand_id[e] = cand_insert<W>(a, c, hxi ^ __ldg(a.xy_hash + k), e);
+#pragma unroll
+        for (int w = 0; w < W; ++w) a.keys[e * W + w] = c[w];
         if (a.hval) a.hval[e] = h;
       }
     }
   }
 }
 
-// occupied slots -> unsorted unique keys and their slots.  A block owns a
-// chunk of kCompactChunk consecutive slots: it counts them, takes its places
-// with one atomic, then writes them in slot order (the chunk is re-read from
-// L2).
-constexpr int kCompactChunk = 8192;
-
+// mark[p] = 1 where sorted position p starts a candidate (its key differs from p - 1)
 template <int W>
-__global__ void __launch_bounds__(256) cand_compact_kernel(const CandArgs a, uint64_t* __restrict__ ukeys,
-                                                           int32_t* __restrict__ uslot) {
-  __shared__ uint32_t wcnt[8];
-  __shared__ unsigned long long s_base;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint64_t cap = 1ull << a.lg;
-  const uint64_t s0 = (uint64_t)blockIdx.x * kCompactChunk;
-  const uint64_t s1 = s0 + kCompactChunk < cap ? s0 + kCompactChunk : cap;
-  uint32_t cnt = 0;
-  for (uint64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) cnt += a.table[s] != kEmptySlot ? 1u : 0u;
-  cnt = __reduce_add_sync(kFull, cnt);
-  if (lane == 0) wcnt[warp] = cnt;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t t = 0;
-    for (int w = 0; w < 8; ++w) t += wcnt[w];
-    s_base = t ? atomicAdd(a.counters, (unsigned long long)t) : 0ull;
-  }
-  __syncthreads();
-  unsigned long long run = s_base;
-  for (uint64_t t0 = s0; t0 < s1; t0 += blockDim.x) {
-    const uint64_t s = t0 + threadIdx.x;
-    const unsigned long long v = s < s1 ? a.table[s] : kEmptySlot;
-    const bool occ = v != kEmptySlot;
-    const uint32_t m = __ballot_sync(kFull, occ);
-    __syncthreads();
-    if (lane == 0) wcnt[warp] = __popc(m);
-    __syncthreads();
-    uint32_t off = 0, total = 0;
-    for (int w = 0; w < 8; ++w) {
-      off += w < warp ? wcnt[w] : 0u;
-      total += wcnt[w];
-    }
-    if (occ) {
-      const uint64_t u = run + off + __popc(m & ((1u << lane) - 1u));
-      uint64_t c[W];
-      entry_key<W>(a, v >> 32, c);
+__global__ void cand_mark_kernel(int64_t m, const uint64_t* __restrict__ keys, int32_t* __restrict__ mark) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+    bool start = p == 0;
+    if (!start) {
 #pragma unroll
-      for (int w = 0; w < W; ++w) ukeys[u * W + w] = c[w];
-      uslot[u] = (int32_t)s;
+      for (int w = 0; w < W; ++w) start = start || __ldg(keys + p * W + w) != __ldg(keys + (p - 1) * W + w);
     }
-    run += total;
+    mark[p] = start ? 1 : 0;
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) mark[m] = 0;
 }
 
-// sorted rank u -> slot_uid[slot]; membership of the candidate in U
-// (the candidate's linear hash, which the staged table of U is keyed by, is
-// the tag its slot keeps)
+// sorted position p (entry idx[p]); scan = exclusive scan of the marks (m + 1 values),
+// so position p starts a candidate when scan[p + 1] - scan[p] = 1 and its candidate is
+// u = scan[p] + start - 1: the entry's candidate index; at a candidate's first position
+// its key and its index in U (or -1)
 template <int W>
-__global__ void cand_assign_kernel(int64_t n_c, const uint64_t* __restrict__ keys, const int32_t* __restrict__ slots,
-                                   int32_t* __restrict__ slot_uid, int32_t* __restrict__ in_u,
-                                   const unsigned long long* __restrict__ utable, int64_t capmask,
-                                   const unsigned long long* __restrict__ ctable, const uint64_t* __restrict__ U,
-                                   unsigned long long* counters) {
-  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n_c; u += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t sl = slots[u];
-    slot_uid[sl] = (int32_t)u;
-    if (!in_u) continue;
+__global__ void cand_scatter_kernel(int64_t m, const uint64_t* __restrict__ keys, const int32_t* __restrict__ idx,
+                                    const int32_t* __restrict__ scan, uint32_t* __restrict__ cand_id, uint64_t* __restrict__ cand,
+                                    int32_t* __restrict__ in_u, const uint32_t* __restrict__ hx,
+                                    const uint32_t* __restrict__ xy_hash, int64_t n_xy,
+                                    const unsigned long long* __restrict__ utable, int64_t capmask,
+                                    const uint64_t* __restrict__ U, unsigned long long* counters) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < m; p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t sc = scan[p];
+    const bool first = scan[p + 1] - sc == 1;
+    const int32_t e = idx[p];
+    const int32_t u = sc + (first ? 1 : 0) - 1;
+    cand_id[e] = (uint32_t)u;
+    if (!first) continue;
     uint64_t c[W];
-    const uint32_t h = (uint32_t)ctable[sl];
 #pragma unroll
-    for (int w = 0; w < W; ++w) c[w] = keys[u * W + w];
+    for (int w = 0; w < W; ++w) {
+      c[w] = keys[p * W + w];
+      cand[(int64_t)u * W + w] = c[w];
+    }
+    if (!in_u) continue;
+    // x' = U_i XOR XY_k has the linear hash h(U_i) ^ h(XY_k), the key of the staged table of U
+    const int64_t i = e / n_xy, k = e - i * n_xy;
+    const uint32_t h = __ldg(hx + i) ^ __ldg(xy_hash + k);
     int32_t j = -1;
     int64_t b = h & capmask;
     bool done = false;
@@ -284,14 +200,9 @@ __global__ void cand_assign_kernel(int64_t n_c, const uint64_t* __restrict__ key
       }
       b = (b + 1) & capmask;
     }
-    if (!done) atomicOr(counters + 1, 1ull);
+    if (!done) atomicOr(counters, 1ull);
     in_u[u] = j;
   }
-}
-
-__global__ void cand_relabel_kernel(int64_t entries, uint32_t* __restrict__ cand_id, const int32_t* __restrict__ slot_uid) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < entries; e += (int64_t)gridDim.x * blockDim.x)
-    cand_id[e] = (uint32_t)__ldg(slot_uid + cand_id[e]);
 }
 
 template <int W>
@@ -301,55 +212,52 @@ static cudaError_t cand_w(const nqs_ham* ham, const uint64_t* U, int64_t n, cons
   const int64_t entries = n * ham->n_xy;
   CandArgs a;
   a.U = U;
-  a.hx = (const uint32_t*)(stage + L.off_hx);
   a.xy = ham->xy;
-  a.xy_hash = ham->xy_hash;
   a.n_unq = n;
   a.n_xy = ham->n_xy;
-  a.table = sc.table;
-  a.lg = 0;
-  while ((1ll << a.lg) < sc.cap) ++a.lg;
-  a.cand_id = cand_id;
+  a.keys = sc.keys[0];
   a.hval = hval;
-  a.counters = sc.counters;
   cudaError_t e;
   if ((e = cudaMemsetAsync(sc.counters, 0, 256, s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(sc.table, 0xFF, 8 * sc.cap, s)) != cudaSuccess) return e;
   const int sms = num_sms();
   const int64_t k_first = ham->has_diag ? 1 : 0;
   const int64_t tiles = n * std::max<int64_t>(1, (ham->n_xy - k_first + kCandTile - 1) / kCandTile);
-  const int ins_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((tiles + kCandWarps - 1) / kCandWarps, 16 * sms));
-  cand_insert_kernel<W><<<ins_blocks, kCandThreads, 0, s>>>(a, melem_tables(ham, n));
-  cand_compact_kernel<W><<<(unsigned)((sc.cap + kCompactChunk - 1) / kCompactChunk), 256, 0, s>>>(a, sc.ukeys,
-                                                                                                sc.uslot);
+  const int gen_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((tiles + kCandWarps - 1) / kCandWarps, 16 * sms));
+  cand_gen_kernel<W><<<gen_blocks, kCandThreads, 0, s>>>(a, melem_tables(ham, n));
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  unsigned long long ctr[2] = {0, 0};
-  if ((e = cudaMemcpyAsync(ctr, sc.counters, sizeof(ctr), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-  *n_cand = (int64_t)ctr[0];
-  *limit_hit = ctr[1] != 0;
-  if (*limit_hit || *n_cand > capacity) return cudaSuccess;
-  // numeric sort of the unique keys over their low ceil(N / 8) bytes, carrying the slots
-  uint64_t* kbuf[2] = {cand, sc.kb};
-  int32_t* ibuf[2] = {sc.ib, sc.uslot};
-  // pass 0 reads ukeys/uslot; the payload ping-pong reuses uslot after pass 0
+  // numeric sort of all entries' keys over their low ceil(N / 8) bytes, carrying the entry index
+  uint64_t* kbuf[2] = {sc.keys[1], sc.keys[0]};
+  int32_t* ibuf[2] = {sc.idx[1], sc.idx[0]};
   int out = -1;
   const int n_bytes = (ham->n_qubits + 7) / 8;
-  if ((e = launch_sort_words(sc.ukeys, sc.uslot, *n_cand, W, n_bytes, kbuf, ibuf, sc.hist, sc.partial, &out, s)) !=
+  if ((e = launch_sort_words(sc.keys[0], nullptr, entries, W, n_bytes, kbuf, ibuf, sc.hist, sc.partial, &out, s)) !=
       cudaSuccess)
     return e;
-  const uint64_t* keys = out >= 0 ? kbuf[out] : sc.ukeys;
-  const int32_t* slots = out >= 0 ? ibuf[out] : sc.uslot;
-  if (keys != cand && *n_cand > 0 &&
-      (e = cudaMemcpyAsync(cand, keys, 8 * W * *n_cand, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-    return e;
-  const int ub = (int)std::max<int64_t>(1, std::min<int64_t>((*n_cand + 255) / 256, 8 * sms));
-  cand_assign_kernel<W><<<ub, 256, 0, s>>>(*n_cand, cand, slots, sc.slot_uid, in_u,
-                                           (const unsigned long long*)(stage + L.off_table), L.cap - 1,
-                                           sc.table, U, sc.counters);
+  const uint64_t* keys = out >= 0 ? kbuf[out] : sc.keys[0];
+  const int32_t* idx = out >= 0 ? ibuf[out] : nullptr;   // n_bytes >= 1, so at least one pass ran
   const int eb = (int)std::max<int64_t>(1, std::min<int64_t>((entries + 255) / 256, 16 * sms));
-  cand_relabel_kernel<<<eb, 256, 0, s>>>(entries, cand_id, sc.slot_uid);
-  return cudaGetLastError();
+  cand_mark_kernel<W><<<eb, 256, 0, s>>>(entries, keys, sc.mark);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_scan_i32(sc.mark, entries + 1, sc.partial, s)) != cudaSuccess) return e;
+  int32_t total = 0;
+  if ((e = cudaMemcpyAsync(&total, sc.mark + entries, sizeof(total), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  *n_cand = total;
+  *limit_hit = 0;
+  if (*n_cand > capacity) return cudaSuccess;
+  cand_scatter_kernel<W><<<eb, 256, 0, s>>>(entries, keys, idx, sc.mark, cand_id, cand, in_u,
+                                            (const uint32_t*)(stage + L.off_hx), ham->xy_hash, ham->n_xy,
+                                            (const unsigned long long*)(stage + L.off_table), L.cap - 1, U,
+                                            sc.counters);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (in_u) {  // the membership probe's limit flag
+    unsigned long long lim = 0;
+    if ((e = cudaMemcpyAsync(&lim, sc.counters, sizeof(lim), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    *limit_hit = lim != 0;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_full_candidates(const nqs_ham* ham, const uint64_t* U, int64_t n, const char* stage,

@@ -265,7 +265,7 @@ cudaError_t launch_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, char*
 // warp's last chunk is marked with i = kNoRecord
 // --------------------------------------------------------------------------
 static inline int64_t a256(int64_t v) { return (v + 255) & ~int64_t(255); }
-constexpr int kSearchThreads = 512;
+constexpr int kSearchThreads = 1024;
 constexpr int kSearchWarps = kSearchThreads / 32;
 constexpr int kRecChunk = 128;
 constexpr uint32_t kNoRecord = 0xFFFFFFFFu;
@@ -301,18 +301,26 @@ PairScratch pair_scratch_view(void* base, int64_t rows, int64_t bytes) {
 // --------------------------------------------------------------------------
 // Oriented LoopOverTerms search.  A warp takes work items from a global
 // counter; item = (segment s of the search table, 8 consecutive entries of
-// the list of samples with bit t_s set).  Lane t scans slot 32 g + t of each
-// group g of the segment; the 32 slots of a group have at most two patterns
-// per hash residue mod 32, so the 32 Bloom-word loads of one row touch each
-// shared-memory bank at most twice.  Per slot a lane keeps a bit mask of the
-// rows whose filter test passed; slots with a hit go to a per-warp queue,
-// which is verified lane-parallel against the hash table when full.
+// the list of samples on the rarer side of qubit t_s, a run of groups of the
+// segment).  Lane t scans slot 32 g + t of each group g; the 32 slots of a
+// group have at most two patterns per hash residue mod 32, so the 32
+// filter-word loads of one row touch each shared-memory bank at most twice.
+// Per slot a lane keeps a bit mask of the rows whose filter test passed; each
+// pass goes to the warp's queue as (candidate hash, slot, row), and the queue
+// is verified against the hash table of U, lane-parallel, when the next group
+// might not fit.  1024 threads per block (one block per SM: the filter takes
+// up to 128 KB of shared memory), at most 64 registers a thread.
 // --------------------------------------------------------------------------
 constexpr int R = kRowsPerWarp;
 constexpr int kMaxSegs = 64 * kMaxWords;
 // work items a warp takes per atomic, and search-table groups per work item
 // (bounds an item's length): launch parameters (SearchTune), 4 and 16 by default
-constexpr int kCandCap = 256;      // per-warp queue of filter survivors (sample, slot)
+constexpr int kQueueCap = 32 * R;   // per-warp queue of filter passes: one group adds at most 32 R
+constexpr int kGens = 2;            // row caches per warp; a queue entry names the one it refers to
+// queue entry: x = candidate hash h(x) ^ h(XY) (after phase 1 of the
+// verification: the first tag match, bit 31 set for the slow path);
+// y = slot | row << 28 | cache << 31 (slots < 2^28)
+constexpr uint32_t kSlotMask = (1u << 28) - 1u;
 
 struct TermsArgs {
   const uint64_t* U;
@@ -341,13 +349,16 @@ struct TermsArgs {
   int32_t* status;
   unsigned long long* item_counter;
   int items_per_grab;
+  int part, n_parts;      // slice `part` of `n_parts` equal slices of the work items
   int groups_per_item;
 };
 
 template <int W>
-struct RowCache {   // per-warp copy of the item's rows (shared memory)
-  uint32_t hx[R];
-  int32_t row[R];
+struct RowCache {   // per-warp copies of the rows of the item (two generations)
+  int32_t row[kGens][R];
+  uint32_t hx[kGens][R];
+  uint32_t cnt[kGens][R];   // COUNT / EMIT: pairs found for the row since the cache was filled
+  uint64_t x[kGens][R][W];
 };
 
 // Place one pair in row r (relative to the range) at the row's next free
@@ -375,7 +386,7 @@ struct RecState {  // warp-uniform: current record chunk (base < 0: none) and it
 // in row i and in row j.
 template <int MODE>
 __device__ __forceinline__ void emit_found(bool found, int64_t i, uint32_t j, uint32_t id, RecState& rs,
-                                           const TermsArgs& a) {
+                                           const TermsArgs& a, uint32_t* icount = nullptr) {
   const int lane = threadIdx.x & 31;
   const bool in_i = found && i >= a.row_begin && i < a.row_end;
   const bool in_j = found && (int64_t)j >= a.row_begin && (int64_t)j < a.row_end;
@@ -385,7 +396,10 @@ __device__ __forceinline__ void emit_found(bool found, int64_t i, uint32_t j, ui
     return;
   }
   if (MODE != kEmitHalf) {
-    if (in_i) atomicAdd((unsigned long long*)(a.counts + (i - a.row_begin)), 1ull);
+    if (in_i) {
+      if (icount) atomicAdd(icount, 1u);  // row i's shared counter, added to counts when the cache is reused
+      else atomicAdd((unsigned long long*)(a.counts + (i - a.row_begin)), 1ull);
+    }
     if (in_j) atomicAdd((unsigned long long*)(a.counts + ((int64_t)j - a.row_begin)), 1ull);
   }
   if (MODE == kEmit || MODE == kEmitHalf) {
@@ -447,49 +461,44 @@ __device__ __noinline__ bool verify_slow(const uint64_t* x, uint32_t pos, uint32
   return false;
 }
 
-// Verification of queued candidates (sample i, search slot pos), in two
-// converged phases.  Phase 1 (four candidates per lane in flight): the hash of
-// x' = U_i XOR XY(pos) (one XOR of two stored hashes) picks a bucket of the
-// table of U; candidates with a tag match, or a full bucket, survive into a
-// compact list.  Phase 2 (four survivors per lane): the first tag match is
-// confirmed exactly (almost always the only one); full buckets or several
-// equal tags take the slow path; found pairs are emitted.
-constexpr int kVerifyWays = 4;
-
-// Phase-1 survivors are compacted in place into the queue's consumed entries;
-// beside each, its first tag match (bits 0-30; kNoMatch if none) and bit 31
-// set when several tags match or the bucket is full (slow path).
-struct Survivors {
-  uint32_t jc[kCandCap];
-};
+// Verification of queued filter passes, in two converged phases.  Phase 1
+// (kWays1 entries per lane in flight): the candidate's hash picks a bucket of
+// the table of U; entries with a tag match, or a full bucket, are compacted
+// in place (the first tag match beside them; bit 31 when several tags match
+// or the bucket is full).  Phase 2: the first tag match is confirmed exactly
+// against x XOR XY (x from the row cache); otherwise, with bit 31, the slow
+// path walks the chain; found pairs are emitted.
 constexpr uint32_t kNoMatch = 0x7FFFFFFFu;  // no sample has this index (n_unq < 2^31)
+constexpr int kWays1 = 2;
+template <int W>
+struct Ways2 {
+  static constexpr int v = 1;
+};
 
 template <int W, int MODE>
-__device__ __forceinline__ void verify_queue(uint2* q, int qn, Survivors* sv, RecState& rs, const TermsArgs& a) {
+__device__ __forceinline__ void verify_queue(uint2* q, int qn, RowCache<W>* rc, RecState& rs,
+                                             const TermsArgs& a) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   int ns = 0;
-  for (int e0 = 0; e0 < qn; e0 += 32 * kVerifyWays) {
-    uint32_t row[kVerifyWays], pos[kVerifyWays], sh[kVerifyWays];
-    uint4 b0[kVerifyWays], b1[kVerifyWays];
+  for (int e0 = 0; e0 < qn; e0 += 32 * kWays1) {
+    uint2 ent[kWays1];
+    uint4 b0[kWays1], b1[kWays1];
 #pragma unroll
-    for (int u = 0; u < kVerifyWays; ++u) {
+    for (int u = 0; u < kWays1; ++u) {
       const int e = e0 + u * 32 + lane;
-      const uint2 ent = q[e < qn ? e : 0];
-      row[u] = ent.x;
-      pos[u] = ent.y;
-      sh[u] = __ldg(a.hx + row[u]) ^ __ldg(a.srch_hash + pos[u]);
+      ent[u] = q[e < qn ? e : 0];
     }
 #pragma unroll
-    for (int u = 0; u < kVerifyWays; ++u) {
-      const uint4* bk = reinterpret_cast<const uint4*>(a.table + (int64_t)(sh[u] & a.capmask) * 4);
+    for (int u = 0; u < kWays1; ++u) {
+      const uint4* bk = reinterpret_cast<const uint4*>(a.table + (int64_t)(ent[u].x & a.capmask) * 4);
       b0[u] = __ldg(bk);
       b1[u] = __ldg(bk + 1);
     }
 #pragma unroll
-    for (int u = 0; u < kVerifyWays; ++u) {
+    for (int u = 0; u < kWays1; ++u) {
       // tag matches among occupied slots; slots fill in order, so slot 3 occupied = full
-      const uint32_t s = sh[u];
+      const uint32_t s = ent[u].x;
       const uint32_t mm = (uint32_t)(b0[u].x == s && b0[u].y != ~0u) | ((uint32_t)(b0[u].z == s && b0[u].w != ~0u) << 1) |
                           ((uint32_t)(b1[u].x == s && b1[u].y != ~0u) << 2) | ((uint32_t)(b1[u].z == s && b1[u].w != ~0u) << 3);
       const uint32_t jc = mm == 0u ? kNoMatch : (mm & 1u) ? b0[u].y : (mm & 2u) ? b0[u].w : (mm & 4u) ? b1[u].y : b1[u].w;
@@ -497,58 +506,57 @@ __device__ __forceinline__ void verify_queue(uint2* q, int qn, Survivors* sv, Re
       const bool keep = e0 + u * 32 + lane < qn && (mm != 0u || full);
       const uint32_t m = __ballot_sync(kFull, keep);
       __syncwarp();  // every lane holds this round's entries before any is overwritten
-      if (keep) {
-        const int o = ns + __popc(m & lt);  // o <= entries consumed so far
-        q[o] = make_uint2(row[u], pos[u]);
-        sv->jc[o] = jc | (((mm & (mm - 1u)) != 0u || full) ? 0x80000000u : 0u);
-      }
+      if (keep) q[ns + __popc(m & lt)] = make_uint2(jc | (((mm & (mm - 1u)) != 0u || full) ? 0x80000000u : 0u), ent[u].y);
       ns += __popc(m);
     }
   }
   __syncwarp();
-  for (int e0 = 0; e0 < ns; e0 += 32 * kVerifyWays) {
-    uint32_t row[kVerifyWays], pos[kVerifyWays], jc[kVerifyWays], fl[kVerifyWays];
-    uint64_t rec0[kVerifyWays], xy[kVerifyWays][W], x[kVerifyWays][W], uj[kVerifyWays][W];
+  constexpr int K2 = Ways2<W>::v;
+  for (int e0 = 0; e0 < ns; e0 += 32 * K2) {
+    uint2 ent[K2];
+    uint64_t rec0[K2], xy[K2][W], uj[K2][W];
 #pragma unroll
-    for (int u = 0; u < kVerifyWays; ++u) {
+    for (int u = 0; u < K2; ++u) {
       const int e = e0 + u * 32 + lane;
-      const int ee = e < ns ? e : 0;
-      const uint2 ent = q[ee];
-      row[u] = ent.x;
-      pos[u] = ent.y;
-      jc[u] = sv->jc[ee] & kNoMatch;
-      fl[u] = sv->jc[ee] >> 31;
-      const uint64_t* rec = a.srch_rec + (int64_t)pos[u] * a.rec_words;
+      ent[u] = q[e < ns ? e : 0];
+      const uint32_t jc = ent[u].x & kNoMatch;
+      const uint64_t* rec = a.srch_rec + (int64_t)(ent[u].y & kSlotMask) * a.rec_words;
       rec0[u] = __ldg(rec);
 #pragma unroll
       for (int w = 0; w < W; ++w) {
         xy[u][w] = __ldg(rec + 1 + w);
-        x[u][w] = __ldg(a.U + (int64_t)row[u] * W + w);
-        uj[u][w] = jc[u] != kNoMatch ? __ldg(a.U + (int64_t)jc[u] * W + w) : ~0ull;
+        uj[u][w] = jc != kNoMatch ? __ldg(a.U + (int64_t)jc * W + w) : ~0ull;
       }
     }
 #pragma unroll
-    for (int u = 0; u < kVerifyWays; ++u) {
+    for (int u = 0; u < K2; ++u) {
       const bool live = e0 + u * 32 + lane < ns;
+      const int r = (int)((ent[u].y >> 28) & 7u), gen = (int)(ent[u].y >> 31);
       const uint32_t id = (uint32_t)(rec0[u] >> 32);
-      bool eq = jc[u] != kNoMatch;
+      uint32_t j = ent[u].x & kNoMatch;
+      uint64_t x[W];
+      bool eq = j != kNoMatch;
 #pragma unroll
-      for (int w = 0; w < W; ++w) eq = eq && ((x[u][w] ^ xy[u][w]) == uj[u][w]);
+      for (int w = 0; w < W; ++w) {
+        x[w] = rc->x[gen][r][w];
+        eq = eq && ((x[w] ^ xy[u][w]) == uj[u][w]);
+      }
       bool found = live && eq;
-      uint32_t j = jc[u];
-      if (live && !eq && fl[u]) found = verify_slow<W>(x[u], pos[u], (uint32_t)__ldg(a.hx + row[u]) ^ (uint32_t)rec0[u], a, j);
+      if (live && !eq && (ent[u].x >> 31))
+        found = verify_slow<W>(x, ent[u].y & kSlotMask, rc->hx[gen][r] ^ (uint32_t)rec0[u], a, j);
       found = found && id != kDummy;  // padding slots carry XY = 0 and never count
-      if (e0 + u * 32 < ns) emit_found<MODE>(found, (int64_t)row[u], j, id, rs, a);
+      if (e0 + u * 32 < ns)
+        emit_found<MODE>(found, (int64_t)rc->row[gen][r], j, id, rs, a, const_cast<uint32_t*>(&rc->cnt[gen][r]));
     }
   }
   __syncwarp();
 }
 
-// Oriented LoopOverTerms search kernel.  A warp probes 8 samples of a
-// per-qubit list against up to groups_per_item groups of that qubit's segment;
-// each filter survivor is queued as (sample, slot) in the warp's queue, which
-// is verified in full rounds whenever the next group might not fit, and once
-// more at the end.
+// Oriented LoopOverTerms search kernel.  The filter test of sample hash hr
+// against pattern hash hk: v = hr ^ hk is the candidate's hash; word
+// v mod nwords of the filter; the three bit positions f are the 5-bit fields
+// of v at bits 15, 20 and 25, and bit f - 1 (mod 32) is tested as bit 31 of
+// the word rotated right by f, which shifts straight into the row mask.
 template <int W, int MODE>
 __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const TermsArgs a) {
   if (MODE == kFill && (*(volatile int32_t*)a.status & kStatusCapacity)) return;  // buffers too small
@@ -558,7 +566,6 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
   uint32_t* bloom = smem;
   RowCache<W>* caches = reinterpret_cast<RowCache<W>*>(smem + a.nwords);
   uint2* queues = reinterpret_cast<uint2*>(caches + kSearchWarps);
-  Survivors* survivors = reinterpret_cast<Survivors*>(queues + kSearchWarps * kCandCap);
   {
     const uint4* src = reinterpret_cast<const uint4*>(a.bloom_g);
     uint4* dst = reinterpret_cast<uint4*>(bloom);
@@ -578,25 +585,64 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  uint2* q = queues + warp * kCandCap;
-  Survivors* sv = survivors + warp;
+  uint2* q = queues + warp * kQueueCap;
   const uint32_t lt = (1u << lane) - 1u;
   RowCache<W>* rc = caches + warp;
-  const int64_t n_items = s_cum[a.n_segs];
+  if (lane < kGens * R) {
+    rc->row[lane / R][lane % R] = -1;
+    rc->cnt[lane / R][lane % R] = 0u;
+  }
+  __syncwarp();
+  // this launch's slice of the work items
+  const int64_t i_begin = s_cum[a.n_segs] * a.part / a.n_parts;
+  const int64_t i_end = s_cum[a.n_segs] * (a.part + 1) / a.n_parts;
   const uint32_t wmask4 = a.wmask << 2;
   const char* bloom_bytes = reinterpret_cast<const char*>(bloom);
   RecState rs{-1, kRecChunk};
   int qn = 0;
   int cur_seg = -1;
   int64_t cur_batch = -1;
-  uint32_t hr4[R], hr17[R], hr22[R], hr27[R];
+  int gen = 1;
+  uint32_t qgens = 0;  // bit c: the queue holds entries of row cache c
+  uint32_t hr4[R];
   uint32_t vmask = 0;
+  // the rows' hashes are re-read from the row cache after every verification,
+  // so that they are not held in registers across it
+  auto load_rows = [&]() {
+    vmask = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      hr4[r] = *reinterpret_cast<volatile const uint32_t*>(&rc->hx[gen][r]) << 2;
+      if (*reinterpret_cast<volatile const int32_t*>(&rc->row[gen][r]) >= 0) vmask |= 1u << (R - 1 - r);
+    }
+  };
+  // add the shared counters of row cache c to the rows' counts (its queue entries are verified)
+  auto add_counts = [&](int c) {
+    if (MODE == kCount || MODE == kEmit) {
+      __syncwarp();
+      if (lane < R) {
+        const int32_t row = rc->row[c][lane];
+        const uint32_t k = rc->cnt[c][lane];
+        if (k != 0u)  // only rows of the range count
+          atomicAdd((unsigned long long*)(a.counts + ((int64_t)row - a.row_begin)), (unsigned long long)k);
+        rc->cnt[c][lane] = 0u;
+      }
+      __syncwarp();
+    }
+  };
+  auto flush = [&]() {
+    __syncwarp();
+    verify_queue<W, MODE>(q, qn, rc, rs, a);
+    __syncwarp();
+    qn = 0;
+    qgens = 0;
+  };
   while (true) {
     unsigned long long itu = 0;
     if (lane == 0) itu = atomicAdd(a.item_counter, (unsigned long long)a.items_per_grab);
-    const int64_t it0 = (int64_t)__shfl_sync(kFull, itu, 0);
-    if (it0 >= n_items) break;
-    const int64_t it1 = it0 + a.items_per_grab < n_items ? it0 + a.items_per_grab : n_items;
+    const int64_t it0 = i_begin + (int64_t)__shfl_sync(kFull, itu, 0);
+    if (it0 >= i_end) break;
+    const int64_t it1 = it0 + a.items_per_grab < i_end ? it0 + a.items_per_grab : i_end;
     for (int64_t it = it0; it < it1; ++it) {
       int lo = 0, hi = a.n_segs;  // s_cum[lo] <= it < s_cum[hi]
       while (hi - lo > 1) {
@@ -610,81 +656,81 @@ __global__ void __launch_bounds__(kSearchThreads, 1) pairs_terms_kernel(const Te
       const int64_t batch = local < 0x7FFFFFFF ? (int64_t)((uint32_t)local / (uint32_t)n_chunks) : local / n_chunks;
       const int g0 = sg.y + (int)(local - batch * n_chunks) * a.groups_per_item;
       const int g1 = g0 + a.groups_per_item < sg.z ? g0 + a.groups_per_item : sg.z;
-      if (lo != cur_seg || batch != cur_batch) {  // new rows (consecutive chunks share them)
+      if (lo != cur_seg || batch != cur_batch) {  // new rows (consecutive chunks share them) in the other cache
         cur_seg = lo;
         cur_batch = batch;
+        if (qgens & (1u << (gen ^ 1))) flush();  // the queue still refers to that cache
+        gen ^= 1;
+        add_counts(gen);
         const int64_t b0 = batch * R;
         const int64_t count_t = list_len(a.qcnt[sg.x], a.n_unq);
         __syncwarp();
         if (lane < R) {
           const bool valid = b0 + lane < count_t;
           const int32_t row = valid ? (int32_t)__ldg(a.qrows + s_qoff[sg.x] + b0 + lane) : -1;
-          rc->hx[lane] = valid ? __ldg(a.hx + row) : 0u;
-          rc->row[lane] = row;
+          rc->hx[gen][lane] = valid ? __ldg(a.hx + row) : 0u;
+          rc->row[gen][lane] = row;
+          rc->cnt[gen][lane] = 0u;
+#pragma unroll
+          for (int w = 0; w < W; ++w) rc->x[gen][lane][w] = valid ? __ldg(a.U + (int64_t)row * W + w) : 0ull;
         }
         __syncwarp();
-        vmask = 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const uint32_t h = rc->hx[r];
-          hr4[r] = h << 2;
-          hr17[r] = h >> 17;
-          hr22[r] = h >> 22;
-          hr27[r] = h >> 27;
-          if (rc->row[r] >= 0) vmask |= 1u << (R - 1 - r);
-        }
       }
+      load_rows();
+      const uint32_t cache_bits = (uint32_t)gen << 31;
       uint32_t hk_next = __ldg(a.srch_hash + (uint32_t)(g0 * 32 + lane));
       for (int g = g0; g < g1; ++g) {
         const uint32_t pos = (uint32_t)(g * 32 + lane);
         const uint32_t hk = hk_next;
         if (g + 1 < g1) hk_next = __ldg(a.srch_hash + pos + 32);  // next group's hashes in flight
-        const uint32_t hk4 = hk << 2, hk17 = hk >> 17, hk22 = hk >> 22, hk27 = hk >> 27;
+        const uint32_t hk4 = hk << 2;
         uint32_t hm = 0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          const uint32_t w = *reinterpret_cast<const uint32_t*>(bloom_bytes + ((hr4[r] ^ hk4) & wmask4));
-          const uint32_t t = __funnelshift_r(w, w, hr17[r] ^ hk17) & __funnelshift_r(w, w, hr22[r] ^ hk22) &
-                             __funnelshift_r(w, w, hr27[r] ^ hk27);
-          hm = (hm << 1) | (t & 1u);
+          const uint32_t v4 = hr4[r] ^ hk4;
+          const uint32_t w = *reinterpret_cast<const uint32_t*>(bloom_bytes + (v4 & wmask4));
+          const uint32_t t = __funnelshift_r(w, w, v4 >> 17) & __funnelshift_r(w, w, v4 >> 22) &
+                             __funnelshift_r(w, w, v4 >> 27);
+          hm = __funnelshift_l(t, hm, 1);  // hm << 1 | bit 31 of t
         }
         hm &= vmask;
         if (__ballot_sync(kFull, hm != 0u)) {
-          const int c = __popc(hm);
-          int incl = c;
+          // exclusive prefix of the lanes' pass counts (at most R = 8) from their bit planes
+          const uint32_t c = __popc(hm);
+          int excl = 0, total = 0;
 #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
+          for (int b = 0; b < 4; ++b) {
+            const uint32_t m = __ballot_sync(kFull, (c >> b) & 1u);
+            excl += __popc(m & lt) << b;
+            total += __popc(m) << b;
           }
-          const int total = __shfl_sync(kFull, incl, 31);
-          if (qn + total > kCandCap) {  // verify the queue first (total <= 32 R = kCandCap fits then)
-            __syncwarp();
-            verify_queue<W, MODE>(q, qn, sv, rs, a);
-            __syncwarp();
-            qn = 0;
+          if (qn + total > kQueueCap) {  // verify the queue first (total <= kQueueCap fits then)
+            flush();
+            load_rows();
           }
-          int at = qn + incl - c;
-          while (hm) {  // one entry per surviving row, rows of an entry in increasing order
+          int at = qn + excl;
+          while (hm) {  // one entry per passing row
             const int b = 31 - __clz(hm);
             hm &= ~(1u << b);
-            q[at++] = make_uint2((uint32_t)rc->row[R - 1 - b], pos);
+            const int r = R - 1 - b;
+            q[at++] = make_uint2(rc->hx[gen][r] ^ hk, pos | ((uint32_t)r << 28) | cache_bits);
           }
           qn += total;
+          qgens |= 1u << gen;
         }
       }
     }  // items of this grab
   }
-  __syncwarp();
-  verify_queue<W, MODE>(q, qn, sv, rs, a);
+  flush();
+  add_counts(0);
+  add_counts(1);
   if ((MODE == kEmit || MODE == kEmitHalf) && rs.base >= 0)  // mark the unused tail of the last chunk
     for (int f = rs.fill + lane; f < kRecChunk; f += 32) a.sc.rec_i[rs.base + f] = kNoRecord;
 }
 
 template <int W>
 static size_t search_smem(int64_t nwords) {
-  return 4 * (size_t)nwords + kSearchWarps * sizeof(RowCache<W>) + (size_t)kSearchWarps * kCandCap * sizeof(uint2) +
-         kSearchWarps * sizeof(Survivors);
+  return 4 * (size_t)nwords + kSearchWarps * sizeof(RowCache<W>) + (size_t)kSearchWarps * kQueueCap * sizeof(uint2);
 }
 constexpr int64_t kMaxBloomWords = 32768;   // stage_layout caps the filter at 128 KB
 
@@ -1248,6 +1294,8 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stag
   a.status = status;
   a.item_counter = ctr + kCtrItems;
   a.items_per_grab = std::max(1, tune.terms_grab);
+  a.part = tune.part;
+  a.n_parts = std::max(1, tune.n_parts);
   a.groups_per_item = std::max(1, tune.terms_groups);
   cudaError_t e;
   if (mode != kEmitHalf &&
@@ -1286,7 +1334,7 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stag
 // the workspace's counters.
 cudaError_t launch_find_half(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L,
                              uint32_t* rec_i, uint32_t* rec_j, uint32_t* rec_k, int64_t capacity,
-                             cudaStream_t s) {
+                             cudaStream_t s, int part, int n_parts) {
   PairScratch sc;
   std::memset(&sc, 0, sizeof(sc));
   sc.cursor = (int64_t*)(stage + L.off_counters) + kCtrHalf;
@@ -1294,7 +1342,109 @@ cudaError_t launch_find_half(const nqs_ham* ham, const uint64_t* U, char* stage,
   sc.rec_i = rec_i;
   sc.rec_j = rec_j;
   sc.rec_k = rec_k;
-  return launch_pairs_terms(ham, U, stage, L, 0, L.n_unq, nullptr, nullptr, nullptr, kEmitHalf, &sc, s);
+  SearchTune tune;
+  tune.part = part;
+  tune.n_parts = n_parts;
+  return launch_pairs_terms(ham, U, stage, L, 0, L.n_unq, nullptr, nullptr, nullptr, kEmitHalf, &sc, s, tune);
+}
+
+// --------------------------------------------------------------------------
+// Sharded search: records to the parts owning their rows, and records -> row
+// counts.  A part owns the rows [bounds[p], bounds[p + 1]).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ int owner_part(const int64_t* b, int n_parts, int64_t row) {
+  int lo = 0, hi = n_parts;  // b[lo] <= row < b[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (b[mid] <= row) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int kMaxParts = 1024;
+
+__global__ void route_count_kernel(const uint32_t* __restrict__ ri, const uint32_t* __restrict__ rj, int64_t n,
+                                   const int64_t* __restrict__ bounds, int n_parts,
+                                   unsigned long long* __restrict__ counts) {
+  __shared__ int64_t b[kMaxParts + 1];
+  __shared__ unsigned int c[kMaxParts];
+  for (int p = threadIdx.x; p <= n_parts; p += blockDim.x) b[p] = bounds[p];
+  for (int p = threadIdx.x; p < n_parts; p += blockDim.x) c[p] = 0u;
+  __syncthreads();
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = ri[q];
+    if (i == kNoRecord) continue;
+    const int pa = owner_part(b, n_parts, i), pb = owner_part(b, n_parts, rj[q]);
+    atomicAdd(&c[pa], 1u);
+    if (pb != pa) atomicAdd(&c[pb], 1u);
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < n_parts; p += blockDim.x)
+    if (c[p]) atomicAdd(counts + p, (unsigned long long)c[p]);
+}
+
+__global__ void route_scatter_kernel(const uint32_t* __restrict__ ri, const uint32_t* __restrict__ rj,
+                                     const uint32_t* __restrict__ rk, int64_t n, const int64_t* __restrict__ bounds,
+                                     int n_parts, unsigned long long* __restrict__ cursors, uint32_t* __restrict__ oi,
+                                     uint32_t* __restrict__ oj, uint32_t* __restrict__ ok) {
+  __shared__ int64_t b[kMaxParts + 1];
+  for (int p = threadIdx.x; p <= n_parts; p += blockDim.x) b[p] = bounds[p];
+  __syncthreads();
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = ri[q];
+    if (i == kNoRecord) continue;
+    const uint32_t j = rj[q], k = rk[q];
+    const int pa = owner_part(b, n_parts, i), pb = owner_part(b, n_parts, j);
+    unsigned long long at = atomicAdd(cursors + pa, 1ull);
+    oi[at] = i; oj[at] = j; ok[at] = k;
+    if (pb != pa) {
+      at = atomicAdd(cursors + pb, 1ull);
+      oi[at] = i; oj[at] = j; ok[at] = k;
+    }
+  }
+}
+
+__global__ void records_count_kernel(const uint32_t* __restrict__ ri, const uint32_t* __restrict__ rj, int64_t n,
+                                     int64_t rb, int64_t rows, unsigned long long* __restrict__ counts) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = ri[q];
+    if (i == kNoRecord) continue;
+    const int64_t a = (int64_t)i - rb, c = (int64_t)rj[q] - rb;
+    if (a >= 0 && a < rows) atomicAdd(counts + a, 1ull);
+    if (c >= 0 && c < rows) atomicAdd(counts + c, 1ull);
+  }
+}
+
+static int stream_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4 * num_sms())); }
+
+cudaError_t launch_route_count(const uint32_t* rec_i, const uint32_t* rec_j, int64_t n_slots, const int64_t* bounds,
+                               int n_parts, unsigned long long* counts, cudaStream_t s) {
+  if (n_parts < 1 || n_parts > kMaxParts) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * n_parts, s);
+  if (e != cudaSuccess || n_slots <= 0) return e;
+  route_count_kernel<<<stream_grid(n_slots), 256, 0, s>>>(rec_i, rec_j, n_slots, bounds, n_parts, counts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_route_scatter(const uint32_t* rec_i, const uint32_t* rec_j, const uint32_t* rec_k, int64_t n_slots,
+                                 const int64_t* bounds, int n_parts, unsigned long long* cursors, uint32_t* out_i,
+                                 uint32_t* out_j, uint32_t* out_k, cudaStream_t s) {
+  if (n_parts < 1 || n_parts > kMaxParts) return cudaErrorInvalidValue;
+  if (n_slots <= 0) return cudaSuccess;
+  route_scatter_kernel<<<stream_grid(n_slots), 256, 0, s>>>(rec_i, rec_j, rec_k, n_slots, bounds, n_parts, cursors,
+                                                            out_i, out_j, out_k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_records_count(const uint32_t* rec_i, const uint32_t* rec_j, int64_t n_rec, int64_t rb,
+                                 int64_t rows, int has_diag, int64_t* counts, int32_t* status, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  cudaError_t e = launch_init(kCount, rows, rb, has_diag, counts, nullptr, nullptr, 0, nullptr, nullptr, -1, nullptr,
+                              status, s);
+  if (e != cudaSuccess || n_rec <= 0) return e;
+  records_count_kernel<<<stream_grid(n_rec), 256, 0, s>>>(rec_i, rec_j, n_rec, rb, rows,
+                                                          (unsigned long long*)counts);
+  return cudaGetLastError();
 }
 
 __global__ void clear_capacity_kernel(int32_t* status) {

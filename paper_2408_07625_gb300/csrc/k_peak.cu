@@ -2,7 +2,7 @@
 // (nqs_probe_peaks).  The paper has no counterpart.
 //
 // Two kernels, each timed with CUDA events on the caller's stream at the
-// LoopOverTerms search kernel's launch shape (one 512-thread block per SM):
+// LoopOverTerms search kernel's launch shape (one 1024-thread block per SM):
 //
 //   alu_mix_kernel  -- register-only integer work made of the operations of
 //     one filter probe (XOR, AND, 32-bit funnel shift, shift-or): sixteen
@@ -19,7 +19,7 @@
 
 namespace nqs {
 
-constexpr int kPeakThreads = 512;
+constexpr int kPeakThreads = 1024;
 constexpr int kAluChains = 16;
 constexpr int kAluOpsPerStep = 4;     // XOR, AND, funnel shift, OR per chain per step
 constexpr int kProbeRows = 8;
@@ -55,26 +55,21 @@ __global__ void __launch_bounds__(kPeakThreads, 1) probe_loop_kernel(const uint3
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t wmask4 = (uint32_t)(kPeakFilterWords - 1) << 2;
   const char* bytes = reinterpret_cast<const char*>(bloom);
-  uint32_t hr4[kProbeRows], hr17[kProbeRows], hr22[kProbeRows], hr27[kProbeRows];
+  uint32_t hr4[kProbeRows];
 #pragma unroll
-  for (int r = 0; r < kProbeRows; ++r) {
-    const uint32_t h = (t * 8u + r + 1u) * 2246822519u ^ seed;
-    hr4[r] = h << 2;
-    hr17[r] = h >> 17;
-    hr22[r] = h >> 22;
-    hr27[r] = h >> 27;
-  }
+  for (int r = 0; r < kProbeRows; ++r) hr4[r] = ((t * 8u + r + 1u) * 2246822519u ^ seed) << 2;
   uint32_t hk = seed * 3266489917u + t;
   uint32_t acc = 0;
   for (int g = 0; g < groups; ++g) {
-    const uint32_t hk4 = hk << 2, hk17 = hk >> 17, hk22 = hk >> 22, hk27 = hk >> 27;
+    const uint32_t hk4 = hk << 2;
     uint32_t hm = 0;
 #pragma unroll
     for (int r = 0; r < kProbeRows; ++r) {
-      const uint32_t w = *reinterpret_cast<const uint32_t*>(bytes + ((hr4[r] ^ hk4) & wmask4));
-      const uint32_t b = __funnelshift_r(w, w, hr17[r] ^ hk17) & __funnelshift_r(w, w, hr22[r] ^ hk22) &
-                         __funnelshift_r(w, w, hr27[r] ^ hk27);
-      hm = (hm << 1) | (b & 1u);
+      const uint32_t v4 = hr4[r] ^ hk4;
+      const uint32_t w = *reinterpret_cast<const uint32_t*>(bytes + (v4 & wmask4));
+      const uint32_t b = __funnelshift_r(w, w, v4 >> 17) & __funnelshift_r(w, w, v4 >> 22) &
+                         __funnelshift_r(w, w, v4 >> 27);
+      hm = __funnelshift_l(b, hm, 1);
     }
     acc += hm;
     hk = hk * 1664525u + 1013904223u;   // next pattern hash (stands in for the table load)

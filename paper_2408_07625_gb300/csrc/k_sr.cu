@@ -21,8 +21,11 @@
 #include <cfloat>
 #include <cstring>
 
+#include <cuda.h>   // CUtensorMap and its enums; the encoder is fetched through the runtime
 #include <cuda_bf16.h>
+#include <mutex>
 
+#include "device_util.cuh"
 #include "nqs_internal.cuh"
 
 namespace nqs {
@@ -87,6 +90,29 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16) completing on bar
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// 2-D tiled tensor copy global -> shared (box of the tensor map at column x, row y)
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -246,26 +272,280 @@ __global__ void __launch_bounds__(kSrThreads) gram_kernel(int n, int64_t P, cons
   if (warp == 0) tmem_dealloc(taddr, kSrRows);
 }
 
+
+// ---------------------------------------------------------------------------
+// Gram kernel, streamed form (P a multiple of 4, so that the rows of O are
+// 16-byte strided): one CTA per SM over a contiguous range of K tiles,
+// warp-specialised.  The producer warp loads each tile (all rows x 64 FP32
+// columns) with two 2-D tensor copies of 128 x 32 values (rows >= n and
+// columns >= P arrive as zeros), 128-byte swizzled so that the converters'
+// 16-byte reads are conflict-free, plus the tile's 64 means with a bulk copy,
+// into one of kBulkStages stages (completion counted in bytes on the stage's
+// mbarrier); kBulkConverters warps centre, scale and split a stage into the
+// bf16 hi / lo operand tiles (two operand stages) and release the FP32 stage;
+// one thread of the MMA warp issues the tile's twelve MMAs and commits them to
+// the operand stage's mbarrier, which releases it to the converters.  Every
+// wait is bounded; a wait that runs out stops the CTA's loop and flags the error.
+// ---------------------------------------------------------------------------
+constexpr int kBulkConverters = 16;
+constexpr int kConvSteps = (kSrRows / 8) * (kSrKTile / 16) / kBulkConverters;   // steps a converter warp owns
+constexpr int kBulkProducer = kBulkConverters;  // warp indices
+constexpr int kBulkMma = kBulkConverters + 1;
+constexpr int kBulkThreads = 32 * (kBulkConverters + 2);
+constexpr int kBulkStages = 4;
+constexpr int kBoxCols = 32;                                   // 128 bytes: the swizzle span
+constexpr int kBoxBytes = kSrRows * kBoxCols * 4;              // 16 KB
+constexpr int kBulkStageBytes = 2 * kBoxBytes;                 // 64 columns
+constexpr int kBulkMeanOff = kBulkStages * kBulkStageBytes;
+constexpr int kBulkOpOff = kBulkMeanOff + kBulkStages * kSrKTile * 4;
+constexpr int kBulkSmem = kBulkOpOff + 2 * 2 * kSrTileBytes + 1024;
+static_assert(kBulkOpOff % 1024 == 0 && kBulkStageBytes % 1024 == 0, "swizzled stages and operand tiles on 1 KB");
+
+__global__ void __launch_bounds__(kBulkThreads, 1)
+    gram_bulk_kernel(const __grid_constant__ CUtensorMap omap, int n, int64_t P, const float* __restrict__ m,
+                     const float* __restrict__ sw, int64_t tiles_per_cta, float* __restrict__ partial,
+                     int32_t* __restrict__ error) {
+  extern __shared__ __align__(1024) unsigned char sr_smem[];
+  __shared__ uint64_t full[kBulkStages], empty[kBulkStages], opfull[2], opempty[2];
+  __shared__ uint32_t s_taddr;
+  __shared__ float s_sw[kSrRows];
+  __shared__ int s_fail;
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)sr_smem + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t n_tiles = (P + kSrKTile - 1) / kSrKTile;
+  const int64_t t0 = (int64_t)blockIdx.x * tiles_per_cta;
+  const int64_t t1 = t0 + tiles_per_cta < n_tiles ? t0 + tiles_per_cta : n_tiles;
+  const int64_t nt = t1 > t0 ? t1 - t0 : 0;
+  if (tid == 0) {
+    for (int s = 0; s < kBulkStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kBulkConverters);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&opfull[s], kBulkConverters);
+      mbar_init(&opempty[s], 1);
+    }
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (tid < kSrRows) s_sw[tid] = tid < n ? sw[tid] : 0.f;
+  {  // operand rows the converters never write (>= n rounded up to 8) stay zero
+    uint4* op = reinterpret_cast<uint4*>(base + kBulkOpOff);
+    for (int i = tid; i < 2 * 2 * kSrTileBytes / 16; i += blockDim.x) op[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (warp == 0) {
+    tmem_alloc(&s_taddr, kSrRows);
+    tmem_relinquish();
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = s_taddr;
+  bool ok = true;
+  if (warp == kBulkProducer) {
+    int64_t issued = 0;
+    if (lane == 0) {
+      for (int64_t it = 0; it < nt; ++it) {
+        const int s = (int)(it % kBulkStages);
+        if (it >= kBulkStages && !mbar_wait(&empty[s], (uint32_t)(((it / kBulkStages) - 1) & 1))) { ok = false; break; }
+        if (*(volatile int*)&s_fail) break;
+        const int64_t k0 = (t0 + it) * kSrKTile;
+        const uint32_t mbytes = 4u * (uint32_t)(P - k0 < kSrKTile ? P - k0 : kSrKTile);
+        unsigned char* st = base + s * kBulkStageBytes;
+        mbar_expect_tx(&full[s], (uint32_t)kBulkStageBytes + mbytes);
+        tma_load_2d(st, &omap, (int)k0, 0, &full[s]);
+        tma_load_2d(st + kBoxBytes, &omap, (int)k0 + kBoxCols, 0, &full[s]);
+        bulk_g2s(base + kBulkMeanOff + s * kSrKTile * 4, m + k0, mbytes, &full[s]);
+        issued = it + 1;
+      }
+      // no copy may still be landing when the CTA leaves: wait for the last fill of every stage
+      for (int64_t it = issued > kBulkStages ? issued - kBulkStages : 0; it < issued; ++it)
+        if (!mbar_wait(&full[it % kBulkStages], (uint32_t)((it / kBulkStages) & 1))) ok = false;
+    }
+    __syncwarp();
+  } else if (warp == kBulkMma) {
+    for (int64_t it = 0; it < nt; ++it) {
+      const int s2 = (int)(it & 1);
+      if (!mbar_wait(&opfull[s2], (uint32_t)((it >> 1) & 1))) { ok = false; break; }
+      if (*(volatile int*)&s_fail) break;
+      if (lane == 0) {
+        tc_fence_after();
+        const uint32_t sh = smem_u32(base + kBulkOpOff + s2 * 2 * kSrTileBytes), sl = sh + kSrTileBytes;
+#pragma unroll
+        for (int j = 0; j < kSrKTile / 16; ++j) {
+          const uint32_t adv = (uint32_t)j * 2 * kSrLbo;
+          const uint64_t dh = umma_desc(sh + adv, kSrLbo, kSrSbo);
+          const uint64_t dl = umma_desc(sl + adv, kSrLbo, kSrSbo);
+          mma_bf16(taddr, dh, dh, kIdescBf16, (it > 0 || j > 0) ? 1u : 0u);
+          mma_bf16(taddr, dh, dl, kIdescBf16, 1u);
+          mma_bf16(taddr, dl, dh, kIdescBf16, 1u);
+        }
+        mma_commit(&opempty[s2]);
+      }
+      __syncwarp();
+    }
+  } else {
+    // this warp's steps (at most kConvSteps): a step = 8 rows x two core matrices along K,
+    // lane (row r % 8, half of 8 k) of core matrix 2 q + lane / 16, so that the warp's
+    // 8-byte stores fill 256 contiguous bytes; the lane's offsets are fixed for all tiles
+    const int n_steps = ((n + 7) / 8) * (kSrKTile / 16);
+    int in_off[kConvSteps], k_of[kConvSteps];
+    uint32_t op_off[kConvSteps];
+    float scale[kConvSteps];
+#pragma unroll
+    for (int q = 0; q < kConvSteps; ++q) {
+      const int step = warp + q * kBulkConverters;
+      const int rg = step / (kSrKTile / 16);
+      const int kc = (step % (kSrKTile / 16)) * 2 + (lane >> 4);
+      const int r = step < n_steps ? rg * 8 + ((lane >> 1) & 7) : 0;
+      const int k = kc * 8 + (lane & 1) * 4;
+      k_of[q] = k;
+      in_off[q] = (k >> 5) * kBoxBytes + r * 128 + ((((k & 31) >> 2) ^ (r & 7)) << 4);  // 128-byte swizzle
+      op_off[q] = tile_off(r, k);
+      scale[q] = s_sw[r];   // 0 for rows >= n
+    }
+    for (int64_t it = 0; it < nt; ++it) {
+      const int s = (int)(it % kBulkStages), s2 = (int)(it & 1);
+      if (!mbar_wait(&full[s], (uint32_t)((it / kBulkStages) & 1))) { ok = false; break; }
+      if (it >= 2 && !mbar_wait(&opempty[s2], (uint32_t)(((it >> 1) - 1) & 1))) { ok = false; break; }
+      if (*(volatile int*)&s_fail) break;
+      const unsigned char* st = base + s * kBulkStageBytes;
+      const float* mm = reinterpret_cast<const float*>(base + kBulkMeanOff + s * kSrKTile * 4);
+      unsigned char* hi = base + kBulkOpOff + s2 * 2 * kSrTileBytes;
+      unsigned char* lo = hi + kSrTileBytes;
+      const int cols = (int)(P - (t0 + it) * kSrKTile < kSrKTile ? P - (t0 + it) * kSrKTile : kSrKTile);
+      // rows >= n arrive as zeros with a zero scale; columns >= P (no mean copied) give 0
+      float4 o[kConvSteps], mv[kConvSteps];
+#pragma unroll
+      for (int q = 0; q < kConvSteps; ++q) {
+        if (warp + q * kBulkConverters < n_steps) {
+          o[q] = *reinterpret_cast<const float4*>(st + in_off[q]);
+          mv[q] = *reinterpret_cast<const float4*>(mm + k_of[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kConvSteps; ++q) {
+        if (warp + q * kBulkConverters >= n_steps) continue;
+        const int k = k_of[q];
+        const float sr = scale[q];
+        const float v[4] = {k + 0 < cols ? sr * (o[q].x - mv[q].x) : 0.f, k + 1 < cols ? sr * (o[q].y - mv[q].y) : 0.f,
+                            k + 2 < cols ? sr * (o[q].z - mv[q].z) : 0.f, k + 3 < cols ? sr * (o[q].w - mv[q].w) : 0.f};
+        float h[4], l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          h[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
+          l[j] = v[j] - h[j];
+        }
+        *reinterpret_cast<uint2*>(hi + op_off[q]) = make_uint2(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]));
+        *reinterpret_cast<uint2*>(lo + op_off[q]) = make_uint2(pack_bf16x2(l[0], l[1]), pack_bf16x2(l[2], l[3]));
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&opfull[s2]);
+        mbar_arrive(&empty[s]);
+      }
+    }
+  }
+  if (!ok) atomicExch(&s_fail, 1);
+  __syncthreads();
+  // the last tile's MMAs complete after all earlier ones: wait for its commit, then read D
+  bool done = !s_fail;
+  if (done && nt > 0) done = mbar_wait(&opempty[(nt - 1) & 1], (uint32_t)(((nt - 1) >> 1) & 1));
+  tc_fence_after();
+  if (warp < 4) {
+    const int row = warp * 32 + lane;
+    float* out = partial + (int64_t)blockIdx.x * kSrRows * kSrRows + (int64_t)row * kSrRows;
+    if (done && nt > 0) {
+#pragma unroll
+      for (int c = 0; c < kSrRows; c += 32) {
+        float v[32];
+        tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) out[c + i] = v[i];
+      }
+    } else {
+      for (int c = 0; c < kSrRows; ++c) out[c] = 0.f;
+    }
+  }
+  if (!done && nt > 0 && tid == 0) atomicOr(error, kStatusLimit);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(taddr, kSrRows);
+}
+
+// The tensor map of O [n rows][P columns] FP32 (row stride 4 P bytes) with 128 x 32 boxes,
+// 128-byte swizzle, zeros outside; the driver's encoder is fetched once through the runtime.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+static bool make_o_map(CUtensorMap* map, const float* O, int n, int64_t P) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)P, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)P * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)kBoxCols, (cuuint32_t)kSrRows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(O), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // ---------------------------------------------------------------------------
 // weights, column mean, Gram sum + regularised solve, step
 // ---------------------------------------------------------------------------
 // w = p / sum p (p = exp(2 (a - max a))), sqrt(w) as FP32 for the Gram kernel and FP64
 __global__ void sr_weights_kernel(int n, const double* __restrict__ a, double* __restrict__ w,
-                                  float* __restrict__ swf) {
-  __shared__ double sh[kSrRows];
-  const int t = threadIdx.x;
-  double amax = -DBL_MAX;
-  for (int i = 0; i < n; ++i) amax = fmax(amax, a[i]);
-  const double p = t < n ? exp(2.0 * (a[t] - amax)) : 0.0;
-  sh[t] = p;
+                                  float* __restrict__ swf, float* __restrict__ wf) {
+  __shared__ double red[kSrRows / 32];
+  __shared__ double s_max, s_sum;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const double at = t < n ? a[t] : -DBL_MAX;
+  double v = at;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+  if (lane == 0) red[warp] = v;
   __syncthreads();
   if (t == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += sh[i];
-    for (int i = 0; i < n; ++i) w[i] = sh[i] / s;
+    double m = red[0];
+    for (int i = 1; i < kSrRows / 32; ++i) m = fmax(m, red[i]);
+    s_max = m;
   }
   __syncthreads();
-  if (t < n) swf[t] = (float)sqrt(w[t]);
+  const double p = t < n ? exp(2.0 * (at - s_max)) : 0.0;
+  v = p;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (t == 0) {
+    double sum = 0.0;
+    for (int i = 0; i < kSrRows / 32; ++i) sum += red[i];
+    s_sum = sum;
+  }
+  __syncthreads();
+  if (t < n) {
+    const double wt = p / s_sum;
+    w[t] = wt;
+    swf[t] = (float)sqrt(wt);
+    wf[t] = (float)wt;
+  }
 }
 
 // m_p = sum_x w_x O_xp (FP64 accumulation over the N_SR rows), stored FP32
@@ -275,6 +555,46 @@ __global__ void sr_mean_kernel(int n, int64_t P, const float* __restrict__ O, co
     double s = 0.0;
     for (int x = 0; x < n; ++x) s += __ldg(w + x) * (double)__ldg(O + (int64_t)x * P + p);
     m[p] = (float)s;
+  }
+}
+
+// Four columns a thread (P a multiple of 4), the rows' loads four at a time in flight: m_p =
+// sum_x w_x O_xp with FP32 products summed with compensation (TwoSum), stored FP32
+__global__ void sr_mean4_kernel(int n, int64_t P, const float* __restrict__ O, const float* __restrict__ wf,
+                                float* __restrict__ m) {
+  const int64_t P4 = P / 4;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P4; q += (int64_t)gridDim.x * blockDim.x) {
+    const float4* col = reinterpret_cast<const float4*>(O) + q;
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    int x = 0;
+    for (; x + 4 <= n; x += 4) {
+      float4 o[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) o[u] = __ldg(col + (int64_t)(x + u) * P4);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float wx = __ldg(wf + x + u);
+        const float t[4] = {wx * o[u].x, wx * o[u].y, wx * o[u].z, wx * o[u].w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float a = s[j] + t[j], bb = a - s[j];
+          c[j] += (s[j] - (a - bb)) + (t[j] - bb);
+          s[j] = a;
+        }
+      }
+    }
+    for (; x < n; ++x) {
+      const float4 o = __ldg(col + (int64_t)x * P4);
+      const float wx = __ldg(wf + x);
+      const float t[4] = {wx * o.x, wx * o.y, wx * o.z, wx * o.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float a = s[j] + t[j], bb = a - s[j];
+        c[j] += (s[j] - (a - bb)) + (t[j] - bb);
+        s[j] = a;
+      }
+    }
+    reinterpret_cast<float4*>(m)[q] = make_float4(s[0] + c[0], s[1] + c[1], s[2] + c[2], s[3] + c[3]);
   }
 }
 
@@ -288,19 +608,57 @@ __global__ void sr_gram_sum_kernel(int n, int n_part, const float* __restrict__ 
   G[i] = s;
 }
 
-// T = (G + G^T) / 2; (T + lambda I + c u u^T) y = eps by Cholesky in FP64, one block of
-// kSrRows threads.  u = sqrt(w) is a unit null vector of the exact T (Obar^T u = sum_x w_x
-// (O_x - m) = 0), so the rank-one term changes y only along u, which the step Obar^T y
-// annihilates: delta is that of (T + lambda I)^{-1}.  With c = tr T / n the u direction
-// no longer has eigenvalue lambda, below the Gram's rounding for small lambda, which
-// would leave T + lambda I indefinite and amplify y along u by 1 / lambda.
-__global__ void sr_solve_kernel(int n, const double* __restrict__ G, const double* __restrict__ w,
-                                const double* __restrict__ eloc, const double* __restrict__ evar, double lambda,
-                                double* __restrict__ T, double* __restrict__ y, int32_t* __restrict__ error) {
-  extern __shared__ double A[];   // [n][n] then b[n]
-  double* b = A + n * n;
-  __shared__ double defl;
+// T = (G + G^T) / 2; (T + lambda I + c u u^T) y = eps by an L D L^T factorisation, one block of kSolveThreads
+// threads.  u = sqrt(w) is a unit null vector of the exact T (Obar^T u = sum_x w_x (O_x - m)
+// = 0), so the rank-one term changes y only along u, which the step Obar^T y annihilates:
+// delta is that of (T + lambda I)^{-1}.  With c = tr T / n the u direction no longer has
+// eigenvalue lambda, below the Gram's rounding for small lambda, which would leave
+// T + lambda I indefinite and amplify y along u by 1 / lambda.
+//
+// The factorisation and the substitutions run in double-float arithmetic (about 48
+// significant bits, FP32 pipes; this GPU's FP64 rate is a small fraction of its FP32
+// rate): the matrix is assembled in FP64, split into (hi, lo) pairs, factorised as
+// L D L^T right-looking (the trailing lower triangle and the right-hand side spread
+// over all threads, one barrier per column), and y is returned in FP64.  A pivot that
+// is not positive flags kStatusRange.
+constexpr int kSolveThreads = 512;
+
+// a - l * m in double-float (l * m's rounding error carried)
+__device__ __forceinline__ df df_sub_prod(df a, df l, df m) {
+  const float p = __fmul_rn(l.hi, m.hi);
+  float e = __fmaf_rn(l.hi, m.hi, -p);
+  e = __fmaf_rn(l.hi, m.lo, e);
+  e = __fmaf_rn(l.lo, m.hi, e);
+  const df s = two_sum(a.hi, -p);
+  return fast_two_sum(s.hi, __fadd_rn(__fsub_rn(a.lo, e), s.lo));
+}
+
+// sqrt and reciprocal of a positive double-float: FP32 estimate and one Newton step in df
+__device__ __forceinline__ df df_sqrt(df d) {
+  const float r0 = sqrtf(d.hi);
+  const df sq = {__fmul_rn(r0, r0), __fmaf_rn(r0, r0, -__fmul_rn(r0, r0))};
+  const float resid = __fadd_rn(__fsub_rn(d.hi, sq.hi), __fsub_rn(d.lo, sq.lo));
+  return fast_two_sum(r0, __fdiv_rn(resid, __fmul_rn(2.f, r0)));
+}
+__device__ __forceinline__ df df_recip(df d) {
+  const float r0 = __fdiv_rn(1.f, d.hi);
+  const df pr = df_mul(d, df{r0, 0.f});          // d r0 = 1 - e
+  const float e = __fsub_rn(__fsub_rn(1.f, pr.hi), pr.lo);
+  return fast_two_sum(r0, __fmul_rn(r0, e));
+}
+
+__global__ void __launch_bounds__(kSolveThreads) sr_solve_kernel(int n, const double* __restrict__ G,
+                                                                  const double* __restrict__ w,
+                                                                  const double* __restrict__ eloc,
+                                                                  const double* __restrict__ evar, double lambda,
+                                                                  double* __restrict__ T, double* __restrict__ y,
+                                                                  int32_t* __restrict__ error) {
+  extern __shared__ df A[];   // [n][n], then b[n] and the pivots' reciprocals [n]
+  df* b = A + n * n;
+  df* rinv = b + n;
+  __shared__ double defl, su[kSrRows];
   const int t = threadIdx.x;
+  if (t < n) su[t] = sqrt(w[t]);
   if (t == 0) {
     double tr = 0.0;
     for (int i = 0; i < n; ++i) tr += G[i * n + i];
@@ -311,43 +669,46 @@ __global__ void sr_solve_kernel(int n, const double* __restrict__ G, const doubl
     const int r = i / n, c = i % n;
     const double v = 0.5 * (G[i] + G[c * n + r]);
     if (T) T[i] = v;
-    A[i] = v + (r == c ? lambda : 0.0) + defl * sqrt(w[r] * w[c]);
+    A[i] = df_from_double(v + (r == c ? lambda : 0.0) + defl * su[r] * su[c]);
   }
-  if (t < n) b[t] = sqrt(w[t]) * (eloc[t] - evar[0]);
+  if (t < n) b[t] = df_from_double(su[t] * (eloc[t] - evar[0]));
   __syncthreads();
-  // Cholesky A = L L^T in place (lower triangle), column by column
+  // A = L D L^T, right-looking: column j is kept unscaled (l_ij = A_ij / d_j is formed where it
+  // is used), the trailing lower triangle and the right-hand side lose column j's
+  // contribution, so that b ends as L^{-1} b; one barrier per column
   for (int j = 0; j < n; ++j) {
-    if (t == 0) {
-      double d = A[j * n + j];
-      for (int k = 0; k < j; ++k) d -= A[j * n + k] * A[j * n + k];
-      if (!(d > 0.0)) {
-        atomicOr(error, kStatusRange);
-        d = DBL_MIN;
+    df d = A[j * n + j];
+    if (!(d.hi > 0.f)) {
+      if (t == 0) atomicOr(error, kStatusRange);
+      d = df{FLT_MIN, 0.f};
+    }
+    const df inv = df_recip(d);
+    if (t == 0) rinv[j] = inv;
+    const int m = n - j - 1;
+    const int tri = m * (m + 1) / 2;
+    for (int e = t; e < tri + m; e += blockDim.x) {
+      if (e >= tri) {  // right-hand side entry j + 1 + (e - tri)
+        const int ii = j + 1 + (e - tri);
+        b[ii] = df_sub_prod(b[ii], A[ii * n + j], df_mul(b[j], inv));
+        continue;
       }
-      A[j * n + j] = sqrt(d);
-    }
-    __syncthreads();
-    for (int i = j + 1 + t; i < n; i += blockDim.x) {
-      double s = A[i * n + j];
-      for (int k = 0; k < j; ++k) s -= A[i * n + k] * A[j * n + k];
-      A[i * n + j] = s / A[j * n + j];
+      int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);  // e = r (r + 1) / 2 + c, 0 <= c <= r
+      while (r * (r + 1) / 2 > e) --r;
+      while ((r + 1) * (r + 2) / 2 <= e) ++r;
+      const int ii = j + 1 + r, kk = j + 1 + (e - r * (r + 1) / 2);
+      A[ii * n + kk] = df_sub_prod(A[ii * n + kk], A[ii * n + j], df_mul(A[kk * n + j], inv));
     }
     __syncthreads();
   }
-  if (t == 0) {  // forward then back substitution
-    for (int i = 0; i < n; ++i) {
-      double s = b[i];
-      for (int k = 0; k < i; ++k) s -= A[i * n + k] * b[k];
-      b[i] = s / A[i * n + i];
-    }
-    for (int i = n - 1; i >= 0; --i) {
-      double s = b[i];
-      for (int k = i + 1; k < n; ++k) s -= A[k * n + i] * b[k];
-      b[i] = s / A[i * n + i];
-    }
-  }
+  // D^{-1}, then L^T y = D^{-1} L^{-1} b column by column from the last (L^T_{ij} = A_ji / d_i)
+  if (t < n) b[t] = df_mul(b[t], rinv[t]);
   __syncthreads();
-  if (t < n) y[t] = b[t];
+  for (int j = n - 1; j >= 0; --j) {
+    const df bj = b[j];
+    for (int i = t; i < j; i += blockDim.x) b[i] = df_sub_prod(b[i], df_mul(A[j * n + i], rinv[i]), bj);
+    __syncthreads();
+  }
+  if (t < n) y[t] = df_to_double(b[t]);
 }
 
 // delta_p = sum_x sqrt(w_x) (O_xp - m_p) y_x, FP32 compensated (two-sum) accumulation
@@ -367,6 +728,43 @@ __global__ void sr_step_kernel(int n, int64_t P, const float* __restrict__ O, co
       s = u;
     }
     delta[p] = (double)s + (double)c;
+  }
+}
+
+// the same with four columns a thread (P a multiple of 4), the rows' loads four at a time in flight
+__global__ void sr_step4_kernel(int n, int64_t P, const float* __restrict__ O, const float* __restrict__ m,
+                                const float* __restrict__ sw, const double* __restrict__ y, double* __restrict__ delta) {
+  __shared__ float cy[kSrRows];
+  if (threadIdx.x < n) cy[threadIdx.x] = (float)(y[threadIdx.x] * (double)sw[threadIdx.x]);
+  __syncthreads();
+  const int64_t P4 = P / 4;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P4; q += (int64_t)gridDim.x * blockDim.x) {
+    const float4* col = reinterpret_cast<const float4*>(O) + q;
+    const float4 mq = __ldg(reinterpret_cast<const float4*>(m) + q);
+    const float mp[4] = {mq.x, mq.y, mq.z, mq.w};
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    auto add_row = [&](const float4& o, float cx) {
+      const float ov[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float tm = cx * (ov[j] - mp[j]);
+        const float a = s[j] + tm, bb = a - s[j];
+        c[j] += (s[j] - (a - bb)) + (tm - bb);
+        s[j] = a;
+      }
+    };
+    int x = 0;
+    for (; x + 4 <= n; x += 4) {
+      float4 o[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) o[u] = __ldg(col + (int64_t)(x + u) * P4);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) add_row(o[u], cy[x + u]);
+    }
+    for (; x < n; ++x) add_row(__ldg(col + (int64_t)x * P4), cy[x]);
+    double2* d = reinterpret_cast<double2*>(delta + 4 * q);
+    d[0] = make_double2((double)s[0] + (double)c[0], (double)s[1] + (double)c[1]);
+    d[1] = make_double2((double)s[2] + (double)c[2], (double)s[3] + (double)c[3]);
   }
 }
 
@@ -414,6 +812,7 @@ cudaError_t launch_sr_top(int64_t n, const double* a, int64_t n_sr, int32_t* out
 struct SrScratch {
   double* w;
   float* sw;
+  float* wf;
   float* m;
   float* partial;
   double* G;
@@ -431,6 +830,7 @@ static SrScratch sr_scratch_view(char* base, int64_t P, int n_part) {
   v.error = (int32_t*)take(256);
   v.w = (double*)take(8 * kSrRows);
   v.sw = (float*)take(4 * kSrRows);
+  v.wf = (float*)take(4 * kSrRows);
   v.y = (double*)take(8 * kSrRows);
   v.G = (double*)take(8 * kSrRows * kSrRows);
   v.m = (float*)take(4 * std::max<int64_t>(P, 1) + 16);
@@ -450,24 +850,46 @@ cudaError_t launch_sr_step(int n, int64_t P, const float* O, const double* a, co
   const SrScratch sc = sr_scratch_view((char*)scratch, P, sr_parts());
   cudaError_t e = cudaMemsetAsync(sc.error, 0, 4, s);
   if (e != cudaSuccess) return e;
-  sr_weights_kernel<<<1, kSrRows, 0, s>>>(n, a, sc.w, sc.sw);
+  sr_weights_kernel<<<1, kSrRows, 0, s>>>(n, a, sc.w, sc.sw, sc.wf);
   const int sms = num_sms();
-  sr_mean_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, 8 * sms)), 256, 0, s>>>(n, P, O, sc.w,
-                                                                                                        sc.m);
   const int64_t n_tiles = (P + kSrKTile - 1) / kSrKTile;
-  const int64_t per = (n_tiles + sc.n_part - 1) / sc.n_part;
-  if ((e = cudaFuncSetAttribute(gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSrSmem)) != cudaSuccess)
-    return e;
-  gram_kernel<<<(int)sc.n_part, kSrThreads, kSrSmem, s>>>(n, P, O, sc.m, sc.sw, per, sc.partial, sc.error);
+  // rows of O on 16-byte boundaries: the streamed kernels (float4 columns, bulk copies)
+  const bool streamed = (P % 4) == 0 && (((uintptr_t)O) & 15) == 0 && (((uintptr_t)delta) & 15) == 0;
+  CUtensorMap omap;
+  const bool tiled = streamed && P < (int64_t(1) << 31) && make_o_map(&omap, O, n, P);
+  const int stream_grid = (int)std::max<int64_t>(1, std::min<int64_t>((P / 4 + 255) / 256, 4 * sms));
+  if (streamed)
+    sr_mean4_kernel<<<stream_grid, 256, 0, s>>>(n, P, O, sc.wf, sc.m);
+  else
+    sr_mean_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, 8 * sms)), 256, 0, s>>>(n, P, O,
+                                                                                                          sc.w, sc.m);
+  int n_part;
+  if (tiled) {
+    n_part = (int)std::min<int64_t>(sms, n_tiles);
+    const int64_t per = (n_tiles + n_part - 1) / n_part;
+    if ((e = cudaFuncSetAttribute(gram_bulk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBulkSmem)) !=
+        cudaSuccess)
+      return e;
+    gram_bulk_kernel<<<n_part, kBulkThreads, kBulkSmem, s>>>(omap, n, P, sc.m, sc.sw, per, sc.partial, sc.error);
+  } else {
+    n_part = (int)sc.n_part;
+    const int64_t per = (n_tiles + n_part - 1) / n_part;
+    if ((e = cudaFuncSetAttribute(gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSrSmem)) != cudaSuccess)
+      return e;
+    gram_kernel<<<n_part, kSrThreads, kSrSmem, s>>>(n, P, O, sc.m, sc.sw, per, sc.partial, sc.error);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const size_t solve_smem = sizeof(double) * (size_t)(n * n + n);
+  const size_t solve_smem = sizeof(df) * (size_t)(n * n + 2 * n);
   if ((e = cudaFuncSetAttribute(sr_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem)) !=
       cudaSuccess)
     return e;
-  sr_gram_sum_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, (int)sc.n_part, sc.partial, sc.G);
-  sr_solve_kernel<<<1, kSrRows, solve_smem, s>>>(n, sc.G, sc.w, eloc, evar, lambda, T, sc.y, sc.error);
-  sr_step_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, 8 * sms)), 256, 0, s>>>(
-      n, P, O, sc.m, sc.sw, sc.y, delta);
+  sr_gram_sum_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, n_part, sc.partial, sc.G);
+  sr_solve_kernel<<<1, kSolveThreads, solve_smem, s>>>(n, sc.G, sc.w, eloc, evar, lambda, T, sc.y, sc.error);
+  if (streamed)
+    sr_step4_kernel<<<stream_grid, 256, 0, s>>>(n, P, O, sc.m, sc.sw, sc.y, delta);
+  else
+    sr_step_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, 8 * sms)), 256, 0, s>>>(
+        n, P, O, sc.m, sc.sw, sc.y, delta);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int32_t err = 0;
   if ((e = cudaMemcpyAsync(&err, sc.error, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;

@@ -229,8 +229,23 @@ static void scan_i32(int32_t* d, int64_t m, int32_t* partial, cudaStream_t s) {
 
 int64_t sort_scan_partials(int64_t n) { return 256 * sort_blocks(n) / kScanTileI + 1; }
 
+cudaError_t launch_scan_i32(int32_t* d, int64_t m, int32_t* partial, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  scan_i32(d, m, partial, s);
+  return cudaGetLastError();
+}
+
 // Stable scatter: warp w of a block owns keys [t0 + 256 w, t0 + 256 w + 256),
-// visited in rounds of 32; equal digits are ranked by (round, lane).
+// visited in rounds of 32; equal digits are ranked by (round, lane).  The
+// block's keys are first placed in shared memory in digit order (the block's
+// own stable sort by this digit), then written out in that order, so that
+// consecutive threads write consecutive positions of each digit's run and
+// the global stores coalesce.  Dynamic shared memory: sort_scatter_smem(W).
+template <int W>
+constexpr size_t sort_scatter_smem() {
+  return (size_t)kSortTile * (8 * W + 4 + 4);
+}
+
 template <int W, bool QORDER>
 __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const uint64_t* __restrict__ kin,
                                                                     const int32_t* __restrict__ iin, int64_t n, int g,
@@ -238,22 +253,30 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const uint64
                                                                     uint64_t* __restrict__ kout,
                                                                     int32_t* __restrict__ iout) {
   __shared__ int32_t wcnt[kSortThreads / 32][256];
+  __shared__ int32_t dstart[256];   // block-local start of each digit's run
+  __shared__ int32_t gbase[256];    // global start of this block's run of each digit
+  __shared__ int32_t wtot[kSortThreads / 32];
+  extern __shared__ __align__(16) unsigned char sort_smem[];
+  uint64_t* sk = reinterpret_cast<uint64_t*>(sort_smem);                 // [kSortTile][W]
+  int32_t* si = reinterpret_cast<int32_t*>(sk + (size_t)kSortTile * W);  // [kSortTile]
+  int32_t* sd = si + kSortTile;                                          // [kSortTile] digits
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   for (int d = lane; d < 256; d += 32) wcnt[warp][d] = 0;
   __syncwarp();
-  const int64_t w0 = (int64_t)blockIdx.x * kSortTile + warp * (32 * kSortItems);
+  const int64_t t0 = (int64_t)blockIdx.x * kSortTile;
+  const int64_t w0 = t0 + warp * (32 * kSortItems);
   uint32_t dig[kSortItems];
   int32_t rank[kSortItems];
+  uint64_t key[kSortItems][W];
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
     const int64_t e = w0 + k * 32 + lane;
     const bool live = e < n;
     uint32_t d = 256u + lane;  // never matches a live digit
     if (live) {
-      uint64_t v[W];
-      load_words<W>(kin + e * W, v);
-      d = sort_digit<W, QORDER>(v, g);
+      load_words<W>(kin + e * W, key[k]);
+      d = sort_digit<W, QORDER>(key[k], g);
     }
     const uint32_t peers = __match_any_sync(kFull, d);
     const int32_t prior = live ? wcnt[warp][d] : 0;
@@ -264,25 +287,47 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const uint64
     rank[k] = prior + __popc(peers & lt);
   }
   __syncthreads();
-  {  // per digit: exclusive prefix over warps, plus the block's global offset
+  {  // thread d: offsets of each warp within the block's run of digit d, then the runs' starts
     const int d = threadIdx.x;
-    int32_t run = hist[(int64_t)d * nblk + blockIdx.x];
+    int32_t run = 0;
     for (int w = 0; w < kSortThreads / 32; ++w) {
       const int32_t c = wcnt[w][d];
       wcnt[w][d] = run;
       run += c;
     }
+    gbase[d] = hist[(int64_t)d * nblk + blockIdx.x];
+    int32_t incl = run;  // exclusive scan of the run lengths over digits (block scan)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t x = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += x;
+    }
+    if (lane == 31) wtot[warp] = incl;
+    __syncthreads();
+    int32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += wtot[w];
+    dstart[d] = before + incl - run;
   }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
     const int64_t e = w0 + k * 32 + lane;
     if (e < n) {
-      const int64_t dst = (int64_t)wcnt[warp][dig[k]] + rank[k];
+      const int32_t p = dstart[dig[k]] + wcnt[warp][dig[k]] + rank[k];
 #pragma unroll
-      for (int w = 0; w < W; ++w) kout[dst * W + w] = __ldg(kin + e * W + w);
-      iout[dst] = iin ? __ldg(iin + e) : (int32_t)e;
+      for (int w = 0; w < W; ++w) sk[(size_t)p * W + w] = key[k][w];
+      si[p] = iin ? __ldg(iin + e) : (int32_t)e;
+      sd[p] = (int32_t)dig[k];
     }
+  }
+  __syncthreads();
+  const int live = (int)(n - t0 < kSortTile ? n - t0 : kSortTile);
+  for (int p = threadIdx.x; p < live; p += kSortThreads) {
+    const int d = sd[p];
+    const int64_t dst = (int64_t)gbase[d] + (p - dstart[d]);
+#pragma unroll
+    for (int w = 0; w < W; ++w) kout[dst * W + w] = sk[(size_t)p * W + w];
+    iout[dst] = si[p];
   }
 }
 
@@ -424,6 +469,13 @@ int64_t trie_bytes(int W, int64_t n) {
   return 2 * 8 * W * n + 5 * 4 * n + 4 * 256 * nblk + 256 + 8 * (n + 1) + 256 + rec * n + 256;
 }
 
+// the scatter's dynamic shared memory may exceed the default 48 KB (W > 1)
+template <int W, bool QORDER>
+static cudaError_t scatter_attr() {
+  return cudaFuncSetAttribute(sort_scatter_kernel<W, QORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sort_scatter_smem<W>());
+}
+
 template <int W>
 static cudaError_t trie_build_w(const nqs_ham* ham, const uint64_t* U, int64_t n, char* stage,
                                 const StageHeader& L, cudaStream_t s) {
@@ -437,7 +489,9 @@ static cudaError_t trie_build_w(const nqs_ham* ham, const uint64_t* U, int64_t n
   for (int g = G - 1; g >= 0; --g) {  // least significant digit (highest qubits) first
     sort_hist_kernel<W, true><<<v.nblk, kSortThreads, 0, s>>>(kin, n, g, v.hist, v.nblk);
     sort_scan_kernel<<<1, 1024, 0, s>>>(v.hist, 256 * (int64_t)v.nblk);
-    sort_scatter_kernel<W, true><<<v.nblk, kSortThreads, 0, s>>>(kin, iin, n, g, v.hist, v.nblk, v.keys[cur], v.idx[cur]);
+    if ((e = scatter_attr<W, true>()) != cudaSuccess) return e;
+    sort_scatter_kernel<W, true><<<v.nblk, kSortThreads, sort_scatter_smem<W>(), s>>>(kin, iin, n, g, v.hist, v.nblk,
+                                                                                    v.keys[cur], v.idx[cur]);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     kin = v.keys[cur];
     iin = v.idx[cur];
@@ -482,8 +536,11 @@ static cudaError_t sort_words_w(const uint64_t* kin, const int32_t* iin, int64_t
   for (int g = 0; g < n_bytes; ++g) {
     sort_hist_kernel<W, false><<<nblk, kSortThreads, 0, s>>>(kin, n, g, hist, nblk);
     scan_i32(hist, 256 * (int64_t)nblk, partial, s);
-    sort_scatter_kernel<W, false><<<nblk, kSortThreads, 0, s>>>(kin, iin, n, g, hist, nblk, kbuf[cur], ibuf[cur]);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = scatter_attr<W, false>();
+    if (e != cudaSuccess) return e;
+    sort_scatter_kernel<W, false><<<nblk, kSortThreads, sort_scatter_smem<W>(), s>>>(kin, iin, n, g, hist, nblk,
+                                                                                   kbuf[cur], ibuf[cur]);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     kin = kbuf[cur];
     iin = ibuf[cur];

@@ -14,7 +14,6 @@ constexpr int kMaxWords = 4;                 // N <= 256 qubits
 constexpr uint32_t kDummy = 0xFFFFFFFFu;     // padding slot of the search table
 constexpr int kHeavyTerms = 24;              // |P_XY| above this: warp-cooperative term loop
 namespace kForm { constexpr int Terms = 0, Local = 1; }
-constexpr int kQueueCap = 256;               // per-warp candidate queue (entries)
 constexpr int kRowsPerWarp = 8;              // rows scanned together by one warp
 constexpr int kSortWarpMax = 512;           // rows with up to this many pairs are sorted by one warp
 constexpr int kSortBlockKeys = 16384;        // longer rows: one block, in shared memory up to this size
@@ -159,6 +158,8 @@ struct SearchTune {
   int terms_grab = 4;
   int terms_groups = 16;
   int trie_pop = 32;
+  int part = 0;      // LoopOverTerms: search only slice `part` of `n_parts` equal slices of the work items
+  int n_parts = 1;
 };
 
 // search modes: COUNT writes per-row counts, FILL writes pairs at given CSR
@@ -218,6 +219,8 @@ cudaError_t launch_scan(int64_t* data, int64_t n, char* stage, const StageHeader
 // LSD radix sort of W-word keys in numeric order with an int32 payload (k_trie.cu)
 int64_t sort_blocks(int64_t n);
 int64_t sort_scan_partials(int64_t n);   // ints of the tiled histogram scan for n keys
+// exclusive scan of m int32 in place (partial: ceil(m / 2048) + 1 ints when m > 2^18)
+cudaError_t launch_scan_i32(int32_t* d, int64_t m, int32_t* partial, cudaStream_t s);
 cudaError_t launch_sort_words(const uint64_t* kin, const int32_t* iin, int64_t n, int W, int n_bytes,
                               uint64_t* kbuf[2], int32_t* ibuf[2], int32_t* hist, int32_t* partial, int* out,
                               cudaStream_t s);
@@ -272,7 +275,20 @@ cudaError_t launch_gumbel_level(int W, int level, int64_t n, const uint64_t* px,
 // half-stored pairs: the records of one EMIT_HALF search (k_half section of k_energy.cu)
 cudaError_t launch_find_half(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L,
                              uint32_t* rec_i, uint32_t* rec_j, uint32_t* rec_k, int64_t capacity,
-                             cudaStream_t s);
+                             cudaStream_t s, int part = 0, int n_parts = 1);
+
+// Sharded search support.  route: the live records (i != 0xFFFFFFFF) copied to
+// the part(s) owning rows i and j (bounds: device [n_parts + 1] row bounds),
+// grouped by part at the device offsets off[p] (exclusive prefix of the counts
+// that route_count produced); counts are 64-bit.
+cudaError_t launch_route_count(const uint32_t* rec_i, const uint32_t* rec_j, int64_t n_slots, const int64_t* bounds,
+                               int n_parts, unsigned long long* counts, cudaStream_t s);
+cudaError_t launch_route_scatter(const uint32_t* rec_i, const uint32_t* rec_j, const uint32_t* rec_k, int64_t n_slots,
+                                 const int64_t* bounds, int n_parts, unsigned long long* cursors, uint32_t* out_i,
+                                 uint32_t* out_j, uint32_t* out_k, cudaStream_t s);
+// records -> per-row counts of rows [rb, rb + rows): has_diag, plus one for each record naming the row
+cudaError_t launch_records_count(const uint32_t* rec_i, const uint32_t* rec_j, int64_t n_rec, int64_t rb,
+                                 int64_t rows, int has_diag, int64_t* counts, int32_t* status, cudaStream_t s);
 cudaError_t launch_local_energy_half(const nqs_ham* ham, const uint64_t* U, int64_t n, const char* stage,
                                      const StageHeader& L, bool cplx, const uint32_t* ri, const uint32_t* rj,
                                      const uint32_t* rk, int64_t n_slots, int precision, double* er, double* ei,

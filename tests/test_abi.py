@@ -60,6 +60,24 @@ def test_host_side_argument_errors(lib):
     assert lib.nqs_stage_bytes(None, 10) < 0
     assert lib.nqs_variational_energy(0, None, None, None, None, None) == -1
     assert lib.nqs_ham_free(None) == 0
+    # the sharded search's host-side checks (no device work is reached)
+    lib.nqs_route_scratch_bytes.restype = ctypes.c_int64
+    assert lib.nqs_route_scratch_bytes(0) < 0 and lib.nqs_route_scratch_bytes(1025) < 0
+    assert lib.nqs_route_scratch_bytes(8) > 0
+    b = np.array([0, 5, 3], np.int64)  # not ascending
+    cnt = np.zeros(2, np.int64)
+    i64 = ctypes.c_int64
+    p64 = ctypes.POINTER(ctypes.c_int64)
+    bp, cp = b.ctypes.data_as(p64), cnt.ctypes.data_as(p64)
+    args = (None, None, None, i64(0), None, None, None, i64(0), cp)
+    assert lib.nqs_route_records(0, bp, *args, None, i64(0), None) == -1
+    assert lib.nqs_route_records(2, None, *args, None, i64(0), None) == -1
+    assert lib.nqs_route_records(2, bp, *args, None, i64(0), None) == -1  # no scratch
+    raw = np.zeros(4096, np.uint8)
+    scr = raw[(-raw.ctypes.data) % 256:][:1024]  # 256-byte aligned (host memory: never reached)
+    assert lib.nqs_route_records(2, bp, *args, scr.ctypes.data, i64(1024), None) == -1
+    assert b"ascending" in lib.nqs_last_error()
+    assert lib.nqs_find_pairs_part(None, None, i64(0), None, 0, 1, None, None, None, i64(0), None, None) == -1
 
 
 def test_product_package_does_not_import_the_oracle():

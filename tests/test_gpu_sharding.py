@@ -59,3 +59,36 @@ def test_device_combine_matches_host():
         h = combine_parts(torch.from_numpy(parts))
         d = combine_parts(torch.from_numpy(parts).cuda())
         assert np.allclose(h.numpy(), d.cpu().numpy(), rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("ws,workload,n_unq", [(2, "h28", 3000), (3, "h28", 3000), (8, "h56", 20000)])
+def test_sharded_search_matches_direct_search(ws, workload, n_unq):
+    """The sharded FindCoupledPairs, emulated on one GPU: every rank's slice of the
+    search's work items, routing of its records to the row owners, the all-to-all
+    (concatenation of every slice's group for a rank) and the CSR assembly give each
+    rank exactly the lists of searching its rows directly (bitwise); the slices
+    together list every unordered pair once."""
+    inst = config_instance(workload, n_unq=n_unq, use_cache=False)
+    ham, batch = gpu_objects(inst)
+    rp_all, _ = nqs.count_pairs(batch)
+    blocks = row_blocks(rp_all.cpu().numpy(), ws)
+    bounds = [b[0] for b in blocks] + [blocks[-1][1]]
+    whole = nqs.half_pairs(batch)
+    live = whole[0][:whole[3]].to(torch.int64) & 0xFFFFFFFF
+    n_whole = int((live != 0xFFFFFFFF).sum().item())
+    routed, n_parts_total = [], 0
+    for p in range(ws):
+        ri, rj, rk, ns = nqs.half_pairs(batch, part=p, n_parts=ws)
+        rec = tuple(t[:ns].clone() for t in (ri, rj, rk)) + (ns,)
+        n_parts_total += int(((rec[0].to(torch.int64) & 0xFFFFFFFF) != 0xFFFFFFFF).sum().item())
+        oi, oj, ok, counts = nqs.route_records(rec, bounds)
+        off = np.concatenate([[0], np.cumsum(counts)])
+        routed.append([(oi[off[d]:off[d + 1]], oj[off[d]:off[d + 1]], ok[off[d]:off[d + 1]]) for d in range(ws)])
+        batch.status()
+    assert n_parts_total == n_whole
+    for d, (r0, r1) in enumerate(blocks):
+        recv = [torch.cat([routed[p][d][c] for p in range(ws)]) for c in range(3)]
+        rp, pj, pk = nqs.pairs_from_records(batch, recv[0], recv[1], recv[2], r0, r1)
+        rp_d, pj_d, pk_d = nqs.coupled_pairs(batch, r0, r1)
+        assert torch.equal(rp, rp_d) and torch.equal(pj, pj_d) and torch.equal(pk, pk_d)
+    batch.status()

@@ -107,3 +107,52 @@ def test_gloo_two_ranks_exchange(h12_ref):
     for _, _, out in res:
         assert abs(out[0] - evar) < 1e-12
     assert res[0][2] == res[1][2]  # every rank holds the same triple
+
+
+def _owner(bounds, row):
+    return int(np.searchsorted(np.asarray(bounds), row, side="right") - 1)
+
+
+def _exchange_main(rank, ws, port, bounds, records, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    torch.distributed.init_process_group("gloo", rank=rank, world_size=ws)
+    from paper_2408_07625_gb300.sharding import exchange_records
+    m = len(records)
+    mine = records[rank * m // ws:(rank + 1) * m // ws]   # this rank's search slice
+    groups = [[] for _ in range(ws)]
+    for rec in mine:  # routed as nqs_route_records does: to the owner of each endpoint row, once per owner
+        owners = {_owner(bounds, rec[0]), _owner(bounds, rec[1])}
+        for d in sorted(owners):
+            groups[d].append(rec)
+    counts = [len(g) for g in groups]
+    flat = [r for g in groups for r in g]
+    send = tuple(torch.tensor([r[c] for r in flat], dtype=torch.int32) for c in range(3))
+    recv = exchange_records(send, counts)
+    q.put((rank, sorted(zip(*(t.tolist() for t in recv)))))
+    torch.distributed.destroy_process_group()
+
+
+def test_gloo_record_exchange():
+    """The all-to-all of the sharded search: every rank receives exactly the records
+    (from every rank's search slice) that name one of its rows, once."""
+    rng = np.random.default_rng(5)
+    n, m, ws = 60, 500, 2
+    i = rng.integers(0, n, m)
+    j = (i + rng.integers(1, n, m)) % n
+    records = [(int(a), int(b), int(k)) for a, b, k in zip(i, j, rng.integers(0, 1000, m))]
+    bounds = [0, 23, n]
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_exchange_main, args=(r, ws, port, bounds, records, q)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r in range(ws):
+        want = sorted(rec for rec in records if bounds[r] <= rec[0] < bounds[r + 1] or bounds[r] <= rec[1] < bounds[r + 1])
+        assert res[r] == want

@@ -198,10 +198,37 @@ __global__ void __launch_bounds__(1024) scan_tile_i32_kernel(int32_t* __restrict
   if (e0 + 1 < m) d[e0 + 1] = ex + v0;
 }
 
-__global__ void scan_tile_offsets_kernel(int32_t* __restrict__ tile_sum, int64_t tiles) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int32_t run = 0;
-  for (int64_t t = 0; t < tiles; ++t) {
+// exclusive scan of the tile totals, one block of 1024 threads: each thread sums a
+// contiguous run of tiles, the runs' totals are scanned across the block, each thread
+// writes its run's offsets
+__global__ void __launch_bounds__(1024) scan_tile_offsets_kernel(int32_t* __restrict__ tile_sum, int64_t tiles) {
+  __shared__ int32_t wsum[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t per = (tiles + 1023) / 1024;
+  const int64_t b = threadIdx.x * per, e = b + per < tiles ? b + per : tiles;
+  int32_t s = 0;
+  for (int64_t t = b; t < e; ++t) s += tile_sum[t];
+  int32_t incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += x;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int32_t w = wsum[lane];
+    int32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t x = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+      if (lane >= o) wi += x;
+    }
+    wsum[lane] = wi - w;
+  }
+  __syncthreads();
+  int32_t run = wsum[warp] + incl - s;
+  for (int64_t t = b; t < e; ++t) {
     const int32_t v = tile_sum[t];
     tile_sum[t] = run;
     run += v;
@@ -223,7 +250,7 @@ static void scan_i32(int32_t* d, int64_t m, int32_t* partial, cudaStream_t s) {
   }
   const int64_t tiles = (m + kScanTileI - 1) / kScanTileI;
   scan_tile_i32_kernel<<<(unsigned)tiles, 1024, 0, s>>>(d, m, partial);
-  scan_tile_offsets_kernel<<<1, 32, 0, s>>>(partial, tiles);
+  scan_tile_offsets_kernel<<<1, 1024, 0, s>>>(partial, tiles);
   scan_tile_add_kernel<<<(unsigned)tiles, 1024, 0, s>>>(d, m, partial);
 }
 

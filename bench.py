@@ -266,7 +266,9 @@ def bench_sr(nqs, torch, n_sr, n_params, steps, flush, peaks):
     torch.cuda.synchronize()
     t = float(np.mean([x.elapsed_time(y) for x, y in ms]))
     o_bytes = 4.0 * n_sr * n_params
-    mma_flops = 3 * 2.0 * 128 * 128 * n_params     # hi hi + hi lo + lo hi, M = N = 128 tiles
+    # streamed form (n_params a multiple of 4): one M = 128, N = 256 MMA per K step ([hi hi^T | hi lo^T]);
+    # otherwise three M = N = 128 MMAs (hi hi, hi lo, lo hi)
+    mma_flops = (2.0 * 128 * 256 if n_params % 4 == 0 else 3 * 2.0 * 128 * 128) * n_params
     useful_flops = 2.0 * n_sr * n_sr * n_params
     return {"workload": f"N_SR = {n_sr} samples, {n_params} parameters (FP32 d log psi / d theta)",
             "ms_per_step": t,

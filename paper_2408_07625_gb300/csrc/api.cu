@@ -117,7 +117,7 @@ static void free_ham(nqs_ham* h) {
   cudaFree(h->xy); cudaFree(h->row_ptr); cudaFree(h->yz); cudaFree(h->coef);
   cudaFree(h->coef_f); cudaFree(h->srch_hash); cudaFree(h->srch_id); cudaFree(h->srch_rec); cudaFree(h->hash_basis);
   cudaFree(h->xy_table); cudaFree(h->wmask); cudaFree(h->xy_trie); cudaFree(h->xy_hash); cudaFree(h->segs);
-  cudaFree(h->fm); cudaFree(h->fv_d); cudaFree(h->fv_f); cudaFree(h->fz); cudaFree(h->quad_d);
+  cudaFree(h->fm); cudaFree(h->fmx); cudaFree(h->fv_d); cudaFree(h->fv_f); cudaFree(h->fz); cudaFree(h->quad_d);
   cudaFree(h->quad_f); cudaFree(h->coef_im); cudaFree(h->coef_f_im); cudaFree(h->fv_d_im); cudaFree(h->fv_f_im);
   delete h;
 }
@@ -325,6 +325,15 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
     fv_im.clear();
     fz.clear();
   }
+  std::vector<int4> fmx;  // N <= 64: the descriptor and the local sign mask in one record
+  if (W == 1) {
+    fmx.resize(2 * (size_t)G);
+    for (int64_t p = 0; p < G; ++p) {
+      const uint64_t a = (fm[p].x & 15) == kForm::Local ? fz[(size_t)fm[p].z] : 0ull;
+      fmx[2 * p] = fm[p];
+      fmx[2 * p + 1] = make_int4((int)(uint32_t)a, (int)(uint32_t)(a >> 32), 0, 0);
+    }
+  }
   std::vector<double> quad_d;
   if (h->has_diag) {
     const int64_t t0 = h->h_row_ptr[0], t1 = h->h_row_ptr[1];
@@ -466,7 +475,7 @@ int nqs_ham_load(int n_qubits, int64_t n_terms, const uint64_t* x_mask, const ui
       (rc = upload(&h->srch_id, srch_id)) || (rc = upload(&h->srch_rec, srch_rec)) ||
       (rc = upload(&h->hash_basis, h->h_hash_basis)) || (rc = upload(&h->xy_table, xy_table)) ||
       (rc = upload(&h->wmask, wmask)) || (rc = upload(&h->xy_trie, xy_trie)) ||
-      (rc = upload(&h->xy_hash, hxy)) || (rc = upload(&h->segs, segs)) || (rc = upload(&h->fm, fm)) ||
+      (rc = upload(&h->xy_hash, hxy)) || (rc = upload(&h->segs, segs)) || (rc = upload(&h->fm, fm)) || (rc = upload(&h->fmx, fmx)) ||
       (rc = upload(&h->fv_d, fv)) || (rc = upload(&h->fv_f, fv_f)) || (rc = upload(&h->fz, fz)) ||
       (rc = upload(&h->quad_d, quad_d)) || (rc = upload(&h->quad_f, quad_f)) ||
       (rc = upload(&h->coef_im, h->h_coef_im)) || (rc = upload(&h->coef_f_im, coef_f_im)) ||
@@ -977,7 +986,7 @@ int nqs_local_energy_half(const nqs_ham* ham, const uint64_t* U, int64_t n, void
   if (n_slots < 0 || (n_slots > 0 && (!rec_i || !rec_j || !rec_k))) return fail(NQS_ERR_ARG, "null record arrays");
   if (n == 0) return NQS_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = launch_amplitudes(a, b, n, precision, (char*)work, L, s);
+  cudaError_t e = launch_amplitudes(a, b, n, precision, (char*)work, L, s, U);
   if (e != cudaSuccess) return cuda_fail(e, "amplitude kernel");
   e = launch_local_energy_half(ham, U, n, (const char*)work, L, b != nullptr, rec_i, rec_j, rec_k, n_slots, precision,
                                eloc_re, eloc_im, hdiag, hrec, s);
@@ -1004,7 +1013,7 @@ int nqs_local_energy_backward_half(const nqs_ham* ham, const uint64_t* U, int64_
   if (n == 0) return NQS_OK;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
-  if (pairs_needed && (e = launch_amplitudes(a, b, n, precision, (char*)work, L, s)) != cudaSuccess)
+  if (pairs_needed && (e = launch_amplitudes(a, b, n, precision, (char*)work, L, s, U)) != cudaSuccess)
     return cuda_fail(e, "amplitude kernel");
   e = launch_backward_half(ham, U, n, (char*)work, L, b != nullptr, a, rec_i, rec_j, rec_k, n_slots, hrec, eloc_re,
                            eloc_im, hdiag, evar, g_re, g_im, g_evar, precision, grad_re, grad_im, s);
@@ -1028,7 +1037,7 @@ int nqs_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n, void* wor
   if (re > rb && (!row_ptr || !pair_j || !pair_k)) return fail(NQS_ERR_ARG, "null pair arrays");
   if (re == rb) return NQS_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = launch_amplitudes(a, b, n, precision, (char*)work, L, s);
+  cudaError_t e = launch_amplitudes(a, b, n, precision, (char*)work, L, s, U);
   if (e != cudaSuccess) return cuda_fail(e, "amplitude kernel");
   e = launch_local_energy(ham, U, n, (char*)work, L, b != nullptr, rb, re, row_ptr, pair_j, pair_k,
                           precision, eloc_re, eloc_im, hdiag, hpair, s);
@@ -1093,7 +1102,7 @@ int nqs_local_energy_backward(const nqs_ham* ham, const uint64_t* U, int64_t n, 
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
   if (pairs_needed) {
-    e = launch_amplitudes(a, b, n, precision, (char*)work, L, s);
+    e = launch_amplitudes(a, b, n, precision, (char*)work, L, s, U);
     if (e != cudaSuccess) return cuda_fail(e, "amplitude kernel");
   }
   e = launch_backward(ham, U, n, (char*)work, L, b != nullptr, a, b, rb, re, row_ptr, pair_j, pair_k,

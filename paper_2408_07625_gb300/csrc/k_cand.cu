@@ -350,7 +350,7 @@ cudaError_t launch_local_energy_full(int64_t n, int64_t n_xy, const char* stage,
                                      double* er, double* ei, cudaStream_t s) {
   AmpD* P = (AmpD*)scratch;
   const int sms = num_sms();
-  cudaError_t e = launch_amplitudes(a, b, n, NQS_PREC_FP64, (char*)stage, L, s);
+  cudaError_t e = launch_amplitudes(a, b, n, NQS_PREC_FP64, (char*)stage, L, s, nullptr);
   if (e != cudaSuccess) return e;
   if (n_cand > 0)
     cand_amp_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((n_cand + 255) / 256, 8 * sms)), 256, 0, s>>>(

@@ -28,7 +28,8 @@ constexpr int kEnergyWarps = kEnergyThreads / 32;
 
 __global__ void amplitudes_kernel(const double* __restrict__ a, const double* __restrict__ b,
                                   int64_t n, int fp64, AmpF* __restrict__ Pf, AmpF* __restrict__ Qf,
-                                  AmpD* __restrict__ Pd, AmpD* __restrict__ Qd) {
+                                  AmpD* __restrict__ Pd, AmpD* __restrict__ Qd, const uint64_t* __restrict__ U,
+                                  int W) {
   const double kLn2 = 0.6931471805599453094;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -53,17 +54,18 @@ __global__ void amplitudes_kernel(const double* __restrict__ a, const double* __
       Qf[i].v = make_float4(dqr.hi, dqr.lo, dqi.hi, dqi.lo);
       Qf[i].k = ki;
     }
+    if (U) Pf[i].x0 = __ldg(U + i * W);  // same bytes in both layouts
   }
 }
 
 cudaError_t launch_amplitudes(const double* a, const double* b, int64_t n, int precision,
-                              char* stage, const StageHeader& L, cudaStream_t s) {
+                              char* stage, const StageHeader& L, cudaStream_t s, const uint64_t* U) {
   if (n == 0) return cudaSuccess;
   const int blocks = (int)std::min<int64_t>((n + 255) / 256, 8 * num_sms());
   const bool fp64 = precision == NQS_PREC_FP64;
   amplitudes_kernel<<<blocks, 256, 0, s>>>(
       a, b, n, fp64 ? 1 : 0, (AmpF*)(stage + L.off_ampP), (AmpF*)(stage + L.off_ampQ),
-      (AmpD*)(stage + L.off_ampP), (AmpD*)(stage + L.off_ampQ));
+      (AmpD*)(stage + L.off_ampP), (AmpD*)(stage + L.off_ampQ), U, L.W);
   return cudaGetLastError();
 }
 
@@ -246,7 +248,20 @@ __device__ __forceinline__ void energy_rounds(const uint64_t* __restrict__ U, co
       jn = __ldg(pair_j + q + 32 * stride);
       kn = __ldg(pair_k + q + 32 * stride);
     }
-    const int4 fm = have ? __ldg(M.fm + k) : make_int4(0, 0, 0, 0);
+    // N <= 64: the pattern's descriptor and sign mask are one 32-byte record, and the
+    // column's bit word rides in its amplitude record (read with the ratio's factor)
+    int4 fm = make_int4(0, 0, 0, 0);
+    uint64_t amask = 0ull;
+    if (W == 1) {
+      if (have) {
+        const int4* rec = M.fmx + 2 * (int64_t)k;
+        fm = __ldg(rec);
+        const int4 m2 = __ldg(rec + 1);
+        amask = (uint64_t)(uint32_t)m2.x | ((uint64_t)(uint32_t)m2.y << 32);
+      }
+    } else if (have) {
+      fm = __ldg(M.fm + k);
+    }
     const bool coop = have && (int64_t)k < M.heavy_end && (fm.x & 15) == kForm::Terms;
     T h = Pol::zero(), h_im = Pol::zero();
     uint32_t hb = __ballot_sync(kFull, coop);
@@ -270,8 +285,10 @@ __device__ __forceinline__ void energy_rounds(const uint64_t* __restrict__ U, co
     if (have) {
       if (!coop) {
         uint64_t xp[W];
-        load_words<W>(U + (int64_t)j * W, xp);
+        if (W == 1) xp[0] = __ldg(reinterpret_cast<const uint64_t*>(P + 32 * (int64_t)j) + 3);
+        else load_words<W>(U + (int64_t)j * W, xp);
         if (CX == kCplxH) melem_lane_c<Pol, W>(xp, k, fm, M, h, h_im);
+        else if (W == 1 && (fm.x & 15) == kForm::Local) h = melem_local1<Pol>(xp[0], fm, amask, M);
         else h = melem_lane<Pol, W>(xp, k, fm, M);
       }
       T rr, ri;
@@ -606,7 +623,7 @@ __global__ void geff_kernel(int64_t n, const double* __restrict__ a, const doubl
                             const double* __restrict__ g_evar, int fp64, double2* __restrict__ gd,
                             float4* __restrict__ gf, int64_t rb, int64_t re, const double* __restrict__ er,
                             const double* __restrict__ ei, const double* __restrict__ hdiag,
-                            double2* __restrict__ own) {
+                            double2* __restrict__ own, char* __restrict__ qrec) {
   const double gE = g_evar ? g_evar[0] : 0.0;
   const double E = evar[0], amax = evar[1], S = evar[2];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -616,9 +633,11 @@ __global__ void geff_kernel(int64_t n, const double* __restrict__ a, const doubl
     const double gi = g_im ? g_im[i] : 0.0;
     if (fp64) {
       gd[i] = make_double2(ge, gi);
+      if (qrec) *reinterpret_cast<double*>(qrec + 32 * i + 24) = ge;
     } else {
       df a1 = df_from_double(ge), a2 = df_from_double(gi);
       gf[i] = make_float4(a1.hi, a1.lo, a2.hi, a2.lo);
+      if (qrec) *reinterpret_cast<float2*>(qrec + 32 * i + 24) = make_float2(a1.hi, a1.lo);
     }
     if (i >= rb && i < re) {
       const double Dr = -(er[i] - hdiag[i]);
@@ -714,7 +733,8 @@ __device__ __forceinline__ void backward_rounds(const uint64_t* __restrict__ U, 
     if (have) {
       T rr, ri, ge, gi;
       ratio<Pol, CX != kReal>(P, Q, y, j, rr, ri, status);
-      load_geff<Pol>(G, j, ge, gi);
+      if (CX == kReal) ge = Pol::load_slot(Q, j);   // the adjoint weight rides in the record of 1/psi(j)
+      else load_geff<Pol>(G, j, ge, gi);
       if (CX == kCplxH) {
         // row y holds H_yj; the pair's term uses H_jy = conj(H_yj) (H Hermitian):
         // T = conj(h) psi(y)/psi(j) = (h rr + h_im ri) + i (h ri - h_im rr)
@@ -862,7 +882,7 @@ cudaError_t launch_backward(const nqs_ham* ham, const uint64_t* U, int64_t n, ch
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * num_sms()));
     geff_kernel<<<blocks, 256, 0, s>>>(n, a, evar, g_re, g_im, g_evar, fp64 ? 1 : 0,
                                        (double2*)(stage + L.off_geff), (float4*)(stage + L.off_geff), rb, re, er,
-                                       ei, hd, (double2*)(stage + L.off_own));
+                                       ei, hd, (double2*)(stage + L.off_own), stage + L.off_ampQ);
   }
   RowSched rs;
   cudaError_t e = launch_row_order(rp, rows, stage, L, rs, s);
@@ -1155,7 +1175,8 @@ cudaError_t launch_backward_half(const nqs_ham* ham, const uint64_t* U, int64_t 
   }
   const bool fp64 = precision == NQS_PREC_FP64;
   geff_kernel<<<blocks, 256, 0, s>>>(n, a, evar, g_re, g_im, g_evar, fp64 ? 1 : 0, (double2*)(stage + L.off_geff),
-                                     (float4*)(stage + L.off_geff), 0, n, er, ei, hd, (double2*)(stage + L.off_own));
+                                     (float4*)(stage + L.off_geff), 0, n, er, ei, hd, (double2*)(stage + L.off_own),
+                                     nullptr);
   half_grad_init_kernel<<<blocks, 256, 0, s>>>(n, (const double2*)(stage + L.off_own), gre, gim);
   const int cx = ham->cplx ? kCplxH : (cplx ? kCplxPsi : kReal);
 #define NQS_HALF_BW_P(POL)                                                                                        \

@@ -151,6 +151,11 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kSrRows >> 3) << 17) |
                                 ((uint32_t)(kSrRows >> 4) << 24);
 
+// the same with N = 256: B = the hi tile followed by the lo tile (rows 128 .. 255), so one
+// MMA gives [hi hi^T | hi lo^T] (lo hi^T is the transpose of the second half)
+constexpr uint32_t kIdescBf16N256 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(256 >> 3) << 17) |
+                                    ((uint32_t)(kSrRows >> 4) << 24);
+
 // byte offset of (row r, k) inside a 128 x 64 tile: core matrix (r / 8, k / 8)
 // at (r / 8) * 1024 + (k / 8) * 128, then row r % 8 at 16 B and k % 8 at 2 B
 __device__ __forceinline__ uint32_t tile_off(int r, int k) {
@@ -283,7 +288,9 @@ __global__ void __launch_bounds__(kSrThreads) gram_kernel(int n, int64_t P, cons
 // into one of kBulkStages stages (completion counted in bytes on the stage's
 // mbarrier); kBulkConverters warps centre, scale and split a stage into the
 // bf16 hi / lo operand tiles (two operand stages) and release the FP32 stage;
-// one thread of the MMA warp issues the tile's twelve MMAs and commits them to
+// one thread of the MMA warp issues the tile's four MMAs (M = 128, N = 256: A = hi,
+// B = hi followed by lo, giving [hi hi^T | hi lo^T] in 256 TMEM columns; lo hi^T is
+// the transpose of the second half, added when the partials are summed) and commits them to
 // the operand stage's mbarrier, which releases it to the converters.  Every
 // wait is bounded; a wait that runs out stops the CTA's loop and flags the error.
 // ---------------------------------------------------------------------------
@@ -334,7 +341,7 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
     for (int i = tid; i < 2 * 2 * kSrTileBytes / 16; i += blockDim.x) op[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   if (warp == 0) {
-    tmem_alloc(&s_taddr, kSrRows);
+    tmem_alloc(&s_taddr, 2 * kSrRows);
     tmem_relinquish();
   }
   fence_async_smem();
@@ -371,15 +378,12 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
       if (*(volatile int*)&s_fail) break;
       if (lane == 0) {
         tc_fence_after();
-        const uint32_t sh = smem_u32(base + kBulkOpOff + s2 * 2 * kSrTileBytes), sl = sh + kSrTileBytes;
+        const uint32_t sh = smem_u32(base + kBulkOpOff + s2 * 2 * kSrTileBytes);
 #pragma unroll
         for (int j = 0; j < kSrKTile / 16; ++j) {
           const uint32_t adv = (uint32_t)j * 2 * kSrLbo;
-          const uint64_t dh = umma_desc(sh + adv, kSrLbo, kSrSbo);
-          const uint64_t dl = umma_desc(sl + adv, kSrLbo, kSrSbo);
-          mma_bf16(taddr, dh, dh, kIdescBf16, (it > 0 || j > 0) ? 1u : 0u);
-          mma_bf16(taddr, dh, dl, kIdescBf16, 1u);
-          mma_bf16(taddr, dl, dh, kIdescBf16, 1u);
+          const uint64_t dh = umma_desc(sh + adv, kSrLbo, kSrSbo);   // A: hi; B: hi then lo (256 rows)
+          mma_bf16(taddr, dh, dh, kIdescBf16N256, (it > 0 || j > 0) ? 1u : 0u);
         }
         mma_commit(&opempty[s2]);
       }
@@ -456,23 +460,23 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
   tc_fence_after();
   if (warp < 4) {
     const int row = warp * 32 + lane;
-    float* out = partial + (int64_t)blockIdx.x * kSrRows * kSrRows + (int64_t)row * kSrRows;
+    float* out = partial + ((int64_t)blockIdx.x * kSrRows + row) * (2 * kSrRows);   // [hi hi^T | hi lo^T] row
     if (done && nt > 0) {
-#pragma unroll
-      for (int c = 0; c < kSrRows; c += 32) {
+#pragma unroll 1
+      for (int c = 0; c < 2 * kSrRows; c += 32) {
         float v[32];
         tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
 #pragma unroll
         for (int i = 0; i < 32; ++i) out[c + i] = v[i];
       }
     } else {
-      for (int c = 0; c < kSrRows; ++c) out[c] = 0.f;
+      for (int c = 0; c < 2 * kSrRows; ++c) out[c] = 0.f;
     }
   }
   if (!done && nt > 0 && tid == 0) atomicOr(error, kStatusLimit);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(taddr, kSrRows);
+  if (warp == 0) tmem_dealloc(taddr, 2 * kSrRows);
 }
 
 // The tensor map of O [n rows][P columns] FP32 (row stride 4 P bytes) with 128 x 32 boxes,
@@ -596,6 +600,21 @@ __global__ void sr_mean4_kernel(int n, int64_t P, const float* __restrict__ O, c
     }
     reinterpret_cast<float4*>(m)[q] = make_float4(s[0] + c[0], s[1] + c[1], s[2] + c[2], s[3] + c[3]);
   }
+}
+
+// G = sum of the streamed kernel's partials [hi hi^T | hi lo^T] in CTA order (FP64): entry
+// (r, c) adds D1[r][c] + D2[r][c] + D2[c][r] (lo hi^T = (hi lo^T)^T)
+__global__ void sr_gram_sum2_kernel(int n, int n_part, const float* __restrict__ partial, double* __restrict__ G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * n) return;
+  const int r = i / n, c = i % n;
+  double s = 0.0;
+  for (int q = 0; q < n_part; ++q) {
+    const float* d = partial + (int64_t)q * kSrRows * 2 * kSrRows;
+    s += (double)__ldg(d + r * 2 * kSrRows + c);
+    s += (double)__ldg(d + r * 2 * kSrRows + kSrRows + c) + (double)__ldg(d + c * 2 * kSrRows + kSrRows + r);
+  }
+  G[i] = s;
 }
 
 // G = sum of the CTAs' partials in CTA order (FP64), one thread per entry of the n x n block
@@ -883,7 +902,10 @@ cudaError_t launch_sr_step(int n, int64_t P, const float* O, const double* a, co
   if ((e = cudaFuncSetAttribute(sr_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem)) !=
       cudaSuccess)
     return e;
-  sr_gram_sum_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, n_part, sc.partial, sc.G);
+  if (tiled)
+    sr_gram_sum2_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, n_part, sc.partial, sc.G);
+  else
+    sr_gram_sum_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, n_part, sc.partial, sc.G);
   sr_solve_kernel<<<1, kSolveThreads, solve_smem, s>>>(n, sc.G, sc.w, eloc, evar, lambda, T, sc.y, sc.error);
   if (streamed)
     sr_step4_kernel<<<stream_grid, 256, 0, s>>>(n, P, O, sc.m, sc.sw, sc.y, delta);

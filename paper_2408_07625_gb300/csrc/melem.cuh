@@ -13,16 +13,22 @@ namespace nqs {
 // A factor (P or Q, FP32 compensated or FP64, real and imaginary parts) with
 // the sample's power-of-two exponent K in one 32-byte record (one L2
 // sector): a pair's gather of P_j and K_j, or Q_j and K_j, is one request.
+// Per-sample amplitude record (one 32-byte L2 sector): the factor, its power-of-two
+// exponent, and the sample's first bit word (read with the factor by the energy
+// kernel when N <= 64, so a pair's column costs one gather)
 struct __align__(32) AmpF {
   float4 v;
   int k;
-  int pad[3];
+  int pad;
+  uint64_t x0;
 };
 struct __align__(32) AmpD {
   double2 v;
   int k;
-  int pad[3];
+  int pad;
+  uint64_t x0;
 };
+static_assert(sizeof(AmpF) == 32 && sizeof(AmpD) == 32, "one sector per amplitude record");
 
 // --------------------------------------------------------------------------
 // arithmetic policies: FP32 compensated (double-float) and FP64
@@ -51,6 +57,11 @@ struct PolicyF {
     const float4 v = __ldg(reinterpret_cast<const float4*>(G) + i);
     re = {v.x, v.y};
     im = {v.z, v.w};
+  }
+  // the record's last 8 bytes as a value (the real adjoint weight in the records of 1/psi)
+  __device__ static T load_slot(const char* R, int64_t i) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(R + 32 * i + 24));
+    return {v.x, v.y};
   }
   __device__ static void load_amp(const char* P, int64_t i, T& re, T& im, int& k) {
     const AmpF* r = reinterpret_cast<const AmpF*>(P) + i;
@@ -82,6 +93,9 @@ struct PolicyD {
     const double2 v = __ldg(reinterpret_cast<const double2*>(G) + i);
     re = v.x;
     im = v.y;
+  }
+  __device__ static T load_slot(const char* R, int64_t i) {
+    return __ldg(reinterpret_cast<const double*>(R + 32 * i + 24));
   }
   __device__ static void load_amp(const char* P, int64_t i, T& re, T& im, int& k) {
     const AmpD* r = reinterpret_cast<const AmpD*>(P) + i;
@@ -126,6 +140,7 @@ struct Melem {
   int has_diag;
   int64_t heavy_end;
   const int4* fm;          // per pattern: {kind | nb << 4, table offset, mask offset, packed qubits}
+  const int4* fmx;         // N <= 64: per pattern {fm, sign mask A (low, high)}, 32 bytes
   const float2* fv_f;
   const double* fv_d;
   const uint64_t* fz;
@@ -142,7 +157,7 @@ struct Melem {
 };
 
 inline Melem melem_tables(const nqs_ham* h, int64_t n_unq) {
-  return Melem{h->row_ptr, h->yz, h->coef_f, h->coef, h->has_diag, h->heavy_end, h->fm,
+  return Melem{h->row_ptr, h->yz, h->coef_f, h->coef, h->has_diag, h->heavy_end, h->fm, h->fmx,
                h->fv_f, h->fv_d, h->fz, h->diag_quad, h->quad_f, h->quad_d, h->n_xy, n_unq,
                h->coef_f_im, h->coef_im, h->fv_f_im, h->fv_d_im};
 }
@@ -160,6 +175,18 @@ __device__ __forceinline__ bool pair_in_range(const Melem& M, uint32_t j, uint32
 // terms t0 + t, t0 + t + 32, ... in order, four loads in flight at a time;
 // every lane runs the same number of steps (terms past t1 add nothing).
 // Every lane returns the same value.
+// N <= 64, local form with its sign mask at hand (from the pattern's 32-byte record)
+template <class Pol>
+__device__ __forceinline__ typename Pol::T melem_local1(uint64_t xp, int4 fm, uint64_t amask, const Melem& M) {
+  const int nb = fm.x >> 4;
+  uint32_t u = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (i < nb) u |= (uint32_t)((xp >> ((fm.w >> (8 * i)) & 255)) & 1ull) << i;
+  const typename Pol::T h = Pol::val(M.fv_f, M.fv_d, (int64_t)fm.y + u);
+  return (__popcll(xp & amask) & 1) ? Pol::neg(h) : h;
+}
+
 template <class Pol, int W>
 __device__ __forceinline__ typename Pol::T melem_warp(const uint64_t (&xp)[W], int64_t t0, int64_t t1,
                                                        const Melem& M);

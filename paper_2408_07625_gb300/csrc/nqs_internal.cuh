@@ -80,6 +80,8 @@ struct nqs_ham_dev {
   //   H_xx = C + sum_{r in x} b_r + sum_{r < s in x} B_rs, stored as
   //   [C, b_0 .. b_{64W-1}, B (64W x 64W, row-major, r < s used)].
   int4* fm = nullptr;            // [n_xy]
+  int4* fmx = nullptr;           // N <= 64: [n_xy][2] one 32-byte record per pattern: fm, then the
+                                 //   local form's sign mask A (low, high 32 bits) -- one gather per pair
   double* fv_d = nullptr;        // value pool
   float2* fv_f = nullptr;        // same, (hi, lo) split
   uint64_t* fz = nullptr;        // mask pool [..][W]
@@ -244,8 +246,9 @@ cudaError_t search_time(double* total_ms, int64_t* launches);
 // probe's ALU mix, out[1] probes/s of the filter loop alone
 cudaError_t probe_peaks(double* out, cudaStream_t s);
 
+// per-sample amplitude records P (factor and exponent, and U's first word when U is given) and Q
 cudaError_t launch_amplitudes(const double* a, const double* b, int64_t n, int precision,
-                              char* stage, const StageHeader& L, cudaStream_t s);
+                              char* stage, const StageHeader& L, cudaStream_t s, const uint64_t* U);
 
 cudaError_t launch_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
                                 const char* stage, const StageHeader& L, bool cplx,

@@ -104,7 +104,7 @@ static cudaError_t enqueue_instance(PlanInstance& I, int precision, const double
     if ((e = launch_pairs_compact(ham, sc, w, I.L, 0, n, I.row_ptr, I.pair_j, I.pair_k, I.capacity, s)))
       return e;
   }
-  if ((e = launch_amplitudes(I.in.logpsi_re, nullptr, n, precision, w, I.L, s)) != cudaSuccess) return e;
+  if ((e = launch_amplitudes(I.in.logpsi_re, nullptr, n, precision, w, I.L, s, I.in.U)) != cudaSuccess) return e;
   if ((e = launch_local_energy(ham, I.in.U, n, w, I.L, false, 0, n, I.row_ptr, I.pair_j, I.pair_k, precision,
                                I.in.eloc_re, nullptr, I.hdiag, nullptr, s)) != cudaSuccess)
     return e;

@@ -602,19 +602,22 @@ __global__ void sr_mean4_kernel(int n, int64_t P, const float* __restrict__ O, c
   }
 }
 
-// G = sum of the streamed kernel's partials [hi hi^T | hi lo^T] in CTA order (FP64): entry
-// (r, c) adds D1[r][c] + D2[r][c] + D2[c][r] (lo hi^T = (hi lo^T)^T)
-__global__ void sr_gram_sum2_kernel(int n, int n_part, const float* __restrict__ partial, double* __restrict__ G) {
+// The streamed kernel's partials [hi hi^T | hi lo^T] (128 x 256 each): S = their sum in CTA
+// order (FP64), one thread per element, coalesced; then G(r, c) = S(r, c) + S(r, 128 + c) +
+// S(c, 128 + r)  (lo hi^T = (hi lo^T)^T)
+__global__ void sr_gram_sum2_kernel(int n_part, const float* __restrict__ partial, double* __restrict__ S) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kSrRows * 2 * kSrRows) return;
+  double s = 0.0;
+  for (int q = 0; q < n_part; ++q) s += (double)__ldg(partial + (int64_t)q * kSrRows * 2 * kSrRows + i);
+  S[i] = s;
+}
+
+__global__ void sr_gram_fold_kernel(int n, const double* __restrict__ S, double* __restrict__ G) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * n) return;
   const int r = i / n, c = i % n;
-  double s = 0.0;
-  for (int q = 0; q < n_part; ++q) {
-    const float* d = partial + (int64_t)q * kSrRows * 2 * kSrRows;
-    s += (double)__ldg(d + r * 2 * kSrRows + c);
-    s += (double)__ldg(d + r * 2 * kSrRows + kSrRows + c) + (double)__ldg(d + c * 2 * kSrRows + kSrRows + r);
-  }
-  G[i] = s;
+  G[i] = S[r * 2 * kSrRows + c] + (S[r * 2 * kSrRows + kSrRows + c] + S[c * 2 * kSrRows + kSrRows + r]);
 }
 
 // G = sum of the CTAs' partials in CTA order (FP64), one thread per entry of the n x n block
@@ -666,31 +669,47 @@ __device__ __forceinline__ df df_recip(df d) {
   return fast_two_sum(r0, __fmul_rn(r0, e));
 }
 
-__global__ void __launch_bounds__(kSolveThreads) sr_solve_kernel(int n, const double* __restrict__ G,
-                                                                  const double* __restrict__ w,
-                                                                  const double* __restrict__ eloc,
-                                                                  const double* __restrict__ evar, double lambda,
-                                                                  double* __restrict__ T, double* __restrict__ y,
+// The system, assembled over many blocks: T = (G + G^T) / 2 (written out when asked),
+// A = T + lambda I + c u u^T with c = tr T / n (each thread sums the diagonal itself), and
+// eps, both split into double-float pairs for the solve
+__global__ void sr_assemble_kernel(int n, const double* __restrict__ G, const double* __restrict__ w,
+                                   const double* __restrict__ eloc, const double* __restrict__ evar,
+                                   double lambda, double* __restrict__ T, float2* __restrict__ A,
+                                   float2* __restrict__ b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * n) return;
+  const int r = i / n, c = i % n;
+  double tr = 0.0;
+  for (int k = 0; k < n; ++k) tr += __ldg(G + k * n + k);
+  const double v = 0.5 * (G[i] + G[c * n + r]);
+  if (T) T[i] = v;
+  const df a = df_from_double(v + (r == c ? lambda : 0.0) + (tr / n) * sqrt(w[r] * w[c]));
+  A[i] = make_float2(a.hi, a.lo);
+  if (c == 0) {
+    const df e = df_from_double(sqrt(w[r]) * (eloc[r] - evar[0]));
+    b[r] = make_float2(e.hi, e.lo);
+  }
+}
+
+__global__ void __launch_bounds__(kSolveThreads) sr_solve_kernel(int n, const float2* __restrict__ Ag,
+                                                                  const float2* __restrict__ bg,
+                                                                  double* __restrict__ y,
                                                                   int32_t* __restrict__ error) {
-  extern __shared__ df A[];   // [n][n], then b[n] and the pivots' reciprocals [n]
+  extern __shared__ df A[];   // [n][n], then b[n], the pivots' reciprocals [n], the triangle table
   df* b = A + n * n;
   df* rinv = b + n;
-  __shared__ double defl, su[kSrRows];
+  uint16_t* tri_rc = reinterpret_cast<uint16_t*>(rinv + n);   // e -> (r, c), e = r (r + 1) / 2 + c
   const int t = threadIdx.x;
-  if (t < n) su[t] = sqrt(w[t]);
-  if (t == 0) {
-    double tr = 0.0;
-    for (int i = 0; i < n; ++i) tr += G[i * n + i];
-    defl = tr / n;
-  }
-  __syncthreads();
   for (int i = t; i < n * n; i += blockDim.x) {
-    const int r = i / n, c = i % n;
-    const double v = 0.5 * (G[i] + G[c * n + r]);
-    if (T) T[i] = v;
-    A[i] = df_from_double(v + (r == c ? lambda : 0.0) + defl * su[r] * su[c]);
+    const float2 v = __ldg(Ag + i);
+    A[i] = df{v.x, v.y};
   }
-  if (t < n) b[t] = df_from_double(su[t] * (eloc[t] - evar[0]));
+  if (t < n) {
+    const float2 v = __ldg(bg + t);
+    b[t] = df{v.x, v.y};
+  }
+  for (int r = t; r < n; r += blockDim.x)
+    for (int c = 0; c <= r; ++c) tri_rc[r * (r + 1) / 2 + c] = (uint16_t)(r | (c << 8));
   __syncthreads();
   // A = L D L^T, right-looking: column j is kept unscaled (l_ij = A_ij / d_j is formed where it
   // is used), the trailing lower triangle and the right-hand side lose column j's
@@ -711,10 +730,8 @@ __global__ void __launch_bounds__(kSolveThreads) sr_solve_kernel(int n, const do
         b[ii] = df_sub_prod(b[ii], A[ii * n + j], df_mul(b[j], inv));
         continue;
       }
-      int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);  // e = r (r + 1) / 2 + c, 0 <= c <= r
-      while (r * (r + 1) / 2 > e) --r;
-      while ((r + 1) * (r + 2) / 2 <= e) ++r;
-      const int ii = j + 1 + r, kk = j + 1 + (e - r * (r + 1) / 2);
+      const uint32_t rc = tri_rc[e];
+      const int ii = j + 1 + (int)(rc & 255u), kk = j + 1 + (int)(rc >> 8);
       A[ii * n + kk] = df_sub_prod(A[ii * n + kk], A[ii * n + j], df_mul(A[kk * n + j], inv));
     }
     __syncthreads();
@@ -835,6 +852,9 @@ struct SrScratch {
   float* m;
   float* partial;
   double* G;
+  double* S;        // [128][256] sums of the streamed kernel's partials
+  float2* Adf;      // [n][n] the assembled system, double-float
+  float2* bdf;      // [n]
   double* y;
   int32_t* error;
   int64_t n_part;
@@ -852,6 +872,9 @@ static SrScratch sr_scratch_view(char* base, int64_t P, int n_part) {
   v.wf = (float*)take(4 * kSrRows);
   v.y = (double*)take(8 * kSrRows);
   v.G = (double*)take(8 * kSrRows * kSrRows);
+  v.S = (double*)take(8 * kSrRows * 2 * kSrRows);
+  v.Adf = (float2*)take(8 * kSrRows * kSrRows);
+  v.bdf = (float2*)take(8 * kSrRows);
   v.m = (float*)take(4 * std::max<int64_t>(P, 1) + 16);
   v.partial = (float*)take(4 * (int64_t)n_part * kSrRows * kSrRows);
   v.n_part = n_part;
@@ -898,15 +921,17 @@ cudaError_t launch_sr_step(int n, int64_t P, const float* O, const double* a, co
     gram_kernel<<<n_part, kSrThreads, kSrSmem, s>>>(n, P, O, sc.m, sc.sw, per, sc.partial, sc.error);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const size_t solve_smem = sizeof(df) * (size_t)(n * n + 2 * n);
+  const size_t solve_smem = sizeof(df) * (size_t)(n * n + 2 * n) + sizeof(uint16_t) * (size_t)(n * (n + 1) / 2);
   if ((e = cudaFuncSetAttribute(sr_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem)) !=
       cudaSuccess)
     return e;
-  if (tiled)
-    sr_gram_sum2_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, n_part, sc.partial, sc.G);
-  else
+  if (tiled) {
+    sr_gram_sum2_kernel<<<kSrRows * 2 * kSrRows / 256, 256, 0, s>>>(n_part, sc.partial, sc.S);
+    sr_gram_fold_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, sc.S, sc.G);
+  } else
     sr_gram_sum_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, n_part, sc.partial, sc.G);
-  sr_solve_kernel<<<1, kSolveThreads, solve_smem, s>>>(n, sc.G, sc.w, eloc, evar, lambda, T, sc.y, sc.error);
+  sr_assemble_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, sc.G, sc.w, eloc, evar, lambda, T, sc.Adf, sc.bdf);
+  sr_solve_kernel<<<1, kSolveThreads, solve_smem, s>>>(n, sc.Adf, sc.bdf, sc.y, sc.error);
   if (streamed)
     sr_step4_kernel<<<stream_grid, 256, 0, s>>>(n, P, O, sc.m, sc.sw, sc.y, delta);
   else

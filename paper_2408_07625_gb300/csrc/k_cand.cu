@@ -24,6 +24,7 @@
 // The candidate order (numeric) and every entry's index are independent of
 // thread timing.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "device_util.cuh"
@@ -275,24 +276,73 @@ cudaError_t launch_full_candidates(const nqs_ham* ham, const uint64_t* U, int64_
 
 // --------------------------------------------------------------------------
 // E_loc(x) = sum_k H_{x, x_k} psi(x_k) / psi(x) over the candidates x_k.
-// psi(x_k) = P_c 2^{K_c} per candidate (FP64 mantissa in [1, 2) and exponent,
-// one exp per candidate), 1/psi(x) = Q_x 2^{-K_x} per sample from the batch
+// psi(x_k) = P_c 2^{K_c} per candidate (FP64 mantissa in [1, 2.03) and exponent,
+// one exponential per candidate), 1/psi(x) = Q_x 2^{-K_x} per sample from the batch
 // workspace's amplitude records; per entry a complex product and an exact
 // power-of-two scaling (a contribution below the FP64 range is zero).  One
 // warp per sample, lanes over the patterns, fixed summation order.
 // --------------------------------------------------------------------------
+// e^a = 2^k m for one candidate per thread, mostly on the FP32 pipes (the candidates are
+// many and this part's FP64 rate is low): table-driven reduction a = (64 k + j) ln2 / 64 + r,
+// 0 <= r < ln2 / 64, so e^a = 2^k 2^(j/64) e^r; 2^(j/64) from a double-float table, e^r by
+// its Taylor series (1 + r + r^2/2 in double-float, the terms of degree 3..6, below
+// 2.2e-7 in all, in FP32), the product in double-float; about 1e-14 relative.  The
+// reduction follows the published table-driven scheme (Tang) with 64 entries.
+struct Exp2Table {
+  float2 t[64];   // 2^(j/64) as (hi, lo)
+};
+
+__device__ __forceinline__ double exp_mantissa(double a, const Exp2Table& T, int& k) {
+  const double kInvStep = 92.332482616893656877;            // 64 / ln 2
+  const double kStep = 0.6931471805599453094 / 64.0;         // ln 2 / 64 (double; the division is exact)
+  const double kStepHi = (double)0.010830424f;               // its leading 24 bits: K kStepHi is exact
+  const double kStepLo = kStep - kStepHi;
+  double K = floor(a * kInvStep);
+  K = fmin(fmax(K, -1.0e11), 1.0e11);
+  const double rd = fma(-K, kStepLo, fma(-K, kStepHi, a));   // in [0, ln 2 / 64) up to rounding
+  const long long Ki = (long long)K;
+  const int j = (int)(Ki & 63);
+  k = (int)((Ki - j) >> 6);
+  const float rh = __double2float_rn(rd);
+  const df r = {rh, __double2float_rn(rd - (double)rh)};
+  // e^r = 1 + r + r^2 / 2 + q with q = r^3 / 6 + r^4 / 24 + r^5 / 120 + r^6 / 720 (< 2.2e-7)
+  float q = __fmaf_rn(rh, 1.f / 720.f, 1.f / 120.f);
+  q = __fmaf_rn(q, rh, 1.f / 24.f);
+  q = __fmaf_rn(q, rh, 1.f / 6.f);
+  q = __fmul_rn(__fmul_rn(q, rh), __fmul_rn(rh, rh));
+  const df r2 = df_mul(r, r);
+  df e = df_add(r, df{0.5f * r2.hi, 0.5f * r2.lo});
+  e = df_add(e, df{q, 0.f});
+  e = df_add(df{1.f, 0.f}, e);
+  const float2 t = T.t[j];
+  const df m = df_mul(df{t.x, t.y}, e);
+  return (double)m.hi + (double)m.lo;
+}
+
 __global__ void cand_amp_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
-                                AmpD* __restrict__ P) {
-  const double kLn2 = 0.6931471805599453094;
+                                AmpD* __restrict__ P, const Exp2Table T) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double ai = a[i];
-    const double k = floor(ai / kLn2);
-    const double m = exp(ai - k * kLn2);
-    double c = 1.0, s = 0.0;
-    if (b) sincos(b[i], &s, &c);
-    P[i].v = make_double2(m * c, m * s);
-    P[i].k = (int)fmax(fmin(k, 2.0e9), -2.0e9);
+    int k;
+    const double m = exp_mantissa(a[i], T, k);
+    if (b) {
+      double c, s;
+      sincos(b[i], &s, &c);
+      P[i].v = make_double2(m * c, m * s);
+    } else {
+      P[i].v = make_double2(m, 0.0);
+    }
+    P[i].k = k;
   }
+}
+
+static Exp2Table exp2_table() {
+  Exp2Table T;
+  for (int j = 0; j < 64; ++j) {
+    const double v = std::exp2(j / 64.0);
+    const float hi = (float)v;
+    T.t[j] = make_float2(hi, (float)(v - (double)hi));
+  }
+  return T;
 }
 
 // one block per sample: thread t takes entries t, t + 256, ...; the warps'
@@ -354,7 +404,7 @@ cudaError_t launch_local_energy_full(int64_t n, int64_t n_xy, const char* stage,
   if (e != cudaSuccess) return e;
   if (n_cand > 0)
     cand_amp_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((n_cand + 255) / 256, 8 * sms)), 256, 0, s>>>(
-        n_cand, ca, cb, P);
+        n_cand, ca, cb, P, exp2_table());
   const int rb = (int)std::max<int64_t>(1, std::min<int64_t>(n, 16 * sms));
   const AmpD* Q = (const AmpD*)(stage + L.off_ampQ);
   int32_t* status = (int32_t*)(stage + offsetof(StageHeader, status));

@@ -805,7 +805,8 @@ def full_candidates(batch: Batch, with_h=True, stream=None):
     cand_id = torch.empty((batch.n, n_xy), dtype=torch.int32, device=dev)
     hval = torch.empty((batch.n, n_xy), dtype=torch.float64, device=dev) if with_h else None
     n = ctypes.c_int64()
-    cap = max(batch.n * n_xy // 4, 1024)
+    # the candidate count of the last call on this batch (a retry reruns the whole pipeline)
+    cap = getattr(batch, "_cand_cap", None) or max(batch.n * n_xy // 4, 1024)
     for _ in range(2):
         cand = torch.empty((cap, ham.n_words), dtype=torch.int64, device=dev)
         in_u = torch.empty(cap, dtype=torch.int32, device=dev)
@@ -814,6 +815,7 @@ def full_candidates(batch: Batch, with_h=True, stream=None):
                                      ctypes.byref(n), _stream(stream))
         if rc == -4 and n.value > cap:
             cap = int(n.value)
+            batch._cand_cap = cap
             continue
         _check(rc)
         break

@@ -912,8 +912,8 @@ __device__ __forceinline__ void warp_exclusive_scan_u32(uint32_t* v, int n) {
 // the column between the row's smallest and largest; a pass counts the
 // buckets, a scan turns the counts into starts, a second pass places each
 // key at its bucket's next slot (shared atomics), and each lane then
-// insertion-sorts its buckets.  Keys are re-read from memory in each pass
-// (the row is in L1), so nothing per key is held in registers.  Returns
+// insertion-sorts its buckets.  The row's keys are read once, each lane
+// holding 16 of them in registers (all loads in flight together).  Returns
 // false, writing nothing, when the largest bucket holds more than kBucketMax
 // keys (clustered columns): the row then goes to the block sort.
 constexpr int kBucketMax = 16;
@@ -936,11 +936,22 @@ __device__ __forceinline__ uint32_t pair_col(const uint64_t* keys, const uint32_
 __device__ __forceinline__ bool warp_sort_row(int64_t a, int n, const uint64_t* keys, uint32_t* pj, uint32_t* pk,
                                               uint32_t* cnt, uint64_t* buf, int32_t* status) {
   const int lane = threadIdx.x & 31;
+  // the row's keys, read once: lane holds positions lane, lane + 32, ... (16 loads in flight)
+  constexpr int kPer = kSortWarpMax / 32;
+  uint64_t kv[kPer];
   uint32_t cmin = 0xFFFFFFFFu, cmax = 0u;
-  for (int e = lane; e < n; e += 32) {
-    const uint32_t c = pair_col(keys, pj, a + e);
-    cmin = min(cmin, c);
-    cmax = max(cmax, c);
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int e = lane + 32 * q;
+    kv[q] = e < n ? pair_key(keys, pj, pk, a + e) : 0ull;
+  }
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    if (lane + 32 * q < n) {
+      const uint32_t c = (uint32_t)(kv[q] >> 32);
+      cmin = min(cmin, c);
+      cmax = max(cmax, c);
+    }
   }
   cmin = __reduce_min_sync(kFull, cmin);
   cmax = __reduce_max_sync(kFull, cmax);
@@ -950,12 +961,15 @@ __device__ __forceinline__ bool warp_sort_row(int64_t a, int n, const uint64_t* 
   for (int b = lane; b < B; b += 32) cnt[b] = 0u;
   __syncwarp();
   // bucket indices below B and places below n hold by construction; a
-  // violation (keys changed under the sort) is flagged and skipped
+  // violation is flagged and skipped
   bool bad = false;
-  for (int e = lane; e < n; e += 32) {
-    const uint32_t bk = bucket_of(pair_col(keys, pj, a + e), cmin, m);
-    if (bk < (uint32_t)B) atomicAdd(&cnt[bk], 1u);
-    else bad = true;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    if (lane + 32 * q < n) {
+      const uint32_t bk = bucket_of((uint32_t)(kv[q] >> 32), cmin, m);
+      if (bk < (uint32_t)B) atomicAdd(&cnt[bk], 1u);
+      else bad = true;
+    }
   }
   __syncwarp();
   uint32_t big = 0u;
@@ -963,12 +977,14 @@ __device__ __forceinline__ bool warp_sort_row(int64_t a, int n, const uint64_t* 
   if (__reduce_max_sync(kFull, big) > kBucketMax) return false;
   warp_exclusive_scan_u32(cnt, B);
   __syncwarp();
-  for (int e = lane; e < n; e += 32) {
-    const uint64_t key = pair_key(keys, pj, pk, a + e);
-    const uint32_t bk = bucket_of((uint32_t)(key >> 32), cmin, m);
-    const uint32_t o = bk < (uint32_t)B ? atomicAdd(&cnt[bk], 1u) : (uint32_t)n;
-    if (o < (uint32_t)n) buf[o] = key;
-    else bad = true;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    if (lane + 32 * q < n) {
+      const uint32_t bk = bucket_of((uint32_t)(kv[q] >> 32), cmin, m);
+      const uint32_t o = bk < (uint32_t)B ? atomicAdd(&cnt[bk], 1u) : (uint32_t)n;
+      if (o < (uint32_t)n) buf[o] = kv[q];
+      else bad = true;
+    }
   }
   if (bad) atomicOr(status, kStatusLimit);
   __syncwarp();
@@ -998,7 +1014,7 @@ constexpr int kSortWarpWarps = kSortWarpThreads / 32;
 // with clustered columns, are queued for the block kernel.  The diagonal
 // pair leads its row and is not sorted.  With `keys` the rows are read from
 // the scatter's sort keys; without, pj/pk are sorted in place.
-__global__ void __launch_bounds__(kSortWarpThreads, 6)
+__global__ void __launch_bounds__(kSortWarpThreads, 3)
 sort_rows_warp_kernel(const int64_t* __restrict__ rp, int64_t rows, const uint64_t* __restrict__ keys,
                       uint32_t* __restrict__ pj, uint32_t* __restrict__ pk, int has_diag, int32_t* __restrict__ big,
                       unsigned long long* __restrict__ big_count, int32_t* __restrict__ status) {

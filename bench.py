@@ -281,6 +281,65 @@ def bench_sr(nqs, torch, n_sr, n_params, steps, flush, peaks):
                        "note": "over the whole step time (mean, Gram, FP64 sum and Cholesky solve, step)"}}
 
 
+def bench_sampler(nqs, torch, n_qubits, K, steps, flush, peak_gbs):
+    """Alg. 1 (ARGumbelTopK) over all n_qubits levels keeping K vectors: per
+    level the extensions, their conditioned perturbed values, the ordering and
+    the top-K cut (the library's kernels; one host read of the level's count).
+    The ansatz's conditional log-probabilities are a seeded stand-in
+    (log sigmoid of N(0, 2) logits, every outcome possible) and the Gumbel(0)
+    draws are seeded; both are drawn before timing, one row per kept vector."""
+    dev = flush.device
+    W = (n_qubits + 63) // 64
+    g = torch.Generator(device=dev).manual_seed(13)
+    z = torch.randn((n_qubits, K), generator=g, device=dev, dtype=torch.float64) * 2.0
+    logp = torch.stack([torch.nn.functional.logsigmoid(z), torch.nn.functional.logsigmoid(-z)], dim=2).contiguous()
+    u = torch.rand((n_qubits, K, 2), generator=g, device=dev, dtype=torch.float64).clamp_min(1e-300)
+    G = (-torch.log(-torch.log(u))).contiguous()
+    del z, u
+    bufs = [(torch.empty((K, W), dtype=torch.int64, device=dev), torch.empty(K, dtype=torch.float64, device=dev),
+             torch.empty(K, dtype=torch.float64, device=dev)) for _ in range(2)]
+    scratch = torch.empty(int(nqs.load_library().nqs_gumbel_scratch_bytes(K)), dtype=torch.uint8, device=dev)
+    zero = torch.zeros(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    counts = []
+
+    def run():
+        x, l, lt = None, zero, zero
+        counts.clear()
+        for i in range(n_qubits):
+            n = int(l.shape[0])
+            x, l, lt = nqs.gumbel_topk_level(n_qubits, i, x, l, lt, logp[i, :n], G[i, :n], K, out=bufs[i & 1],
+                                             scratch=scratch)
+            counts.append(n)
+        return x, l, lt
+
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, l, lt = run()
+        e1.record(stream)
+        ms.append((e0, e1))
+    torch.cuda.synchronize()
+    t = float(np.mean([a.elapsed_time(b) for a, b in ms]))
+    kept = int(l.shape[0])
+    # algorithmic bytes per level: each parent's words, l, L~, two log-probabilities and two
+    # draws read; each kept child's words, l' and L~' written
+    outs = counts[1:] + [kept]
+    bytes_ = sum(n * (8 * W + 16 + 32) + o * (8 * W + 16) for n, o in zip(counts, outs))
+    return {"workload": f"{n_qubits} qubits, K = {K} kept vectors, {sum(counts)} parents over {n_qubits} levels",
+            "ms_per_sampling": t, "us_per_level": 1e3 * t / n_qubits, "samples_per_s": kept / (t * 1e-3),
+            "hbm": {"bytes": bytes_, "achieved_gbs": bytes_ / (t * 1e-3) / 1e9, "peak_gbs": peak_gbs,
+                    "frac": bytes_ / (t * 1e-3) / 1e9 / peak_gbs,
+                    "note": "per level one host read of the kept count (the API returns it); "
+                            "the working set stays in L2"},
+            "steps": steps}
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -611,6 +670,9 @@ def run_ours(args):
     if ws == 1 and args.full_n > 0:
         line["full_eloc"] = bench_full_eloc(nqs, torch, inst, min(args.full_n, n), max(3, args.steps // 4), 3, flush,
                                             peaks.get("hbm_gbs"))
+    if ws == 1 and args.sampler_k > 0:
+        line["sampler"] = bench_sampler(nqs, torch, inst.n_qubits, args.sampler_k, max(3, args.steps // 4), flush,
+                                        peaks.get("hbm_gbs"))
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(inst, seconds=args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -632,6 +694,18 @@ def run_sr_only(args):
     sr = bench_sr(nqs, torch, 100, args.sr_params, args.steps, flush, peaks)
     print(json.dumps(dict(sr, metric="min-SR step time (N_SR = 100)", unit="ms", higher_is_better=False,
                           value=sr["ms_per_step"], steps=args.steps)), flush=True)
+
+
+def run_sampler_only(args):
+    """ARGumbelTopK alone (``--sampler-only``): one JSON line with the sampler measurement."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2408_07625_gb300 as nqs
+    peaks, _ = _peaks()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    sm = bench_sampler(nqs, torch, args.sampler_qubits, args.sampler_k, args.steps, flush, peaks.get("hbm_gbs"))
+    print(json.dumps(dict(sm, metric="ARGumbelTopK samples/s", unit="samples/s", higher_is_better=True,
+                          value=sm["samples_per_s"], steps=args.steps)), flush=True)
 
 
 def run_batched(args):
@@ -777,6 +851,11 @@ def main():
                    help="parameters of the min-SR measurement (100 samples); 0 skips it")
     p.add_argument("--no-batch64", action="store_true", help="skip the 64-instance batched measurement")
     p.add_argument("--sr-only", action="store_true", help="time only the min-SR step (--sr-params parameters)")
+    p.add_argument("--sampler-k", type=int, default=100_000,
+                   help="vectors kept per level by the ARGumbelTopK measurement; 0 skips it")
+    p.add_argument("--sampler-only", action="store_true",
+                   help="time only the ARGumbelTopK sampler (--sampler-qubits levels, --sampler-k kept)")
+    p.add_argument("--sampler-qubits", type=int, default=56)
     p.add_argument("--full-n", type=int, default=1000,
                    help="samples of the exact-local-energy (Eq. local_energy) measurement; 0 skips it")
     args = p.parse_args()
@@ -786,6 +865,8 @@ def main():
         run_reference(args)
     elif args.sr_only:
         run_sr_only(args)
+    elif args.sampler_only:
+        run_sampler_only(args)
     elif args.workload == "batch64":
         run_batched(args)
     else:

@@ -699,8 +699,13 @@ def local_energy_backward_half(batch: Batch, logpsi_re, logpsi_im, eloc_re, eloc
 
 
 def gumbel_topk_level(n_qubits, level, parent_x, parent_l, parent_lt, cond_logp, gumbel, K, device="cuda",
-                      stream=None):
-    """One qubit of Alg. 1 (ARGumbelTopK) on the GPU: (child_x [m, W] int64, child_l, child_lt)."""
+                      stream=None, out=None, scratch=None):
+    """One qubit of Alg. 1 (ARGumbelTopK) on the GPU: (child_x [m, W] int64, child_l, child_lt).
+
+    out: optional (child_x, child_l, child_lt) device tensors with room for
+    min(K, 2 n_parents) vectors; scratch: optional uint8 device tensor of at
+    least nqs_gumbel_scratch_bytes(n_parents) bytes (the returned tensors are
+    then views of ``out``)."""
     lib = load_library()
     W = (int(n_qubits) + 63) // 64
     pl, plt = _f64(parent_l, device), _f64(parent_lt, device)
@@ -711,11 +716,21 @@ def gumbel_topk_level(n_qubits, level, parent_x, parent_l, parent_lt, cond_logp,
     n = int(pl.shape[0])
     px = None if parent_x is None else _dev_u64(parent_x)
     m = min(int(K), 2 * n)
-    cx = torch.empty((max(m, 1), W), dtype=torch.int64, device=device)
-    cl = torch.empty(max(m, 1), dtype=torch.float64, device=device)
-    clt = torch.empty(max(m, 1), dtype=torch.float64, device=device)
+    if out is None:
+        cx = torch.empty((max(m, 1), W), dtype=torch.int64, device=device)
+        cl = torch.empty(max(m, 1), dtype=torch.float64, device=device)
+        clt = torch.empty(max(m, 1), dtype=torch.float64, device=device)
+    else:
+        cx, cl, clt = out
+        if cx.shape[0] < m or cx.shape[1] != W or cl.shape[0] < m or clt.shape[0] < m:
+            raise ValueError("out has no room for min(K, 2 n_parents) vectors")
     nbytes = int(lib.nqs_gumbel_scratch_bytes(n))
-    scratch = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    if scratch is None:
+        scratch = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    elif scratch.numel() < nbytes:
+        raise ValueError("scratch is smaller than nqs_gumbel_scratch_bytes(n_parents)")
+    else:
+        nbytes = int(scratch.numel())
     out = ctypes.c_int64()
     _check(lib.nqs_gumbel_topk_level(int(n_qubits), int(level), n, _ptr(px), _ptr(pl), _ptr(plt), _ptr(lp), _ptr(g),
                                      int(K), _ptr(scratch), nbytes, _ptr(cx), _ptr(cl), _ptr(clt), ctypes.byref(out),

@@ -63,6 +63,12 @@ def _xor_rows(U, rows, cols):
     return U[rows] ^ U[cols]
 
 
+def _spin_mask(n_words, parity):
+    """Word masks of the even (parity 0, alpha) or odd (parity 1, beta) qubits."""
+    m = 0x5555555555555555 if parity == 0 else 0xAAAAAAAAAAAAAAAA
+    return np.full(n_words, m, dtype=np.uint64)
+
+
 @pytest.mark.parametrize("name", ["h56", "h84"])
 def test_every_row_against_oracle(name):
     fs, g, inst = _load(name)
@@ -85,9 +91,23 @@ def test_every_row_against_oracle(name):
     xy = ham.export()[0]
     U = np.ascontiguousarray(inst.U)
     rows = np.repeat(np.arange(inst.n_unq), lens)
+    n_diag = 0
     for s0 in range(0, len(pj), 1 << 22):
         sl = slice(s0, s0 + (1 << 22))
-        assert np.array_equal(_xor_rows(U, rows[sl], pj[sl].astype(np.int64)), xy[pk[sl].astype(np.int64)])
+        d = _xor_rows(U, rows[sl], pj[sl].astype(np.int64))
+        assert np.array_equal(d, xy[pk[sl].astype(np.int64)])
+        # a two-body H moves at most two electrons: |U_i XOR U_j| in {0, 2, 4}; and with
+        # interleaved spin-orbitals (even qubits alpha, odd beta) both spin counts are kept
+        pc = np.bitwise_count(d).sum(axis=1)
+        assert np.isin(pc, (0, 2, 4)).all()
+        cols = pj[sl].astype(np.int64)
+        for mask in (_spin_mask(inst.n_words, 0), _spin_mask(inst.n_words, 1)):
+            ni = np.bitwise_count(U[rows[sl]] & mask).sum(axis=1)
+            nj = np.bitwise_count(U[cols] & mask).sum(axis=1)
+            assert np.array_equal(ni, nj)
+        n_diag += int((cols == rows[sl]).sum())
+    # the diagonal pair of every row is listed exactly once
+    assert n_diag == inst.n_unq
     # long rows: block-reduced (>= 1024 pairs) and block-sorted (> 512) ones are compared here too
     assert (lens >= 1024).sum() > 0 and (lens > 512).sum() > 0
     want = g["eloc"]

@@ -409,3 +409,33 @@ def test_stored_matrix_elements_h28(h28, prec):
     x, _ = nqs.local_energy_backward(*args)
     y, _ = nqs.local_energy_backward(*args, hpair=hp)
     assert torch.equal(x, y)
+
+
+def test_cross_sector_pairs_have_vanishing_elements():
+    """Samples from every particle-number sector of the 12-qubit molecule: the
+    CUDA path lists the oracle's pairs (patterns do connect sectors) and the
+    stored element of every cross-sector pair vanishes, because the molecular
+    H conserves both spin counts."""
+    inst = config_instance("h12")
+    ref_ham = oracle_for(inst)
+    scale = math.fsum(abs(float(c)) for c in inst.coef)
+    rng = np.random.default_rng(17)
+    U_ints = sorted(int(v) for v in rng.choice(1 << 12, size=400, replace=False))
+    ham = nqs.Hamiltonian.from_instance(inst)
+    batch = nqs.Batch(ham, to_dev_u(pack_ints(U_ints, 12)))
+    lre = np.random.default_rng(18).normal(0, 1, len(U_ints))
+    res = nqs.evaluate(batch, lre, None, "fp64", keep_h=True)
+    batch.status()
+    rows, j, k = pair_set_gpu(batch, res["pairs"])
+    want = sorted(oracle.find_coupled_pairs(U_ints, ref_ham, "terms"))
+    assert sorted(zip(rows.tolist(), j.tolist())) == want
+    h = res["hpair"].double().cpu().numpy()
+    even = int("01" * 6, 2)
+    cross = 0
+    for q in range(len(j)):
+        a, b = U_ints[rows[q]], U_ints[int(j[q])]
+        if (bin(a & even).count("1") != bin(b & even).count("1")
+                or bin(a & ~even).count("1") != bin(b & ~even).count("1")):
+            cross += 1
+            assert abs(h[q]) <= 1e-12 * scale
+    assert cross > 0

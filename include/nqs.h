@@ -352,7 +352,11 @@ int64_t nqs_gumbel_scratch_bytes(int64_t n_parents);
  * are ordered by L~' descending (stable: ties keep the parent order, x = 0
  * first) and the first min(K, possible) are written to child_x [..][W],
  * child_l, child_lt (device, room for min(K, 2 n_parents)); *n_children
- * (host) is their number.  FP64 throughout.
+ * (host) is their number.  FP64 throughout.  Ordering: the extensions go to
+ * buckets between splitters drawn from a sample of their keys and each bucket
+ * is sorted by (L~', extension index) in one block's shared memory; when a
+ * bucket would exceed 2048 extensions (many equal values) an LSD radix sort
+ * of all keys is used instead.  The result is the same either way.
  * scratch: device, 256-byte aligned, nqs_gumbel_scratch_bytes(n_parents).
  * Synchronises the stream (to learn the count).  The paper's own
  * contribution is the use of this sampler (Ref. on ancestral Gumbel top-k
@@ -362,6 +366,26 @@ int nqs_gumbel_topk_level(int n_qubits, int level, int64_t n_parents, const uint
                           const double* gumbel, int64_t K, void* scratch, int64_t scratch_bytes,
                           uint64_t* child_x, double* child_l, double* child_lt, int64_t* n_children,
                           void* stream);
+
+/* Largest max_parents nqs_gumbel_topk_level_async takes (262144). */
+int64_t nqs_gumbel_async_max_parents(void);
+
+/* The same level with the parent count held on the device, for a run of
+ * levels enqueued (or captured in a CUDA graph) without a host round trip:
+ * *n_parents (device int64, at most max_parents) is the number of parents;
+ * parent_l, parent_lt, cond_logp, gumbel and the child arrays are sized for
+ * max_parents (room for min(K, 2 max_parents) children); counts (device
+ * int64 [2]) receives the kept count and a status: 1 when done, 0 when a
+ * bucket would exceed 2048 extensions (then nothing is kept, so later levels
+ * that read this count start from no parents; repeat the run with
+ * nqs_gumbel_topk_level).  Pass the previous level's counts as the next
+ * level's n_parents.  scratch: nqs_gumbel_scratch_bytes(max_parents).  Does
+ * not synchronise; errors of the arguments are returned at once. */
+int nqs_gumbel_topk_level_async(int n_qubits, int level, int64_t max_parents, const int64_t* n_parents,
+                                const uint64_t* parent_x, const double* parent_l, const double* parent_lt,
+                                const double* cond_logp, const double* gumbel, int64_t K, void* scratch,
+                                int64_t scratch_bytes, uint64_t* child_x, double* child_l, double* child_lt,
+                                int64_t* counts, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Stochastic reconfiguration on the most probable samples (Sec. "ANQS-

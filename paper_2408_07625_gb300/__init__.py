@@ -91,6 +91,9 @@ def load_library(path: str = None):
         "nqs_probe_peaks": (_i32, [ctypes.POINTER(ctypes.c_double), _vp]),
         "nqs_candidates_scratch_bytes": (_i64, [_vp, _i64]),
         "nqs_gumbel_scratch_bytes": (_i64, [_i64]),
+        "nqs_gumbel_async_max_parents": (_i64, []),
+        "nqs_gumbel_topk_level_async": (_i32, [_i32, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _i64,
+                                               _vp, _vp, _vp, _vp, _vp]),
         "nqs_sr_scratch_bytes": (_i64, [_i64, _i64]),
         "nqs_sr_top": (_i32, [_i64, _vp, _i64, _vp, _vp, _i64, _vp]),
         "nqs_sr_step": (_i32, [_i32, _i64, _vp, _vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _i64, _vp]),
@@ -698,6 +701,9 @@ def local_energy_backward_half(batch: Batch, logpsi_re, logpsi_im, eloc_re, eloc
     return gr, gi
 
 
+_GUMBEL_BYTES = {}   # scratch bytes of nqs_gumbel_topk_level by parent count
+
+
 def gumbel_topk_level(n_qubits, level, parent_x, parent_l, parent_lt, cond_logp, gumbel, K, device="cuda",
                       stream=None, out=None, scratch=None):
     """One qubit of Alg. 1 (ARGumbelTopK) on the GPU: (child_x [m, W] int64, child_l, child_lt).
@@ -706,13 +712,17 @@ def gumbel_topk_level(n_qubits, level, parent_x, parent_l, parent_lt, cond_logp,
     min(K, 2 n_parents) vectors; scratch: optional uint8 device tensor of at
     least nqs_gumbel_scratch_bytes(n_parents) bytes (the returned tensors are
     then views of ``out``)."""
-    lib = load_library()
+    lib = _lib if _lib is not None else load_library()
     W = (int(n_qubits) + 63) // 64
-    pl, plt = _f64(parent_l, device), _f64(parent_lt, device)
-    lp = _f64(np.asarray(cond_logp, dtype=np.float64).reshape(-1) if not torch.is_tensor(cond_logp)
-              else cond_logp.reshape(-1), device)
-    g = _f64(np.asarray(gumbel, dtype=np.float64).reshape(-1) if not torch.is_tensor(gumbel)
-             else gumbel.reshape(-1), device)
+
+    def dev(t):   # device FP64, flat; tensors already so pass through untouched
+        if torch.is_tensor(t) and t.dtype == torch.float64 and t.is_cuda and t.is_contiguous():
+            return t.view(-1)
+        if not torch.is_tensor(t):
+            t = np.asarray(t, dtype=np.float64).reshape(-1)
+        return _f64(t, device).view(-1)
+
+    pl, plt, lp, g = dev(parent_l), dev(parent_lt), dev(cond_logp), dev(gumbel)
     n = int(pl.shape[0])
     px = None if parent_x is None else _dev_u64(parent_x)
     m = min(int(K), 2 * n)
@@ -724,7 +734,9 @@ def gumbel_topk_level(n_qubits, level, parent_x, parent_l, parent_lt, cond_logp,
         cx, cl, clt = out
         if cx.shape[0] < m or cx.shape[1] != W or cl.shape[0] < m or clt.shape[0] < m:
             raise ValueError("out has no room for min(K, 2 n_parents) vectors")
-    nbytes = int(lib.nqs_gumbel_scratch_bytes(n))
+    nbytes = _GUMBEL_BYTES.get(n)
+    if nbytes is None:
+        nbytes = _GUMBEL_BYTES.setdefault(n, int(lib.nqs_gumbel_scratch_bytes(n)))
     if scratch is None:
         scratch = torch.empty(nbytes, dtype=torch.uint8, device=device)
     elif scratch.numel() < nbytes:
@@ -732,11 +744,36 @@ def gumbel_topk_level(n_qubits, level, parent_x, parent_l, parent_lt, cond_logp,
     else:
         nbytes = int(scratch.numel())
     out = ctypes.c_int64()
-    _check(lib.nqs_gumbel_topk_level(int(n_qubits), int(level), n, _ptr(px), _ptr(pl), _ptr(plt), _ptr(lp), _ptr(g),
-                                     int(K), _ptr(scratch), nbytes, _ptr(cx), _ptr(cl), _ptr(clt), ctypes.byref(out),
-                                     _stream(stream)))
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib.nqs_gumbel_topk_level(int(n_qubits), int(level), n, None if px is None else px.data_ptr(),
+                                     pl.data_ptr(), plt.data_ptr(), lp.data_ptr(), g.data_ptr(), int(K),
+                                     scratch.data_ptr(), nbytes, cx.data_ptr(), cl.data_ptr(), clt.data_ptr(),
+                                     ctypes.byref(out), s.cuda_stream))
     k = int(out.value)
     return cx[:k], cl[:k], clt[:k]
+
+
+def gumbel_topk_level_async(n_qubits, level, max_parents, n_parents, parent_x, parent_l, parent_lt, cond_logp,
+                            gumbel, K, out, scratch, counts, stream=None):
+    """One qubit of Alg. 1 with the parent count on the device (nqs_gumbel_topk_level_async):
+    no host synchronisation, so a run of levels can be enqueued or captured in a CUDA graph.
+
+    n_parents: int64 CUDA tensor holding the count (the previous level's ``counts``, or 1);
+    parent_l, parent_lt, cond_logp [.., 2], gumbel [.., 2]: FP64 CUDA tensors with at least
+    max_parents rows; out = (child_x [.., W] int64, child_l, child_lt) with room for
+    min(K, 2 max_parents); scratch: uint8 CUDA tensor of nqs_gumbel_scratch_bytes(max_parents);
+    counts: int64 CUDA tensor [2] receiving (kept count, status 1 / 0 = a bucket overflowed)."""
+    lib = _lib if _lib is not None else load_library()
+    cx, cl, clt = out
+    for t in (n_parents, parent_l, parent_lt, cond_logp, gumbel, cx, cl, clt, scratch, counts):
+        if not (torch.is_tensor(t) and t.is_cuda and t.is_contiguous()):
+            raise TypeError("the device-count form takes contiguous CUDA tensors only")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib.nqs_gumbel_topk_level_async(int(n_qubits), int(level), int(max_parents), n_parents.data_ptr(),
+                                           None if parent_x is None else parent_x.data_ptr(), parent_l.data_ptr(),
+                                           parent_lt.data_ptr(), cond_logp.data_ptr(), gumbel.data_ptr(), int(K),
+                                           scratch.data_ptr(), int(scratch.numel()), cx.data_ptr(), cl.data_ptr(),
+                                           clt.data_ptr(), counts.data_ptr(), s.cuda_stream))
 
 
 def ar_gumbel_topk(n_qubits, K, cond_logp, gumbel, device="cuda"):

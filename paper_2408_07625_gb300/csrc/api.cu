@@ -856,6 +856,29 @@ int nqs_gumbel_topk_level(int n_qubits, int level, int64_t n_parents, const uint
   return NQS_OK;
 }
 
+int nqs_gumbel_topk_level_async(int n_qubits, int level, int64_t max_parents, const int64_t* n_parents,
+                                const uint64_t* parent_x, const double* parent_l, const double* parent_lt,
+                                const double* cond_logp, const double* gumbel, int64_t K, void* scratch,
+                                int64_t scratch_bytes, uint64_t* child_x, double* child_l, double* child_lt,
+                                int64_t* counts, void* stream) {
+  if (n_qubits < 1 || n_qubits > 64 * kMaxWords) return fail(NQS_ERR_ARG, "n_qubits out of range");
+  if (level < 0 || level >= n_qubits) return fail(NQS_ERR_ARG, "level out of range");
+  if (max_parents < 1 || K < 1) return fail(NQS_ERR_ARG, "max_parents and K must be positive");
+  if (max_parents > sample_async_limit()) return fail(NQS_ERR_UNSUPPORTED, "max_parents above the device-count limit");
+  if (!n_parents || !counts || (level > 0 && !parent_x) || !parent_l || !parent_lt || !cond_logp || !gumbel ||
+      !child_x || !child_l || !child_lt)
+    return fail(NQS_ERR_ARG, "null array");
+  if (!scratch || scratch_bytes < sample_scratch_bytes(max_parents)) return fail(NQS_ERR_CAPACITY, "scratch too small");
+  if (((uintptr_t)scratch) & 255) return fail(NQS_ERR_ARG, "scratch not 256-byte aligned");
+  cudaError_t e = launch_gumbel_level_async((n_qubits + 63) / 64, level, max_parents, (const long long*)n_parents,
+                                            parent_x, parent_l, parent_lt, cond_logp, gumbel, K, scratch, child_x,
+                                            child_l, child_lt, (long long*)counts, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sampling kernels");
+  return NQS_OK;
+}
+
+int64_t nqs_gumbel_async_max_parents(void) { return sample_async_limit(); }
+
 int nqs_find_pairs_half(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, uint32_t* rec_i,
                         uint32_t* rec_j, uint32_t* rec_k, int64_t capacity, int64_t* n_slots, void* stream) {
   return nqs_find_pairs_part(ham, U, n, work, 0, 1, rec_i, rec_j, rec_k, capacity, n_slots, stream);

@@ -274,6 +274,11 @@ int64_t sample_scratch_bytes(int64_t n_parents);
 cudaError_t launch_gumbel_level(int W, int level, int64_t n, const uint64_t* px, const double* pl, const double* plt,
                                 const double* logp, const double* G, int64_t K, void* scratch, uint64_t* cx,
                                 double* cl, double* clt, int64_t* n_out, cudaStream_t s);
+cudaError_t launch_gumbel_level_async(int W, int level, int64_t max_n, const long long* n_dev, const uint64_t* px,
+                                      const double* pl, const double* plt, const double* logp, const double* G,
+                                      int64_t K, void* scratch, uint64_t* cx, double* cl, double* clt,
+                                      long long* counts, cudaStream_t s);
+int64_t sample_async_limit();
 
 // half-stored pairs: the records of one EMIT_HALF search (k_half section of k_energy.cu)
 cudaError_t launch_find_half(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L,

@@ -78,6 +78,15 @@ def test_host_side_argument_errors(lib):
     assert lib.nqs_route_records(2, bp, *args, scr.ctypes.data, i64(1024), None) == -1
     assert b"ascending" in lib.nqs_last_error()
     assert lib.nqs_find_pairs_part(None, None, i64(0), None, 0, 1, None, None, None, i64(0), None, None) == -1
+    # the device-count sampler: its limit, and argument errors before any device work
+    lib.nqs_gumbel_async_max_parents.restype = ctypes.c_int64
+    limit = lib.nqs_gumbel_async_max_parents()
+    assert limit == 262144
+    one = np.ones(1, np.int64)
+    ga = (None, None, None, None, None, i64(4), None, i64(0), None, None, None, one.ctypes.data, None)
+    assert lib.nqs_gumbel_topk_level_async(8, 0, i64(limit + 1), one.ctypes.data, *ga) == -2
+    assert lib.nqs_gumbel_topk_level_async(8, 0, i64(10), None, *ga) == -1
+    assert lib.nqs_gumbel_topk_level_async(8, 9, i64(10), one.ctypes.data, *ga) == -1
 
 
 def test_product_package_does_not_import_the_oracle():

@@ -1,4 +1,5 @@
-// Device helpers: bit-vector words, parities, compensated FP32 arithmetic.
+// Device helpers: bit-vector words, parities, compensated FP32 arithmetic, a
+// block-wide bitonic sort.
 #pragma once
 
 #include <cstdint>
@@ -119,6 +120,89 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
+}
+
+// Bitonic sort of N elements (a power of two, N <= E * blockDim.x) by (key,
+// payload) ascending (by key alone when PAY is false), E per thread: thread t
+// holds elements E t .. E t + E - 1.  Partners within a thread are compared
+// in registers, partners in another lane of the warp through shuffles, and
+// only partners in another warp through shared memory (sk, sp: N entries).
+// Warps whose elements all lie past N skip the comparisons (their partners
+// lie past N too) but take part in every barrier.
+template <int E, bool PAY, class Key>
+__device__ __forceinline__ void block_bitonic(Key (&key)[E], int32_t (&pay)[E], int N, Key* sk, int32_t* sp) {
+  const int tid = threadIdx.x;
+  const bool live = E * 32 * (tid >> 5) < N;
+  auto less = [&](Key ka, int32_t pa, Key kb, int32_t pb) {
+    if (PAY) return ka < kb || (ka == kb && pa < pb);
+    return ka < kb;
+  };
+  for (int k = 2; k <= N; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j < 32 * E) {
+        if (!live) continue;
+        if (j < E) {
+#pragma unroll
+          for (int jj = 1; jj < E; jj <<= 1) {
+            if (jj != j) continue;
+#pragma unroll
+            for (int u = 0; u < E; ++u) {
+              const int w = u ^ jj;   // known at compile time: the arrays stay in registers
+              if (w > u) {
+                const int i = E * tid + u;
+                if (((i & k) == 0) == less(key[w], pay[w], key[u], pay[u])) {
+                  const Key tk = key[u];
+                  key[u] = key[w];
+                  key[w] = tk;
+                  if (PAY) {
+                    const int32_t tp = pay[u];
+                    pay[u] = pay[w];
+                    pay[w] = tp;
+                  }
+                }
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < E; ++u) {
+            const Key ok = __shfl_xor_sync(0xFFFFFFFFu, key[u], j / E);
+            const int32_t op = PAY ? __shfl_xor_sync(0xFFFFFFFFu, pay[u], j / E) : 0;
+            const int i = E * tid + u;
+            const bool take_min = ((i & k) == 0) == ((i & j) == 0);
+            if (take_min == less(ok, op, key[u], pay[u])) {
+              key[u] = ok;
+              if (PAY) pay[u] = op;
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < E; ++u) {
+          if (E * tid + u < N) {
+            sk[E * tid + u] = key[u];
+            if (PAY) sp[E * tid + u] = pay[u];
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < E; ++u) {
+          const int i = E * tid + u;
+          if (i < N) {
+            const int l = i ^ j;
+            const Key ok = sk[l];
+            const int32_t op = PAY ? sp[l] : 0;
+            const bool take_min = ((i & k) == 0) == ((i & j) == 0);
+            if (take_min == less(ok, op, key[u], pay[u])) {
+              key[u] = ok;
+              if (PAY) pay[u] = op;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
 }
 
 }  // namespace nqs

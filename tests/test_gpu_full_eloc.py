@@ -148,3 +148,59 @@ def test_capacity_error_reports_the_count():
     rc = lib.nqs_full_candidates(ham.handle, p(batch.U), batch.n, p(batch.work), p(scratch), 1000,
                                  p(cid), None, p(cand), None, 4, ctypes.byref(n), None)
     assert rc == -4
+
+
+def _check_by_definition(ham, batch, U_ints_arr, fc):
+    """Candidates = the distinct values of U_i XOR XY_k (numpy's unique), in
+    numeric order; every entry's index into them; each candidate's index in U."""
+    xy = ham.export()[0][:, 0]
+    keys = (U_ints_arr[:, None] ^ xy[None, :]).reshape(-1)
+    u, inv = np.unique(keys, return_inverse=True)
+    got = np.ascontiguousarray(fc.cand.cpu().numpy()).view(np.uint64).reshape(-1)
+    assert np.array_equal(got, u)
+    cid = fc.cand_id.cpu().numpy().view(np.uint32).astype(np.int64).reshape(-1)
+    assert np.array_equal(cid, inv.reshape(-1))
+    order = np.argsort(U_ints_arr)
+    pos = np.searchsorted(U_ints_arr[order], u)
+    pos = np.minimum(pos, len(order) - 1)
+    want_in_u = np.where(U_ints_arr[order][pos] == u, order[pos], -1)
+    assert np.array_equal(fc.in_u.cpu().numpy(), want_in_u)
+
+
+def test_deduplication_h56_300_samples():
+    """13.8 M entries (300 samples x 46,163 patterns at 56 qubits): the
+    deduplication checked against the definition, and a sample of matrix
+    elements against the oracle."""
+    inst = config_instance("h56")
+    U = np.ascontiguousarray(inst.U[:300, 0])
+    ham = nqs.Hamiltonian.from_instance(inst)
+    batch = nqs.Batch(ham, to_dev_u(U[:, None]))
+    fc = nqs.full_candidates(batch)
+    batch.status()
+    _check_by_definition(ham, batch, U, fc)
+    ref_ham = oracle.prepare_hamiltonian(inst.x_mask, inst.z_mask, inst.coef, inst.n_qubits)
+    xy = ham.export()[0][:, 0]
+    hv = fc.hval.cpu().numpy()
+    rng = np.random.default_rng(56)
+    for _ in range(200):
+        i, k = int(rng.integers(0, 300)), int(rng.integers(0, len(xy)))
+        want = oracle.matrix_element(int(U[i]), int(U[i] ^ xy[k]), ref_ham)
+        assert abs(hv[i, k] - want.real) <= 1e-12 * max(1.0, abs(want))
+
+
+def test_one_candidate_shared_by_5000_entries():
+    """5,000 samples each coupled to x' = 0 by its own pattern (U = the XY
+    patterns): 5,000 entries share one candidate; the result is the
+    definition's."""
+    rng = np.random.default_rng(5)
+    n = 24
+    pats = np.unique(rng.integers(1, 1 << n, 6000, dtype=np.int64))[:5000].astype(np.uint64)
+    x = pats[:, None].copy()
+    z = rng.integers(0, 1 << n, (len(pats), 1), dtype=np.int64).astype(np.uint64) & ~x
+    c = rng.normal(0.0, 1.0, len(pats))
+    ham = nqs.Hamiltonian(x, z, c, n)
+    batch = nqs.Batch(ham, to_dev_u(pats[:, None]))
+    fc = nqs.full_candidates(batch)
+    batch.status()
+    _check_by_definition(ham, batch, pats, fc)
+    assert int((fc.cand_id.cpu().numpy().reshape(-1) == 0).sum()) >= 5000   # candidate 0 is x' = 0

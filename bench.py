@@ -472,7 +472,8 @@ def run_ours(args):
             # sharded search: this rank's slice of the work items, records exchanged to the row owners
             rp, pj, pk = sharded_coupled_pairs(batch_obj, bounds, rank, ws)
         else:
-            rp, pj, pk = nqs.coupled_pairs(batch_obj, r0, r1, schedule=args.schedule, reuse=True)
+            # rows as the search placed them: the energy and adjoint sums are exact, so no row sort
+            rp, pj, pk = nqs.coupled_pairs(batch_obj, r0, r1, schedule=args.schedule, reuse=True, sort_rows=False)
         total = int(pj.numel())
         mark()
         hdt = torch.float64 if prec == "fp64" else torch.float32
@@ -666,11 +667,11 @@ def run_ours(args):
                     "per term + (8W + 4) B per XY pattern; pair list 12 B per pair written once and read "
                     "twice (E_loc^var, adjoint)"}
     # library kernels per step: staging (hash table and filter, per-qubit lists), the pairs phase
-    # (terms: count init, search, 3-kernel scan, row init, scatter, warp and block row sorts;
+    # (terms: count init, search, 3-kernel scan, row init, scatter, no row sort;
     # batch: count, scan, fill; trie: tree build, count, scan, fill), then amplitudes + row order (2)
     # + E_loc^var, E^var (+ combination across ranks), amplitudes + adjoint weights + row order (2)
     # + adjoint
-    pairs_kernels = {"terms": 2 + 1 + 1 + 3 + 1 + 1 + 2, "batch": 2 + 1 + 3 + 1,
+    pairs_kernels = {"terms": 2 + 1 + 1 + 3 + 1 + 1, "batch": 2 + 1 + 3 + 1,
                      "trie": 2 + 3 * ((inst.n_qubits + 7) // 8) + 7 + 1 + 3 + 1}[args.schedule]
     if ws > 1 and args.schedule == "terms":
         # sharded: staging, search slice, routing (count, scatter), record counts (init, count),

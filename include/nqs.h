@@ -66,14 +66,25 @@ enum {
                                   check failed and the access was skipped
                                   (corrupt input or pair list)                     */
     NQS_ERR_OOM = -7,          /* device allocation inside nqs_ham_load failed      */
-    NQS_ERR_RANGE = -8         /* an amplitude ratio leaves the FP32 exponent range */
+    NQS_ERR_RANGE = -8         /* an amplitude ratio leaves the FP32 exponent range,
+                                  or a term of a local-energy or adjoint row sum
+                                  reaches 2^55 in magnitude                        */
 };
 
 enum {
     NQS_SCHED_AUTO = 0,   /* library's choice                                      */
     NQS_SCHED_TERMS = 1,  /* loop over unique XY per sample (Alg. 2A)               */
     NQS_SCHED_BATCH = 2,  /* loop over the batch per sample (Alg. 2B)               */
-    NQS_SCHED_TRIE = 3    /* joint prefix-tree traversal (Algs. 3 and 2C)          */
+    NQS_SCHED_TRIE = 3,   /* joint prefix-tree traversal (Algs. 3 and 2C)          */
+    /* Flag OR-ed into the schedule of nqs_find_coupled_pairs and
+     * nqs_fill_coupled_pairs: leave each LoopOverTerms row (after its leading
+     * diagonal pair) in the order the search placed its pairs, which depends
+     * on thread timing, instead of ascending column order.  The set of pairs
+     * of every row is the same; the row sort is skipped.  nqs_local_energy
+     * and nqs_local_energy_backward sum every row exactly, so their results
+     * are bitwise the same for either order.  Ignored by the other schedules
+     * (their rows come out in column order). */
+    NQS_ROWS_UNSORTED = 0x100
 };
 
 enum {
@@ -186,7 +197,8 @@ int nqs_count_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n_unq
                             void* stream);
 
 /* Fill pass for offsets from nqs_count_coupled_pairs with the same arguments:
- * pair_j, pair_k device uint32 [row_ptr[last]].  Asynchronous. */
+ * pair_j, pair_k device uint32 [row_ptr[last]] (schedule may carry
+ * NQS_ROWS_UNSORTED).  Asynchronous. */
 int nqs_fill_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
                            void* work, int64_t row_begin, int64_t row_end,
                            int schedule, const int64_t* row_ptr, uint32_t* pair_j,
@@ -198,7 +210,8 @@ int64_t nqs_pairs_scratch_bytes(int64_t rows, int64_t max_pairs);
 
 /* One search pass.  The pairs are written to scratch (device, 256-byte
  * aligned, scratch_bytes from nqs_pairs_scratch_bytes) while the rows are
- * counted, then copied in CSR order to pair_j/pair_k (device uint32,
+ * counted, then copied in CSR order (each row sorted by column unless the
+ * schedule carries NQS_ROWS_UNSORTED) to pair_j/pair_k (device uint32,
  * `capacity` entries).  The call waits until the count is known (the total
  * is returned in *n_pairs); the copy into pair_j/pair_k may still be running
  * on the stream when it returns (later work on the stream sees it done).
@@ -317,9 +330,14 @@ int nqs_local_energy_backward_half(const nqs_ham* ham, const uint64_t* U, int64_
  *              re lo, im hi, im lo) or double2 per pair (16-byte aligned);
  *              nqs_local_energy_backward can read it instead of recomputing
  *              the matrix elements.
- * logpsi_re/_im: device FP64 [n_unq] for the whole batch.  Each row is a
- * fixed-order reduction by one warp, so results are bitwise reproducible
- * (rows are handed out heaviest first; the order does not affect any row).
+ * logpsi_re/_im: device FP64 [n_unq] for the whole batch.  Each row's terms
+ * (H times the amplitude ratio, in the precision chosen) are cut to whole
+ * units of 2^-64 (an error below 2^-64 per term), summed exactly as signed
+ * 128-bit integers and rounded to FP64 once, so a row's result does not
+ * depend on the order of its pairs (sorted
+ * or NQS_ROWS_UNSORTED), on which thread took which pair, or on the order in
+ * which rows are handed out; results are bitwise reproducible.  A term of
+ * magnitude 2^55 or more is dropped and NQS_ERR_RANGE is recorded.
  * The call overwrites the per-sample scratch of work.  Asynchronous. */
 int nqs_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, void* work,
                      const double* logpsi_re, const double* logpsi_im,

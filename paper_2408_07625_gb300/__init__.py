@@ -28,6 +28,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "libnqs.so")
 
 SCHEDULES = {"auto": 0, "terms": 1, "batch": 2, "trie": 3}
+ROWS_UNSORTED = 0x100   # schedule flag: LoopOverTerms rows left in search order (no row sort)
 PRECISIONS = {"fp64": 0, "fp32c": 1}
 
 _c_i64p = ctypes.POINTER(ctypes.c_int64)
@@ -284,14 +285,16 @@ def count_pairs(batch: Batch, row_begin=0, row_end=None, schedule="terms", strea
     return row_ptr, int(n.value)
 
 
-def fill_pairs(batch: Batch, row_ptr, n_pairs, row_begin=0, row_end=None, schedule="terms", stream=None):
+def fill_pairs(batch: Batch, row_ptr, n_pairs, row_begin=0, row_end=None, schedule="terms", stream=None,
+               sort_rows=True):
     row_end = batch.n if row_end is None else int(row_end)
     if schedule == "trie":
         batch.prefix_tree(stream)
     pj = torch.empty(max(n_pairs, 1), dtype=torch.int32, device=batch.device)
     pk = torch.empty(max(n_pairs, 1), dtype=torch.int32, device=batch.device)
+    sched = SCHEDULES[schedule] | (0 if sort_rows else ROWS_UNSORTED)
     _check(_lib.nqs_fill_coupled_pairs(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work),
-                                       int(row_begin), row_end, SCHEDULES[schedule], _ptr(row_ptr),
+                                       int(row_begin), row_end, sched, _ptr(row_ptr),
                                        _pair_ptr(pj), _pair_ptr(pk), _stream(stream)))
     return pj[:n_pairs], pk[:n_pairs]
 
@@ -306,10 +309,14 @@ def _grow(batch, rows, max_pairs):
 
 
 def coupled_pairs(batch: Batch, row_begin=0, row_end=None, schedule="terms", one_pass=True,
-                  reuse=False, stream=None):
+                  reuse=False, stream=None, sort_rows=True):
     """FindCoupledPairs over rows [row_begin, row_end): CSR (row_ptr, j, k) as CUDA tensors.
 
     ``j`` and ``k`` are int32 tensors holding uint32 column and pattern indices.
+    Each row holds its diagonal pair first, then the rest by ascending column;
+    with ``sort_rows=False`` (LoopOverTerms) the rest stay in the order the
+    search placed them (same pairs, no row sort): enough for ``local_energy``
+    and ``local_energy_backward``, whose row sums do not depend on the order.
     With ``one_pass`` the search runs once, writing into a scratch kept on the
     batch (grown and retried through the fill pass when too small).  With
     ``reuse`` the returned pair tensors are views of buffers that the next
@@ -321,15 +328,16 @@ def coupled_pairs(batch: Batch, row_begin=0, row_end=None, schedule="terms", one
         batch.prefix_tree(stream)
     if not one_pass:
         row_ptr, n = count_pairs(batch, row_begin, row_end, schedule, stream)
-        pj, pk = fill_pairs(batch, row_ptr, n, row_begin, row_end, schedule, stream)
+        pj, pk = fill_pairs(batch, row_ptr, n, row_begin, row_end, schedule, stream, sort_rows)
         return row_ptr, pj, pk
+    flag = 0 if sort_rows else ROWS_UNSORTED
     guess = batch._pair_guess or max(256 * rows, 1024)
     _grow(batch, rows, guess)
     row_ptr = torch.empty(rows + 1, dtype=torch.int64, device=batch.device)
     n = ctypes.c_int64()
     pj, pk = batch._pair_buf
     rc = _lib.nqs_find_coupled_pairs(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work),
-                                     int(row_begin), row_end, SCHEDULES[schedule], _ptr(batch._scratch),
+                                     int(row_begin), row_end, SCHEDULES[schedule] | flag, _ptr(batch._scratch),
                                      batch._scratch.numel(), _ptr(row_ptr), _ptr(pj), _ptr(pk),
                                      pj.numel(), ctypes.byref(n), _stream(stream))
     total = int(n.value)
@@ -338,7 +346,7 @@ def coupled_pairs(batch: Batch, row_begin=0, row_end=None, schedule="terms", one
         _grow(batch, rows, batch._pair_guess)
         pj, pk = batch._pair_buf
         _check(_lib.nqs_fill_coupled_pairs(batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work),
-                                           int(row_begin), row_end, SCHEDULES[schedule], _ptr(row_ptr),
+                                           int(row_begin), row_end, SCHEDULES[schedule] | flag, _ptr(row_ptr),
                                            _pair_ptr(pj), _pair_ptr(pk), _stream(stream)))
     else:
         _check(rc)
@@ -494,7 +502,8 @@ def evaluate(batch: Batch, logpsi_re, logpsi_im=None, precision="fp32c", schedul
     kept = None
     hpair = None
     if max_pairs is None:
-        pairs = coupled_pairs(batch, 0, batch.n, schedule, reuse=not keep_pairs, stream=stream)
+        pairs = coupled_pairs(batch, 0, batch.n, schedule, reuse=not keep_pairs, stream=stream,
+                              sort_rows=keep_pairs)
         row_ptr, total, chunks = pairs[0], int(pairs[1].numel()), [(0, batch.n)]
         if keep_h:
             hpair = pair_h_buffer(total, precision, dev, batch.ham.complex)
@@ -506,7 +515,8 @@ def evaluate(batch: Batch, logpsi_re, logpsi_im=None, precision="fp32c", schedul
         chunks = _row_chunks(rp_host, int(max_pairs)) if total > max_pairs else [(0, batch.n)]
         for (r0, r1) in chunks:
             rp = row_ptr[r0:r1 + 1]
-            pj, pk = fill_pairs(batch, rp, int(rp_host[r1] - rp_host[r0]), r0, r1, schedule, stream)
+            pj, pk = fill_pairs(batch, rp, int(rp_host[r1] - rp_host[r0]), r0, r1, schedule, stream,
+                                sort_rows=keep_pairs and len(chunks) == 1)
             local_energy(batch, a, b, (rp, pj, pk), precision, r0, r1, (er, ei, hd), stream=stream)
             if len(chunks) == 1 and keep_pairs:
                 kept = (rp, pj, pk)
@@ -560,7 +570,7 @@ class LocalEnergy(torch.autograd.Function):
             for (r0, r1) in res["chunks"]:
                 rp = row_ptr[r0:r1 + 1]
                 npairs = int(rp_host[r1] - rp_host[r0])
-                pj, pk = fill_pairs(batch, rp, npairs, r0, r1, res["schedule"])
+                pj, pk = fill_pairs(batch, rp, npairs, r0, r1, res["schedule"], sort_rows=False)
                 local_energy_backward(batch, lre, lim, res["eloc_re"], res["eloc_im"], res["hdiag"],
                                       res["evar"], g_er, g_ei, g_e, (rp, pj, pk), ctx.precision,
                                       r0, r1, (gr, gi))

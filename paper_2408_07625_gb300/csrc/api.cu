@@ -526,7 +526,8 @@ static int status_to_code(int st) {
   if (st & kStatusBadBits) return fail(NQS_ERR_ARG, "a sample has bits >= n_qubits");
   if (st & kStatusLimit)
     return fail(NQS_ERR_DEVICE_LIMIT, "a bounded device loop ran out or an index check skipped an access");
-  if (st & kStatusRange) return fail(NQS_ERR_RANGE, "an amplitude ratio leaves the FP32 range");
+  if (st & kStatusRange)
+    return fail(NQS_ERR_RANGE, "an amplitude ratio leaves the FP32 range or a local-energy term reaches 2^55");
   if (st & kStatusCapacity) return fail(NQS_ERR_CAPACITY, "a pair buffer sized at planning time was too small");
   if (st & kStatusNoTrie) return fail(NQS_ERR_ARG, "trie schedule without nqs_stage_trie after nqs_stage");
   return NQS_OK;
@@ -607,16 +608,25 @@ static int pick_schedule(const nqs_ham* ham, int64_t n, int schedule) {
   return (n < ham->n_xy) ? NQS_SCHED_BATCH : NQS_SCHED_TERMS;
 }
 
+// The schedule argument of the pair calls carries NQS_ROWS_UNSORTED as a flag
+// bit; split it off.
+static int split_schedule(int schedule, bool* sorted) {
+  *sorted = (schedule & NQS_ROWS_UNSORTED) == 0;
+  return schedule & ~NQS_ROWS_UNSORTED;
+}
+
 static cudaError_t launch_search(const nqs_ham* ham, const uint64_t* U, int64_t n, char* work,
                                  const StageHeader& L, int64_t rb, int64_t re, int schedule,
                                  int64_t* rp, uint32_t* pj, uint32_t* pk, int mode,
-                                 const PairScratch* sc, cudaStream_t s) {
+                                 const PairScratch* sc, cudaStream_t s, bool sorted = true) {
   const int sched = pick_schedule(ham, n, schedule);
   if (sched == NQS_SCHED_BATCH)
     return launch_pairs_batch(ham, U, n, work, L, rb, re, rp, pj, pk, mode == kFill ? kFill : kCount, s);
   if (sched == NQS_SCHED_TRIE)
     return launch_pairs_trie(ham, U, n, work, L, rb, re, rp, pj, pk, mode == kFill ? kFill : kCount, s);
-  return launch_pairs_terms(ham, U, work, L, rb, re, rp, pj, pk, mode, sc, s);
+  SearchTune tune;
+  tune.sort_rows = sorted;
+  return launch_pairs_terms(ham, U, work, L, rb, re, rp, pj, pk, mode, sc, s, tune);
 }
 
 static int count_pass(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, const StageHeader& L,
@@ -639,6 +649,8 @@ int nqs_count_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, vo
                             int64_t rb, int64_t re, int schedule, int64_t* row_ptr,
                             int64_t* n_pairs, void* stream) {
   StageHeader L;
+  bool sorted;
+  schedule = split_schedule(schedule, &sorted);
   int rc = check_work(ham, U, n, work, &L);
   if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(ham, n, schedule))) return rc;
   if (!row_ptr || !n_pairs) return fail(NQS_ERR_ARG, "null row_ptr or n_pairs");
@@ -653,12 +665,14 @@ int nqs_fill_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
                            int64_t rb, int64_t re, int schedule, const int64_t* row_ptr,
                            uint32_t* pair_j, uint32_t* pair_k, void* stream) {
   StageHeader L;
+  bool sorted;
+  schedule = split_schedule(schedule, &sorted);
   int rc = check_work(ham, U, n, work, &L);
   if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(ham, n, schedule))) return rc;
   if (!row_ptr || !pair_j || !pair_k) return fail(NQS_ERR_ARG, "null output");
   if (re == rb) return NQS_OK;
   cudaError_t e = launch_search(ham, U, n, (char*)work, L, rb, re, schedule, (int64_t*)row_ptr, pair_j,
-                                pair_k, kFill, nullptr, (cudaStream_t)stream);
+                                pair_k, kFill, nullptr, (cudaStream_t)stream, sorted);
   if (e != cudaSuccess) return cuda_fail(e, "pair fill kernel");
   return NQS_OK;
 }
@@ -692,6 +706,9 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
                            int64_t* row_ptr, uint32_t* pair_j, uint32_t* pair_k, int64_t capacity,
                            int64_t* n_pairs, void* stream) {
   StageHeader L;
+  const int flags = schedule & NQS_ROWS_UNSORTED;
+  bool sorted;
+  schedule = split_schedule(schedule, &sorted);
   int rc = check_work(ham, U, n, work, &L);
   if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(ham, n, schedule))) return rc;
   if (!row_ptr || !n_pairs) return fail(NQS_ERR_ARG, "null row_ptr or n_pairs");
@@ -703,7 +720,7 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
     if (rc) return rc;
     if (*n_pairs > capacity) return fail(NQS_ERR_CAPACITY, "pair capacity too small");
     if (*n_pairs > 0 && (!pair_j || !pair_k)) return fail(NQS_ERR_ARG, "null pair arrays");
-    return nqs_fill_coupled_pairs(ham, U, n, work, rb, re, schedule, row_ptr, pair_j, pair_k, stream);
+    return nqs_fill_coupled_pairs(ham, U, n, work, rb, re, schedule | flags, row_ptr, pair_j, pair_k, stream);
   }
   if (((uintptr_t)scratch) & 255) return fail(NQS_ERR_ARG, "scratch not 256-byte aligned");
   PairScratch sc = pair_scratch_view(scratch, rows, scratch_bytes);
@@ -732,7 +749,8 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
   e = cudaEventRecord(counted, s);
   const bool arrays = pair_j && pair_k;
   if (e == cudaSuccess && rows > 0)
-    e = launch_pairs_compact(ham, sc, (char*)work, L, rb, rows, row_ptr, pair_j, pair_k, arrays ? capacity : 0, s);
+    e = launch_pairs_compact(ham, sc, (char*)work, L, rb, rows, row_ptr, pair_j, pair_k, arrays ? capacity : 0, s,
+                             sorted);
   const cudaError_t es = cudaEventSynchronize(counted);
   cudaEventDestroy(counted);
   if (e != cudaSuccess) return cuda_fail(e, "compaction kernel");

@@ -1,5 +1,5 @@
-// Device helpers: bit-vector words, parities, compensated FP32 arithmetic, a
-// block-wide bitonic sort.
+// Device helpers: bit-vector words, parities, compensated FP32 arithmetic,
+// exact fixed-point sums, a block-wide bitonic sort.
 #pragma once
 
 #include <cstdint>
@@ -120,6 +120,126 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
+}
+
+// --------------------------------------------------------------------------
+// Exact sums ("Fx"): a signed 128-bit integer counting units of 2^-64
+// (64 integer bits with the sign, 64 fraction bits).  A float, double or
+// double-float term is turned into a whole number of units (the magnitude's
+// bits below one unit are cut off, so a term is off by less than 2^-64) and
+// added exactly.  Integer addition is associative, so a sum of terms does not
+// depend on their order, on how they are dealt to lanes or on the reduction
+// tree: a row's E_loc^var is the same whatever order its pairs are listed in.
+// A term of magnitude 2^55 or more is not taken; the add functions then
+// return false and leave the sum alone.  The conversions are branch-free
+// (selects only), so the lanes of a warp do not diverge on the terms' scales.
+// --------------------------------------------------------------------------
+struct Fx {
+  unsigned long long lo;
+  long long hi;
+};
+
+__device__ __forceinline__ Fx fx_zero() { return {0ull, 0ll}; }
+
+__device__ __forceinline__ void fx_add(Fx& a, const Fx& b) {
+  unsigned long long ahi = (unsigned long long)a.hi;
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(ahi) : "l"(b.lo), "l"((unsigned long long)b.hi));
+  a.hi = (long long)ahi;
+}
+
+// a += (neg ? -1 : 1) * floor(v 2^t) units, t <= 63
+__device__ __forceinline__ void fx_add_scaled(Fx& a, unsigned long long v, int t, bool neg) {
+  const int tp = t > 0 ? t : 0;
+  const int tn = t < 0 ? -t : 0;
+  const unsigned long long up = v << tp;
+  const unsigned long long uh = (v >> 1) >> (63 - tp);
+  const unsigned long long dn = tn < 64 ? v >> tn : 0ull;
+  const unsigned long long mask = neg ? ~0ull : 0ull;
+  const unsigned long long lo = (t >= 0 ? up : dn) ^ mask;
+  const unsigned long long hi = (t >= 0 ? uh : 0ull) ^ mask;
+  unsigned long long ahi = (unsigned long long)a.hi;
+  // a + ~x + 1 = a - x when neg
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(ahi) : "l"(lo), "l"(hi));
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, 0;" : "+l"(a.lo), "+l"(ahi) : "l"(neg ? 1ull : 0ull));
+  a.hi = (long long)ahi;
+}
+
+// f = +-m 2^(e - 150), m < 2^24: +-(m 2^40) 2^(e - 126) units
+__device__ __forceinline__ bool fx_add(Fx& a, float f) {
+  const uint32_t u = __float_as_uint(f);
+  const int e = (int)((u >> 23) & 0xFFu);
+  if (e > 181) return false;
+  const unsigned long long m = (u & 0x7FFFFFu) | (e ? 0x800000u : 0u);
+  fx_add_scaled(a, m << 40, e - 126, (u >> 31) != 0u);
+  return true;
+}
+
+// d = +-m 2^(e - 1075), m < 2^53: +-(m 2^11) 2^(e - 1022) units
+__device__ __forceinline__ bool fx_add(Fx& a, double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((u >> 52) & 0x7FFull);
+  if (e > 1077) return false;
+  const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
+  fx_add_scaled(a, m << 11, e - 1022, (u >> 63) != 0ull);
+  return true;
+}
+
+// a normalised double-float hi + lo (|lo| <= ulp(hi)/2, so lo's exponent is at
+// least 24 below hi's) as one 64-bit magnitude on hi's scale: m_hi 2^40 plus
+// or minus lo's mantissa shifted to that scale (at most 2^40); anything else
+// (zero hi, a part out of order) is added part by part
+__device__ __forceinline__ bool fx_add(Fx& a, float hi, float lo) {
+  const uint32_t uh = __float_as_uint(hi), ul = __float_as_uint(lo);
+  const int eh = (int)((uh >> 23) & 0xFFu), el = (int)((ul >> 23) & 0xFFu);
+  const int d = el - eh + 40;
+  if (eh == 0 || eh > 181 || d > 16) return fx_add(a, hi) & fx_add(a, lo);
+  const unsigned long long mh = (unsigned long long)((uh & 0x7FFFFFu) | 0x800000u) << 40;
+  const unsigned long long ml = (ul & 0x7FFFFFu) | (el ? 0x800000u : 0u);
+  const unsigned long long l = d >= 0 ? ml << d : (d > -64 ? ml >> (-d) : 0ull);
+  const bool same = ((uh ^ ul) >> 31) == 0u;
+  fx_add_scaled(a, same ? mh + l : mh - l, eh - 126, (uh >> 31) != 0u);
+  return true;
+}
+
+// warp all-reduce: every lane ends with the exact sum
+__device__ __forceinline__ Fx fx_warp_sum(Fx v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Fx w;
+    w.lo = __shfl_xor_sync(kFull, v.lo, o);
+    w.hi = __shfl_xor_sync(kFull, v.hi, o);
+    fx_add(v, w);
+  }
+  return v;
+}
+
+// the sum rounded once to the nearest double: the magnitude's leading 64
+// bits, with a sticky bit for any lower ones, rounded by the conversion, then
+// scaled by a power of two (exact)
+__device__ __forceinline__ double fx_to_double(Fx a) {
+  const bool neg = a.hi < 0;
+  unsigned long long lo = a.lo, hi = (unsigned long long)a.hi;
+  if (neg) {
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+  }
+  if ((hi | lo) == 0ull) return 0.0;
+  const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+  unsigned long long top, rest;
+  if (lz >= 64) {
+    top = lo << (lz - 64);
+    rest = 0ull;
+  } else if (lz == 0) {
+    top = hi;
+    rest = lo;
+  } else {
+    top = (hi << lz) | (lo >> (64 - lz));
+    rest = lo << lz;
+  }
+  top |= rest != 0ull ? 1ull : 0ull;
+  // the magnitude is (top + a fraction) 2^(64 - lz) units of 2^-64, i.e. about top 2^-lz
+  const double r = __ull2double_rn(top) * __longlong_as_double((long long)(1023 - lz) << 52);
+  return neg ? -r : r;
 }
 
 // Bitonic sort of N elements (a power of two, N <= E * blockDim.x) by (key,

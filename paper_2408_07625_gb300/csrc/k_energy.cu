@@ -216,22 +216,31 @@ template <> struct HStore<PolicyD> {
 // local energies are complex whatever log psi is).
 constexpr int kReal = 0, kCplxPsi = 1, kCplxH = 2;
 
+// a term added to an exact row sum (Fx); a term out of its range flags the status
+template <class Pol>
+__device__ __forceinline__ void fx_term(Fx& a, typename Pol::T t, int32_t* status) {
+  if (!Pol::fx(a, t)) atomicOr(status, kStatusRange);
+}
+
 // --------------------------------------------------------------------------
 // E_loc^var over CSR pairs.  A row is a sequence of rounds of 32 pairs; each
 // pair is evaluated by the lane that holds it (linear form or the pattern's
 // terms), and heavy patterns without a linear form are summed by all lanes
 // (then reduced across the warp).  The pair's lane adds H * ratio to its
-// accumulator and, if asked, stores H for the adjoint.  The next round's pair
-// indices are loaded while the current round is evaluated.  A short row is
-// one warp's rounds; a long row's rounds are dealt to the block's warps in
-// turn and the warps' sums are added in warp order.
+// exact fixed-point sum and, if asked, stores H for the adjoint.  The next
+// round's pair indices are loaded while the current round is evaluated.  A
+// short row is one warp's rounds; a long row's rounds are dealt to the
+// block's warps in turn.  The sums are exact, so a row's E_loc^var does not
+// depend on the order of its pairs (sorted by column or as the search placed
+// them) nor on the lane or warp that took each pair; it is rounded to FP64
+// once at the end.
 // --------------------------------------------------------------------------
 template <class Pol, int W, int CX, bool STORE_H>
 __device__ __forceinline__ void energy_rounds(const uint64_t* __restrict__ U, const Melem& M, const char* P,
                                               const char* Q, int64_t i, int64_t p, int64_t p1,
                                               int64_t first, int64_t stride, const uint32_t* __restrict__ pair_j,
                                               const uint32_t* __restrict__ pair_k, void* hpair, int32_t* status,
-                                              typename Pol::T& acc_re, typename Pol::T& acc_im) {
+                                              Fx& acc_re, Fx& acc_im) {
   using T = typename Pol::T;
   const int lane = threadIdx.x & 31;
   uint32_t jn = 0u, kn = 0u;
@@ -294,14 +303,14 @@ __device__ __forceinline__ void energy_rounds(const uint64_t* __restrict__ U, co
       T rr, ri;
       ratio<Pol, CX != kReal>(P, Q, j, i, rr, ri, status);
       if (CX == kCplxH) {  // (h + i h_im)(rr + i ri)
-        Pol::acc(acc_re, Pol::mul(h, rr));
-        Pol::acc(acc_re, Pol::neg(Pol::mul(h_im, ri)));
-        Pol::acc(acc_im, Pol::mul(h, ri));
-        Pol::acc(acc_im, Pol::mul(h_im, rr));
+        fx_term<Pol>(acc_re, Pol::mul(h, rr), status);
+        fx_term<Pol>(acc_re, Pol::neg(Pol::mul(h_im, ri)), status);
+        fx_term<Pol>(acc_im, Pol::mul(h, ri), status);
+        fx_term<Pol>(acc_im, Pol::mul(h_im, rr), status);
         if (STORE_H) HStore<Pol>::put2(hpair, q, h, h_im);
       } else {
-        Pol::acc(acc_re, Pol::mul(h, rr));
-        if (CX == kCplxPsi) Pol::acc(acc_im, Pol::mul(h, ri));
+        fx_term<Pol>(acc_re, Pol::mul(h, rr), status);
+        if (CX == kCplxPsi) fx_term<Pol>(acc_im, Pol::mul(h, ri), status);
         if (STORE_H) HStore<Pol>::put(hpair, q, h);
       }
     }
@@ -312,14 +321,14 @@ __device__ __forceinline__ void energy_rounds(const uint64_t* __restrict__ U, co
 template <class Pol, int W, int CX, bool STORE_H>
 __device__ __forceinline__ bool energy_diag(const uint64_t* __restrict__ U, const Melem& M, int64_t i, int64_t p,
                                             int64_t p1, const uint32_t* __restrict__ pair_k, void* hpair,
-                                            typename Pol::T& acc_re, double& hd) {
+                                            Fx& acc_re, double& hd, int32_t* status) {
   if (!(M.has_diag && p < p1 && __ldg(pair_k + p) == 0u)) return false;
   uint64_t xi[W];
   load_words<W>(U + i * W, xi);
   const typename Pol::T h = melem_diag<Pol, W>(xi, M);
   hd = Pol::to_d(h);
   if ((threadIdx.x & 31) == 0) {
-    Pol::acc(acc_re, h);
+    fx_term<Pol>(acc_re, h, status);
     if (STORE_H) {
       if (CX == kCplxH) HStore<Pol>::put2(hpair, p, h, Pol::zero());  // H_xx is real
       else HStore<Pol>::put(hpair, p, h);
@@ -328,16 +337,18 @@ __device__ __forceinline__ bool energy_diag(const uint64_t* __restrict__ U, cons
   return true;
 }
 
+// Real H and amplitudes on one-word samples are held to 48 registers (five
+// blocks per SM, no spills); the other forms keep the compiler's choice, which
+// a cap would make spill.
 template <class Pol, int W, int CX, bool STORE_H>
-__global__ void __launch_bounds__(kEnergyThreads)
+__global__ void __launch_bounds__(kEnergyThreads, (W == 1 && CX == 0) ? 5 : 1)
 local_energy_kernel(const uint64_t* __restrict__ U, const Melem M, const char* __restrict__ P,
                     const char* __restrict__ Q, int64_t row_begin, RowSched rs,
                     const int64_t* __restrict__ rp, const uint32_t* __restrict__ pair_j,
                     const uint32_t* __restrict__ pair_k, double* __restrict__ eloc_re,
                     double* __restrict__ eloc_im, double* __restrict__ hdiag, void* __restrict__ hpair,
                     int32_t* __restrict__ status) {
-  using T = typename Pol::T;
-  __shared__ T s_re[kEnergyWarps], s_im[kEnergyWarps];
+  __shared__ Fx s_re[kEnergyWarps], s_im[kEnergyWarps];
   __shared__ int64_t s_row;
   if (*(volatile int32_t*)status & kStatusCapacity) return;  // the pair list was not written
   const int lane = threadIdx.x & 31;
@@ -347,27 +358,27 @@ local_energy_kernel(const uint64_t* __restrict__ U, const Melem M, const char* _
     const int64_t i = row + row_begin;
     int64_t p = rp[row] - rp[0];
     const int64_t p1 = rp[row + 1] - rp[0];
-    T acc_re = Pol::zero(), acc_im = Pol::zero();
+    Fx acc_re = fx_zero(), acc_im = fx_zero();
     double hd = 0.0;
-    if (warp == 0) energy_diag<Pol, W, CX, STORE_H>(U, M, i, p, p1, pair_k, hpair, acc_re, hd);
+    if (warp == 0) energy_diag<Pol, W, CX, STORE_H>(U, M, i, p, p1, pair_k, hpair, acc_re, hd, status);
     if (M.has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
     energy_rounds<Pol, W, CX, STORE_H>(U, M, P, Q, i, p, p1, warp, kEnergyWarps, pair_j, pair_k, hpair,
                                        status, acc_re, acc_im);
-    const T er = Pol::warp_sum(acc_re);
-    const T ei = CX != kReal ? Pol::warp_sum(acc_im) : Pol::zero();
+    const Fx er = fx_warp_sum(acc_re);
+    const Fx ei = CX != kReal ? fx_warp_sum(acc_im) : fx_zero();
     if (lane == 0) {
       s_re[warp] = er;
       s_im[warp] = ei;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      T tr = s_re[0], ti = s_im[0];
+      Fx tr = s_re[0], ti = s_im[0];
       for (int w = 1; w < kEnergyWarps; ++w) {
-        tr = Pol::add(tr, s_re[w]);
-        ti = Pol::add(ti, s_im[w]);
+        fx_add(tr, s_re[w]);
+        fx_add(ti, s_im[w]);
       }
-      eloc_re[i] = Pol::to_d(tr);
-      if (eloc_im) eloc_im[i] = Pol::to_d(ti);
+      eloc_re[i] = fx_to_double(tr);
+      if (eloc_im) eloc_im[i] = fx_to_double(ti);
       if (hdiag) hdiag[i] = hd;
     }
   }
@@ -375,16 +386,16 @@ local_energy_kernel(const uint64_t* __restrict__ U, const Melem M, const char* _
     const int64_t i = row + row_begin;
     int64_t p = rp[row] - rp[0];
     const int64_t p1 = rp[row + 1] - rp[0];
-    T acc_re = Pol::zero(), acc_im = Pol::zero();
+    Fx acc_re = fx_zero(), acc_im = fx_zero();
     double hd = 0.0;
-    if (energy_diag<Pol, W, CX, STORE_H>(U, M, i, p, p1, pair_k, hpair, acc_re, hd)) ++p;
+    if (energy_diag<Pol, W, CX, STORE_H>(U, M, i, p, p1, pair_k, hpair, acc_re, hd, status)) ++p;
     energy_rounds<Pol, W, CX, STORE_H>(U, M, P, Q, i, p, p1, 0, 1, pair_j, pair_k, hpair, status, acc_re,
                                          acc_im);
-    const T er = Pol::warp_sum(acc_re);
-    const T ei = CX != kReal ? Pol::warp_sum(acc_im) : Pol::zero();
+    const Fx er = fx_warp_sum(acc_re);
+    const Fx ei = CX != kReal ? fx_warp_sum(acc_im) : fx_zero();
     if (lane == 0) {
-      eloc_re[i] = Pol::to_d(er);
-      if (eloc_im) eloc_im[i] = Pol::to_d(ei);
+      eloc_re[i] = fx_to_double(er);
+      if (eloc_im) eloc_im[i] = fx_to_double(ei);
       if (hdiag) hdiag[i] = hd;
     }
   }
@@ -668,8 +679,9 @@ __device__ __forceinline__ void load_geff(const char* G, int64_t i, typename Pol
 }
 
 // row y: sum over pairs (y, x), x != y, of ge(x) Re T + gi(x) Im T (and the
-// Im-part analogue) with T = H_yx psi(y)/psi(x) = H_xy psi(y)/psi(x); then the
-// diagonal term D_yy = -(E_loc(y) - H_yy) and g_E 2 w_y (Re E_loc(y) - E).
+// Im-part analogue) with T = H_yx psi(y)/psi(x) = H_xy psi(y)/psi(x), summed
+// exactly (fixed point, independent of the pairs' order); then the diagonal
+// term D_yy = -(E_loc(y) - H_yy) and g_E 2 w_y (Re E_loc(y) - E).
 // With LOAD_H the matrix elements come from the forward call's store (one
 // lane per pair, no term loop); otherwise they are recomputed exactly as the
 // forward computes them, so both forms give the same bits.
@@ -679,7 +691,7 @@ __device__ __forceinline__ void backward_rounds(const uint64_t* __restrict__ U, 
                                                 int64_t p1, int64_t first, int64_t stride,
                                                 const uint32_t* __restrict__ pair_j,
                                                 const uint32_t* __restrict__ pair_k, const void* hpair,
-                                                int32_t* status, typename Pol::T& da, typename Pol::T& db) {
+                                                int32_t* status, Fx& da, Fx& db) {
   using T = typename Pol::T;
   const int lane = threadIdx.x & 31;
   uint32_t jn = 0u, kn = 0u;
@@ -740,18 +752,18 @@ __device__ __forceinline__ void backward_rounds(const uint64_t* __restrict__ U, 
         // T = conj(h) psi(y)/psi(j) = (h rr + h_im ri) + i (h ri - h_im rr)
         const T tr = Pol::add(Pol::mul(h, rr), Pol::mul(h_im, ri));
         const T ti = Pol::add(Pol::mul(h, ri), Pol::neg(Pol::mul(h_im, rr)));
-        Pol::acc(da, Pol::mul(ge, tr));
-        Pol::acc(da, Pol::mul(gi, ti));
-        Pol::acc(db, Pol::neg(Pol::mul(ge, ti)));
-        Pol::acc(db, Pol::mul(gi, tr));
+        fx_term<Pol>(da, Pol::mul(ge, tr), status);
+        fx_term<Pol>(da, Pol::mul(gi, ti), status);
+        fx_term<Pol>(db, Pol::neg(Pol::mul(ge, ti)), status);
+        fx_term<Pol>(db, Pol::mul(gi, tr), status);
       } else {
         const T tr = Pol::mul(h, rr);
-        Pol::acc(da, Pol::mul(ge, tr));
+        fx_term<Pol>(da, Pol::mul(ge, tr), status);
         if (CX == kCplxPsi) {
           const T ti = Pol::mul(h, ri);
-          Pol::acc(da, Pol::mul(gi, ti));
-          Pol::acc(db, Pol::neg(Pol::mul(ge, ti)));
-          Pol::acc(db, Pol::mul(gi, tr));
+          fx_term<Pol>(da, Pol::mul(gi, ti), status);
+          fx_term<Pol>(db, Pol::neg(Pol::mul(ge, ti)), status);
+          fx_term<Pol>(db, Pol::mul(gi, tr), status);
         }
       }
     }
@@ -775,8 +787,7 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
                       const uint32_t* __restrict__ pair_j, const uint32_t* __restrict__ pair_k,
                       const void* __restrict__ hpair, const double2* __restrict__ own,
                       double* __restrict__ gre, double* __restrict__ gim, int32_t* __restrict__ status) {
-  using T = typename Pol::T;
-  __shared__ T s_a[kEnergyWarps], s_b[kEnergyWarps];
+  __shared__ Fx s_a[kEnergyWarps], s_b[kEnergyWarps];
   __shared__ int64_t s_row;
   if (*(volatile int32_t*)status & kStatusCapacity) return;  // the pair list was not written
   const int lane = threadIdx.x & 31;
@@ -787,23 +798,23 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
     int64_t p = rp[row] - rp[0];
     const int64_t p1 = rp[row + 1] - rp[0];
     if (M.has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
-    T da = Pol::zero(), db = Pol::zero();
+    Fx da = fx_zero(), db = fx_zero();
     backward_rounds<Pol, W, CX, LOAD_H>(U, M, P, Q, G, y, p, p1, warp, kEnergyWarps, pair_j, pair_k, hpair,
                                           status, da, db);
-    da = Pol::warp_sum(da);
-    db = CX != kReal ? Pol::warp_sum(db) : Pol::zero();
+    da = fx_warp_sum(da);
+    db = CX != kReal ? fx_warp_sum(db) : fx_zero();
     if (lane == 0) {
       s_a[warp] = da;
       s_b[warp] = db;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      T ta = s_a[0], tb = s_b[0];
+      Fx ta = s_a[0], tb = s_b[0];
       for (int w = 1; w < kEnergyWarps; ++w) {
-        ta = Pol::add(ta, s_a[w]);
-        tb = Pol::add(tb, s_b[w]);
+        fx_add(ta, s_a[w]);
+        fx_add(tb, s_b[w]);
       }
-      backward_finish<CX != kReal>(y, Pol::to_d(ta), CX != kReal ? Pol::to_d(tb) : 0.0, own, gre, gim);
+      backward_finish<CX != kReal>(y, fx_to_double(ta), CX != kReal ? fx_to_double(tb) : 0.0, own, gre, gim);
     }
   }
   for (int64_t row = next_row(rs, n_long); row >= 0; row = next_row(rs, n_long)) {
@@ -811,10 +822,10 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
     int64_t p = rp[row] - rp[0];
     const int64_t p1 = rp[row + 1] - rp[0];
     if (M.has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
-    T da = Pol::zero(), db = Pol::zero();
+    Fx da = fx_zero(), db = fx_zero();
     backward_rounds<Pol, W, CX, LOAD_H>(U, M, P, Q, G, y, p, p1, 0, 1, pair_j, pair_k, hpair, status, da, db);
-    const double sa = Pol::to_d(Pol::warp_sum(da));
-    const double sb = CX != kReal ? Pol::to_d(Pol::warp_sum(db)) : 0.0;
+    const double sa = fx_to_double(fx_warp_sum(da));
+    const double sb = CX != kReal ? fx_to_double(fx_warp_sum(db)) : 0.0;
     if (lane == 0) backward_finish<CX != kReal>(y, sa, sb, own, gre, gim);
   }
 }

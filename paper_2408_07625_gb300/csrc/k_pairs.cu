@@ -835,8 +835,11 @@ __global__ void pairs_init_kernel(int mode, int64_t rows, int64_t rb, int has_di
 // cursors hold each row's next free position, and no write passes the end
 // of the list.  A warp's records come from few search rows, so the lanes
 // sharing their first row take their places with one atomic.
+// With pj/pk the pairs go straight to the CSR arrays (rows left unsorted),
+// otherwise to the sort keys.
 __global__ void pairs_scatter_kernel(PairScratch sc, int64_t rb, int64_t re, const int64_t* __restrict__ rp,
-                                     unsigned long long* __restrict__ cursor, int32_t* __restrict__ status) {
+                                     unsigned long long* __restrict__ cursor, int32_t* __restrict__ status,
+                                     uint32_t* __restrict__ pj, uint32_t* __restrict__ pk) {
   if (*(volatile const int32_t*)status & kStatusCapacity) return;
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
@@ -862,15 +865,17 @@ __global__ void pairs_scatter_kernel(PairScratch sc, int64_t rb, int64_t re, con
     base = __shfl_sync(kFull, base, leader);
     if (in0) {
       const unsigned long long pos = base + __popc(peers & lt);
-      if (pos < total) sc.keys[pos] = ((uint64_t)j << 32) | k;
-      else atomicOr(status, kStatusLimit);
+      if (pos >= total) atomicOr(status, kStatusLimit);
+      else if (pj) { pj[pos] = (uint32_t)j; pk[pos] = (uint32_t)k; }
+      else sc.keys[pos] = ((uint64_t)j << 32) | k;
     }
     // second row
     const int64_t r1 = j - rb;
     if (live && r1 >= 0 && r1 < rows) {
       const unsigned long long pos = atomicAdd(cursor + r1, 1ull);
-      if (pos < total) sc.keys[pos] = ((uint64_t)i << 32) | k;
-      else atomicOr(status, kStatusLimit);
+      if (pos >= total) atomicOr(status, kStatusLimit);
+      else if (pj) { pj[pos] = (uint32_t)i; pk[pos] = (uint32_t)k; }
+      else sc.keys[pos] = ((uint64_t)i << 32) | k;
     }
   }
 }
@@ -1339,7 +1344,7 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stag
 #undef NQS_TERMS
     if (e != cudaSuccess) return e;
   }
-  if (mode == kFill) return launch_sort_rows(rp, rows, nullptr, pj, pk, ham->has_diag, stage, L, s);
+  if (mode == kFill && tune.sort_rows) return launch_sort_rows(rp, rows, nullptr, pj, pk, ham->has_diag, stage, L, s);
   return cudaSuccess;
 }
 
@@ -1474,15 +1479,16 @@ cudaError_t launch_clear_capacity(char* stage, cudaStream_t s) {
 
 cudaError_t launch_pairs_compact(const nqs_ham* ham, const PairScratch& sc, char* stage, const StageHeader& L,
                                  int64_t rb, int64_t rows, const int64_t* row_ptr, uint32_t* pair_j,
-                                 uint32_t* pair_k, int64_t capacity, cudaStream_t s) {
+                                 uint32_t* pair_k, int64_t capacity, cudaStream_t s, bool sort_rows) {
   auto* status = (int32_t*)(stage + offsetof(StageHeader, status));
   auto* cursor = (unsigned long long*)(stage + L.off_rowcur);
   const int64_t cap = std::min<int64_t>(capacity, sc.max_pairs);
   cudaError_t e = launch_init(kFill, rows, rb, ham->has_diag, nullptr, row_ptr, cursor, 1, pair_j, pair_k, cap,
                               sc.cursor + 1, status, s);
   if (e != cudaSuccess) return e;
-  pairs_scatter_kernel<<<8 * num_sms(), 256, 0, s>>>(sc, rb, rb + rows, row_ptr, cursor, status);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  pairs_scatter_kernel<<<8 * num_sms(), 256, 0, s>>>(sc, rb, rb + rows, row_ptr, cursor, status,
+                                                     sort_rows ? nullptr : pair_j, sort_rows ? nullptr : pair_k);
+  if ((e = cudaGetLastError()) != cudaSuccess || !sort_rows) return e;
   return launch_sort_rows(row_ptr, rows, sc.keys, pair_j, pair_k, ham->has_diag, stage, L, s);
 }
 

@@ -45,6 +45,8 @@ struct PolicyF {
     return {v.x, v.y};
   }
   __device__ static void acc(T& a, T t) { df_acc(a, t); }
+  // exact addition of both parts to a fixed-point sum; false if a part is out of its range
+  __device__ static bool fx(Fx& a, T t) { return fx_add(a, t.hi, t.lo); }
   __device__ static T add(T a, T b) { return df_add(a, b); }
   __device__ static T mul(T a, T b) { return df_mul(a, b); }
   __device__ static T neg(T a) { return df_neg(a); }
@@ -81,6 +83,7 @@ struct PolicyD {
   }
   __device__ static T val(const float2*, const double* d, int64_t i) { return __ldg(d + i); }
   __device__ static void acc(T& a, T t) { a += t; }
+  __device__ static bool fx(Fx& a, T t) { return fx_add(a, t); }
   __device__ static T add(T a, T b) { return a + b; }
   __device__ static T mul(T a, T b) { return a * b; }
   __device__ static T neg(T a) { return -a; }

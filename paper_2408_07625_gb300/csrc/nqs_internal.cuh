@@ -162,6 +162,7 @@ struct SearchTune {
   int trie_pop = 32;
   int part = 0;      // LoopOverTerms: search only slice `part` of `n_parts` equal slices of the work items
   int n_parts = 1;
+  bool sort_rows = true;  // LoopOverTerms FILL: sort each row by column (else the order the search placed them)
 };
 
 // search modes: COUNT writes per-row counts, FILL writes pairs at given CSR
@@ -198,7 +199,7 @@ cudaError_t launch_clear_capacity(char* stage, cudaStream_t s);
 // pairs outgrow `capacity` or the scratch, sets kStatusCapacity and writes nothing.
 cudaError_t launch_pairs_compact(const nqs_ham* ham, const PairScratch& sc, char* stage, const StageHeader& L,
                                  int64_t rb, int64_t rows, const int64_t* row_ptr, uint32_t* pair_j,
-                                 uint32_t* pair_k, int64_t capacity, cudaStream_t s);
+                                 uint32_t* pair_k, int64_t capacity, cudaStream_t s, bool sort_rows = true);
 
 cudaError_t launch_pairs_batch(const nqs_ham* ham, const uint64_t* U, int64_t n_unq, char* stage,
                                const StageHeader& L, int64_t row_begin, int64_t row_end,

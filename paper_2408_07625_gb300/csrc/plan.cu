@@ -101,7 +101,8 @@ static cudaError_t enqueue_instance(PlanInstance& I, int precision, const double
     if ((e = launch_pairs_terms(ham, I.in.U, w, I.L, 0, n, I.row_ptr + 1, nullptr, nullptr, kEmit, &sc, s, I.tune)))
       return e;
     if ((e = launch_scan(I.row_ptr + 1, n, w, I.L, s)) != cudaSuccess) return e;
-    if ((e = launch_pairs_compact(ham, sc, w, I.L, 0, n, I.row_ptr, I.pair_j, I.pair_k, I.capacity, s)))
+    // rows as the search placed them: the row sums are exact, so their order does not matter
+    if ((e = launch_pairs_compact(ham, sc, w, I.L, 0, n, I.row_ptr, I.pair_j, I.pair_k, I.capacity, s, false)))
       return e;
   }
   if ((e = launch_amplitudes(I.in.logpsi_re, nullptr, n, precision, w, I.L, s, I.in.U)) != cudaSuccess) return e;

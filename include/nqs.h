@@ -225,6 +225,26 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
                            int64_t* row_ptr, uint32_t* pair_j, uint32_t* pair_k,
                            int64_t capacity, int64_t* n_pairs, void* stream);
 
+/* The same search without any host wait (Sec. "FindCoupledPairs
+ * implementations", Alg. 2A; Algs. 2B/2C through count + fill): every step is
+ * enqueued on `stream` and the call returns at once, so a whole energy step
+ * can be enqueued (or captured in a CUDA graph) without a round trip.  The
+ * pair total stays on the device in row_ptr[row_end - row_begin].  pair_j,
+ * pair_k: device uint32 [capacity], sized by the caller (for example from an
+ * earlier batch's count).  With scratch (LoopOverTerms) the one-pass search is
+ * used, else count, then fill.  If the pairs outgrow `capacity` or the
+ * scratch, nothing is written to pair_j/pair_k, the workspace's capacity bit
+ * is set, and later nqs_local_energy / nqs_local_energy_backward calls on the
+ * workspace skip their rows; nqs_stage_status then returns NQS_ERR_CAPACITY
+ * (row_ptr is valid: size the buffers from it and call again).  The capacity
+ * bit is cleared at the start of every call.  Schedule flags as for
+ * nqs_find_coupled_pairs.  Argument errors are returned at once. */
+int nqs_find_coupled_pairs_async(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
+                                 void* work, int64_t row_begin, int64_t row_end,
+                                 int schedule, void* scratch, int64_t scratch_bytes,
+                                 int64_t* row_ptr, uint32_t* pair_j, uint32_t* pair_k,
+                                 int64_t capacity, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Half-stored pairs (Sec. "FindCoupledPairs implementations", Alg. 2A; the
  * symmetry x XOR x' = XY of Eq. pauli_melem): each unordered coupled pair

@@ -22,7 +22,8 @@ __all__ = ["NQSError", "load_library", "Hamiltonian", "Batch", "coupled_pairs", 
            "ar_gumbel_topk", "sr_top", "sr_step",
            "full_candidates", "local_energy_full",
            "local_energy", "variational_energy", "local_energy_backward", "LocalEnergy",
-           "evaluate", "BatchedPlan", "SCHEDULES", "PRECISIONS", "library_path"]
+           "evaluate", "BatchedPlan", "SCHEDULES", "PRECISIONS", "library_path",
+           "coupled_pairs_async", "ROWS_UNSORTED"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "libnqs.so")
@@ -71,6 +72,8 @@ def load_library(path: str = None):
         "nqs_fill_coupled_pairs": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _vp, _vp, _vp, _vp]),
         "nqs_find_coupled_pairs": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _vp, _i64, _vp, _vp, _vp,
                                           _i64, _c_i64p, _vp]),
+        "nqs_find_coupled_pairs_async": (_i32, [_vp, _vp, _i64, _vp, _i64, _i64, _i32, _vp, _i64, _vp, _vp,
+                                                _vp, _i64, _vp]),
         "nqs_pairs_scratch_bytes": (_i64, [_i64, _i64]),
         "nqs_local_energy": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _i64, _i64, _vp, _vp, _vp, _i32,
                                     _vp, _vp, _vp, _vp, _vp]),
@@ -248,6 +251,7 @@ class Batch:
         self._scratch = None          # one-pass search scratch, grown on demand
         self._pair_buf = None         # (pair_j, pair_k) buffers reused between calls
         self._pair_guess = None
+        self._async_rp = None         # row_ptr of coupled_pairs_async, reused between calls
         self._trie = False            # prefix tree of U built since the last staging
         _check(_lib.nqs_stage(ham.handle, _ptr(self.U), self.n, _ptr(self.work), nbytes,
                               1 if check else 0, _stream(stream)))
@@ -353,6 +357,35 @@ def coupled_pairs(batch: Batch, row_begin=0, row_end=None, schedule="terms", one
     if reuse:
         return row_ptr, pj[:total], pk[:total]
     return row_ptr, pj[:total].clone(), pk[:total].clone()
+
+
+def coupled_pairs_async(batch: Batch, capacity, row_begin=0, row_end=None, schedule="terms",
+                        sort_rows=True, stream=None):
+    """FindCoupledPairs with no host wait: (row_ptr, j, k) with j, k of length ``capacity``.
+
+    The pair total stays on the device (``row_ptr[-1]``); the buffers are kept
+    on the batch and reused by the next call.  If the pairs do not fit,
+    nothing is written and the batch's status (``Batch.status()``) reports
+    NQS_ERR_CAPACITY; later ``local_energy`` / ``local_energy_backward`` calls
+    on the batch skip their rows until a call fits.
+    """
+    row_end = batch.n if row_end is None else int(row_end)
+    rows = row_end - int(row_begin)
+    capacity = int(capacity)
+    if schedule == "trie":
+        batch.prefix_tree(stream)
+    _grow(batch, rows, max(capacity, 1))
+    if batch._async_rp is None or batch._async_rp.numel() != rows + 1:
+        batch._async_rp = torch.empty(rows + 1, dtype=torch.int64, device=batch.device)
+    row_ptr = batch._async_rp
+    pj, pk = batch._pair_buf
+    flag = 0 if sort_rows else ROWS_UNSORTED
+    scratch = batch._scratch if schedule in ("terms", "auto") else None
+    _check(_lib.nqs_find_coupled_pairs_async(
+        batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work), int(row_begin), row_end,
+        SCHEDULES[schedule] | flag, _ptr(scratch), 0 if scratch is None else scratch.numel(),
+        _ptr(row_ptr), _ptr(pj), _ptr(pk), capacity, _stream(stream)))
+    return row_ptr, pj[:capacity], pk[:capacity]
 
 
 def search_timing(on: bool):

@@ -768,6 +768,46 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n, voi
   return NQS_OK;
 }
 
+int nqs_find_coupled_pairs_async(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work,
+                                 int64_t rb, int64_t re, int schedule, void* scratch, int64_t scratch_bytes,
+                                 int64_t* row_ptr, uint32_t* pair_j, uint32_t* pair_k, int64_t capacity,
+                                 void* stream) {
+  StageHeader L;
+  bool sorted;
+  schedule = split_schedule(schedule, &sorted);
+  int rc = check_work(ham, U, n, work, &L);
+  if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(ham, n, schedule))) return rc;
+  if (!row_ptr || capacity < 0 || (capacity > 0 && (!pair_j || !pair_k)))
+    return fail(NQS_ERR_ARG, "null row_ptr or pair arrays");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t rows = re - rb;
+  const int sched = pick_schedule(ham, n, schedule);
+  const bool one_pass = scratch && sched == NQS_SCHED_TERMS;
+  if (one_pass && (((uintptr_t)scratch) & 255)) return fail(NQS_ERR_ARG, "scratch not 256-byte aligned");
+  PairScratch sc;
+  if (one_pass) {
+    sc = pair_scratch_view(scratch, rows, scratch_bytes);
+    if (sc.max_pairs < 1) return fail(NQS_ERR_CAPACITY, "scratch too small");
+  }
+  // the capacity bit then tells about this call alone
+  cudaError_t e = launch_clear_capacity((char*)work, s);
+  if (e != cudaSuccess) return cuda_fail(e, "status reset");
+  if ((rc = count_pass(ham, U, n, work, L, rb, re, schedule, row_ptr, one_pass ? &sc : nullptr, s))) return rc;
+  if (rows == 0) return NQS_OK;
+  if (one_pass) {
+    // the compaction checks the total against min(capacity, scratch) and the scratch's
+    // overflow flag, and writes nothing (capacity bit set) when the pairs do not fit
+    e = launch_pairs_compact(ham, sc, (char*)work, L, rb, rows, row_ptr, pair_j, pair_k, capacity, s, sorted);
+    if (e != cudaSuccess) return cuda_fail(e, "compaction kernel");
+    return NQS_OK;
+  }
+  if ((e = launch_capacity_check(row_ptr, rows, capacity, (char*)work, s)) != cudaSuccess)
+    return cuda_fail(e, "capacity check");
+  e = launch_search(ham, U, n, (char*)work, L, rb, re, schedule, row_ptr, pair_j, pair_k, kFill, nullptr, s, sorted);
+  if (e != cudaSuccess) return cuda_fail(e, "pair fill kernel");
+  return NQS_OK;
+}
+
 int64_t nqs_candidates_scratch_bytes(const nqs_ham* ham, int64_t n_unq) {
   if (!ham || n_unq < 0) return fail(NQS_ERR_ARG, "bad argument to nqs_candidates_scratch_bytes");
   return cand_scratch_bytes(ham, n_unq);

@@ -1472,6 +1472,16 @@ __global__ void clear_capacity_kernel(int32_t* status) {
   if (threadIdx.x == 0 && blockIdx.x == 0) atomicAnd(status, ~kStatusCapacity);
 }
 
+// flag the capacity bit when the rows' total exceeds `capacity` (stream-ordered)
+__global__ void capacity_flag_kernel(const int64_t* rp, int64_t rows, int64_t capacity, int32_t* status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && rp[rows] - rp[0] > capacity) atomicOr(status, kStatusCapacity);
+}
+
+cudaError_t launch_capacity_check(const int64_t* rp, int64_t rows, int64_t capacity, char* stage, cudaStream_t s) {
+  capacity_flag_kernel<<<1, 32, 0, s>>>(rp, rows, capacity, (int32_t*)(stage + offsetof(StageHeader, status)));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_clear_capacity(char* stage, cudaStream_t s) {
   clear_capacity_kernel<<<1, 32, 0, s>>>((int32_t*)(stage + offsetof(StageHeader, status)));
   return cudaGetLastError();

@@ -194,6 +194,8 @@ cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stag
 
 // clear the capacity bit of the status word (stream-ordered)
 cudaError_t launch_clear_capacity(char* stage, cudaStream_t s);
+// set the capacity bit if rp[rows] - rp[0] > capacity (stream-ordered)
+cudaError_t launch_capacity_check(const int64_t* rp, int64_t rows, int64_t capacity, char* stage, cudaStream_t s);
 
 // EMIT records -> CSR rows of [row_begin, row_begin + rows), sorted.  If the
 // pairs outgrow `capacity` or the scratch, sets kStatusCapacity and writes nothing.

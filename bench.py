@@ -526,6 +526,9 @@ def run_ours(args):
     nqs.search_timing(False)
     search_ms, search_launches = nqs.search_time()
     batch.status()  # the no-wait searches of the timed steps all fit their buffers
+    if ws == 1 or args.schedule != "terms":
+        # the pair count of the batch (the buffers of the no-wait search are larger)
+        total_pairs = int(batch._async_rp[-1]) if batch._async_rp is not None else total_pairs
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_ms = float(np.sum(step_ms))
     if ws > 1:
@@ -676,11 +679,11 @@ def run_ours(args):
                     "per term + (8W + 4) B per XY pattern; pair list 12 B per pair written once and read "
                     "twice (E_loc^var, adjoint)"}
     # library kernels per step: staging (hash table and filter, per-qubit lists), the pairs phase
-    # (terms: count init, search, 3-kernel scan, row init, scatter, no row sort;
+    # (terms: count init, search, 3-kernel scan, row init, scatter, key split (no row sort);
     # batch: count, scan, fill; trie: tree build, count, scan, fill), then amplitudes + row order (2)
     # + E_loc^var, E^var (+ combination across ranks), amplitudes + adjoint weights + row order (2)
     # + adjoint
-    pairs_kernels = {"terms": 2 + 1 + 1 + 3 + 1 + 1, "batch": 2 + 1 + 3 + 1,
+    pairs_kernels = {"terms": 2 + 1 + 1 + 3 + 1 + 1 + 1 + 1, "batch": 2 + 1 + 3 + 1,
                      "trie": 2 + 3 * ((inst.n_qubits + 7) // 8) + 7 + 1 + 3 + 1}[args.schedule]
     if ws > 1 and args.schedule == "terms":
         # sharded: staging, search slice, routing (count, scatter), record counts (init, count),

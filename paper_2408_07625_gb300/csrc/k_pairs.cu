@@ -801,14 +801,15 @@ cudaError_t search_time(double* total_ms, int64_t* launches) {
 
 // COUNT/EMIT: counts[r] = has_diag.  FILL: the diagonal pair at the row's
 // start (it leads the row and is not sorted) and cursor[r] = has_diag, or,
-// with `absolute`, the row's first free position in the list.  In FILL mode,
+// with `absolute`, the row's first free position in the list (with `keys`
+// the diagonal pair goes to the sort keys instead of pj/pk).  In FILL mode,
 // if the pairs outgrow `capacity` or the scratch overflowed, flag the status
 // and write nothing.
 __global__ void pairs_init_kernel(int mode, int64_t rows, int64_t rb, int has_diag, int64_t* __restrict__ counts,
                                   const int64_t* __restrict__ rp, unsigned long long* __restrict__ cursor,
                                   int absolute, uint32_t* __restrict__ pj, uint32_t* __restrict__ pk,
                                   int64_t capacity, const int64_t* __restrict__ overflow,
-                                  int32_t* __restrict__ status) {
+                                  int32_t* __restrict__ status, uint64_t* __restrict__ keys) {
   if (mode == kFill) {
     const bool too_small = (capacity >= 0 && rp[rows] - rp[0] > capacity) || (overflow && *overflow != 0);
     if (too_small) {
@@ -824,8 +825,12 @@ __global__ void pairs_init_kernel(int mode, int64_t rows, int64_t rb, int has_di
       const int64_t p = rp[r] - rp[0];
       cursor[r] = (unsigned long long)((absolute ? p : 0) + has_diag);
       if (has_diag) {
-        pj[p] = (uint32_t)(rb + r);
-        pk[p] = 0u;
+        if (keys) {
+          keys[p] = (uint64_t)(rb + r) << 32;
+        } else {
+          pj[p] = (uint32_t)(rb + r);
+          pk[p] = 0u;
+        }
       }
     }
   }
@@ -835,11 +840,8 @@ __global__ void pairs_init_kernel(int mode, int64_t rows, int64_t rb, int has_di
 // cursors hold each row's next free position, and no write passes the end
 // of the list.  A warp's records come from few search rows, so the lanes
 // sharing their first row take their places with one atomic.
-// With pj/pk the pairs go straight to the CSR arrays (rows left unsorted),
-// otherwise to the sort keys.
 __global__ void pairs_scatter_kernel(PairScratch sc, int64_t rb, int64_t re, const int64_t* __restrict__ rp,
-                                     unsigned long long* __restrict__ cursor, int32_t* __restrict__ status,
-                                     uint32_t* __restrict__ pj, uint32_t* __restrict__ pk) {
+                                     unsigned long long* __restrict__ cursor, int32_t* __restrict__ status) {
   if (*(volatile const int32_t*)status & kStatusCapacity) return;
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
@@ -865,17 +867,15 @@ __global__ void pairs_scatter_kernel(PairScratch sc, int64_t rb, int64_t re, con
     base = __shfl_sync(kFull, base, leader);
     if (in0) {
       const unsigned long long pos = base + __popc(peers & lt);
-      if (pos >= total) atomicOr(status, kStatusLimit);
-      else if (pj) { pj[pos] = (uint32_t)j; pk[pos] = (uint32_t)k; }
-      else sc.keys[pos] = ((uint64_t)j << 32) | k;
+      if (pos < total) sc.keys[pos] = ((uint64_t)j << 32) | k;
+      else atomicOr(status, kStatusLimit);
     }
     // second row
     const int64_t r1 = j - rb;
     if (live && r1 >= 0 && r1 < rows) {
       const unsigned long long pos = atomicAdd(cursor + r1, 1ull);
-      if (pos >= total) atomicOr(status, kStatusLimit);
-      else if (pj) { pj[pos] = (uint32_t)i; pk[pos] = (uint32_t)k; }
-      else sc.keys[pos] = ((uint64_t)i << 32) | k;
+      if (pos < total) sc.keys[pos] = ((uint64_t)i << 32) | k;
+      else atomicOr(status, kStatusLimit);
     }
   }
 }
@@ -1270,11 +1270,26 @@ static cudaError_t launch_sort_rows(const int64_t* rp, int64_t rows, uint64_t* k
 
 static cudaError_t launch_init(int mode, int64_t rows, int64_t rb, int has_diag, int64_t* counts, const int64_t* rp,
                                unsigned long long* cursor, int absolute, uint32_t* pj, uint32_t* pk,
-                               int64_t capacity, const int64_t* overflow, int32_t* status, cudaStream_t s) {
+                               int64_t capacity, const int64_t* overflow, int32_t* status, cudaStream_t s,
+                               uint64_t* keys = nullptr) {
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 4 * num_sms()));
   pairs_init_kernel<<<blocks, 256, 0, s>>>(mode, rows, rb, has_diag, counts, rp, cursor, absolute, pj, pk, capacity,
-                                           overflow, status);
+                                           overflow, status, keys);
   return cudaGetLastError();
+}
+
+// keys (column << 32 | pattern) -> pj, pk in list order: a coalesced pass that
+// replaces the row sort when the rows stay in search order
+__global__ void split_keys_kernel(const uint64_t* __restrict__ keys, const int64_t* __restrict__ rp, int64_t rows,
+                                  uint32_t* __restrict__ pj, uint32_t* __restrict__ pk,
+                                  const int32_t* __restrict__ status) {
+  if (*(volatile const int32_t*)status & kStatusCapacity) return;
+  const int64_t total = rp[rows] - rp[0];
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t v = keys[q];
+    pj[q] = (uint32_t)(v >> 32);
+    pk[q] = (uint32_t)v;
+  }
 }
 
 cudaError_t launch_pairs_terms(const nqs_ham* ham, const uint64_t* U, char* stage, const StageHeader& L,
@@ -1493,12 +1508,17 @@ cudaError_t launch_pairs_compact(const nqs_ham* ham, const PairScratch& sc, char
   auto* status = (int32_t*)(stage + offsetof(StageHeader, status));
   auto* cursor = (unsigned long long*)(stage + L.off_rowcur);
   const int64_t cap = std::min<int64_t>(capacity, sc.max_pairs);
+  // rows left in search order: the diagonal pairs go to the keys too, and one
+  // coalesced pass splits every key into pair_j/pair_k
   cudaError_t e = launch_init(kFill, rows, rb, ham->has_diag, nullptr, row_ptr, cursor, 1, pair_j, pair_k, cap,
-                              sc.cursor + 1, status, s);
+                              sc.cursor + 1, status, s, sort_rows ? nullptr : sc.keys);
   if (e != cudaSuccess) return e;
-  pairs_scatter_kernel<<<8 * num_sms(), 256, 0, s>>>(sc, rb, rb + rows, row_ptr, cursor, status,
-                                                     sort_rows ? nullptr : pair_j, sort_rows ? nullptr : pair_k);
-  if ((e = cudaGetLastError()) != cudaSuccess || !sort_rows) return e;
+  pairs_scatter_kernel<<<8 * num_sms(), 256, 0, s>>>(sc, rb, rb + rows, row_ptr, cursor, status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (!sort_rows) {
+    split_keys_kernel<<<8 * num_sms(), 256, 0, s>>>(sc.keys, row_ptr, rows, pair_j, pair_k, status);
+    return cudaGetLastError();
+  }
   return launch_sort_rows(row_ptr, rows, sc.keys, pair_j, pair_k, ham->has_diag, stage, L, s);
 }
 

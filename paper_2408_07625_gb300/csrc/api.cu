@@ -563,8 +563,10 @@ int nqs_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, void* work, int6
   if (bytes < L.total_bytes) return fail(NQS_ERR_CAPACITY, "workspace smaller than nqs_stage_bytes");
   cudaStream_t s = (cudaStream_t)stream;
   char* base = (char*)work;
-  cudaError_t e = cudaMemcpyAsync(base, &L, sizeof(L), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(e, "header copy");
+  // by a kernel, not a copy from this stack frame: a CUDA graph that captures
+  // the call replays the write with the header's value
+  cudaError_t e = launch_write_header(L, base, s);
+  if (e != cudaSuccess) return cuda_fail(e, "header write");
   if ((e = cudaMemsetAsync(base + kRedOffset, 0, 256, s)) != cudaSuccess) return cuda_fail(e, "memset");
   if ((e = launch_stage(ham, U, n, base, L, s)) != cudaSuccess) return cuda_fail(e, "stage kernel");
   if (check) return read_status(work, s);

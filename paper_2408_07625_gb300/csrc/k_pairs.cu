@@ -1483,6 +1483,15 @@ cudaError_t launch_records_count(const uint32_t* rec_i, const uint32_t* rec_j, i
   return cudaGetLastError();
 }
 
+__global__ void write_header_kernel(StageHeader h, StageHeader* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = h;
+}
+
+cudaError_t launch_write_header(const StageHeader& L, char* stage, cudaStream_t s) {
+  write_header_kernel<<<1, 32, 0, s>>>(L, reinterpret_cast<StageHeader*>(stage));
+  return cudaGetLastError();
+}
+
 __global__ void clear_capacity_kernel(int32_t* status) {
   if (threadIdx.x == 0 && blockIdx.x == 0) atomicAnd(status, ~kStatusCapacity);
 }

@@ -152,6 +152,9 @@ int cuda_fail(cudaError_t e, const char* what);
 // per-qubit lists of U (the header must already be in place)
 cudaError_t launch_stage(const nqs_ham* ham, const uint64_t* U, int64_t n, char* stage,
                          const StageHeader& L, cudaStream_t s);
+// the header written into the workspace by a one-thread kernel (the header
+// travels as a kernel argument, so the write can be captured in a CUDA graph)
+cudaError_t launch_write_header(const StageHeader& L, char* stage, cudaStream_t s);
 
 // launch parameters of the searches, chosen per instance by the batched plan's
 // autotuner: LoopOverTerms work items per atomic and search-table groups per

@@ -134,3 +134,61 @@ def test_async_step_matches_waiting_step(prec):
     batch.status()
     for x, y in zip(want, [er2, hd2, ev2, gr2]):
         assert torch.equal(x, y)
+
+
+def test_step_captured_in_a_cuda_graph():
+    """Staging, the no-wait search, E_loc^var, E^var and the adjoint enqueue no host
+    work, so a whole step can be captured once and replayed; a replay on new
+    contents of the captured buffers (the batch in another order) gives the eager
+    results bitwise."""
+    inst = _inst()
+    ham, batch = gpu_objects(inst)
+    n = batch.n
+    U_dev = batch.U.clone()
+    a_dev = torch.from_numpy(np.asarray(inst.logpsi_re, dtype=np.float64)).cuda()
+    g_dev = torch.from_numpy(np.random.default_rng(3).normal(0.0, 1.0, n)).cuda()
+    gE = torch.ones(1, dtype=torch.float64, device="cuda")
+    total = int(nqs.coupled_pairs(batch)[1].numel())
+    cap = total + 2048
+    hp = nqs.pair_h_buffer(cap, "fp32c", "cuda")
+    out_e = (torch.zeros(n, dtype=torch.float64, device="cuda"), None,
+             torch.zeros(n, dtype=torch.float64, device="cuda"))
+    out_g = (torch.zeros(n, dtype=torch.float64, device="cuda"), None)
+    out_v = torch.zeros(3, dtype=torch.float64, device="cuda")
+
+    def step():
+        batch.restage(U_dev)
+        pairs = nqs.coupled_pairs_async(batch, cap, sort_rows=False)
+        er, ei, hd = nqs.local_energy(batch, a_dev, None, pairs, "fp32c", out=out_e, hpair=hp)
+        ev = nqs.variational_energy(batch, a_dev, er, out=out_v)
+        nqs.local_energy_backward(batch, a_dev, None, er, ei, hd, ev, g_dev, None, gE, pairs, "fp32c",
+                                  out=out_g, hpair=hp)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    perm = torch.from_numpy(np.random.default_rng(5).permutation(n)).cuda()
+    U_perm, a_perm, g_perm = batch.U.clone()[perm], a_dev[perm], g_dev[perm]
+    for Ux, ax, gx in ((batch.U.clone(), a_dev.clone(), g_dev.clone()), (U_perm, a_perm, g_perm)):
+        U_dev.copy_(Ux)
+        a_dev.copy_(ax)
+        g_dev.copy_(gx)
+        graph.replay()
+        torch.cuda.synchronize()
+        batch.status()
+        got = [out_e[0].clone(), out_e[2].clone(), out_v.clone(), out_g[0].clone()]
+        # eager reference on a fresh batch of the same contents
+        ref = nqs.Batch(ham, Ux)
+        pairs = nqs.coupled_pairs(ref)
+        er, ei, hd = nqs.local_energy(ref, ax, None, pairs, "fp32c")
+        ev = nqs.variational_energy(ref, ax, er)
+        gr, _ = nqs.local_energy_backward(ref, ax, None, er, ei, hd, ev, gx, None, gE, pairs, "fp32c")
+        ref.status()
+        for x, y in zip(got, [er, hd, ev, gr]):
+            assert torch.equal(x, y)

@@ -639,6 +639,23 @@ def run_ours(args):
     out_v = torch.empty(3, dtype=torch.float64).pin_memory()
     U2 = torch.empty_like(U); a2 = torch.empty_like(a)
     batch2 = nqs.Batch(ham, U, check=True)
+    U2.copy_(U); a2.copy_(a)
+    e_graph = None
+    if graph is not None and "ms_per_step" in graph:
+        # as the headline: the step on the copied-in buffers captured once, replayed each step
+        er, evar, gr, _, _ = step(batch2, U2, a2)   # sizes the no-wait search's buffers
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            step(batch2, U2, a2)
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        e_graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(e_graph):
+            er, evar, gr, _, _ = step(batch2, U2, a2)
+        for _ in range(3):
+            e_graph.replay()
+        torch.cuda.synchronize()
     e_starts, e_ends = [], []
     for it in range(args.steps):
         flush.zero_()
@@ -646,7 +663,10 @@ def run_ours(args):
         s0.record(stream)
         U2.copy_(U_host, non_blocking=True)
         a2.copy_(a_host, non_blocking=True)
-        er, evar, gr, _, _ = step(batch2, U2, a2)
+        if e_graph is not None:
+            e_graph.replay()
+        else:
+            er, evar, gr, _, _ = step(batch2, U2, a2)
         out_e[r0:r1].copy_(er[r0:r1], non_blocking=True)
         out_g[r0:r1].copy_(gr[r0:r1], non_blocking=True)
         out_v.copy_(evar, non_blocking=True)

@@ -5,9 +5,8 @@ calls ``oracle/`` only (RowOracle: LoopOverTerms per row, Alg. 2A; matrix
 elements by the supplementary MatrixElement algorithm; E_loc^var by Eq.
 local_energy restricted to U; E^var by Eq. variational_energy; correctly
 rounded sums).  For every row of the 56-qubit batch (1e5 samples) and the
-84-qubit batch (2e5 samples, two words per sample) this test checks, in the
-launch configuration bench.py times (one-pass LoopOverTerms search, FP32C
-and FP64):
+84-qubit batch (2e5 samples, two words per sample) this test checks, with the
+one-pass LoopOverTerms search and canonical (sorted) rows, FP32C and FP64:
 
 * the number of coupled pairs and a digest of the row's column set, exactly;
 * for every pair, U_i XOR U_j equals the XY pattern the library names;
@@ -18,6 +17,8 @@ and FP64):
 Rows of at least 1024 pairs (reduced by a whole block) and of more than 512
 pairs (sorted by the block sort) are among them (295 at 56 qubits, the
 Hartree-Fock row with 7,676 pairs the longest); the test asserts they occur.
+The last test repeats the 56-qubit checks in the form bench.py times (the
+no-wait search, rows left in search order).
 """
 
 import importlib.util
@@ -117,3 +118,29 @@ def test_every_row_against_oracle(name):
         assert err.max() <= tol, (prec, int(err.argmax()), float(err.max()))
         ev = res[prec]["evar"][0].item()
         assert abs(ev - float(g["evar"][0])) <= tol, (prec, ev, float(g["evar"][0]))
+
+
+def test_bench_step_configuration_h56():
+    """The form bench.py times at 56 qubits: the no-wait search with rows left in
+    search order, then E_loc^var, E^var and the adjoint on those lists.  Every row's
+    pair count and column set against the oracle's, and E_loc^var / E^var bitwise
+    equal to the canonical (sorted-row) path, which the test above holds to the
+    oracle, in both precisions."""
+    fs, g, inst = _load("h56")
+    ham, batch = gpu_objects(inst)
+    for prec, tol in (("fp64", TOL64), ("fp32c", TOL32)):
+        ref = nqs.evaluate(batch, inst.logpsi_re, None, prec)
+        total = int(ref["n_pairs"])
+        rp, pj, pk = nqs.coupled_pairs_async(batch, total + 1024, sort_rows=False)
+        er, ei, hd = nqs.local_energy(batch, inst.logpsi_re, None, (rp, pj, pk), prec)
+        ev = nqs.variational_energy(batch, inst.logpsi_re, er)
+        batch.status()
+        rph = rp.cpu().numpy()
+        assert int(rph[-1]) == int(g["n_pairs"][0])
+        assert np.array_equal(np.diff(rph), g["count"])
+        dig = fs.set_digest_np(rph, pj[:total].cpu().numpy().view(np.uint32))
+        assert np.array_equal(dig, g["digest"])
+        assert torch.equal(er, ref["eloc_re"]) and torch.equal(hd, ref["hdiag"])
+        assert torch.equal(ev, ref["evar"])
+        err = np.abs(er.cpu().numpy() - g["eloc"])
+        assert err.max() <= tol, (prec, float(err.max()))

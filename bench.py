@@ -480,7 +480,7 @@ def run_ours(args):
             # no host wait: the buffers are sized from the first call; an overflow would show in
             # the workspace status, which is checked after the timed steps
             rp, pj, pk = nqs.coupled_pairs_async(batch_obj, cap[0], r0, r1, schedule=args.schedule,
-                                                 sort_rows=False)
+                                                 sort_rows=False, packed=args.schedule == "terms")
         total = int(pj.numel())
         mark()
         hdt = torch.float64 if prec == "fp64" else torch.float32
@@ -742,11 +742,11 @@ def run_ours(args):
                     "per term + (8W + 4) B per XY pattern; pair list 12 B per pair written once and read "
                     "twice (E_loc^var, adjoint)"}
     # library kernels per step: staging (hash table and filter, per-qubit lists), the pairs phase
-    # (terms: count init, search, 3-kernel scan, row init, scatter, key split (no row sort);
+    # (terms: count init, search, 3-kernel scan, row init, scatter into packed pair words (no row sort);
     # batch: count, scan, fill; trie: tree build, count, scan, fill), then amplitudes + row order (2)
     # + E_loc^var, E^var (+ combination across ranks), amplitudes + adjoint weights + row order (2)
     # + adjoint
-    pairs_kernels = {"terms": 2 + 1 + 1 + 3 + 1 + 1 + 1 + 1, "batch": 2 + 1 + 3 + 1,
+    pairs_kernels = {"terms": 2 + 1 + 1 + 3 + 1 + 1 + 1, "batch": 2 + 1 + 3 + 1,
                      "trie": 2 + 3 * ((inst.n_qubits + 7) // 8) + 7 + 1 + 3 + 1}[args.schedule]
     if ws > 1 and args.schedule == "terms":
         # sharded: staging, search slice, routing (count, scatter), record counts (init, count),

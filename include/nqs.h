@@ -238,7 +238,12 @@ int nqs_find_coupled_pairs(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
  * workspace skip their rows; nqs_stage_status then returns NQS_ERR_CAPACITY
  * (row_ptr is valid: size the buffers from it and call again).  The capacity
  * bit is cleared at the start of every call.  Schedule flags as for
- * nqs_find_coupled_pairs.  Argument errors are returned at once. */
+ * nqs_find_coupled_pairs.  Packed form: with pair_k == NULL, LoopOverTerms
+ * with scratch and NQS_ROWS_UNSORTED, each pair is one 64-bit word
+ * (column << 32 | pattern) in pair_j (8-byte aligned, `capacity` words), the
+ * layout nqs_local_energy and nqs_local_energy_backward accept with
+ * pair_k == NULL; it skips the pass that splits the words into two arrays.
+ * Argument errors are returned at once. */
 int nqs_find_coupled_pairs_async(const nqs_ham* ham, const uint64_t* U, int64_t n_unq,
                                  void* work, int64_t row_begin, int64_t row_end,
                                  int schedule, void* scratch, int64_t scratch_bytes,
@@ -340,7 +345,8 @@ int nqs_local_energy_backward_half(const nqs_ham* ham, const uint64_t* U, int64_
  * ------------------------------------------------------------------------- */
 
 /* For rows r in [row_begin, row_end), with their pairs from a fill pass over
- * the same range, write
+ * the same range (pair_j/pair_k, or pair_k == NULL and pair_j holding the
+ * packed 64-bit words of nqs_find_coupled_pairs_async), write
  *   eloc_re[r], eloc_im[r] = E_loc^var(U_r)  (eloc_im may be NULL only if
  *                                              logpsi_im is NULL and H is real),
  *   hdiag[r] = H_{U_r U_r} (may be NULL; real for any Hermitian H),
@@ -564,7 +570,8 @@ int nqs_evar_combine_host(const double* parts, int k, double* out);
 /* ---------------------------------------------------------------------------
  * Adjoint: gradient of L = sum_x [g_re(x) Re E_loc(x) + g_im(x) Im E_loc(x)]
  *          + g_evar E^var with respect to (Re log psi, Im log psi).
- * For rows y in [row_begin, row_end) (pairs of those rows) writes
+ * For rows y in [row_begin, row_end) (pairs of those rows, as two arrays or,
+ * with pair_k == NULL, packed in pair_j as for nqs_local_energy) writes
  * grad_re[y], grad_im[y] (grad_im may be NULL if logpsi_im is NULL).
  *   eloc_re/_im, hdiag: the forward results for the WHOLE batch.
  *   evar: device FP64 [3] from nqs_variational_energy.

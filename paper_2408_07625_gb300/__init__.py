@@ -252,6 +252,7 @@ class Batch:
         self._pair_buf = None         # (pair_j, pair_k) buffers reused between calls
         self._pair_guess = None
         self._async_rp = None         # row_ptr of coupled_pairs_async, reused between calls
+        self._packed_buf = None       # packed pair words of coupled_pairs_async, reused between calls
         self._trie = False            # prefix tree of U built since the last staging
         _check(_lib.nqs_stage(ham.handle, _ptr(self.U), self.n, _ptr(self.work), nbytes,
                               1 if check else 0, _stream(stream)))
@@ -360,8 +361,13 @@ def coupled_pairs(batch: Batch, row_begin=0, row_end=None, schedule="terms", one
 
 
 def coupled_pairs_async(batch: Batch, capacity, row_begin=0, row_end=None, schedule="terms",
-                        sort_rows=True, stream=None):
+                        sort_rows=True, packed=False, stream=None):
     """FindCoupledPairs with no host wait: (row_ptr, j, k) with j, k of length ``capacity``.
+
+    With ``packed`` (LoopOverTerms, ``sort_rows=False``) the pairs come as one
+    int64 tensor of (column << 32 | pattern) words and ``k`` is None; that is
+    the form ``local_energy`` and ``local_energy_backward`` read without a
+    split pass.
 
     The pair total stays on the device (``row_ptr[-1]``); the buffers are kept
     on the batch and reused by the next call.  If the pairs do not fit,
@@ -379,13 +385,17 @@ def coupled_pairs_async(batch: Batch, capacity, row_begin=0, row_end=None, sched
         batch._async_rp = torch.empty(rows + 1, dtype=torch.int64, device=batch.device)
     row_ptr = batch._async_rp
     pj, pk = batch._pair_buf
+    if packed:
+        if batch._packed_buf is None or batch._packed_buf.numel() < max(capacity, 1):
+            batch._packed_buf = torch.empty(max(capacity, 1), dtype=torch.int64, device=batch.device)
+        pj, pk = batch._packed_buf, None
     flag = 0 if sort_rows else ROWS_UNSORTED
     scratch = batch._scratch if schedule in ("terms", "auto") else None
     _check(_lib.nqs_find_coupled_pairs_async(
         batch.ham.handle, _ptr(batch.U), batch.n, _ptr(batch.work), int(row_begin), row_end,
         SCHEDULES[schedule] | flag, _ptr(scratch), 0 if scratch is None else scratch.numel(),
         _ptr(row_ptr), _ptr(pj), _ptr(pk), capacity, _stream(stream)))
-    return row_ptr, pj[:capacity], pk[:capacity]
+    return row_ptr, pj[:capacity], (None if pk is None else pk[:capacity])
 
 
 def search_timing(on: bool):

@@ -779,12 +779,15 @@ int nqs_find_coupled_pairs_async(const nqs_ham* ham, const uint64_t* U, int64_t 
   schedule = split_schedule(schedule, &sorted);
   int rc = check_work(ham, U, n, work, &L);
   if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(ham, n, schedule))) return rc;
-  if (!row_ptr || capacity < 0 || (capacity > 0 && (!pair_j || !pair_k)))
-    return fail(NQS_ERR_ARG, "null row_ptr or pair arrays");
+  const bool packed = !pair_k;  // one 64-bit word per pair in pair_j (column << 32 | pattern)
+  if (!row_ptr || capacity < 0 || (capacity > 0 && !pair_j)) return fail(NQS_ERR_ARG, "null row_ptr or pair arrays");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t rows = re - rb;
   const int sched = pick_schedule(ham, n, schedule);
   const bool one_pass = scratch && sched == NQS_SCHED_TERMS;
+  if (packed && (sorted || !one_pass))
+    return fail(NQS_ERR_UNSUPPORTED, "packed pairs need LoopOverTerms, a scratch and NQS_ROWS_UNSORTED");
+  if (packed && (((uintptr_t)pair_j) & 7)) return fail(NQS_ERR_ARG, "packed pairs not 8-byte aligned");
   if (one_pass && (((uintptr_t)scratch) & 255)) return fail(NQS_ERR_ARG, "scratch not 256-byte aligned");
   PairScratch sc;
   if (one_pass) {
@@ -1117,7 +1120,8 @@ int nqs_local_energy(const nqs_ham* ham, const uint64_t* U, int64_t n, void* wor
   if (!eloc_re) return fail(NQS_ERR_ARG, "null eloc_re");
   if (b && !eloc_im) return fail(NQS_ERR_ARG, "complex log psi needs eloc_im");
   if (ham->cplx && !eloc_im) return fail(NQS_ERR_ARG, "a complex Hamiltonian needs eloc_im");
-  if (re > rb && (!row_ptr || !pair_j || !pair_k)) return fail(NQS_ERR_ARG, "null pair arrays");
+  if (re > rb && (!row_ptr || !pair_j)) return fail(NQS_ERR_ARG, "null pair arrays");
+  if (!pair_k && (((uintptr_t)pair_j) & 7)) return fail(NQS_ERR_ARG, "packed pairs not 8-byte aligned");
   if (re == rb) return NQS_OK;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = launch_amplitudes(a, b, n, precision, (char*)work, L, s, U);
@@ -1179,7 +1183,9 @@ int nqs_local_energy_backward(const nqs_ham* ham, const uint64_t* U, int64_t n, 
   if (b && (!grad_im || !eloc_im)) return fail(NQS_ERR_ARG, "complex log psi needs grad_im and eloc_im");
   if (ham->cplx && !eloc_im) return fail(NQS_ERR_ARG, "a complex Hamiltonian needs eloc_im");
   const bool pairs_needed = g_re || g_im;
-  if (pairs_needed && re > rb && (!row_ptr || !pair_j || !pair_k || !hdiag))
+  if (pairs_needed && !pair_k && (((uintptr_t)pair_j) & 7))
+    return fail(NQS_ERR_ARG, "packed pairs not 8-byte aligned");
+  if (pairs_needed && re > rb && (!row_ptr || !pair_j || !hdiag))
     return fail(NQS_ERR_ARG, "upstream E_loc gradient needs pairs and hdiag");
   if (re == rb) return NQS_OK;
   cudaStream_t s = (cudaStream_t)stream;

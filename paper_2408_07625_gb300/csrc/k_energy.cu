@@ -216,6 +216,28 @@ template <> struct HStore<PolicyD> {
 // local energies are complex whatever log psi is).
 constexpr int kReal = 0, kCplxPsi = 1, kCplxH = 2;
 
+// Pair lists come as two uint32 arrays (pair_j: column, pair_k: pattern) or,
+// with pair_k == NULL, as packed 64-bit words in pair_j (column << 32 | pattern).
+__device__ __forceinline__ void load_pair(const uint32_t* __restrict__ pj, const uint32_t* __restrict__ pk,
+                                          int64_t q, uint32_t& j, uint32_t& k) {
+  if (pk) {
+    j = __ldg(pj + q);
+    k = __ldg(pk + q);
+  } else {
+    const unsigned long long v = __ldg(reinterpret_cast<const unsigned long long*>(pj) + q);
+    j = (uint32_t)(v >> 32);
+    k = (uint32_t)v;
+  }
+}
+__device__ __forceinline__ uint32_t load_col(const uint32_t* __restrict__ pj, const uint32_t* __restrict__ pk,
+                                             int64_t q) {
+  return pk ? __ldg(pj + q) : (uint32_t)(__ldg(reinterpret_cast<const unsigned long long*>(pj) + q) >> 32);
+}
+__device__ __forceinline__ uint32_t load_pat(const uint32_t* __restrict__ pj, const uint32_t* __restrict__ pk,
+                                             int64_t q) {
+  return pk ? __ldg(pk + q) : (uint32_t)__ldg(reinterpret_cast<const unsigned long long*>(pj) + q);
+}
+
 // a term added to an exact row sum (Fx); a term out of its range flags the status
 template <class Pol>
 __device__ __forceinline__ void fx_term(Fx& a, typename Pol::T t, int32_t* status) {
@@ -246,16 +268,14 @@ __device__ __forceinline__ void energy_rounds(const uint64_t* __restrict__ U, co
   uint32_t jn = 0u, kn = 0u;
   int64_t base = p + 32 * first;
   if (base + lane < p1) {
-    jn = __ldg(pair_j + base + lane);
-    kn = __ldg(pair_k + base + lane);
+    load_pair(pair_j, pair_k, base + lane, jn, kn);
   }
   for (; base < p1; base += 32 * stride) {
     const int64_t q = base + lane;
     const uint32_t j = jn, k = kn;
     const bool have = q < p1 && pair_in_range(M, j, k, status);
     if (q + 32 * stride < p1) {
-      jn = __ldg(pair_j + q + 32 * stride);
-      kn = __ldg(pair_k + q + 32 * stride);
+      load_pair(pair_j, pair_k, q + 32 * stride, jn, kn);
     }
     // N <= 64: the pattern's descriptor and sign mask are one 32-byte record, and the
     // column's bit word rides in its amplitude record (read with the ratio's factor)
@@ -320,9 +340,10 @@ __device__ __forceinline__ void energy_rounds(const uint64_t* __restrict__ U, co
 // the diagonal pair, if the row starts with it: H_xx added by lane 0 (psi(x)/psi(x) = 1)
 template <class Pol, int W, int CX, bool STORE_H>
 __device__ __forceinline__ bool energy_diag(const uint64_t* __restrict__ U, const Melem& M, int64_t i, int64_t p,
-                                            int64_t p1, const uint32_t* __restrict__ pair_k, void* hpair,
+                                            int64_t p1, const uint32_t* __restrict__ pair_j,
+                                            const uint32_t* __restrict__ pair_k, void* hpair,
                                             Fx& acc_re, double& hd, int32_t* status) {
-  if (!(M.has_diag && p < p1 && __ldg(pair_k + p) == 0u)) return false;
+  if (!(M.has_diag && p < p1 && load_pat(pair_j, pair_k, p) == 0u)) return false;
   uint64_t xi[W];
   load_words<W>(U + i * W, xi);
   const typename Pol::T h = melem_diag<Pol, W>(xi, M);
@@ -360,8 +381,8 @@ local_energy_kernel(const uint64_t* __restrict__ U, const Melem M, const char* _
     const int64_t p1 = rp[row + 1] - rp[0];
     Fx acc_re = fx_zero(), acc_im = fx_zero();
     double hd = 0.0;
-    if (warp == 0) energy_diag<Pol, W, CX, STORE_H>(U, M, i, p, p1, pair_k, hpair, acc_re, hd, status);
-    if (M.has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
+    if (warp == 0) energy_diag<Pol, W, CX, STORE_H>(U, M, i, p, p1, pair_j, pair_k, hpair, acc_re, hd, status);
+    if (M.has_diag && p < p1 && load_pat(pair_j, pair_k, p) == 0u) ++p;
     energy_rounds<Pol, W, CX, STORE_H>(U, M, P, Q, i, p, p1, warp, kEnergyWarps, pair_j, pair_k, hpair,
                                        status, acc_re, acc_im);
     const Fx er = fx_warp_sum(acc_re);
@@ -388,7 +409,7 @@ local_energy_kernel(const uint64_t* __restrict__ U, const Melem M, const char* _
     const int64_t p1 = rp[row + 1] - rp[0];
     Fx acc_re = fx_zero(), acc_im = fx_zero();
     double hd = 0.0;
-    if (energy_diag<Pol, W, CX, STORE_H>(U, M, i, p, p1, pair_k, hpair, acc_re, hd, status)) ++p;
+    if (energy_diag<Pol, W, CX, STORE_H>(U, M, i, p, p1, pair_j, pair_k, hpair, acc_re, hd, status)) ++p;
     energy_rounds<Pol, W, CX, STORE_H>(U, M, P, Q, i, p, p1, 0, 1, pair_j, pair_k, hpair, status, acc_re,
                                          acc_im);
     const Fx er = fx_warp_sum(acc_re);
@@ -697,16 +718,16 @@ __device__ __forceinline__ void backward_rounds(const uint64_t* __restrict__ U, 
   uint32_t jn = 0u, kn = 0u;
   int64_t base = p + 32 * first;
   if (base + lane < p1) {
-    jn = __ldg(pair_j + base + lane);
-    if (!LOAD_H) kn = __ldg(pair_k + base + lane);
+    if (LOAD_H) jn = load_col(pair_j, pair_k, base + lane);
+    else load_pair(pair_j, pair_k, base + lane, jn, kn);
   }
   for (; base < p1; base += 32 * stride) {
     const int64_t q = base + lane;
     const uint32_t j = jn, k = kn;
     const bool have = q < p1 && pair_in_range(M, j, k, status);
     if (q + 32 * stride < p1) {
-      jn = __ldg(pair_j + q + 32 * stride);
-      if (!LOAD_H) kn = __ldg(pair_k + q + 32 * stride);
+      if (LOAD_H) jn = load_col(pair_j, pair_k, q + 32 * stride);
+      else load_pair(pair_j, pair_k, q + 32 * stride, jn, kn);
     }
     T h = Pol::zero(), h_im = Pol::zero();
     if (LOAD_H) {
@@ -797,7 +818,7 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
     const int64_t y = row + row_begin;
     int64_t p = rp[row] - rp[0];
     const int64_t p1 = rp[row + 1] - rp[0];
-    if (M.has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
+    if (M.has_diag && p < p1 && load_pat(pair_j, pair_k, p) == 0u) ++p;
     Fx da = fx_zero(), db = fx_zero();
     backward_rounds<Pol, W, CX, LOAD_H>(U, M, P, Q, G, y, p, p1, warp, kEnergyWarps, pair_j, pair_k, hpair,
                                           status, da, db);
@@ -821,7 +842,7 @@ backward_pairs_kernel(const uint64_t* __restrict__ U, const Melem M,
     const int64_t y = row + row_begin;
     int64_t p = rp[row] - rp[0];
     const int64_t p1 = rp[row + 1] - rp[0];
-    if (M.has_diag && p < p1 && __ldg(pair_k + p) == 0u) ++p;
+    if (M.has_diag && p < p1 && load_pat(pair_j, pair_k, p) == 0u) ++p;
     Fx da = fx_zero(), db = fx_zero();
     backward_rounds<Pol, W, CX, LOAD_H>(U, M, P, Q, G, y, p, p1, 0, 1, pair_j, pair_k, hpair, status, da, db);
     const double sa = fx_to_double(fx_warp_sum(da));

@@ -1518,12 +1518,16 @@ cudaError_t launch_pairs_compact(const nqs_ham* ham, const PairScratch& sc, char
   auto* cursor = (unsigned long long*)(stage + L.off_rowcur);
   const int64_t cap = std::min<int64_t>(capacity, sc.max_pairs);
   // rows left in search order: the diagonal pairs go to the keys too, and one
-  // coalesced pass splits every key into pair_j/pair_k
+  // coalesced pass splits every key into pair_j/pair_k; with pair_k == NULL
+  // (packed list, rows unsorted) the keys are written straight into pair_j
+  PairScratch out = sc;
+  const bool packed = !sort_rows && !pair_k;
+  if (packed) out.keys = reinterpret_cast<uint64_t*>(pair_j);
   cudaError_t e = launch_init(kFill, rows, rb, ham->has_diag, nullptr, row_ptr, cursor, 1, pair_j, pair_k, cap,
-                              sc.cursor + 1, status, s, sort_rows ? nullptr : sc.keys);
+                              sc.cursor + 1, status, s, sort_rows ? nullptr : out.keys);
   if (e != cudaSuccess) return e;
-  pairs_scatter_kernel<<<8 * num_sms(), 256, 0, s>>>(sc, rb, rb + rows, row_ptr, cursor, status);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  pairs_scatter_kernel<<<8 * num_sms(), 256, 0, s>>>(out, rb, rb + rows, row_ptr, cursor, status);
+  if ((e = cudaGetLastError()) != cudaSuccess || packed) return e;
   if (!sort_rows) {
     split_keys_kernel<<<8 * num_sms(), 256, 0, s>>>(sc.keys, row_ptr, rows, pair_j, pair_k, status);
     return cudaGetLastError();

@@ -122,7 +122,7 @@ def test_every_row_against_oracle(name):
 
 def test_bench_step_configuration_h56():
     """The form bench.py times at 56 qubits: the no-wait search with rows left in
-    search order, then E_loc^var, E^var and the adjoint on those lists.  Every row's
+    search order and each pair packed in one 64-bit word, then E_loc^var, E^var and the adjoint on those lists.  Every row's
     pair count and column set against the oracle's, and E_loc^var / E^var bitwise
     equal to the canonical (sorted-row) path, which the test above holds to the
     oracle, in both precisions."""
@@ -131,14 +131,15 @@ def test_bench_step_configuration_h56():
     for prec, tol in (("fp64", TOL64), ("fp32c", TOL32)):
         ref = nqs.evaluate(batch, inst.logpsi_re, None, prec)
         total = int(ref["n_pairs"])
-        rp, pj, pk = nqs.coupled_pairs_async(batch, total + 1024, sort_rows=False)
-        er, ei, hd = nqs.local_energy(batch, inst.logpsi_re, None, (rp, pj, pk), prec)
+        rp, words, _ = nqs.coupled_pairs_async(batch, total + 1024, sort_rows=False, packed=True)
+        er, ei, hd = nqs.local_energy(batch, inst.logpsi_re, None, (rp, words, None), prec)
         ev = nqs.variational_energy(batch, inst.logpsi_re, er)
         batch.status()
         rph = rp.cpu().numpy()
         assert int(rph[-1]) == int(g["n_pairs"][0])
         assert np.array_equal(np.diff(rph), g["count"])
-        dig = fs.set_digest_np(rph, pj[:total].cpu().numpy().view(np.uint32))
+        cols = (words[:total].cpu().numpy().view(np.uint64) >> np.uint64(32)).astype(np.uint32)
+        dig = fs.set_digest_np(rph, cols)
         assert np.array_equal(dig, g["digest"])
         assert torch.equal(er, ref["eloc_re"]) and torch.equal(hd, ref["hdiag"])
         assert torch.equal(ev, ref["evar"])

@@ -192,3 +192,49 @@ def test_step_captured_in_a_cuda_graph():
         ref.status()
         for x, y in zip(got, [er, hd, ev, gr]):
             assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_packed_pairs(prec):
+    """Pairs as one 64-bit word each (column << 32 | pattern), written by the no-wait
+    search with no split pass: the same pairs row by row as the two-array form, and
+    E_loc^var, E^var and the adjoint (stored and recomputed H) bitwise the same."""
+    inst = _inst()
+    ham, batch = gpu_objects(inst)
+    g = np.random.default_rng(11).normal(0.0, 1.0, batch.n)
+    canon = nqs.coupled_pairs(batch)
+    total = int(canon[1].numel())
+    cap = total + 512
+    rp, words, none = nqs.coupled_pairs_async(batch, cap, sort_rows=False, packed=True)
+    batch.status()
+    assert none is None and words.dtype == torch.int64
+    assert torch.equal(rp, canon[0])
+    w = words[:total].cpu().numpy().view(np.uint64)
+    cols, pats = (w >> np.uint64(32)).astype(np.int64), (w & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    r = rp.cpu().numpy()
+    cj = canon[1].cpu().numpy().view(np.uint32).astype(np.int64)
+    ck = canon[2].cpu().numpy().view(np.uint32).astype(np.int64)
+    has_diag = ham.info["has_diag"]
+    for i in range(batch.n):
+        a, b = r[i], r[i + 1]
+        if has_diag:
+            assert cols[a] == i and pats[a] == 0
+            a += 1
+        o = np.lexsort((pats[a:b], cols[a:b]))
+        assert np.array_equal(cols[a:b][o], cj[a:b]) and np.array_equal(pats[a:b][o], ck[a:b])
+    for store_h in (True, False):
+        res = []
+        for pairs in (canon, (rp, words, None)):
+            hp = nqs.pair_h_buffer(int(pairs[1].numel()), prec, "cuda") if store_h else None
+            er, ei, hd = nqs.local_energy(batch, inst.logpsi_re, None, pairs, prec, hpair=hp)
+            ev = nqs.variational_energy(batch, inst.logpsi_re, er)
+            gr, _ = nqs.local_energy_backward(batch, inst.logpsi_re, None, er, ei, hd, ev, g, None, [1.0], pairs,
+                                              prec, hpair=hp)
+            batch.status()
+            res.append([er.clone(), hd.clone(), ev.clone(), gr.clone()])
+        for x, y in zip(*res):
+            assert torch.equal(x, y)
+    # the packed form needs rows left in search order and the one-pass search
+    with pytest.raises(nqs.NQSError) as err:
+        nqs.coupled_pairs_async(batch, cap, sort_rows=True, packed=True)
+    assert err.value.code == -2

@@ -268,8 +268,11 @@ int nqs_batch_plan(const nqs_instance* insts, int n_inst, int precision, int fla
     I.planned_pairs = np_terms;
     I.capacity = np_terms + np_terms / 4 + 4096;
     I.scratch_bytes = pair_scratch_bytes(n, I.capacity);
-    if ((e = cudaMalloc((void**)&I.pair_j, 4 * I.capacity)) != cudaSuccess ||
-        (e = cudaMalloc((void**)&I.pair_k, 4 * I.capacity)) != cudaSuccess ||
+    // LoopOverTerms instances keep their pairs packed (one 64-bit word each, pair_k unused):
+    // the compaction writes them as the energy and adjoint kernels read them
+    const bool packed = I.schedule == NQS_SCHED_TERMS;
+    if ((e = cudaMalloc((void**)&I.pair_j, (packed ? 8 : 4) * I.capacity)) != cudaSuccess ||
+        (!packed && (e = cudaMalloc((void**)&I.pair_k, 4 * I.capacity)) != cudaSuccess) ||
         (e = cudaMalloc(&I.scratch, I.scratch_bytes)) != cudaSuccess) {
       rc = fail(NQS_ERR_OOM, "cudaMalloc in nqs_batch_plan");
       break;

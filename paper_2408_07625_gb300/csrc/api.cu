@@ -779,7 +779,7 @@ int nqs_find_coupled_pairs_async(const nqs_ham* ham, const uint64_t* U, int64_t 
   schedule = split_schedule(schedule, &sorted);
   int rc = check_work(ham, U, n, work, &L);
   if (rc || (rc = check_rows(n, rb, re)) || (rc = check_schedule(ham, n, schedule))) return rc;
-  const bool packed = !pair_k;  // one 64-bit word per pair in pair_j (column << 32 | pattern)
+  const bool packed = pair_j && !pair_k;  // one 64-bit word per pair in pair_j (column << 32 | pattern)
   if (!row_ptr || capacity < 0 || (capacity > 0 && !pair_j)) return fail(NQS_ERR_ARG, "null row_ptr or pair arrays");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t rows = re - rb;

@@ -238,3 +238,26 @@ def test_packed_pairs(prec):
     with pytest.raises(nqs.NQSError) as err:
         nqs.coupled_pairs_async(batch, cap, sort_rows=True, packed=True)
     assert err.value.code == -2
+
+
+def test_async_count_only():
+    """No pair buffers at all (capacity 0): the row offsets are still written and the
+    status reports that the pairs did not fit."""
+    inst = _inst()
+    ham, batch = gpu_objects(inst)
+    rp = nqs.coupled_pairs(batch)[0]
+    nqs.coupled_pairs(batch, sort_rows=False)  # sizes the batch's scratch
+    row_ptr = torch.empty(batch.n + 1, dtype=torch.int64, device="cuda")
+    lib = nqs.load_library()
+    for sched in (nqs.SCHEDULES["terms"], nqs.SCHEDULES["terms"] | nqs.ROWS_UNSORTED):
+        rc = lib.nqs_find_coupled_pairs_async(batch.ham.handle, nqs._ptr(batch.U), batch.n, nqs._ptr(batch.work), 0,
+                                              batch.n, sched, nqs._ptr(batch._scratch), batch._scratch.numel(),
+                                              nqs._ptr(row_ptr), None, None, 0, nqs._stream(None))
+        assert rc == 0
+        with pytest.raises(nqs.NQSError) as err:
+            batch.status()
+        assert err.value.code == -4
+        assert torch.equal(row_ptr, rp)
+    # a call with room clears the condition
+    nqs.coupled_pairs_async(batch, int(rp[-1]), sort_rows=False)
+    batch.status()
